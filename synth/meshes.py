@@ -1,0 +1,203 @@
+"""Seeded synthetic conductor meshes.
+
+These generators produce the inputs of the method only: vertex coordinates,
+triangle connectivity (counter-clockwise seen from outside, so the right-hand
+normal points out of the conductor), a conductor id per triangle, the
+conductivity of each conductor and the port contact sets.  They hold none of
+the method's arithmetic and are shared by the oracle, the tests and the bench.
+
+A port is a pair (source triangles, sink triangles) on one conductor, the
+electrode faces between which a unit voltage source is applied (Sec. III-C of
+the paper: a voltage source between two circuit nodes; a contact face made of
+many triangles is one node).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+
+@dataclass
+class Mesh:
+    xyz: np.ndarray          # float64 [nv, 3], metres
+    tri: np.ndarray          # int32   [nt, 3], CCW seen from outside
+    cond: np.ndarray         # int32   [nt], conductor id
+    sigma: np.ndarray        # float64 [ncond], S/m
+    ports: list = field(default_factory=list)  # [(src int32[], sink int32[])]
+    name: str = ""
+
+    @property
+    def nv(self):
+        return int(self.xyz.shape[0])
+
+    @property
+    def nt(self):
+        return int(self.tri.shape[0])
+
+    @property
+    def ncond(self):
+        return int(self.sigma.shape[0])
+
+    def bbox(self):
+        return self.xyz.min(axis=0), self.xyz.max(axis=0)
+
+
+def _orient(xyz, tris, outward):
+    """Flip triangles whose right-hand normal points against `outward`."""
+    tris = np.asarray(tris, dtype=np.int64)
+    p0, p1, p2 = xyz[tris[:, 0]], xyz[tris[:, 1]], xyz[tris[:, 2]]
+    n = np.cross(p1 - p0, p2 - p0)
+    flip = np.einsum("ij,ij->i", n, outward) < 0
+    tris[flip] = tris[flip][:, [0, 2, 1]]
+    return tris
+
+
+def box_mesh(L, W, T, nx, ny, nz, jitter=0.0, seed=1, sigma=5.8e7, origin=(0.0, 0.0, 0.0),
+             with_port=True, name="box"):
+    """Closed triangulated surface of the box [0,L]x[0,W]x[0,T] (+origin).
+
+    Each face is a structured grid of quads (nx, ny, nz divisions along x, y,
+    z), each quad split into two triangles with alternating diagonals.  Face
+    vertices that do not lie on a box edge are moved in-plane by a seeded
+    uniform jitter of +-`jitter` times the local spacing.  The port (if
+    requested) drives current from the x=0 end face to the x=L end face.
+    """
+    rng = np.random.default_rng(seed)
+    hx, hy, hz = L / nx, W / ny, T / nz
+    vid = {}
+    verts = []
+
+    def vertex(i, j, k):
+        key = (i, j, k)
+        if key not in vid:
+            vid[key] = len(verts)
+            verts.append((i, j, k))
+        return vid[key]
+
+    faces = []   # (quad vertex ids, outward normal, face tag)
+    # each face: fixed axis a at value v, two running axes (u, w)
+    dims = (nx, ny, nz)
+    for axis in range(3):
+        for side in (0, 1):
+            fixed = side * dims[axis]
+            ua, wa = [a for a in range(3) if a != axis]
+            nrm = np.zeros(3)
+            nrm[axis] = 1.0 if side else -1.0
+            tag = 2 * axis + side
+            for u in range(dims[ua]):
+                for w in range(dims[wa]):
+                    def lat(du, dw):
+                        c = [0, 0, 0]
+                        c[axis] = fixed
+                        c[ua] = u + du
+                        c[wa] = w + dw
+                        return vertex(*c)
+                    q = (lat(0, 0), lat(1, 0), lat(1, 1), lat(0, 1))
+                    faces.append((q, nrm, tag, (u + w) % 2))
+    lattice = np.array(verts, dtype=np.float64)
+    xyz = lattice * np.array([hx, hy, hz]) + np.asarray(origin, dtype=np.float64)
+    if jitter > 0.0:
+        for n, (i, j, k) in enumerate(verts):
+            on = [i in (0, nx), j in (0, ny), k in (0, nz)]
+            if sum(on) != 1:
+                continue          # on a box edge or corner: keep
+            axis = on.index(True)
+            for a, h in zip(range(3), (hx, hy, hz)):
+                if a != axis:
+                    xyz[n, a] += rng.uniform(-jitter, jitter) * h
+    tris, outward, tags = [], [], []
+    for (a, b, c, d), nrm, tag, par in faces:
+        if par == 0:
+            tris += [(a, b, c), (a, c, d)]
+        else:
+            tris += [(a, b, d), (b, c, d)]
+        outward += [nrm, nrm]
+        tags += [tag, tag]
+    tris = _orient(xyz, tris, np.array(outward))
+    tags = np.array(tags)
+    mesh = Mesh(xyz=xyz, tri=tris.astype(np.int32), cond=np.zeros(len(tris), np.int32),
+                sigma=np.array([sigma], dtype=np.float64), name=name)
+    if with_port:
+        src = np.nonzero(tags == 0)[0].astype(np.int32)   # x = 0 face
+        snk = np.nonzero(tags == 1)[0].astype(np.int32)   # x = L face
+        mesh.ports = [(src, snk)]
+    return mesh
+
+
+def wire_array_mesh(n_wires, radius, length, pitch, n_sides=16, seg_len=None, n_seg=None,
+                    jitter=0.0, seed=2, sigma=4.1e7, name="wires"):
+    """Parallel round wires along x, polygonal cross-section with `n_sides` sides.
+
+    Wire w has its axis on (y, z) = (w * pitch, 0).  The lateral surface is a
+    ring-by-ring structured quad mesh split into triangles; each end cap is a
+    fan around a centre vertex.  Interior ring positions get a seeded axial
+    jitter of +-`jitter` times the segment length.  Port w drives wire w from
+    its x=0 cap (source) to its x=length cap (sink).
+    """
+    rng = np.random.default_rng(seed)
+    if n_seg is None:
+        n_seg = max(1, int(round(length / seg_len)))
+    xyz, tris, outward, cond, ports = [], [], [], [], []
+    th = 2.0 * np.pi * np.arange(n_sides) / n_sides
+    for w in range(n_wires):
+        y0 = w * pitch
+        base = len(xyz)
+        xs = np.linspace(0.0, length, n_seg + 1)
+        if jitter > 0.0 and n_seg > 1:
+            xs[1:-1] += rng.uniform(-jitter, jitter, n_seg - 1) * (length / n_seg)
+        for s in range(n_seg + 1):
+            for k in range(n_sides):
+                xyz.append((xs[s], y0 + radius * np.cos(th[k]), radius * np.sin(th[k])))
+        c0 = len(xyz)
+        xyz.append((0.0, y0, 0.0))
+        c1 = len(xyz)
+        xyz.append((length, y0, 0.0))
+
+        def rv(s, k):
+            return base + s * n_sides + (k % n_sides)
+        t_start = len(tris)
+        for s in range(n_seg):
+            for k in range(n_sides):
+                a, b, c, d = rv(s, k), rv(s + 1, k), rv(s + 1, k + 1), rv(s, k + 1)
+                mid = 0.5 * (th[k] + th[(k + 1) % n_sides] + (2 * np.pi if k == n_sides - 1 else 0.0))
+                nrm = np.array([0.0, np.cos(mid), np.sin(mid)])
+                if (s + k) % 2 == 0:
+                    tris += [(a, b, c), (a, c, d)]
+                else:
+                    tris += [(a, b, d), (b, c, d)]
+                outward += [nrm, nrm]
+        src = []
+        for k in range(n_sides):
+            src.append(len(tris))
+            tris.append((c0, rv(0, k), rv(0, k + 1)))
+            outward.append(np.array([-1.0, 0.0, 0.0]))
+        snk = []
+        for k in range(n_sides):
+            snk.append(len(tris))
+            tris.append((c1, rv(n_seg, k), rv(n_seg, k + 1)))
+            outward.append(np.array([1.0, 0.0, 0.0]))
+        cond += [w] * (len(tris) - t_start)
+        ports.append((np.array(src, np.int32), np.array(snk, np.int32)))
+    xyz = np.array(xyz, dtype=np.float64)
+    tris = _orient(xyz, tris, np.array(outward))
+    return Mesh(xyz=xyz, tri=tris.astype(np.int32), cond=np.array(cond, np.int32),
+                sigma=np.full(n_wires, sigma, dtype=np.float64), ports=ports, name=name)
+
+
+def merge(meshes, name="merged"):
+    """Concatenate meshes into one multi-conductor mesh (ids and ports shifted)."""
+    xyz, tri, cond, sigma, ports = [], [], [], [], []
+    nv = nt = nc = 0
+    for m in meshes:
+        xyz.append(m.xyz)
+        tri.append(m.tri + nv)
+        cond.append(m.cond + nc)
+        sigma.append(m.sigma)
+        for s, k in m.ports:
+            ports.append((s + nt, k + nt))
+        nv += m.nv
+        nt += m.nt
+        nc += m.ncond
+    return Mesh(xyz=np.concatenate(xyz), tri=np.concatenate(tri).astype(np.int32),
+                cond=np.concatenate(cond).astype(np.int32), sigma=np.concatenate(sigma),
+                ports=ports, name=name)

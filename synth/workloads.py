@@ -1,0 +1,65 @@
+"""Named synthetic workloads (geometry, frequencies, grid sizes) and seeded vectors.
+
+The shapes follow the paper's example classes: a straight rectangular copper
+interconnect (Sec. V-A) and an array of bond wires (Sec. V-B).  All sizes are
+in metres, conductivities in S/m, frequencies in Hz.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .meshes import box_mesh, wire_array_mesh, merge
+
+UM = 1e-6
+
+
+def bar_1500():
+    """Cu bar 1000 x 20 x 10 um, ~1,500 triangles (8 x 10 x 10 um cells),
+    in-plane jitter +-15% (seed 1), one port between the x end faces.
+    Frequency 1 GHz; pFFT grid 64 x 16 x 16."""
+    m = box_mesh(1000 * UM, 20 * UM, 10 * UM, 125, 2, 1, jitter=0.15, seed=1, sigma=5.8e7,
+                 name="bar_1000x20x10um")
+    return dict(mesh=m, freqs=np.array([1e9]), grid=(64, 16, 16), name="bar_1000x20x10um_1.5k")
+
+
+def bondwires_40k():
+    """8 Au round wires, r = 12.5 um (16-gon), 2 mm long, pitch 100 um,
+    axial segment 12.8 um (156 rings, ~40k triangles), axial jitter +-10%
+    (seed 2), 8 ports (one per wire, end cap to end cap), 16 log-spaced
+    frequencies 1 MHz - 10 GHz; pFFT grid 128 x 64 x 32."""
+    m = wire_array_mesh(8, 12.5 * UM, 2000 * UM, 100 * UM, n_sides=16, n_seg=156,
+                        jitter=0.10, seed=2, sigma=4.1e7, name="bondwires_8x2mm")
+    return dict(mesh=m, freqs=np.logspace(6, 10, 16), grid=(128, 64, 32),
+                name="bondwires_8x2mm_40k")
+
+
+def tiny_bar(nx=10, ny=2, nz=1, L=100 * UM, W=20 * UM, T=10 * UM, jitter=0.15, seed=3):
+    """Small Cu bar for dense checks (128 triangles at the default sizes)."""
+    return box_mesh(L, W, T, nx, ny, nz, jitter=jitter, seed=seed, sigma=5.8e7, name="tiny_bar")
+
+
+def tiny_wires(n_wires=2, n_sides=8, n_seg=6, length=120 * UM, radius=10 * UM, pitch=40 * UM,
+               seed=4):
+    """Two short polygonal wires, two ports (multi-port checks)."""
+    return wire_array_mesh(n_wires, radius, length, pitch, n_sides=n_sides, n_seg=n_seg,
+                           jitter=0.1, seed=seed, sigma=4.1e7, name="tiny_wires")
+
+
+def tiny_two_bars():
+    """Two parallel bars side by side as separate conductors."""
+    a = box_mesh(100 * UM, 10 * UM, 10 * UM, 8, 1, 1, jitter=0.1, seed=5, name="a")
+    b = box_mesh(100 * UM, 10 * UM, 10 * UM, 8, 1, 1, jitter=0.1, seed=6, name="b",
+                 origin=(0.0, 30 * UM, 0.0))
+    return merge([a, b], name="tiny_two_bars")
+
+
+WORKLOADS = {
+    "bar_1000x20x10um_1.5k": bar_1500,
+    "bondwires_8x2mm_40k": bondwires_40k,
+}
+
+
+def complex_gaussian(n, nrhs=1, seed=7):
+    """Seeded complex Gaussian vectors, shape [nrhs, n], complex128."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((nrhs, n)) + 1j * rng.standard_normal((nrhs, n))) / np.sqrt(2.0)
