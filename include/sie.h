@@ -1,0 +1,207 @@
+/*
+ * sie.h - C ABI of the GB300 pFFT / loop-basis GMRES library (libsie).
+ *
+ * The library computes the port impedance of conductors described by a
+ * triangle surface mesh with the magneto-quasi-static surface integral
+ * equation of arXiv 2210.04891:
+ *   Eq. (MPIE3)/(Zb): Z_b = Z_s G + (j w mu0 / 4 pi) Lt, branch = shared edge,
+ *   Eq. (FinalME):    A Z_b A^T I_l = V_l in fundamental-loop space,
+ *   Eq. (LoopWithP):  left-preconditioned GMRES with P = A diag(Z_b) A^T,
+ *   Eq. (Lb):         Lt applied by the pre-corrected FFT, Lt ~ L_d + I H B.
+ *
+ * Conventions shared by every call
+ *   - Units: metres, siemens per metre, hertz, radians per second, ohms.
+ *   - Complex numbers are interleaved (re, im) pairs, FP64 unless stated.
+ *   - Return value: SIE_OK (0) or a negative SIE_ERR_* code; nothing aborts
+ *     or exits.  sie_last_error() gives a message for the calling thread.
+ *   - Host input arrays are copied; the caller keeps ownership.  Handles are
+ *     owned by the library and released by the matching *_destroy call
+ *     (destroying NULL is a no-op).
+ *   - Device pointers are CUDA device addresses on the device current when the
+ *     plan was created.  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ *     stream); work is enqueued on it and the call returns when the results are
+ *     ready unless stated otherwise.
+ *   - A plan may be used by one thread at a time; separate plans are
+ *     independent.
+ */
+#ifndef SIE_H
+#define SIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SIE_OK = 0,
+    SIE_ERR_ARG = -1,           /* invalid argument or size                      */
+    SIE_ERR_NONMANIFOLD = -2,   /* an edge shared by more than two triangles     */
+    SIE_ERR_BAD_PORT = -3,      /* empty contact, source == sink, or the two on
+                                   separate conductors                           */
+    SIE_ERR_OOM = -4,           /* host or device allocation failed              */
+    SIE_ERR_CUDA = -5,          /* a CUDA call failed (message has the detail)   */
+    SIE_ERR_NOT_CONVERGED = -6, /* GMRES hit its iteration cap                   */
+    SIE_ERR_BREAKDOWN = -7,     /* zero pivot in the preconditioner or a
+                                   non-finite value in the Krylov recurrence     */
+    SIE_ERR_TIMEOUT = -8        /* a bounded device wait ran out                 */
+};
+
+enum { SIE_SPACE_LOOP = 0, SIE_SPACE_BRANCH = 1 };
+enum { SIE_PREC_FP64 = 0, SIE_PREC_MIXED = 1 };
+enum { SIE_KERNEL_STATIC = 0 };
+
+typedef struct sie_mesh sie_mesh;
+typedef struct sie_loops sie_loops;
+typedef struct pfft_plan pfft_plan;
+typedef struct { double re, im; } sie_c64;
+
+/* A port (Sec. III-C): a unit voltage source between two contact faces.
+ * Each face is a set of triangle indices contracted into one circuit node. */
+typedef struct {
+    const int32_t *src;
+    int32_t n_src;
+    const int32_t *sink;
+    int32_t n_sink;
+} sie_port;
+
+typedef struct {
+    int64_t n_nodes;     /* circuit nodes after contact contraction            */
+    int64_t n_branches;  /* b: edges shared by two triangles (port links not
+                            counted)                                           */
+    int64_t n_comp;      /* s: separate conductors                              */
+    int64_t n_loops;     /* l = b - n + s + p (Sec. III-A, III-C)               */
+    int64_t n_ports;     /* p                                                  */
+    int64_t tree_depth;  /* depth of the breadth-first spanning forest         */
+    int64_t nnz_A;       /* nonzeros of the loop matrix A (sum of loop lengths)*/
+} sie_loop_stats;
+
+/* pFFT parameters (Sec. IV-B leaves them open; these are the readings used). */
+typedef struct {
+    int32_t grid[3];       /* N_x, N_y, N_z grid nodes spanning the mesh box   */
+    int32_t order;         /* stencil order O_s per axis, 2..4                 */
+    double near_factor;    /* near radius = max(near_factor * max h,           */
+    double near_min_diam;  /*                   near_min_diam * max diameter)  */
+    int32_t n_touch;       /* outer Gauss order for pairs sharing a vertex     */
+    int32_t kernel;        /* SIE_KERNEL_STATIC: 1/(4 pi R)                    */
+    double h0;             /* kernel value at zero grid offset (result does not
+                              depend on it; kept for the independence check)   */
+} pfft_params;
+
+typedef struct {
+    double tol;            /* preconditioned relative residual, e.g. 1e-6      */
+    int32_t restart;       /* GMRES(m) restart length                          */
+    int32_t max_iter;      /* iteration cap per right-hand side               */
+    int32_t precond;       /* 0: none, 1: P = A diag(Z_b) A^T (Eq. Precond)    */
+    int32_t prec;          /* SIE_PREC_FP64 or SIE_PREC_MIXED                  */
+} sie_solve_opts;
+
+typedef struct {
+    int32_t iterations_max;   /* largest iteration count over right-hand sides */
+    int32_t iterations_sum;
+    int32_t n_not_converged;
+    double residual_max;      /* final preconditioned relative residual        */
+    double seconds;           /* wall time of the solve phase                  */
+    int64_t matvecs;          /* right-hand-side matvecs applied               */
+} sie_solve_stats;
+
+/* Mesh (Sec. II-B): nv vertices xyz[nv][3]; nt triangles tri[nt][3] whose
+ * right-hand normal points out of the conductor; cond_id[nt] in [0, ncond);
+ * sigma[ncond] > 0.  Errors: SIE_ERR_ARG for out-of-range indices, degenerate
+ * triangles or non-positive conductivity. */
+int sie_mesh_load(const double *xyz, int64_t nv, const int32_t *tri, int64_t nt,
+                  const int32_t *cond_id, const double *sigma, int32_t ncond, sie_mesh **out);
+void sie_mesh_destroy(sie_mesh *m);
+
+/* Circuit graph and fundamental loops (Sec. II-D, III): nodes = triangles
+ * (contacts contracted), branches = shared edges oriented from the lower to the
+ * higher triangle index, breadth-first spanning forest rooted at each part's
+ * lowest node id, one loop per link, port links last.  `st` may be NULL.
+ * Errors: SIE_ERR_NONMANIFOLD, SIE_ERR_BAD_PORT, SIE_ERR_ARG. */
+int loop_basis_build(const sie_mesh *m, const sie_port *ports, int32_t np, sie_loops **out,
+                     sie_loop_stats *st);
+void sie_loops_destroy(sie_loops *l);
+
+/* Export the loop matrix A (Eq. VolT) as CSR over loops: row_ptr[n_loops + 1],
+ * col[nnz_A] (branch id; port p is column n_branches + p), val[nnz_A] (+1/-1),
+ * columns of a row in the order the loop is walked.  Arrays are caller-owned
+ * host memory of the sizes in sie_loop_stats; any pointer may be NULL to skip.
+ * Also exports each branch's (T+, T-) pair when br_tri[2 * n_branches] != NULL. */
+int sie_loops_export(const sie_loops *l, int64_t *row_ptr, int32_t *col, int8_t *val,
+                     int32_t *br_tri);
+
+/* Build the pFFT operator on the current device (Sec. IV-B): grid, stencils,
+ * kernel spectrum, near list, closed-form near-field integrals minus the grid's
+ * own near contribution (L_d = L_direct - (I H B)_near), Gram blocks and the
+ * preconditioner's diagonal.  Allocates device memory for the plan's lifetime.
+ * Errors: SIE_ERR_ARG (grid < 2 * order in an axis, order outside 2..4),
+ * SIE_ERR_OOM, SIE_ERR_CUDA. */
+int pfft_plan_create(const sie_mesh *m, const sie_loops *l, const pfft_params *p, void *cuda_stream,
+                     pfft_plan **out);
+void pfft_plan_destroy(pfft_plan *p);
+
+/* The product of Eq. (FinalME) for nrhs right-hand sides at once (Sec. IV-A/B):
+ *   space = SIE_SPACE_LOOP:   y = A [Z_s G + c_L (L_d + I H B)] A^T x,
+ *                              x, y device complex128 [nrhs][n_loops];
+ *   space = SIE_SPACE_BRANCH: y = [Z_s G + c_L (L_d + I H B)] x,
+ *                              x, y device complex128 [nrhs][n_branches];
+ * with c_L = j w mu0 / (4 pi) and Z_s = (1 + j) sqrt(w mu0 / (2 sigma)) of each
+ * conductor, w = omega[r] (host array, one angular frequency per right-hand
+ * side).  prec = SIE_PREC_FP64 computes every step in FP64; SIE_PREC_MIXED runs
+ * projection, FFT convolution, interpolation and the near field in FP32 and the
+ * loop/branch maps and output in FP64.  x and y must not overlap.  Scratch is
+ * plan-owned and grown on demand (SIE_ERR_OOM if that fails). */
+int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega,
+                int32_t space, int32_t prec, void *cuda_stream);
+
+/* Apply the preconditioner of Eq. (Precond), z = P^-1 y with
+ * P = A diag(Z_b) A^T (port links carry no impedance), for nrhs loop-space
+ * vectors y, z (device complex128 [nrhs][n_loops]) at omega[r].  Factorises
+ * P(omega) on first use of each distinct omega set.  Errors: SIE_ERR_BREAKDOWN
+ * for a zero pivot. */
+int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
+                       void *cuda_stream);
+
+/* Port impedance extraction (Sec. III-C, V): for every frequency f and every
+ * port q a unit source in port q's loop, GMRES on Eq. (LoopWithP), then
+ * Y[f][p][q] = loop current of port p, Z(f) = Y(f)^-1.  ports[np] selects the
+ * plan's ports (indices into the ports given to loop_basis_build).
+ * Z_out: caller-owned host [nf][np][np].  On SIE_ERR_NOT_CONVERGED Z_out and
+ * st are still filled.  `st` may be NULL. */
+int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
+              const sie_solve_opts *opts, sie_c64 *Z_out, sie_solve_stats *st);
+
+/* Plan introspection for tests and benchmarks: sizes (any pointer may be NULL). */
+int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, int64_t *n_tri,
+                   int64_t *n_near_pairs, double *grid_h /* [3] */, double *r_near,
+                   int64_t *device_bytes);
+
+/* Copy one of the plan's setup arrays to caller-owned host memory (for checks):
+ *   SIE_EXPORT_NEAR_PTR  int64  [n_tri + 1]   near-list row offsets (rows = triangles)
+ *   SIE_EXPORT_NEAR_COL  int32  [n_near]      near triangles of each row, ascending
+ *   SIE_EXPORT_LD        double [n_near][3][3] pre-corrected blocks L_direct - (I H B)
+ *   SIE_EXPORT_LDIRECT   double [n_near][3][3] direct blocks
+ *   SIE_EXPORT_HHAT      double [N_y+1][N_z+1][N_x+1] kernel spectrum / (8 N_x N_y N_z),
+ *                        index k folded to min(k, 2N - k) per axis
+ *   SIE_EXPORT_START     int32  [n_tri][7][3] stencil start node of each sample point
+ * capacity_bytes is the size of host_out; SIE_ERR_ARG if it is too small. */
+enum { SIE_EXPORT_NEAR_PTR = 0, SIE_EXPORT_NEAR_COL = 1, SIE_EXPORT_LD = 2, SIE_EXPORT_LDIRECT = 3,
+       SIE_EXPORT_HHAT = 4, SIE_EXPORT_START = 5 };
+int pfft_plan_export(const pfft_plan *p, int32_t what, void *host_out, int64_t capacity_bytes);
+
+/* Step 2 of Sec. IV-B alone: phi_g = H Q_g for nbatch grids, in place.
+ * grid: device [nbatch][N_x][N_y][N_z] complex (complex128 for SIE_PREC_FP64,
+ * complex64 for SIE_PREC_MIXED), node (i, j, k) at h-spaced offsets from the
+ * mesh box's low corner.  Aperiodic convolution with H(d) = 1/|d o h| (h0 at
+ * d = 0) via the zero-padded FFT. */
+int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream);
+
+/* Number of this library's kernel launches since the plan was created. */
+int64_t pfft_plan_launches(const pfft_plan *p);
+
+const char *sie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIE_H */

@@ -1,0 +1,211 @@
+"""Python binding of libsie: argument marshalling only.
+
+Every step of the method runs in the library (host graph code and CUDA
+kernels); this module converts numpy/torch arguments to the C ABI of
+include/sie.h and raises SieError on any non-zero return code.  Device
+buffers are torch tensors (complex128, CUDA); streams are torch streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native as N
+from .native import check, lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Mesh:
+    def __init__(self, xyz, tri, cond, sigma):
+        self._keep = [np.ascontiguousarray(xyz, np.float64), np.ascontiguousarray(tri, np.int32),
+                      np.ascontiguousarray(cond, np.int32), np.ascontiguousarray(sigma, np.float64)]
+        xyz, tri, cond, sigma = self._keep
+        h = ctypes.c_void_p()
+        check(lib().sie_mesh_load(_ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], _ptr(cond), _ptr(sigma),
+                                  sigma.shape[0], ctypes.byref(h)))
+        self.h = h
+        self.nt = tri.shape[0]
+
+    @classmethod
+    def from_synth(cls, m):
+        return cls(m.xyz, m.tri, m.cond, m.sigma)
+
+    def __del__(self):
+        if getattr(self, "h", None) and lib is not None:
+            lib().sie_mesh_destroy(self.h)
+            self.h = None
+
+
+def sie_mesh_load(xyz, tri, cond, sigma):
+    return Mesh(xyz, tri, cond, sigma)
+
+
+class Loops:
+    def __init__(self, mesh: Mesh, ports):
+        self.mesh = mesh
+        arrs = []
+        P = (N.SiePort * max(1, len(ports)))()
+        for i, (src, snk) in enumerate(ports):
+            s = np.ascontiguousarray(src, np.int32)
+            k = np.ascontiguousarray(snk, np.int32)
+            arrs += [s, k]
+            P[i].src = s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            P[i].n_src = s.shape[0]
+            P[i].sink = k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            P[i].n_sink = k.shape[0]
+        st = N.SieLoopStats()
+        h = ctypes.c_void_p()
+        check(lib().loop_basis_build(mesh.h, P, len(ports), ctypes.byref(h), ctypes.byref(st)))
+        self.h = h
+        self.stats = {f: getattr(st, f) for f, _ in N.SieLoopStats._fields_}
+        self.nl = st.n_loops
+        self.nb = st.n_branches
+        self.np = st.n_ports
+
+    def export(self):
+        """(row_ptr, col, val, br_tri) of the loop matrix A and the branch triangles."""
+        s = self.stats
+        row_ptr = np.zeros(s["n_loops"] + 1, np.int64)
+        col = np.zeros(s["nnz_A"], np.int32)
+        val = np.zeros(s["nnz_A"], np.int8)
+        br = np.zeros((s["n_branches"], 2), np.int32)
+        check(lib().sie_loops_export(self.h, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(br)))
+        return row_ptr, col, val, br
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().sie_loops_destroy(self.h)
+            self.h = None
+
+
+def loop_basis_build(mesh, ports):
+    return Loops(mesh, ports)
+
+
+DEFAULT_PARAMS = dict(grid=(16, 8, 8), order=3, near_factor=4.0, near_min_diam=2.0, n_touch=16, h0=0.0)
+
+
+class Plan:
+    def __init__(self, mesh: Mesh, loops: Loops, params=None, stream=None):
+        import torch
+        p = dict(DEFAULT_PARAMS)
+        p.update(params or {})
+        self.params = p
+        cp = N.PfftParams()
+        for i in range(3):
+            cp.grid[i] = int(p["grid"][i])
+        cp.order = int(p["order"])
+        cp.near_factor = float(p["near_factor"])
+        cp.near_min_diam = float(p["near_min_diam"])
+        cp.n_touch = int(p["n_touch"])
+        cp.kernel = N.KERNEL_STATIC
+        cp.h0 = float(p["h0"])
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        check(lib().pfft_plan_create(mesh.h, loops.h, ctypes.byref(cp), _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.mesh, self.loops = mesh, loops      # the plan borrows the loop basis
+        self.nl, self.nb, self.np = loops.nl, loops.nb, loops.np
+
+    def info(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        gh = (ctypes.c_double * 3)()
+        rn = ctypes.c_double()
+        db = ctypes.c_int64()
+        check(lib().pfft_plan_info(self.h, *[ctypes.byref(x) for x in v], gh, ctypes.byref(rn), ctypes.byref(db)))
+        return dict(n_loops=v[0].value, n_branches=v[1].value, n_tri=v[2].value, n_near_pairs=v[3].value,
+                    grid_h=list(gh), r_near=rn.value, device_bytes=db.value)
+
+    def export(self, what):
+        """Copy a setup array to the host (see pfft_plan_export in include/sie.h)."""
+        info = self.info()
+        nt, nn = info["n_tri"], info["n_near_pairs"]
+        g = self.params["grid"]
+        shapes = {N.EXPORT_NEAR_PTR: ((nt + 1,), np.int64), N.EXPORT_NEAR_COL: ((nn,), np.int32),
+                  N.EXPORT_LD: ((nn, 3, 3), np.float64), N.EXPORT_LDIRECT: ((nn, 3, 3), np.float64),
+                  N.EXPORT_HHAT: ((g[1] + 1, g[2] + 1, g[0] + 1), np.float64),
+                  N.EXPORT_START: ((nt, 7, 3), np.int32)}
+        shape, dt = shapes[what]
+        out = np.zeros(shape, dt)
+        check(lib().pfft_plan_export(self.h, what, _ptr(out), out.nbytes))
+        return out
+
+    def launches(self):
+        return int(lib().pfft_plan_launches(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().pfft_plan_destroy(self.h)
+            self.h = None
+
+
+def pfft_plan_create(mesh, loops, params=None, stream=None):
+    return Plan(mesh, loops, params, stream)
+
+
+def _check_vec(x, n, name):
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128):
+        raise TypeError(f"{name} must be a CUDA complex128 tensor")
+    if x.dim() != 2 or x.shape[1] != n or not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous [nrhs, {n}]")
+
+
+def pfft_matvec(plan: Plan, x, omega, space=N.SPACE_LOOP, prec=N.PREC_FP64, out=None, stream=None):
+    """y = A Z_b(omega) A^T x (space=LOOP) or Z_b(omega) x (space=BRANCH), x [nrhs, n]."""
+    import torch
+    n = plan.nl if space == N.SPACE_LOOP else plan.nb
+    _check_vec(x, n, "x")
+    om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, np.float64), (x.shape[0],)))
+    y = torch.empty_like(x) if out is None else out
+    _check_vec(y, n, "out")
+    check(lib().pfft_matvec(plan.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.shape[0],
+                            _ptr(om), space, prec, _stream(stream)))
+    return y
+
+
+def pfft_convolve(plan: Plan, grid, prec=N.PREC_FP64, stream=None):
+    """phi_g = H Q_g in place for grid [nbatch, N_x, N_y, N_z] (complex128 or complex64)."""
+    import torch
+    g = plan.params["grid"]
+    want = torch.complex128 if prec == N.PREC_FP64 else torch.complex64
+    if not (grid.is_cuda and grid.dtype == want and grid.is_contiguous() and tuple(grid.shape[1:]) == tuple(g)):
+        raise ValueError("grid must be a contiguous CUDA tensor [nbatch, N_x, N_y, N_z] of the precision's dtype")
+    check(lib().pfft_convolve(plan.h, ctypes.c_void_p(grid.data_ptr()), grid.shape[0], prec, _stream(stream)))
+    return grid
+
+
+def pfft_precond_apply(plan: Plan, y, omega, stream=None):
+    import torch
+    _check_vec(y, plan.nl, "y")
+    om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, np.float64), (y.shape[0],)))
+    z = torch.empty_like(y)
+    check(lib().pfft_precond_apply(plan.h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                   y.shape[0], _ptr(om), _stream(stream)))
+    return z
+
+
+def sie_solve(plan: Plan, freqs, ports=None, tol=1e-6, restart=200, max_iter=2000, precond=1,
+              prec=N.PREC_FP64):
+    f = np.ascontiguousarray(freqs, np.float64)
+    pr = np.arange(plan.np, dtype=np.int32) if ports is None else np.ascontiguousarray(ports, np.int32)
+    o = N.SolveOpts(tol=tol, restart=restart, max_iter=max_iter, precond=precond, prec=prec)
+    Z = np.zeros((f.shape[0], pr.shape[0], pr.shape[0]), np.complex128)
+    st = N.SolveStats()
+    rc = lib().sie_solve(plan.h, _ptr(f), f.shape[0], _ptr(pr), pr.shape[0], ctypes.byref(o), _ptr(Z),
+                         ctypes.byref(st))
+    stats = {k: getattr(st, k) for k, _ in N.SolveStats._fields_}
+    if rc not in (N.SIE_OK, -6):
+        check(rc)
+    stats["converged"] = rc == N.SIE_OK
+    return Z, stats

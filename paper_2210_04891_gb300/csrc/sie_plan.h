@@ -1,0 +1,109 @@
+// pFFT plan: everything the matvec, the preconditioner and the solver need,
+// resident in device memory for the plan's lifetime.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "sie_common.cuh"
+
+namespace sie {
+
+template <typename T> struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+struct PrecondState;   // sie_solve.cu
+
+struct Scratch {
+    int32_t cap_rhs = 0;   // right-hand sides the buffers are sized for
+    int prec = -1;
+    void *tour = nullptr;      // complex128 [R][2 n_nodes]
+    void *c_tri = nullptr;     // complex T [R][nt][3]
+    void *jq = nullptr;        // complex T [R][nt*Q][3]
+    void *grid = nullptr;      // complex T [R][3][Ng]
+    void *spec = nullptr;      // complex T [R][3][Nx][My][Mz]
+    void *phiq = nullptr;      // complex T [R][nt*Q][3]
+    void *y_tri = nullptr;     // complex128 [R][nt][3]
+    void *y_br = nullptr;      // complex128 [R][nb + np]
+    double *coef = nullptr;    // per RHS: Z_s per conductor (re, im), c_L (im) -> [R][2 ncond + 1]
+    size_t bytes = 0;
+};
+
+}  // namespace sie
+
+struct pfft_plan {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t launches = 0;
+    // sizes
+    int64_t nt = 0, nb = 0, nl = 0, np = 0, nn = 0;
+    int32_t ncond = 0;
+    int Nx = 0, Ny = 0, Nz = 0, Mx = 0, My = 0, Mz = 0, O = 3, Q = 7;
+    int64_t Ng = 0;
+    double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+    double r_near = 0.0;
+    pfft_params params{};
+    const sie_loops *loops = nullptr;   // borrowed: must outlive the plan
+    std::vector<double> sigma;          // per conductor
+    // per triangle (device)
+    int32_t *d_tb = nullptr;            // [nt][3] branch of local edge k (-1: none)
+    int8_t *d_ts = nullptr;             // [nt][3] +1 on T+, -1 on T-
+    int32_t *d_cond = nullptr;          // [nt]
+    double *d_gram = nullptr;           // [nt][3][3]  int (r-v_k).(r-v_l) dS / (4A^2)
+    double *d_mom64 = nullptr;          // [nt*Q][3][3] (w_q/2)(r_q - v_k)
+    float *d_mom32 = nullptr;
+    int32_t *d_start = nullptr;         // [nt*Q][3] stencil start nodes
+    double *d_lw64 = nullptr;           // [nt*Q][3][O] Lagrange weights
+    float *d_lw32 = nullptr;
+    // projection gather: node -> (point, weight)
+    int64_t *d_pj_ptr = nullptr;        // [Ng + 1]
+    int32_t *d_pj_pt = nullptr;         // [nnz]
+    double *d_pj_w64 = nullptr;
+    float *d_pj_w32 = nullptr;
+    // near field CSR over triangles (row T: near T', ascending), 3x3 blocks
+    int64_t n_near = 0;
+    int64_t *d_near_ptr = nullptr;
+    int32_t *d_near_col = nullptr;
+    double *d_Ld64 = nullptr;           // [n_near][3][3]  L_direct - L_grid
+    float *d_Ld32 = nullptr;
+    double *d_Ldir64 = nullptr;         // [n_near][3][3]  L_direct (kept for diag and checks)
+    // kernel spectrum, folded [My/2+1][Mz/2+1][Mx/2+1], scaled by 1/(Mx My Mz)
+    double *d_H64 = nullptr;
+    float *d_H32 = nullptr;
+    double2 *d_tw64[3] = {nullptr, nullptr, nullptr};   // per axis, length M_d
+    float2 *d_tw32[3] = {nullptr, nullptr, nullptr};
+    // loop basis on the device
+    int32_t *d_tour_node = nullptr;     // [2 nn]
+    int8_t *d_tour_enter = nullptr;     // [2 nn]
+    int32_t *d_enter = nullptr, *d_exit = nullptr;   // [nn]
+    int32_t *d_nl_ptr = nullptr, *d_nl_loop = nullptr;
+    int8_t *d_nl_sign = nullptr;
+    int32_t *d_parent_branch = nullptr;  // [nn]
+    int32_t *d_twig_node = nullptr;      // [nb]: node whose parent branch it is, -1 for links
+    int32_t *d_loop_of_branch = nullptr; // [nb + np]
+    int32_t *d_tail = nullptr, *d_head = nullptr;  // [nb + np]
+    int32_t *d_link_branch = nullptr;    // [nl]
+    int32_t *d_br_tri = nullptr;         // [nb][2]
+    int8_t *d_br_local = nullptr;        // [nb][2]
+    // branch diagonal of Z_b pieces (preconditioner, Eq. Precond)
+    double *d_diag_gram = nullptr;       // [nb]
+    double *d_diag_L = nullptr;          // [nb]
+    int32_t *d_br_cond = nullptr;        // [nb]
+    sie::Scratch scr;
+    sie::PrecondState *pc = nullptr;
+    size_t device_bytes = 0;
+    std::vector<void *> allocations;
+};
+
+namespace sie {
+int plan_alloc(pfft_plan *p, void **ptr, size_t bytes);
+void plan_free(pfft_plan *p, void *ptr);
+void plan_free_precond(pfft_plan *p);
+int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
+template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
+int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
+int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s);
+}  // namespace sie

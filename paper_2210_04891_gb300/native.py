@@ -1,0 +1,99 @@
+"""ctypes loader of libsie.so (the C ABI declared in include/sie.h).
+
+The library is built in-tree by paper_2210_04891_gb300.build (or
+__graft_entry__.build()).  There is no fallback: if the library is missing or
+fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsie.so")
+
+SIE_OK = 0
+ERRORS = {-1: "SIE_ERR_ARG", -2: "SIE_ERR_NONMANIFOLD", -3: "SIE_ERR_BAD_PORT", -4: "SIE_ERR_OOM",
+          -5: "SIE_ERR_CUDA", -6: "SIE_ERR_NOT_CONVERGED", -7: "SIE_ERR_BREAKDOWN", -8: "SIE_ERR_TIMEOUT"}
+SPACE_LOOP, SPACE_BRANCH = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+KERNEL_STATIC = 0
+
+# every symbol include/sie.h declares
+EXPORTS = ["sie_mesh_load", "sie_mesh_destroy", "loop_basis_build", "sie_loops_destroy", "sie_loops_export",
+           "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
+           "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_plan_launches", "sie_last_error"]
+EXPORT_NEAR_PTR, EXPORT_NEAR_COL, EXPORT_LD, EXPORT_LDIRECT, EXPORT_HHAT, EXPORT_START = range(6)
+
+
+class SiePort(ctypes.Structure):
+    _fields_ = [("src", ctypes.POINTER(ctypes.c_int32)), ("n_src", ctypes.c_int32),
+                ("sink", ctypes.POINTER(ctypes.c_int32)), ("n_sink", ctypes.c_int32)]
+
+
+class SieLoopStats(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_branches", ctypes.c_int64), ("n_comp", ctypes.c_int64),
+                ("n_loops", ctypes.c_int64), ("n_ports", ctypes.c_int64), ("tree_depth", ctypes.c_int64),
+                ("nnz_A", ctypes.c_int64)]
+
+
+class PfftParams(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32 * 3), ("order", ctypes.c_int32), ("near_factor", ctypes.c_double),
+                ("near_min_diam", ctypes.c_double), ("n_touch", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("h0", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations_max", ctypes.c_int32), ("iterations_sum", ctypes.c_int32),
+                ("n_not_converged", ctypes.c_int32), ("residual_max", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("matvecs", ctypes.c_int64)]
+
+
+class SieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsie.so is not built ({LIB_PATH}); run paper_2210_04891_gb300.build.build() "
+                          "or __graft_entry__.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    L.sie_mesh_load.argtypes = [P, I64, P, I64, P, P, I32, PP]
+    L.sie_mesh_destroy.argtypes = [P]
+    L.loop_basis_build.argtypes = [P, ctypes.POINTER(SiePort), I32, PP, ctypes.POINTER(SieLoopStats)]
+    L.sie_loops_destroy.argtypes = [P]
+    L.sie_loops_export.argtypes = [P, P, P, P, P]
+    L.pfft_plan_create.argtypes = [P, P, ctypes.POINTER(PfftParams), P, PP]
+    L.pfft_plan_destroy.argtypes = [P]
+    L.pfft_matvec.argtypes = [P, P, P, I32, P, I32, I32, P]
+    L.pfft_precond_apply.argtypes = [P, P, P, I32, P, P]
+    L.sie_solve.argtypes = [P, P, I32, P, I32, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveStats)]
+    L.pfft_plan_info.argtypes = [P, P, P, P, P, P, P, P]
+    L.pfft_plan_export.argtypes = [P, I32, P, I64]
+    L.pfft_convolve.argtypes = [P, P, I32, I32, P]
+    L.pfft_plan_launches.argtypes = [P]
+    L.pfft_plan_launches.restype = I64
+    L.sie_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(rc):
+    if rc != SIE_OK:
+        raise SieError(rc, lib().sie_last_error().decode())
+    return rc
