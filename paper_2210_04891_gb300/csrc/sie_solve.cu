@@ -1,0 +1,909 @@
+// Preconditioner and solver of Sec. IV-A (arXiv 2210.04891).
+//
+// Eq. (Precond): P = A Z_b^N A^T, Z_b^N = diag(Z_b) (port links carry no
+// impedance).  P^-1 y is applied exactly through the nodal form of the same
+// circuit: with D = diag(Z_b) every branch e is an impedance D_e, each link
+// carries the loop's EMF y_l, each port is an ideal source of EMF y_p between
+// its sink and source nodes.  Node potentials phi solve the weighted graph
+// Laplacian  sum_e (1/D_e)(phi_tail - phi_head + emf_e) = 0  per node (one
+// grounded node per conductor, source nodes fixed by their port EMF); the link
+// currents (1/D_e)(phi_tail - phi_head + emf_e) and the port currents are then
+// z = P^-1 y.  This equals the loop-space solve because the fundamental loops
+// span exactly the currents that satisfy Kirchhoff's current law.  The
+// Laplacian is far sparser than P (a triangle has three neighbours) and does
+// not depend on the spanning tree.  Each conductor's Laplacian is ordered by
+// reverse Cuthill-McKee and factorised as a band LDL^T without pivoting (its
+// Hermitian part, the Laplacian of Re(1/D_e) > 0, is positive definite).
+//
+// Eq. (LoopWithP): restarted GMRES on P^-1 Z_l I_l = P^-1 V_l for all
+// (frequency, port) right-hand sides at once; Arnoldi by classical
+// Gram-Schmidt applied twice, in FP64 on the device; Givens rotations and the
+// small least-squares solve on the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <deque>
+#include <map>
+#include <numeric>
+#include <vector>
+
+#include "sie_plan.h"
+
+using namespace sie;
+
+namespace sie {
+int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega, int space, int prec,
+                 cudaStream_t st);
+
+struct PrecondState {
+    // symbolic (host-built once)
+    int64_t nunk = 0;                 // unknowns (permuted, concatenated by block)
+    int32_t W = 0;                    // band width (max over blocks)
+    std::vector<int64_t> blk_off;     // [nblk + 1] unknown offset of each block
+    int32_t *d_blk_off32 = nullptr;
+    int64_t *d_blk_off = nullptr;
+    int32_t *d_unk_of_node = nullptr;  // [nn] permuted unknown index, -1 fixed
+    int32_t *d_off_ptr = nullptr, *d_off_port = nullptr;  // node -> (port, sign) potential offsets
+    int8_t *d_off_sign = nullptr;
+    int32_t *d_row_ptr = nullptr, *d_row_br = nullptr;    // unknown row -> incident branches
+    int8_t *d_row_sg = nullptr;                            // +1 tail in row's group, -1 head
+    int32_t *d_row_oth = nullptr;                          // other end's unknown (-1 fixed / same)
+    int32_t *d_src_ptr = nullptr, *d_src_br = nullptr;     // port -> branches at its source node
+    int8_t *d_src_sg = nullptr;
+    int32_t *d_port_loop = nullptr;
+    // numeric
+    int32_t nslots = 0;
+    std::vector<double> slot_omega;
+    double2 *d_band = nullptr;        // [nslots][nunk][W + 1], band[i][d] = K[i][i-d]
+    double2 *d_a = nullptr;           // [nslots][nb] 1/D_e
+    double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
+    int32_t cap_rhs = 0;
+    int32_t *d_slot = nullptr;        // [R] factor slot per right-hand side
+    int *d_status = nullptr;
+    std::vector<void *> allocs;
+};
+
+void plan_free_precond(pfft_plan *p) {
+    if (!p || !p->pc) return;
+    for (void *a : p->pc->allocs) cudaFree(a);
+    for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
+                    (void *)p->pc->d_ibr, (void *)p->pc->d_slot})
+        if (a) cudaFree(a);
+    delete p->pc;
+    p->pc = nullptr;
+}
+}  // namespace sie
+
+namespace {
+
+constexpr double kMu0 = 4e-7 * M_PI;
+
+template <typename T>
+int pc_upload(PrecondState *s, T **dst, const std::vector<T> &v) {
+    size_t b = std::max<size_t>(v.size() * sizeof(T), 16);
+    SIE_CUDA(cudaMalloc((void **)dst, b));
+    s->allocs.push_back(*dst);
+    if (!v.empty()) SIE_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SIE_OK;
+}
+
+// Symbolic set-up: grounds, port offsets, unknown numbering (RCM per block),
+// row -> branch lists.
+int build_symbolic(pfft_plan *p) {
+    const sie_loops *L = p->loops;
+    const int64_t nn = L->n_nodes, nb = L->nb, np = L->np;
+    auto *s = new (std::nothrow) PrecondState;
+    if (!s) return fail(SIE_ERR_OOM, "preconditioner: out of host memory");
+    p->pc = s;
+    // port groups: nodes linked by port sources (union-find), offsets by BFS
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> padj(nn);   // (other node, +-(port+1))
+    for (int64_t q = 0; q < np; ++q) {
+        int32_t snk = L->port_sink[q], src = L->port_src[q];
+        padj[snk].emplace_back(src, int32_t(q + 1));     // phi_src = phi_snk + y_q
+        padj[src].emplace_back(snk, -int32_t(q + 1));
+    }
+    for (int64_t q = 0; q < np; ++q)
+        for (int64_t r = 0; r < np; ++r)
+            if (q != r && (L->port_src[q] == L->port_src[r] || L->port_src[q] == L->port_sink[r]))
+                return fail(SIE_ERR_BAD_PORT, "preconditioner: a port's source contact is shared with another port");
+    std::vector<int32_t> group(nn, -1);
+    std::vector<std::vector<std::pair<int32_t, int8_t>>> off(nn);
+    std::vector<int32_t> ground_of_comp(L->n_comp, -1);
+    for (int64_t q = 0; q < np; ++q)
+        if (ground_of_comp[L->comp[L->port_sink[q]]] < 0) ground_of_comp[L->comp[L->port_sink[q]]] = L->port_sink[q];
+    for (int64_t v = 0; v < nn; ++v)
+        if (ground_of_comp[L->comp[v]] < 0) ground_of_comp[L->comp[v]] = int32_t(v);
+    std::vector<char> fixed(nn, 0);
+    int32_t ngroups = 0;
+    for (int64_t v0 = 0; v0 < nn; ++v0) {
+        if (group[v0] >= 0 || padj[v0].empty()) continue;
+        // BFS over port edges from v0
+        std::vector<int32_t> members{int32_t(v0)};
+        group[v0] = ngroups;
+        for (size_t k = 0; k < members.size(); ++k) {
+            int32_t u = members[k];
+            for (auto [w, sp] : padj[u]) {
+                if (group[w] >= 0) {
+                    if (group[w] != ngroups) return fail(SIE_ERR_BAD_PORT, "preconditioner: inconsistent port groups");
+                    continue;
+                }
+                group[w] = ngroups;
+                off[w] = off[u];
+                off[w].emplace_back(std::abs(sp) - 1, int8_t(sp > 0 ? 1 : -1));
+                members.push_back(w);
+            }
+        }
+        if (members.size() > size_t(np) + 1)
+            return fail(SIE_ERR_BAD_PORT, "preconditioner: ports form a closed loop of sources");
+        // rebase offsets on the group's ground if it holds one
+        int32_t g = ground_of_comp[L->comp[v0]];
+        if (group[g] == ngroups) {
+            auto base = off[g];
+            for (int32_t m : members) {
+                for (auto [q, sg] : base) off[m].emplace_back(q, int8_t(-sg));
+                fixed[m] = 1;
+            }
+        }
+        ++ngroups;
+    }
+    for (int64_t c = 0; c < L->n_comp; ++c) fixed[ground_of_comp[c]] = 1;
+    // unknowns: one per free group (its members share it), one per other free node
+    std::vector<int32_t> unk_raw(nn, -1);
+    std::vector<int32_t> group_unk(ngroups, -1);
+    int64_t nunk = 0;
+    for (int64_t v = 0; v < nn; ++v) {
+        if (fixed[v]) continue;
+        if (group[v] >= 0) {
+            if (group_unk[group[v]] < 0) group_unk[group[v]] = int32_t(nunk++);
+            unk_raw[v] = group_unk[group[v]];
+        } else {
+            unk_raw[v] = int32_t(nunk++);
+        }
+    }
+    s->nunk = nunk;
+    // unknown adjacency
+    std::vector<std::vector<int32_t>> uadj(nunk);
+    for (int64_t e = 0; e < nb; ++e) {
+        int32_t a = unk_raw[L->tail[e]], b = unk_raw[L->head[e]];
+        if (a >= 0 && b >= 0 && a != b) { uadj[a].push_back(b); uadj[b].push_back(a); }
+    }
+    for (auto &v : uadj) { std::sort(v.begin(), v.end()); v.erase(std::unique(v.begin(), v.end()), v.end()); }
+    // blocks = connected components of the unknown graph; RCM inside each
+    std::vector<int32_t> perm;       // new -> raw
+    perm.reserve(nunk);
+    std::vector<char> seen(nunk, 0);
+    s->blk_off.assign(1, 0);
+    for (int64_t r0 = 0; r0 < nunk; ++r0) {
+        if (seen[r0]) continue;
+        // component members
+        std::vector<int32_t> comp{int32_t(r0)};
+        seen[r0] = 1;
+        for (size_t k = 0; k < comp.size(); ++k)
+            for (int32_t w : uadj[comp[k]])
+                if (!seen[w]) { seen[w] = 1; comp.push_back(w); }
+        // pseudo-peripheral start: farthest node of two BFS sweeps, ties by lower degree
+        auto bfs_far = [&](int32_t st) {
+            std::map<int32_t, int32_t> dist;
+            std::deque<int32_t> q{st};
+            dist[st] = 0;
+            int32_t far = st;
+            while (!q.empty()) {
+                int32_t u = q.front();
+                q.pop_front();
+                if (dist[u] > dist[far] || (dist[u] == dist[far] && uadj[u].size() < uadj[far].size())) far = u;
+                for (int32_t w : uadj[u])
+                    if (!dist.count(w)) { dist[w] = dist[u] + 1; q.push_back(w); }
+            }
+            return far;
+        };
+        int32_t start = bfs_far(bfs_far(comp[0]));
+        std::vector<int32_t> order{start};
+        std::map<int32_t, char> vis;
+        vis[start] = 1;
+        for (size_t k = 0; k < order.size(); ++k) {
+            std::vector<int32_t> nbr;
+            for (int32_t w : uadj[order[k]])
+                if (!vis.count(w)) { vis[w] = 1; nbr.push_back(w); }
+            std::sort(nbr.begin(), nbr.end(), [&](int32_t a, int32_t b) {
+                return uadj[a].size() != uadj[b].size() ? uadj[a].size() < uadj[b].size() : a < b;
+            });
+            order.insert(order.end(), nbr.begin(), nbr.end());
+        }
+        std::reverse(order.begin(), order.end());
+        perm.insert(perm.end(), order.begin(), order.end());
+        s->blk_off.push_back(int64_t(perm.size()));
+    }
+    std::vector<int32_t> inv(nunk);
+    for (int64_t i = 0; i < nunk; ++i) inv[perm[i]] = int32_t(i);
+    int32_t W = 0;
+    for (int64_t a = 0; a < nunk; ++a)
+        for (int32_t b : uadj[a]) W = std::max<int32_t>(W, std::abs(inv[a] - inv[b]));
+    s->W = std::max<int32_t>(W, 1);
+    std::vector<int32_t> unk(nn, -1);
+    for (int64_t v = 0; v < nn; ++v) unk[v] = unk_raw[v] >= 0 ? inv[unk_raw[v]] : -1;
+    // rows: incident branches of each unknown's member nodes
+    std::vector<std::vector<std::pair<int32_t, int8_t>>> rows(nunk);
+    for (int64_t e = 0; e < nb; ++e) {
+        int32_t a = unk[L->tail[e]], b = unk[L->head[e]];
+        if (a >= 0 && a != b) rows[a].emplace_back(int32_t(e), int8_t(1));
+        if (b >= 0 && a != b) rows[b].emplace_back(int32_t(e), int8_t(-1));
+    }
+    std::vector<int32_t> row_ptr{0}, row_br, row_oth;
+    std::vector<int8_t> row_sg;
+    for (int64_t i = 0; i < nunk; ++i) {
+        for (auto [e, sg] : rows[i]) {
+            row_br.push_back(e);
+            row_sg.push_back(sg);
+            int32_t o = sg > 0 ? unk[L->head[e]] : unk[L->tail[e]];
+            row_oth.push_back(o);
+        }
+        row_ptr.push_back(int32_t(row_br.size()));
+    }
+    std::vector<int32_t> off_ptr{0}, off_port;
+    std::vector<int8_t> off_sign;
+    for (int64_t v = 0; v < nn; ++v) {
+        for (auto [q, sg] : off[v]) { off_port.push_back(q); off_sign.push_back(sg); }
+        off_ptr.push_back(int32_t(off_port.size()));
+    }
+    std::vector<int32_t> src_ptr{0}, src_br;
+    std::vector<int8_t> src_sg;
+    for (int64_t q = 0; q < np; ++q) {
+        int32_t v = L->port_src[q];
+        for (int64_t e = 0; e < nb; ++e) {
+            if (L->tail[e] == v) { src_br.push_back(int32_t(e)); src_sg.push_back(1); }
+            else if (L->head[e] == v) { src_br.push_back(int32_t(e)); src_sg.push_back(-1); }
+        }
+        src_ptr.push_back(int32_t(src_br.size()));
+    }
+    std::vector<int32_t> port_loop(std::max<int64_t>(np, 1), 0);
+    for (int64_t q = 0; q < np; ++q) port_loop[q] = L->loop_of_branch[nb + q];
+    std::vector<int64_t> bo(s->blk_off);
+    int rc;
+    if ((rc = pc_upload(s, &s->d_blk_off, bo))) return rc;
+    if ((rc = pc_upload(s, &s->d_unk_of_node, unk))) return rc;
+    if ((rc = pc_upload(s, &s->d_off_ptr, off_ptr))) return rc;
+    if ((rc = pc_upload(s, &s->d_off_port, off_port))) return rc;
+    if ((rc = pc_upload(s, &s->d_off_sign, off_sign))) return rc;
+    if ((rc = pc_upload(s, &s->d_row_ptr, row_ptr))) return rc;
+    if ((rc = pc_upload(s, &s->d_row_br, row_br))) return rc;
+    if ((rc = pc_upload(s, &s->d_row_sg, row_sg))) return rc;
+    if ((rc = pc_upload(s, &s->d_row_oth, row_oth))) return rc;
+    if ((rc = pc_upload(s, &s->d_src_ptr, src_ptr))) return rc;
+    if ((rc = pc_upload(s, &s->d_src_br, src_br))) return rc;
+    if ((rc = pc_upload(s, &s->d_src_sg, src_sg))) return rc;
+    if ((rc = pc_upload(s, &s->d_port_loop, port_loop))) return rc;
+    SIE_CUDA(cudaMalloc((void **)&s->d_status, sizeof(int)));
+    s->allocs.push_back(s->d_status);
+    return SIE_OK;
+}
+
+// 1/D_e with D_e = Z_s(sigma_e, w) G_ee + j w mu0/(4 pi) Lt_ee (Eq. Zb diagonal).
+__global__ void k_pc_admittance(const double *__restrict__ diag_gram, const double *__restrict__ diag_L,
+                                const int32_t *__restrict__ br_cond, const double *__restrict__ zs_cl, int ncond,
+                                int64_t nb, int32_t nslots, double2 *__restrict__ a) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nb * nslots) return;
+    int64_t f = i / nb, e = i % nb;
+    const double *cf = zs_cl + f * (ncond + 1);
+    double zs = cf[br_cond[e]], cl = cf[ncond];
+    double dr = zs * diag_gram[e], di = zs * diag_gram[e] + cl * diag_L[e];
+    double den = dr * dr + di * di;
+    a[i] = make_double2(dr / den, -di / den);
+}
+
+// Assemble the band of each (slot, block) and factorise it in place:
+// K = L diag(d) L^T, unit L stored below the diagonal, d on the diagonal.
+__global__ void __launch_bounds__(256) k_pc_factor(const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W,
+                                                   int64_t nunk, const int32_t *__restrict__ row_ptr,
+                                                   const int32_t *__restrict__ row_br,
+                                                   const int32_t *__restrict__ row_oth, const double2 *__restrict__ a,
+                                                   int64_t nb, double2 *__restrict__ band, int *status) {
+    const int32_t f = blockIdx.x / nblk, b = blockIdx.x % nblk;
+    const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
+    const int Wp = W + 1;
+    double2 *B = band + (int64_t(f) * nunk + o) * Wp;
+    const double2 *af = a + int64_t(f) * nb;
+    for (int64_t i = threadIdx.x; i < n * Wp; i += blockDim.x) B[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t gi = o + i;
+        double2 d = make_double2(0.0, 0.0);
+        for (int32_t k = row_ptr[gi]; k < row_ptr[gi + 1]; ++k) {
+            double2 w = af[row_br[k]];
+            d = cadd(d, w);
+            int32_t j = row_oth[k];
+            if (j >= 0 && j < gi) {   // lower triangle entry (i, j): K_ij -= a_e
+                int64_t dd = gi - j;
+                B[i * Wp + dd] = csub(B[i * Wp + dd], w);
+            }
+        }
+        B[i * Wp] = d;
+    }
+    __syncthreads();
+    for (int64_t k = 0; k < n; ++k) {
+        const double2 dk = B[k * Wp];
+        if (dk.x == 0.0 && dk.y == 0.0) {
+            if (threadIdx.x == 0) *status = SIE_ERR_BREAKDOWN;
+            return;
+        }
+        const double den = dk.x * dk.x + dk.y * dk.y;
+        const double2 inv = make_double2(dk.x / den, -dk.y / den);
+        const int64_t m = (int64_t(W) < n - 1 - k) ? int64_t(W) : n - 1 - k;
+        // rows i = k + r (r = 1..m): update K[i][j] for j in (k, i] by l_ik d_k l_jk
+        const int64_t tri = m * (m + 1) / 2;
+        for (int64_t t = threadIdx.x; t < tri; t += blockDim.x) {
+            // t -> (r, c) with 1 <= c <= r <= m
+            int64_t r = int64_t((sqrt(8.0 * double(t) + 1.0) - 1.0) / 2.0);
+            while (r * (r + 1) / 2 > t) --r;
+            while ((r + 1) * (r + 2) / 2 <= t) ++r;
+            int64_t c = t - r * (r + 1) / 2;   // 0..r
+            r += 1;
+            c += 1;
+            const double2 kik = B[(k + r) * Wp + r];     // K[k+r][k]
+            const double2 kjk = B[(k + c) * Wp + c];     // K[k+c][k]
+            double2 upd = cmul(cmul(kik, inv), kjk);
+            double2 &dst = B[(k + r) * Wp + (r - c)];
+            dst = csub(dst, upd);
+        }
+        __syncthreads();
+        for (int64_t r = 1 + threadIdx.x; r <= m; r += blockDim.x)
+            B[(k + r) * Wp + r] = cmul(B[(k + r) * Wp + r], inv);   // l_{k+r,k}
+        __syncthreads();
+    }
+}
+
+// Drive of each branch: kappa_e = a_e (off_tail - off_head + emf_e), emf on links.
+__global__ void k_pc_drive(const double2 *__restrict__ y, int64_t nl, const double2 *__restrict__ a,
+                           const int32_t *__restrict__ slot, const int32_t *__restrict__ loop_of_branch,
+                           const int32_t *__restrict__ tail, const int32_t *__restrict__ head,
+                           const int32_t *__restrict__ off_ptr, const int32_t *__restrict__ off_port,
+                           const int8_t *__restrict__ off_sign, const int32_t *__restrict__ port_loop, int64_t nb,
+                           int32_t nrhs, double2 *__restrict__ kappa) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nb * nrhs) return;
+    int64_t r = i / nb, e = i % nb;
+    const double2 *yr = y + r * nl;
+    double2 v = make_double2(0.0, 0.0);
+    int32_t l = loop_of_branch[e];
+    if (l >= 0) v = yr[l];
+    int32_t t = tail[e], h = head[e];
+    for (int32_t k = off_ptr[t]; k < off_ptr[t + 1]; ++k) {
+        double2 q = yr[port_loop[off_port[k]]];
+        v = off_sign[k] > 0 ? cadd(v, q) : csub(v, q);
+    }
+    for (int32_t k = off_ptr[h]; k < off_ptr[h + 1]; ++k) {
+        double2 q = yr[port_loop[off_port[k]]];
+        v = off_sign[k] > 0 ? csub(v, q) : cadd(v, q);
+    }
+    kappa[i] = cmul(a[int64_t(slot[r]) * nb + e], v);
+}
+
+// rhs_i = -sum over incident branches of s * kappa_e; then band solve
+// L d L^T u = rhs per (rhs, block) on one warp.
+__global__ void k_pc_solve(const double2 *__restrict__ kappa, const int32_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ row_br, const int8_t *__restrict__ row_sg,
+                           const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk, int64_t nb,
+                           const double2 *__restrict__ band, const int32_t *__restrict__ slot, int32_t nrhs,
+                           double2 *__restrict__ u) {
+    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (wid >= int64_t(nrhs) * nblk) return;
+    const int64_t r = wid / nblk, b = wid % nblk;
+    const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
+    const int Wp = W + 1;
+    const double2 *B = band + (int64_t(slot[r]) * nunk + o) * Wp;
+    double2 *x = u + r * nunk + o;
+    const double2 *kr = kappa + r * nb;
+    for (int64_t i = lane; i < n; i += 32) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int32_t k = row_ptr[o + i]; k < row_ptr[o + i + 1]; ++k)
+            acc = row_sg[k] > 0 ? csub(acc, kr[row_br[k]]) : cadd(acc, kr[row_br[k]]);
+        x[i] = acc;
+    }
+    __syncwarp();
+    // forward: x_i -= sum_{d=1..W} L[i][i-d] x_{i-d}
+    for (int64_t i = 0; i < n; ++i) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int d = 1 + lane; d <= W; d += 32)
+            if (i - d >= 0) acc = cadd(acc, cmul(B[i * Wp + d], x[i - d]));
+        for (int s = 16; s > 0; s >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, s);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, s);
+        }
+        if (lane == 0) x[i] = csub(x[i], acc);
+        __syncwarp();
+    }
+    for (int64_t i = lane; i < n; i += 32) {
+        double2 d = B[i * Wp];
+        double den = d.x * d.x + d.y * d.y;
+        x[i] = cmul(x[i], make_double2(d.x / den, -d.y / den));
+    }
+    __syncwarp();
+    // backward: x_i -= sum_{d=1..W} L[i+d][d] x_{i+d}
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int d = 1 + lane; d <= W; d += 32)
+            if (i + d < n) acc = cadd(acc, cmul(B[(i + d) * Wp + d], x[i + d]));
+        for (int s = 16; s > 0; s >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, s);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, s);
+        }
+        if (lane == 0) x[i] = csub(x[i], acc);
+        __syncwarp();
+    }
+}
+
+// Branch currents i_e = a_e (phi_tail - phi_head + emf_e) = a_e (u_t - u_h) + kappa_e.
+__global__ void k_pc_currents(const double2 *__restrict__ u, int64_t nunk, const double2 *__restrict__ kappa,
+                              const double2 *__restrict__ a, const int32_t *__restrict__ slot,
+                              const int32_t *__restrict__ unk, const int32_t *__restrict__ tail,
+                              const int32_t *__restrict__ head, int64_t nb, int32_t nrhs, double2 *__restrict__ ibr) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nb * nrhs) return;
+    int64_t r = i / nb, e = i % nb;
+    int32_t ut = unk[tail[e]], uh = unk[head[e]];
+    double2 d = make_double2(0.0, 0.0);
+    if (ut >= 0) d = cadd(d, u[r * nunk + ut]);
+    if (uh >= 0) d = csub(d, u[r * nunk + uh]);
+    ibr[i] = cadd(cmul(a[int64_t(slot[r]) * nb + e], d), kappa[i]);
+}
+
+__global__ void k_pc_out(const double2 *__restrict__ ibr, const int32_t *__restrict__ link_branch,
+                         const int32_t *__restrict__ src_ptr, const int32_t *__restrict__ src_br,
+                         const int8_t *__restrict__ src_sg, int64_t nb, int64_t nl, int32_t nrhs,
+                         double2 *__restrict__ z) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nl * nrhs) return;
+    int64_t r = i / nl, l = i % nl;
+    int32_t e = link_branch[l];
+    const double2 *ir = ibr + r * nb;
+    double2 v;
+    if (e < nb) {
+        v = ir[e];
+    } else {
+        int32_t q = int32_t(e - nb);
+        v = make_double2(0.0, 0.0);
+        for (int32_t k = src_ptr[q]; k < src_ptr[q + 1]; ++k)
+            v = src_sg[k] > 0 ? cadd(v, ir[src_br[k]]) : csub(v, ir[src_br[k]]);
+    }
+    z[i] = v;
+}
+
+inline unsigned nblk_(int64_t n, int t = 256) { return unsigned((n + t - 1) / t); }
+
+// Factor slots for the distinct omegas of a right-hand-side batch.
+int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t> &slot, cudaStream_t st) {
+    if (!p->pc) {
+        int rc = build_symbolic(p);
+        if (rc) { plan_free_precond(p); return rc; }
+    }
+    PrecondState *s = p->pc;
+    std::vector<double> uniq(omega, omega + R);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    for (double w : uniq)
+        if (!(w > 0.0) || !std::isfinite(w)) return fail(SIE_ERR_ARG, "preconditioner: omega must be positive");
+    slot.resize(R);
+    for (int32_t r = 0; r < R; ++r) slot[r] = int32_t(std::lower_bound(uniq.begin(), uniq.end(), omega[r]) - uniq.begin());
+    if (R > s->cap_rhs) {
+        for (void *a : {(void *)s->d_kappa, (void *)s->d_u, (void *)s->d_ibr, (void *)s->d_slot})
+            if (a) cudaFree(a);
+        s->d_kappa = s->d_u = s->d_ibr = nullptr;
+        s->d_slot = nullptr;
+        SIE_CUDA(cudaMalloc((void **)&s->d_kappa, size_t(R) * p->nb * sizeof(double2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_ibr, size_t(R) * p->nb * sizeof(double2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_u, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(double2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_slot, size_t(R) * sizeof(int32_t)));
+        s->cap_rhs = R;
+    }
+    SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (uniq == s->slot_omega) return SIE_OK;   // factors cached
+    const int32_t ns = int32_t(uniq.size());
+    if (s->d_band) cudaFree(s->d_band);
+    if (s->d_a) cudaFree(s->d_a);
+    s->d_band = nullptr;
+    s->d_a = nullptr;
+    s->slot_omega.clear();
+    SIE_CUDA(cudaMalloc((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
+    SIE_CUDA(cudaMalloc((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2)));
+    std::vector<double> zc(size_t(ns) * (p->ncond + 1));
+    for (int32_t f = 0; f < ns; ++f) {
+        for (int c = 0; c < p->ncond; ++c) zc[f * (p->ncond + 1) + c] = std::sqrt(uniq[f] * kMu0 / (2.0 * p->sigma[c]));
+        zc[f * (p->ncond + 1) + p->ncond] = uniq[f] * kMu0 / (4.0 * M_PI);
+    }
+    double *d_zc = nullptr;
+    SIE_CUDA(cudaMalloc((void **)&d_zc, zc.size() * sizeof(double)));
+    SIE_CUDA(cudaMemcpyAsync(d_zc, zc.data(), zc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zc, p->ncond,
+                                                       p->nb, ns, s->d_a);
+    SIE_LAUNCH_CHECK(p);
+    int zero = 0;
+    SIE_CUDA(cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    const int32_t nblk = int32_t(s->blk_off.size() - 1);
+    if (s->nunk > 0) {
+        k_pc_factor<<<ns * nblk, 256, 0, st>>>(s->d_blk_off, nblk, s->W, s->nunk, s->d_row_ptr, s->d_row_br,
+                                                s->d_row_oth, s->d_a, p->nb, s->d_band, s->d_status);
+        SIE_LAUNCH_CHECK(p);
+    }
+    int status = 0;
+    SIE_CUDA(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SIE_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d_zc);
+    if (status) return fail(SIE_ERR_BREAKDOWN, "preconditioner: zero pivot in the band LDL^T");
+    s->slot_omega = uniq;
+    s->nslots = ns;
+    return SIE_OK;
+}
+
+int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream_t st) {
+    PrecondState *s = p->pc;
+    const int32_t nblk = int32_t(s->blk_off.size() - 1);
+    k_pc_drive<<<nblk_(p->nb * R), 256, 0, st>>>(y, p->nl, s->d_a, s->d_slot, p->d_loop_of_branch, p->d_tail,
+                                                 p->d_head, s->d_off_ptr, s->d_off_port, s->d_off_sign,
+                                                 s->d_port_loop, p->nb, R, s->d_kappa);
+    SIE_LAUNCH_CHECK(p);
+    if (s->nunk > 0) {
+        const int64_t warps = int64_t(R) * nblk;
+        k_pc_solve<<<nblk_(warps * 32, 128), 128, 0, st>>>(s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
+                                                            s->d_blk_off, nblk, s->W, s->nunk, p->nb, s->d_band,
+                                                            s->d_slot, R, s->d_u);
+        SIE_LAUNCH_CHECK(p);
+    }
+    k_pc_currents<<<nblk_(p->nb * R), 256, 0, st>>>(s->d_u, s->nunk, s->d_kappa, s->d_a, s->d_slot,
+                                                    s->d_unk_of_node, p->d_tail, p->d_head, p->nb, R, s->d_ibr);
+    SIE_LAUNCH_CHECK(p);
+    k_pc_out<<<nblk_(p->nl * R), 256, 0, st>>>(s->d_ibr, p->d_link_branch, s->d_src_ptr, s->d_src_br, s->d_src_sg,
+                                               p->nb, p->nl, R, z);
+    SIE_LAUNCH_CHECK(p);
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ GMRES kernels
+
+// Krylov basis layout [m+1][R][n]: vector j of right-hand side r at
+// V + j * kstride + r * ldv, so each basis vector is a contiguous [R][n] block
+// the batched matvec can take directly.
+// h[r][j] = <V_j[r], w[r]> for j < k (one CTA per (r, j)).
+__global__ void k_dots(const double2 *__restrict__ V, int64_t ldv, int64_t kstride, const double2 *__restrict__ w,
+                       int64_t n, int32_t k, const int32_t *__restrict__ active, double2 *__restrict__ h, int32_t ldh) {
+    const int32_t r = blockIdx.x / k, j = blockIdx.x % k;
+    if (!active[r]) return;
+    const double2 *v = V + int64_t(j) * kstride + int64_t(r) * ldv;
+    const double2 *x = w + int64_t(r) * ldv;
+    double re = 0.0, im = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 a = v[i], b = x[i];
+        re += a.x * b.x + a.y * b.y;   // conj(a) b
+        im += a.x * b.y - a.y * b.x;
+    }
+    __shared__ double sr[32], si[32];
+    for (int s = 16; s > 0; s >>= 1) { re += __shfl_xor_sync(0xffffffffu, re, s); im += __shfl_xor_sync(0xffffffffu, im, s); }
+    if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = re; si[threadIdx.x >> 5] = im; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        re = threadIdx.x < blockDim.x / 32 ? sr[threadIdx.x] : 0.0;
+        im = threadIdx.x < blockDim.x / 32 ? si[threadIdx.x] : 0.0;
+        for (int s = 16; s > 0; s >>= 1) { re += __shfl_xor_sync(0xffffffffu, re, s); im += __shfl_xor_sync(0xffffffffu, im, s); }
+        if (threadIdx.x == 0) h[int64_t(r) * ldh + j] = make_double2(re, im);
+    }
+}
+
+// w[r] -= sum_{j<k} h[r][j] V_j[r]
+__global__ void k_orth_update(const double2 *__restrict__ V, int64_t ldv, int64_t kstride, double2 *__restrict__ w,
+                              int64_t n, int32_t k, const int32_t *__restrict__ active, const double2 *__restrict__ h,
+                              int32_t ldh, int32_t R) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n * R) return;
+    int64_t r = i / n, e = i % n;
+    if (!active[r]) return;
+    double2 acc = w[r * ldv + e];
+    const double2 *hr = h + r * ldh;
+    const double2 *v = V + r * ldv + e;
+    for (int32_t j = 0; j < k; ++j) acc = csub(acc, cmul(hr[j], v[int64_t(j) * kstride]));
+    w[r * ldv + e] = acc;
+}
+
+// V_k[r] = w[r] * scale[r]
+__global__ void k_scale_store(const double2 *__restrict__ w, int64_t ldv, double2 *__restrict__ V, int64_t kstride,
+                              int32_t k, int64_t n, const double *__restrict__ scale, const int32_t *__restrict__ active,
+                              int32_t R) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n * R) return;
+    int64_t r = i / n, e = i % n;
+    if (!active[r]) return;
+    V[int64_t(k) * kstride + r * ldv + e] = cscale(w[r * ldv + e], scale[r]);
+}
+
+// x[r] += sum_j y[r][j] V_j[r]
+__global__ void k_update_x(const double2 *__restrict__ V, int64_t ldv, int64_t kstride, double2 *__restrict__ x,
+                           int64_t n, const int32_t *__restrict__ kr, const double2 *__restrict__ y, int32_t ldy,
+                           int32_t R) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n * R) return;
+    int64_t r = i / n, e = i % n;
+    double2 acc = x[r * ldv + e];
+    for (int32_t j = 0; j < kr[r]; ++j) acc = cadd(acc, cmul(y[r * ldy + j], V[int64_t(j) * kstride + r * ldv + e]));
+    x[r * ldv + e] = acc;
+}
+
+__global__ void k_sub(const double2 *__restrict__ a, const double2 *__restrict__ b, double2 *__restrict__ c, int64_t n) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = csub(a[i], b[i]);
+}
+
+}  // namespace
+
+extern "C" int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
+                                  void *cuda_stream) {
+    if (!p || !y || !z || !omega || nrhs < 1) return fail(SIE_ERR_ARG, "pfft_precond_apply: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    (void)cudaGetLastError();
+    std::vector<int32_t> slot;
+    int rc = pc_prepare(p, omega, nrhs, slot, st);
+    if (rc) return rc;
+    rc = pc_apply_async(p, (const double2 *)y, (double2 *)z, nrhs, st);
+    if (rc) return rc;
+    SIE_CUDA(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
+extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
+                         const sie_solve_opts *opts, sie_c64 *Z_out, sie_solve_stats *st_out) {
+    if (!p || !freqs || nf < 1 || !ports || np < 1 || !opts || !Z_out) return fail(SIE_ERR_ARG, "sie_solve: bad argument");
+    for (int32_t i = 0; i < np; ++i)
+        if (ports[i] < 0 || ports[i] >= p->np) return fail(SIE_ERR_ARG, "sie_solve: port index out of range");
+    for (int32_t i = 0; i < nf; ++i)
+        if (!(freqs[i] > 0.0) || !std::isfinite(freqs[i]))
+            return fail(SIE_ERR_ARG, "sie_solve: frequencies must be positive (the surface impedance model has no DC limit)");
+    const int m = std::max(1, std::min(opts->restart, 1000));
+    if (!(opts->tol > 0.0) || opts->max_iter < 1) return fail(SIE_ERR_ARG, "sie_solve: bad tolerance or iteration cap");
+    if (opts->prec != SIE_PREC_FP64 && opts->prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "sie_solve: bad precision");
+    (void)cudaGetLastError();
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = p->stream;
+    const int32_t R = nf * np;
+    const int64_t n = p->nl;
+    std::vector<double> om(R);
+    for (int32_t f = 0; f < nf; ++f)
+        for (int32_t q = 0; q < np; ++q) om[f * np + q] = 2.0 * M_PI * freqs[f];
+    const bool use_pc = opts->precond != 0;
+    std::vector<int32_t> slot;
+    int rc;
+    if (use_pc && (rc = pc_prepare(p, om.data(), R, slot, st))) return rc;
+    // device buffers: V [m+1][R][n], w [R][n], b [R][n], x [R][n], t [R][n]
+    const int64_t ldv = n, kstride = int64_t(R) * n, mstride = kstride;
+    double2 *V = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *t = nullptr, *dh = nullptr;
+    int32_t *act = nullptr, *dk = nullptr;
+    double *scl = nullptr;
+    auto cleanup = [&]() {
+        for (void *a : {(void *)V, (void *)w, (void *)b, (void *)x, (void *)t, (void *)dh, (void *)act, (void *)dk,
+                        (void *)scl})
+            if (a) cudaFree(a);
+    };
+#define GM_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); set_error(std::string(#call) + ": " + cudaGetErrorString(_e)); return _e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA; } } while (0)
+#define GM_RC(expr) do { int _r = (expr); if (_r) { cleanup(); return _r; } } while (0)
+    GM_CUDA(cudaMalloc((void **)&V, size_t(m + 1) * kstride * sizeof(double2)));
+    GM_CUDA(cudaMalloc((void **)&w, size_t(R) * n * sizeof(double2)));
+    GM_CUDA(cudaMalloc((void **)&b, size_t(R) * n * sizeof(double2)));
+    GM_CUDA(cudaMalloc((void **)&x, size_t(R) * n * sizeof(double2)));
+    GM_CUDA(cudaMalloc((void **)&t, size_t(R) * n * sizeof(double2)));
+    GM_CUDA(cudaMalloc((void **)&dh, size_t(R) * (m + 2) * sizeof(double2)));
+    GM_CUDA(cudaMalloc((void **)&act, size_t(R) * sizeof(int32_t)));
+    GM_CUDA(cudaMalloc((void **)&dk, size_t(R) * sizeof(int32_t)));
+    GM_CUDA(cudaMalloc((void **)&scl, size_t(R) * sizeof(double)));
+    GM_CUDA(cudaMemsetAsync(V, 0, size_t(m + 1) * kstride * sizeof(double2), st));
+    GM_CUDA(cudaMemsetAsync(b, 0, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(cudaMemsetAsync(x, 0, size_t(R) * n * sizeof(double2), st));
+    for (int32_t f = 0; f < nf; ++f)
+        for (int32_t q = 0; q < np; ++q) {
+            double2 one = make_double2(1.0, 0.0);
+            int64_t pl = p->loops->loop_of_branch[p->nb + ports[q]];
+            GM_CUDA(cudaMemcpyAsync(b + int64_t(f * np + q) * n + pl, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
+        }
+    auto apply_op = [&](const double2 *in, double2 *out) -> int {   // out = P^-1 Z in
+        int r2 = matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, opts->prec, st);
+        if (r2) return r2;
+        if (use_pc) return pc_apply_async(p, t, out, R, st);
+        return SIE_OK;
+    };
+    auto dots = [&](const double2 *vec, int32_t k, std::vector<double2> &h) -> int {   // h[r][j] for j < k
+        k_dots<<<R * k, 256, 0, st>>>(V, ldv, mstride, vec, n, k, act, dh, m + 2);
+        SIE_LAUNCH_CHECK(p);
+        h.resize(size_t(R) * (m + 2));
+        SIE_CUDA(cudaMemcpyAsync(h.data(), dh, size_t(R) * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        SIE_CUDA(cudaStreamSynchronize(st));
+        return SIE_OK;
+    };
+    // norms via a dot with itself: place the vector in V's slot m temporarily is avoided by a separate pass
+    auto norms = [&](const double2 *vec, std::vector<double> &nr) -> int {
+        // reuse k_dots on a one-vector "basis" = vec itself
+        k_dots<<<R, 256, 0, st>>>(vec, ldv, ldv, vec, n, 1, act, dh, m + 2);
+        SIE_LAUNCH_CHECK(p);
+        std::vector<double2> h(size_t(R) * (m + 2));
+        SIE_CUDA(cudaMemcpyAsync(h.data(), dh, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        SIE_CUDA(cudaStreamSynchronize(st));
+        nr.resize(R);
+        for (int32_t r = 0; r < R; ++r) nr[r] = std::sqrt(std::max(h[size_t(r) * (m + 2)].x, 0.0));
+        return SIE_OK;
+    };
+    std::vector<int32_t> active(R, 1), done(R, 0), iters(R, 0);
+    std::vector<double> bnorm(R), resid(R, 1.0);
+    GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // ||P^-1 b||
+    if (use_pc) GM_RC(pc_apply_async(p, b, w, R, st));
+    else GM_CUDA(cudaMemcpyAsync(w, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    GM_RC(norms(w, bnorm));
+    int64_t matvecs = 0;
+    using cd = std::complex<double>;
+    int total_iters = 0;
+    bool breakdown = false;
+    while (true) {
+        // residual r = P^-1 (b - Z x)
+        GM_RC(apply_op(x, w));   // w = P^-1 Z x
+        matvecs += R;
+        if (use_pc) {
+            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, t, int64_t(R) * n);   // t = b - Z x (t held Z x)
+            SIE_LAUNCH_CHECK(p);
+            GM_RC(pc_apply_async(p, t, w, R, st));
+        } else {
+            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, w, w, int64_t(R) * n);
+            SIE_LAUNCH_CHECK(p);
+        }
+        std::vector<double> beta;
+        GM_RC(norms(w, beta));
+        bool any = false;
+        for (int32_t r = 0; r < R; ++r) {
+            resid[r] = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+            if (!std::isfinite(resid[r])) breakdown = true;
+            active[r] = !done[r] && !(resid[r] < opts->tol) && iters[r] < opts->max_iter && bnorm[r] > 0 &&
+                        std::isfinite(resid[r]);
+            if (resid[r] < opts->tol) done[r] = 1;
+            any |= active[r] != 0;
+        }
+        if (!any || breakdown) break;
+        GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        std::vector<double> sc(R);
+        for (int32_t r = 0; r < R; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+        GM_CUDA(cudaMemcpyAsync(scl, sc.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, 0, n, scl, act, R);
+        SIE_LAUNCH_CHECK(p);
+        // Arnoldi with Givens, per right-hand side
+        std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m, 0.0));
+        std::vector<std::vector<cd>> cs(R, std::vector<cd>(m)), sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1, 0.0));
+        for (int32_t r = 0; r < R; ++r) g[r][0] = beta[r];
+        std::vector<int32_t> kdone(R, 0);
+        std::vector<int32_t> run(active);
+        for (int k = 0; k < m; ++k) {
+            bool any_run = false;
+            for (int32_t r = 0; r < R; ++r) any_run |= run[r] != 0;
+            if (!any_run) break;
+            GM_CUDA(cudaMemcpyAsync(act, run.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            // w = P^-1 Z v_k
+            GM_RC(apply_op(V + int64_t(k) * kstride, w));
+            matvecs += R;
+            std::vector<double2> h1, h2;
+            GM_RC(dots(w, k + 1, h1));   // CGS pass 1
+            k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, act, dh, m + 2, R);
+            SIE_LAUNCH_CHECK(p);
+            GM_RC(dots(w, k + 1, h2));   // CGS pass 2
+            k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, act, dh, m + 2, R);
+            SIE_LAUNCH_CHECK(p);
+            std::vector<double> hn;
+            GM_RC(norms(w, hn));
+            std::vector<double> sc2(R, 0.0);
+            for (int32_t r = 0; r < R; ++r) {
+                if (!run[r]) continue;
+                std::vector<cd> col(k + 2);
+                for (int j = 0; j <= k; ++j)
+                    col[j] = cd(h1[size_t(r) * (m + 2) + j].x + h2[size_t(r) * (m + 2) + j].x,
+                                h1[size_t(r) * (m + 2) + j].y + h2[size_t(r) * (m + 2) + j].y);
+                col[k + 1] = hn[r];
+                if (!std::isfinite(hn[r])) { breakdown = true; run[r] = 0; continue; }
+                for (int i = 0; i < k; ++i) {   // rotation i: [[conj c, conj s], [-s, c]]
+                    cd tmp = std::conj(cs[r][i]) * col[i] + std::conj(sn[r][i]) * col[i + 1];
+                    col[i + 1] = -sn[r][i] * col[i] + cs[r][i] * col[i + 1];
+                    col[i] = tmp;
+                }
+                double den = std::sqrt(std::norm(col[k]) + std::norm(col[k + 1]));
+                cs[r][k] = den > 0 ? col[k] / den : cd(1.0);
+                sn[r][k] = den > 0 ? col[k + 1] / den : cd(0.0);
+                col[k] = den;
+                col[k + 1] = 0.0;
+                g[r][k + 1] = -sn[r][k] * g[r][k];
+                g[r][k] = std::conj(cs[r][k]) * g[r][k];
+                for (int j = 0; j <= k; ++j) H[r][size_t(j) * m + k] = col[j];
+                kdone[r] = k + 1;
+                iters[r] += 1;
+                resid[r] = std::abs(g[r][k + 1]) / bnorm[r];
+                sc2[r] = hn[r] > 0 ? 1.0 / hn[r] : 0.0;
+                if (resid[r] < opts->tol || iters[r] >= opts->max_iter || hn[r] == 0.0) run[r] = 0;
+            }
+            total_iters = std::max(total_iters, k + 1);
+            if (k + 1 < m) {
+                GM_CUDA(cudaMemcpyAsync(scl, sc2.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
+                k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, k + 1, n, scl, act, R);
+                SIE_LAUNCH_CHECK(p);
+            }
+        }
+        // x += V y, y from the triangular system
+        std::vector<double2> yv(size_t(R) * (m + 1), make_double2(0.0, 0.0));
+        for (int32_t r = 0; r < R; ++r) {
+            int kk = kdone[r];
+            std::vector<cd> yy(kk);
+            for (int i = kk - 1; i >= 0; --i) {
+                cd s = g[r][i];
+                for (int j = i + 1; j < kk; ++j) s -= H[r][size_t(i) * m + j] * yy[j];
+                yy[i] = s / H[r][size_t(i) * m + i];
+            }
+            for (int i = 0; i < kk; ++i) yv[size_t(r) * (m + 1) + i] = make_double2(yy[i].real(), yy[i].imag());
+        }
+        double2 *dy = nullptr;
+        GM_CUDA(cudaMalloc((void **)&dy, yv.size() * sizeof(double2)));
+        GM_CUDA(cudaMemcpyAsync(dy, yv.data(), yv.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        GM_CUDA(cudaMemcpyAsync(dk, kdone.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_update_x<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, x, n, dk, dy, m + 1, R);
+        SIE_LAUNCH_CHECK(p);
+        GM_CUDA(cudaStreamSynchronize(st));
+        cudaFree(dy);
+        for (int32_t r = 0; r < R; ++r)
+            if (active[r] && resid[r] < opts->tol) done[r] = 1;
+        bool cont = false;
+        for (int32_t r = 0; r < R; ++r) cont |= !done[r] && iters[r] < opts->max_iter;
+        if (!cont) break;
+        for (int32_t r = 0; r < R; ++r) active[r] = !done[r] && iters[r] < opts->max_iter;
+        GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    // port currents -> Y -> Z
+    std::vector<double2> xh(size_t(R) * n);
+    GM_CUDA(cudaMemcpyAsync(xh.data(), x, xh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    GM_CUDA(cudaStreamSynchronize(st));
+    int32_t nnc = 0, itmax = 0, itsum = 0;
+    double rmax = 0.0;
+    for (int32_t r = 0; r < R; ++r) {
+        nnc += !(resid[r] < opts->tol);
+        itmax = std::max(itmax, iters[r]);
+        itsum += iters[r];
+        rmax = std::max(rmax, resid[r]);
+    }
+    for (int32_t f = 0; f < nf; ++f) {
+        // Y[q][p] = current in port q's loop with port p driven; Z = Y^-1 (Gauss-Jordan)
+        std::vector<cd> Y(size_t(np) * np), Zi(size_t(np) * np, 0.0);
+        for (int32_t q = 0; q < np; ++q)
+            for (int32_t pp = 0; pp < np; ++pp) {
+                int64_t pl = p->loops->loop_of_branch[p->nb + ports[q]];
+                double2 v = xh[size_t(f * np + pp) * n + pl];
+                Y[size_t(q) * np + pp] = cd(v.x, v.y);
+            }
+        for (int32_t i = 0; i < np; ++i) Zi[size_t(i) * np + i] = 1.0;
+        for (int32_t c = 0; c < np; ++c) {
+            int32_t piv = c;
+            for (int32_t r2 = c + 1; r2 < np; ++r2)
+                if (std::abs(Y[size_t(r2) * np + c]) > std::abs(Y[size_t(piv) * np + c])) piv = r2;
+            for (int32_t j = 0; j < np; ++j) { std::swap(Y[size_t(c) * np + j], Y[size_t(piv) * np + j]); std::swap(Zi[size_t(c) * np + j], Zi[size_t(piv) * np + j]); }
+            cd d = Y[size_t(c) * np + c];
+            if (d == cd(0.0)) { cleanup(); return fail(SIE_ERR_BREAKDOWN, "sie_solve: singular port admittance matrix"); }
+            for (int32_t j = 0; j < np; ++j) { Y[size_t(c) * np + j] /= d; Zi[size_t(c) * np + j] /= d; }
+            for (int32_t r2 = 0; r2 < np; ++r2) {
+                if (r2 == c) continue;
+                cd fct = Y[size_t(r2) * np + c];
+                for (int32_t j = 0; j < np; ++j) { Y[size_t(r2) * np + j] -= fct * Y[size_t(c) * np + j]; Zi[size_t(r2) * np + j] -= fct * Zi[size_t(c) * np + j]; }
+            }
+        }
+        for (int32_t i = 0; i < np * np; ++i) Z_out[size_t(f) * np * np + i] = sie_c64{Zi[i].real(), Zi[i].imag()};
+    }
+    cleanup();
+    if (st_out) {
+        st_out->iterations_max = itmax;
+        st_out->iterations_sum = itsum;
+        st_out->n_not_converged = nnc;
+        st_out->residual_max = rmax;
+        st_out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        st_out->matvecs = matvecs;
+    }
+#undef GM_CUDA
+#undef GM_RC
+    if (breakdown) return fail(SIE_ERR_BREAKDOWN, "sie_solve: non-finite value in the Arnoldi recurrence");
+    if (nnc) return fail(SIE_ERR_NOT_CONVERGED, "sie_solve: " + std::to_string(nnc) + " right-hand sides did not converge");
+    return SIE_OK;
+}
