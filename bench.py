@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the pFFT matvec and preconditioned loop-basis GMRES on GB300.
+
+Workload (default): 8 bond wires (Au, r = 12.5 um 16-gon, 2 mm, pitch 100 um,
+40,192 triangles, 20,096 loops), pFFT grid 128 x 64 x 32, 16 log-spaced
+frequencies 1 MHz - 10 GHz x 8 ports = 128 right-hand sides.
+
+One step = one application of the preconditioned loop operator
+z = P(w)^-1 A Z_b(w) A^T x to all 128 right-hand sides (mixed precision: FP32
+grid, FFT and near field; FP64 loop maps and preconditioner), i.e. 128 pFFT
+matvecs.  `value` = matvecs per second over all ranks.  Beside it: the plain
+FP64 form, GMRES time to a 1e-6 preconditioned residual (plain and mixed), the
+roofline of the dominant stage (device time from CUDA events recorded on the
+launching stream during the timed region), an end-to-end number through host
+buffers, clocks sampled during the timed region and the CPU oracle baseline.
+
+--impl reference times the plain FP64 CPU oracle on a bounded sample of the
+same workload (see cpu_oracle_rate).  Multi-GPU: independent replicas (the
+method has no exchange step on one geometry); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PLAN_PARAMS = dict(order=3, near_factor=4.0, near_min_diam=2.0, n_touch=16, h0=0.0)
+
+
+def workload(name):
+    import synth
+    w = synth.WORKLOADS[name]()
+    m = w["mesh"]
+    return w, m
+
+
+def rhs_omegas(freqs, nports):
+    return np.repeat(2 * np.pi * np.asarray(freqs), nports)
+
+
+def peaks():
+    if os.path.exists(MEASURED):
+        with open(MEASURED) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d.get("bf16_tflops"), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------ algorithmic bytes per stage launch
+
+def stage_bytes(stage, plan_info, R, mixed, Ng, Nx, My, Mz, nt, Q, n_near, nl, nb, O=3):
+    cb = 8 if mixed else 16                   # grid complex size
+    rb = 4 if mixed else 8                    # real size
+    if stage == "fft_plane_fwd":
+        return 3 * R * (Ng + Nx * My * Mz) * cb
+    if stage == "fft_pencil":
+        return 3 * R * 2 * Nx * My * Mz * cb + (Nx + 1) * (My // 2 + 1) * (Mz // 2 + 1) * rb
+    if stage == "fft_plane_inv":
+        return 3 * R * (Nx * My * Mz + Ng) * cb
+    if stage == "near":
+        # L_d read once, point potentials + currents read once, y_tri written once
+        return n_near * 9 * rb + R * nt * Q * 3 * cb + R * nt * 3 * cb + R * nt * 3 * 16
+    if stage == "project":
+        return R * nt * Q * 3 * cb + 3 * R * Ng * cb + nt * Q * O ** 3 * (4 + rb)
+    if stage == "interp":
+        return 3 * R * Ng * cb + R * nt * Q * 3 * cb
+    if stage == "point_currents":
+        return R * nt * 3 * cb + R * nt * Q * 3 * cb
+    if stage == "loop_to_branch":
+        return R * nl * 16 + R * nt * 3 * cb
+    if stage == "branch_to_loop":
+        return R * nt * 3 * 16 + R * nl * 16
+    if stage == "precond_apply":
+        return 2 * R * nl * 16
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def aggregate(local_seconds, local_units, dist):
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    if dist is None:
+        return local_units / local_seconds, local_seconds
+    import torch
+    t = torch.tensor([local_seconds], dtype=torch.float64)
+    u = torch.tensor([local_units], dtype=torch.float64)
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t, u = t.to(dev), u.to(dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def cpu_oracle_rate(name, steps=1, warmup=0):
+    """Plain FP64 oracle pFFT matvec (oracle.pfft, unchanged) on a bounded sample.
+
+    The oracle's set-up for the full array is minutes of CPU; the sample is one
+    of the array's wires (its first conductor) on the full array's grid, so the
+    FFT convolution is the full-size one.  Per right-hand side:
+      t(full) = t_fft + (wires) * (t_sample - t_fft)
+    (projection, interpolation, near field, Gram and loop maps grow with the
+    triangle count; the FFT part does not)."""
+    import synth
+    from synth.meshes import Mesh
+    from oracle.graph import build_loops
+    from oracle.pfft import PfftSystem, PfftParams
+    w, m = workload(name)
+    ncond = m.ncond
+    if ncond > 1:
+        keep = np.nonzero(m.cond == 0)[0]
+        vmap = -np.ones(m.nv, np.int64)
+        used = np.unique(m.tri[keep])
+        vmap[used] = np.arange(used.shape[0])
+        sub = Mesh(xyz=m.xyz[used], tri=vmap[m.tri[keep]].astype(np.int32), cond=np.zeros(keep.shape[0], np.int32),
+                   sigma=m.sigma[:1], ports=[m.ports[0]])
+    else:
+        sub = m
+    O = build_loops(sub)
+    box = m.bbox()   # the full array's box: the sample's FFT is the full-size one
+    params = PfftParams(grid=w["grid"], box=box, **{k: v for k, v in PLAN_PARAMS.items() if k != "h0"})
+    S = PfftSystem(sub, O, params)
+    x = synth.complex_gaussian(O.nl, 1, seed=7)[0]
+    om = 2 * np.pi * 1e9
+    for _ in range(warmup):
+        S.matvec(x, om)
+    t_mv, t_fft = [], []
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        S.matvec(x, om)
+        t_mv.append(time.perf_counter() - t0)
+        g = np.zeros((3,) + tuple(S.op.N), complex)
+        t0 = time.perf_counter()
+        for c in range(3):
+            S.op.convolve(g[c])
+        t_fft.append(time.perf_counter() - t0)
+    tm, tf = float(np.median(t_mv)), float(np.median(t_fft))
+    wires = max(1, ncond)
+    t_full = tf + wires * max(tm - tf, 0.0)
+    sample = (f"conductor 0 of {wires} ({sub.nt} triangles, {O.nl} loops) on the full "
+              f"{'x'.join(map(str, w['grid']))} grid, 1 RHS at 1 GHz; full-array time per RHS = "
+              f"t_fft + {wires} x (t_sample - t_fft); t_sample = {tm:.3f} s, t_fft = {tf:.3f} s")
+    return 1.0 / t_full, sample, t_full
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bondwires_8x2mm_40k")
+    ap.add_argument("--no-gmres", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w, m = workload(args.workload)
+    freqs = w["freqs"]
+    nports = len(m.ports)
+    R = len(freqs) * nports
+    metric = "pFFT matvecs/s; GMRES time-to-1e-6 residual, plain vs mixed/learned form"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        nthreads = os.cpu_count()
+        t0 = time.perf_counter()
+        rate, sample, t_full = cpu_oracle_rate(args.workload, steps=args.steps, warmup=args.warmup)
+        wall = time.perf_counter() - t0
+        line = {"impl": "reference", "metric": metric, "value": rate, "unit": "matvec/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_full,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": w["name"], "rhs_per_step": 1},
+                "cpu_baseline": {"value": rate, "unit": "matvec/s", "cores": nthreads, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": rate, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": wall}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as tdist
+    dist = None
+    if world > 1:
+        tdist.init_process_group("nccl")
+        dist = tdist
+    torch.cuda.set_device(local)
+    from paper_2210_04891_gb300 import api, SPACE_LOOP, PREC_FP64, PREC_MIXED
+
+    M = api.Mesh.from_synth(m)
+    L = api.Loops(M, m.ports)
+    P = api.Plan(M, L, dict(PLAN_PARAMS, grid=w["grid"]))
+    info = P.info()
+    om = rhs_omegas(freqs, nports)
+    import synth
+    x = torch.from_numpy(synth.complex_gaussian(L.nl, R, seed=7)).cuda()
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        api.pfft_matvec(P, x, om, SPACE_LOOP, prec, out=y)
+        api.pfft_precond_apply(P, y, om, out=z)
+
+    def timed(prec, K, W, profile=False):
+        for _ in range(W):
+            step(prec)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        l0 = P.launches()
+        if profile:
+            P.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        prof = P.profile_read() if profile else None
+        if profile:
+            P.profile(False)
+        return e0.elapsed_time(e1) / 1e3, P.launches() - l0, prof
+
+    K, W = args.steps, max(3, args.warmup)
+    # mixed form: the headline
+    sampler = ClockSampler(local)
+    step(PREC_MIXED)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_mixed, launches, prof = timed(PREC_MIXED, K, W, profile=True)
+    clocks = sampler.stop()
+    value, tmax = aggregate(t_mixed, R * K, dist)
+    # plain FP64 form
+    t_plain, _, _ = timed(PREC_FP64, max(3, K // 3), 2)
+    value_plain, _ = aggregate(t_plain, R * max(3, K // 3), dist)
+
+    # roofline of the dominant stage
+    hbm, bf16, src = peaks()
+    nt, Q = info["n_tri"], 7
+    Nx, Ny, Nz = w["grid"]
+    dom = max((s for s in prof if prof[s][1] > 0), key=lambda s: prof[s][0])
+    ms_dom, n_dom = prof[dom]
+    algo = stage_bytes(dom, info, R, True, Nx * Ny * Nz, Nx, 2 * Ny, 2 * Nz, nt, Q, info["n_near_pairs"],
+                       L.nl, L.nb)
+    stage_table = {s: {"ms_per_step": v[0] / K, "launch_groups": v[1]} for s, v in prof.items() if v[1]}
+    roofline = None
+    if algo:
+        achieved = algo / (ms_dom / n_dom / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "kernel": dom, "peak_source": src,
+                    "algorithmic_bytes_per_launch": algo, "launch_ms": ms_dom / n_dom}
+
+    # end to end through host buffers (pinned)
+    xh = x.cpu().pin_memory()
+    zh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        x.copy_(xh, non_blocking=True)
+        step(PREC_MIXED)
+        zh.copy_(z, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ke = max(3, K // 2)
+    e0.record(stream)
+    for _ in range(Ke):
+        x.copy_(xh, non_blocking=True)
+        step(PREC_MIXED)
+        zh.copy_(z, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_val, _ = aggregate(e0.elapsed_time(e1) / 1e3, R * Ke, dist)
+    e2e = {"value": e2e_val, "unit": "matvec/s", "h2d_bytes_per_step": int(xh.numel() * 16),
+           "d2h_bytes_per_step": int(zh.numel() * 16)}
+
+    gm = None
+    if not args.no_gmres:
+        gm = {"tol": 1e-6, "rhs": R}
+        for nm, prec in (("plain_fp64", PREC_FP64), ("mixed", PREC_MIXED)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Z, st = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=400, prec=prec)
+            dt = time.perf_counter() - t0
+            gm[nm] = {"seconds": dt, "iterations_max": st["iterations_max"], "converged": st["converged"],
+                      "residual_max": st["residual_max"], "matvecs": st["matvecs"]}
+            if nm == "plain_fp64":
+                Zref = Z
+        gm["mixed_vs_plain_Z_rel"] = float(np.abs(Z - Zref).max() / np.abs(Zref).max())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, sample, _ = cpu_oracle_rate(args.workload, steps=2, warmup=0)
+        cpu = {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": "matvec/s", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": 1e3 * tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": w["name"], "triangles": int(m.nt), "loops": int(L.nl),
+                           "grid": list(w["grid"]), "rhs_per_step": R, "frequencies": len(freqs), "ports": nports,
+                           "near_pairs": info["n_near_pairs"], "step": "z = P^-1 A Z_b A^T x (mixed)",
+                           "l2": "inputs larger than L2 (per-step grids and spectra ~4 GB)",
+                           "parallelism": f"replicas x{world}"},
+                "plain_fp64": {"value": value_plain, "unit": "matvec/s", "ms_per_step": 1e3 * t_plain / max(3, K // 3)},
+                "gmres": gm, "roofline": roofline, "stages": stage_table, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

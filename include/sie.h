@@ -196,6 +196,19 @@ int pfft_plan_export(const pfft_plan *p, int32_t what, void *host_out, int64_t c
  * d = 0) via the zero-padded FFT. */
 int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream);
 
+/* Stage timing (tracing).  When enabled, every stage of pfft_matvec,
+ * pfft_precond_apply and sie_solve is bracketed by CUDA events recorded on the
+ * stream the stage runs on; pfft_profile_read waits for them and returns the
+ * accumulated device time (ms) and launch count of each stage since the last
+ * enable.  Disabled by default; enabling resets the counters. */
+enum { SIE_STAGE_LOOP_TO_BRANCH = 0, SIE_STAGE_POINT_CURRENTS = 1, SIE_STAGE_PROJECT = 2,
+       SIE_STAGE_FFT_PLANE_FWD = 3, SIE_STAGE_FFT_PENCIL = 4, SIE_STAGE_FFT_PLANE_INV = 5,
+       SIE_STAGE_INTERP = 6, SIE_STAGE_NEAR = 7, SIE_STAGE_BRANCH_TO_LOOP = 8,
+       SIE_STAGE_PRECOND_APPLY = 9, SIE_STAGE_PRECOND_FACTOR = 10, SIE_STAGE_ARNOLDI = 11,
+       SIE_NSTAGES = 12 };
+int pfft_profile_enable(pfft_plan *p, int32_t on);
+int pfft_profile_read(pfft_plan *p, double *ms /* [SIE_NSTAGES] */, int64_t *launches /* [SIE_NSTAGES] */);
+
 /* Number of this library's kernel launches since the plan was created. */
 int64_t pfft_plan_launches(const pfft_plan *p);
 

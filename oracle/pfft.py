@@ -48,10 +48,11 @@ class PfftParams:
     near_min_diam: float = 2.0  # r_near >= near_min_diam * max triangle diameter
     n_touch: int = 16         # collapsed-Gauss order for touching near pairs
     h0: float = 0.0           # H at zero offset
+    box: tuple = None         # (lo, hi) grid box; default the mesh's bounding box
 
 
-def grid_of(mesh, N):
-    lo, hi = mesh.bbox()
+def grid_of(mesh, N, box=None):
+    lo, hi = mesh.bbox() if box is None else (np.asarray(box[0], float), np.asarray(box[1], float))
     N = np.asarray(N, dtype=np.int64)
     h = (hi - lo) / (N - 1)
     return lo, h, N
@@ -79,7 +80,7 @@ class Pfft:
     def __init__(self, mesh, loops, params: PfftParams, rule=None):
         self.mesh, self.loops, self.p = mesh, loops, params
         self.rule = radon7() if rule is None else rule
-        self.lo, self.h, self.N = grid_of(mesh, params.grid)
+        self.lo, self.h, self.N = grid_of(mesh, params.grid, params.box)
         g = tri_geometry(mesh.xyz, mesh.tri)
         self.geo = g
         nt = mesh.nt

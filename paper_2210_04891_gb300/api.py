@@ -140,6 +140,16 @@ class Plan:
         check(lib().pfft_plan_export(self.h, what, _ptr(out), out.nbytes))
         return out
 
+    def profile(self, on=True):
+        check(lib().pfft_profile_enable(self.h, int(on)))
+
+    def profile_read(self):
+        """{stage: (ms, launches)} accumulated since profile(True)."""
+        ms = np.zeros(len(N.STAGES))
+        cnt = np.zeros(len(N.STAGES), np.int64)
+        check(lib().pfft_profile_read(self.h, _ptr(ms), _ptr(cnt)))
+        return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(N.STAGES)}
+
     def launches(self):
         return int(lib().pfft_plan_launches(self.h))
 
@@ -185,11 +195,13 @@ def pfft_convolve(plan: Plan, grid, prec=N.PREC_FP64, stream=None):
     return grid
 
 
-def pfft_precond_apply(plan: Plan, y, omega, stream=None):
+def pfft_precond_apply(plan: Plan, y, omega, out=None, stream=None):
+    """z = P(omega)^-1 y, P = A diag(Z_b) A^T, for y [nrhs, n_loops]."""
     import torch
     _check_vec(y, plan.nl, "y")
     om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, np.float64), (y.shape[0],)))
-    z = torch.empty_like(y)
+    z = torch.empty_like(y) if out is None else out
+    _check_vec(z, plan.nl, "out")
     check(lib().pfft_precond_apply(plan.h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(z.data_ptr()),
                                    y.shape[0], _ptr(om), _stream(stream)))
     return z

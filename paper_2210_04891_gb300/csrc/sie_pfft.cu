@@ -17,6 +17,7 @@
 // Both are exact rewrites of the sparse products (no approximation).
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "sie_plan.h"
@@ -366,6 +367,7 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     } else {
         mom = (const T *)p->d_mom32; lw = (const T *)p->d_lw32; pjw = (const T *)p->d_pj_w32; Ld = (const T *)p->d_Ld32;
     }
+    std::unique_ptr<StageTimer> tm(new StageTimer(p, SIE_STAGE_LOOP_TO_BRANCH, st));
     if (space == SIE_SPACE_LOOP) {
         k_tour_inject<<<nblk(nslots * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tour_node, p->d_tour_enter,
                                                          p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign, R);
@@ -378,18 +380,24 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
                                                          space, p->nb, c_tri);
     SIE_LAUNCH_CHECK(p);
     const int64_t npt = p->nt * p->Q;
+    tm.reset(new StageTimer(p, SIE_STAGE_POINT_CURRENTS, st));
     k_point_currents<T><<<nblk(npt * R), 256, 0, st>>>(c_tri, mom, p->nt, p->Q, R, jq);
     SIE_LAUNCH_CHECK(p);
+    tm.reset(new StageTimer(p, SIE_STAGE_PROJECT, st));
     k_project<T><<<nblk(p->Ng * R), 256, 0, st>>>(jq, npt, p->d_pj_ptr, p->d_pj_pt, pjw, p->Ng, R, grid);
     SIE_LAUNCH_CHECK(p);
+    tm.reset();
     int rc = fft_conv(p, grid, spec, R, sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED, st);
     if (rc) return rc;
     C<T> *phiq = (C<T> *)s.phiq;
+    tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
     k_point_potentials<T><<<nblk(npt * R), 256, 0, st>>>(grid, p->d_start, lw, p->O, p->Ny, p->Nz, p->Ng, npt, R, phiq);
     SIE_LAUNCH_CHECK(p);
+    tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
     k_tri_out<T><<<nblk(p->nt * R, 128), 128, 0, st>>>(phiq, mom, c_tri, p->d_near_ptr, p->d_near_col, Ld, p->d_gram,
                                                    p->d_cond, s.coef, p->ncond, p->nt, p->Q, R, y_tri);
     SIE_LAUNCH_CHECK(p);
+    tm.reset(new StageTimer(p, SIE_STAGE_BRANCH_TO_LOOP, st));
     if (space == SIE_SPACE_BRANCH) {
         k_branch_out<<<nblk(p->nb * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, p->nb, R, y);
         SIE_LAUNCH_CHECK(p);

@@ -368,10 +368,13 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     int rc = set_smem((const void *)k_fft_plane<T>, plane_bytes);
     if (rc) return rc;
     const int thr = fft_threads(p->My * p->Mz);
+    {
+    StageTimer tm(p, SIE_STAGE_FFT_PLANE_FWD, s);
     k_fft_plane<T><<<nb, thr, plane_bytes, s>>>(grid, int64_t(p->Ny) * p->Nz, p->Ny, p->Nz, spec,
                                                int64_t(p->My) * p->Mz, p->My, p->Mz, p->My, p->Mz,
                                                twiddle<T>(p, 1), twiddle<T>(p, 2), 0);
     SIE_LAUNCH_CHECK(p);
+    }
     const int KT = 16;
     const int ncols = p->My * p->Mz;
     const size_t pb = size_t(KT) * (p->Mx + 1) * sizeof(C<T>);
@@ -379,9 +382,13 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     if (rc) return rc;
     const T *H = nullptr;
     if constexpr (sizeof(T) == 8) H = reinterpret_cast<const T *>(p->d_H64); else H = reinterpret_cast<const T *>(p->d_H32);
+    {
+    StageTimer tm(p, SIE_STAGE_FFT_PENCIL, s);
     k_fft_pencil<T><<<ngrids * (ncols / KT), fft_threads(KT * p->Mx), pb, s>>>(
         spec, int64_t(p->Nx) * ncols, ncols, p->Nx, p->Nx, p->Mx, p->My, p->Mz, KT, twiddle<T>(p, 0), H);
     SIE_LAUNCH_CHECK(p);
+    }
+    StageTimer tm(p, SIE_STAGE_FFT_PLANE_INV, s);
     k_fft_plane<T><<<nb, thr, plane_bytes, s>>>(spec, int64_t(p->My) * p->Mz, p->My, p->Mz, grid,
                                                int64_t(p->Ny) * p->Nz, p->Ny, p->Nz, p->My, p->Mz,
                                                twiddle<T>(p, 1), twiddle<T>(p, 2), 1);
@@ -747,6 +754,7 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
 extern "C" void pfft_plan_destroy(pfft_plan *p) {
     if (!p) return;
     sie::plan_free_precond(p);
+    for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void *a : p->allocations) cudaFree(a);
     // scr.phiq aliases scr.jq and is not freed separately
     for (void *a : {p->scr.tour, p->scr.c_tri, p->scr.jq, p->scr.grid, p->scr.spec, p->scr.y_tri, p->scr.y_br,
@@ -804,6 +812,34 @@ extern "C" int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t p
     }
     if (rc) return rc;
     SIE_CUDA(cudaStreamSynchronize(s));
+    return SIE_OK;
+}
+
+extern "C" int pfft_profile_enable(pfft_plan *p, int32_t on) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_profile_enable: NULL plan");
+    for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    p->prof_pending.clear();
+    for (int i = 0; i < SIE_NSTAGES; ++i) { p->prof_ms[i] = 0.0; p->prof_count[i] = 0; }
+    p->prof_on = on != 0;
+    return SIE_OK;
+}
+
+extern "C" int pfft_profile_read(pfft_plan *p, double *ms, int64_t *launches) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_profile_read: NULL plan");
+    for (auto &e : p->prof_pending) {
+        SIE_CUDA(cudaEventSynchronize(e.b));
+        float t = 0.f;
+        SIE_CUDA(cudaEventElapsedTime(&t, e.a, e.b));
+        p->prof_ms[e.stage] += t;
+        p->prof_count[e.stage] += 1;
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    p->prof_pending.clear();
+    for (int i = 0; i < SIE_NSTAGES; ++i) {
+        if (ms) ms[i] = p->prof_ms[i];
+        if (launches) launches[i] = p->prof_count[i];
+    }
     return SIE_OK;
 }
 

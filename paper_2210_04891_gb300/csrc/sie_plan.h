@@ -92,6 +92,12 @@ struct pfft_plan {
     double *d_diag_gram = nullptr;       // [nb]
     double *d_diag_L = nullptr;          // [nb]
     int32_t *d_br_cond = nullptr;        // [nb]
+    // stage timing
+    bool prof_on = false;
+    struct ProfEv { int stage; cudaEvent_t a, b; };
+    std::vector<ProfEv> prof_pending;
+    double prof_ms[SIE_NSTAGES] = {0};
+    int64_t prof_count[SIE_NSTAGES] = {0};
     sie::Scratch scr;
     sie::PrecondState *pc = nullptr;
     size_t device_bytes = 0;
@@ -99,6 +105,26 @@ struct pfft_plan {
 };
 
 namespace sie {
+// Brackets one stage with CUDA events on its stream when profiling is on.
+struct StageTimer {
+    pfft_plan *p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(pfft_plan *plan, int st, cudaStream_t stream) : p(plan), stage(st), s(stream) {
+        if (p->prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    }
+    ~StageTimer() {
+        if (!a) return;
+        cudaEvent_t b;
+        if (cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, s);
+            p->prof_pending.push_back({stage, a, b});
+        } else {
+            cudaEventDestroy(a);
+        }
+    }
+};
 int plan_alloc(pfft_plan *p, void **ptr, size_t bytes);
 void plan_free(pfft_plan *p, void *ptr);
 void plan_free_precond(pfft_plan *p);

@@ -521,6 +521,7 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     int zero = 0;
     SIE_CUDA(cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
+    StageTimer tm(p, SIE_STAGE_PRECOND_FACTOR, st);
     if (s->nunk > 0) {
         k_pc_factor<<<ns * nblk, 256, 0, st>>>(s->d_blk_off, nblk, s->W, s->nunk, s->d_row_ptr, s->d_row_br,
                                                 s->d_row_oth, s->d_a, p->nb, s->d_band, s->d_status);
@@ -538,6 +539,7 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
 
 int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream_t st) {
     PrecondState *s = p->pc;
+    StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
     k_pc_drive<<<nblk_(p->nb * R), 256, 0, st>>>(y, p->nl, s->d_a, s->d_slot, p->d_loop_of_branch, p->d_tail,
                                                  p->d_head, s->d_off_ptr, s->d_off_port, s->d_off_sign,
@@ -708,6 +710,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
         return SIE_OK;
     };
     auto dots = [&](const double2 *vec, int32_t k, std::vector<double2> &h) -> int {   // h[r][j] for j < k
+        StageTimer tm(p, SIE_STAGE_ARNOLDI, st);
         k_dots<<<R * k, 256, 0, st>>>(V, ldv, mstride, vec, n, k, act, dh, m + 2);
         SIE_LAUNCH_CHECK(p);
         h.resize(size_t(R) * (m + 2));
