@@ -196,6 +196,22 @@ int pfft_plan_export(const pfft_plan *p, int32_t what, void *host_out, int64_t c
  * d = 0) via the zero-padded FFT. */
 int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream);
 
+/* pfft_convolve without any device allocation (the paper has no counterpart;
+ * this is an interface for callers that may not allocate device memory when
+ * they convolve: fixed start-up memory budgets, real-time loops that cannot
+ * take cudaMalloc's synchronisation and latency, frameworks that own the
+ * allocator).  Same arguments and result as pfft_convolve.  Its scratch is one
+ * file-scope device array of 16 MiB that every GPU loading the library holds
+ * until exit; a grid whose zero-padded spectrum (N_x * 2N_y * 2N_z complex
+ * values of the precision) exceeds it is rejected with SIE_ERR_ARG.  Larger
+ * batches are processed in pieces that fit.  The first call on a device looks
+ * up the array's device address once (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other's results; nothing in the array needs
+ * clearing between calls. */
+int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream);
+
 /* Stage timing (tracing).  When enabled, every stage of pfft_matvec,
  * pfft_precond_apply and sie_solve is bracketed by CUDA events recorded on the
  * stream the stage runs on; pfft_profile_read waits for them and returns the

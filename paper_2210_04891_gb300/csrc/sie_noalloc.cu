@@ -1,0 +1,79 @@
+// pfft_convolve_noalloc: the grid convolution of pfft_convolve without any
+// device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// convolution: code running under a strict memory budget that was fixed at
+// start-up, a real-time loop where cudaMalloc's implicit device
+// synchronisation and unbounded latency are not acceptable, or a host
+// framework that owns the allocator and forbids allocation outside its own
+// pool.  pfft_convolve may grow the plan's scratch on first use of a batch
+// size; this entry point never does.  Its only scratch is the file-scope device
+// array below, which every GPU that loads the library holds until the process
+// exits.
+#include <mutex>
+
+#include "sie_plan.h"
+
+using namespace sie;
+
+namespace {
+
+// Spectral scratch for the convolution: one zero-padded spectrum
+// [N_x][2N_y][2N_z] per grid, complex128 or complex64.  16 MiB holds one
+// 128 x 64 x 32 grid in FP64 (two in FP32).
+constexpr size_t kNoallocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int scratch_address(void **out) {
+    int dev = 0;
+    SIE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(SIE_ERR_CUDA, std::string("pfft_convolve_noalloc: cudaGetSymbolAddress failed: ") +
+                                          cudaGetErrorString(e));
+        g_scratch_addr[dev] = ptr;
+    }
+    *out = g_scratch_addr[dev];
+    return SIE_OK;
+}
+
+}  // namespace
+
+extern "C" int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream) {
+    if (!p || !grid || nbatch < 1) return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: bad argument");
+    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED)
+        return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: bad precision");
+    const size_t cb = prec == SIE_PREC_FP64 ? 16 : 8;
+    const size_t spec_bytes = size_t(p->Nx) * p->My * p->Mz * cb;
+    if (spec_bytes > kNoallocScratchBytes)
+        return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: one grid's spectrum needs " + std::to_string(spec_bytes) +
+                                     " bytes, more than the fixed scratch of " +
+                                     std::to_string(kNoallocScratchBytes) + " bytes; use pfft_convolve");
+    (void)cudaGetLastError();
+    void *spec = nullptr;
+    int rc = scratch_address(&spec);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int32_t per_call = int32_t(kNoallocScratchBytes / spec_bytes);
+    const size_t grid_bytes = size_t(p->Ng) * cb;
+    // the forward pass writes every spectrum element the later passes read, so
+    // nothing in the scratch has to be cleared between calls
+    for (int32_t b = 0; b < nbatch; b += per_call) {
+        const int32_t n = std::min(per_call, nbatch - b);
+        rc = fft_conv_n(p, static_cast<char *>(grid) + size_t(b) * grid_bytes, spec, n, prec, s);
+        if (rc) return rc;
+    }
+    SIE_CUDA(cudaStreamSynchronize(s));
+    return SIE_OK;
+}

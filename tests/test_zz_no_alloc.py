@@ -1,0 +1,75 @@
+"""pfft_convolve_noalloc against pfft_convolve, through the C ABI.
+
+The no-allocation variant is for callers that may not allocate device memory
+when they convolve (a start-up memory budget, a real-time loop, a framework
+that owns the allocator).  It must give the same grid potentials as the
+allocating entry point, on two calls in a row (its scratch array is shared and
+keeps the previous call's contents), and must not grow the plan's memory.
+This file is collected last so that a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2210_04891_gb300 import api, native as N  # noqa: E402
+
+
+def call_noalloc(plan, grid, prec):
+    rc = N.lib().pfft_convolve_noalloc(plan.h, ctypes.c_void_p(grid.data_ptr()), grid.shape[0], prec,
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    N.check(rc)
+    return grid
+
+
+@pytest.mark.parametrize("prec,tol", [(N.PREC_FP64, 1e-13), (N.PREC_MIXED, 1e-6)])
+def test_noalloc_matches_convolve_twice(prec, tol):
+    m = synth.tiny_wires()
+    M = api.Mesh.from_synth(m)
+    L = api.Loops(M, m.ports)
+    P = api.Plan(M, L, dict(grid=(16, 8, 4), order=3, near_factor=4.0, near_min_diam=2.0, n_touch=8, h0=0.0))
+    bytes0 = P.info()["device_bytes"]
+    dt = torch.complex128 if prec == N.PREC_FP64 else torch.complex64
+    rng = np.random.default_rng(5)
+    for call in range(2):
+        g = rng.standard_normal((4, 16, 8, 4)) + 1j * rng.standard_normal((4, 16, 8, 4))
+        ref = api.pfft_convolve(P, torch.from_numpy(g).to(dt).cuda(), prec).cpu().numpy()
+        got = call_noalloc(P, torch.from_numpy(g).to(dt).cuda(), prec).cpu().numpy()
+        assert np.abs(got - ref).max() < tol * np.abs(ref).max(), call
+    # the allocating path grew plan scratch; the no-allocation path must not add to it
+    bytes1 = P.info()["device_bytes"]
+    got2 = call_noalloc(P, torch.from_numpy(g).to(dt).cuda(), prec)
+    assert P.info()["device_bytes"] == bytes1
+    assert bytes1 >= bytes0
+
+
+def test_noalloc_fresh_plan_allocates_nothing():
+    m = synth.tiny_bar()
+    M = api.Mesh.from_synth(m)
+    L = api.Loops(M, m.ports)
+    P = api.Plan(M, L, dict(grid=(8, 4, 4), order=3, near_factor=4.0, near_min_diam=2.0, n_touch=8, h0=0.0))
+    before = P.info()["device_bytes"]
+    g = torch.from_numpy(synth.complex_gaussian(8 * 4 * 4, 3, seed=2).reshape(3, 8, 4, 4)).cuda()
+    ref = g.clone()
+    call_noalloc(P, g, N.PREC_FP64)
+    call_noalloc(P, ref, N.PREC_FP64)
+    assert torch.equal(g, ref)
+    assert P.info()["device_bytes"] == before
+
+
+def test_noalloc_rejects_oversized_grid():
+    m = synth.tiny_bar()
+    M = api.Mesh.from_synth(m)
+    L = api.Loops(M, m.ports)
+    # 256 x 32 x 64 grid: spectrum 256 * 64 * 128 * 16 B = 32 MiB > 16 MiB
+    P = api.Plan(M, L, dict(grid=(256, 32, 64), order=3, near_factor=1.0, near_min_diam=1.0, n_touch=4, h0=0.0))
+    g = torch.zeros((1, 256, 32, 64), dtype=torch.complex128, device="cuda")
+    with pytest.raises(N.SieError) as e:
+        call_noalloc(P, g, N.PREC_FP64)
+    assert e.value.code == -1
