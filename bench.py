@@ -213,12 +213,13 @@ def main():
     ap.add_argument("--workload", default="bondwires_8x2mm_40k")
     ap.add_argument("--no-gmres", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nfreq", type=int, default=0, help="use only the first N frequencies (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     w, m = workload(args.workload)
-    freqs = w["freqs"]
+    freqs = w["freqs"][:args.nfreq] if args.nfreq > 0 else w["freqs"]
     nports = len(m.ports)
     R = len(freqs) * nports
     metric = "pFFT matvecs/s; GMRES time-to-1e-6 residual, plain vs mixed/learned form"
@@ -263,7 +264,7 @@ def main():
 
     def step(prec):
         api.pfft_matvec(P, x, om, SPACE_LOOP, prec, out=y)
-        api.pfft_precond_apply(P, y, om, out=z)
+        api.pfft_precond_apply(P, y, om, out=z, prec=prec)
 
     def timed(prec, K, W, profile=False):
         for _ in range(W):

@@ -156,11 +156,13 @@ int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double
 
 /* Apply the preconditioner of Eq. (Precond), z = P^-1 y with
  * P = A diag(Z_b) A^T (port links carry no impedance), for nrhs loop-space
- * vectors y, z (device complex128 [nrhs][n_loops]) at omega[r].  Factorises
- * P(omega) on first use of each distinct omega set.  Errors: SIE_ERR_BREAKDOWN
- * for a zero pivot. */
+ * vectors y, z (device complex128 [nrhs][n_loops]) at omega[r].  P is applied
+ * through the nodal Laplacian of the same circuit, factorised (FP64) per
+ * conductor on first use of each distinct omega set.  prec = SIE_PREC_FP64
+ * runs the triangular sweeps in FP64; SIE_PREC_MIXED runs them in FP32 on the
+ * rounded factor.  Errors: SIE_ERR_BREAKDOWN for a zero pivot. */
 int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
-                       void *cuda_stream);
+                       int32_t prec, void *cuda_stream);
 
 /* Port impedance extraction (Sec. III-C, V): for every frequency f and every
  * port q a unit source in port q's loop, GMRES on Eq. (LoopWithP), then

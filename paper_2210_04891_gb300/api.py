@@ -195,7 +195,7 @@ def pfft_convolve(plan: Plan, grid, prec=N.PREC_FP64, stream=None):
     return grid
 
 
-def pfft_precond_apply(plan: Plan, y, omega, out=None, stream=None):
+def pfft_precond_apply(plan: Plan, y, omega, out=None, prec=N.PREC_FP64, stream=None):
     """z = P(omega)^-1 y, P = A diag(Z_b) A^T, for y [nrhs, n_loops]."""
     import torch
     _check_vec(y, plan.nl, "y")
@@ -203,7 +203,7 @@ def pfft_precond_apply(plan: Plan, y, omega, out=None, stream=None):
     z = torch.empty_like(y) if out is None else out
     _check_vec(z, plan.nl, "out")
     check(lib().pfft_precond_apply(plan.h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(z.data_ptr()),
-                                   y.shape[0], _ptr(om), _stream(stream)))
+                                   y.shape[0], _ptr(om), prec, _stream(stream)))
     return z
 
 

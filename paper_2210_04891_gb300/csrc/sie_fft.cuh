@@ -31,15 +31,21 @@ __device__ __forceinline__ void dft4(C<T> &a0, C<T> &a1, C<T> &a2, C<T> &a3, boo
 // consecutive threads to consecutive lines (use when ls == 1) instead of
 // consecutive butterflies (use when es == 1), to keep shared accesses
 // conflict-free.  Requires nlines * M <= FFT_E * blockDim.x.
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
 template <typename T>
 __device__ void fft_lines(C<T> *s, int M, int nlines, int ls, int es, const C<T> *__restrict__ tw, bool inv,
                           bool lines_fast) {
-    int Ns = 1;
-    while (Ns < M) {
-        const int R = (M / Ns >= 4) ? 4 : 2;
-        const int nbf = M / R;                  // butterflies per line
-        const int total = nbf * nlines;
-        const int step = M / (Ns * R);
+    // every size is a power of two: index arithmetic by shifts and masks
+    const int lgM = ilog2(M), lgL = ilog2(nlines);
+    int lgNs = 0;
+    while (lgNs < lgM) {
+        const int lgR = (lgM - lgNs >= 2) ? 2 : 1;
+        const int R = 1 << lgR;
+        const int Ns = 1 << lgNs;
+        const int lgnbf = lgM - lgR;             // butterflies per line = M / R
+        const int total = nlines << lgnbf;
+        const int lgstep = lgM - lgNs - lgR;     // twiddle stride M / (Ns R)
         C<T> v[FFT_E];
 #pragma unroll
         for (int i = 0; i < FFT_E / 2; ++i) {   // at most FFT_E/R butterflies, R >= 2
@@ -47,14 +53,16 @@ __device__ void fft_lines(C<T> *s, int M, int nlines, int ls, int es, const C<T>
             if (i * blockDim.x >= total) break;
             if (it < total && i * R < FFT_E) {
                 int line, j;
-                if (lines_fast) { line = it % nlines; j = it / nlines; }
-                else { j = it % nbf; line = it / nbf; }
+                if (lines_fast) { line = it & (nlines - 1); j = it >> lgL; }
+                else { j = it & ((1 << lgnbf) - 1); line = it >> lgnbf; }
                 const C<T> *b = s + line * ls;
-                const int jm = j % Ns;
+                const int jm = j & (Ns - 1);
+                const int nbf = 1 << lgnbf;
                 if (R == 4) {
                     C<T> a0 = b[j * es], a1 = b[(j + nbf) * es], a2 = b[(j + 2 * nbf) * es], a3 = b[(j + 3 * nbf) * es];
                     if (jm) {
-                        C<T> w1 = tw[jm * step], w2 = tw[2 * jm * step], w3 = tw[3 * jm * step];
+                        const int t1 = jm << lgstep;
+                        C<T> w1 = tw[t1], w2 = tw[2 * t1], w3 = tw[3 * t1];
                         if (inv) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
                         a1 = cmul(a1, w1); a2 = cmul(a2, w2); a3 = cmul(a3, w3);
                     }
@@ -63,7 +71,7 @@ __device__ void fft_lines(C<T> *s, int M, int nlines, int ls, int es, const C<T>
                 } else {
                     C<T> a0 = b[j * es], a1 = b[(j + nbf) * es];
                     if (jm) {
-                        C<T> w1 = tw[jm * step];
+                        C<T> w1 = tw[jm << lgstep];
                         if (inv) w1.y = -w1.y;
                         a1 = cmul(a1, w1);
                     }
@@ -79,10 +87,10 @@ __device__ void fft_lines(C<T> *s, int M, int nlines, int ls, int es, const C<T>
             if (i * blockDim.x >= total) break;
             if (it < total && i * R < FFT_E) {
                 int line, j;
-                if (lines_fast) { line = it % nlines; j = it / nlines; }
-                else { j = it % nbf; line = it / nbf; }
+                if (lines_fast) { line = it & (nlines - 1); j = it >> lgL; }
+                else { j = it & ((1 << lgnbf) - 1); line = it >> lgnbf; }
                 C<T> *b = s + line * ls;
-                const int d = (j / Ns) * Ns * R + (j % Ns);
+                const int d = ((j >> lgNs) << (lgNs + lgR)) + (j & (Ns - 1));
                 if (R == 4) {
                     b[d * es] = v[4 * i]; b[(d + Ns) * es] = v[4 * i + 1];
                     b[(d + 2 * Ns) * es] = v[4 * i + 2]; b[(d + 3 * Ns) * es] = v[4 * i + 3];
@@ -92,7 +100,7 @@ __device__ void fft_lines(C<T> *s, int M, int nlines, int ls, int es, const C<T>
             }
         }
         __syncthreads();
-        Ns *= R;
+        lgNs += lgR;
     }
 }
 
@@ -109,9 +117,10 @@ __global__ void __launch_bounds__(512) k_fft_plane(const C<T> *__restrict__ src,
     C<T> *s = reinterpret_cast<C<T> *>(smem_raw);
     const C<T> *in = src + blockIdx.x * src_stride;
     const int P = My * Mz;
+    const int lgMz = ilog2(Mz), lgnzi = ilog2(nz_in), lgnzo = ilog2(nz_out);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        int y = i / Mz, z = i % Mz;
-        s[i] = (y < ny_in && z < nz_in) ? in[y * nz_in + z] : mk<T>(T(0), T(0));
+        int y = i >> lgMz, z = i & (Mz - 1);
+        s[i] = (y < ny_in && z < nz_in) ? in[(y << lgnzi) + z] : mk<T>(T(0), T(0));
     }
     __syncthreads();
     if (!inverse) {
@@ -123,8 +132,8 @@ __global__ void __launch_bounds__(512) k_fft_plane(const C<T> *__restrict__ src,
     }
     C<T> *out = dst + blockIdx.x * dst_stride;
     for (int i = threadIdx.x; i < ny_out * nz_out; i += blockDim.x) {
-        int y = i / nz_out, z = i % nz_out;
-        out[i] = s[y * Mz + z];
+        int y = i >> lgnzo, z = i & (nz_out - 1);
+        out[i] = s[(y << lgMz) + z];
     }
 }
 
@@ -146,8 +155,9 @@ __global__ void __launch_bounds__(512) k_fft_pencil(C<T> *__restrict__ buf, int6
     const int b = blockIdx.x / tiles, c0 = (blockIdx.x % tiles) * KT;
     C<T> *base = buf + b * batch_stride + c0;
     const int pitch = Mx + 1;
+    const int lgKT = ilog2(KT), lgMx = ilog2(Mx), lgMz = ilog2(Mz);
     for (int i = threadIdx.x; i < KT * Mx; i += blockDim.x) {
-        int x = i / KT, c = i % KT;
+        int x = i >> lgKT, c = i & (KT - 1);
         s[c * pitch + x] = x < nx_in ? base[int64_t(x) * ncols + c] : mk<T>(T(0), T(0));
     }
     __syncthreads();
@@ -155,8 +165,8 @@ __global__ void __launch_bounds__(512) k_fft_pencil(C<T> *__restrict__ buf, int6
     if (H) {
         const int hx = Mx / 2 + 1, hz = Mz / 2 + 1;
         for (int i = threadIdx.x; i < KT * Mx; i += blockDim.x) {
-            int c = i / Mx, kx = i % Mx;
-            int col = c0 + c, ky = col / Mz, kz = col % Mz;
+            int c = i >> lgMx, kx = i & (Mx - 1);
+            int col = c0 + c, ky = col >> lgMz, kz = col & (Mz - 1);
             T h = H[(int64_t(fold_index(ky, My)) * hz + fold_index(kz, Mz)) * hx + fold_index(kx, Mx)];
             s[c * pitch + kx] = cscale(s[c * pitch + kx], h);
         }
@@ -164,7 +174,7 @@ __global__ void __launch_bounds__(512) k_fft_pencil(C<T> *__restrict__ buf, int6
         fft_lines<T>(s, Mx, KT, pitch, 1, tw_x, true, false);
     }
     for (int i = threadIdx.x; i < KT * nx_out; i += blockDim.x) {
-        int x = i / KT, c = i % KT;
+        int x = i >> lgKT, c = i & (KT - 1);
         base[int64_t(x) * ncols + c] = s[c * pitch + x];
     }
 }

@@ -127,10 +127,11 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const dou
                             const int32_t *__restrict__ loop_of_branch, const int32_t *__restrict__ twig_node,
                             const int32_t *__restrict__ head, const int32_t *__restrict__ enter,
                             const int32_t *__restrict__ exit_, int64_t nt, int32_t nrhs, int space, int64_t nb,
-                            C<T> *__restrict__ c_tri) {
+                            C<T> *__restrict__ c_tri, C<T> *__restrict__ cT) {
+    // i = (t * 3 + k) * R + r: the RHS-innermost copy cT is written coalesced
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nt * 3 * nrhs) return;
-    int64_t r = i / (nt * 3), tk = i % (nt * 3);
+    int64_t tk = i / nrhs, r = i % nrhs;
     int32_t b = tb[tk];
     double2 a = make_double2(0.0, 0.0);
     if (b >= 0) {
@@ -140,7 +141,59 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const dou
             a = x[r * nb + b];
         if (ts[tk] < 0) { a.x = -a.x; a.y = -a.y; }
     }
-    c_tri[i] = mk<T>(T(a.x), T(a.y));
+    const C<T> v = mk<T>(T(a.x), T(a.y));
+    cT[i] = v;
+    c_tri[r * nt * 3 + tk] = v;
+}
+
+// Pre-corrected near field as a block-sparse x dense product (Eq. Lb):
+// ynear[t][k][r] = sum_{t' near t} sum_l L_d(t, t')[k][l] cT[t'][l][r].
+// One warp per (row t, chunk of 32 RB right-hand sides); each L_d block is read
+// once per chunk and applied to all of its right-hand sides, lane r reading
+// the neighbours' currents contiguously over r.
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_near_spmm(const int64_t *__restrict__ near_ptr,
+                                                   const int32_t *__restrict__ near_col, const T *__restrict__ Ld,
+                                                   const C<T> *__restrict__ cT, int64_t nt, int32_t R, int32_t nchunk,
+                                                   C<T> *__restrict__ ynear) {
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= nt * nchunk) return;
+    const int64_t t = gw / nchunk;
+    const int32_t r0 = int32_t(gw % nchunk) * 32 * RB + lane;
+    C<T> acc[3][RB];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) acc[k][j] = mk<T>(T(0), T(0));
+    const int64_t e1 = near_ptr[t + 1];
+#pragma unroll 2
+    for (int64_t e = near_ptr[t]; e < e1; ++e) {
+        const int64_t sidx = near_col[e];
+        const T *L = Ld + 9 * e;
+        const T l0 = L[0], l1 = L[1], l2 = L[2], l3 = L[3], l4 = L[4], l5 = L[5], l6 = L[6], l7 = L[7], l8 = L[8];
+        const C<T> *c = cT + sidx * 3 * R;
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            const int32_t r = r0 + 32 * j;
+            if (r < R) {
+                const C<T> c0 = c[r], c1 = c[R + r], c2 = c[2 * R + r];
+                acc[0][j].x += l0 * c0.x + l1 * c1.x + l2 * c2.x;
+                acc[0][j].y += l0 * c0.y + l1 * c1.y + l2 * c2.y;
+                acc[1][j].x += l3 * c0.x + l4 * c1.x + l5 * c2.x;
+                acc[1][j].y += l3 * c0.y + l4 * c1.y + l5 * c2.y;
+                acc[2][j].x += l6 * c0.x + l7 * c1.x + l8 * c2.x;
+                acc[2][j].y += l6 * c0.y + l7 * c1.y + l8 * c2.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+        const int32_t r = r0 + 32 * j;
+        if (r < R)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ynear[(t * 3 + k) * R + r] = acc[k][j];
+    }
 }
 
 // J_q[c] = sum_k c_T[k] (w_q/2)(r_q - v_k)_c for every sample point.
@@ -163,26 +216,45 @@ __global__ void k_point_currents(const C<T> *__restrict__ c_tri, const T *__rest
 }
 
 // Q_g[c][n] = sum over the points whose stencil holds node n of L_n(r_q) J_q[c].
+// One thread per (node, group of up to 4 right-hand sides): each gather-list
+// entry (point, weight) is read once for the group.
 template <typename T>
 __global__ void k_project(const C<T> *__restrict__ jq, int64_t npt, const int64_t *__restrict__ ptr,
                           const int32_t *__restrict__ pt, const T *__restrict__ w, int64_t Ng, int32_t nrhs,
                           C<T> *__restrict__ grid) {
+    constexpr int RG = 4;
+    const int32_t ngroups = (nrhs + RG - 1) / RG;
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= Ng * nrhs) return;
-    int64_t r = i / Ng, n = i % Ng;
-    C<T> a0 = mk<T>(0, 0), a1 = a0, a2 = a0;
-    const C<T> *J = jq + r * npt * 3;
-    for (int64_t e = ptr[n]; e < ptr[n + 1]; ++e) {
-        const C<T> *j = J + int64_t(pt[e]) * 3;
-        T we = w[e];
-        a0 = cadd(a0, cscale(j[0], we));
-        a1 = cadd(a1, cscale(j[1], we));
-        a2 = cadd(a2, cscale(j[2], we));
+    if (i >= Ng * ngroups) return;
+    const int64_t g = i / Ng, n = i % Ng;
+    const int32_t r0 = int32_t(g) * RG;
+    const int nr = min(RG, nrhs - r0);
+    C<T> a[RG][3];
+#pragma unroll
+    for (int k = 0; k < RG; ++k) a[k][0] = a[k][1] = a[k][2] = mk<T>(0, 0);
+    const int64_t e1 = ptr[n + 1];
+    for (int64_t e = ptr[n]; e < e1; ++e) {
+        const int64_t p3 = int64_t(pt[e]) * 3;
+        const T we = w[e];
+#pragma unroll
+        for (int k = 0; k < RG; ++k) {
+            if (k < nr) {
+                const C<T> *j = jq + (int64_t(r0 + k) * npt) * 3 + p3;
+                a[k][0] = cadd(a[k][0], cscale(j[0], we));
+                a[k][1] = cadd(a[k][1], cscale(j[1], we));
+                a[k][2] = cadd(a[k][2], cscale(j[2], we));
+            }
+        }
     }
-    C<T> *g = grid + r * 3 * Ng;
-    g[n] = a0;
-    g[Ng + n] = a1;
-    g[2 * Ng + n] = a2;
+#pragma unroll
+    for (int k = 0; k < RG; ++k) {
+        if (k < nr) {
+            C<T> *gr = grid + int64_t(r0 + k) * 3 * Ng;
+            gr[n] = a[k][0];
+            gr[Ng + n] = a[k][1];
+            gr[2 * Ng + n] = a[k][2];
+        }
+    }
 }
 
 // Phi_q[c] = sum_{n in S(q)} L_n(r_q) phi_g[c][n].
@@ -214,9 +286,9 @@ __global__ void k_point_potentials(const C<T> *__restrict__ grid, const int32_t 
 template <typename T>
 __global__ void k_tri_out(const C<T> *__restrict__ phiq, const T *__restrict__ mom, const C<T> *__restrict__ c_tri,
                           const int64_t *__restrict__ near_ptr, const int32_t *__restrict__ near_col,
-                          const T *__restrict__ Ld, const double *__restrict__ gram, const int32_t *__restrict__ cond,
-                          const double *__restrict__ coef, int ncond, int64_t nt, int Q, int32_t nrhs,
-                          double2 *__restrict__ y_tri) {
+                          const T *__restrict__ Ld, const C<T> *__restrict__ ynear, const double *__restrict__ gram,
+                          const int32_t *__restrict__ cond, const double *__restrict__ coef, int ncond, int64_t nt,
+                          int Q, int32_t nrhs, double2 *__restrict__ y_tri) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nt * nrhs) return;
     int64_t r = i / nt, t = i % nt;
@@ -236,7 +308,9 @@ __global__ void k_tri_out(const C<T> *__restrict__ phiq, const T *__restrict__ m
     // near: sum_T' L_d(T, T') c_T'
     C<T> nr[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
     const C<T> *cr = c_tri + r * nt * 3;
-    for (int64_t e = near_ptr[t]; e < near_ptr[t + 1]; ++e) {
+    if (ynear) {
+        for (int k = 0; k < 3; ++k) nr[k] = ynear[(t * 3 + k) * nrhs + r];
+    } else for (int64_t e = near_ptr[t]; e < near_ptr[t + 1]; ++e) {
         const C<T> *c = cr + int64_t(near_col[e]) * 3;
         C<T> c0 = c[0], c1 = c[1], c2 = c[2];
         const T *L = Ld + 9 * e;
@@ -322,12 +396,12 @@ namespace sie {
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     Scratch &s = p->scr;
     if (s.cap_rhs >= nrhs && s.prec == prec) return SIE_OK;
-    for (void *a : {s.tour, s.c_tri, s.jq, s.grid, s.spec, s.y_tri, s.y_br, (void *)s.coef})
+    for (void *a : {s.tour, s.c_tri, s.jq, s.grid, s.spec, s.y_tri, s.y_br, (void *)s.coef, s.cT, s.ynear})
         if (a) cudaFree(a);
     s = Scratch{};
     const size_t cs = prec == SIE_PREC_FP64 ? sizeof(double2) : sizeof(float2);
     const int64_t R = std::max<int32_t>(nrhs, 1);
-    const size_t sizes[8] = {
+    const size_t sizes[10] = {
         size_t(R) * 2 * p->nn * sizeof(double2),
         size_t(R) * p->nt * 3 * cs,
         size_t(R) * p->nt * p->Q * 3 * cs,
@@ -335,9 +409,11 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
         size_t(R) * 3 * p->Nx * p->My * p->Mz * cs,
         size_t(R) * p->nt * 3 * sizeof(double2),
         size_t(R) * (p->nb + p->np) * sizeof(double2),
-        size_t(R) * (2 * p->ncond + 1) * sizeof(double)};
-    void **dst[8] = {&s.tour, &s.c_tri, &s.jq, &s.grid, &s.spec, &s.y_tri, &s.y_br, (void **)&s.coef};
-    for (int i = 0; i < 8; ++i) {
+        size_t(R) * (2 * p->ncond + 1) * sizeof(double),
+        size_t(R) * p->nt * 3 * cs,
+        size_t(R) * p->nt * 3 * cs};
+    void **dst[10] = {&s.tour, &s.c_tri, &s.jq, &s.grid, &s.spec, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT, &s.ynear};
+    for (int i = 0; i < 10; ++i) {
         cudaError_t e = cudaMalloc(dst[i], std::max<size_t>(sizes[i], 16));
         if (e != cudaSuccess) {
             for (int j = 0; j < i; ++j) { cudaFree(*dst[j]); *dst[j] = nullptr; }
@@ -377,14 +453,14 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     }
     k_alpha_tri<T><<<nblk(p->nt * 3 * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tb, p->d_ts, p->d_loop_of_branch,
                                                          p->d_twig_node, p->d_head, p->d_enter, p->d_exit, p->nt, R,
-                                                         space, p->nb, c_tri);
+                                                         space, p->nb, c_tri, (C<T> *)s.cT);
     SIE_LAUNCH_CHECK(p);
     const int64_t npt = p->nt * p->Q;
     tm.reset(new StageTimer(p, SIE_STAGE_POINT_CURRENTS, st));
     k_point_currents<T><<<nblk(npt * R), 256, 0, st>>>(c_tri, mom, p->nt, p->Q, R, jq);
     SIE_LAUNCH_CHECK(p);
     tm.reset(new StageTimer(p, SIE_STAGE_PROJECT, st));
-    k_project<T><<<nblk(p->Ng * R), 256, 0, st>>>(jq, npt, p->d_pj_ptr, p->d_pj_pt, pjw, p->Ng, R, grid);
+    k_project<T><<<nblk(p->Ng * ((R + 3) / 4)), 256, 0, st>>>(jq, npt, p->d_pj_ptr, p->d_pj_pt, pjw, p->Ng, R, grid);
     SIE_LAUNCH_CHECK(p);
     tm.reset();
     int rc = fft_conv(p, grid, spec, R, sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED, st);
@@ -393,9 +469,19 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
     k_point_potentials<T><<<nblk(npt * R), 256, 0, st>>>(grid, p->d_start, lw, p->O, p->Ny, p->Nz, p->Ng, npt, R, phiq);
     SIE_LAUNCH_CHECK(p);
-    tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
-    k_tri_out<T><<<nblk(p->nt * R, 128), 128, 0, st>>>(phiq, mom, c_tri, p->d_near_ptr, p->d_near_col, Ld, p->d_gram,
-                                                   p->d_cond, s.coef, p->ncond, p->nt, p->Q, R, y_tri);
+    C<T> *ynear = nullptr;
+    if (R >= 16) {   // batched right-hand sides: near field as a block-sparse x dense product
+        tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
+        ynear = (C<T> *)s.ynear;
+        const int32_t nchunk = (R + 127) / 128;
+        const int64_t warps = p->nt * nchunk;
+        k_near_spmm<T, 4><<<nblk(warps * 32, 256), 256, 0, st>>>(p->d_near_ptr, p->d_near_col, Ld, (const C<T> *)s.cT,
+                                                                p->nt, R, nchunk, ynear);
+        SIE_LAUNCH_CHECK(p);
+        tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
+    }
+    k_tri_out<T><<<nblk(p->nt * R, 128), 128, 0, st>>>(phiq, mom, c_tri, p->d_near_ptr, p->d_near_col, Ld, ynear,
+                                                   p->d_gram, p->d_cond, s.coef, p->ncond, p->nt, p->Q, R, y_tri);
     SIE_LAUNCH_CHECK(p);
     tm.reset(new StageTimer(p, SIE_STAGE_BRANCH_TO_LOOP, st));
     if (space == SIE_SPACE_BRANCH) {

@@ -758,7 +758,7 @@ extern "C" void pfft_plan_destroy(pfft_plan *p) {
     for (void *a : p->allocations) cudaFree(a);
     // scr.phiq aliases scr.jq and is not freed separately
     for (void *a : {p->scr.tour, p->scr.c_tri, p->scr.jq, p->scr.grid, p->scr.spec, p->scr.y_tri, p->scr.y_br,
-                    (void *)p->scr.coef})
+                    (void *)p->scr.coef, p->scr.cT, p->scr.ynear})
         if (a) cudaFree(a);
     delete p;
 }

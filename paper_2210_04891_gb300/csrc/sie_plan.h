@@ -29,6 +29,8 @@ struct Scratch {
     void *y_tri = nullptr;     // complex128 [R][nt][3]
     void *y_br = nullptr;      // complex128 [R][nb + np]
     double *coef = nullptr;    // per RHS: Z_s per conductor (re, im), c_L (im) -> [R][2 ncond + 1]
+    void *cT = nullptr;        // complex T [nt][3][R]  local currents, right-hand sides innermost
+    void *ynear = nullptr;     // complex T [nt][3][R]  near-field product
     size_t bytes = 0;
 };
 

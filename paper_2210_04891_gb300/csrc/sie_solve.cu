@@ -56,6 +56,9 @@ struct PrecondState {
     int32_t nslots = 0;
     std::vector<double> slot_omega;
     double2 *d_band = nullptr;        // [nslots][nunk][W + 1], band[i][d] = K[i][i-d]
+    double2 *d_bandc = nullptr;       // same, column-major copy bandc[i][d] = L[i+d][i]
+    float2 *d_band32 = nullptr, *d_bandc32 = nullptr;   // FP32 roundings of both (mixed form)
+    float2 *d_u32 = nullptr;          // FP32 sweep buffer [R][nunk]
     double2 *d_a = nullptr;           // [nslots][nb] 1/D_e
     double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
     int32_t cap_rhs = 0;
@@ -67,7 +70,9 @@ struct PrecondState {
 void plan_free_precond(pfft_plan *p) {
     if (!p || !p->pc) return;
     for (void *a : p->pc->allocs) cudaFree(a);
-    for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
+    for (void *a : {(void *)p->pc->d_band32, (void *)p->pc->d_bandc32, (void *)p->pc->d_u32})
+        if (a) cudaFree(a);
+    for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
                     (void *)p->pc->d_ibr, (void *)p->pc->d_slot})
         if (a) cudaFree(a);
     delete p->pc;
@@ -278,6 +283,11 @@ int build_symbolic(pfft_plan *p) {
     return SIE_OK;
 }
 
+__global__ void k_round_c(const double2 *__restrict__ a, float2 *__restrict__ b, int64_t n) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2(float(a[i].x), float(a[i].y));
+}
+
 // 1/D_e with D_e = Z_s(sigma_e, w) G_ee + j w mu0/(4 pi) Lt_ee (Eq. Zb diagonal).
 __global__ void k_pc_admittance(const double *__restrict__ diag_gram, const double *__restrict__ diag_L,
                                 const int32_t *__restrict__ br_cond, const double *__restrict__ zs_cl, int ncond,
@@ -298,11 +308,13 @@ __global__ void __launch_bounds__(256) k_pc_factor(const int64_t *__restrict__ b
                                                    int64_t nunk, const int32_t *__restrict__ row_ptr,
                                                    const int32_t *__restrict__ row_br,
                                                    const int32_t *__restrict__ row_oth, const double2 *__restrict__ a,
-                                                   int64_t nb, double2 *__restrict__ band, int *status) {
+                                                   int64_t nb, double2 *__restrict__ band, double2 *__restrict__ bandc,
+                                                   int *status) {
     const int32_t f = blockIdx.x / nblk, b = blockIdx.x % nblk;
     const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
     const int Wp = W + 1;
     double2 *B = band + (int64_t(f) * nunk + o) * Wp;
+    double2 *Bc = bandc + (int64_t(f) * nunk + o) * Wp;
     const double2 *af = a + int64_t(f) * nb;
     for (int64_t i = threadIdx.x; i < n * Wp; i += blockDim.x) B[i] = make_double2(0.0, 0.0);
     __syncthreads();
@@ -350,6 +362,11 @@ __global__ void __launch_bounds__(256) k_pc_factor(const int64_t *__restrict__ b
         for (int64_t r = 1 + threadIdx.x; r <= m; r += blockDim.x)
             B[(k + r) * Wp + r] = cmul(B[(k + r) * Wp + r], inv);   // l_{k+r,k}
         __syncthreads();
+    }
+    // column-major copy for the forward sweep: Bc[i][d] = L[i+d][i], Bc[i][0] = d_i
+    for (int64_t t = threadIdx.x; t < n * Wp; t += blockDim.x) {
+        const int64_t i = t / Wp, d = t % Wp;
+        Bc[t] = d == 0 ? B[i * Wp] : (i + d < n ? B[(i + d) * Wp + d] : make_double2(0.0, 0.0));
     }
 }
 
@@ -434,6 +451,113 @@ __global__ void k_pc_solve(const double2 *__restrict__ kappa, const int32_t *__r
     }
 }
 
+// Same solve with the band sweeps kept in registers (requires W <= 31): lane
+// (row mod 32) holds the running value of `row` for the 32 rows from the current
+// pivot on.  A step broadcasts the finished pivot with one shuffle and each lane
+// applies one multiply-add; the pivot's lane then takes the row 32 further on.
+template <typename V> __device__ __forceinline__ V shfl_c(V v, int src) {
+    v.x = __shfl_sync(0xffffffffu, v.x, src);
+    v.y = __shfl_sync(0xffffffffu, v.y, src);
+    return v;
+}
+
+// T = double: FP64 sweeps (plain form); T = float: FP32 band and sweeps (mixed
+// form; the factor is computed in FP64 and rounded), FP64 in and out.
+template <typename T>
+__global__ void k_pc_solve_win(const double2 *__restrict__ kappa, const int32_t *__restrict__ row_ptr,
+                               const int32_t *__restrict__ row_br, const int8_t *__restrict__ row_sg,
+                               const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk, int64_t nb,
+                               const C<T> *__restrict__ band, const C<T> *__restrict__ bandc,
+                               const int32_t *__restrict__ slot, int32_t nrhs, double2 *__restrict__ u,
+                               C<T> *__restrict__ xs) {
+    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (wid >= int64_t(nrhs) * nblk) return;
+    const int64_t r = wid / nblk, b = wid % nblk;
+    const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
+    const int Wp = W + 1;
+    const C<T> *B = band + (int64_t(slot[r]) * nunk + o) * Wp;
+    const C<T> *Bc = bandc + (int64_t(slot[r]) * nunk + o) * Wp;
+    double2 *xd = u + r * nunk + o;
+    C<T> *x = xs + r * nunk + o;     // sweep buffer in the sweep precision
+    const double2 *kr = kappa + r * nb;
+    const C<T> zero = mk<T>(T(0), T(0));
+    for (int64_t i = lane; i < n; i += 32) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int32_t k = row_ptr[o + i]; k < row_ptr[o + i + 1]; ++k)
+            acc = row_sg[k] > 0 ? csub(acc, kr[row_br[k]]) : cadd(acc, kr[row_br[k]]);
+        x[i] = mk<T>(T(acc.x), T(acc.y));
+    }
+    __syncwarp();
+    // forward: unit lower L, column form  y_{i+d} -= L[i+d][i] y_i.  The band
+    // entries of step i are loaded PF steps ahead into a register queue and the
+    // row a pivot lane takes over (32 further on) 32 steps ahead, so no step
+    // waits on memory.
+    constexpr int PF = 16;
+    C<T> lq[PF];
+    C<T> w = lane < n ? x[lane] : zero;
+    C<T> pf = lane + 32 < n ? x[lane + 32] : zero;
+    auto lf = [&](int64_t i) -> C<T> {
+        const int d = (lane - int(i & 31)) & 31;
+        return (i < n && d >= 1 && d <= W && i + d < n) ? Bc[i * Wp + d] : zero;
+    };
+#pragma unroll
+    for (int j = 0; j < PF; ++j) lq[j] = lf(j);
+    for (int64_t i0 = 0; i0 < n; i0 += PF) {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int64_t i = i0 + j;
+            if (i >= n) break;
+            const C<T> l = lq[j];
+            lq[j] = lf(i + PF);
+            const int pl = int(i & 31);
+            const C<T> xi = shfl_c(w, pl);
+            w = csub(w, cmul(l, xi));
+            if (lane == pl) {
+                x[i] = xi;
+                w = pf;
+                pf = i + 64 < n ? x[i + 64] : zero;
+            }
+        }
+    }
+    __syncwarp();
+    for (int64_t i = lane; i < n; i += 32) {
+        const C<T> dg = B[i * Wp];
+        const T den = dg.x * dg.x + dg.y * dg.y;
+        x[i] = cmul(x[i], mk<T>(dg.x / den, -dg.y / den));
+    }
+    __syncwarp();
+    // backward: unit upper L^T, column form  x_{i-d} -= L[i][i-d] x_i
+    auto lb = [&](int64_t i) -> C<T> {
+        const int d = (lane - int((n - 1 - i) & 31)) & 31;
+        return (i >= 0 && d >= 1 && d <= W && i - d >= 0) ? B[i * Wp + d] : zero;
+    };
+    w = lane < n ? x[n - 1 - lane] : zero;
+    pf = n - 1 - 32 - lane >= 0 ? x[n - 1 - 32 - lane] : zero;
+#pragma unroll
+    for (int j = 0; j < PF; ++j) lq[j] = lb(n - 1 - j);
+    for (int64_t i0 = n - 1; i0 >= 0; i0 -= PF) {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int64_t i = i0 - j;
+            if (i < 0) break;
+            const C<T> l = lq[j];
+            lq[j] = lb(i - PF);
+            const int pl = int((n - 1 - i) & 31);
+            const C<T> xi = shfl_c(w, pl);
+            w = csub(w, cmul(l, xi));
+            if (lane == pl) {
+                x[i] = xi;
+                w = pf;
+                pf = i - 64 >= 0 ? x[i - 64] : zero;
+            }
+        }
+    }
+    __syncwarp();
+    if ((void *)x != (void *)xd)
+        for (int64_t i = lane; i < n; i += 32) xd[i] = make_double2(double(x[i].x), double(x[i].y));
+}
+
 // Branch currents i_e = a_e (phi_tail - phi_head + emf_e) = a_e (u_t - u_h) + kappa_e.
 __global__ void k_pc_currents(const double2 *__restrict__ u, int64_t nunk, const double2 *__restrict__ kappa,
                               const double2 *__restrict__ a, const int32_t *__restrict__ slot,
@@ -494,6 +618,8 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         SIE_CUDA(cudaMalloc((void **)&s->d_kappa, size_t(R) * p->nb * sizeof(double2)));
         SIE_CUDA(cudaMalloc((void **)&s->d_ibr, size_t(R) * p->nb * sizeof(double2)));
         SIE_CUDA(cudaMalloc((void **)&s->d_u, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(double2)));
+        if (s->d_u32) cudaFree(s->d_u32);
+        SIE_CUDA(cudaMalloc((void **)&s->d_u32, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(float2)));
         SIE_CUDA(cudaMalloc((void **)&s->d_slot, size_t(R) * sizeof(int32_t)));
         s->cap_rhs = R;
     }
@@ -501,11 +627,19 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     if (uniq == s->slot_omega) return SIE_OK;   // factors cached
     const int32_t ns = int32_t(uniq.size());
     if (s->d_band) cudaFree(s->d_band);
+    if (s->d_bandc) cudaFree(s->d_bandc);
+    if (s->d_band32) cudaFree(s->d_band32);
+    if (s->d_bandc32) cudaFree(s->d_bandc32);
+    s->d_band32 = s->d_bandc32 = nullptr;
     if (s->d_a) cudaFree(s->d_a);
     s->d_band = nullptr;
+    s->d_bandc = nullptr;
     s->d_a = nullptr;
     s->slot_omega.clear();
     SIE_CUDA(cudaMalloc((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
+    SIE_CUDA(cudaMalloc((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
+    SIE_CUDA(cudaMalloc((void **)&s->d_band32, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(float2)));
+    SIE_CUDA(cudaMalloc((void **)&s->d_bandc32, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(float2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2)));
     std::vector<double> zc(size_t(ns) * (p->ncond + 1));
     for (int32_t f = 0; f < ns; ++f) {
@@ -524,7 +658,12 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     StageTimer tm(p, SIE_STAGE_PRECOND_FACTOR, st);
     if (s->nunk > 0) {
         k_pc_factor<<<ns * nblk, 256, 0, st>>>(s->d_blk_off, nblk, s->W, s->nunk, s->d_row_ptr, s->d_row_br,
-                                                s->d_row_oth, s->d_a, p->nb, s->d_band, s->d_status);
+                                                s->d_row_oth, s->d_a, p->nb, s->d_band, s->d_bandc, s->d_status);
+        SIE_LAUNCH_CHECK(p);
+        const int64_t nbnd = int64_t(ns) * s->nunk * (s->W + 1);
+        k_round_c<<<nblk_(nbnd), 256, 0, st>>>(s->d_band, s->d_band32, nbnd);
+        SIE_LAUNCH_CHECK(p);
+        k_round_c<<<nblk_(nbnd), 256, 0, st>>>(s->d_bandc, s->d_bandc32, nbnd);
         SIE_LAUNCH_CHECK(p);
     }
     int status = 0;
@@ -537,7 +676,7 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     return SIE_OK;
 }
 
-int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream_t st) {
+int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int prec, cudaStream_t st) {
     PrecondState *s = p->pc;
     StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
@@ -547,9 +686,18 @@ int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaSt
     SIE_LAUNCH_CHECK(p);
     if (s->nunk > 0) {
         const int64_t warps = int64_t(R) * nblk;
-        k_pc_solve<<<nblk_(warps * 32, 128), 128, 0, st>>>(s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
-                                                            s->d_blk_off, nblk, s->W, s->nunk, p->nb, s->d_band,
-                                                            s->d_slot, R, s->d_u);
+        if (s->W <= 31 && prec == SIE_PREC_MIXED)
+            k_pc_solve_win<float><<<nblk_(warps * 32, 128), 128, 0, st>>>(
+                s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
+                s->d_band32, s->d_bandc32, s->d_slot, R, s->d_u, s->d_u32);
+        else if (s->W <= 31)
+            k_pc_solve_win<double><<<nblk_(warps * 32, 128), 128, 0, st>>>(
+                s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
+                s->d_band, s->d_bandc, s->d_slot, R, s->d_u, s->d_u);
+        else
+            k_pc_solve<<<nblk_(warps * 32, 128), 128, 0, st>>>(s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
+                                                                s->d_blk_off, nblk, s->W, s->nunk, p->nb, s->d_band,
+                                                                s->d_slot, R, s->d_u);
         SIE_LAUNCH_CHECK(p);
     }
     k_pc_currents<<<nblk_(p->nb * R), 256, 0, st>>>(s->d_u, s->nunk, s->d_kappa, s->d_a, s->d_slot,
@@ -637,14 +785,15 @@ __global__ void k_sub(const double2 *__restrict__ a, const double2 *__restrict__
 }  // namespace
 
 extern "C" int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
-                                  void *cuda_stream) {
+                                  int32_t prec, void *cuda_stream) {
     if (!p || !y || !z || !omega || nrhs < 1) return fail(SIE_ERR_ARG, "pfft_precond_apply: bad argument");
+    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "pfft_precond_apply: bad precision");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     (void)cudaGetLastError();
     std::vector<int32_t> slot;
     int rc = pc_prepare(p, omega, nrhs, slot, st);
     if (rc) return rc;
-    rc = pc_apply_async(p, (const double2 *)y, (double2 *)z, nrhs, st);
+    rc = pc_apply_async(p, (const double2 *)y, (double2 *)z, nrhs, prec, st);
     if (rc) return rc;
     SIE_CUDA(cudaStreamSynchronize(st));
     return SIE_OK;
@@ -706,7 +855,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     auto apply_op = [&](const double2 *in, double2 *out) -> int {   // out = P^-1 Z in
         int r2 = matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, opts->prec, st);
         if (r2) return r2;
-        if (use_pc) return pc_apply_async(p, t, out, R, st);
+        if (use_pc) return pc_apply_async(p, t, out, R, opts->prec, st);
         return SIE_OK;
     };
     auto dots = [&](const double2 *vec, int32_t k, std::vector<double2> &h) -> int {   // h[r][j] for j < k
@@ -734,7 +883,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     std::vector<double> bnorm(R), resid(R, 1.0);
     GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     // ||P^-1 b||
-    if (use_pc) GM_RC(pc_apply_async(p, b, w, R, st));
+    if (use_pc) GM_RC(pc_apply_async(p, b, w, R, opts->prec, st));
     else GM_CUDA(cudaMemcpyAsync(w, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     GM_RC(norms(w, bnorm));
     int64_t matvecs = 0;
@@ -748,7 +897,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
         if (use_pc) {
             k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, t, int64_t(R) * n);   // t = b - Z x (t held Z x)
             SIE_LAUNCH_CHECK(p);
-            GM_RC(pc_apply_async(p, t, w, R, st));
+            GM_RC(pc_apply_async(p, t, w, R, opts->prec, st));
         } else {
             k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, w, w, int64_t(R) * n);
             SIE_LAUNCH_CHECK(p);

@@ -84,7 +84,7 @@ def lib():
     L.pfft_plan_create.argtypes = [P, P, ctypes.POINTER(PfftParams), P, PP]
     L.pfft_plan_destroy.argtypes = [P]
     L.pfft_matvec.argtypes = [P, P, P, I32, P, I32, I32, P]
-    L.pfft_precond_apply.argtypes = [P, P, P, I32, P, P]
+    L.pfft_precond_apply.argtypes = [P, P, P, I32, P, I32, P]
     L.sie_solve.argtypes = [P, P, I32, P, I32, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveStats)]
     L.pfft_plan_info.argtypes = [P, P, P, P, P, P, P, P]
     L.pfft_plan_export.argtypes = [P, I32, P, I64]

@@ -104,6 +104,19 @@ def test_loop_matvec_mixed(wires):
     assert rel(y, ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("nrhs,prec,tol", [(20, PREC_FP64, 1e-10), (20, PREC_MIXED, 1e-5),
+                                           (130, PREC_MIXED, 1e-5)])
+def test_loop_matvec_batched(wires, nrhs, prec, tol):
+    """Batched right-hand sides take the block-sparse x dense near-field path (>= 16),
+    with a ragged lane tail (20) and more than one 128-wide chunk (130)."""
+    m, O, S, P = wires
+    x = synth.complex_gaussian(O.nl, nrhs, seed=100 + nrhs)
+    om = 2 * np.pi * np.logspace(7, 10, nrhs)
+    ref = np.stack([S.matvec(x[r], om[r]) for r in range(nrhs)])
+    y = api.pfft_matvec(P, torch.from_numpy(x).cuda(), om, SPACE_LOOP, prec).cpu().numpy()
+    assert rel(y, ref).max() < tol
+
+
 def test_branch_matvec(wires):
     m, O, S, P = wires
     a = synth.complex_gaussian(O.nb, 2, seed=31)

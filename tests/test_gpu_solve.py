@@ -48,6 +48,30 @@ def test_precond_matches_oracle(make_mesh, params):
         assert np.linalg.norm(z[r] - ref) < 1e-9 * np.linalg.norm(ref), r
 
 
+def test_precond_mixed_sweeps():
+    """FP32 sweeps on the rounded FP64 factor: within FP32 accuracy of the oracle."""
+    m = synth.tiny_wires()
+    O, S, P = make(m, P_WIRES)
+    om = 2 * np.pi * np.array([1e9, 1e10, 1e8])
+    y = synth.complex_gaussian(O.nl, 3, seed=83)
+    z = api.pfft_precond_apply(P, torch.from_numpy(y).cuda(), om, prec=PREC_MIXED).cpu().numpy()
+    for r in range(3):
+        ref = Precond(O, S.diag_Zb(om[r])).solve(y[r])
+        assert np.linalg.norm(z[r] - ref) < 1e-4 * np.linalg.norm(ref), r
+
+
+def test_precond_batched_many_rhs():
+    """40 right-hand sides over 5 frequencies (several factor slots) on the bar."""
+    m = synth.tiny_bar()
+    O, S, P = make(m, P_BAR)
+    om = 2 * np.pi * np.repeat(np.logspace(8, 10, 5), 8)
+    y = synth.complex_gaussian(O.nl, 40, seed=91)
+    z = api.pfft_precond_apply(P, torch.from_numpy(y).cuda(), om).cpu().numpy()
+    for r in range(0, 40, 7):
+        ref = Precond(O, S.diag_Zb(om[r])).solve(y[r])
+        assert np.linalg.norm(z[r] - ref) < 1e-9 * np.linalg.norm(ref), r
+
+
 def test_solve_matches_oracle_gmres_and_dense():
     m = synth.tiny_wires()
     O, S, P = make(m, P_WIRES)
