@@ -203,7 +203,7 @@ int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *
  * they convolve: fixed start-up memory budgets, real-time loops that cannot
  * take cudaMalloc's synchronisation and latency, frameworks that own the
  * allocator).  Same arguments and result as pfft_convolve.  Its scratch is one
- * file-scope device array of 16 MiB that every GPU loading the library holds
+ * file-scope device array of 8 MiB that every GPU loading the library holds
  * until exit; a grid whose zero-padded spectrum (N_x * 2N_y * 2N_z complex
  * values of the precision) exceeds it is rejected with SIE_ERR_ARG.  Larger
  * batches are processed in pieces that fit.  The first call on a device looks

@@ -19,9 +19,9 @@ using namespace sie;
 namespace {
 
 // Spectral scratch for the convolution: one zero-padded spectrum
-// [N_x][2N_y][2N_z] per grid, complex128 or complex64.  16 MiB holds one
-// 128 x 64 x 32 grid in FP64 (two in FP32).
-constexpr size_t kNoallocScratchBytes = size_t(16) << 20;
+// [N_x][2N_y][2N_z] per grid, complex128 or complex64.  8 MiB holds one
+// 128 x 64 x 32 grid in FP32 (the mixed form's convolution precision).
+constexpr size_t kNoallocScratchBytes = size_t(8) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;

@@ -364,34 +364,33 @@ namespace sie {
 template <typename T>
 int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s) {
     const int nb = ngrids * p->Nx;
-    const size_t plane_bytes = size_t(p->My) * p->Mz * sizeof(C<T>);
-    int rc = set_smem((const void *)k_fft_plane<T>, plane_bytes);
+    int NX1, NX2;
+    split4(p->Mx, NX1, NX2);
+    const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
+    int rc = set_smem((const void *)k_fft_yz4<T>, plane_bytes);
     if (rc) return rc;
-    const int thr = fft_threads(p->My * p->Mz);
     {
-    StageTimer tm(p, SIE_STAGE_FFT_PLANE_FWD, s);
-    k_fft_plane<T><<<nb, thr, plane_bytes, s>>>(grid, int64_t(p->Ny) * p->Nz, p->Ny, p->Nz, spec,
-                                               int64_t(p->My) * p->Mz, p->My, p->Mz, p->My, p->Mz,
-                                               twiddle<T>(p, 1), twiddle<T>(p, 2), 0);
-    SIE_LAUNCH_CHECK(p);
+        StageTimer tm(p, SIE_STAGE_FFT_PLANE_FWD, s);
+        k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(grid, int64_t(p->Ny) * p->Nz, spec, int64_t(p->My) * p->Mz, p->Ny,
+                                                 p->Nz, p->My, p->Mz, twiddle<T>(p, 1), twiddle<T>(p, 2), 0);
+        SIE_LAUNCH_CHECK(p);
     }
     const int KT = 16;
     const int ncols = p->My * p->Mz;
     const size_t pb = size_t(KT) * (p->Mx + 1) * sizeof(C<T>);
-    rc = set_smem((const void *)k_fft_pencil<T>, pb);
+    rc = set_smem((const void *)k_fft_x4<T>, pb);
     if (rc) return rc;
     const T *H = nullptr;
     if constexpr (sizeof(T) == 8) H = reinterpret_cast<const T *>(p->d_H64); else H = reinterpret_cast<const T *>(p->d_H32);
     {
-    StageTimer tm(p, SIE_STAGE_FFT_PENCIL, s);
-    k_fft_pencil<T><<<ngrids * (ncols / KT), fft_threads(KT * p->Mx), pb, s>>>(
-        spec, int64_t(p->Nx) * ncols, ncols, p->Nx, p->Nx, p->Mx, p->My, p->Mz, KT, twiddle<T>(p, 0), H);
-    SIE_LAUNCH_CHECK(p);
+        StageTimer tm(p, SIE_STAGE_FFT_PENCIL, s);
+        k_fft_x4<T><<<ngrids * (ncols / KT), KT * std::max(NX1, NX2), pb, s>>>(
+            spec, int64_t(p->Nx) * ncols, ncols, p->Nx, p->Mx, p->My, p->Mz, twiddle<T>(p, 0), H);
+        SIE_LAUNCH_CHECK(p);
     }
     StageTimer tm(p, SIE_STAGE_FFT_PLANE_INV, s);
-    k_fft_plane<T><<<nb, thr, plane_bytes, s>>>(spec, int64_t(p->My) * p->Mz, p->My, p->Mz, grid,
-                                               int64_t(p->Ny) * p->Nz, p->Ny, p->Nz, p->My, p->Mz,
-                                               twiddle<T>(p, 1), twiddle<T>(p, 2), 1);
+    k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(spec, int64_t(p->My) * p->Mz, grid, int64_t(p->Ny) * p->Nz, p->Ny, p->Nz,
+                                             p->My, p->Mz, twiddle<T>(p, 1), twiddle<T>(p, 2), 1);
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
@@ -415,11 +414,12 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     const int O = prm->order;
     if (O < 2 || O > 4) return fail(SIE_ERR_ARG, "pfft_plan_create: order must be 2..4");
     for (int d = 0; d < 3; ++d)
-        if (!is_pow2(prm->grid[d]) || prm->grid[d] < O || prm->grid[d] < 4 || prm->grid[d] > 512)
-            return fail(SIE_ERR_ARG, "pfft_plan_create: grid sizes must be powers of two in [max(4, order), 512]");
-    if (4 * prm->grid[1] * prm->grid[2] > FFT_MAX_ELEMS || 16 * 2 * prm->grid[0] > FFT_MAX_ELEMS)
-        return fail(SIE_ERR_ARG, "pfft_plan_create: padded y-z plane or x pencil tile exceeds one CTA's shared-memory FFT "
-                                 "(2N_y * 2N_z <= 8192, N_x <= 256)");
+        if (!is_pow2(prm->grid[d]) || prm->grid[d] < O || prm->grid[d] < 4 || prm->grid[d] > 128)
+            return fail(SIE_ERR_ARG, "pfft_plan_create: grid sizes must be powers of two in [max(4, order), 128]");
+    if (3 * prm->grid[1] * (2 * prm->grid[2] + 1) * 16 > 200 * 1024 || 4 * prm->grid[1] * prm->grid[2] > FFT_MAX_ELEMS ||
+        16 * 2 * prm->grid[0] > FFT_MAX_ELEMS)
+        return fail(SIE_ERR_ARG, "pfft_plan_create: padded y-z plane exceeds one CTA's shared memory "
+                                 "(2N_y * 2N_z <= 8192 and 3 N_y (2N_z + 1) * 16 B <= 200 KiB)");
     if (prm->n_touch < 1 || prm->n_touch > 64) return fail(SIE_ERR_ARG, "pfft_plan_create: n_touch must be 1..64");
     if (!(prm->near_factor >= 0.0) || !(prm->near_min_diam >= 0.0)) return fail(SIE_ERR_ARG, "pfft_plan_create: negative near radius");
     if (prm->kernel != SIE_KERNEL_STATIC) return fail(SIE_ERR_ARG, "pfft_plan_create: only the static kernel is built");

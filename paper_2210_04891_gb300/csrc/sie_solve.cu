@@ -63,6 +63,9 @@ struct PrecondState {
     double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
     int32_t cap_rhs = 0;
     int32_t *d_slot = nullptr;        // [R] factor slot per right-hand side
+    // runs of right-hand sides with equal slots (one per warp; see pc_prepare)
+    int32_t *d_grp_start[2] = {nullptr, nullptr}, *d_grp_count[2] = {nullptr, nullptr};
+    int32_t ngroups[2] = {0, 0};
     int *d_status = nullptr;
     std::vector<void *> allocs;
 };
@@ -72,6 +75,9 @@ void plan_free_precond(pfft_plan *p) {
     for (void *a : p->pc->allocs) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band32, (void *)p->pc->d_bandc32, (void *)p->pc->d_u32})
         if (a) cudaFree(a);
+    for (int v = 0; v < 2; ++v)
+        for (void *a : {(void *)p->pc->d_grp_start[v], (void *)p->pc->d_grp_count[v]})
+            if (a) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
                     (void *)p->pc->d_ibr, (void *)p->pc->d_slot})
         if (a) cudaFree(a);
@@ -558,6 +564,184 @@ __global__ void k_pc_solve_win(const double2 *__restrict__ kappa, const int32_t 
         for (int64_t i = lane; i < n; i += 32) xd[i] = make_double2(double(x[i].x), double(x[i].y));
 }
 
+// Grouped band solve: one warp sweeps RB right-hand sides that share a factor
+// slot (the ports of one frequency) through one block.  The band is staged
+// in shared memory 32 rows at a time with asynchronous copies issued two
+// chunks ahead; lane (row mod 32) holds the running values of `row` for all RB
+// right-hand sides; the rows a lane takes over and the rows it finishes are
+// loaded and stored once per 32-row chunk, coalesced.  Requires W <= 31.
+constexpr int PC_CH = 32;
+
+template <typename T>
+__device__ __forceinline__ void pc_stage_rows(C<T> *dst, const C<T> *src, int64_t row0, int64_t nrows, int Wp,
+                                              int64_t n, int lane) {
+    // rows [row0, row0 + nrows) of a [n][Wp] band -> dst[(row - row0) * Wp]
+    const int64_t r0 = row0 < 0 ? 0 : row0;
+    const int64_t r1 = row0 + nrows > n ? n : row0 + nrows;
+    if (r1 <= r0) return;
+    const char *s = reinterpret_cast<const char *>(src + r0 * Wp);
+    char *d = reinterpret_cast<char *>(dst + (r0 - row0) * Wp);
+    const int64_t bytes = (r1 - r0) * Wp * int64_t(sizeof(C<T>));
+    for (int64_t o = int64_t(lane) * 8; o < bytes; o += 32 * 8) {
+        const unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(d + o));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(s + o));
+    }
+}
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(128) k_pc_solve_grp(
+    const double2 *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
+    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
+    int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
+    const int32_t *__restrict__ grp_start, const int32_t *__restrict__ grp_count, int32_t ngroups,
+    double2 *__restrict__ u, C<T> *__restrict__ xs) {
+    extern __shared__ __align__(16) unsigned char pc_smem[];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= int64_t(ngroups) * nblk) return;
+    const int32_t g = int32_t(wid / nblk), b = int32_t(wid % nblk);
+    const int32_t r0 = grp_start[g], nr = grp_count[g];
+    const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
+    const int Wp = W + 1;
+    const C<T> *B = band + (int64_t(slot[r0]) * nunk + o) * Wp;
+    const C<T> *Bc = bandc + (int64_t(slot[r0]) * nunk + o) * Wp;
+    const C<T> zero = mk<T>(T(0), T(0));
+    C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_CH * Wp;   // [warp][2][32][Wp]
+    C<T> *buf1 = buf0 + PC_CH * Wp;
+    // right-hand sides of the nodal system
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (k >= nr) break;
+        const double2 *kr = kappa + int64_t(r0 + k) * nb;
+        C<T> *x = xs + int64_t(r0 + k) * nunk + o;
+        for (int64_t i = lane; i < n; i += 32) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int32_t q = row_ptr[o + i]; q < row_ptr[o + i + 1]; ++q)
+                acc = row_sg[q] > 0 ? csub(acc, kr[row_br[q]]) : cadd(acc, kr[row_br[q]]);
+            x[i] = mk<T>(T(acc.x), T(acc.y));
+        }
+    }
+    __syncwarp();
+    const int64_t nch = (n + PC_CH - 1) / PC_CH;
+    C<T> w[RB], pf[RB], pn[RB], done[RB];
+    // ---------------- forward: y_{i+d} -= L[i+d][i] y_i   (chunk c = steps [32c, 32c+32))
+    pc_stage_rows<T>(buf0, Bc, 0, PC_CH, Wp, n, lane);
+    asm volatile("cp.async.commit_group;\n" ::);
+    pc_stage_rows<T>(buf1, Bc, PC_CH, PC_CH, Wp, n, lane);
+    asm volatile("cp.async.commit_group;\n" ::);
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
+        w[k] = lane < n ? x[lane] : zero;
+        pf[k] = lane + 32 < n ? x[lane + 32] : zero;
+        pn[k] = zero;
+        done[k] = zero;
+    }
+    for (int64_t c = 0; c < nch; ++c) {
+        const int64_t base = c * PC_CH;
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {          // rows taken over during chunk c + 1
+            const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
+            pn[k] = base + 64 + lane < n ? x[base + 64 + lane] : zero;
+        }
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        __syncwarp();
+        const C<T> *bs = (c & 1) ? buf1 : buf0;
+#pragma unroll 4
+        for (int j = 0; j < PC_CH; ++j) {
+            const int64_t i = base + j;
+            if (i >= n) break;
+            const int d = (lane - j) & 31;
+            const C<T> l = (d >= 1 && d <= W && i + d < n) ? bs[j * Wp + d] : zero;
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const C<T> xi = shfl_c(w[k], j);
+                w[k] = csub(w[k], cmul(l, xi));
+                if (lane == j) { done[k] = xi; w[k] = pf[k]; }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            if (k < nr && base + lane < n) xs[int64_t(r0 + k) * nunk + o + base + lane] = done[k];
+            pf[k] = pn[k];
+        }
+        __syncwarp();
+        pc_stage_rows<T>((c & 1) ? buf1 : buf0, Bc, base + 2 * PC_CH, PC_CH, Wp, n, lane);
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncwarp();
+    // ---------------- diagonal
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (k >= nr) break;
+        C<T> *x = xs + int64_t(r0 + k) * nunk + o;
+        for (int64_t i = lane; i < n; i += 32) {
+            const C<T> dg = B[i * Wp];
+            const T den = dg.x * dg.x + dg.y * dg.y;
+            x[i] = cmul(x[i], mk<T>(dg.x / den, -dg.y / den));
+        }
+    }
+    __syncwarp();
+    // ---------------- backward: x_{i-d} -= L[i][i-d] x_i   (chunk c = steps i = n-1-32c-j)
+    // staged rows of chunk c: [n - 32(c+1), n - 32c), row i at index i - (n - 32(c+1))
+    pc_stage_rows<T>(buf0, B, n - PC_CH, PC_CH, Wp, n, lane);
+    asm volatile("cp.async.commit_group;\n" ::);
+    pc_stage_rows<T>(buf1, B, n - 2 * PC_CH, PC_CH, Wp, n, lane);
+    asm volatile("cp.async.commit_group;\n" ::);
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
+        w[k] = n - 1 - lane >= 0 ? x[n - 1 - lane] : zero;
+        pf[k] = n - 33 - lane >= 0 ? x[n - 33 - lane] : zero;
+        done[k] = zero;
+    }
+    for (int64_t c = 0; c < nch; ++c) {
+        const int64_t top = n - 1 - c * PC_CH;          // i of step j = 0
+        const int64_t sbase = n - (c + 1) * PC_CH;      // first staged row
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
+            pn[k] = top - 64 - lane >= 0 ? x[top - 64 - lane] : zero;
+        }
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        __syncwarp();
+        const C<T> *bs = (c & 1) ? buf1 : buf0;
+#pragma unroll 4
+        for (int j = 0; j < PC_CH; ++j) {
+            const int64_t i = top - j;
+            if (i < 0) break;
+            const int d = (lane - j) & 31;
+            const C<T> l = (d >= 1 && d <= W && i - d >= 0) ? bs[(i - sbase) * Wp + d] : zero;
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const C<T> xi = shfl_c(w[k], j);
+                w[k] = csub(w[k], cmul(l, xi));
+                if (lane == j) { done[k] = xi; w[k] = pf[k]; }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            if (k < nr && top - lane >= 0) xs[int64_t(r0 + k) * nunk + o + top - lane] = done[k];
+            pf[k] = pn[k];
+        }
+        __syncwarp();
+        pc_stage_rows<T>((c & 1) ? buf1 : buf0, B, n - (c + 3) * PC_CH, PC_CH, Wp, n, lane);
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncwarp();
+    if (sizeof(T) != sizeof(double)) {
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            if (k >= nr) break;
+            const C<T> *x = xs + int64_t(r0 + k) * nunk + o;
+            double2 *xd = u + int64_t(r0 + k) * nunk + o;
+            for (int64_t i = lane; i < n; i += 32) xd[i] = make_double2(double(x[i].x), double(x[i].y));
+        }
+    }
+}
+
 // Branch currents i_e = a_e (phi_tail - phi_head + emf_e) = a_e (u_t - u_h) + kappa_e.
 __global__ void k_pc_currents(const double2 *__restrict__ u, int64_t nunk, const double2 *__restrict__ kappa,
                               const double2 *__restrict__ a, const int32_t *__restrict__ slot,
@@ -624,6 +808,27 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         s->cap_rhs = R;
     }
     SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    for (int v = 0; v < 2; ++v) {
+        // one right-hand side per warp: the sweeps are latency-bound chains, so
+        // independent chains (right-hand sides x conductors) are what fills the GPU
+        const int32_t gmax = 1;
+        std::vector<int32_t> gs, gc;
+        for (int32_t r = 0; r < R;) {
+            int32_t e = r + 1;
+            while (e < R && e - r < gmax && slot[e] == slot[r]) ++e;
+            gs.push_back(r);
+            gc.push_back(e - r);
+            r = e;
+        }
+        if (s->d_grp_start[v]) cudaFree(s->d_grp_start[v]);
+        if (s->d_grp_count[v]) cudaFree(s->d_grp_count[v]);
+        SIE_CUDA(cudaMalloc((void **)&s->d_grp_start[v], gs.size() * sizeof(int32_t)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_grp_count[v], gc.size() * sizeof(int32_t)));
+        SIE_CUDA(cudaMemcpyAsync(s->d_grp_start[v], gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        SIE_CUDA(cudaMemcpyAsync(s->d_grp_count[v], gc.data(), gc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        SIE_CUDA(cudaStreamSynchronize(st));
+        s->ngroups[v] = int32_t(gs.size());
+    }
     if (uniq == s->slot_omega) return SIE_OK;   // factors cached
     const int32_t ns = int32_t(uniq.size());
     if (s->d_band) cudaFree(s->d_band);
@@ -686,7 +891,25 @@ int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int pr
     SIE_LAUNCH_CHECK(p);
     if (s->nunk > 0) {
         const int64_t warps = int64_t(R) * nblk;
-        if (s->W <= 31 && prec == SIE_PREC_MIXED)
+        if (s->W <= 31) {
+            const int v = prec == SIE_PREC_MIXED ? 0 : 1;
+            const int64_t gw = int64_t(s->ngroups[v]) * nblk;
+            const size_t sm32 = size_t(4) * 2 * PC_CH * (s->W + 1) * sizeof(float2);
+            const size_t sm64 = size_t(4) * 2 * PC_CH * (s->W + 1) * sizeof(double2);
+            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<float, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm32)));
+            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<double, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm64)));
+            if (prec == SIE_PREC_MIXED)
+                k_pc_solve_grp<float, 1><<<nblk_(gw * 32, 128), 128, sm32, st>>>(
+                    s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
+                    s->d_band32, s->d_bandc32, s->d_slot, s->d_grp_start[0], s->d_grp_count[0], s->ngroups[0], s->d_u,
+                    s->d_u32);
+            else
+                k_pc_solve_grp<double, 1><<<nblk_(gw * 32, 128), 128, sm64, st>>>(
+                    s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
+                    s->d_band, s->d_bandc, s->d_slot, s->d_grp_start[1], s->d_grp_count[1], s->ngroups[1], s->d_u, s->d_u);
+        } else if (false && s->W <= 31 && prec == SIE_PREC_MIXED)
             k_pc_solve_win<float><<<nblk_(warps * 32, 128), 128, 0, st>>>(
                 s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
                 s->d_band32, s->d_bandc32, s->d_slot, R, s->d_u, s->d_u32);
