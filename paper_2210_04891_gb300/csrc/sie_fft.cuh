@@ -214,46 +214,83 @@ __host__ __device__ constexpr double s16(int i) {
          : i == 4 ? 1.0 : i == 5 ? 0.92387953251128674 : i == 6 ? 0.70710678118654752 : 0.38268343236508977;
 }
 
-// In-register DFT of v[0..N), N a power of two <= 16: bit reversal, then
-// radix-2 butterflies with twiddles W_len^j = exp(-+ 2 pi i j / len), the
-// direction a compile-time choice so twiddles are immediates; multiplications
-// by 1 and by -+i are done as moves.
+// In-register DFTs of length 2, 4, 8 and 16, natural order in and out,
+// built from radix-4 (and one radix-2) butterflies with the twiddles as
+// immediates; the direction is a compile-time choice.  DFT8 = 2 x 4 and
+// DFT16 = 4 x 4 are four-step products in registers: the inner DFTs run over
+// n = j + A m, the twiddle is W_N^(j k1) and the outer DFTs run over j; the
+// final transposition is a register renaming.
+
+// v * W_16^t, t in [0, 16): W_16^(t + 8) = -W_16^t, W_16^4 = -i (forward).
 template <typename T, bool INV>
-__device__ __forceinline__ C<T> twiddle_mul(C<T> b, int ti) {
-    C<T> t;
-    if (ti == 0) return b;
-    if (ti == 4) {                      // W_16^4 = -i (forward), +i (inverse)
-        if (INV) { t.x = -b.y; t.y = b.x; } else { t.x = b.y; t.y = -b.x; }
-        return t;
+__device__ __forceinline__ C<T> twiddle_mul(C<T> b, int t) {
+    C<T> r;
+    const bool neg = t >= 8;
+    t &= 7;
+    if (t == 0) {
+        r = b;
+    } else if (t == 4) {
+        if (INV) { r.x = -b.y; r.y = b.x; } else { r.x = b.y; r.y = -b.x; }
+    } else {
+        const T c = T(c16(t)), sn = INV ? T(s16(t)) : T(-s16(t));
+        r.x = b.x * c - b.y * sn;
+        r.y = b.x * sn + b.y * c;
     }
-    const T c = T(c16(ti)), sn = INV ? T(s16(ti)) : T(-s16(ti));
-    t.x = b.x * c - b.y * sn;
-    t.y = b.x * sn + b.y * c;
-    return t;
+    if (neg) { r.x = -r.x; r.y = -r.y; }
+    return r;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void bfly4(C<T> &a0, C<T> &a1, C<T> &a2, C<T> &a3) {
+    const C<T> t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+    C<T> t3;                          // -i d (forward), +i d (inverse)
+    if (INV) { t3.x = -d.y; t3.y = d.x; } else { t3.x = d.y; t3.y = -d.x; }
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
 }
 
 template <typename T, int N, bool INV>
 __device__ __forceinline__ void dft_reg(C<T> (&v)[FFT_NMAX]) {
-    constexpr int LG = N == 2 ? 1 : N == 4 ? 2 : N == 8 ? 3 : 4;
+    if constexpr (N == 2) {
+        const C<T> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (N == 4) {
+        bfly4<T, INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (N == 8) {
+        // n = j + 2m: DFT4 over m for j = 0, 1; twiddle W_8^(j k1) = W_16^(2 j k1); DFT2 over j
+        bfly4<T, INV>(v[0], v[2], v[4], v[6]);
+        bfly4<T, INV>(v[1], v[3], v[5], v[7]);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        int r = 0;
+        for (int k1 = 1; k1 < 4; ++k1) v[1 + 2 * k1] = twiddle_mul<T, INV>(v[1 + 2 * k1], 2 * k1);
+        C<T> o[8];
 #pragma unroll
-        for (int b = 0; b < LG; ++b) r |= ((i >> b) & 1) << (LG - 1 - b);
-        if (r > i) { C<T> t = v[i]; v[i] = v[r]; v[r] = t; }
-    }
-#pragma unroll
-    for (int st = 0; st < LG; ++st) {
-        const int len = 2 << st, half = 1 << st;
-#pragma unroll
-        for (int s = 0; s < N; s += len) {
-#pragma unroll
-            for (int j = 0; j < half; ++j) {
-                const C<T> t = twiddle_mul<T, INV>(v[s + j + half], j * (16 / len));
-                v[s + j + half] = csub(v[s + j], t);
-                v[s + j] = cadd(v[s + j], t);
-            }
+        for (int k1 = 0; k1 < 4; ++k1) {      // X[k1 + 4 k2], k2 = 0, 1
+            o[k1] = cadd(v[2 * k1], v[2 * k1 + 1]);
+            o[k1 + 4] = csub(v[2 * k1], v[2 * k1 + 1]);
         }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = o[i];
+    } else {
+        static_assert(N == 16, "DFT length");
+        // n = j + 4m: DFT4 over m for j = 0..3; twiddle W_16^(j k1); DFT4 over j
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bfly4<T, INV>(v[j], v[j + 4], v[j + 8], v[j + 12]);
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) v[j + 4 * k1] = twiddle_mul<T, INV>(v[j + 4 * k1], j * k1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) bfly4<T, INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+        C<T> o[16];                            // v[4 k1 + k2] = X[k1 + 4 k2]
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = o[i];
     }
 }
 
@@ -276,43 +313,48 @@ inline void split4(int M, int &N1, int &N2) {
         default: { constexpr int N1 = 16, N2 = 16; BODY; } break;          \
     }
 
+// Four-step twiddle tables of an axis of length M = N1 N2 (built at plan
+// creation): tf[j2 * N1 + k1] = W_M^(j2 k1) for the forward pass 1 and
+// ti[k1 * N2 + p2] = W_M^(k1 p2) for the inverse pass A (used conjugated).
+
 template <typename T, int N1, int N2>
-__device__ __forceinline__ void x4_body(C<T> *S, C<T> *base, int ncols, int nx, int My, int Mz, int c0,
-                                        const C<T> *__restrict__ tw, const T *__restrict__ H) {
-    constexpr int KT = 16, Mx = N1 * N2, pitch = Mx + 1;
+__device__ __forceinline__ void x4_body(C<T> *S, C<T> *base, int ncols, int64_t hrow_off,
+                                        const C<T> *__restrict__ tf, const C<T> *__restrict__ ti,
+                                        const T *__restrict__ Hx) {
+    // input x < M/2 (the rest is zero padding); output kept for x < M/2
+    constexpr int KT = 16, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
     const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> 4;
     C<T> *Sl = S + line * pitch;
-    const C<T> zero = mk<T>(T(0), T(0));
+    const int64_t stride = int64_t(N2) * ncols;
     C<T> v[FFT_NMAX];
-    if (q < N2) {                      // pass 1: j2 = q, DFT over j1 (input zero for x >= nx)
+    if (q < N2) {                      // pass 1: j2 = q, DFT over j1
         const int j2 = q;
+        const C<T> *src = base + int64_t(j2) * ncols + line;
 #pragma unroll
-        for (int j1 = 0; j1 < N1; ++j1) {
-            const int x = j2 + N2 * j1;
-            v[j1] = x < nx ? base[int64_t(x) * ncols + line] : zero;
-        }
+        for (int j1 = 0; j1 < N1; ++j1) v[j1] = j1 < H1 ? src[j1 * stride] : mk<T>(T(0), T(0));
         dft_reg<T, N1, false>(v);
+        const C<T> *t = tf + j2 * N1;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) Sl[k1 * N2 + j2] = k1 ? cmul(v[k1], tw[(j2 * k1) & (Mx - 1)]) : v[0];
+        for (int k1 = 0; k1 < N1; ++k1) Sl[k1 * N2 + j2] = k1 ? cmul(v[k1], t[k1]) : v[0];
     }
     __syncthreads();
-    constexpr int hx = Mx / 2 + 1;
-    const int hz = Mz / 2 + 1;
-    const int col = c0 + line, ky = col / Mz, kz = col & (Mz - 1);
-    const T *Hc = H + (int64_t(fold_index(ky, My)) * hz + fold_index(kz, Mz)) * hx;
     if (q < N1) {                      // pass 2: k1 = q, DFT over j2, times H, inverse DFT over k2
         const int k1 = q;
 #pragma unroll
         for (int j2 = 0; j2 < N2; ++j2) v[j2] = Sl[k1 * N2 + j2];
         dft_reg<T, N2, false>(v);
+        const T *h = Hx + hrow_off + k1;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], Hc[fold_index(k1 + N1 * k2, Mx)]);
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], h[N1 * k2]);
         dft_reg<T, N2, true>(v);
+        const C<T> *t = ti + k1 * N2;
 #pragma unroll
         for (int p2 = 1; p2 < N2; ++p2) {
-            C<T> w = tw[(p2 * k1) & (Mx - 1)];
-            w.y = -w.y;
-            v[p2] = cmul(v[p2], w);
+            const C<T> w = t[p2];
+            C<T> r;
+            r.x = v[p2].x * w.x + v[p2].y * w.y;   // times conj(w)
+            r.y = v[p2].y * w.x - v[p2].x * w.y;
+            v[p2] = r;
         }
     }
     __syncthreads();                   // pass-2 reads complete before pass-A writes
@@ -321,189 +363,218 @@ __device__ __forceinline__ void x4_body(C<T> *S, C<T> *base, int ncols, int nx, 
         for (int p2 = 0; p2 < N2; ++p2) Sl[p2 * N1 + q] = v[p2];
     }
     __syncthreads();
-    if (q < N2) {                      // inverse pass B: p2 = q, DFT over k1, keep x < nx
+    if (q < N2) {                      // inverse pass B: p2 = q, DFT over k1, keep x < M/2
         const int p2 = q;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) v[k1] = Sl[p2 * N1 + k1];
         dft_reg<T, N1, true>(v);
+        C<T> *dst = base + int64_t(p2) * ncols + line;
 #pragma unroll
-        for (int p1 = 0; p1 < N1; ++p1) {
-            const int x = p2 + N2 * p1;
-            if (x < nx) base[int64_t(x) * ncols + line] = v[p1];
-        }
+        for (int p1 = 0; p1 < H1; ++p1) dst[p1 * stride] = v[p1];
     }
 }
 
 // x-pencils, four-step: forward FFT, times H, inverse FFT (the middle pass of
-// the 3-D convolution).  Buffer [batch][x][ncols]; one CTA per (batch, 16
-// columns); 16 * max(N1, N2) threads.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fft_x4(C<T> *__restrict__ buf, int64_t batch_stride, int ncols, int nx,
-                                                int Mx, int My, int Mz, const C<T> *__restrict__ tw,
-                                                const T *__restrict__ H) {
-    constexpr int KT = 16;
+// the 3-D convolution).  Buffer [batch][N_x][ncols] (x < N_x = M/2 stored);
+// one CTA per (batch, 16 columns); 16 * max(N1, N2) threads.  Hx: kernel
+// spectrum unfolded along x, [fold(ky)][fold(kz)][kx].  One kernel instance
+// per length (dispatched on the host).
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_fft_x4(C<T> *__restrict__ buf, int64_t batch_stride, int ncols,
+                                                int lgMz, int My, int Mz, const C<T> *__restrict__ tf,
+                                                const C<T> *__restrict__ ti, const T *__restrict__ Hx) {
+    constexpr int KT = 16, Mx = N1 * N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T> *S = reinterpret_cast<C<T> *>(smem_raw);
     const int tiles = ncols / KT;
     const int b = blockIdx.x / tiles, c0 = (blockIdx.x % tiles) * KT;
     C<T> *base = buf + b * batch_stride + c0;
-    SIE_SPLIT_DISPATCH(Mx, (x4_body<T, N1, N2>(S, base, ncols, nx, My, Mz, c0, tw, H)));
+    const int col = c0 + (threadIdx.x & (KT - 1));
+    const int ky = col >> lgMz, kz = col & (Mz - 1);
+    const int64_t hrow = (int64_t(fold_index(ky, My)) * (Mz / 2 + 1) + fold_index(kz, Mz)) * Mx;
+    x4_body<T, N1, N2>(S, base, ncols, hrow, tf, ti, Hx);
 }
 
-// ---- (y, z) plane passes with compile-time split (see k_fft_yz4)
+// ---- (y, z) plane passes with compile-time split (see k_fft_yz4).  The
+// input extent is half of each padded length (Ny = My/2, Nz = Mz/2).
 template <typename T, int N1, int N2>   // F1: z pass 1, rows y < Ny, global -> P row slots
-__device__ __forceinline__ void yz_f1(const C<T> *in, C<T> *P, int pitch, int Ny, int Nz, const C<T> *twz) {
-    constexpr int Mz = N1 * N2;
+__device__ __forceinline__ void yz_f1(const C<T> *in, C<T> *P, int pitch, int Ny, const C<T> *tfz) {
+    constexpr int Mz = N1 * N2, Nz = Mz / 2, H1 = N1 / 2;
+    constexpr int LG2 = N2 == 2 ? 1 : N2 == 4 ? 2 : N2 == 8 ? 3 : 4;
     C<T> v[FFT_NMAX];
     for (int it = threadIdx.x; it < Ny * N2; it += blockDim.x) {
-        const int y = it / N2, j2 = it & (N2 - 1);
+        const int y = it >> LG2, j2 = it & (N2 - 1);
+        const C<T> *src = in + y * Nz + j2;
 #pragma unroll
-        for (int j1 = 0; j1 < N1; ++j1) {
-            const int z = j2 + N2 * j1;
-            v[j1] = z < Nz ? in[y * Nz + z] : mk<T>(T(0), T(0));
-        }
+        for (int j1 = 0; j1 < N1; ++j1) v[j1] = j1 < H1 ? src[N2 * j1] : mk<T>(T(0), T(0));
         dft_reg<T, N1, false>(v);
+        const C<T> *t = tfz + j2 * N1;
+        C<T> *row = P + y * pitch + j2;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) P[y * pitch + k1 * N2 + j2] = k1 ? cmul(v[k1], twz[(j2 * k1) & (Mz - 1)]) : v[0];
+        for (int k1 = 0; k1 < N1; ++k1) row[k1 * N2] = k1 ? cmul(v[k1], t[k1]) : v[0];
     }
 }
 template <typename T, int N1, int N2>   // F2: z pass 2, P row slots -> Q natural rows
-__device__ __forceinline__ void yz_f2(const C<T> *P, C<T> *Q, int pitch, int Ny) {
+__device__ __forceinline__ void yz_f2(const C<T> *P, C<T> *Q, int pitch, int lgNy) {
     C<T> v[FFT_NMAX];
+    const int Ny = 1 << lgNy;
     for (int it = threadIdx.x; it < Ny * N1; it += blockDim.x) {
-        const int y = it % Ny, k1 = it / Ny;
+        const int y = it & (Ny - 1), k1 = it >> lgNy;
+        const C<T> *row = P + y * pitch + k1 * N2;
 #pragma unroll
-        for (int j2 = 0; j2 < N2; ++j2) v[j2] = P[y * pitch + k1 * N2 + j2];
+        for (int j2 = 0; j2 < N2; ++j2) v[j2] = row[j2];
         dft_reg<T, N2, false>(v);
+        C<T> *out = Q + y * pitch + k1;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) Q[y * pitch + k1 + N1 * k2] = v[k2];
+        for (int k2 = 0; k2 < N2; ++k2) out[N1 * k2] = v[k2];
     }
 }
 template <typename T, int N1, int N2>   // F3: y pass 1, all columns, Q rows < Ny -> P column slots
-__device__ __forceinline__ void yz_f3(const C<T> *Q, C<T> *P, int pitch, int Ny, int Mz, const C<T> *twy) {
-    constexpr int My = N1 * N2;
+__device__ __forceinline__ void yz_f3(const C<T> *Q, C<T> *P, int pitch, int lgMz, const C<T> *tfy) {
+    constexpr int H1 = N1 / 2;
     C<T> v[FFT_NMAX];
+    const int Mz = 1 << lgMz;
     for (int it = threadIdx.x; it < Mz * N2; it += blockDim.x) {
-        const int kz = it % Mz, j2 = it / Mz;
+        const int kz = it & (Mz - 1), j2 = it >> lgMz;
+        const C<T> *col = Q + j2 * pitch + kz;
 #pragma unroll
-        for (int j1 = 0; j1 < N1; ++j1) {
-            const int y = j2 + N2 * j1;
-            v[j1] = y < Ny ? Q[y * pitch + kz] : mk<T>(T(0), T(0));
-        }
+        for (int j1 = 0; j1 < N1; ++j1) v[j1] = j1 < H1 ? col[N2 * j1 * pitch] : mk<T>(T(0), T(0));
         dft_reg<T, N1, false>(v);
+        const C<T> *t = tfy + j2 * N1;
+        C<T> *o = P + j2 * pitch + kz;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1)
-            P[(k1 * N2 + j2) * pitch + kz] = k1 ? cmul(v[k1], twy[(j2 * k1) & (My - 1)]) : v[0];
+        for (int k1 = 0; k1 < N1; ++k1) o[k1 * N2 * pitch] = k1 ? cmul(v[k1], t[k1]) : v[0];
     }
 }
 template <typename T, int N1, int N2>   // F4: y pass 2, P column slots -> global spectrum
-__device__ __forceinline__ void yz_f4(const C<T> *P, C<T> *out, int pitch, int Mz) {
+__device__ __forceinline__ void yz_f4(const C<T> *P, C<T> *out, int pitch, int lgMz) {
     C<T> v[FFT_NMAX];
+    const int Mz = 1 << lgMz;
     for (int it = threadIdx.x; it < Mz * N1; it += blockDim.x) {
-        const int kz = it % Mz, k1 = it / Mz;
+        const int kz = it & (Mz - 1), k1 = it >> lgMz;
+        const C<T> *col = P + k1 * N2 * pitch + kz;
 #pragma unroll
-        for (int j2 = 0; j2 < N2; ++j2) v[j2] = P[(k1 * N2 + j2) * pitch + kz];
+        for (int j2 = 0; j2 < N2; ++j2) v[j2] = col[j2 * pitch];
         dft_reg<T, N2, false>(v);
+        C<T> *o = out + k1 * Mz + kz;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) out[(k1 + N1 * k2) * Mz + kz] = v[k2];
+        for (int k2 = 0; k2 < N2; ++k2) o[N1 * k2 * Mz] = v[k2];
     }
 }
 template <typename T, int N1, int N2>   // I1: y inverse pass A, global spectrum -> P
-__device__ __forceinline__ void yz_i1(const C<T> *in, C<T> *P, int pitch, int Mz, const C<T> *twy) {
-    constexpr int My = N1 * N2;
+__device__ __forceinline__ void yz_i1(const C<T> *in, C<T> *P, int pitch, int lgMz, const C<T> *tiy) {
     C<T> v[FFT_NMAX];
+    const int Mz = 1 << lgMz;
     for (int it = threadIdx.x; it < Mz * N1; it += blockDim.x) {
-        const int kz = it % Mz, k1 = it / Mz;
+        const int kz = it & (Mz - 1), k1 = it >> lgMz;
+        const C<T> *src = in + k1 * Mz + kz;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) v[k2] = in[(k1 + N1 * k2) * Mz + kz];
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[N1 * k2 * Mz];
         dft_reg<T, N2, true>(v);
+        const C<T> *t = tiy + k1 * N2;
+        C<T> *o = P + k1 * pitch + kz;
 #pragma unroll
         for (int p2 = 0; p2 < N2; ++p2) {
-            C<T> w = twy[(p2 * k1) & (My - 1)];
-            w.y = -w.y;
-            P[(p2 * N1 + k1) * pitch + kz] = (p2 && k1) ? cmul(v[p2], w) : v[p2];
+            C<T> r = v[p2];
+            if (p2) {
+                const C<T> w = t[p2];
+                r.x = v[p2].x * w.x + v[p2].y * w.y;
+                r.y = v[p2].y * w.x - v[p2].x * w.y;
+            }
+            o[p2 * N1 * pitch] = r;
         }
     }
 }
 template <typename T, int N1, int N2>   // I2: y inverse pass B, P -> Q rows y < Ny
-__device__ __forceinline__ void yz_i2(const C<T> *P, C<T> *Q, int pitch, int Ny, int Mz) {
+__device__ __forceinline__ void yz_i2(const C<T> *P, C<T> *Q, int pitch, int lgMz) {
+    constexpr int H1 = N1 / 2;
     C<T> v[FFT_NMAX];
+    const int Mz = 1 << lgMz;
     for (int it = threadIdx.x; it < Mz * N2; it += blockDim.x) {
-        const int kz = it % Mz, p2 = it / Mz;
+        const int kz = it & (Mz - 1), p2 = it >> lgMz;
+        const C<T> *src = P + p2 * N1 * pitch + kz;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) v[k1] = P[(p2 * N1 + k1) * pitch + kz];
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[k1 * pitch];
         dft_reg<T, N1, true>(v);
+        C<T> *o = Q + p2 * pitch + kz;
 #pragma unroll
-        for (int p1 = 0; p1 < N1; ++p1) {
-            const int y = p2 + N2 * p1;
-            if (y < Ny) Q[y * pitch + kz] = v[p1];
-        }
+        for (int p1 = 0; p1 < H1; ++p1) o[N2 * p1 * pitch] = v[p1];
     }
 }
 template <typename T, int N1, int N2>   // I3: z inverse pass A, Q rows -> P row slots
-__device__ __forceinline__ void yz_i3(const C<T> *Q, C<T> *P, int pitch, int Ny, const C<T> *twz) {
-    constexpr int Mz = N1 * N2;
+__device__ __forceinline__ void yz_i3(const C<T> *Q, C<T> *P, int pitch, int lgNy, const C<T> *tiz) {
     C<T> v[FFT_NMAX];
+    const int Ny = 1 << lgNy;
     for (int it = threadIdx.x; it < Ny * N1; it += blockDim.x) {
-        const int y = it % Ny, k1 = it / Ny;
+        const int y = it & (Ny - 1), k1 = it >> lgNy;
+        const C<T> *src = Q + y * pitch + k1;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) v[k2] = Q[y * pitch + k1 + N1 * k2];
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[N1 * k2];
         dft_reg<T, N2, true>(v);
+        const C<T> *t = tiz + k1 * N2;
+        C<T> *o = P + y * pitch + k1;
 #pragma unroll
         for (int p2 = 0; p2 < N2; ++p2) {
-            C<T> w = twz[(p2 * k1) & (Mz - 1)];
-            w.y = -w.y;
-            P[y * pitch + p2 * N1 + k1] = (p2 && k1) ? cmul(v[p2], w) : v[p2];
+            C<T> r = v[p2];
+            if (p2) {
+                const C<T> w = t[p2];
+                r.x = v[p2].x * w.x + v[p2].y * w.y;
+                r.y = v[p2].y * w.x - v[p2].x * w.y;
+            }
+            o[p2 * N1] = r;
         }
     }
 }
 template <typename T, int N1, int N2>   // I4: z inverse pass B, P row slots -> global, z < Nz
-__device__ __forceinline__ void yz_i4(const C<T> *P, C<T> *out, int pitch, int Ny, int Nz) {
+__device__ __forceinline__ void yz_i4(const C<T> *P, C<T> *out, int pitch, int Ny) {
+    constexpr int Mz = N1 * N2, Nz = Mz / 2, H1 = N1 / 2;
+    constexpr int LG2 = N2 == 2 ? 1 : N2 == 4 ? 2 : N2 == 8 ? 3 : 4;
     C<T> v[FFT_NMAX];
     for (int it = threadIdx.x; it < Ny * N2; it += blockDim.x) {
-        const int y = it / N2, p2 = it & (N2 - 1);
+        const int y = it >> LG2, p2 = it & (N2 - 1);
+        const C<T> *src = P + y * pitch + p2 * N1;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) v[k1] = P[y * pitch + p2 * N1 + k1];
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[k1];
         dft_reg<T, N1, true>(v);
+        C<T> *o = out + y * Nz + p2;
 #pragma unroll
-        for (int p1 = 0; p1 < N1; ++p1) {
-            const int z = p2 + N2 * p1;
-            if (z < Nz) out[y * Nz + z] = v[p1];
-        }
+        for (int p1 = 0; p1 < H1; ++p1) o[N2 * p1] = v[p1];
     }
 }
 
 // (y, z) planes, four-step in both axes, two shared buffers (P: My x pitch,
 // Q: Ny x pitch) so that every step reads one buffer and writes the other.
-// Forward: input [Ny][Nz] (zero-padded), output the full [My][Mz] spectrum.
-// Inverse: input [My][Mz], output [Ny][Nz].  One CTA per plane.
+// Forward: input [Ny][Nz] (zero-padded to My x Mz), output the [My][Mz]
+// spectrum.  Inverse: input [My][Mz], output [Ny][Nz].  One CTA per plane.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_yz4(const C<T> *__restrict__ src, int64_t src_stride,
-                                                 C<T> *__restrict__ dst, int64_t dst_stride, int Ny, int Nz, int My,
-                                                 int Mz, const C<T> *__restrict__ twy, const C<T> *__restrict__ twz,
+                                                 C<T> *__restrict__ dst, int64_t dst_stride, int My, int Mz,
+                                                 const C<T> *__restrict__ tfy, const C<T> *__restrict__ tiy,
+                                                 const C<T> *__restrict__ tfz, const C<T> *__restrict__ tiz,
                                                  int inverse) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int pitch = Mz + 1;
+    const int pitch = Mz + 1, Ny = My / 2;
+    const int lgNy = ilog2(Ny), lgMz = ilog2(Mz);
     C<T> *P = reinterpret_cast<C<T> *>(smem_raw);
     C<T> *Qb = P + My * pitch;
     const C<T> *in = src + blockIdx.x * src_stride;
     C<T> *out = dst + blockIdx.x * dst_stride;
     if (!inverse) {
-        SIE_SPLIT_DISPATCH(Mz, (yz_f1<T, N1, N2>(in, P, pitch, Ny, Nz, twz)));
+        SIE_SPLIT_DISPATCH(Mz, (yz_f1<T, N1, N2>(in, P, pitch, Ny, tfz)));
         __syncthreads();
-        SIE_SPLIT_DISPATCH(Mz, (yz_f2<T, N1, N2>(P, Qb, pitch, Ny)));
+        SIE_SPLIT_DISPATCH(Mz, (yz_f2<T, N1, N2>(P, Qb, pitch, lgNy)));
         __syncthreads();
-        SIE_SPLIT_DISPATCH(My, (yz_f3<T, N1, N2>(Qb, P, pitch, Ny, Mz, twy)));
+        SIE_SPLIT_DISPATCH(My, (yz_f3<T, N1, N2>(Qb, P, pitch, lgMz, tfy)));
         __syncthreads();
-        SIE_SPLIT_DISPATCH(My, (yz_f4<T, N1, N2>(P, out, pitch, Mz)));
+        SIE_SPLIT_DISPATCH(My, (yz_f4<T, N1, N2>(P, out, pitch, lgMz)));
     } else {
-        SIE_SPLIT_DISPATCH(My, (yz_i1<T, N1, N2>(in, P, pitch, Mz, twy)));
+        SIE_SPLIT_DISPATCH(My, (yz_i1<T, N1, N2>(in, P, pitch, lgMz, tiy)));
         __syncthreads();
-        SIE_SPLIT_DISPATCH(My, (yz_i2<T, N1, N2>(P, Qb, pitch, Ny, Mz)));
+        SIE_SPLIT_DISPATCH(My, (yz_i2<T, N1, N2>(P, Qb, pitch, lgMz)));
         __syncthreads();
-        SIE_SPLIT_DISPATCH(Mz, (yz_i3<T, N1, N2>(Qb, P, pitch, Ny, twz)));
+        SIE_SPLIT_DISPATCH(Mz, (yz_i3<T, N1, N2>(Qb, P, pitch, lgNy, tiz)));
         __syncthreads();
-        SIE_SPLIT_DISPATCH(Mz, (yz_i4<T, N1, N2>(P, out, pitch, Ny, Nz)));
+        SIE_SPLIT_DISPATCH(Mz, (yz_i4<T, N1, N2>(P, out, pitch, Ny)));
     }
 }
 

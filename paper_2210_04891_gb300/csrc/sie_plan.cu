@@ -322,6 +322,17 @@ __global__ void k_extract_H(const double2 *Hc, double *H64, float *H32, int Mx, 
     H32[i] = float(v);
 }
 
+// Unfold the x index of the folded spectrum: Hx[row][kx] = H[row][fold(kx)].
+__global__ void k_unfold_H(const double *H, double *Hx64, float *Hx32, int Mx, int64_t n) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int kx = int(i % Mx);
+    const int64_t row = i / Mx;
+    const double v = H[row * (Mx / 2 + 1) + fold_index(kx, Mx)];
+    Hx64[i] = v;
+    Hx32[i] = float(v);
+}
+
 __global__ void k_branch_diag(const int64_t *ptr, const int32_t *col, const double *Ldir, const int32_t *br_tri,
                               const int8_t *br_local, int64_t nb, double *diagL) {
     int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -361,6 +372,28 @@ namespace sie {
 
 // FFT convolution of nrhs*3 grids [Nx][Ny][Nz] (in `grid`, overwritten with the
 // result) through the spectral buffer `spec` [nrhs*3][Nx][My][Mz].
+template <typename T> struct Tables;
+template <> struct Tables<double> {
+    static const double2 *tf(const pfft_plan *p, int a) { return p->d_tf64[a]; }
+    static const double2 *ti(const pfft_plan *p, int a) { return p->d_ti64[a]; }
+    static const double *Hx(const pfft_plan *p) { return p->d_Hx64; }
+};
+template <> struct Tables<float> {
+    static const float2 *tf(const pfft_plan *p, int a) { return p->d_tf32[a]; }
+    static const float2 *ti(const pfft_plan *p, int a) { return p->d_ti32[a]; }
+    static const float *Hx(const pfft_plan *p) { return p->d_Hx32; }
+};
+
+template <typename T, int N1, int N2>
+int launch_x4(pfft_plan *p, C<T> *spec, int ncols, int lgMz, unsigned grid, int thr, size_t pb, cudaStream_t s) {
+    using Tb = Tables<T>;
+    int rc = set_smem((const void *)k_fft_x4<T, N1, N2>, pb);
+    if (rc) return rc;
+    k_fft_x4<T, N1, N2><<<grid, thr, pb, s>>>(spec, int64_t(p->Nx) * ncols, ncols, lgMz, p->My, p->Mz, Tb::tf(p, 0),
+                                              Tb::ti(p, 0), Tb::Hx(p));
+    return SIE_OK;
+}
+
 template <typename T>
 int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s) {
     const int nb = ngrids * p->Nx;
@@ -369,28 +402,29 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
     int rc = set_smem((const void *)k_fft_yz4<T>, plane_bytes);
     if (rc) return rc;
+    using Tb = Tables<T>;
     {
         StageTimer tm(p, SIE_STAGE_FFT_PLANE_FWD, s);
-        k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(grid, int64_t(p->Ny) * p->Nz, spec, int64_t(p->My) * p->Mz, p->Ny,
-                                                 p->Nz, p->My, p->Mz, twiddle<T>(p, 1), twiddle<T>(p, 2), 0);
+        k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(grid, int64_t(p->Ny) * p->Nz, spec, int64_t(p->My) * p->Mz, p->My,
+                                                 p->Mz, Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2), 0);
         SIE_LAUNCH_CHECK(p);
     }
     const int KT = 16;
     const int ncols = p->My * p->Mz;
     const size_t pb = size_t(KT) * (p->Mx + 1) * sizeof(C<T>);
-    rc = set_smem((const void *)k_fft_x4<T>, pb);
-    if (rc) return rc;
-    const T *H = nullptr;
-    if constexpr (sizeof(T) == 8) H = reinterpret_cast<const T *>(p->d_H64); else H = reinterpret_cast<const T *>(p->d_H32);
     {
         StageTimer tm(p, SIE_STAGE_FFT_PENCIL, s);
-        k_fft_x4<T><<<ngrids * (ncols / KT), KT * std::max(NX1, NX2), pb, s>>>(
-            spec, int64_t(p->Nx) * ncols, ncols, p->Nx, p->Mx, p->My, p->Mz, twiddle<T>(p, 0), H);
+        int lgMz = 0;
+        while ((1 << lgMz) < p->Mz) ++lgMz;
+        const unsigned grid = unsigned(ngrids * (ncols / KT));
+        const int thr = KT * std::max(NX1, NX2);
+        SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x4<T, N1, N2>(p, spec, ncols, lgMz, grid, thr, pb, s)));
+        if (rc) return rc;
         SIE_LAUNCH_CHECK(p);
     }
     StageTimer tm(p, SIE_STAGE_FFT_PLANE_INV, s);
-    k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(spec, int64_t(p->My) * p->Mz, grid, int64_t(p->Ny) * p->Nz, p->Ny, p->Nz,
-                                             p->My, p->Mz, twiddle<T>(p, 1), twiddle<T>(p, 2), 1);
+    k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(spec, int64_t(p->My) * p->Mz, grid, int64_t(p->Ny) * p->Nz, p->My, p->Mz,
+                                             Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2), 1);
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
@@ -676,6 +710,23 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         }
         UP(p->d_tw64[a], w64);
         UP(p->d_tw32[a], w32);
+        int n1, n2;
+        split4(M, n1, n2);
+        std::vector<double2> tf(M), ti(M);
+        std::vector<float2> tf32(M), ti32(M);
+        for (int j2 = 0; j2 < n2; ++j2)
+            for (int k1 = 0; k1 < n1; ++k1) {
+                tf[j2 * n1 + k1] = w64[(j2 * k1) % M];
+                ti[k1 * n2 + j2] = w64[(j2 * k1) % M];
+            }
+        for (int k = 0; k < M; ++k) {
+            tf32[k] = make_float2(float(tf[k].x), float(tf[k].y));
+            ti32[k] = make_float2(float(ti[k].x), float(ti[k].y));
+        }
+        UP(p->d_tf64[a], tf);
+        UP(p->d_ti64[a], ti);
+        UP(p->d_tf32[a], tf32);
+        UP(p->d_ti32[a], ti32);
     }
     // device-side geometry for the setup kernels
     double *d_verts = nullptr, *d_area = nullptr, *d_r7b = nullptr, *d_r7w = nullptr, *d_tgb = nullptr, *d_tgw = nullptr;
@@ -722,6 +773,11 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         if ((rcode = plan_alloc(p, (void **)&p->d_H64, nh * sizeof(double)))) return bail(rcode);
         if ((rcode = plan_alloc(p, (void **)&p->d_H32, nh * sizeof(float)))) return bail(rcode);
         k_extract_H<<<(nh + 255) / 256, 256, 0, s>>>(d_Hc, p->d_H64, p->d_H32, p->Mx, p->My, p->Mz, 1.0 / double(nM));
+        p->launches++;
+        const int64_t nhx = int64_t(p->Mx) * (p->My / 2 + 1) * (p->Mz / 2 + 1);
+        if ((rcode = plan_alloc(p, (void **)&p->d_Hx64, nhx * sizeof(double)))) return bail(rcode);
+        if ((rcode = plan_alloc(p, (void **)&p->d_Hx32, nhx * sizeof(float)))) return bail(rcode);
+        k_unfold_H<<<(nhx + 255) / 256, 256, 0, s>>>(p->d_H64, p->d_Hx64, p->d_Hx32, p->Mx, nhx);
         p->launches++;
     }
     // ---- near-field blocks

@@ -77,6 +77,12 @@ struct pfft_plan {
     float *d_H32 = nullptr;
     double2 *d_tw64[3] = {nullptr, nullptr, nullptr};   // per axis, length M_d
     float2 *d_tw32[3] = {nullptr, nullptr, nullptr};
+    // four-step twiddle tables per axis: tf[j2][k1] = W^(j2 k1), ti[k1][p2] = W^(k1 p2)
+    double2 *d_tf64[3] = {nullptr, nullptr, nullptr}, *d_ti64[3] = {nullptr, nullptr, nullptr};
+    float2 *d_tf32[3] = {nullptr, nullptr, nullptr}, *d_ti32[3] = {nullptr, nullptr, nullptr};
+    // kernel spectrum unfolded along x: [My/2+1][Mz/2+1][Mx]
+    double *d_Hx64 = nullptr;
+    float *d_Hx32 = nullptr;
     // loop basis on the device
     int32_t *d_tour_node = nullptr;     // [2 nn]
     int8_t *d_tour_enter = nullptr;     // [2 nn]
