@@ -57,32 +57,45 @@ def peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-# ------------------------------------------------------------------ algorithmic bytes per stage launch
+# ------------------------------------------------------------------ algorithmic work per stage launch
 
-def stage_bytes(stage, plan_info, R, mixed, Ng, Nx, My, Mz, nt, Q, n_near, nl, nb, O=3):
-    cb = 8 if mixed else 16                   # grid complex size
-    rb = 4 if mixed else 8                    # real size
+SM_COUNT, FP32_LANES_PER_SM = 152, 128      # GB300: 2 dies x 76 SMs, 128 FP32 FMA lanes per SM
+
+
+def alu_peak_tflops(sm_mhz):
+    """FP32 FMA peak of the CUDA cores: SMs x lanes x 2 flop x SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def stage_work(stage, c):
+    """(bound, algorithmic amount per launch group, unit) of one stage.
+
+    Bytes are the unique data a stage must move (each operand read once,
+    each result written once); flops count the real multiply-adds of the
+    block-sparse products (a 3x3 real block times a complex 3-vector = 18 FMA
+    = 36 flop per right-hand side).  c: sizes of the workload and plan."""
+    R, cb = c["R"], c["cb"]
+    Ng, Nx, My, Mz, nt, nl = c["Ng"], c["Nx"], c["My"], c["Mz"], c["nt"], c["nl"]
     if stage == "fft_plane_fwd":
-        return 3 * R * (Ng + Nx * My * Mz) * cb
+        return "hbm", 3 * R * (Ng + Nx * My * Mz) * cb, "B"
     if stage == "fft_pencil":
-        return 3 * R * 2 * Nx * My * Mz * cb + (Nx + 1) * (My // 2 + 1) * (Mz // 2 + 1) * rb
+        return "hbm", 3 * R * 2 * Nx * My * Mz * cb + Nx * (My // 2 + 1) * (Mz // 2 + 1) * cb // 2, "B"
     if stage == "fft_plane_inv":
-        return 3 * R * (Nx * My * Mz + Ng) * cb
-    if stage == "near":
-        # L_d read once, point potentials + currents read once, y_tri written once
-        return n_near * 9 * rb + R * nt * Q * 3 * cb + R * nt * 3 * cb + R * nt * 3 * 16
+        return "hbm", 3 * R * (Nx * My * Mz + Ng) * cb, "B"
     if stage == "project":
-        return R * nt * Q * 3 * cb + 3 * R * Ng * cb + nt * Q * O ** 3 * (4 + rb)
+        # c_T read, node-ordered block records read, grid written
+        return "hbm", R * nt * 3 * cb + c["n_pair"] * c["rec"] + (Ng + 1) * 8 + 3 * R * Ng * cb, "B"
     if stage == "interp":
-        return 3 * R * Ng * cb + R * nt * Q * 3 * cb
-    if stage == "point_currents":
-        return R * nt * 3 * cb + R * nt * Q * 3 * cb
+        # potentials of the nodes in use read and written once
+        return "hbm", 2 * 3 * R * c["n_active"] * cb, "B"
+    if stage == "near":
+        return "alu", 36 * R * (c["n_near"] + c["n_pair"]), "flop"
     if stage == "loop_to_branch":
-        return R * nl * 16 + R * nt * 3 * cb
+        return "hbm", R * nl * 16 + R * nt * 3 * cb, "B"
     if stage == "branch_to_loop":
-        return R * nt * 3 * 16 + R * nl * 16
+        return "hbm", R * nt * 3 * 16 + R * nl * 16, "B"
     if stage == "precond_apply":
-        return 2 * R * nl * 16
+        return "hbm", 2 * R * nl * 16, "B"
     return None
 
 
@@ -304,19 +317,34 @@ def main():
 
     # roofline of the dominant stage
     hbm, bf16, src = peaks()
-    nt, Q = info["n_tri"], 7
     Nx, Ny, Nz = w["grid"]
+    from paper_2210_04891_gb300 import native as N
+    pnode = P.export(N.EXPORT_PROJ_NODE)
+    ctx = dict(R=R, cb=8, rec=48, Ng=Nx * Ny * Nz, Nx=Nx, My=2 * Ny, Mz=2 * Nz, nt=info["n_tri"], nl=L.nl,
+               n_near=info["n_near_pairs"], n_pair=int(pnode.size), n_active=int(np.unique(pnode).size))
     dom = max((s for s in prof if prof[s][1] > 0), key=lambda s: prof[s][0])
     ms_dom, n_dom = prof[dom]
-    algo = stage_bytes(dom, info, R, True, Nx * Ny * Nz, Nx, 2 * Ny, 2 * Nz, nt, Q, info["n_near_pairs"],
-                       L.nl, L.nb)
     stage_table = {s: {"ms_per_step": v[0] / K, "launch_groups": v[1]} for s, v in prof.items() if v[1]}
     roofline = None
-    if algo:
-        achieved = algo / (ms_dom / n_dom / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": None, "kernel": dom, "peak_source": src,
-                    "algorithmic_bytes_per_launch": algo, "launch_ms": ms_dom / n_dom}
+    work = stage_work(dom, ctx)
+    if work:
+        bound, amount, unit = work
+        sec = ms_dom / n_dom / 1e3
+        if bound == "hbm":
+            achieved, peak, u, psrc = amount / sec / 1e9, hbm, "GB/s", src
+        else:
+            mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+            achieved, peak, u = amount / sec / 1e12, alu_peak_tflops(mhz), "TFLOP/s"
+            psrc = f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {mhz:.0f} MHz"
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": u, "frac": achieved / peak,
+                    "traffic": None, "kernel": dom, "peak_source": psrc,
+                    "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": ms_dom / n_dom}
+        for s in stage_table:
+            wk = stage_work(s, ctx)
+            if wk:
+                sec = stage_table[s]["ms_per_step"] * K / stage_table[s]["launch_groups"] / 1e3
+                stage_table[s]["bound"] = wk[0]
+                stage_table[s]["achieved"] = wk[1] / sec / (1e9 if wk[0] == "hbm" else 1e12)
 
     # end to end through host buffers (pinned)
     xh = x.cpu().pin_memory()

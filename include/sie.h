@@ -186,9 +186,15 @@ int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, in
  *   SIE_EXPORT_HHAT      double [N_y+1][N_z+1][N_x+1] kernel spectrum / (8 N_x N_y N_z),
  *                        index k folded to min(k, 2N - k) per axis
  *   SIE_EXPORT_START     int32  [n_tri][7][3] stencil start node of each sample point
+ *   SIE_EXPORT_PROJ_PTR  int64  [n_tri + 1]   projection-block row offsets (rows = triangles);
+ *                        the last entry is the number of (node, triangle) pairs n_pair
+ *   SIE_EXPORT_PROJ_NODE int32  [n_pair]      grid node n of each block, ascending per row
+ *   SIE_EXPORT_PROJ_W    double [n_pair][3][3] W(n, T)[d][k] = sum_q L_n(r_q) (w_q/2)(r_q - v_k)_d,
+ *                        the projection of Sec. IV-B with the point currents folded in
  * capacity_bytes is the size of host_out; SIE_ERR_ARG if it is too small. */
 enum { SIE_EXPORT_NEAR_PTR = 0, SIE_EXPORT_NEAR_COL = 1, SIE_EXPORT_LD = 2, SIE_EXPORT_LDIRECT = 3,
-       SIE_EXPORT_HHAT = 4, SIE_EXPORT_START = 5 };
+       SIE_EXPORT_HHAT = 4, SIE_EXPORT_START = 5, SIE_EXPORT_PROJ_PTR = 6, SIE_EXPORT_PROJ_NODE = 7,
+       SIE_EXPORT_PROJ_W = 8 };
 int pfft_plan_export(const pfft_plan *p, int32_t what, void *host_out, int64_t capacity_bytes);
 
 /* Step 2 of Sec. IV-B alone: phi_g = H Q_g for nbatch grids, in place.
@@ -218,7 +224,16 @@ int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec
  * pfft_precond_apply and sie_solve is bracketed by CUDA events recorded on the
  * stream the stage runs on; pfft_profile_read waits for them and returns the
  * accumulated device time (ms) and launch count of each stage since the last
- * enable.  Disabled by default; enabling resets the counters. */
+ * enable.  Disabled by default; enabling resets the counters.  In pfft_matvec:
+ *   LOOP_TO_BRANCH  loop currents -> local edge currents c_T (A^T, Euler-tour scan)
+ *   POINT_CURRENTS  not launched: the point currents are folded into the projection blocks
+ *   PROJECT         grid currents Q_g = sum_T W(n, T) c_T (Sec. IV-B step 1)
+ *   FFT_*           phi_g = H Q_g (step 2): forward y/z planes, x pencils with the
+ *                   kernel product, inverse y/z planes
+ *   INTERP          grid potentials regrouped with the right-hand sides innermost
+ *   NEAR            per triangle: pre-corrected near blocks (step 4) + interpolation
+ *                   (step 3) + Z_s Gram term, one fused gather
+ *   BRANCH_TO_LOOP  triangle outputs -> branch voltages -> loop voltages (A) */
 enum { SIE_STAGE_LOOP_TO_BRANCH = 0, SIE_STAGE_POINT_CURRENTS = 1, SIE_STAGE_PROJECT = 2,
        SIE_STAGE_FFT_PLANE_FWD = 3, SIE_STAGE_FFT_PENCIL = 4, SIE_STAGE_FFT_PLANE_INV = 5,
        SIE_STAGE_INTERP = 6, SIE_STAGE_NEAR = 7, SIE_STAGE_BRANCH_TO_LOOP = 8,

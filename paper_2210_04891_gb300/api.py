@@ -135,6 +135,11 @@ class Plan:
                   N.EXPORT_LD: ((nn, 3, 3), np.float64), N.EXPORT_LDIRECT: ((nn, 3, 3), np.float64),
                   N.EXPORT_HHAT: ((g[1] + 1, g[2] + 1, g[0] + 1), np.float64),
                   N.EXPORT_START: ((nt, 7, 3), np.int32)}
+        if what in (N.EXPORT_PROJ_NODE, N.EXPORT_PROJ_W):
+            npair = int(self.export(N.EXPORT_PROJ_PTR)[-1])
+            shapes[N.EXPORT_PROJ_NODE] = ((npair,), np.int32)
+            shapes[N.EXPORT_PROJ_W] = ((npair, 3, 3), np.float64)
+        shapes[N.EXPORT_PROJ_PTR] = ((nt + 1,), np.int64)
         shape, dt = shapes[what]
         out = np.zeros(shape, dt)
         check(lib().pfft_plan_export(self.h, what, _ptr(out), out.nbytes))

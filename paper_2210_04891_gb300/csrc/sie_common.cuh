@@ -31,6 +31,42 @@ template <typename V> __device__ __forceinline__ V mul_mi(V a, bool inv) {
     return z;
 }
 
+// One 3x3 real block of a block-sparse matrix with its column index, packed so
+// a warp reads it with a few uniform 16-byte loads: out[a] += sum_b b[3a+b] x[b].
+template <typename T> struct Rec;
+template <> struct alignas(16) Rec<float> {
+    float b[9];
+    int32_t col;
+    float pad[2];
+};
+template <> struct alignas(16) Rec<double> {
+    double b[9];
+    int64_t col;
+};
+static_assert(sizeof(Rec<float>) == 48 && sizeof(Rec<double>) == 80, "packed block records");
+
+template <typename T> __device__ __forceinline__ int64_t load_rec(const Rec<T> *__restrict__ r, T (&b)[9]);
+template <> __device__ __forceinline__ int64_t load_rec<float>(const Rec<float> *__restrict__ r, float (&b)[9]) {
+    const float4 *v = reinterpret_cast<const float4 *>(r);
+    const float4 u0 = __ldg(v), u1 = __ldg(v + 1), u2 = __ldg(v + 2);
+    b[0] = u0.x; b[1] = u0.y; b[2] = u0.z; b[3] = u0.w;
+    b[4] = u1.x; b[5] = u1.y; b[6] = u1.z; b[7] = u1.w;
+    b[8] = u2.x;
+    return __float_as_int(u2.y);
+}
+template <> __device__ __forceinline__ int64_t load_rec<double>(const Rec<double> *__restrict__ r, double (&b)[9]) {
+    const double2 *v = reinterpret_cast<const double2 *>(r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 u = __ldg(v + i);
+        b[2 * i] = u.x;
+        b[2 * i + 1] = u.y;
+    }
+    const double2 u = __ldg(v + 4);
+    b[8] = u.x;
+    return __double_as_longlong(u.y);
+}
+
 inline bool cuda_ok(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return true;
     set_error(std::string(what) + ": " + cudaGetErrorString(e));

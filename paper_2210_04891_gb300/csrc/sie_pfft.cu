@@ -2,11 +2,11 @@
 // applied by the pre-corrected FFT (Sec. IV-A, IV-B of arXiv 2210.04891):
 //
 //   alpha = A^T x                     (Eq. CurT; Euler-tour subtree sums)
-//   J_q   = sum_k s_k alpha_k (w_q/2)(r_q - v_k)   point currents (Eq. RWG)
-//   Q_g   = B alpha                   (Eq. Projection; node gather lists)
+//   Q_g   = sum_T W(n,T) c_T          (Eq. Projection with the point currents
+//                                      J_q = sum_k c_k (w_q/2)(r_q - v_k) folded in)
 //   phi_g = H Q_g                     (Eq. FFTCal; zero-padded FFT convolution)
-//   Phi_q = sum_n L_n(r_q) phi_n      (Eq. interpolation, I = B^T)
-//   y_T   = Z_s G_T c_T + c_L (far_T + sum_T' L_d(T,T') c_T')    (Eq. Zb, Eq. Lb)
+//   y_T   = Z_s G_T c_T + c_L (sum_n W(n,T)^T phi_n + sum_T' L_d(T,T') c_T')
+//                                     (Eq. interpolation with I = B^T, Eq. Zb, Eq. Lb)
 //   y     = A y_b                     (Eq. VolT; Euler-tour root-path sums)
 //
 // A^T x: the current of a twig equals minus the current its subtree receives
@@ -15,6 +15,12 @@
 // its link's voltage plus psi(head) - psi(tail), psi(v) the sum of twig
 // voltages on v's path to the root = a prefix sum of +-delta over the tour.
 // Both are exact rewrites of the sparse products (no approximation).
+//
+// Projection, interpolation and near field are block-sparse x dense products
+// with 3x3 real blocks and complex right-hand sides: every dense operand is
+// stored with the right-hand sides innermost (c_T as [T][3][R], potentials as
+// [n][3][R]), one warp reads a block once and applies it to a slab of up to
+// 128 right-hand sides with coalesced loads.
 #include <algorithm>
 #include <cmath>
 #include <memory>
@@ -127,8 +133,8 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const dou
                             const int32_t *__restrict__ loop_of_branch, const int32_t *__restrict__ twig_node,
                             const int32_t *__restrict__ head, const int32_t *__restrict__ enter,
                             const int32_t *__restrict__ exit_, int64_t nt, int32_t nrhs, int space, int64_t nb,
-                            C<T> *__restrict__ c_tri, C<T> *__restrict__ cT) {
-    // i = (t * 3 + k) * R + r: the RHS-innermost copy cT is written coalesced
+                            C<T> *__restrict__ cT) {
+    // i = (t * 3 + k) * R + r: the right-hand sides innermost
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nt * 3 * nrhs) return;
     int64_t tk = i / nrhs, r = i % nrhs;
@@ -141,199 +147,196 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const dou
             a = x[r * nb + b];
         if (ts[tk] < 0) { a.x = -a.x; a.y = -a.y; }
     }
-    const C<T> v = mk<T>(T(a.x), T(a.y));
-    cT[i] = v;
-    c_tri[r * nt * 3 + tk] = v;
+    cT[i] = mk<T>(T(a.x), T(a.y));
 }
 
-// Pre-corrected near field as a block-sparse x dense product (Eq. Lb):
-// ynear[t][k][r] = sum_{t' near t} sum_l L_d(t, t')[k][l] cT[t'][l][r].
-// One warp per (row t, chunk of 32 RB right-hand sides); each L_d block is read
-// once per chunk and applied to all of its right-hand sides, lane r reading
-// the neighbours' currents contiguously over r.
-template <typename T, int RB>
-__global__ void __launch_bounds__(256) k_near_spmm(const int64_t *__restrict__ near_ptr,
-                                                   const int32_t *__restrict__ near_col, const T *__restrict__ Ld,
-                                                   const C<T> *__restrict__ cT, int64_t nt, int32_t R, int32_t nchunk,
-                                                   C<T> *__restrict__ ynear) {
+// V complex values at p (16-byte aligned when V = 2).
+template <typename T, int V> __device__ __forceinline__ void ldv(const C<T> *p, C<T> (&v)[V]) {
+    if constexpr (V == 2) {
+        static_assert(sizeof(T) == 4, "two complex per load only in FP32");
+        const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = make_float2(u.x, u.y);
+        v[1] = make_float2(u.z, u.w);
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+template <typename T, int V> __device__ __forceinline__ void stv(C<T> *p, const C<T> (&v)[V]) {
+    if constexpr (V == 2) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+        *p = v[0];
+    }
+}
+
+// acc[a][j][v] += sum over the records e of row [e0, e1) of
+//                 sum_b rec_e.b[3a+b] X[col_e][b][r],   r = rl + 32 V j + v.
+// X is [rows][3][R] (right-hand sides innermost).  FULL: every r < R.
+template <typename T, int V, int J, bool FULL>
+__device__ __forceinline__ void gather_rows(const Rec<T> *__restrict__ rec, int64_t e0, int64_t e1,
+                                            const C<T> *__restrict__ X, int32_t R, int32_t rl,
+                                            C<T> (&acc)[3][J][V]) {
+    const int64_t ld = 3 * int64_t(R);
+#pragma unroll 2
+    for (int64_t e = e0; e < e1; ++e) {
+        T b[9];
+        const int64_t col = load_rec<T>(rec + e, b);
+        const C<T> *x = X + col * ld;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int32_t r = rl + 32 * V * j;
+            if (FULL || r < R) {
+                C<T> x0[V], x1[V], x2[V];
+                ldv<T, V>(x + r, x0);
+                ldv<T, V>(x + R + r, x1);
+                ldv<T, V>(x + 2 * R + r, x2);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        acc[a][j][v].x += b[3 * a] * x0[v].x + b[3 * a + 1] * x1[v].x + b[3 * a + 2] * x2[v].x;
+                        acc[a][j][v].y += b[3 * a] * x0[v].y + b[3 * a + 1] * x1[v].y + b[3 * a + 2] * x2[v].y;
+                    }
+            }
+        }
+    }
+}
+
+template <typename T, int V, int J> __device__ __forceinline__ void zero(C<T> (&acc)[3][J][V]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[a][j][v] = mk<T>(T(0), T(0));
+}
+
+// Grid currents (Eq. Projection): Q_g[d][n] = sum_T sum_k W(n,T)[d][k] c_T[k]
+// for a slab of 32 V J right-hand sides.  A block of 8 warps takes 8
+// consecutive nodes, one per warp (lanes over right-hand sides); the block's
+// results go through shared memory so that each of the 3 x slab grids gets an
+// 8-node run per block.  Grid layout [3][R][Ng].
+constexpr int kProjNodes = 8;
+template <typename T, int V, int J> __host__ __device__ constexpr int proj_rows() { return 3 * 32 * V * J + 2; }
+template <typename T, int V, int J> constexpr size_t proj_smem() {
+    return size_t(kProjNodes) * proj_rows<T, V, J>() * sizeof(C<T>);
+}
+
+template <typename T, int V, int J>
+__global__ void __launch_bounds__(256) k_project(const int64_t *__restrict__ ptr, const Rec<T> *__restrict__ rec,
+                                                 const C<T> *__restrict__ cT, int64_t Ng, int32_t R,
+                                                 C<T> *__restrict__ grid) {
+    constexpr int SLAB = 32 * V * J;
+    // row stride 3 SLAB + 2 (= 2 mod 16 complex): the 8-node reads below hit distinct banks
+    constexpr int ROWS = proj_rows<T, V, J>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T> *sm = reinterpret_cast<C<T> *>(smem_raw);   // [kProjNodes][ROWS]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n0 = int64_t(blockIdx.x) * kProjNodes, n = n0 + w;
+    const int32_t rbase = int32_t(blockIdx.y) * SLAB;
+    const int32_t rl = rbase + V * lane;
+    C<T> acc[3][J][V];
+    zero<T, V, J>(acc);
+    if (n < Ng) {
+        if (rbase + SLAB <= R) gather_rows<T, V, J, true>(rec, ptr[n], ptr[n + 1], cT, R, rl, acc);
+        else gather_rows<T, V, J, false>(rec, ptr[n], ptr[n + 1], cT, R, rl, acc);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int j = 0; j < J; ++j) stv<T, V>(sm + w * ROWS + d * SLAB + V * lane + 32 * V * j, acc[d][j]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * SLAB * kProjNodes; i += blockDim.x) {
+        const int row = i / kProjNodes, nd = i % kProjNodes;
+        const int d = row / SLAB;
+        const int32_t r = rbase + row % SLAB;
+        const int64_t nn = n0 + nd;
+        if (r < R && nn < Ng) grid[(int64_t(d) * R + r) * Ng + nn] = sm[nd * ROWS + row];
+    }
+}
+
+// Grid potentials regrouped with the right-hand sides innermost:
+// phiT[n][b] = grid[b][n], b = d R + r, for the 32-node tiles that hold a
+// stencil node (no other node is interpolated from).
+template <typename T>
+__global__ void __launch_bounds__(256) k_regroup(const C<T> *__restrict__ grid, const int32_t *__restrict__ tiles,
+                                                 int64_t Ng, int32_t B, C<T> *__restrict__ phiT) {
+    __shared__ C<T> s[32][33];
+    const int64_t n0 = int64_t(tiles[blockIdx.x]) * 32;
+    const int32_t b0 = int32_t(blockIdx.y) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = ty; i < 32; i += 8) {
+        const int32_t b = b0 + i;
+        const int64_t n = n0 + tx;
+        if (b < B && n < Ng) s[i][tx] = grid[int64_t(b) * Ng + n];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t n = n0 + i;
+        const int32_t b = b0 + tx;
+        if (b < B && n < Ng) phiT[n * B + b] = s[tx][i];
+    }
+}
+
+// Per triangle T and right-hand side r:
+//   f_T[k] = sum_{T' near T} sum_l L_d(T,T')[k][l] c_T'[l]          (Eq. Lb, pre-corrected)
+//          + sum_n sum_d W(n,T)[d][k] phi_g[d][n]                   (interpolation, I = B^T)
+//   y_T[k] = Z_s sum_l G_T[k][l] c_T[l] + j c_L f_T[k]             (Eq. Zb, FP64)
+// One warp per (T, slab of 32 V J right-hand sides), lanes over right-hand
+// sides; each block record is read once per slab.  y_tri layout [R][nt][3].
+template <typename T, int V, int J>
+__global__ void __launch_bounds__(256)
+    k_tri_gather(const int64_t *__restrict__ near_ptr, const Rec<T> *__restrict__ near_rec,
+                 const int64_t *__restrict__ pt_ptr, const Rec<T> *__restrict__ pt_rec, const C<T> *__restrict__ cT,
+                 const C<T> *__restrict__ phiT, const double *__restrict__ gram, const int32_t *__restrict__ cond,
+                 const double *__restrict__ coef, int ncond, int64_t nt, int32_t R, int32_t nslab,
+                 double2 *__restrict__ y_tri) {
+    constexpr int SLAB = 32 * V * J;
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (gw >= nt * nchunk) return;
-    const int64_t t = gw / nchunk;
-    const int32_t r0 = int32_t(gw % nchunk) * 32 * RB + lane;
-    C<T> acc[3][RB];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int j = 0; j < RB; ++j) acc[k][j] = mk<T>(T(0), T(0));
-    const int64_t e1 = near_ptr[t + 1];
-#pragma unroll 2
-    for (int64_t e = near_ptr[t]; e < e1; ++e) {
-        const int64_t sidx = near_col[e];
-        const T *L = Ld + 9 * e;
-        const T l0 = L[0], l1 = L[1], l2 = L[2], l3 = L[3], l4 = L[4], l5 = L[5], l6 = L[6], l7 = L[7], l8 = L[8];
-        const C<T> *c = cT + sidx * 3 * R;
-#pragma unroll
-        for (int j = 0; j < RB; ++j) {
-            const int32_t r = r0 + 32 * j;
-            if (r < R) {
-                const C<T> c0 = c[r], c1 = c[R + r], c2 = c[2 * R + r];
-                acc[0][j].x += l0 * c0.x + l1 * c1.x + l2 * c2.x;
-                acc[0][j].y += l0 * c0.y + l1 * c1.y + l2 * c2.y;
-                acc[1][j].x += l3 * c0.x + l4 * c1.x + l5 * c2.x;
-                acc[1][j].y += l3 * c0.y + l4 * c1.y + l5 * c2.y;
-                acc[2][j].x += l6 * c0.x + l7 * c1.x + l8 * c2.x;
-                acc[2][j].y += l6 * c0.y + l7 * c1.y + l8 * c2.y;
-            }
-        }
+    if (gw >= nt * nslab) return;
+    const int64_t t = gw / nslab;
+    const int32_t rbase = int32_t(gw % nslab) * SLAB;
+    const int32_t rl = rbase + V * lane;
+    C<T> acc[3][J][V];
+    zero<T, V, J>(acc);
+    if (rbase + SLAB <= R) {
+        gather_rows<T, V, J, true>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
+        gather_rows<T, V, J, true>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
+    } else {
+        gather_rows<T, V, J, false>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
+        gather_rows<T, V, J, false>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
     }
+    double G[9];
 #pragma unroll
-    for (int j = 0; j < RB; ++j) {
-        const int32_t r = r0 + 32 * j;
-        if (r < R)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) ynear[(t * 3 + k) * R + r] = acc[k][j];
-    }
-}
-
-// J_q[c] = sum_k c_T[k] (w_q/2)(r_q - v_k)_c for every sample point.
-template <typename T>
-__global__ void k_point_currents(const C<T> *__restrict__ c_tri, const T *__restrict__ mom, int64_t nt, int Q,
-                                 int32_t nrhs, C<T> *__restrict__ jq) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t npt = nt * Q;
-    if (i >= npt * nrhs) return;
-    int64_t r = i / npt, pt = i % npt, t = pt / Q;
-    const C<T> *c = c_tri + (r * nt + t) * 3;
-    C<T> c0 = c[0], c1 = c[1], c2 = c[2];
-    const T *m = mom + 9 * pt;
-    for (int d = 0; d < 3; ++d) {
-        C<T> j = cscale(c0, m[d]);
-        j = cadd(j, cscale(c1, m[3 + d]));
-        j = cadd(j, cscale(c2, m[6 + d]));
-        jq[i * 3 + d] = j;
-    }
-}
-
-// Q_g[c][n] = sum over the points whose stencil holds node n of L_n(r_q) J_q[c].
-// One thread per (node, group of up to 4 right-hand sides): each gather-list
-// entry (point, weight) is read once for the group.
-template <typename T>
-__global__ void k_project(const C<T> *__restrict__ jq, int64_t npt, const int64_t *__restrict__ ptr,
-                          const int32_t *__restrict__ pt, const T *__restrict__ w, int64_t Ng, int32_t nrhs,
-                          C<T> *__restrict__ grid) {
-    constexpr int RG = 4;
-    const int32_t ngroups = (nrhs + RG - 1) / RG;
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= Ng * ngroups) return;
-    const int64_t g = i / Ng, n = i % Ng;
-    const int32_t r0 = int32_t(g) * RG;
-    const int nr = min(RG, nrhs - r0);
-    C<T> a[RG][3];
-#pragma unroll
-    for (int k = 0; k < RG; ++k) a[k][0] = a[k][1] = a[k][2] = mk<T>(0, 0);
-    const int64_t e1 = ptr[n + 1];
-    for (int64_t e = ptr[n]; e < e1; ++e) {
-        const int64_t p3 = int64_t(pt[e]) * 3;
-        const T we = w[e];
-#pragma unroll
-        for (int k = 0; k < RG; ++k) {
-            if (k < nr) {
-                const C<T> *j = jq + (int64_t(r0 + k) * npt) * 3 + p3;
-                a[k][0] = cadd(a[k][0], cscale(j[0], we));
-                a[k][1] = cadd(a[k][1], cscale(j[1], we));
-                a[k][2] = cadd(a[k][2], cscale(j[2], we));
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < RG; ++k) {
-        if (k < nr) {
-            C<T> *gr = grid + int64_t(r0 + k) * 3 * Ng;
-            gr[n] = a[k][0];
-            gr[Ng + n] = a[k][1];
-            gr[2 * Ng + n] = a[k][2];
-        }
-    }
-}
-
-// Phi_q[c] = sum_{n in S(q)} L_n(r_q) phi_g[c][n].
-template <typename T>
-__global__ void k_point_potentials(const C<T> *__restrict__ grid, const int32_t *__restrict__ start,
-                                   const T *__restrict__ lw, int O, int Ny, int Nz, int64_t Ng, int64_t npt,
-                                   int32_t nrhs, C<T> *__restrict__ phiq) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= npt * nrhs) return;
-    int64_t r = i / npt, pt = i % npt;
-    const int sx = start[3 * pt], sy = start[3 * pt + 1], sz = start[3 * pt + 2];
-    const T *wx = lw + (3 * pt) * O, *wy = wx + O, *wz = wy + O;
-    const C<T> *g = grid + r * 3 * Ng;
-    C<T> a[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
-    for (int ii = 0; ii < O; ++ii)
-        for (int jj = 0; jj < O; ++jj) {
-            T wxy = wx[ii] * wy[jj];
-            int64_t rowb = (int64_t(sx + ii) * Ny + (sy + jj)) * Nz + sz;
-            for (int kk = 0; kk < O; ++kk) {
-                T wgt = wxy * wz[kk];
-                for (int c = 0; c < 3; ++c) a[c] = cadd(a[c], cscale(g[c * Ng + rowb + kk], wgt));
-            }
-        }
-    for (int c = 0; c < 3; ++c) phiq[i * 3 + c] = a[c];
-}
-
-// Per triangle and right-hand side: far (interpolated), near (pre-corrected)
-// and Gram terms combined into y_T[k] (FP64).
-template <typename T>
-__global__ void k_tri_out(const C<T> *__restrict__ phiq, const T *__restrict__ mom, const C<T> *__restrict__ c_tri,
-                          const int64_t *__restrict__ near_ptr, const int32_t *__restrict__ near_col,
-                          const T *__restrict__ Ld, const C<T> *__restrict__ ynear, const double *__restrict__ gram,
-                          const int32_t *__restrict__ cond, const double *__restrict__ coef, int ncond, int64_t nt,
-                          int Q, int32_t nrhs, double2 *__restrict__ y_tri) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= nt * nrhs) return;
-    int64_t r = i / nt, t = i % nt;
-    // far: sum_q mom_q[k] . Phi_q
-    C<T> far[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
-    for (int q = 0; q < Q; ++q) {
-        const int64_t pt = t * Q + q;
-        const C<T> *ph = phiq + (r * nt * Q + pt) * 3;
-        C<T> p0 = ph[0], p1 = ph[1], p2 = ph[2];
-        const T *m = mom + 9 * pt;
-        for (int k = 0; k < 3; ++k) {
-            far[k] = cadd(far[k], cscale(p0, m[3 * k]));
-            far[k] = cadd(far[k], cscale(p1, m[3 * k + 1]));
-            far[k] = cadd(far[k], cscale(p2, m[3 * k + 2]));
-        }
-    }
-    // near: sum_T' L_d(T, T') c_T'
-    C<T> nr[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
-    const C<T> *cr = c_tri + r * nt * 3;
-    if (ynear) {
-        for (int k = 0; k < 3; ++k) nr[k] = ynear[(t * 3 + k) * nrhs + r];
-    } else for (int64_t e = near_ptr[t]; e < near_ptr[t + 1]; ++e) {
-        const C<T> *c = cr + int64_t(near_col[e]) * 3;
-        C<T> c0 = c[0], c1 = c[1], c2 = c[2];
-        const T *L = Ld + 9 * e;
-        for (int k = 0; k < 3; ++k) {
-            nr[k] = cadd(nr[k], cscale(c0, L[3 * k]));
-            nr[k] = cadd(nr[k], cscale(c1, L[3 * k + 1]));
-            nr[k] = cadd(nr[k], cscale(c2, L[3 * k + 2]));
-        }
-    }
-    const C<T> *ct = cr + t * 3;
-    const double *gm = gram + 9 * t;
-    const double *cf = coef + r * (2 * ncond + 1);
+    for (int i = 0; i < 9; ++i) G[i] = __ldg(gram + 9 * t + i);
     const int cd = cond[t];
-    const double zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * ncond];
-    for (int k = 0; k < 3; ++k) {
-        double gr = 0.0, gi = 0.0;
-        for (int l = 0; l < 3; ++l) { gr += gm[3 * k + l] * double(ct[l].x); gi += gm[3 * k + l] * double(ct[l].y); }
-        double fr = double(far[k].x) + double(nr[k].x), fi = double(far[k].y) + double(nr[k].y);
-        // Z_s * gram + j c_L * (far + near)
-        double yr = zr * gr - zi * gi - cl * fi;
-        double yi = zr * gi + zi * gr + cl * fr;
-        y_tri[i * 3 + k] = make_double2(yr, yi);
-    }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int32_t r = rl + 32 * V * j + v;
+            if (r >= R) continue;
+            const double *cf = coef + int64_t(r) * (2 * ncond + 1);
+            const double zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * ncond];
+            double2 c[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const C<T> u = cT[(t * 3 + l) * R + r];
+                c[l] = make_double2(double(u.x), double(u.y));
+            }
+            double2 *out = y_tri + (int64_t(r) * nt + t) * 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double gr = G[3 * k] * c[0].x + G[3 * k + 1] * c[1].x + G[3 * k + 2] * c[2].x;
+                const double gi = G[3 * k] * c[0].y + G[3 * k + 1] * c[1].y + G[3 * k + 2] * c[2].y;
+                const double fr = double(acc[k][j][v].x), fi = double(acc[k][j][v].y);
+                // Z_s * gram + j c_L * f
+                out[k] = make_double2(zr * gr - zi * gi - cl * fi, zr * gi + zi * gr + cl * fr);
+            }
+        }
 }
 
 // y_b = sum over the branch's two triangles of s * y_T[k].
@@ -396,24 +399,23 @@ namespace sie {
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     Scratch &s = p->scr;
     if (s.cap_rhs >= nrhs && s.prec == prec) return SIE_OK;
-    for (void *a : {s.tour, s.c_tri, s.jq, s.grid, s.spec, s.y_tri, s.y_br, (void *)s.coef, s.cT, s.ynear})
+    for (void *a : {s.tour, s.grid, s.spec, s.phiT, s.y_tri, s.y_br, (void *)s.coef, s.cT})
         if (a) cudaFree(a);
     s = Scratch{};
     const size_t cs = prec == SIE_PREC_FP64 ? sizeof(double2) : sizeof(float2);
     const int64_t R = std::max<int32_t>(nrhs, 1);
-    const size_t sizes[10] = {
+    constexpr int kBufs = 8;
+    const size_t sizes[kBufs] = {
         size_t(R) * 2 * p->nn * sizeof(double2),
-        size_t(R) * p->nt * 3 * cs,
-        size_t(R) * p->nt * p->Q * 3 * cs,
         size_t(R) * 3 * p->Ng * cs,
         size_t(R) * 3 * p->Nx * p->My * p->Mz * cs,
+        size_t(R) * 3 * p->Ng * cs,
         size_t(R) * p->nt * 3 * sizeof(double2),
         size_t(R) * (p->nb + p->np) * sizeof(double2),
         size_t(R) * (2 * p->ncond + 1) * sizeof(double),
-        size_t(R) * p->nt * 3 * cs,
         size_t(R) * p->nt * 3 * cs};
-    void **dst[10] = {&s.tour, &s.c_tri, &s.jq, &s.grid, &s.spec, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT, &s.ynear};
-    for (int i = 0; i < 10; ++i) {
+    void **dst[kBufs] = {&s.tour, &s.grid, &s.spec, &s.phiT, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT};
+    for (int i = 0; i < kBufs; ++i) {
         cudaError_t e = cudaMalloc(dst[i], std::max<size_t>(sizes[i], 16));
         if (e != cudaSuccess) {
             for (int j = 0; j < i; ++j) { cudaFree(*dst[j]); *dst[j] = nullptr; }
@@ -423,10 +425,50 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
         }
         s.bytes += sizes[i];
     }
-    s.phiq = s.jq;   // the point currents are consumed before the potentials are written
     s.cap_rhs = int32_t(R);
     s.prec = prec;
     return SIE_OK;
+}
+
+// Block-sparse stages for one slab shape: V complex per load, J loads per lane.
+template <typename T, int V, int J> struct Blocks {
+    static constexpr int SLAB = 32 * V * J;
+    static const Rec<T> *pn(const pfft_plan *p) {
+        if constexpr (sizeof(T) == 8) return p->d_pn_rec64; else return p->d_pn_rec32;
+    }
+    static const Rec<T> *pt(const pfft_plan *p) {
+        if constexpr (sizeof(T) == 8) return p->d_pt_rec64; else return p->d_pt_rec32;
+    }
+    static const Rec<T> *nr(const pfft_plan *p) {
+        if constexpr (sizeof(T) == 8) return p->d_near_rec64; else return p->d_near_rec32;
+    }
+    static int project(pfft_plan *p, int32_t R, cudaStream_t st) {
+        const dim3 grid(unsigned((p->Ng + kProjNodes - 1) / kProjNodes), unsigned((R + SLAB - 1) / SLAB));
+        k_project<T, V, J><<<grid, 32 * kProjNodes, proj_smem<T, V, J>(), st>>>(
+            p->d_pn_ptr, pn(p), (const C<T> *)p->scr.cT, p->Ng, R, (C<T> *)p->scr.grid);
+        SIE_LAUNCH_CHECK(p);
+        return SIE_OK;
+    }
+    static int tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
+        const int32_t nslab = (R + SLAB - 1) / SLAB;
+        const int64_t warps = p->nt * nslab;
+        k_tri_gather<T, V, J><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
+            p->d_near_ptr, nr(p), p->d_pt_ptr, pt(p), (const C<T> *)p->scr.cT, (const C<T> *)p->scr.phiT,
+            p->d_gram, p->d_cond, p->scr.coef, p->ncond, p->nt, R, nslab, (double2 *)p->scr.y_tri);
+        SIE_LAUNCH_CHECK(p);
+        return SIE_OK;
+    }
+};
+
+// FP64: one complex per load; FP32: two per 16-byte load when R is even (rows
+// of [.][3][R] then start on 16-byte boundaries), else one.
+template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) {
+    if constexpr (sizeof(T) == 8) return Blocks<double, 1, 2>::project(p, R, st);
+    else return R % 2 == 0 ? Blocks<float, 2, 2>::project(p, R, st) : Blocks<float, 1, 4>::project(p, R, st);
+}
+template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
+    if constexpr (sizeof(T) == 8) return Blocks<double, 1, 2>::tri_gather(p, R, st);
+    else return R % 2 == 0 ? Blocks<float, 2, 2>::tri_gather(p, R, st) : Blocks<float, 1, 4>::tri_gather(p, R, st);
 }
 
 template <typename T>
@@ -435,14 +477,7 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     const int64_t nslots = 2 * p->nn;
     const int64_t ldy = p->nb + p->np;
     double2 *tour = (double2 *)s.tour;
-    C<T> *c_tri = (C<T> *)s.c_tri, *jq = (C<T> *)s.jq, *grid = (C<T> *)s.grid, *spec = (C<T> *)s.spec;
     double2 *y_tri = (double2 *)s.y_tri, *y_br = (double2 *)s.y_br;
-    const T *mom, *lw, *pjw, *Ld;
-    if constexpr (sizeof(T) == 8) {
-        mom = (const T *)p->d_mom64; lw = (const T *)p->d_lw64; pjw = (const T *)p->d_pj_w64; Ld = (const T *)p->d_Ld64;
-    } else {
-        mom = (const T *)p->d_mom32; lw = (const T *)p->d_lw32; pjw = (const T *)p->d_pj_w32; Ld = (const T *)p->d_Ld32;
-    }
     std::unique_ptr<StageTimer> tm(new StageTimer(p, SIE_STAGE_LOOP_TO_BRANCH, st));
     if (space == SIE_SPACE_LOOP) {
         k_tour_inject<<<nblk(nslots * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tour_node, p->d_tour_enter,
@@ -453,36 +488,24 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     }
     k_alpha_tri<T><<<nblk(p->nt * 3 * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tb, p->d_ts, p->d_loop_of_branch,
                                                          p->d_twig_node, p->d_head, p->d_enter, p->d_exit, p->nt, R,
-                                                         space, p->nb, c_tri, (C<T> *)s.cT);
-    SIE_LAUNCH_CHECK(p);
-    const int64_t npt = p->nt * p->Q;
-    tm.reset(new StageTimer(p, SIE_STAGE_POINT_CURRENTS, st));
-    k_point_currents<T><<<nblk(npt * R), 256, 0, st>>>(c_tri, mom, p->nt, p->Q, R, jq);
+                                                         space, p->nb, (C<T> *)s.cT);
     SIE_LAUNCH_CHECK(p);
     tm.reset(new StageTimer(p, SIE_STAGE_PROJECT, st));
-    k_project<T><<<nblk(p->Ng * ((R + 3) / 4)), 256, 0, st>>>(jq, npt, p->d_pj_ptr, p->d_pj_pt, pjw, p->Ng, R, grid);
-    SIE_LAUNCH_CHECK(p);
-    tm.reset();
-    int rc = fft_conv(p, grid, spec, R, sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED, st);
+    int rc = run_project<T>(p, R, st);
     if (rc) return rc;
-    C<T> *phiq = (C<T> *)s.phiq;
+    tm.reset();
+    rc = fft_conv(p, s.grid, s.spec, R, sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED, st);
+    if (rc) return rc;
     tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
-    k_point_potentials<T><<<nblk(npt * R), 256, 0, st>>>(grid, p->d_start, lw, p->O, p->Ny, p->Nz, p->Ng, npt, R, phiq);
-    SIE_LAUNCH_CHECK(p);
-    C<T> *ynear = nullptr;
-    if (R >= 16) {   // batched right-hand sides: near field as a block-sparse x dense product
-        tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
-        ynear = (C<T> *)s.ynear;
-        const int32_t nchunk = (R + 127) / 128;
-        const int64_t warps = p->nt * nchunk;
-        k_near_spmm<T, 4><<<nblk(warps * 32, 256), 256, 0, st>>>(p->d_near_ptr, p->d_near_col, Ld, (const C<T> *)s.cT,
-                                                                p->nt, R, nchunk, ynear);
+    {
+        const int32_t B = 3 * R;
+        const dim3 grid(unsigned(p->n_tiles), unsigned((B + 31) / 32));
+        k_regroup<T><<<grid, 256, 0, st>>>((const C<T> *)s.grid, p->d_tiles, p->Ng, B, (C<T> *)s.phiT);
         SIE_LAUNCH_CHECK(p);
-        tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
     }
-    k_tri_out<T><<<nblk(p->nt * R, 128), 128, 0, st>>>(phiq, mom, c_tri, p->d_near_ptr, p->d_near_col, Ld, ynear,
-                                                   p->d_gram, p->d_cond, s.coef, p->ncond, p->nt, p->Q, R, y_tri);
-    SIE_LAUNCH_CHECK(p);
+    tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
+    rc = run_tri_gather<T>(p, R, st);
+    if (rc) return rc;
     tm.reset(new StageTimer(p, SIE_STAGE_BRANCH_TO_LOOP, st));
     if (space == SIE_SPACE_BRANCH) {
         k_branch_out<<<nblk(p->nb * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, p->nb, R, y);

@@ -354,9 +354,21 @@ __global__ void k_branch_diag(const int64_t *ptr, const int32_t *col, const doub
     diagL[e] = acc;
 }
 
-__global__ void k_to_f32(const double *a, float *b, int64_t n) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = float(a[i]);
+// Near blocks and their columns as packed records, FP64 and rounded to FP32.
+__global__ void k_pack_near(const int32_t *__restrict__ col, const double *__restrict__ Ld, int64_t n,
+                            Rec<double> *__restrict__ r64, Rec<float> *__restrict__ r32) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    Rec<double> a{};
+    Rec<float> b{};
+    for (int i = 0; i < 9; ++i) {
+        a.b[i] = Ld[9 * e + i];
+        b.b[i] = float(a.b[i]);
+    }
+    a.col = col[e];
+    b.col = col[e];
+    r64[e] = a;
+    r32[e] = b;
 }
 
 int set_smem(const void *fn, size_t bytes) {
@@ -537,31 +549,90 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
             }
         }
     }
-    // ---- projection gather lists: node -> (point, weight), points ascending
-    std::vector<int64_t> pj_ptr(p->Ng + 1, 0);
+    // ---- projection blocks (Sec. IV-B step 1 with the point currents folded in):
+    // W(n, T)[d][k] = sum over T's points q whose stencil holds n of
+    // L_n(r_q) (w_q/2)(r_q - v_k)_d, so that the grid current at node n is
+    // Q_g[d][n] = sum_T sum_k W(n, T)[d][k] c_T[k], and the interpolated
+    // far-field potential of triangle T is sum_n sum_d W(n, T)[d][k] phi_g[d][n].
     const int O3 = O * O * O;
-    for (int64_t pt = 0; pt < npt; ++pt)
-        for (int i = 0; i < O; ++i)
-            for (int j = 0; j < O; ++j)
-                for (int k = 0; k < O; ++k) {
-                    int64_t node = (int64_t(start[3 * pt] + i) * p->Ny + (start[3 * pt + 1] + j)) * p->Nz + (start[3 * pt + 2] + k);
-                    pj_ptr[node + 1]++;
-                }
-    for (int64_t i = 0; i < p->Ng; ++i) pj_ptr[i + 1] += pj_ptr[i];
-    std::vector<int32_t> pj_pt(npt * O3);
-    std::vector<double> pj_w(npt * O3);
+    std::vector<int64_t> pt_ptr(nt + 1, 0);
+    std::vector<int32_t> pt_node;
+    std::vector<double> pt_W;   // [pair][3][3] as W[d][k]
+    pt_node.reserve(size_t(nt) * 64);
+    pt_W.reserve(size_t(nt) * 64 * 9);
     {
-        std::vector<int64_t> fill(pj_ptr.begin(), pj_ptr.end() - 1);
-        for (int64_t pt = 0; pt < npt; ++pt)
-            for (int i = 0; i < O; ++i)
-                for (int j = 0; j < O; ++j)
-                    for (int k = 0; k < O; ++k) {
-                        int64_t node = (int64_t(start[3 * pt] + i) * p->Ny + (start[3 * pt + 1] + j)) * p->Nz + (start[3 * pt + 2] + k);
-                        int64_t at = fill[node]++;
-                        pj_pt[at] = int32_t(pt);
-                        pj_w[at] = (lw[(3 * pt) * O + i] * lw[(3 * pt + 1) * O + j]) * lw[(3 * pt + 2) * O + k];
-                    }
+        struct Item { int64_t node; int q; double w; };
+        std::vector<Item> items(size_t(Q) * O3);
+        for (int64_t t = 0; t < nt; ++t) {
+            size_t at = 0;
+            for (int q = 0; q < Q; ++q) {
+                const int64_t pt = t * Q + q;
+                for (int i = 0; i < O; ++i)
+                    for (int j = 0; j < O; ++j)
+                        for (int k = 0; k < O; ++k) {
+                            const int64_t node = (int64_t(start[3 * pt] + i) * p->Ny + (start[3 * pt + 1] + j)) * p->Nz +
+                                                 (start[3 * pt + 2] + k);
+                            const double w = (lw[(3 * pt) * O + i] * lw[(3 * pt + 1) * O + j]) * lw[(3 * pt + 2) * O + k];
+                            items[at++] = Item{node, q, w};
+                        }
+            }
+            // nodes ascending; per node the points in ascending order
+            std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.node < b.node; });
+            for (size_t a = 0; a < items.size();) {
+                size_t b = a;
+                double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                for (; b < items.size() && items[b].node == items[a].node; ++b) {
+                    const double *mq = &mom[9 * (t * Q + items[b].q)];   // [k][d]
+                    for (int d = 0; d < 3; ++d)
+                        for (int k = 0; k < 3; ++k) W[3 * d + k] += items[b].w * mq[3 * k + d];
+                }
+                pt_node.push_back(int32_t(items[a].node));
+                pt_W.insert(pt_W.end(), W, W + 9);
+                a = b;
+            }
+            pt_ptr[t + 1] = int64_t(pt_node.size());
+        }
     }
+    const int64_t n_pair = int64_t(pt_node.size());
+    p->n_pair = n_pair;
+    // the same blocks by node (triangles ascending), and the 32-node tiles in use
+    std::vector<int64_t> pn_ptr(p->Ng + 1, 0);
+    for (int64_t e = 0; e < n_pair; ++e) pn_ptr[pt_node[e] + 1]++;
+    for (int64_t i = 0; i < p->Ng; ++i) pn_ptr[i + 1] += pn_ptr[i];
+    std::vector<Rec<double>> pn_rec64(n_pair), pt_rec64(n_pair);
+    std::vector<Rec<float>> pn_rec32(n_pair), pt_rec32(n_pair);
+    {
+        std::vector<int64_t> fill(pn_ptr.begin(), pn_ptr.end() - 1);
+        for (int64_t t = 0; t < nt; ++t)
+            for (int64_t e = pt_ptr[t]; e < pt_ptr[t + 1]; ++e) {
+                const double *W = &pt_W[9 * e];
+                Rec<double> &a = pn_rec64[fill[pt_node[e]]++];
+                Rec<double> &b = pt_rec64[e];
+                a = Rec<double>{};
+                b = Rec<double>{};
+                for (int d = 0; d < 3; ++d)
+                    for (int k = 0; k < 3; ++k) {
+                        a.b[3 * d + k] = W[3 * d + k];   // out d, in k: grid current from c_T
+                        b.b[3 * k + d] = W[3 * d + k];   // out k, in d: triangle potential from phi_g
+                    }
+                a.col = t;
+                b.col = pt_node[e];
+            }
+        for (int64_t e = 0; e < n_pair; ++e) {
+            pn_rec32[e] = Rec<float>{};
+            pt_rec32[e] = Rec<float>{};
+            for (int i = 0; i < 9; ++i) {
+                pn_rec32[e].b[i] = float(pn_rec64[e].b[i]);
+                pt_rec32[e].b[i] = float(pt_rec64[e].b[i]);
+            }
+            pn_rec32[e].col = int32_t(pn_rec64[e].col);
+            pt_rec32[e].col = int32_t(pt_rec64[e].col);
+        }
+    }
+    std::vector<int32_t> tiles;
+    for (int64_t tl = 0; tl * 32 < p->Ng; ++tl)
+        if (pn_ptr[std::min<int64_t>(p->Ng, tl * 32 + 32)] > pn_ptr[tl * 32]) tiles.push_back(int32_t(tl));
+    p->n_tiles = int64_t(tiles.size());
     // ---- near list (exact criterion per pair; a cell list only prunes candidates)
     std::vector<int32_t> bmin(3 * nt), bmax(3 * nt);
     for (int64_t t = 0; t < nt; ++t)
@@ -662,10 +733,13 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     UP(p->d_start, start);
     UP(p->d_lw64, lw);
     UP(p->d_lw32, to_f32(lw));
-    UP(p->d_pj_ptr, pj_ptr);
-    UP(p->d_pj_pt, pj_pt);
-    UP(p->d_pj_w64, pj_w);
-    UP(p->d_pj_w32, to_f32(pj_w));
+    UP(p->d_pn_ptr, pn_ptr);
+    UP(p->d_pn_rec64, pn_rec64);
+    UP(p->d_pn_rec32, pn_rec32);
+    UP(p->d_pt_ptr, pt_ptr);
+    UP(p->d_pt_rec64, pt_rec64);
+    UP(p->d_pt_rec32, pt_rec32);
+    UP(p->d_tiles, tiles);
     UP(p->d_near_ptr, near_ptr);
     UP(p->d_near_col, near_col);
     {
@@ -783,7 +857,8 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     // ---- near-field blocks
     if ((rcode = plan_alloc(p, (void **)&p->d_Ldir64, p->n_near * 9 * sizeof(double)))) return bail(rcode);
     if ((rcode = plan_alloc(p, (void **)&p->d_Ld64, p->n_near * 9 * sizeof(double)))) return bail(rcode);
-    if ((rcode = plan_alloc(p, (void **)&p->d_Ld32, p->n_near * 9 * sizeof(float)))) return bail(rcode);
+    if ((rcode = plan_alloc(p, (void **)&p->d_near_rec64, p->n_near * sizeof(Rec<double>)))) return bail(rcode);
+    if ((rcode = plan_alloc(p, (void **)&p->d_near_rec32, p->n_near * sizeof(Rec<float>)))) return bail(rcode);
     {
         NearArgs a{p->d_near_ptr, p->d_near_col, nt, d_verts, d_area, d_tri, d_r7b, d_r7w, d_tgb, d_tgw,
                    int(tgw.size()), p->d_start, p->d_lw64, p->d_mom64, d_Hpad, int(Q), O, p->Mx, p->My, p->Mz,
@@ -792,7 +867,8 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         p->launches++;
     }
     SIE_CUDA(cudaGetLastError());
-    k_to_f32<<<(9 * p->n_near + 255) / 256, 256, 0, s>>>(p->d_Ld64, p->d_Ld32, 9 * p->n_near);
+    k_pack_near<<<(p->n_near + 255) / 256, 256, 0, s>>>(p->d_near_col, p->d_Ld64, p->n_near, p->d_near_rec64,
+                                                         p->d_near_rec32);
     p->launches++;
     if ((rcode = plan_alloc(p, (void **)&p->d_diag_L, L->nb * sizeof(double)))) return bail(rcode);
     k_branch_diag<<<(L->nb + 255) / 256, 256, 0, s>>>(p->d_near_ptr, p->d_near_col, p->d_Ldir64, p->d_br_tri,
@@ -812,9 +888,8 @@ extern "C" void pfft_plan_destroy(pfft_plan *p) {
     sie::plan_free_precond(p);
     for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void *a : p->allocations) cudaFree(a);
-    // scr.phiq aliases scr.jq and is not freed separately
-    for (void *a : {p->scr.tour, p->scr.c_tri, p->scr.jq, p->scr.grid, p->scr.spec, p->scr.y_tri, p->scr.y_br,
-                    (void *)p->scr.coef, p->scr.cT, p->scr.ynear})
+    for (void *a : {p->scr.tour, p->scr.grid, p->scr.spec, p->scr.phiT, p->scr.y_tri, p->scr.y_br,
+                    (void *)p->scr.coef, p->scr.cT})
         if (a) cudaFree(a);
     delete p;
 }
@@ -843,6 +918,25 @@ extern "C" int pfft_plan_export(const pfft_plan *p, int32_t what, void *host_out
         case SIE_EXPORT_LDIRECT: src = p->d_Ldir64; bytes = p->n_near * 72; break;
         case SIE_EXPORT_HHAT: src = p->d_H64; bytes = int64_t(p->Nx + 1) * (p->Ny + 1) * (p->Nz + 1) * 8; break;
         case SIE_EXPORT_START: src = p->d_start; bytes = p->nt * p->Q * 3 * 4; break;
+        case SIE_EXPORT_PROJ_PTR: src = p->d_pt_ptr; bytes = (p->nt + 1) * 8; break;
+        case SIE_EXPORT_PROJ_NODE:
+        case SIE_EXPORT_PROJ_W: {
+            // unpacked from the per-triangle records {b[3k + d] = W[d][k], col = n}
+            bytes = p->n_pair * (what == SIE_EXPORT_PROJ_NODE ? 4 : 72);
+            if (capacity_bytes < bytes) return fail(SIE_ERR_ARG, "pfft_plan_export: buffer too small");
+            std::vector<Rec<double>> rec(size_t(p->n_pair));
+            SIE_CUDA(cudaMemcpy(rec.data(), p->d_pt_rec64, rec.size() * sizeof(Rec<double>), cudaMemcpyDeviceToHost));
+            for (int64_t e = 0; e < p->n_pair; ++e) {
+                if (what == SIE_EXPORT_PROJ_NODE) {
+                    static_cast<int32_t *>(host_out)[e] = int32_t(rec[e].col);
+                } else {
+                    double *W = static_cast<double *>(host_out) + 9 * e;
+                    for (int d = 0; d < 3; ++d)
+                        for (int k = 0; k < 3; ++k) W[3 * d + k] = rec[e].b[3 * k + d];
+                }
+            }
+            return SIE_OK;
+        }
         default: return fail(SIE_ERR_ARG, "pfft_plan_export: unknown array");
     }
     if (capacity_bytes < bytes) return fail(SIE_ERR_ARG, "pfft_plan_export: buffer too small");

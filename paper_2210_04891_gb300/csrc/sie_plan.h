@@ -21,16 +21,13 @@ struct Scratch {
     int32_t cap_rhs = 0;   // right-hand sides the buffers are sized for
     int prec = -1;
     void *tour = nullptr;      // complex128 [R][2 n_nodes]
-    void *c_tri = nullptr;     // complex T [R][nt][3]
-    void *jq = nullptr;        // complex T [R][nt*Q][3]
-    void *grid = nullptr;      // complex T [R][3][Ng]
-    void *spec = nullptr;      // complex T [R][3][Nx][My][Mz]
-    void *phiq = nullptr;      // complex T [R][nt*Q][3]
+    void *grid = nullptr;      // complex T [3][R][Ng]   grid currents, then grid potentials
+    void *spec = nullptr;      // complex T [3R][Nx][My][Mz]
+    void *phiT = nullptr;      // complex T [Ng][3][R]   grid potentials, right-hand sides innermost
     void *y_tri = nullptr;     // complex128 [R][nt][3]
     void *y_br = nullptr;      // complex128 [R][nb + np]
     double *coef = nullptr;    // per RHS: Z_s per conductor (re, im), c_L (im) -> [R][2 ncond + 1]
     void *cT = nullptr;        // complex T [nt][3][R]  local currents, right-hand sides innermost
-    void *ynear = nullptr;     // complex T [nt][3][R]  near-field product
     size_t bytes = 0;
 };
 
@@ -60,18 +57,26 @@ struct pfft_plan {
     int32_t *d_start = nullptr;         // [nt*Q][3] stencil start nodes
     double *d_lw64 = nullptr;           // [nt*Q][3][O] Lagrange weights
     float *d_lw32 = nullptr;
-    // projection gather: node -> (point, weight)
-    int64_t *d_pj_ptr = nullptr;        // [Ng + 1]
-    int32_t *d_pj_pt = nullptr;         // [nnz]
-    double *d_pj_w64 = nullptr;
-    float *d_pj_w32 = nullptr;
+    // projection blocks, one per (grid node n, triangle T) pair:
+    //   W(n, T)[d][k] = sum_q L_n(r_q) (w_q/2)(r_q - v_k)_d
+    // stored twice as packed records (sie_common.cuh, Rec<T>)
+    int64_t n_pair = 0;
+    int64_t *d_pn_ptr = nullptr;        // [Ng + 1]  rows = nodes, triangles ascending
+    sie::Rec<double> *d_pn_rec64 = nullptr;  //   b[3d + k] = W[d][k], col = T
+    sie::Rec<float> *d_pn_rec32 = nullptr;
+    int64_t *d_pt_ptr = nullptr;        // [nt + 1]  rows = triangles, nodes ascending
+    sie::Rec<double> *d_pt_rec64 = nullptr;  //   b[3k + d] = W[d][k], col = n
+    sie::Rec<float> *d_pt_rec32 = nullptr;
+    int64_t n_tiles = 0;                // 32-node tiles that hold at least one stencil node
+    int32_t *d_tiles = nullptr;         // [n_tiles] tile index n / 32, ascending
     // near field CSR over triangles (row T: near T', ascending), 3x3 blocks
     int64_t n_near = 0;
     int64_t *d_near_ptr = nullptr;
     int32_t *d_near_col = nullptr;
     double *d_Ld64 = nullptr;           // [n_near][3][3]  L_direct - L_grid
-    float *d_Ld32 = nullptr;
     double *d_Ldir64 = nullptr;         // [n_near][3][3]  L_direct (kept for diag and checks)
+    sie::Rec<double> *d_near_rec64 = nullptr;   // [n_near] {b = L_d block [k][l], col = T'}
+    sie::Rec<float> *d_near_rec32 = nullptr;
     // kernel spectrum, folded [My/2+1][Mz/2+1][Mx/2+1], scaled by 1/(Mx My Mz)
     double *d_H64 = nullptr;
     float *d_H32 = nullptr;

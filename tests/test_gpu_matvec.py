@@ -71,6 +71,43 @@ def test_setup_arrays_match_oracle(wires):
     assert np.abs(P.export(N.EXPORT_HHAT) - ref).max() < 1e-13 * np.abs(ref).max()
 
 
+def test_projection_blocks_rebuild_oracle_B(wires):
+    """The per-(node, triangle) projection blocks, scattered to branches with
+    the triangles' edge signs, reproduce the oracle's projection matrix B
+    (Eq. Projection) to FP64 rounding; each (node, triangle) pair appears once,
+    nodes ascending per triangle."""
+    import scipy.sparse as sp
+    from paper_2210_04891_gb300 import native as N
+    m, O, S, P = wires
+    op = S.op
+    ptr = P.export(N.EXPORT_PROJ_PTR)
+    node = P.export(N.EXPORT_PROJ_NODE)
+    W = P.export(N.EXPORT_PROJ_W)
+    assert ptr[0] == 0 and ptr[-1] == node.size == W.shape[0]
+    tri = np.repeat(np.arange(m.nt), np.diff(ptr))
+    for t in range(m.nt):
+        row = node[ptr[t]:ptr[t + 1]]
+        assert np.all(np.diff(row) > 0)
+        # exactly the union of the triangle's 7 stencils
+        s = op.start[t]
+        want = set()
+        for q in range(s.shape[0]):
+            for i in range(op.p.order):
+                for j in range(op.p.order):
+                    for k in range(op.p.order):
+                        want.add(((s[q, 0] + i) * op.N[1] + s[q, 1] + j) * op.N[2] + s[q, 2] + k)
+        assert set(row.tolist()) == want
+    rows, cols, vals = [], [], []
+    for kk in range(3):
+        ok = op.tb[tri, kk] >= 0
+        for d in range(3):
+            rows.append(d * op.ng + node[ok])
+            cols.append(op.tb[tri, kk][ok])
+            vals.append(op.ts[tri, kk][ok] * W[ok, d, kk])
+    B = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=op.B.shape)
+    assert abs(B - op.B).max() < 1e-14 * abs(op.B).max()
+
+
 @pytest.mark.parametrize("nbatch", [1, 3, 4])
 def test_convolve_matches_oracle(wires, nbatch):
     from paper_2210_04891_gb300 import native as N
