@@ -209,8 +209,8 @@ int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *
  * they convolve: fixed start-up memory budgets, real-time loops that cannot
  * take cudaMalloc's synchronisation and latency, frameworks that own the
  * allocator).  Same arguments and result as pfft_convolve.  Its scratch is one
- * file-scope device array of 8 MiB that every GPU loading the library holds
- * until exit; a grid whose zero-padded spectrum (N_x * 2N_y * 2N_z complex
+ * file-scope device array of 4 MiB that every GPU loading the library holds
+ * until exit; a grid whose copy zero-padded along x (2N_x * N_y * N_z complex
  * values of the precision) exceeds it is rejected with SIE_ERR_ARG.  Larger
  * batches are processed in pieces that fit.  The first call on a device looks
  * up the array's device address once (cudaGetSymbolAddress, with that device
@@ -228,14 +228,16 @@ int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec
  *   LOOP_TO_BRANCH  loop currents -> local edge currents c_T (A^T, Euler-tour scan)
  *   POINT_CURRENTS  not launched: the point currents are folded into the projection blocks
  *   PROJECT         grid currents Q_g = sum_T W(n, T) c_T (Sec. IV-B step 1)
- *   FFT_*           phi_g = H Q_g (step 2): forward y/z planes, x pencils with the
- *                   kernel product, inverse y/z planes
+ *   FFT_X_FWD       phi_g = H Q_g (step 2): x pencils forward (zero-padded along x)
+ *   FFT_YZ          per x-frequency plane: zero-padded y/z transform, kernel product,
+ *                   inverse y/z transform, crop
+ *   FFT_X_INV       x pencils inverse, crop
  *   INTERP          grid potentials regrouped with the right-hand sides innermost
  *   NEAR            per triangle: pre-corrected near blocks (step 4) + interpolation
  *                   (step 3) + Z_s Gram term, one fused gather
  *   BRANCH_TO_LOOP  triangle outputs -> branch voltages -> loop voltages (A) */
 enum { SIE_STAGE_LOOP_TO_BRANCH = 0, SIE_STAGE_POINT_CURRENTS = 1, SIE_STAGE_PROJECT = 2,
-       SIE_STAGE_FFT_PLANE_FWD = 3, SIE_STAGE_FFT_PENCIL = 4, SIE_STAGE_FFT_PLANE_INV = 5,
+       SIE_STAGE_FFT_X_FWD = 3, SIE_STAGE_FFT_YZ = 4, SIE_STAGE_FFT_X_INV = 5,
        SIE_STAGE_INTERP = 6, SIE_STAGE_NEAR = 7, SIE_STAGE_BRANCH_TO_LOOP = 8,
        SIE_STAGE_PRECOND_APPLY = 9, SIE_STAGE_PRECOND_FACTOR = 10, SIE_STAGE_ARNOLDI = 11,
        SIE_NSTAGES = 12 };

@@ -317,19 +317,26 @@ inline void split4(int M, int &N1, int &N2) {
 // creation): tf[j2 * N1 + k1] = W_M^(j2 k1) for the forward pass 1 and
 // ti[k1 * N2 + p2] = W_M^(k1 p2) for the inverse pass A (used conjugated).
 
+// ---- x pencils.  Buffers [batch][rows][ncols], row x at x * ncols; one CTA
+// per (batch, 16 consecutive columns), 16 * max(N1, N2) threads, a shared
+// line per column (pitch M + 1).
+
+// Forward: in [batch][M/2][ncols] (zero-padded to M) -> out [batch][M][ncols].
 template <typename T, int N1, int N2>
-__device__ __forceinline__ void x4_body(C<T> *S, C<T> *base, int ncols, int64_t hrow_off,
-                                        const C<T> *__restrict__ tf, const C<T> *__restrict__ ti,
-                                        const T *__restrict__ Hx) {
-    // input x < M/2 (the rest is zero padding); output kept for x < M/2
+__global__ void __launch_bounds__(256) k_fft_xf(const C<T> *__restrict__ in, C<T> *__restrict__ out, int ncols,
+                                                const C<T> *__restrict__ tf) {
     constexpr int KT = 16, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T> *S = reinterpret_cast<C<T> *>(smem_raw);
+    const int tiles = ncols / KT;
+    const int b = blockIdx.x / tiles, c0 = (blockIdx.x % tiles) * KT;
     const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> 4;
     C<T> *Sl = S + line * pitch;
     const int64_t stride = int64_t(N2) * ncols;
     C<T> v[FFT_NMAX];
-    if (q < N2) {                      // pass 1: j2 = q, DFT over j1
+    if (q < N2) {                      // pass 1: j2 = q, DFT over j1 (x = j2 + N2 j1 < M/2)
         const int j2 = q;
-        const C<T> *src = base + int64_t(j2) * ncols + line;
+        const C<T> *src = in + int64_t(b) * (M / 2) * ncols + c0 + line + int64_t(j2) * ncols;
 #pragma unroll
         for (int j1 = 0; j1 < N1; ++j1) v[j1] = j1 < H1 ? src[j1 * stride] : mk<T>(T(0), T(0));
         dft_reg<T, N1, false>(v);
@@ -338,64 +345,60 @@ __device__ __forceinline__ void x4_body(C<T> *S, C<T> *base, int ncols, int64_t 
         for (int k1 = 0; k1 < N1; ++k1) Sl[k1 * N2 + j2] = k1 ? cmul(v[k1], t[k1]) : v[0];
     }
     __syncthreads();
-    if (q < N1) {                      // pass 2: k1 = q, DFT over j2, times H, inverse DFT over k2
+    if (q < N1) {                      // pass 2: k1 = q, DFT over j2 -> X[k1 + N1 k2]
         const int k1 = q;
 #pragma unroll
         for (int j2 = 0; j2 < N2; ++j2) v[j2] = Sl[k1 * N2 + j2];
         dft_reg<T, N2, false>(v);
-        const T *h = Hx + hrow_off + k1;
+        C<T> *dst = out + int64_t(b) * M * ncols + c0 + line + int64_t(k1) * ncols;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], h[N1 * k2]);
-        dft_reg<T, N2, true>(v);
-        const C<T> *t = ti + k1 * N2;
-#pragma unroll
-        for (int p2 = 1; p2 < N2; ++p2) {
-            const C<T> w = t[p2];
-            C<T> r;
-            r.x = v[p2].x * w.x + v[p2].y * w.y;   // times conj(w)
-            r.y = v[p2].y * w.x - v[p2].x * w.y;
-            v[p2] = r;
-        }
-    }
-    __syncthreads();                   // pass-2 reads complete before pass-A writes
-    if (q < N1) {
-#pragma unroll
-        for (int p2 = 0; p2 < N2; ++p2) Sl[p2 * N1 + q] = v[p2];
-    }
-    __syncthreads();
-    if (q < N2) {                      // inverse pass B: p2 = q, DFT over k1, keep x < M/2
-        const int p2 = q;
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) v[k1] = Sl[p2 * N1 + k1];
-        dft_reg<T, N1, true>(v);
-        C<T> *dst = base + int64_t(p2) * ncols + line;
-#pragma unroll
-        for (int p1 = 0; p1 < H1; ++p1) dst[p1 * stride] = v[p1];
+        for (int k2 = 0; k2 < N2; ++k2) dst[N1 * k2 * int64_t(ncols)] = v[k2];
     }
 }
 
-// x-pencils, four-step: forward FFT, times H, inverse FFT (the middle pass of
-// the 3-D convolution).  Buffer [batch][N_x][ncols] (x < N_x = M/2 stored);
-// one CTA per (batch, 16 columns); 16 * max(N1, N2) threads.  Hx: kernel
-// spectrum unfolded along x, [fold(ky)][fold(kz)][kx].  One kernel instance
-// per length (dispatched on the host).
+// Inverse: in [batch][M][ncols] -> out [batch][M/2][ncols] (rows x < M/2 kept).
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(256) k_fft_x4(C<T> *__restrict__ buf, int64_t batch_stride, int ncols,
-                                                int lgMz, int My, int Mz, const C<T> *__restrict__ tf,
-                                                const C<T> *__restrict__ ti, const T *__restrict__ Hx) {
-    constexpr int KT = 16, Mx = N1 * N2;
+__global__ void __launch_bounds__(256) k_fft_xi(const C<T> *__restrict__ in, C<T> *__restrict__ out, int ncols,
+                                                const C<T> *__restrict__ ti) {
+    constexpr int KT = 16, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T> *S = reinterpret_cast<C<T> *>(smem_raw);
     const int tiles = ncols / KT;
     const int b = blockIdx.x / tiles, c0 = (blockIdx.x % tiles) * KT;
-    C<T> *base = buf + b * batch_stride + c0;
-    const int col = c0 + (threadIdx.x & (KT - 1));
-    const int ky = col >> lgMz, kz = col & (Mz - 1);
-    const int64_t hrow = (int64_t(fold_index(ky, My)) * (Mz / 2 + 1) + fold_index(kz, Mz)) * Mx;
-    x4_body<T, N1, N2>(S, base, ncols, hrow, tf, ti, Hx);
+    const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> 4;
+    C<T> *Sl = S + line * pitch;
+    C<T> v[FFT_NMAX];
+    if (q < N1) {                      // pass A: k1 = q, inverse DFT over k2, conj twiddle
+        const int k1 = q;
+        const C<T> *src = in + int64_t(b) * M * ncols + c0 + line + int64_t(k1) * ncols;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[N1 * k2 * int64_t(ncols)];
+        dft_reg<T, N2, true>(v);
+        const C<T> *t = ti + k1 * N2;
+#pragma unroll
+        for (int p2 = 0; p2 < N2; ++p2) {
+            C<T> r = v[p2];
+            if (p2) {
+                const C<T> w = t[p2];
+                r.x = v[p2].x * w.x + v[p2].y * w.y;
+                r.y = v[p2].y * w.x - v[p2].x * w.y;
+            }
+            Sl[p2 * N1 + k1] = r;
+        }
+    }
+    __syncthreads();
+    if (q < N2) {                      // pass B: p2 = q, inverse DFT over k1, x = p2 + N2 p1 < M/2
+        const int p2 = q;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = Sl[p2 * N1 + k1];
+        dft_reg<T, N1, true>(v);
+        C<T> *dst = out + int64_t(b) * (M / 2) * ncols + c0 + line + int64_t(p2) * ncols;
+#pragma unroll
+        for (int p1 = 0; p1 < H1; ++p1) dst[p1 * int64_t(N2) * ncols] = v[p1];
+    }
 }
 
-// ---- (y, z) plane passes with compile-time split (see k_fft_yz4).  The
+// ---- (y, z) plane passes with compile-time split (see k_fft_yzc).  The
 // input extent is half of each padded length (Ny = My/2, Nz = Mz/2).
 template <typename T, int N1, int N2>   // F1: z pass 1, rows y < Ny, global -> P row slots
 __device__ __forceinline__ void yz_f1(const C<T> *in, C<T> *P, int pitch, int Ny, const C<T> *tfz) {
@@ -444,45 +447,6 @@ __device__ __forceinline__ void yz_f3(const C<T> *Q, C<T> *P, int pitch, int lgM
         C<T> *o = P + j2 * pitch + kz;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) o[k1 * N2 * pitch] = k1 ? cmul(v[k1], t[k1]) : v[0];
-    }
-}
-template <typename T, int N1, int N2>   // F4: y pass 2, P column slots -> global spectrum
-__device__ __forceinline__ void yz_f4(const C<T> *P, C<T> *out, int pitch, int lgMz) {
-    C<T> v[FFT_NMAX];
-    const int Mz = 1 << lgMz;
-    for (int it = threadIdx.x; it < Mz * N1; it += blockDim.x) {
-        const int kz = it & (Mz - 1), k1 = it >> lgMz;
-        const C<T> *col = P + k1 * N2 * pitch + kz;
-#pragma unroll
-        for (int j2 = 0; j2 < N2; ++j2) v[j2] = col[j2 * pitch];
-        dft_reg<T, N2, false>(v);
-        C<T> *o = out + k1 * Mz + kz;
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) o[N1 * k2 * Mz] = v[k2];
-    }
-}
-template <typename T, int N1, int N2>   // I1: y inverse pass A, global spectrum -> P
-__device__ __forceinline__ void yz_i1(const C<T> *in, C<T> *P, int pitch, int lgMz, const C<T> *tiy) {
-    C<T> v[FFT_NMAX];
-    const int Mz = 1 << lgMz;
-    for (int it = threadIdx.x; it < Mz * N1; it += blockDim.x) {
-        const int kz = it & (Mz - 1), k1 = it >> lgMz;
-        const C<T> *src = in + k1 * Mz + kz;
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[N1 * k2 * Mz];
-        dft_reg<T, N2, true>(v);
-        const C<T> *t = tiy + k1 * N2;
-        C<T> *o = P + k1 * pitch + kz;
-#pragma unroll
-        for (int p2 = 0; p2 < N2; ++p2) {
-            C<T> r = v[p2];
-            if (p2) {
-                const C<T> w = t[p2];
-                r.x = v[p2].x * w.x + v[p2].y * w.y;
-                r.y = v[p2].y * w.x - v[p2].x * w.y;
-            }
-            o[p2 * N1 * pitch] = r;
-        }
     }
 }
 template <typename T, int N1, int N2>   // I2: y inverse pass B, P -> Q rows y < Ny
@@ -542,40 +506,83 @@ __device__ __forceinline__ void yz_i4(const C<T> *P, C<T> *out, int pitch, int N
     }
 }
 
-// (y, z) planes, four-step in both axes, two shared buffers (P: My x pitch,
-// Q: Ny x pitch) so that every step reads one buffer and writes the other.
-// Forward: input [Ny][Nz] (zero-padded to My x Mz), output the [My][Mz]
-// spectrum.  Inverse: input [My][Mz], output [Ny][Nz].  One CTA per plane.
+// y pass 2, times H(kx, ky, kz), inverse y pass A, in place on the column
+// slots of P (rows k1 N2 + j2 in, rows k1 + N1 p2 out).  A round takes
+// CW = blockDim / N1 complete kz columns (every k1 of them), so all reads of a
+// column precede all writes to it; lanes run over kz (conflict-free).
+// Hk: this kx's kernel spectrum [fold(ky)][fold(kz)], pitch Mz/2 + 1.
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const T *__restrict__ Hk,
+                                       const C<T> *__restrict__ tiy) {
+    constexpr int My = N1 * N2;
+    const int Mz = 1 << lgMz, hz = Mz / 2 + 1;
+    const int CW = blockDim.x / N1;
+    const int k1 = threadIdx.x / CW, kzl = threadIdx.x - k1 * CW;
+    C<T> v[FFT_NMAX];
+    for (int kz0 = 0; kz0 < Mz; kz0 += CW) {
+        const int kz = kz0 + kzl;
+        const bool act = k1 < N1 && kz < Mz;
+        if (act) {
+            const C<T> *col = P + k1 * N2 * pitch + kz;
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) v[j2] = col[j2 * pitch];
+            dft_reg<T, N2, false>(v);      // v[k2] = X[ky = k1 + N1 k2]
+            const T *h = Hk + fold_index(kz, Mz);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], h[fold_index(k1 + N1 * k2, My) * hz]);
+            dft_reg<T, N2, true>(v);
+            const C<T> *t = tiy + k1 * N2;
+#pragma unroll
+            for (int p2 = 1; p2 < N2; ++p2) {
+                const C<T> w = t[p2];
+                C<T> r;
+                r.x = v[p2].x * w.x + v[p2].y * w.y;   // times conj(w)
+                r.y = v[p2].y * w.x - v[p2].x * w.y;
+                v[p2] = r;
+            }
+        }
+        __syncthreads();
+        if (act) {
+            C<T> *o = P + k1 * pitch + kz;
+#pragma unroll
+            for (int p2 = 0; p2 < N2; ++p2) o[p2 * N1 * pitch] = v[p2];
+        }
+        __syncthreads();
+    }
+}
+
+// The (y, z) part of the 3-D convolution for one x-frequency plane, in place:
+// plane [Ny][Nz] of buffer [batch][Mx][Ny][Nz] -> zero-padded 2-D FFT ->
+// times H(kx, ., .) -> inverse 2-D FFT -> cropped to [Ny][Nz].  Four-step in
+// both axes through two shared buffers (P: My x pitch, Q: Ny x pitch) so that
+// every step reads one and writes the other.  One CTA per (batch, kx).
+// Hp: kernel spectrum [fold(kx)][fold(ky)][fold(kz)], scaled by 1/(Mx My Mz).
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_yz4(const C<T> *__restrict__ src, int64_t src_stride,
-                                                 C<T> *__restrict__ dst, int64_t dst_stride, int My, int Mz,
-                                                 const C<T> *__restrict__ tfy, const C<T> *__restrict__ tiy,
-                                                 const C<T> *__restrict__ tfz, const C<T> *__restrict__ tiz,
-                                                 int inverse) {
+__global__ void __launch_bounds__(256) k_fft_yzc(C<T> *__restrict__ buf, int lgMx, int My, int Mz,
+                                                 const T *__restrict__ Hp, const C<T> *__restrict__ tfy,
+                                                 const C<T> *__restrict__ tiy, const C<T> *__restrict__ tfz,
+                                                 const C<T> *__restrict__ tiz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int pitch = Mz + 1, Ny = My / 2;
+    const int pitch = Mz + 1, Ny = My / 2, Nz = Mz / 2;
     const int lgNy = ilog2(Ny), lgMz = ilog2(Mz);
+    const int Mx = 1 << lgMx;
+    const int kx = blockIdx.x & (Mx - 1);
     C<T> *P = reinterpret_cast<C<T> *>(smem_raw);
     C<T> *Qb = P + My * pitch;
-    const C<T> *in = src + blockIdx.x * src_stride;
-    C<T> *out = dst + blockIdx.x * dst_stride;
-    if (!inverse) {
-        SIE_SPLIT_DISPATCH(Mz, (yz_f1<T, N1, N2>(in, P, pitch, Ny, tfz)));
-        __syncthreads();
-        SIE_SPLIT_DISPATCH(Mz, (yz_f2<T, N1, N2>(P, Qb, pitch, lgNy)));
-        __syncthreads();
-        SIE_SPLIT_DISPATCH(My, (yz_f3<T, N1, N2>(Qb, P, pitch, lgMz, tfy)));
-        __syncthreads();
-        SIE_SPLIT_DISPATCH(My, (yz_f4<T, N1, N2>(P, out, pitch, lgMz)));
-    } else {
-        SIE_SPLIT_DISPATCH(My, (yz_i1<T, N1, N2>(in, P, pitch, lgMz, tiy)));
-        __syncthreads();
-        SIE_SPLIT_DISPATCH(My, (yz_i2<T, N1, N2>(P, Qb, pitch, lgMz)));
-        __syncthreads();
-        SIE_SPLIT_DISPATCH(Mz, (yz_i3<T, N1, N2>(Qb, P, pitch, lgNy, tiz)));
-        __syncthreads();
-        SIE_SPLIT_DISPATCH(Mz, (yz_i4<T, N1, N2>(P, out, pitch, Ny)));
-    }
+    C<T> *plane = buf + int64_t(blockIdx.x) * Ny * Nz;
+    const T *Hk = Hp + int64_t(fold_index(kx, Mx)) * (My / 2 + 1) * (Mz / 2 + 1);
+    SIE_SPLIT_DISPATCH(Mz, (yz_f1<T, N1, N2>(plane, P, pitch, Ny, tfz)));
+    __syncthreads();
+    SIE_SPLIT_DISPATCH(Mz, (yz_f2<T, N1, N2>(P, Qb, pitch, lgNy)));
+    __syncthreads();
+    SIE_SPLIT_DISPATCH(My, (yz_f3<T, N1, N2>(Qb, P, pitch, lgMz, tfy)));
+    __syncthreads();
+    SIE_SPLIT_DISPATCH(My, (yz_mid<T, N1, N2>(P, pitch, lgMz, Hk, tiy)));
+    SIE_SPLIT_DISPATCH(My, (yz_i2<T, N1, N2>(P, Qb, pitch, lgMz)));
+    __syncthreads();
+    SIE_SPLIT_DISPATCH(Mz, (yz_i3<T, N1, N2>(Qb, P, pitch, lgNy, tiz)));
+    __syncthreads();
+    SIE_SPLIT_DISPATCH(Mz, (yz_i4<T, N1, N2>(P, plane, pitch, Ny)));
 }
 
 }  // namespace sie

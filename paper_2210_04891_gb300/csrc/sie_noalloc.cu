@@ -18,10 +18,10 @@ using namespace sie;
 
 namespace {
 
-// Spectral scratch for the convolution: one zero-padded spectrum
-// [N_x][2N_y][2N_z] per grid, complex128 or complex64.  8 MiB holds one
-// 128 x 64 x 32 grid in FP32 (the mixed form's convolution precision).
-constexpr size_t kNoallocScratchBytes = size_t(8) << 20;
+// Scratch for the convolution: one grid transformed along x, [2N_x][N_y][N_z]
+// per grid, complex128 or complex64.  4 MiB holds one 128 x 64 x 32 grid in
+// FP32 (the mixed form's convolution precision).
+constexpr size_t kNoallocScratchBytes = size_t(4) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -55,9 +55,9 @@ extern "C" int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, i
     if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED)
         return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: bad precision");
     const size_t cb = prec == SIE_PREC_FP64 ? 16 : 8;
-    const size_t spec_bytes = size_t(p->Nx) * p->My * p->Mz * cb;
+    const size_t spec_bytes = size_t(p->Mx) * p->Ny * p->Nz * cb;
     if (spec_bytes > kNoallocScratchBytes)
-        return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: one grid's spectrum needs " + std::to_string(spec_bytes) +
+        return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: one grid's x-transformed copy needs " + std::to_string(spec_bytes) +
                                      " bytes, more than the fixed scratch of " +
                                      std::to_string(kNoallocScratchBytes) + " bytes; use pfft_convolve");
     (void)cudaGetLastError();

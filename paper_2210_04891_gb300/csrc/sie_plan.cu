@@ -322,15 +322,15 @@ __global__ void k_extract_H(const double2 *Hc, double *H64, float *H32, int Mx, 
     H32[i] = float(v);
 }
 
-// Unfold the x index of the folded spectrum: Hx[row][kx] = H[row][fold(kx)].
-__global__ void k_unfold_H(const double *H, double *Hx64, float *Hx32, int Mx, int64_t n) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int kx = int(i % Mx);
-    const int64_t row = i / Mx;
-    const double v = H[row * (Mx / 2 + 1) + fold_index(kx, Mx)];
-    Hx64[i] = v;
-    Hx32[i] = float(v);
+// The folded spectrum reordered with kx outermost: Hp[kx][ky][kz] = H[ky][kz][kx]
+// (all indices folded), so that one x-frequency plane reads a contiguous slice.
+__global__ void k_permute_H(const double *H, double *Hp64, float *Hp32, int hx, int hy, int hz) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(hx) * hy * hz) return;
+    const int kz = int(i % hz), ky = int((i / hz) % hy), kx = int(i / (int64_t(hy) * hz));
+    const double v = H[(int64_t(ky) * hz + kz) * hx + kx];
+    Hp64[i] = v;
+    Hp32[i] = float(v);
 }
 
 __global__ void k_branch_diag(const int64_t *ptr, const int32_t *col, const double *Ldir, const int32_t *br_tri,
@@ -382,61 +382,69 @@ bool is_pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
 
 namespace sie {
 
-// FFT convolution of nrhs*3 grids [Nx][Ny][Nz] (in `grid`, overwritten with the
-// result) through the spectral buffer `spec` [nrhs*3][Nx][My][Mz].
+// FFT convolution of ngrids grids [Nx][Ny][Nz] (in `grid`, overwritten with
+// the result) through the buffer `spec` [ngrids][Mx][Ny][Nz]: x pencils
+// forward, then per x-frequency plane the zero-padded (y, z) transform, the
+// kernel product and the inverse (y, z) transform, then x pencils inverse.
+// Only the x-padded grid (2 N_g per grid) goes through device memory.
 template <typename T> struct Tables;
 template <> struct Tables<double> {
     static const double2 *tf(const pfft_plan *p, int a) { return p->d_tf64[a]; }
     static const double2 *ti(const pfft_plan *p, int a) { return p->d_ti64[a]; }
-    static const double *Hx(const pfft_plan *p) { return p->d_Hx64; }
+    static const double *Hp(const pfft_plan *p) { return p->d_Hp64; }
 };
 template <> struct Tables<float> {
     static const float2 *tf(const pfft_plan *p, int a) { return p->d_tf32[a]; }
     static const float2 *ti(const pfft_plan *p, int a) { return p->d_ti32[a]; }
-    static const float *Hx(const pfft_plan *p) { return p->d_Hx32; }
+    static const float *Hp(const pfft_plan *p) { return p->d_Hp32; }
 };
 
+constexpr int kPencilCols = 16;   // columns per x-pencil CTA
+
 template <typename T, int N1, int N2>
-int launch_x4(pfft_plan *p, C<T> *spec, int ncols, int lgMz, unsigned grid, int thr, size_t pb, cudaStream_t s) {
+int launch_x(pfft_plan *p, const C<T> *in, C<T> *out, int ngrids, bool inverse, cudaStream_t s) {
     using Tb = Tables<T>;
-    int rc = set_smem((const void *)k_fft_x4<T, N1, N2>, pb);
-    if (rc) return rc;
-    k_fft_x4<T, N1, N2><<<grid, thr, pb, s>>>(spec, int64_t(p->Nx) * ncols, ncols, lgMz, p->My, p->Mz, Tb::tf(p, 0),
-                                              Tb::ti(p, 0), Tb::Hx(p));
+    const int ncols = p->Ny * p->Nz;
+    const size_t pb = size_t(kPencilCols) * (N1 * N2 + 1) * sizeof(C<T>);
+    const unsigned grid = unsigned(ngrids * (ncols / kPencilCols));
+    const int thr = kPencilCols * std::max(N1, N2);
+    if (!inverse) {
+        int rc = set_smem((const void *)k_fft_xf<T, N1, N2>, pb);
+        if (rc) return rc;
+        k_fft_xf<T, N1, N2><<<grid, thr, pb, s>>>(in, out, ncols, Tb::tf(p, 0));
+    } else {
+        int rc = set_smem((const void *)k_fft_xi<T, N1, N2>, pb);
+        if (rc) return rc;
+        k_fft_xi<T, N1, N2><<<grid, thr, pb, s>>>(in, out, ncols, Tb::ti(p, 0));
+    }
     return SIE_OK;
 }
 
 template <typename T>
 int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s) {
-    const int nb = ngrids * p->Nx;
-    int NX1, NX2;
-    split4(p->Mx, NX1, NX2);
-    const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
-    int rc = set_smem((const void *)k_fft_yz4<T>, plane_bytes);
-    if (rc) return rc;
     using Tb = Tables<T>;
+    int rc;
     {
-        StageTimer tm(p, SIE_STAGE_FFT_PLANE_FWD, s);
-        k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(grid, int64_t(p->Ny) * p->Nz, spec, int64_t(p->My) * p->Mz, p->My,
-                                                 p->Mz, Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2), 0);
-        SIE_LAUNCH_CHECK(p);
-    }
-    const int KT = 16;
-    const int ncols = p->My * p->Mz;
-    const size_t pb = size_t(KT) * (p->Mx + 1) * sizeof(C<T>);
-    {
-        StageTimer tm(p, SIE_STAGE_FFT_PENCIL, s);
-        int lgMz = 0;
-        while ((1 << lgMz) < p->Mz) ++lgMz;
-        const unsigned grid = unsigned(ngrids * (ncols / KT));
-        const int thr = KT * std::max(NX1, NX2);
-        SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x4<T, N1, N2>(p, spec, ncols, lgMz, grid, thr, pb, s)));
+        StageTimer tm(p, SIE_STAGE_FFT_X_FWD, s);
+        SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x<T, N1, N2>(p, grid, spec, ngrids, false, s)));
         if (rc) return rc;
         SIE_LAUNCH_CHECK(p);
     }
-    StageTimer tm(p, SIE_STAGE_FFT_PLANE_INV, s);
-    k_fft_yz4<T><<<nb, 256, plane_bytes, s>>>(spec, int64_t(p->My) * p->Mz, grid, int64_t(p->Ny) * p->Nz, p->My, p->Mz,
-                                             Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2), 1);
+    {
+        StageTimer tm(p, SIE_STAGE_FFT_YZ, s);
+        const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
+        rc = set_smem((const void *)k_fft_yzc<T>, plane_bytes);
+        if (rc) return rc;
+        int lgMx = 0;
+        while ((1 << lgMx) < p->Mx) ++lgMx;
+        k_fft_yzc<T><<<unsigned(ngrids * p->Mx), 256, plane_bytes, s>>>(spec, lgMx, p->My, p->Mz, Tb::Hp(p),
+                                                                         Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2),
+                                                                         Tb::ti(p, 2));
+        SIE_LAUNCH_CHECK(p);
+    }
+    StageTimer tm(p, SIE_STAGE_FFT_X_INV, s);
+    SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x<T, N1, N2>(p, spec, grid, ngrids, true, s)));
+    if (rc) return rc;
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
@@ -848,10 +856,10 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         if ((rcode = plan_alloc(p, (void **)&p->d_H32, nh * sizeof(float)))) return bail(rcode);
         k_extract_H<<<(nh + 255) / 256, 256, 0, s>>>(d_Hc, p->d_H64, p->d_H32, p->Mx, p->My, p->Mz, 1.0 / double(nM));
         p->launches++;
-        const int64_t nhx = int64_t(p->Mx) * (p->My / 2 + 1) * (p->Mz / 2 + 1);
-        if ((rcode = plan_alloc(p, (void **)&p->d_Hx64, nhx * sizeof(double)))) return bail(rcode);
-        if ((rcode = plan_alloc(p, (void **)&p->d_Hx32, nhx * sizeof(float)))) return bail(rcode);
-        k_unfold_H<<<(nhx + 255) / 256, 256, 0, s>>>(p->d_H64, p->d_Hx64, p->d_Hx32, p->Mx, nhx);
+        if ((rcode = plan_alloc(p, (void **)&p->d_Hp64, nh * sizeof(double)))) return bail(rcode);
+        if ((rcode = plan_alloc(p, (void **)&p->d_Hp32, nh * sizeof(float)))) return bail(rcode);
+        k_permute_H<<<(nh + 255) / 256, 256, 0, s>>>(p->d_H64, p->d_Hp64, p->d_Hp32, p->Mx / 2 + 1, p->My / 2 + 1,
+                                                     p->Mz / 2 + 1);
         p->launches++;
     }
     // ---- near-field blocks

@@ -22,7 +22,7 @@ struct Scratch {
     int prec = -1;
     void *tour = nullptr;      // complex128 [R][2 n_nodes]
     void *grid = nullptr;      // complex T [3][R][Ng]   grid currents, then grid potentials
-    void *spec = nullptr;      // complex T [3R][Nx][My][Mz]
+    void *spec = nullptr;      // complex T [3R][Mx][Ny][Nz]  grids transformed along x
     void *phiT = nullptr;      // complex T [Ng][3][R]   grid potentials, right-hand sides innermost
     void *y_tri = nullptr;     // complex128 [R][nt][3]
     void *y_br = nullptr;      // complex128 [R][nb + np]
@@ -85,9 +85,9 @@ struct pfft_plan {
     // four-step twiddle tables per axis: tf[j2][k1] = W^(j2 k1), ti[k1][p2] = W^(k1 p2)
     double2 *d_tf64[3] = {nullptr, nullptr, nullptr}, *d_ti64[3] = {nullptr, nullptr, nullptr};
     float2 *d_tf32[3] = {nullptr, nullptr, nullptr}, *d_ti32[3] = {nullptr, nullptr, nullptr};
-    // kernel spectrum unfolded along x: [My/2+1][Mz/2+1][Mx]
-    double *d_Hx64 = nullptr;
-    float *d_Hx32 = nullptr;
+    // the same spectrum with kx outermost: [Mx/2+1][My/2+1][Mz/2+1]
+    double *d_Hp64 = nullptr;
+    float *d_Hp32 = nullptr;
     // loop basis on the device
     int32_t *d_tour_node = nullptr;     // [2 nn]
     int8_t *d_tour_enter = nullptr;     // [2 nn]

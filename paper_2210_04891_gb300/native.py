@@ -24,7 +24,7 @@ EXPORTS = ["sie_mesh_load", "sie_mesh_destroy", "loop_basis_build", "sie_loops_d
            "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "sie_last_error"]
-STAGES = ["loop_to_branch", "point_currents", "project", "fft_plane_fwd", "fft_pencil", "fft_plane_inv", "interp",
+STAGES = ["loop_to_branch", "point_currents", "project", "fft_x_fwd", "fft_yz", "fft_x_inv", "interp",
           "near", "branch_to_loop", "precond_apply", "precond_factor", "arnoldi"]
 (EXPORT_NEAR_PTR, EXPORT_NEAR_COL, EXPORT_LD, EXPORT_LDIRECT, EXPORT_HHAT, EXPORT_START, EXPORT_PROJ_PTR,
  EXPORT_PROJ_NODE, EXPORT_PROJ_W) = range(9)

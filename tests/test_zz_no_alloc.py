@@ -67,7 +67,7 @@ def test_noalloc_rejects_oversized_grid():
     m = synth.tiny_bar()
     M = api.Mesh.from_synth(m)
     L = api.Loops(M, m.ports)
-    # 128 x 64 x 32 grid: spectrum 128 * 128 * 64 values = 16 MiB in FP64 (> 8 MiB), 8 MiB in FP32
+    # 128 x 64 x 32 grid padded along x: 256 * 64 * 32 values = 8 MiB in FP64 (> 4 MiB), 4 MiB in FP32
     P = api.Plan(M, L, dict(grid=(128, 64, 32), order=3, near_factor=1.0, near_min_diam=1.0, n_touch=4, h0=0.0))
     g = torch.zeros((1, 128, 64, 32), dtype=torch.complex128, device="cuda")
     with pytest.raises(N.SieError) as e:
