@@ -112,6 +112,8 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Starts sampling and returns once the first sample is written, so that
+        nvidia-smi's own start-up does not fall inside the timed region."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -121,6 +123,12 @@ class ClockSampler:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:

@@ -127,6 +127,8 @@ __device__ __forceinline__ double2 branch_current(int32_t b, int64_t r, const do
     return head[b] == v ? mk<double>(-S.x, -S.y) : S;
 }
 
+// Local currents c_T[k] = s_k alpha_{b(T,k)}: one thread per (T, r) for the
+// three local edges, written as cT [T][3][R] (right-hand sides innermost).
 template <typename T>
 __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const double2 *__restrict__ P, int64_t nslots,
                             const int32_t *__restrict__ tb, const int8_t *__restrict__ ts,
@@ -134,20 +136,23 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const dou
                             const int32_t *__restrict__ head, const int32_t *__restrict__ enter,
                             const int32_t *__restrict__ exit_, int64_t nt, int32_t nrhs, int space, int64_t nb,
                             C<T> *__restrict__ cT) {
-    // i = (t * 3 + k) * R + r: the right-hand sides innermost
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= nt * 3 * nrhs) return;
-    int64_t tk = i / nrhs, r = i % nrhs;
-    int32_t b = tb[tk];
-    double2 a = make_double2(0.0, 0.0);
-    if (b >= 0) {
-        if (space == SIE_SPACE_LOOP)
-            a = branch_current(b, r, x, nl, P, nslots, loop_of_branch, twig_node, head, enter, exit_);
-        else
-            a = x[r * nb + b];
-        if (ts[tk] < 0) { a.x = -a.x; a.y = -a.y; }
+    if (i >= nt * nrhs) return;
+    const int64_t t = i / nrhs, r = i % nrhs;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int64_t tk = t * 3 + k;
+        const int32_t b = tb[tk];
+        double2 a = make_double2(0.0, 0.0);
+        if (b >= 0) {
+            if (space == SIE_SPACE_LOOP)
+                a = branch_current(b, r, x, nl, P, nslots, loop_of_branch, twig_node, head, enter, exit_);
+            else
+                a = x[r * nb + b];
+            if (ts[tk] < 0) { a.x = -a.x; a.y = -a.y; }
+        }
+        cT[tk * nrhs + r] = mk<T>(T(a.x), T(a.y));
     }
-    cT[i] = mk<T>(T(a.x), T(a.y));
 }
 
 // V complex values at p (16-byte aligned when V = 2).
@@ -339,6 +344,32 @@ __global__ void __launch_bounds__(256)
         }
 }
 
+// Interpolated far field alone (mixed form, where the near blocks run on the
+// tensor cores): ffar[T][k][r] = sum_n sum_d W(n,T)[d][k] phi_g[d][n].
+template <typename T, int V, int J>
+__global__ void __launch_bounds__(256)
+    k_far_gather(const int64_t *__restrict__ pt_ptr, const Rec<T> *__restrict__ pt_rec,
+                 const C<T> *__restrict__ phiT, int64_t nt, int32_t R, int32_t nslab, C<T> *__restrict__ ffar) {
+    constexpr int SLAB = 32 * V * J;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= nt * nslab) return;
+    const int64_t t = gw / nslab;
+    const int32_t rbase = int32_t(gw % nslab) * SLAB;
+    const int32_t rl = rbase + V * lane;
+    C<T> acc[3][J][V];
+    zero<T, V, J>(acc);
+    if (rbase + SLAB <= R) gather_rows<T, V, J, true>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
+    else gather_rows<T, V, J, false>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int32_t r = rl + 32 * V * j;
+        if (r < R)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) stv<T, V>(ffar + (t * 3 + k) * R + r, acc[k][j]);
+    }
+}
+
 // y_b = sum over the branch's two triangles of s * y_T[k].
 __global__ void k_branch_out(const double2 *__restrict__ y_tri, const int32_t *__restrict__ br_tri,
                              const int8_t *__restrict__ br_local, int64_t nt, int64_t nb, int64_t ldy, int32_t nrhs,
@@ -399,12 +430,13 @@ namespace sie {
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     Scratch &s = p->scr;
     if (s.cap_rhs >= nrhs && s.prec == prec) return SIE_OK;
-    for (void *a : {s.tour, s.grid, s.spec, s.phiT, s.y_tri, s.y_br, (void *)s.coef, s.cT})
+    for (void *a : {s.tour, s.grid, s.spec, s.phiT, s.y_tri, s.y_br, (void *)s.coef, s.cT, s.ffar})
         if (a) cudaFree(a);
     s = Scratch{};
-    const size_t cs = prec == SIE_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    const bool mixed = prec != SIE_PREC_FP64;
+    const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
     const int64_t R = std::max<int32_t>(nrhs, 1);
-    constexpr int kBufs = 8;
+    constexpr int kBufs = 9;
     const size_t sizes[kBufs] = {
         size_t(R) * 2 * p->nn * sizeof(double2),
         size_t(R) * 3 * p->Ng * cs,
@@ -413,12 +445,15 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
         size_t(R) * p->nt * 3 * sizeof(double2),
         size_t(R) * (p->nb + p->np) * sizeof(double2),
         size_t(R) * (2 * p->ncond + 1) * sizeof(double),
-        size_t(R) * p->nt * 3 * cs};
-    void **dst[kBufs] = {&s.tour, &s.grid, &s.spec, &s.phiT, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT};
+        size_t(R) * p->nt * 3 * cs,
+        mixed ? size_t(R) * p->nt * 3 * sizeof(float2) : 0};
+    void **dst[kBufs] = {&s.tour, &s.grid, &s.spec, &s.phiT, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT,
+                         &s.ffar};
     for (int i = 0; i < kBufs; ++i) {
-        cudaError_t e = cudaMalloc(dst[i], std::max<size_t>(sizes[i], 16));
+        if (!sizes[i]) continue;
+        cudaError_t e = cudaMalloc(dst[i], sizes[i]);
         if (e != cudaSuccess) {
-            for (int j = 0; j < i; ++j) { cudaFree(*dst[j]); *dst[j] = nullptr; }
+            for (int j = 0; j < i; ++j) if (*dst[j]) { cudaFree(*dst[j]); *dst[j] = nullptr; }
             set_error(std::string("scratch allocation failed: ") + cudaGetErrorString(e));
             s = Scratch{};
             return SIE_ERR_OOM;
@@ -449,6 +484,14 @@ template <typename T, int V, int J> struct Blocks {
         SIE_LAUNCH_CHECK(p);
         return SIE_OK;
     }
+    static int far_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
+        const int32_t nslab = (R + SLAB - 1) / SLAB;
+        const int64_t warps = p->nt * nslab;
+        k_far_gather<T, V, J><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
+            p->d_pt_ptr, pt(p), (const C<T> *)p->scr.phiT, p->nt, R, nslab, (C<T> *)p->scr.ffar);
+        SIE_LAUNCH_CHECK(p);
+        return SIE_OK;
+    }
     static int tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
         const int32_t nslab = (R + SLAB - 1) / SLAB;
         const int64_t warps = p->nt * nslab;
@@ -465,6 +508,9 @@ template <typename T, int V, int J> struct Blocks {
 template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) {
     if constexpr (sizeof(T) == 8) return Blocks<double, 1, 2>::project(p, R, st);
     else return R % 2 == 0 ? Blocks<float, 2, 2>::project(p, R, st) : Blocks<float, 1, 4>::project(p, R, st);
+}
+int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
+    return R % 2 == 0 ? Blocks<float, 2, 2>::far_gather(p, R, st) : Blocks<float, 1, 4>::far_gather(p, R, st);
 }
 template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
     if constexpr (sizeof(T) == 8) return Blocks<double, 1, 2>::tri_gather(p, R, st);
@@ -486,9 +532,9 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
         k_scan_rows<<<R, 1024, 0, st>>>(tour, nslots);
         SIE_LAUNCH_CHECK(p);
     }
-    k_alpha_tri<T><<<nblk(p->nt * 3 * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tb, p->d_ts, p->d_loop_of_branch,
-                                                         p->d_twig_node, p->d_head, p->d_enter, p->d_exit, p->nt, R,
-                                                         space, p->nb, (C<T> *)s.cT);
+    k_alpha_tri<T><<<nblk(p->nt * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tb, p->d_ts, p->d_loop_of_branch,
+                                                     p->d_twig_node, p->d_head, p->d_enter, p->d_exit, p->nt, R, space,
+                                                     p->nb, (C<T> *)s.cT);
     SIE_LAUNCH_CHECK(p);
     tm.reset(new StageTimer(p, SIE_STAGE_PROJECT, st));
     int rc = run_project<T>(p, R, st);
@@ -503,8 +549,17 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
         k_regroup<T><<<grid, 256, 0, st>>>((const C<T> *)s.grid, p->d_tiles, p->Ng, B, (C<T> *)s.phiT);
         SIE_LAUNCH_CHECK(p);
     }
-    tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
-    rc = run_tri_gather<T>(p, R, st);
+    // mixed form, R even: near blocks on the tensor cores (their operand rows are
+    // 16-byte aligned only for even R); otherwise one CUDA-core gather
+    if (sizeof(T) == 4 && R % 2 == 0) {
+        rc = run_far_gather(p, R, st);          // interpolation (step 3) on the CUDA cores
+        if (rc) return rc;
+        tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
+        rc = near_mma_launch(p, R, st);         // near blocks on the tensor cores + y_T
+    } else {
+        tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
+        rc = run_tri_gather<T>(p, R, st);       // near + interpolation + y_T in one gather
+    }
     if (rc) return rc;
     tm.reset(new StageTimer(p, SIE_STAGE_BRANCH_TO_LOOP, st));
     if (space == SIE_SPACE_BRANCH) {
@@ -570,5 +625,5 @@ extern "C" int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, c
     int rc = sie::matvec_async(p, x, y, nrhs, omega, space, prec, st);
     if (rc) return rc;
     SIE_CUDA(cudaStreamSynchronize(st));
-    return SIE_OK;
+    return sie::check_device_errors(p);
 }

@@ -458,6 +458,16 @@ int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaS
     return fft_conv_n(p, grid, spec, 3 * nrhs, prec, s);
 }
 
+// Reads and clears the plan's device error flags (call after the work that
+// may have set them has completed).
+int check_device_errors(pfft_plan *p) {
+    int flags = 0;
+    SIE_CUDA(cudaMemcpy(&flags, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flags) return SIE_OK;
+    SIE_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    return fail(SIE_ERR_TIMEOUT, "a bounded device-side wait ran out (tensor-core near field); results are invalid");
+}
+
 }  // namespace sie
 
 extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pfft_params *prm, void *cuda_stream,
@@ -878,6 +888,9 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     k_pack_near<<<(p->n_near + 255) / 256, 256, 0, s>>>(p->d_near_col, p->d_Ld64, p->n_near, p->d_near_rec64,
                                                          p->d_near_rec32);
     p->launches++;
+    if ((rcode = near_mma_prepare(p, near_ptr, near_col, s))) return bail(rcode);
+    if ((rcode = plan_alloc(p, (void **)&p->d_err, sizeof(int)))) return bail(rcode);
+    SIE_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
     if ((rcode = plan_alloc(p, (void **)&p->d_diag_L, L->nb * sizeof(double)))) return bail(rcode);
     k_branch_diag<<<(L->nb + 255) / 256, 256, 0, s>>>(p->d_near_ptr, p->d_near_col, p->d_Ldir64, p->d_br_tri,
                                                       p->d_br_local, L->nb, p->d_diag_L);

@@ -28,6 +28,7 @@ struct Scratch {
     void *y_br = nullptr;      // complex128 [R][nb + np]
     double *coef = nullptr;    // per RHS: Z_s per conductor (re, im), c_L (im) -> [R][2 ncond + 1]
     void *cT = nullptr;        // complex T [nt][3][R]  local currents, right-hand sides innermost
+    void *ffar = nullptr;      // complex64 [nt][3][R]  interpolated far field (mixed form)
     size_t bytes = 0;
 };
 
@@ -77,6 +78,12 @@ struct pfft_plan {
     double *d_Ldir64 = nullptr;         // [n_near][3][3]  L_direct (kept for diag and checks)
     sie::Rec<double> *d_near_rec64 = nullptr;   // [n_near] {b = L_d block [k][l], col = T'}
     sie::Rec<float> *d_near_rec32 = nullptr;
+    // tensor-core near field: row tiles of 42 triangles, their column unions
+    int64_t nm_tiles = 0, nm_union = 0;
+    int64_t *d_nm_uptr = nullptr;       // [nm_tiles + 1] union offsets (even counts)
+    int32_t *d_nm_utri = nullptr;       // [nm_union] column triangles, ascending per tile
+    float *d_nm_A = nullptr;            // [nm_union][128][3] dense L_d blocks of each tile (fp32)
+    int *d_err = nullptr;               // device error flags (a bounded wait ran out)
     // kernel spectrum, folded [My/2+1][Mz/2+1][Mx/2+1], scaled by 1/(Mx My Mz)
     double *d_H64 = nullptr;
     float *d_H32 = nullptr;
@@ -145,4 +152,8 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
 int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s);
+int near_mma_prepare(pfft_plan *p, const std::vector<int64_t> &near_ptr, const std::vector<int32_t> &near_col,
+                     cudaStream_t s);
+int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st);
+int check_device_errors(pfft_plan *p);
 }  // namespace sie

@@ -1278,6 +1278,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     }
 #undef GM_CUDA
 #undef GM_RC
+    if (int dev_rc = check_device_errors(p)) return dev_rc;
     if (breakdown) return fail(SIE_ERR_BREAKDOWN, "sie_solve: non-finite value in the Arnoldi recurrence");
     if (nnc) return fail(SIE_ERR_NOT_CONVERGED, "sie_solve: " + std::to_string(nnc) + " right-hand sides did not converge");
     return SIE_OK;
