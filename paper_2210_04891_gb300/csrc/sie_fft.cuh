@@ -555,10 +555,12 @@ __device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const T *__
 // plane [Ny][Nz] of buffer [batch][Mx][Ny][Nz] -> zero-padded 2-D FFT ->
 // times H(kx, ., .) -> inverse 2-D FFT -> cropped to [Ny][Nz].  Four-step in
 // both axes through two shared buffers (P: My x pitch, Q: Ny x pitch) so that
-// every step reads one and writes the other.  One CTA per (batch, kx).
+// every step reads one and writes the other.  One CTA per (batch, kx), NT
+// threads (512 in FP32: two CTAs and 32 warps per SM; 256 in FP64, whose
+// plane fills the shared memory of one SM).
 // Hp: kernel spectrum [fold(kx)][fold(ky)][fold(kz)], scaled by 1/(Mx My Mz).
-template <typename T>
-__global__ void __launch_bounds__(256) k_fft_yzc(C<T> *__restrict__ buf, int lgMx, int My, int Mz,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fft_yzc(C<T> *__restrict__ buf, int lgMx, int My, int Mz,
                                                  const T *__restrict__ Hp, const C<T> *__restrict__ tfy,
                                                  const C<T> *__restrict__ tiy, const C<T> *__restrict__ tfz,
                                                  const C<T> *__restrict__ tiz) {

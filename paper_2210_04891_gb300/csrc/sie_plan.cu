@@ -432,14 +432,15 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     }
     {
         StageTimer tm(p, SIE_STAGE_FFT_YZ, s);
+        constexpr int NT = sizeof(T) == 4 ? 512 : 256;
         const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
-        rc = set_smem((const void *)k_fft_yzc<T>, plane_bytes);
+        rc = set_smem((const void *)k_fft_yzc<T, NT>, plane_bytes);
         if (rc) return rc;
         int lgMx = 0;
         while ((1 << lgMx) < p->Mx) ++lgMx;
-        k_fft_yzc<T><<<unsigned(ngrids * p->Mx), 256, plane_bytes, s>>>(spec, lgMx, p->My, p->Mz, Tb::Hp(p),
-                                                                         Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2),
-                                                                         Tb::ti(p, 2));
+        k_fft_yzc<T, NT><<<unsigned(ngrids * p->Mx), NT, plane_bytes, s>>>(spec, lgMx, p->My, p->Mz, Tb::Hp(p),
+                                                                            Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2),
+                                                                            Tb::ti(p, 2));
         SIE_LAUNCH_CHECK(p);
     }
     StageTimer tm(p, SIE_STAGE_FFT_X_INV, s);
@@ -910,7 +911,7 @@ extern "C" void pfft_plan_destroy(pfft_plan *p) {
     for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void *a : p->allocations) cudaFree(a);
     for (void *a : {p->scr.tour, p->scr.grid, p->scr.spec, p->scr.phiT, p->scr.y_tri, p->scr.y_br,
-                    (void *)p->scr.coef, p->scr.cT})
+                    (void *)p->scr.coef, p->scr.cT, p->scr.ffar})
         if (a) cudaFree(a);
     delete p;
 }

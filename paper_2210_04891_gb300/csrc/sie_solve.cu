@@ -467,129 +467,57 @@ template <typename V> __device__ __forceinline__ V shfl_c(V v, int src) {
     return v;
 }
 
-// T = double: FP64 sweeps (plain form); T = float: FP32 band and sweeps (mixed
-// form; the factor is computed in FP64 and rounded), FP64 in and out.
-template <typename T>
-__global__ void k_pc_solve_win(const double2 *__restrict__ kappa, const int32_t *__restrict__ row_ptr,
-                               const int32_t *__restrict__ row_br, const int8_t *__restrict__ row_sg,
-                               const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk, int64_t nb,
-                               const C<T> *__restrict__ band, const C<T> *__restrict__ bandc,
-                               const int32_t *__restrict__ slot, int32_t nrhs, double2 *__restrict__ u,
-                               C<T> *__restrict__ xs) {
-    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
-    const int lane = threadIdx.x & 31;
-    if (wid >= int64_t(nrhs) * nblk) return;
-    const int64_t r = wid / nblk, b = wid % nblk;
-    const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
-    const int Wp = W + 1;
-    const C<T> *B = band + (int64_t(slot[r]) * nunk + o) * Wp;
-    const C<T> *Bc = bandc + (int64_t(slot[r]) * nunk + o) * Wp;
-    double2 *xd = u + r * nunk + o;
-    C<T> *x = xs + r * nunk + o;     // sweep buffer in the sweep precision
-    const double2 *kr = kappa + r * nb;
-    const C<T> zero = mk<T>(T(0), T(0));
-    for (int64_t i = lane; i < n; i += 32) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int32_t k = row_ptr[o + i]; k < row_ptr[o + i + 1]; ++k)
-            acc = row_sg[k] > 0 ? csub(acc, kr[row_br[k]]) : cadd(acc, kr[row_br[k]]);
-        x[i] = mk<T>(T(acc.x), T(acc.y));
-    }
-    __syncwarp();
-    // forward: unit lower L, column form  y_{i+d} -= L[i+d][i] y_i.  The band
-    // entries of step i are loaded PF steps ahead into a register queue and the
-    // row a pivot lane takes over (32 further on) 32 steps ahead, so no step
-    // waits on memory.
-    constexpr int PF = 16;
-    C<T> lq[PF];
-    C<T> w = lane < n ? x[lane] : zero;
-    C<T> pf = lane + 32 < n ? x[lane + 32] : zero;
-    auto lf = [&](int64_t i) -> C<T> {
-        const int d = (lane - int(i & 31)) & 31;
-        return (i < n && d >= 1 && d <= W && i + d < n) ? Bc[i * Wp + d] : zero;
-    };
-#pragma unroll
-    for (int j = 0; j < PF; ++j) lq[j] = lf(j);
-    for (int64_t i0 = 0; i0 < n; i0 += PF) {
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int64_t i = i0 + j;
-            if (i >= n) break;
-            const C<T> l = lq[j];
-            lq[j] = lf(i + PF);
-            const int pl = int(i & 31);
-            const C<T> xi = shfl_c(w, pl);
-            w = csub(w, cmul(l, xi));
-            if (lane == pl) {
-                x[i] = xi;
-                w = pf;
-                pf = i + 64 < n ? x[i + 64] : zero;
-            }
-        }
-    }
-    __syncwarp();
-    for (int64_t i = lane; i < n; i += 32) {
-        const C<T> dg = B[i * Wp];
-        const T den = dg.x * dg.x + dg.y * dg.y;
-        x[i] = cmul(x[i], mk<T>(dg.x / den, -dg.y / den));
-    }
-    __syncwarp();
-    // backward: unit upper L^T, column form  x_{i-d} -= L[i][i-d] x_i
-    auto lb = [&](int64_t i) -> C<T> {
-        const int d = (lane - int((n - 1 - i) & 31)) & 31;
-        return (i >= 0 && d >= 1 && d <= W && i - d >= 0) ? B[i * Wp + d] : zero;
-    };
-    w = lane < n ? x[n - 1 - lane] : zero;
-    pf = n - 1 - 32 - lane >= 0 ? x[n - 1 - 32 - lane] : zero;
-#pragma unroll
-    for (int j = 0; j < PF; ++j) lq[j] = lb(n - 1 - j);
-    for (int64_t i0 = n - 1; i0 >= 0; i0 -= PF) {
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int64_t i = i0 - j;
-            if (i < 0) break;
-            const C<T> l = lq[j];
-            lq[j] = lb(i - PF);
-            const int pl = int((n - 1 - i) & 31);
-            const C<T> xi = shfl_c(w, pl);
-            w = csub(w, cmul(l, xi));
-            if (lane == pl) {
-                x[i] = xi;
-                w = pf;
-                pf = i - 64 >= 0 ? x[i - 64] : zero;
-            }
-        }
-    }
-    __syncwarp();
-    if ((void *)x != (void *)xd)
-        for (int64_t i = lane; i < n; i += 32) xd[i] = make_double2(double(x[i].x), double(x[i].y));
-}
-
-// Grouped band solve: one warp sweeps RB right-hand sides that share a factor
-// slot (the ports of one frequency) through one block.  The band is staged
-// in shared memory 32 rows at a time with asynchronous copies issued two
-// chunks ahead; lane (row mod 32) holds the running values of `row` for all RB
-// right-hand sides; the rows a lane takes over and the rows it finishes are
-// loaded and stored once per 32-row chunk, coalesced.  Requires W <= 31.
+// Band solve L d L^T u = rhs of one conductor block for RB right-hand sides
+// that share a factor slot (requires W <= 31), one warp, after assembling
+// rhs_i = -sum over the incident branches of s * kappa_e.
+//
+// The sweeps keep a circular window in registers: lane (row mod 32) holds the
+// running value of its row for the 32 rows from the current pivot on.  A step
+// broadcasts the finished pivot with a shuffle, every lane subtracts its band
+// entry times the pivot, and the pivot's lane takes over the row 32 further
+// on.  The band is staged into shared memory 32 rows at a time with
+// asynchronous copies issued two chunks ahead, at a pitch of 32 entries: a
+// lane's entry of a step sits at (step, (lane - step) mod 32) and every entry
+// the copies do not write (the diagonal, distances beyond W) stays zero, so a
+// full chunk runs unrolled with no bounds tests.  The factor stores zeros
+// outside the block (forward: i + d >= n; backward: i - d < 0).
 constexpr int PC_CH = 32;
 
 template <typename T>
-__device__ __forceinline__ void pc_stage_rows(C<T> *dst, const C<T> *src, int64_t row0, int64_t nrows, int Wp,
-                                              int64_t n, int lane) {
-    // rows [row0, row0 + nrows) of a [n][Wp] band -> dst[(row - row0) * Wp]
-    const int64_t r0 = row0 < 0 ? 0 : row0;
-    const int64_t r1 = row0 + nrows > n ? n : row0 + nrows;
-    if (r1 <= r0) return;
-    const char *s = reinterpret_cast<const char *>(src + r0 * Wp);
-    char *d = reinterpret_cast<char *>(dst + (r0 - row0) * Wp);
-    const int64_t bytes = (r1 - r0) * Wp * int64_t(sizeof(C<T>));
-    for (int64_t o = int64_t(lane) * 8; o < bytes; o += 32 * 8) {
-        const unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(d + o));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(s + o));
+__device__ __forceinline__ void pc_stage32(C<T> *dst, const C<T> *src, int64_t row0, int W, int64_t n, int lane) {
+    // entries d = 1..W of rows [row0, row0 + 32) of a [n][W + 1] band -> dst[(row - row0) * 32 + d];
+    // lane d copies entry d of every row
+    const int Wp = W + 1;
+    const bool mine = lane >= 1 && lane <= W;
+    const unsigned s0 = static_cast<unsigned>(__cvta_generic_to_shared(dst + lane));
+#pragma unroll 8
+    for (int r = 0; r < PC_CH; ++r) {
+        const int64_t i = row0 + r;
+        if (!mine || i < 0 || i >= n) continue;
+        const unsigned saddr = s0 + unsigned(r * PC_CH * sizeof(C<T>));
+        const C<T> *g = src + i * Wp + lane;
+        if constexpr (sizeof(C<T>) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(g));
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g));
+    }
+}
+
+// One step of a sweep: pivot j of the chunk, its band entries at row jr of the staged chunk.
+template <typename T, int RB>
+__device__ __forceinline__ void pc_step(const C<T> *bs, int j, int jr, int lane, C<T> (&w)[RB], C<T> (&pf)[RB],
+                                        C<T> (&done)[RB]) {
+    const C<T> l = bs[jr * PC_CH + ((lane - j) & 31)];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        const C<T> xi = shfl_c(w[k], j);
+        w[k] = csub(w[k], cmul(l, xi));
+        if (lane == j) { done[k] = xi; w[k] = pf[k]; }
     }
 }
 
 template <typename T, int RB>
-__global__ void __launch_bounds__(128) k_pc_solve_grp(
+__global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
     const double2 *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
     const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
     int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
@@ -606,8 +534,9 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
     const C<T> *B = band + (int64_t(slot[r0]) * nunk + o) * Wp;
     const C<T> *Bc = bandc + (int64_t(slot[r0]) * nunk + o) * Wp;
     const C<T> zero = mk<T>(T(0), T(0));
-    C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_CH * Wp;   // [warp][2][32][Wp]
-    C<T> *buf1 = buf0 + PC_CH * Wp;
+    C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_CH * PC_CH;   // [warp][2][32][32]
+    C<T> *buf1 = buf0 + PC_CH * PC_CH;
+    for (int t = lane; t < 2 * PC_CH * PC_CH; t += 32) buf0[t] = zero;
     // right-hand sides of the nodal system
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
@@ -625,16 +554,15 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
     const int64_t nch = (n + PC_CH - 1) / PC_CH;
     C<T> w[RB], pf[RB], pn[RB], done[RB];
     // ---------------- forward: y_{i+d} -= L[i+d][i] y_i   (chunk c = steps [32c, 32c+32))
-    pc_stage_rows<T>(buf0, Bc, 0, PC_CH, Wp, n, lane);
+    pc_stage32<T>(buf0, Bc, 0, W, n, lane);
     asm volatile("cp.async.commit_group;\n" ::);
-    pc_stage_rows<T>(buf1, Bc, PC_CH, PC_CH, Wp, n, lane);
+    pc_stage32<T>(buf1, Bc, PC_CH, W, n, lane);
     asm volatile("cp.async.commit_group;\n" ::);
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
         const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
         w[k] = lane < n ? x[lane] : zero;
         pf[k] = lane + 32 < n ? x[lane + 32] : zero;
-        pn[k] = zero;
         done[k] = zero;
     }
     for (int64_t c = 0; c < nch; ++c) {
@@ -647,18 +575,11 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
         const C<T> *bs = (c & 1) ? buf1 : buf0;
-#pragma unroll 4
-        for (int j = 0; j < PC_CH; ++j) {
-            const int64_t i = base + j;
-            if (i >= n) break;
-            const int d = (lane - j) & 31;
-            const C<T> l = (d >= 1 && d <= W && i + d < n) ? bs[j * Wp + d] : zero;
+        if (base + PC_CH <= n) {
 #pragma unroll
-            for (int k = 0; k < RB; ++k) {
-                const C<T> xi = shfl_c(w[k], j);
-                w[k] = csub(w[k], cmul(l, xi));
-                if (lane == j) { done[k] = xi; w[k] = pf[k]; }
-            }
+            for (int j = 0; j < PC_CH; ++j) pc_step<T, RB>(bs, j, j, lane, w, pf, done);
+        } else {
+            for (int j = 0; j < int(n - base); ++j) pc_step<T, RB>(bs, j, j, lane, w, pf, done);
         }
 #pragma unroll
         for (int k = 0; k < RB; ++k) {
@@ -666,7 +587,7 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
             pf[k] = pn[k];
         }
         __syncwarp();
-        pc_stage_rows<T>((c & 1) ? buf1 : buf0, Bc, base + 2 * PC_CH, PC_CH, Wp, n, lane);
+        pc_stage32<T>((c & 1) ? buf1 : buf0, Bc, base + 2 * PC_CH, W, n, lane);
         asm volatile("cp.async.commit_group;\n" ::);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -685,9 +606,9 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
     __syncwarp();
     // ---------------- backward: x_{i-d} -= L[i][i-d] x_i   (chunk c = steps i = n-1-32c-j)
     // staged rows of chunk c: [n - 32(c+1), n - 32c), row i at index i - (n - 32(c+1))
-    pc_stage_rows<T>(buf0, B, n - PC_CH, PC_CH, Wp, n, lane);
+    pc_stage32<T>(buf0, B, n - PC_CH, W, n, lane);
     asm volatile("cp.async.commit_group;\n" ::);
-    pc_stage_rows<T>(buf1, B, n - 2 * PC_CH, PC_CH, Wp, n, lane);
+    pc_stage32<T>(buf1, B, n - 2 * PC_CH, W, n, lane);
     asm volatile("cp.async.commit_group;\n" ::);
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
@@ -698,7 +619,6 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
     }
     for (int64_t c = 0; c < nch; ++c) {
         const int64_t top = n - 1 - c * PC_CH;          // i of step j = 0
-        const int64_t sbase = n - (c + 1) * PC_CH;      // first staged row
 #pragma unroll
         for (int k = 0; k < RB; ++k) {
             const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
@@ -707,18 +627,11 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
         const C<T> *bs = (c & 1) ? buf1 : buf0;
-#pragma unroll 4
-        for (int j = 0; j < PC_CH; ++j) {
-            const int64_t i = top - j;
-            if (i < 0) break;
-            const int d = (lane - j) & 31;
-            const C<T> l = (d >= 1 && d <= W && i - d >= 0) ? bs[(i - sbase) * Wp + d] : zero;
+        if (top - (PC_CH - 1) >= 0) {
 #pragma unroll
-            for (int k = 0; k < RB; ++k) {
-                const C<T> xi = shfl_c(w[k], j);
-                w[k] = csub(w[k], cmul(l, xi));
-                if (lane == j) { done[k] = xi; w[k] = pf[k]; }
-            }
+            for (int j = 0; j < PC_CH; ++j) pc_step<T, RB>(bs, j, PC_CH - 1 - j, lane, w, pf, done);
+        } else {
+            for (int j = 0; j <= int(top); ++j) pc_step<T, RB>(bs, j, PC_CH - 1 - j, lane, w, pf, done);
         }
 #pragma unroll
         for (int k = 0; k < RB; ++k) {
@@ -726,7 +639,7 @@ __global__ void __launch_bounds__(128) k_pc_solve_grp(
             pf[k] = pn[k];
         }
         __syncwarp();
-        pc_stage_rows<T>((c & 1) ? buf1 : buf0, B, n - (c + 3) * PC_CH, PC_CH, Wp, n, lane);
+        pc_stage32<T>((c & 1) ? buf1 : buf0, B, n - (c + 3) * PC_CH, W, n, lane);
         asm volatile("cp.async.commit_group;\n" ::);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -894,8 +807,8 @@ int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int pr
         if (s->W <= 31) {
             const int v = prec == SIE_PREC_MIXED ? 0 : 1;
             const int64_t gw = int64_t(s->ngroups[v]) * nblk;
-            const size_t sm32 = size_t(4) * 2 * PC_CH * (s->W + 1) * sizeof(float2);
-            const size_t sm64 = size_t(4) * 2 * PC_CH * (s->W + 1) * sizeof(double2);
+            const size_t sm32 = size_t(4) * 2 * PC_CH * PC_CH * sizeof(float2);
+            const size_t sm64 = size_t(4) * 2 * PC_CH * PC_CH * sizeof(double2);
             SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<float, 1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm32)));
             SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<double, 1>,
@@ -909,18 +822,11 @@ int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int pr
                 k_pc_solve_grp<double, 1><<<nblk_(gw * 32, 128), 128, sm64, st>>>(
                     s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
                     s->d_band, s->d_bandc, s->d_slot, s->d_grp_start[1], s->d_grp_count[1], s->ngroups[1], s->d_u, s->d_u);
-        } else if (false && s->W <= 31 && prec == SIE_PREC_MIXED)
-            k_pc_solve_win<float><<<nblk_(warps * 32, 128), 128, 0, st>>>(
-                s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
-                s->d_band32, s->d_bandc32, s->d_slot, R, s->d_u, s->d_u32);
-        else if (s->W <= 31)
-            k_pc_solve_win<double><<<nblk_(warps * 32, 128), 128, 0, st>>>(
-                s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
-                s->d_band, s->d_bandc, s->d_slot, R, s->d_u, s->d_u);
-        else
+        } else {
             k_pc_solve<<<nblk_(warps * 32, 128), 128, 0, st>>>(s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
                                                                 s->d_blk_off, nblk, s->W, s->nunk, p->nb, s->d_band,
                                                                 s->d_slot, R, s->d_u);
+        }
         SIE_LAUNCH_CHECK(p);
     }
     k_pc_currents<<<nblk_(p->nb * R), 256, 0, st>>>(s->d_u, s->nunk, s->d_kappa, s->d_a, s->d_slot,
