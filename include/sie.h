@@ -94,6 +94,10 @@ typedef struct {
     int32_t max_iter;      /* iteration cap per right-hand side               */
     int32_t precond;       /* 0: none, 1: P = A diag(Z_b) A^T (Eq. Precond)    */
     int32_t prec;          /* SIE_PREC_FP64 or SIE_PREC_MIXED                  */
+    int32_t refine;        /* with SIE_PREC_MIXED: 1 = iterative refinement:
+                              every restart residual P^-1 (b - Z x) (and the
+                              convergence test) in FP64, the Arnoldi cycles in
+                              the mixed form; 0 = all in the mixed form        */
 } sie_solve_opts;
 
 typedef struct {

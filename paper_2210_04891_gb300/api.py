@@ -213,10 +213,10 @@ def pfft_precond_apply(plan: Plan, y, omega, out=None, prec=N.PREC_FP64, stream=
 
 
 def sie_solve(plan: Plan, freqs, ports=None, tol=1e-6, restart=200, max_iter=2000, precond=1,
-              prec=N.PREC_FP64):
+              prec=N.PREC_FP64, refine=False):
     f = np.ascontiguousarray(freqs, np.float64)
     pr = np.arange(plan.np, dtype=np.int32) if ports is None else np.ascontiguousarray(ports, np.int32)
-    o = N.SolveOpts(tol=tol, restart=restart, max_iter=max_iter, precond=precond, prec=prec)
+    o = N.SolveOpts(tol=tol, restart=restart, max_iter=max_iter, precond=precond, prec=prec, refine=int(refine))
     Z = np.zeros((f.shape[0], pr.shape[0], pr.shape[0]), np.complex128)
     st = N.SolveStats()
     rc = lib().sie_solve(plan.h, _ptr(f), f.shape[0], _ptr(pr), pr.shape[0], ctypes.byref(o), _ptr(Z),

@@ -427,15 +427,21 @@ inline unsigned nblk(int64_t n, int t = 256) { return unsigned((n + t - 1) / t);
 
 namespace sie {
 
+// Grows the matvec scratch to hold nrhs right-hand sides in precision `prec`.
+// Buffers only grow: a plan used in both precisions keeps FP64-sized buffers
+// (the mixed form reads them as complex64) and the mixed form's far-field
+// buffer, so alternating precisions (iterative refinement) never reallocates.
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     Scratch &s = p->scr;
-    if (s.cap_rhs >= nrhs && s.prec == prec) return SIE_OK;
+    const bool mixed = prec != SIE_PREC_FP64;
+    const int want_cs = mixed ? int(sizeof(float2)) : int(sizeof(double2));
+    if (s.cap_rhs >= nrhs && s.cs >= want_cs && (!mixed || s.ffar)) return SIE_OK;
+    const int64_t R = std::max<int64_t>({int64_t(nrhs), int64_t(s.cap_rhs), 1});
+    const size_t cs = size_t(std::max(want_cs, s.cs));
+    const bool with_far = mixed || s.ffar != nullptr;
     for (void *a : {s.tour, s.grid, s.spec, s.phiT, s.y_tri, s.y_br, (void *)s.coef, s.cT, s.ffar})
         if (a) cudaFree(a);
     s = Scratch{};
-    const bool mixed = prec != SIE_PREC_FP64;
-    const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
-    const int64_t R = std::max<int32_t>(nrhs, 1);
     constexpr int kBufs = 9;
     const size_t sizes[kBufs] = {
         size_t(R) * 2 * p->nn * sizeof(double2),
@@ -446,7 +452,7 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
         size_t(R) * (p->nb + p->np) * sizeof(double2),
         size_t(R) * (2 * p->ncond + 1) * sizeof(double),
         size_t(R) * p->nt * 3 * cs,
-        mixed ? size_t(R) * p->nt * 3 * sizeof(float2) : 0};
+        with_far ? size_t(R) * p->nt * 3 * sizeof(float2) : 0};
     void **dst[kBufs] = {&s.tour, &s.grid, &s.spec, &s.phiT, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT,
                          &s.ffar};
     for (int i = 0; i < kBufs; ++i) {
@@ -461,7 +467,7 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
         s.bytes += sizes[i];
     }
     s.cap_rhs = int32_t(R);
-    s.prec = prec;
+    s.cs = int(cs);
     return SIE_OK;
 }
 

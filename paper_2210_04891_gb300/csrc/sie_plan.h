@@ -19,7 +19,7 @@ struct PrecondState;   // sie_solve.cu
 
 struct Scratch {
     int32_t cap_rhs = 0;   // right-hand sides the buffers are sized for
-    int prec = -1;
+    int cs = 0;            // complex element size the buffers are sized for (8 or 16)
     void *tour = nullptr;      // complex128 [R][2 n_nodes]
     void *grid = nullptr;      // complex T [3][R][Ng]   grid currents, then grid potentials
     void *spec = nullptr;      // complex T [3R][Mx][Ny][Nz]  grids transformed along x

@@ -948,6 +948,9 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     for (int32_t f = 0; f < nf; ++f)
         for (int32_t q = 0; q < np; ++q) om[f * np + q] = 2.0 * M_PI * freqs[f];
     const bool use_pc = opts->precond != 0;
+    // iterative refinement: restart residuals and the convergence test in FP64
+    const int outer_prec = (opts->refine && opts->prec == SIE_PREC_MIXED) ? SIE_PREC_FP64 : opts->prec;
+    const bool refine = outer_prec != opts->prec;
     std::vector<int32_t> slot;
     int rc;
     if (use_pc && (rc = pc_prepare(p, om.data(), R, slot, st))) return rc;
@@ -981,10 +984,10 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
             int64_t pl = p->loops->loop_of_branch[p->nb + ports[q]];
             GM_CUDA(cudaMemcpyAsync(b + int64_t(f * np + q) * n + pl, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
         }
-    auto apply_op = [&](const double2 *in, double2 *out) -> int {   // out = P^-1 Z in
-        int r2 = matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, opts->prec, st);
+    auto apply_op = [&](const double2 *in, double2 *out, int prec) -> int {   // out = P^-1 Z in
+        int r2 = matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, prec, st);
         if (r2) return r2;
-        if (use_pc) return pc_apply_async(p, t, out, R, opts->prec, st);
+        if (use_pc) return pc_apply_async(p, t, out, R, prec, st);
         return SIE_OK;
     };
     auto dots = [&](const double2 *vec, int32_t k, std::vector<double2> &h) -> int {   // h[r][j] for j < k
@@ -1012,7 +1015,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     std::vector<double> bnorm(R), resid(R, 1.0);
     GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     // ||P^-1 b||
-    if (use_pc) GM_RC(pc_apply_async(p, b, w, R, opts->prec, st));
+    if (use_pc) GM_RC(pc_apply_async(p, b, w, R, outer_prec, st));
     else GM_CUDA(cudaMemcpyAsync(w, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     GM_RC(norms(w, bnorm));
     int64_t matvecs = 0;
@@ -1020,13 +1023,13 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     int total_iters = 0;
     bool breakdown = false;
     while (true) {
-        // residual r = P^-1 (b - Z x)
-        GM_RC(apply_op(x, w));   // w = P^-1 Z x
+        // residual r = P^-1 (b - Z x), in FP64 under iterative refinement
+        GM_RC(apply_op(x, w, outer_prec));   // w = P^-1 Z x
         matvecs += R;
         if (use_pc) {
             k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, t, int64_t(R) * n);   // t = b - Z x (t held Z x)
             SIE_LAUNCH_CHECK(p);
-            GM_RC(pc_apply_async(p, t, w, R, opts->prec, st));
+            GM_RC(pc_apply_async(p, t, w, R, outer_prec, st));
         } else {
             k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, w, w, int64_t(R) * n);
             SIE_LAUNCH_CHECK(p);
@@ -1061,7 +1064,7 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
             if (!any_run) break;
             GM_CUDA(cudaMemcpyAsync(act, run.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             // w = P^-1 Z v_k
-            GM_RC(apply_op(V + int64_t(k) * kstride, w));
+            GM_RC(apply_op(V + int64_t(k) * kstride, w, opts->prec));
             matvecs += R;
             std::vector<double2> h1, h2;
             GM_RC(dots(w, k + 1, h1));   // CGS pass 1
@@ -1127,8 +1130,11 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
         SIE_LAUNCH_CHECK(p);
         GM_CUDA(cudaStreamSynchronize(st));
         cudaFree(dy);
-        for (int32_t r = 0; r < R; ++r)
-            if (active[r] && resid[r] < opts->tol) done[r] = 1;
+        // without refinement the cycle's residual estimate decides; with it the
+        // FP64 residual at the top of the next restart does
+        if (!refine)
+            for (int32_t r = 0; r < R; ++r)
+                if (active[r] && resid[r] < opts->tol) done[r] = 1;
         bool cont = false;
         for (int32_t r = 0; r < R; ++r) cont |= !done[r] && iters[r] < opts->max_iter;
         if (!cont) break;

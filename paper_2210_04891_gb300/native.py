@@ -49,7 +49,7 @@ class PfftParams(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("precond", ctypes.c_int32), ("prec", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("prec", ctypes.c_int32), ("refine", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):

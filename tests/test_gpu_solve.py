@@ -108,6 +108,25 @@ def test_solve_mixed_precision():
     assert np.abs(Z32 - Z64).max() < 1e-4 * np.abs(Z64).max()
 
 
+def test_solve_mixed_with_fp64_refinement_matches_fp64():
+    """Iterative refinement (FP64 restart residuals, mixed Arnoldi cycles):
+    the mixed solve converges on the true FP64 residual, so its Z agrees with
+    the FP64 solve far more closely than the mixed solve alone."""
+    m = synth.tiny_wires()
+    O, S, P = make(m, P_WIRES)
+    freqs = np.array([1e8, 3e9])
+    Z64, st64 = api.sie_solve(P, freqs, tol=1e-10, restart=60, prec=PREC_FP64)
+    Zir, st = api.sie_solve(P, freqs, tol=1e-10, restart=60, prec=PREC_MIXED, refine=True)
+    assert st["converged"] and st["residual_max"] < 1e-10
+    assert np.abs(Zir - Z64).max() < 1e-8 * np.abs(Z64).max()
+    # the refined solve alternates precisions on one plan: FP64 matvecs still match the oracle
+    om = 2 * np.pi * np.array([2e9])
+    x = synth.complex_gaussian(O.nl, 1, seed=5)
+    y = api.pfft_matvec(P, torch.from_numpy(x).cuda(), om).cpu().numpy()
+    ref = S.matvec(x[0], om[0])
+    assert np.linalg.norm(y[0] - ref) < 1e-10 * np.linalg.norm(ref)
+
+
 def test_solve_without_preconditioner_needs_more_iterations():
     m = synth.tiny_wires()
     O, S, P = make(m, P_WIRES)
