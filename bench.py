@@ -61,6 +61,12 @@ def peaks():
 
 SM_COUNT, FP32_LANES_PER_SM = 152, 128      # GB300: 2 dies x 76 SMs, 128 FP32 FMA lanes per SM
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu capture of the
+# current kernel, with the number of grids (3 x right-hand sides) of that capture; the
+# figure is scaled to a launch of the bench by grids.  Only kernels captured since their
+# last change are listed.
+MEASURED_TRAFFIC = {"fft_yz": (345.96e6, 48)}   # k_fft_yzc<float, 512>, 2 frequencies x 8 ports
+
 
 def alu_peak_tflops(sm_mhz):
     """FP32 FMA peak of the CUDA cores: SMs x lanes x 2 flop x SM clock."""
@@ -344,8 +350,12 @@ def main():
             mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
             achieved, peak, u = amount / sec / 1e12, alu_peak_tflops(mhz), "TFLOP/s"
             psrc = f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {mhz:.0f} MHz"
+        traffic = None
+        if dom in MEASURED_TRAFFIC:
+            tb, grids = MEASURED_TRAFFIC[dom]
+            traffic = tb * (3 * R) / grids
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": u, "frac": achieved / peak,
-                    "traffic": None, "kernel": dom, "peak_source": psrc,
+                    "traffic": traffic, "kernel": dom, "peak_source": psrc,
                     "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": ms_dom / n_dom}
         for s in stage_table:
             wk = stage_work(s, ctx)
