@@ -208,6 +208,20 @@ int pfft_plan_export(const pfft_plan *p, int32_t what, void *host_out, int64_t c
  * d = 0) via the zero-padded FFT. */
 int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream);
 
+/* Step 2 of Sec. IV-B with the lossy-conductor kernel instead of the static one:
+ * phi_g = H_k Q_g with H_k(d) = exp(-j k R) / R, R = |d o h| (h0 at d = 0),
+ * k = (1 - j) / delta and delta = sqrt(2 / (omega mu0 sigma)) the skin depth,
+ * in the e^{j w t} convention of Z_s (Eq. ImpedanceOp), so |H_k| decays as
+ * exp(-R / delta) and H_k -> 1/R as omega -> 0.  The paper states only the
+ * static Green's function (Eq. StaticGF); this is the interior-region kernel of
+ * the same MQS equations, for lossy-region variants of the method.  Grids,
+ * layout and padding as pfft_convolve (nbatch grids, in place).  The complex
+ * kernel spectrum is built (FP64) on first use of an (omega, sigma) pair and
+ * kept until another pair is asked for.  Errors: SIE_ERR_ARG for omega or sigma
+ * not finite and positive. */
+int pfft_convolve_lossy(pfft_plan *p, void *grid, int32_t nbatch, double omega, double sigma, int32_t prec,
+                        void *cuda_stream);
+
 /* pfft_convolve without any device allocation (the paper has no counterpart;
  * this is an interface for callers that may not allocate device memory when
  * they convolve: fixed start-up memory budgets, real-time loops that cannot

@@ -200,6 +200,19 @@ def pfft_convolve(plan: Plan, grid, prec=N.PREC_FP64, stream=None):
     return grid
 
 
+def pfft_convolve_lossy(plan: Plan, grid, omega, sigma, prec=N.PREC_FP64, stream=None):
+    """phi_g = H_k Q_g in place with the lossy kernel exp(-jkR)/R, k = (1 - j)/delta (skin depth
+    delta of sigma at omega), grid [nbatch, N_x, N_y, N_z] (complex128 or complex64)."""
+    import torch
+    g = plan.params["grid"]
+    want = torch.complex128 if prec == N.PREC_FP64 else torch.complex64
+    if not (grid.is_cuda and grid.dtype == want and grid.is_contiguous() and tuple(grid.shape[1:]) == tuple(g)):
+        raise ValueError("grid must be a contiguous CUDA tensor [nbatch, N_x, N_y, N_z] of the precision's dtype")
+    check(lib().pfft_convolve_lossy(plan.h, ctypes.c_void_p(grid.data_ptr()), grid.shape[0], float(omega),
+                                    float(sigma), prec, _stream(stream)))
+    return grid
+
+
 def pfft_precond_apply(plan: Plan, y, omega, out=None, prec=N.PREC_FP64, stream=None):
     """z = P(omega)^-1 y, P = A diag(Z_b) A^T, for y [nrhs, n_loops]."""
     import torch

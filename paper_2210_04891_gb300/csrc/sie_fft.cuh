@@ -511,8 +511,12 @@ __device__ __forceinline__ void yz_i4(const C<T> *P, C<T> *out, int pitch, int N
 // CW = blockDim / N1 complete kz columns (every k1 of them), so all reads of a
 // column precede all writes to it; lanes run over kz (conflict-free).
 // Hk: this kx's kernel spectrum [fold(ky)][fold(kz)], pitch Mz/2 + 1.
-template <typename T, int N1, int N2>
-__device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const T *__restrict__ Hk,
+// v times a kernel value: real (static kernel) or complex (lossy kernel).
+template <typename T> __device__ __forceinline__ C<T> hmul(C<T> v, T h) { return cscale(v, h); }
+template <typename T> __device__ __forceinline__ C<T> hmul(C<T> v, C<T> h) { return cmul(v, h); }
+
+template <typename T, int N1, int N2, typename HT>
+__device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const HT *__restrict__ Hk,
                                        const C<T> *__restrict__ tiy) {
     constexpr int My = N1 * N2;
     const int Mz = 1 << lgMz, hz = Mz / 2 + 1;
@@ -527,9 +531,9 @@ __device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const T *__
 #pragma unroll
             for (int j2 = 0; j2 < N2; ++j2) v[j2] = col[j2 * pitch];
             dft_reg<T, N2, false>(v);      // v[k2] = X[ky = k1 + N1 k2]
-            const T *h = Hk + fold_index(kz, Mz);
+            const HT *h = Hk + fold_index(kz, Mz);
 #pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], h[fold_index(k1 + N1 * k2, My) * hz]);
+            for (int k2 = 0; k2 < N2; ++k2) v[k2] = hmul<T>(v[k2], h[fold_index(k1 + N1 * k2, My) * hz]);
             dft_reg<T, N2, true>(v);
             const C<T> *t = tiy + k1 * N2;
 #pragma unroll
@@ -558,10 +562,11 @@ __device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const T *__
 // every step reads one and writes the other.  One CTA per (batch, kx), NT
 // threads (512 in FP32: two CTAs and 32 warps per SM; 256 in FP64, whose
 // plane fills the shared memory of one SM).
-// Hp: kernel spectrum [fold(kx)][fold(ky)][fold(kz)], scaled by 1/(Mx My Mz).
-template <typename T, int NT>
+// Hp: kernel spectrum [fold(kx)][fold(ky)][fold(kz)], scaled by 1/(Mx My Mz):
+// real (HT = T, the static kernel) or complex (HT = C<T>, the lossy kernel).
+template <typename T, int NT, typename HT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fft_yzc(C<T> *__restrict__ buf, int lgMx, int My, int Mz,
-                                                 const T *__restrict__ Hp, const C<T> *__restrict__ tfy,
+                                                 const HT *__restrict__ Hp, const C<T> *__restrict__ tfy,
                                                  const C<T> *__restrict__ tiy, const C<T> *__restrict__ tfz,
                                                  const C<T> *__restrict__ tiz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -572,14 +577,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fft_yzc(C<T> *__
     C<T> *P = reinterpret_cast<C<T> *>(smem_raw);
     C<T> *Qb = P + My * pitch;
     C<T> *plane = buf + int64_t(blockIdx.x) * Ny * Nz;
-    const T *Hk = Hp + int64_t(fold_index(kx, Mx)) * (My / 2 + 1) * (Mz / 2 + 1);
+    const HT *Hk = Hp + int64_t(fold_index(kx, Mx)) * (My / 2 + 1) * (Mz / 2 + 1);
     SIE_SPLIT_DISPATCH(Mz, (yz_f1<T, N1, N2>(plane, P, pitch, Ny, tfz)));
     __syncthreads();
     SIE_SPLIT_DISPATCH(Mz, (yz_f2<T, N1, N2>(P, Qb, pitch, lgNy)));
     __syncthreads();
     SIE_SPLIT_DISPATCH(My, (yz_f3<T, N1, N2>(Qb, P, pitch, lgMz, tfy)));
     __syncthreads();
-    SIE_SPLIT_DISPATCH(My, (yz_mid<T, N1, N2>(P, pitch, lgMz, Hk, tiy)));
+    SIE_SPLIT_DISPATCH(My, (yz_mid<T, N1, N2, HT>(P, pitch, lgMz, Hk, tiy)));
     SIE_SPLIT_DISPATCH(My, (yz_i2<T, N1, N2>(P, Qb, pitch, lgMz)));
     __syncthreads();
     SIE_SPLIT_DISPATCH(Mz, (yz_i3<T, N1, N2>(Qb, P, pitch, lgNy, tiz)));

@@ -333,6 +333,43 @@ __global__ void k_permute_H(const double *H, double *Hp64, float *Hp32, int hx, 
     Hp32[i] = float(v);
 }
 
+// The lossy kernel exp(-jkR)/R, k = (1 - j)/delta, on the padded grid (same
+// offsets, wrap and zeroed +-N planes as k_fill_kernel):
+// exp(-jkR) = exp(-R/delta) (cos(R/delta) - j sin(R/delta)).
+__global__ void k_fill_kernel_lossy(double2 *Hc, int Mx, int My, int Mz, double hx, double hy, double hz, double h0,
+                                    double inv_delta) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t n = int64_t(Mx) * My * Mz;
+    if (i >= n) return;
+    const int iz = int(i % Mz), iy = int((i / Mz) % My), ix = int(i / (int64_t(My) * Mz));
+    double2 v = make_double2(0.0, 0.0);
+    if (ix != Mx / 2 && iy != My / 2 && iz != Mz / 2) {
+        const int dx = ix < Mx / 2 ? ix : ix - Mx, dy = iy < My / 2 ? iy : iy - My, dz = iz < Mz / 2 ? iz : iz - Mz;
+        if (dx == 0 && dy == 0 && dz == 0) {
+            v = make_double2(h0, 0.0);
+        } else {
+            const double x = double(dx) * hx, y = double(dy) * hy, z = double(dz) * hz;
+            const double r = sqrt(x * x + y * y + z * z);
+            const double a = r * inv_delta, m = exp(-a) / r;
+            double sn, cs;
+            sincos(a, &sn, &cs);
+            v = make_double2(m * cs, -m * sn);
+        }
+    }
+    Hc[i] = v;
+}
+
+// Complex spectrum folded to one octant with kx outermost, [hx][hy][hz], scaled.
+__global__ void k_extract_Hc(const double2 *Hc, double2 *H64, float2 *H32, int Mx, int My, int Mz, double scale) {
+    const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = Mz / 2 + 1;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(hx) * hy * hz) return;
+    const int kz = int(i % hz), ky = int((i / hz) % hy), kx = int(i / (int64_t(hy) * hz));
+    const double2 v = Hc[(int64_t(kx) * My + ky) * Mz + kz];
+    H64[i] = make_double2(v.x * scale, v.y * scale);
+    H32[i] = make_float2(float(v.x * scale), float(v.y * scale));
+}
+
 __global__ void k_branch_diag(const int64_t *ptr, const int32_t *col, const double *Ldir, const int32_t *br_tri,
                               const int8_t *br_local, int64_t nb, double *diagL) {
     int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -392,11 +429,13 @@ template <> struct Tables<double> {
     static const double2 *tf(const pfft_plan *p, int a) { return p->d_tf64[a]; }
     static const double2 *ti(const pfft_plan *p, int a) { return p->d_ti64[a]; }
     static const double *Hp(const pfft_plan *p) { return p->d_Hp64; }
+    static const double2 *Hl(const pfft_plan *p) { return p->d_Hl64; }
 };
 template <> struct Tables<float> {
     static const float2 *tf(const pfft_plan *p, int a) { return p->d_tf32[a]; }
     static const float2 *ti(const pfft_plan *p, int a) { return p->d_ti32[a]; }
     static const float *Hp(const pfft_plan *p) { return p->d_Hp32; }
+    static const float2 *Hl(const pfft_plan *p) { return p->d_Hl32; }
 };
 
 constexpr int kPencilCols = 16;   // columns per x-pencil CTA
@@ -420,8 +459,23 @@ int launch_x(pfft_plan *p, const C<T> *in, C<T> *out, int ngrids, bool inverse, 
     return SIE_OK;
 }
 
+template <typename T, typename HT>
+int launch_yzc(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s) {
+    using Tb = Tables<T>;
+    constexpr int NT = sizeof(T) == 4 ? 512 : 256;
+    const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
+    int rc = set_smem((const void *)k_fft_yzc<T, NT, HT>, plane_bytes);
+    if (rc) return rc;
+    int lgMx = 0;
+    while ((1 << lgMx) < p->Mx) ++lgMx;
+    k_fft_yzc<T, NT, HT><<<unsigned(ngrids * p->Mx), NT, plane_bytes, s>>>(spec, lgMx, p->My, p->Mz, Hp, Tb::tf(p, 1),
+                                                                        Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2));
+    SIE_LAUNCH_CHECK(p);
+    return SIE_OK;
+}
+
 template <typename T>
-int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s) {
+int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s, bool lossy) {
     using Tb = Tables<T>;
     int rc;
     {
@@ -432,16 +486,8 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     }
     {
         StageTimer tm(p, SIE_STAGE_FFT_YZ, s);
-        constexpr int NT = sizeof(T) == 4 ? 512 : 256;
-        const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
-        rc = set_smem((const void *)k_fft_yzc<T, NT>, plane_bytes);
+        rc = lossy ? launch_yzc<T>(p, spec, ngrids, Tb::Hl(p), s) : launch_yzc<T>(p, spec, ngrids, Tb::Hp(p), s);
         if (rc) return rc;
-        int lgMx = 0;
-        while ((1 << lgMx) < p->Mx) ++lgMx;
-        k_fft_yzc<T, NT><<<unsigned(ngrids * p->Mx), NT, plane_bytes, s>>>(spec, lgMx, p->My, p->Mz, Tb::Hp(p),
-                                                                            Tb::tf(p, 1), Tb::ti(p, 1), Tb::tf(p, 2),
-                                                                            Tb::ti(p, 2));
-        SIE_LAUNCH_CHECK(p);
     }
     StageTimer tm(p, SIE_STAGE_FFT_X_INV, s);
     SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x<T, N1, N2>(p, spec, grid, ngrids, true, s)));
@@ -450,9 +496,9 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     return SIE_OK;
 }
 
-int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s) {
-    if (prec == SIE_PREC_FP64) return fft_conv_t<double>(p, (double2 *)grid, (double2 *)spec, ngrids, s);
-    return fft_conv_t<float>(p, (float2 *)grid, (float2 *)spec, ngrids, s);
+int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s, bool lossy) {
+    if (prec == SIE_PREC_FP64) return fft_conv_t<double>(p, (double2 *)grid, (double2 *)spec, ngrids, s, lossy);
+    return fft_conv_t<float>(p, (float2 *)grid, (float2 *)spec, ngrids, s, lossy);
 }
 
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s) {
@@ -982,6 +1028,68 @@ extern "C" int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t p
         const size_t gb = size_t(p->Ng) * (prec == SIE_PREC_FP64 ? 16 : 8);
         for (int32_t b = 0; b < nbatch && !rc; ++b) rc = fft_conv_n(p, (char *)grid + b * gb, p->scr.spec, 1, prec, s);
     }
+    if (rc) return rc;
+    SIE_CUDA(cudaStreamSynchronize(s));
+    return SIE_OK;
+}
+
+namespace sie {
+// Spectrum of the lossy kernel for (omega, sigma), kept until another pair is asked for.
+int lossy_spectrum(pfft_plan *p, double omega, double sigma, cudaStream_t s) {
+    if (p->d_Hl64 && p->lossy_omega == omega && p->lossy_sigma == sigma) return SIE_OK;
+    const int64_t nM = int64_t(p->Mx) * p->My * p->Mz;
+    const int64_t nh = int64_t(p->Mx / 2 + 1) * (p->My / 2 + 1) * (p->Mz / 2 + 1);
+    int rc;
+    if (!p->d_Hl64) {
+        if ((rc = plan_alloc(p, (void **)&p->d_Hl64, nh * sizeof(double2)))) return rc;
+        if ((rc = plan_alloc(p, (void **)&p->d_Hl32, nh * sizeof(float2)))) return rc;
+    }
+    double2 *d_Hc = nullptr, *d_Hc2 = nullptr;
+    if ((rc = plan_alloc(p, (void **)&d_Hc, nM * sizeof(double2)))) return rc;
+    if ((rc = plan_alloc(p, (void **)&d_Hc2, nM * sizeof(double2)))) { plan_free(p, d_Hc); return rc; }
+    auto done = [&](int r) { plan_free(p, d_Hc); plan_free(p, d_Hc2); return r; };
+    const double mu0 = 4e-7 * M_PI;
+    const double inv_delta = std::sqrt(omega * mu0 * sigma / 2.0);   // 1/delta, delta the skin depth
+    k_fill_kernel_lossy<<<unsigned((nM + 255) / 256), 256, 0, s>>>(d_Hc, p->Mx, p->My, p->Mz, p->h[0], p->h[1],
+                                                                   p->h[2], p->params.h0, inv_delta);
+    p->launches++;
+    const size_t pbytes = size_t(p->My) * p->Mz * sizeof(double2);
+    if ((rc = set_smem((const void *)k_fft_plane<double>, pbytes))) return done(rc);
+    k_fft_plane<double><<<p->Mx, fft_threads(p->My * p->Mz), pbytes, s>>>(
+        d_Hc, int64_t(p->My) * p->Mz, p->My, p->Mz, d_Hc2, int64_t(p->My) * p->Mz, p->My, p->Mz, p->My, p->Mz,
+        p->d_tw64[1], p->d_tw64[2], 0);
+    p->launches++;
+    const int KT = 16, ncols = p->My * p->Mz;
+    const size_t kb = size_t(KT) * (p->Mx + 1) * sizeof(double2);
+    if ((rc = set_smem((const void *)k_fft_pencil<double>, kb))) return done(rc);
+    k_fft_pencil<double><<<ncols / KT, fft_threads(KT * p->Mx), kb, s>>>(d_Hc2, 0, ncols, p->Mx, p->Mx, p->Mx, p->My,
+                                                                       p->Mz, KT, p->d_tw64[0], nullptr);
+    p->launches++;
+    k_extract_Hc<<<unsigned((nh + 255) / 256), 256, 0, s>>>(d_Hc2, p->d_Hl64, p->d_Hl32, p->Mx, p->My, p->Mz,
+                                                          1.0 / double(nM));
+    p->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(fail(SIE_ERR_CUDA, std::string("lossy spectrum: ") + cudaGetErrorString(e)));
+    p->lossy_omega = omega;
+    p->lossy_sigma = sigma;
+    return done(SIE_OK);
+}
+}  // namespace sie
+
+extern "C" int pfft_convolve_lossy(pfft_plan *p, void *grid, int32_t nbatch, double omega, double sigma, int32_t prec,
+                                   void *cuda_stream) {
+    if (!p || !grid || nbatch < 1) return fail(SIE_ERR_ARG, "pfft_convolve_lossy: bad argument");
+    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "pfft_convolve_lossy: bad precision");
+    if (!(omega > 0.0) || !std::isfinite(omega) || !(sigma > 0.0) || !std::isfinite(sigma))
+        return fail(SIE_ERR_ARG, "pfft_convolve_lossy: omega and sigma must be finite and > 0");
+    (void)cudaGetLastError();
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int rc = lossy_spectrum(p, omega, sigma, s);
+    if (rc) return rc;
+    rc = scratch_reserve(p, (nbatch + 2) / 3, prec);   // its x-transform buffer holds 3 grids per right-hand side
+    if (rc) return rc;
+    rc = fft_conv_n(p, grid, p->scr.spec, nbatch, prec, s, true);
     if (rc) return rc;
     SIE_CUDA(cudaStreamSynchronize(s));
     return SIE_OK;

@@ -95,6 +95,10 @@ struct pfft_plan {
     // the same spectrum with kx outermost: [Mx/2+1][My/2+1][Mz/2+1]
     double *d_Hp64 = nullptr;
     float *d_Hp32 = nullptr;
+    // lossy kernel exp(-jkR)/R: complex spectrum of the last (omega, sigma), same layout
+    double lossy_omega = -1.0, lossy_sigma = -1.0;
+    double2 *d_Hl64 = nullptr;
+    float2 *d_Hl32 = nullptr;
     // loop basis on the device
     int32_t *d_tour_node = nullptr;     // [2 nn]
     int8_t *d_tour_enter = nullptr;     // [2 nn]
@@ -151,7 +155,8 @@ void plan_free_precond(pfft_plan *p);
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
-int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s);
+int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s,
+               bool lossy = false);
 int near_mma_prepare(pfft_plan *p, const std::vector<int64_t> &near_ptr, const std::vector<int32_t> &near_col,
                      cudaStream_t s);
 int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st);
