@@ -465,6 +465,9 @@ __device__ __forceinline__ void yz_i2(const C<T> *P, C<T> *Q, int pitch, int lgM
         for (int p1 = 0; p1 < H1; ++p1) o[N2 * p1 * pitch] = v[p1];
     }
 }
+// I3 writes row slot p2 + N2 k1 (not k1 + N1 p2) so that I4's threads, which
+// run over p2 with k1 fixed per load, read consecutive slots: both passes hit
+// distinct shared-memory banks.
 template <typename T, int N1, int N2>   // I3: z inverse pass A, Q rows -> P row slots
 __device__ __forceinline__ void yz_i3(const C<T> *Q, C<T> *P, int pitch, int lgNy, const C<T> *tiz) {
     C<T> v[FFT_NMAX];
@@ -476,7 +479,7 @@ __device__ __forceinline__ void yz_i3(const C<T> *Q, C<T> *P, int pitch, int lgN
         for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[N1 * k2];
         dft_reg<T, N2, true>(v);
         const C<T> *t = tiz + k1 * N2;
-        C<T> *o = P + y * pitch + k1;
+        C<T> *o = P + y * pitch + k1 * N2;
 #pragma unroll
         for (int p2 = 0; p2 < N2; ++p2) {
             C<T> r = v[p2];
@@ -485,7 +488,7 @@ __device__ __forceinline__ void yz_i3(const C<T> *Q, C<T> *P, int pitch, int lgN
                 r.x = v[p2].x * w.x + v[p2].y * w.y;
                 r.y = v[p2].y * w.x - v[p2].x * w.y;
             }
-            o[p2 * N1] = r;
+            o[p2] = r;
         }
     }
 }
@@ -496,9 +499,9 @@ __device__ __forceinline__ void yz_i4(const C<T> *P, C<T> *out, int pitch, int N
     C<T> v[FFT_NMAX];
     for (int it = threadIdx.x; it < Ny * N2; it += blockDim.x) {
         const int y = it >> LG2, p2 = it & (N2 - 1);
-        const C<T> *src = P + y * pitch + p2 * N1;
+        const C<T> *src = P + y * pitch + p2;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[k1];
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[k1 * N2];
         dft_reg<T, N1, true>(v);
         C<T> *o = out + y * Nz + p2;
 #pragma unroll

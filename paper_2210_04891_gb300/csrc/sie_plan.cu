@@ -462,7 +462,8 @@ int launch_x(pfft_plan *p, const C<T> *in, C<T> *out, int ngrids, bool inverse, 
 template <typename T, typename HT>
 int launch_yzc(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s) {
     using Tb = Tables<T>;
-    constexpr int NT = sizeof(T) == 4 ? 512 : 256;
+    // 512 threads for the FP32 static kernel (64 registers); the complex kernel value needs more
+    constexpr int NT = (sizeof(T) == 4 && sizeof(HT) == sizeof(T)) ? 512 : 256;
     const size_t plane_bytes = size_t(p->My + p->Ny) * (p->Mz + 1) * sizeof(C<T>);
     int rc = set_smem((const void *)k_fft_yzc<T, NT, HT>, plane_bytes);
     if (rc) return rc;

@@ -537,17 +537,37 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
     C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_CH * PC_CH;   // [warp][2][32][32]
     C<T> *buf1 = buf0 + PC_CH * PC_CH;
     for (int t = lane; t < 2 * PC_CH * PC_CH; t += 32) buf0[t] = zero;
-    // right-hand sides of the nodal system
+    // right-hand sides of the nodal system; four rows per lane and step so that
+    // their gathers overlap (a triangle node has up to three branches)
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
         if (k >= nr) break;
         const double2 *kr = kappa + int64_t(r0 + k) * nb;
         C<T> *x = xs + int64_t(r0 + k) * nunk + o;
-        for (int64_t i = lane; i < n; i += 32) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int32_t q = row_ptr[o + i]; q < row_ptr[o + i + 1]; ++q)
-                acc = row_sg[q] > 0 ? csub(acc, kr[row_br[q]]) : cadd(acc, kr[row_br[q]]);
-            x[i] = mk<T>(T(acc.x), T(acc.y));
+        for (int64_t i0 = lane; i0 < n; i0 += 4 * 32) {
+            int32_t qa[4], qb[4];
+            double2 acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + 32 * u;
+                qa[u] = i < n ? row_ptr[o + i] : 0;
+                qb[u] = i < n ? row_ptr[o + i + 1] : 0;
+                acc[u] = make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t q = qa[u] + d;
+                    if (q < qb[u]) acc[u] = row_sg[q] > 0 ? csub(acc[u], kr[row_br[q]]) : cadd(acc[u], kr[row_br[q]]);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                for (int32_t q = qa[u] + 3; q < qb[u]; ++q)   // contact nodes: many branches
+                    acc[u] = row_sg[q] > 0 ? csub(acc[u], kr[row_br[q]]) : cadd(acc[u], kr[row_br[q]]);
+                const int64_t i = i0 + 32 * u;
+                if (i < n) x[i] = mk<T>(T(acc[u].x), T(acc[u].y));
+            }
         }
     }
     __syncwarp();
@@ -572,6 +592,8 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
             const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
             pn[k] = base + 64 + lane < n ? x[base + 64 + lane] : zero;
         }
+        // pivot of the row this lane finishes in chunk c (the diagonal step is applied at the store)
+        const C<T> dg = base + lane < n ? B[(base + lane) * Wp] : mk<T>(T(1), T(0));
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
         const C<T> *bs = (c & 1) ? buf1 : buf0;
@@ -581,28 +603,20 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
         } else {
             for (int j = 0; j < int(n - base); ++j) pc_step<T, RB>(bs, j, j, lane, w, pf, done);
         }
+        {
+            const T den = dg.x * dg.x + dg.y * dg.y;
+            const C<T> inv = mk<T>(dg.x / den, -dg.y / den);
 #pragma unroll
-        for (int k = 0; k < RB; ++k) {
-            if (k < nr && base + lane < n) xs[int64_t(r0 + k) * nunk + o + base + lane] = done[k];
-            pf[k] = pn[k];
+            for (int k = 0; k < RB; ++k) {
+                if (k < nr && base + lane < n) xs[int64_t(r0 + k) * nunk + o + base + lane] = cmul(done[k], inv);
+                pf[k] = pn[k];
+            }
         }
         __syncwarp();
         pc_stage32<T>((c & 1) ? buf1 : buf0, Bc, base + 2 * PC_CH, W, n, lane);
         asm volatile("cp.async.commit_group;\n" ::);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncwarp();
-    // ---------------- diagonal
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-        if (k >= nr) break;
-        C<T> *x = xs + int64_t(r0 + k) * nunk + o;
-        for (int64_t i = lane; i < n; i += 32) {
-            const C<T> dg = B[i * Wp];
-            const T den = dg.x * dg.x + dg.y * dg.y;
-            x[i] = cmul(x[i], mk<T>(dg.x / den, -dg.y / den));
-        }
-    }
     __syncwarp();
     // ---------------- backward: x_{i-d} -= L[i][i-d] x_i   (chunk c = steps i = n-1-32c-j)
     // staged rows of chunk c: [n - 32(c+1), n - 32c), row i at index i - (n - 32(c+1))
@@ -634,8 +648,9 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
             for (int j = 0; j <= int(top); ++j) pc_step<T, RB>(bs, j, PC_CH - 1 - j, lane, w, pf, done);
         }
 #pragma unroll
-        for (int k = 0; k < RB; ++k) {
-            if (k < nr && top - lane >= 0) xs[int64_t(r0 + k) * nunk + o + top - lane] = done[k];
+        for (int k = 0; k < RB; ++k) {   // final values straight to the FP64 solution
+            if (k < nr && top - lane >= 0)
+                u[int64_t(r0 + k) * nunk + o + top - lane] = make_double2(double(done[k].x), double(done[k].y));
             pf[k] = pn[k];
         }
         __syncwarp();
@@ -643,16 +658,6 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
         asm volatile("cp.async.commit_group;\n" ::);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncwarp();
-    if (sizeof(T) != sizeof(double)) {
-#pragma unroll
-        for (int k = 0; k < RB; ++k) {
-            if (k >= nr) break;
-            const C<T> *x = xs + int64_t(r0 + k) * nunk + o;
-            double2 *xd = u + int64_t(r0 + k) * nunk + o;
-            for (int64_t i = lane; i < n; i += 32) xd[i] = make_double2(double(x[i].x), double(x[i].y));
-        }
-    }
 }
 
 // Branch currents i_e = a_e (phi_tail - phi_head + emf_e) = a_e (u_t - u_h) + kappa_e.
