@@ -84,17 +84,28 @@ def stage_work(stage, c):
     Ng, Nx, My, Mz, nt, nl = c["Ng"], c["Nx"], c["My"], c["Mz"], c["nt"], c["nl"]
     if stage == "fft_x_fwd":          # grid read, x-padded grid written
         return "hbm", 3 * R * (Ng + 2 * Ng) * cb, "B"
-    if stage == "fft_yz":             # x-padded grid read and written, kernel slice per plane
-        return "hbm", 3 * R * 4 * Ng * cb + (Nx + 1) * (My // 2 + 1) * (Mz // 2 + 1) * cb // 2, "B"
+    if stage == "fft_yz":
+        # per x-frequency plane: forward and inverse My x Mz complex FFTs at the standard
+        # 5 N log2 N flops each, and the real kernel product (2 flops per point); the kernel
+        # is instruction-issue bound (ncu), not HBM bound (its bytes: 3R * 4 N_g * c)
+        npl = My * Mz
+        return "alu", 3 * R * 2 * Nx * (2 * 5 * npl * np.log2(npl) + 2 * npl), "flop"
     if stage == "fft_x_inv":          # x-padded grid read, grid written
         return "hbm", 3 * R * (2 * Ng + Ng) * cb, "B"
     if stage == "project":
         # c_T read, node-ordered block records read, grid written
         return "hbm", R * nt * 3 * cb + c["n_pair"] * c["rec"] + (Ng + 1) * 8 + 3 * R * Ng * cb, "B"
     if stage == "interp":
-        # potentials of the nodes in use read and written once
-        return "hbm", 2 * 3 * R * c["n_active"] * cb, "B"
+        # regroup: potentials of the nodes in use read and written once; far gather (mixed
+        # form): those potentials and the triangle-ordered blocks read, the far field written
+        b = 2 * 3 * R * c["n_active"] * cb
+        if c.get("mixed", True):
+            b += 3 * R * c["n_active"] * cb + c["n_pair"] * c["rec"] + R * nt * 3 * cb
+        return "hbm", b, "B"
     if stage == "near":
+        if c.get("mixed", True) and R % 2 == 0:
+            # tensor cores (split tf32): the near 3x3 blocks times complex right-hand sides
+            return "tensor", 36 * R * c["n_near"], "flop"
         return "alu", 36 * R * (c["n_near"] + c["n_pair"]), "flop"
     if stage == "loop_to_branch":
         return "hbm", R * nl * 16 + R * nt * 3 * cb, "B"
@@ -346,6 +357,10 @@ def main():
         sec = ms_dom / n_dom / 1e3
         if bound == "hbm":
             achieved, peak, u, psrc = amount / sec / 1e9, hbm, "GB/s", src
+        elif bound == "tensor":
+            # tf32 dense peak = measured bf16 burst peak x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s)
+            achieved, peak, u = amount / sec / 1e12, (bf16 or 1900.0) * 1.1 / 2.25, "TFLOP/s"
+            psrc = f"{src} bf16 x 1.1/2.25 (tf32 nominal ratio)"
         else:
             mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
             achieved, peak, u = amount / sec / 1e12, alu_peak_tflops(mhz), "TFLOP/s"
@@ -363,6 +378,7 @@ def main():
                 sec = stage_table[s]["ms_per_step"] * K / stage_table[s]["launch_groups"] / 1e3
                 stage_table[s]["bound"] = wk[0]
                 stage_table[s]["achieved"] = wk[1] / sec / (1e9 if wk[0] == "hbm" else 1e12)
+                stage_table[s]["achieved_unit"] = "GB/s" if wk[0] == "hbm" else "TFLOP/s"
 
     # end to end through host buffers (pinned)
     xh = x.cpu().pin_memory()
