@@ -1,0 +1,73 @@
+// Double-float arithmetic for the mixed form's loop/branch maps.
+//
+// The loop-space product sums triangle and branch voltages around loops and
+// subtree currents along the spanning tree; those sums cancel strongly, so the
+// values after the FP32 field computation are carried in more than FP32
+// precision.  A double-float value is an unevaluated pair hi + lo of FP32
+// numbers (about 48 significant bits); sums and products use the error-free
+// transformations two-sum (Knuth) and two-product (one FMA), which run on the
+// FP32 pipe.  GB300's FP64 rate is a small fraction of its FP32 rate, so this
+// keeps FP64's cancellation safety at FP32 cost.  A complex value is a float4
+// (re_hi, re_lo, im_hi, im_lo), the size of a complex128.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sie {
+
+struct DD {
+    float hi, lo;
+};
+
+// a + b exactly: hi = fl(a + b), lo the rounding error.
+__device__ __forceinline__ DD two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return DD{s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+    const DD s = two_sum(a.hi, b.hi);
+    const float e = s.lo + (a.lo + b.lo);
+    const float hi = s.hi + e;
+    return DD{hi, e - (hi - s.hi)};
+}
+
+__device__ __forceinline__ DD dd_neg(DD a) { return DD{-a.hi, -a.lo}; }
+
+// a * b for a double-float a and an FP32 b (a.hi * b exactly by one FMA).
+__device__ __forceinline__ DD dd_mul(DD a, float b) {
+    const float p = a.hi * b;
+    const float e = fmaf(a.hi, b, -p) + a.lo * b;
+    const float hi = p + e;
+    return DD{hi, e - (hi - p)};
+}
+
+__device__ __forceinline__ DD dd_mul(DD a, DD b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+    const float hi = p + e;
+    return DD{hi, e - (hi - p)};
+}
+
+__device__ __forceinline__ DD dd_from(double d) {
+    const float hi = __double2float_rn(d);
+    return DD{hi, __double2float_rn(d - double(hi))};
+}
+
+__device__ __forceinline__ float4 cdd(DD re, DD im) { return make_float4(re.hi, re.lo, im.hi, im.lo); }
+__device__ __forceinline__ DD cdd_re(float4 v) { return DD{v.x, v.y}; }
+__device__ __forceinline__ DD cdd_im(float4 v) { return DD{v.z, v.w}; }
+
+// One local voltage of Eq. Zb from FP32 field values, carried in double-float:
+//   Re y = zr gr - zi gi - cl fi,   Im y = zr gi + zi gr + cl fr,
+// with (zr, zi) = Z_s and cl = c_L given as (hi, lo) pairs, g the Gram term and
+// f the inductive term.
+__device__ __forceinline__ float4 dd_zb(float2 zr, float2 zi, float2 cl, float gr, float gi, DD fr, DD fi) {
+    const DD Zr{zr.x, zr.y}, Zi{zi.x, zi.y}, Cl{cl.x, cl.y};
+    const DD re = dd_add(dd_add(dd_mul(Zr, gr), dd_neg(dd_mul(Zi, gi))), dd_neg(dd_mul(Cl, fi)));
+    const DD im = dd_add(dd_add(dd_mul(Zr, gi), dd_mul(Zi, gr)), dd_mul(Cl, fr));
+    return cdd(re, im);
+}
+
+}  // namespace sie

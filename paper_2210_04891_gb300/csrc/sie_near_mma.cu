@@ -25,14 +25,16 @@
 //   warp 0     producer: bulk copies of the compact operands, 6-stage raw ring
 //   warp 1     TMEM owner (2 accumulators x 256 columns) and MMA issuer
 //   warps 2-5  converters: raw ring -> split, MMA-layout images (3-stage ring)
-//   warps 6-9  epilogue: accumulator -> + far field + Z_s Gram term -> y_T,
-//              overlapping the next item's MMAs (double-buffered TMEM)
+//   warps 6-9  epilogue: accumulator -> + far field + Z_s Gram term -> y_T
+//              (double-float complex), overlapping the next item's MMAs
+//              (double-buffered TMEM)
 // Every wait is bounded (2 s); a wait that runs out sets the plan's error
 // flag, the role stops, and the CTA still drains its MMAs and frees its TMEM.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
+#include "sie_dd.cuh"
 #include "sie_plan.h"
 #include "sie_tc.cuh"
 
@@ -64,12 +66,12 @@ struct NearMmaArgs {
     const float2 *cT;         // [nt][3][R]
     const double *gram;       // [nt][3][3]
     const int32_t *cond;      // [nt]
-    const double *coef;       // [R][2 ncond + 1]
+    const float2 *coef;       // [R][2 ncond + 1] double-float (hi, lo)
     int ncond;
     int64_t nt;
     int32_t R;                // even
     int32_t ntiles, nslab;
-    double2 *y_tri;           // [R][nt][3]
+    float4 *y_tri;            // [R][nt][3] double-float complex
     int *err;
 };
 
@@ -260,16 +262,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int32_t r = r0 + i0 + i + e;
-                        const float fr = v[2 * (i + e)] + (e ? f2.z : f2.x);
-                        const float fi = v[2 * (i + e) + 1] + (e ? f2.w : f2.y);
+                        // near + far exactly, as a double-float
+                        const DD fr = two_sum(v[2 * (i + e)], e ? f2.z : f2.x);
+                        const DD fi = two_sum(v[2 * (i + e) + 1], e ? f2.w : f2.y);
                         const float gr = G[0] * (e ? x0.z : x0.x) + G[1] * (e ? x1.z : x1.x) + G[2] * (e ? x2.z : x2.x);
                         const float gi = G[0] * (e ? x0.w : x0.y) + G[1] * (e ? x1.w : x1.y) + G[2] * (e ? x2.w : x2.y);
-                        const double *cf = a.coef + int64_t(r) * ldc;
-                        const double zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * a.ncond];
-                        // Z_s * gram + j c_L * (near + far), combined in FP64
+                        const float2 *cf = a.coef + int64_t(r) * ldc;
+                        // Z_s * gram + j c_L * (near + far), combined in double-float
                         a.y_tri[(int64_t(r) * a.nt + t) * 3 + k] =
-                            make_double2(zr * double(gr) - zi * double(gi) - cl * double(fi),
-                                         zr * double(gi) + zi * double(gr) + cl * double(fr));
+                            dd_zb(cf[2 * cd], cf[2 * cd + 1], cf[2 * a.ncond], gr, gi, fr, fi);
                     }
                 }
             }
@@ -378,8 +379,8 @@ int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st) {
     Scratch &s = p->scr;
     const int32_t nslab = (R + kSlabRhs - 1) / kSlabRhs;
     NearMmaArgs a{p->d_nm_uptr, p->d_nm_utri, p->d_nm_A, (const float2 *)s.ffar, (const float2 *)s.cT,
-                  p->d_gram, p->d_cond, s.coef, p->ncond, p->nt, R, int32_t(p->nm_tiles), nslab,
-                  (double2 *)s.y_tri, p->d_err};
+                  p->d_gram, p->d_cond, coef_dd(p), p->ncond, p->nt, R, int32_t(p->nm_tiles), nslab,
+                  (float4 *)s.y_tri, p->d_err};
     const int64_t items = p->nm_tiles * nslab;
     k_near_mma<<<unsigned(std::min<int64_t>(items, nsm)), kThreads, kSmemBytes, st>>>(a);
     SIE_LAUNCH_CHECK(p);

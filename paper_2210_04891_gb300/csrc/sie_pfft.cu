@@ -24,8 +24,10 @@
 #include <algorithm>
 #include <cmath>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
+#include "sie_dd.cuh"
 #include "sie_plan.h"
 
 using namespace sie;
@@ -41,49 +43,81 @@ template <typename V> __device__ __forceinline__ V shfl_up(V v, int d) {
     return o;
 }
 
-// Inclusive prefix sum of each row (complex128) of a [R][n] array, in place.
+// Elements of the loop/branch maps after the field computation: complex128 in
+// the FP64 form, double-float float4 (sie_dd.cuh) in the mixed form.
+template <typename T> using TourE = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+
+__device__ __forceinline__ double2 eadd(double2 a, double2 b) { return cadd(a, b); }
+__device__ __forceinline__ float4 eadd(float4 a, float4 b) {
+    return cdd(dd_add(cdd_re(a), cdd_re(b)), dd_add(cdd_im(a), cdd_im(b)));
+}
+__device__ __forceinline__ double2 eneg(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ float4 eneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+template <typename E> __device__ __forceinline__ E ezero();
+template <> __device__ __forceinline__ double2 ezero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float4 ezero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// conversions: FP64 value -> element; element -> FP64, FP32 or another element type
+__device__ __forceinline__ void eset(double2 &e, double2 v) { e = v; }
+__device__ __forceinline__ void eset(float4 &e, double2 v) { e = cdd(dd_from(v.x), dd_from(v.y)); }
+__device__ __forceinline__ void eset(double2 &e, float4 v) {
+    e = make_double2(double(v.x) + double(v.y), double(v.z) + double(v.w));
+}
+__device__ __forceinline__ void eset(float4 &e, float4 v) { e = v; }
+__device__ __forceinline__ double2 to_c(double2 v, double2) { return v; }
+__device__ __forceinline__ float2 to_c(double2 v, float2) { return make_float2(float(v.x), float(v.y)); }
+__device__ __forceinline__ float2 to_c(float4 e, float2) { return make_float2(e.x + e.y, e.z + e.w); }
+__device__ __forceinline__ float4 shfl_up(float4 v, int d) {
+    v.x = __shfl_up_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_up_sync(0xffffffffu, v.y, d);
+    v.z = __shfl_up_sync(0xffffffffu, v.z, d);
+    v.w = __shfl_up_sync(0xffffffffu, v.w, d);
+    return v;
+}
+
+// Inclusive prefix sum of each row of a [R][n] array of elements, in place.
 // One CTA of 1024 threads per row, 4 items per thread per chunk.
-__global__ void __launch_bounds__(1024) k_scan_rows(double2 *buf, int64_t n) {
-    __shared__ double2 warp_tot[32];
-    __shared__ double2 carry_s;
-    double2 *row = buf + blockIdx.x * n;
-    double2 carry = make_double2(0.0, 0.0);
+template <typename E>
+__global__ void __launch_bounds__(1024) k_scan_rows(E *buf, int64_t n) {
+    __shared__ E warp_tot[32];
+    __shared__ E carry_s;
+    E *row = buf + blockIdx.x * n;
+    E carry = ezero<E>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t base = 0; base < n; base += 4 * 1024) {
-        double2 v[4];
-        double2 run = make_double2(0.0, 0.0);
+        E v[4];
+        E run = ezero<E>();
         const int64_t i0 = base + 4 * int64_t(threadIdx.x);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            v[k] = (i0 + k < n) ? row[i0 + k] : make_double2(0.0, 0.0);
-            run = cadd(run, v[k]);
+            v[k] = (i0 + k < n) ? row[i0 + k] : ezero<E>();
+            run = eadd(run, v[k]);
             v[k] = run;
         }
-        double2 incl = run;   // warp inclusive scan of thread totals
+        E incl = run;   // warp inclusive scan of thread totals
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            double2 o = shfl_up(incl, d);
-            if (lane >= d) incl = cadd(incl, o);
+            E o = shfl_up(incl, d);
+            if (lane >= d) incl = eadd(incl, o);
         }
         if (lane == 31) warp_tot[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            double2 w = warp_tot[lane];
+            E w = warp_tot[lane];
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                double2 o = shfl_up(w, d);
-                if (lane >= d) w = cadd(w, o);
+                E o = shfl_up(w, d);
+                if (lane >= d) w = eadd(w, o);
             }
             warp_tot[lane] = w;
         }
         __syncthreads();
-        double2 off = carry;
-        if (warp > 0) off = cadd(off, warp_tot[warp - 1]);
-        off = cadd(off, csub(incl, run));   // exclusive within the warp
+        E off = carry;
+        if (warp > 0) off = eadd(off, warp_tot[warp - 1]);
+        off = eadd(off, eadd(incl, eneg(run)));   // exclusive within the warp
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (i0 + k < n) row[i0 + k] = cadd(v[k], off);
-        if (threadIdx.x == 1023) carry_s = cadd(off, run);
+            if (i0 + k < n) row[i0 + k] = eadd(v[k], off);
+        if (threadIdx.x == 1023) carry_s = eadd(off, run);
         __syncthreads();
         carry = carry_s;
         __syncthreads();
@@ -92,45 +126,51 @@ __global__ void __launch_bounds__(1024) k_scan_rows(double2 *buf, int64_t n) {
 
 // Tour values for A^T: at node v's enter slot the current the links inject
 // into v (+x on links entering v, -x on links leaving it); 0 at exit slots.
-__global__ void k_tour_inject(const double2 *__restrict__ x, int64_t nl, double2 *__restrict__ tour, int64_t nslots,
+template <typename E>
+__global__ void k_tour_inject(const double2 *__restrict__ x, int64_t nl, E *__restrict__ tour, int64_t nslots,
                               const int32_t *__restrict__ tour_node, const int8_t *__restrict__ tour_enter,
                               const int32_t *__restrict__ nl_ptr, const int32_t *__restrict__ nl_loop,
                               const int8_t *__restrict__ nl_sign, int32_t nrhs) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nslots * nrhs) return;
     int64_t r = i / nslots, s = i % nslots;
-    double2 acc = make_double2(0.0, 0.0);
-    if (tour_enter[s]) {
-        int v = tour_node[s];
+    E out = ezero<E>();
+    const int v = tour_node[s];
+    if (tour_enter[s] && nl_ptr[v] < nl_ptr[v + 1]) {
+        double2 acc = make_double2(0.0, 0.0);   // a few link currents, exact inputs
         for (int k = nl_ptr[v]; k < nl_ptr[v + 1]; ++k) {
-            double2 xv = x[r * nl + nl_loop[k]];
-            if (nl_sign[k] > 0) acc = cadd(acc, xv); else acc = csub(acc, xv);
+            const double2 xv = x[r * nl + nl_loop[k]];
+            acc = nl_sign[k] > 0 ? cadd(acc, xv) : csub(acc, xv);
         }
+        eset(out, acc);
     }
-    tour[i] = acc;
+    tour[i] = out;
 }
 
 // Branch current of branch b for right-hand side r (loop space): a link carries
-// its loop current; a twig above node v carries -sigma * (subtree inflow).
-__device__ __forceinline__ double2 branch_current(int32_t b, int64_t r, const double2 *__restrict__ x, int64_t nl,
-                                                  const double2 *__restrict__ P, int64_t nslots,
-                                                  const int32_t *__restrict__ loop_of_branch,
-                                                  const int32_t *__restrict__ twig_node, const int32_t *__restrict__ head,
-                                                  const int32_t *__restrict__ enter, const int32_t *__restrict__ exit_) {
+// its loop current; a twig above node v carries -sigma * (subtree inflow), a
+// difference of two prefix sums taken in the tour's arithmetic.
+template <typename T, typename E>
+__device__ __forceinline__ C<T> branch_current(int32_t b, int64_t r, const double2 *__restrict__ x, int64_t nl,
+                                               const E *__restrict__ P, int64_t nslots,
+                                               const int32_t *__restrict__ loop_of_branch,
+                                               const int32_t *__restrict__ twig_node, const int32_t *__restrict__ head,
+                                               const int32_t *__restrict__ enter, const int32_t *__restrict__ exit_) {
     int32_t l = loop_of_branch[b];
-    if (l >= 0) return x[r * nl + l];
+    if (l >= 0) return to_c(x[r * nl + l], C<T>{});
     int32_t v = twig_node[b];
-    const double2 *row = P + r * nslots;
-    double2 S = row[exit_[v]];
+    const E *row = P + r * nslots;
+    E S = row[exit_[v]];
     int32_t e = enter[v];
-    if (e > 0) S = csub(S, row[e - 1]);
-    return head[b] == v ? mk<double>(-S.x, -S.y) : S;
+    if (e > 0) S = eadd(S, eneg(row[e - 1]));
+    const C<T> d = to_c(S, C<T>{});
+    return head[b] == v ? mk<T>(-d.x, -d.y) : d;
 }
 
 // Local currents c_T[k] = s_k alpha_{b(T,k)}: one thread per (T, r) for the
 // three local edges, written as cT [T][3][R] (right-hand sides innermost).
 template <typename T>
-__global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const double2 *__restrict__ P, int64_t nslots,
+__global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const TourE<T> *__restrict__ P, int64_t nslots,
                             const int32_t *__restrict__ tb, const int8_t *__restrict__ ts,
                             const int32_t *__restrict__ loop_of_branch, const int32_t *__restrict__ twig_node,
                             const int32_t *__restrict__ head, const int32_t *__restrict__ enter,
@@ -143,15 +183,15 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const dou
     for (int k = 0; k < 3; ++k) {
         const int64_t tk = t * 3 + k;
         const int32_t b = tb[tk];
-        double2 a = make_double2(0.0, 0.0);
+        C<T> a = mk<T>(T(0), T(0));
         if (b >= 0) {
             if (space == SIE_SPACE_LOOP)
-                a = branch_current(b, r, x, nl, P, nslots, loop_of_branch, twig_node, head, enter, exit_);
+                a = branch_current<T>(b, r, x, nl, P, nslots, loop_of_branch, twig_node, head, enter, exit_);
             else
-                a = x[r * nb + b];
+                a = to_c(x[r * nb + b], C<T>{});
             if (ts[tk] < 0) { a.x = -a.x; a.y = -a.y; }
         }
-        cT[tk * nrhs + r] = mk<T>(T(a.x), T(a.y));
+        cT[tk * nrhs + r] = a;
     }
 }
 
@@ -296,8 +336,8 @@ __global__ void __launch_bounds__(256)
     k_tri_gather(const int64_t *__restrict__ near_ptr, const Rec<T> *__restrict__ near_rec,
                  const int64_t *__restrict__ pt_ptr, const Rec<T> *__restrict__ pt_rec, const C<T> *__restrict__ cT,
                  const C<T> *__restrict__ phiT, const double *__restrict__ gram, const int32_t *__restrict__ cond,
-                 const double *__restrict__ coef, int ncond, int64_t nt, int32_t R, int32_t nslab,
-                 double2 *__restrict__ y_tri) {
+                 const double *__restrict__ coef, const float2 *__restrict__ coef_dd, int ncond, int64_t nt,
+                 int32_t R, int32_t nslab, TourE<T> *__restrict__ y_tri) {
     constexpr int SLAB = 32 * V * J;
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -314,34 +354,60 @@ __global__ void __launch_bounds__(256)
         gather_rows<T, V, J, false>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
         gather_rows<T, V, J, false>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
     }
-    double G[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) G[i] = __ldg(gram + 9 * t + i);
     const int cd = cond[t];
+    if constexpr (sizeof(T) == 4) {
+        // mixed form: Gram term in FP32 like the field, Eq. Zb in double-float
+        float G[9];
 #pragma unroll
-    for (int j = 0; j < J; ++j)
+        for (int i = 0; i < 9; ++i) G[i] = float(__ldg(gram + 9 * t + i));
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const int32_t r = rl + 32 * V * j + v;
-            if (r >= R) continue;
-            const double *cf = coef + int64_t(r) * (2 * ncond + 1);
-            const double zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * ncond];
-            double2 c[3];
+        for (int j = 0; j < J; ++j)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                const C<T> u = cT[(t * 3 + l) * R + r];
-                c[l] = make_double2(double(u.x), double(u.y));
+            for (int v = 0; v < V; ++v) {
+                const int32_t r = rl + 32 * V * j + v;
+                if (r >= R) continue;
+                const float2 *cf = coef_dd + int64_t(r) * (2 * ncond + 1);
+                const float2 zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * ncond];
+                float2 c[3];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) c[l] = cT[(t * 3 + l) * R + r];
+                float4 *out = y_tri + (int64_t(r) * nt + t) * 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float gr = G[3 * k] * c[0].x + G[3 * k + 1] * c[1].x + G[3 * k + 2] * c[2].x;
+                    const float gi = G[3 * k] * c[0].y + G[3 * k + 1] * c[1].y + G[3 * k + 2] * c[2].y;
+                    out[k] = dd_zb(zr, zi, cl, gr, gi, DD{acc[k][j][v].x, 0.f}, DD{acc[k][j][v].y, 0.f});
+                }
             }
-            double2 *out = y_tri + (int64_t(r) * nt + t) * 3;
+    } else {
+        double G[9];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const double gr = G[3 * k] * c[0].x + G[3 * k + 1] * c[1].x + G[3 * k + 2] * c[2].x;
-                const double gi = G[3 * k] * c[0].y + G[3 * k + 1] * c[1].y + G[3 * k + 2] * c[2].y;
-                const double fr = double(acc[k][j][v].x), fi = double(acc[k][j][v].y);
-                // Z_s * gram + j c_L * f
-                out[k] = make_double2(zr * gr - zi * gi - cl * fi, zr * gi + zi * gr + cl * fr);
+        for (int i = 0; i < 9; ++i) G[i] = __ldg(gram + 9 * t + i);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int32_t r = rl + 32 * V * j + v;
+                if (r >= R) continue;
+                const double *cf = coef + int64_t(r) * (2 * ncond + 1);
+                const double zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * ncond];
+                double2 c[3];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const C<T> u = cT[(t * 3 + l) * R + r];
+                    c[l] = make_double2(double(u.x), double(u.y));
+                }
+                double2 *out = y_tri + (int64_t(r) * nt + t) * 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double gr = G[3 * k] * c[0].x + G[3 * k + 1] * c[1].x + G[3 * k + 2] * c[2].x;
+                    const double gi = G[3 * k] * c[0].y + G[3 * k + 1] * c[1].y + G[3 * k + 2] * c[2].y;
+                    const double fr = double(acc[k][j][v].x), fi = double(acc[k][j][v].y);
+                    // Z_s * gram + j c_L * f
+                    out[k] = make_double2(zr * gr - zi * gi - cl * fi, zr * gi + zi * gr + cl * fr);
+                }
             }
-        }
+    }
 }
 
 // Interpolated far field alone (mixed form, where the near blocks run on the
@@ -370,55 +436,62 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// y_b = sum over the branch's two triangles of s * y_T[k].
-__global__ void k_branch_out(const double2 *__restrict__ y_tri, const int32_t *__restrict__ br_tri,
+// y_b = sum over the branch's two triangles of s * y_T[k]; EO is the output
+// element (complex128 for a branch-space result).
+template <typename E, typename EO>
+__global__ void k_branch_out(const E *__restrict__ y_tri, const int32_t *__restrict__ br_tri,
                              const int8_t *__restrict__ br_local, int64_t nt, int64_t nb, int64_t ldy, int32_t nrhs,
-                             double2 *__restrict__ y) {
+                             EO *__restrict__ y) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= ldy * nrhs) return;
     int64_t r = i / ldy, b = i % ldy;
-    double2 v = make_double2(0.0, 0.0);
+    E v = ezero<E>();
     if (b < nb) {
-        double2 a = y_tri[(r * nt + br_tri[2 * b]) * 3 + br_local[2 * b]];
-        double2 c = y_tri[(r * nt + br_tri[2 * b + 1]) * 3 + br_local[2 * b + 1]];
-        v = csub(a, c);
+        const E a = y_tri[(r * nt + br_tri[2 * b]) * 3 + br_local[2 * b]];
+        const E c = y_tri[(r * nt + br_tri[2 * b + 1]) * 3 + br_local[2 * b + 1]];
+        v = eadd(a, eneg(c));
     }
-    y[i] = v;
+    EO o;
+    eset(o, v);
+    y[i] = o;
 }
 
 // Tour values for A: +delta(v) at v's enter slot, -delta(v) at its exit slot,
 // delta(v) = voltage of v's parent twig walked from v towards the root.
-__global__ void k_tour_voltage(const double2 *__restrict__ y_br, int64_t ldy, double2 *__restrict__ tour,
-                               int64_t nslots, const int32_t *__restrict__ tour_node,
-                               const int8_t *__restrict__ tour_enter, const int32_t *__restrict__ parent_branch,
-                               const int32_t *__restrict__ tail, int32_t nrhs) {
+template <typename E>
+__global__ void k_tour_voltage(const E *__restrict__ y_br, int64_t ldy, E *__restrict__ tour, int64_t nslots,
+                               const int32_t *__restrict__ tour_node, const int8_t *__restrict__ tour_enter,
+                               const int32_t *__restrict__ parent_branch, const int32_t *__restrict__ tail,
+                               int32_t nrhs) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nslots * nrhs) return;
     int64_t r = i / nslots, s = i % nslots;
     int v = tour_node[s];
     int t = parent_branch[v];
-    double2 d = make_double2(0.0, 0.0);
+    E d = ezero<E>();
     if (t >= 0) {
         d = y_br[r * ldy + t];
-        if (tail[t] != v) { d.x = -d.x; d.y = -d.y; }
-        if (!tour_enter[s]) { d.x = -d.x; d.y = -d.y; }
+        if ((tail[t] != v) != !tour_enter[s]) d = eneg(d);
     }
     tour[i] = d;
 }
 
-__global__ void k_loop_out(const double2 *__restrict__ y_br, int64_t ldy, const double2 *__restrict__ P,
-                           int64_t nslots, const int32_t *__restrict__ link_branch, const int32_t *__restrict__ tail,
+template <typename E>
+__global__ void k_loop_out(const E *__restrict__ y_br, int64_t ldy, const E *__restrict__ P, int64_t nslots,
+                           const int32_t *__restrict__ link_branch, const int32_t *__restrict__ tail,
                            const int32_t *__restrict__ head, const int32_t *__restrict__ enter, int64_t nl,
                            int32_t nrhs, double2 *__restrict__ y) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nl * nrhs) return;
     int64_t r = i / nl, l = i % nl;
     int32_t e = link_branch[l];
-    const double2 *row = P + r * nslots;
-    double2 v = y_br[r * ldy + e];
-    v = cadd(v, row[enter[head[e]]]);
-    v = csub(v, row[enter[tail[e]]]);
-    y[i] = v;
+    const E *row = P + r * nslots;
+    E v = y_br[r * ldy + e];
+    v = eadd(v, row[enter[head[e]]]);
+    v = eadd(v, eneg(row[enter[tail[e]]]));
+    double2 o;
+    eset(o, v);
+    y[i] = o;
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return unsigned((n + t - 1) / t); }
@@ -450,7 +523,7 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
         size_t(R) * 3 * p->Ng * cs,
         size_t(R) * p->nt * 3 * sizeof(double2),
         size_t(R) * (p->nb + p->np) * sizeof(double2),
-        size_t(R) * (2 * p->ncond + 1) * sizeof(double),
+        size_t(R) * (2 * p->ncond + 1) * (sizeof(double) + sizeof(float2)),
         size_t(R) * p->nt * 3 * cs,
         with_far ? size_t(R) * p->nt * 3 * sizeof(float2) : 0};
     void **dst[kBufs] = {&s.tour, &s.grid, &s.spec, &s.phiT, &s.y_tri, &s.y_br, (void **)&s.coef, &s.cT,
@@ -503,7 +576,7 @@ template <typename T, int V, int J> struct Blocks {
         const int64_t warps = p->nt * nslab;
         k_tri_gather<T, V, J><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
             p->d_near_ptr, nr(p), p->d_pt_ptr, pt(p), (const C<T> *)p->scr.cT, (const C<T> *)p->scr.phiT,
-            p->d_gram, p->d_cond, p->scr.coef, p->ncond, p->nt, R, nslab, (double2 *)p->scr.y_tri);
+            p->d_gram, p->d_cond, p->scr.coef, coef_dd(p), p->ncond, p->nt, R, nslab, (TourE<T> *)p->scr.y_tri);
         SIE_LAUNCH_CHECK(p);
         return SIE_OK;
     }
@@ -528,14 +601,15 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     Scratch &s = p->scr;
     const int64_t nslots = 2 * p->nn;
     const int64_t ldy = p->nb + p->np;
-    double2 *tour = (double2 *)s.tour;
-    double2 *y_tri = (double2 *)s.y_tri, *y_br = (double2 *)s.y_br;
+    using E = TourE<T>;
+    E *tour = (E *)s.tour;
+    E *y_tri = (E *)s.y_tri, *y_br = (E *)s.y_br;
     std::unique_ptr<StageTimer> tm(new StageTimer(p, SIE_STAGE_LOOP_TO_BRANCH, st));
     if (space == SIE_SPACE_LOOP) {
         k_tour_inject<<<nblk(nslots * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tour_node, p->d_tour_enter,
                                                          p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign, R);
         SIE_LAUNCH_CHECK(p);
-        k_scan_rows<<<R, 1024, 0, st>>>(tour, nslots);
+        k_scan_rows<E><<<R, 1024, 0, st>>>(tour, nslots);
         SIE_LAUNCH_CHECK(p);
     }
     k_alpha_tri<T><<<nblk(p->nt * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tb, p->d_ts, p->d_loop_of_branch,
@@ -569,26 +643,35 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     if (rc) return rc;
     tm.reset(new StageTimer(p, SIE_STAGE_BRANCH_TO_LOOP, st));
     if (space == SIE_SPACE_BRANCH) {
-        k_branch_out<<<nblk(p->nb * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, p->nb, R, y);
+        k_branch_out<E, double2><<<nblk(p->nb * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb,
+                                                                  p->nb, R, y);
         SIE_LAUNCH_CHECK(p);
         return SIE_OK;
     }
-    k_branch_out<<<nblk(ldy * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, ldy, R, y_br);
+    k_branch_out<E, E><<<nblk(ldy * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, ldy, R,
+                                                        y_br);
     SIE_LAUNCH_CHECK(p);
-    k_tour_voltage<<<nblk(nslots * R), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_tour_node, p->d_tour_enter,
-                                                      p->d_parent_branch, p->d_tail, R);
+    k_tour_voltage<E><<<nblk(nslots * R), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_tour_node, p->d_tour_enter,
+                                                         p->d_parent_branch, p->d_tail, R);
     SIE_LAUNCH_CHECK(p);
-    k_scan_rows<<<R, 1024, 0, st>>>(tour, nslots);
+    k_scan_rows<E><<<R, 1024, 0, st>>>(tour, nslots);
     SIE_LAUNCH_CHECK(p);
-    k_loop_out<<<nblk(p->nl * R), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_link_branch, p->d_tail, p->d_head,
-                                                 p->d_enter, p->nl, R, y);
+    k_loop_out<E><<<nblk(p->nl * R), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_link_branch, p->d_tail, p->d_head,
+                                                    p->d_enter, p->nl, R, y);
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
 
-// Per right-hand side: Z_s of each conductor and c_L / j (Eq. ImpedanceOp, Eq. Zb).
+float2 *coef_dd(const pfft_plan *p) {
+    return reinterpret_cast<float2 *>(p->scr.coef + size_t(p->scr.cap_rhs) * (2 * p->ncond + 1));
+}
+
+// Per right-hand side: Z_s of each conductor and c_L / j (Eq. ImpedanceOp, Eq. Zb),
+// in FP64 and as double-float pairs.
 int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
-    std::vector<double> cf(size_t(R) * (2 * p->ncond + 1));
+    const size_t n = size_t(R) * (2 * p->ncond + 1);
+    std::vector<double> cf(n);
+    std::vector<float2> cd(n);
     for (int32_t r = 0; r < R; ++r) {
         const double w = omega[r];
         if (!(w >= 0.0) || !std::isfinite(w)) return fail(SIE_ERR_ARG, "pfft_matvec: omega must be finite and >= 0");
@@ -599,7 +682,12 @@ int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
         }
         cf[r * (2 * p->ncond + 1) + 2 * p->ncond] = w * kMu0 / (4.0 * M_PI);
     }
-    SIE_CUDA(cudaMemcpyAsync(p->scr.coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    for (size_t i = 0; i < n; ++i) {
+        const float hi = float(cf[i]);
+        cd[i] = make_float2(hi, float(cf[i] - double(hi)));
+    }
+    SIE_CUDA(cudaMemcpyAsync(p->scr.coef, cf.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    SIE_CUDA(cudaMemcpyAsync(coef_dd(p), cd.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st));
     return SIE_OK;
 }
 

@@ -20,13 +20,17 @@ struct PrecondState;   // sie_solve.cu
 struct Scratch {
     int32_t cap_rhs = 0;   // right-hand sides the buffers are sized for
     int cs = 0;            // complex element size the buffers are sized for (8 or 16)
-    void *tour = nullptr;      // complex128 [R][2 n_nodes]
+    // tour, y_tri and y_br hold complex128 in the FP64 form and double-float
+    // complex (float4: re hi, re lo, im hi, im lo) in the mixed form
+    void *tour = nullptr;      // [R][2 n_nodes]
     void *grid = nullptr;      // complex T [3][R][Ng]   grid currents, then grid potentials
     void *spec = nullptr;      // complex T [3R][Mx][Ny][Nz]  grids transformed along x
     void *phiT = nullptr;      // complex T [Ng][3][R]   grid potentials, right-hand sides innermost
-    void *y_tri = nullptr;     // complex128 [R][nt][3]
-    void *y_br = nullptr;      // complex128 [R][nb + np]
-    double *coef = nullptr;    // per RHS: Z_s per conductor (re, im), c_L (im) -> [R][2 ncond + 1]
+    void *y_tri = nullptr;     // [R][nt][3]
+    void *y_br = nullptr;      // [R][nb + np]
+    // per RHS: Z_s per conductor (re, im), c_L (im) -> double [R][2 ncond + 1],
+    // followed by the same table as double-float (hi, lo) pairs, see coef_dd()
+    double *coef = nullptr;
     void *cT = nullptr;        // complex T [nt][3][R]  local currents, right-hand sides innermost
     void *ffar = nullptr;      // complex64 [nt][3][R]  interpolated far field (mixed form)
     size_t bytes = 0;
@@ -153,6 +157,7 @@ int plan_alloc(pfft_plan *p, void **ptr, size_t bytes);
 void plan_free(pfft_plan *p, void *ptr);
 void plan_free_precond(pfft_plan *p);
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
+float2 *coef_dd(const pfft_plan *p);   // double-float copy of scr.coef
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
 int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s,
