@@ -60,6 +60,7 @@ struct PrecondState {
     float2 *d_band32 = nullptr, *d_bandc32 = nullptr;   // FP32 roundings of both (mixed form)
     float2 *d_u32 = nullptr;          // FP32 sweep buffer [R][nunk]
     double2 *d_a = nullptr;           // [nslots][nb] 1/D_e
+    float2 *d_a32 = nullptr;          // its FP32 rounding (mixed form)
     double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
     int32_t cap_rhs = 0;
     int32_t *d_slot = nullptr;        // [R] factor slot per right-hand side
@@ -73,7 +74,7 @@ struct PrecondState {
 void plan_free_precond(pfft_plan *p) {
     if (!p || !p->pc) return;
     for (void *a : p->pc->allocs) cudaFree(a);
-    for (void *a : {(void *)p->pc->d_band32, (void *)p->pc->d_bandc32, (void *)p->pc->d_u32})
+    for (void *a : {(void *)p->pc->d_band32, (void *)p->pc->d_bandc32, (void *)p->pc->d_u32, (void *)p->pc->d_a32})
         if (a) cudaFree(a);
     for (int v = 0; v < 2; ++v)
         for (void *a : {(void *)p->pc->d_grp_start[v], (void *)p->pc->d_grp_count[v]})
@@ -377,26 +378,30 @@ __global__ void __launch_bounds__(256) k_pc_factor(const int64_t *__restrict__ b
 }
 
 // Drive of each branch: kappa_e = a_e (off_tail - off_head + emf_e), emf on links.
-__global__ void k_pc_drive(const double2 *__restrict__ y, int64_t nl, const double2 *__restrict__ a,
+// T = float (mixed form): the preconditioner is an approximation of P, so its
+// bookkeeping runs in FP32 like its band factors.
+template <typename T>
+__global__ void k_pc_drive(const double2 *__restrict__ y, int64_t nl, const C<T> *__restrict__ a,
                            const int32_t *__restrict__ slot, const int32_t *__restrict__ loop_of_branch,
                            const int32_t *__restrict__ tail, const int32_t *__restrict__ head,
                            const int32_t *__restrict__ off_ptr, const int32_t *__restrict__ off_port,
                            const int8_t *__restrict__ off_sign, const int32_t *__restrict__ port_loop, int64_t nb,
-                           int32_t nrhs, double2 *__restrict__ kappa) {
+                           int32_t nrhs, C<T> *__restrict__ kappa) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nb * nrhs) return;
     int64_t r = i / nb, e = i % nb;
     const double2 *yr = y + r * nl;
-    double2 v = make_double2(0.0, 0.0);
+    auto ld = [&](int64_t k) { const double2 q = yr[k]; return mk<T>(T(q.x), T(q.y)); };
+    C<T> v = mk<T>(T(0), T(0));
     int32_t l = loop_of_branch[e];
-    if (l >= 0) v = yr[l];
+    if (l >= 0) v = ld(l);
     int32_t t = tail[e], h = head[e];
     for (int32_t k = off_ptr[t]; k < off_ptr[t + 1]; ++k) {
-        double2 q = yr[port_loop[off_port[k]]];
+        const C<T> q = ld(port_loop[off_port[k]]);
         v = off_sign[k] > 0 ? cadd(v, q) : csub(v, q);
     }
     for (int32_t k = off_ptr[h]; k < off_ptr[h + 1]; ++k) {
-        double2 q = yr[port_loop[off_port[k]]];
+        const C<T> q = ld(port_loop[off_port[k]]);
         v = off_sign[k] > 0 ? csub(v, q) : cadd(v, q);
     }
     kappa[i] = cmul(a[int64_t(slot[r]) * nb + e], v);
@@ -518,11 +523,11 @@ __device__ __forceinline__ void pc_step(const C<T> *bs, int j, int jr, int lane,
 
 template <typename T, int RB>
 __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
-    const double2 *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
+    const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
     const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
     int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
     const int32_t *__restrict__ grp_start, const int32_t *__restrict__ grp_count, int32_t ngroups,
-    double2 *__restrict__ u, C<T> *__restrict__ xs) {
+    C<T> *__restrict__ xs) {
     extern __shared__ __align__(16) unsigned char pc_smem[];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -542,17 +547,17 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
         if (k >= nr) break;
-        const double2 *kr = kappa + int64_t(r0 + k) * nb;
+        const C<T> *kr = kappa + int64_t(r0 + k) * nb;
         C<T> *x = xs + int64_t(r0 + k) * nunk + o;
         for (int64_t i0 = lane; i0 < n; i0 += 4 * 32) {
             int32_t qa[4], qb[4];
-            double2 acc[4];
+            C<T> acc[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t i = i0 + 32 * u;
                 qa[u] = i < n ? row_ptr[o + i] : 0;
                 qb[u] = i < n ? row_ptr[o + i + 1] : 0;
-                acc[u] = make_double2(0.0, 0.0);
+                acc[u] = zero;
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d)
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
                 for (int32_t q = qa[u] + 3; q < qb[u]; ++q)   // contact nodes: many branches
                     acc[u] = row_sg[q] > 0 ? csub(acc[u], kr[row_br[q]]) : cadd(acc[u], kr[row_br[q]]);
                 const int64_t i = i0 + 32 * u;
-                if (i < n) x[i] = mk<T>(T(acc[u].x), T(acc[u].y));
+                if (i < n) x[i] = acc[u];
             }
         }
     }
@@ -648,9 +653,8 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
             for (int j = 0; j <= int(top); ++j) pc_step<T, RB>(bs, j, PC_CH - 1 - j, lane, w, pf, done);
         }
 #pragma unroll
-        for (int k = 0; k < RB; ++k) {   // final values straight to the FP64 solution
-            if (k < nr && top - lane >= 0)
-                u[int64_t(r0 + k) * nunk + o + top - lane] = make_double2(double(done[k].x), double(done[k].y));
+        for (int k = 0; k < RB; ++k) {   // final values in place (every row still to be read lies below)
+            if (k < nr && top - lane >= 0) xs[int64_t(r0 + k) * nunk + o + top - lane] = done[k];
             pf[k] = pn[k];
         }
         __syncwarp();
@@ -661,21 +665,23 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
 }
 
 // Branch currents i_e = a_e (phi_tail - phi_head + emf_e) = a_e (u_t - u_h) + kappa_e.
-__global__ void k_pc_currents(const double2 *__restrict__ u, int64_t nunk, const double2 *__restrict__ kappa,
-                              const double2 *__restrict__ a, const int32_t *__restrict__ slot,
+template <typename T>
+__global__ void k_pc_currents(const C<T> *__restrict__ u, int64_t nunk, const C<T> *__restrict__ kappa,
+                              const C<T> *__restrict__ a, const int32_t *__restrict__ slot,
                               const int32_t *__restrict__ unk, const int32_t *__restrict__ tail,
-                              const int32_t *__restrict__ head, int64_t nb, int32_t nrhs, double2 *__restrict__ ibr) {
+                              const int32_t *__restrict__ head, int64_t nb, int32_t nrhs, C<T> *__restrict__ ibr) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nb * nrhs) return;
     int64_t r = i / nb, e = i % nb;
     int32_t ut = unk[tail[e]], uh = unk[head[e]];
-    double2 d = make_double2(0.0, 0.0);
+    C<T> d = mk<T>(T(0), T(0));
     if (ut >= 0) d = cadd(d, u[r * nunk + ut]);
     if (uh >= 0) d = csub(d, u[r * nunk + uh]);
     ibr[i] = cadd(cmul(a[int64_t(slot[r]) * nb + e], d), kappa[i]);
 }
 
-__global__ void k_pc_out(const double2 *__restrict__ ibr, const int32_t *__restrict__ link_branch,
+template <typename T>
+__global__ void k_pc_out(const C<T> *__restrict__ ibr, const int32_t *__restrict__ link_branch,
                          const int32_t *__restrict__ src_ptr, const int32_t *__restrict__ src_br,
                          const int8_t *__restrict__ src_sg, int64_t nb, int64_t nl, int32_t nrhs,
                          double2 *__restrict__ z) {
@@ -683,17 +689,17 @@ __global__ void k_pc_out(const double2 *__restrict__ ibr, const int32_t *__restr
     if (i >= nl * nrhs) return;
     int64_t r = i / nl, l = i % nl;
     int32_t e = link_branch[l];
-    const double2 *ir = ibr + r * nb;
-    double2 v;
+    const C<T> *ir = ibr + r * nb;
+    C<T> v;
     if (e < nb) {
         v = ir[e];
     } else {
         int32_t q = int32_t(e - nb);
-        v = make_double2(0.0, 0.0);
+        v = mk<T>(T(0), T(0));
         for (int32_t k = src_ptr[q]; k < src_ptr[q + 1]; ++k)
             v = src_sg[k] > 0 ? cadd(v, ir[src_br[k]]) : csub(v, ir[src_br[k]]);
     }
-    z[i] = v;
+    z[i] = make_double2(double(v.x), double(v.y));
 }
 
 inline unsigned nblk_(int64_t n, int t = 256) { return unsigned((n + t - 1) / t); }
@@ -755,15 +761,18 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     if (s->d_bandc32) cudaFree(s->d_bandc32);
     s->d_band32 = s->d_bandc32 = nullptr;
     if (s->d_a) cudaFree(s->d_a);
+    if (s->d_a32) cudaFree(s->d_a32);
     s->d_band = nullptr;
     s->d_bandc = nullptr;
     s->d_a = nullptr;
+    s->d_a32 = nullptr;
     s->slot_omega.clear();
     SIE_CUDA(cudaMalloc((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_band32, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(float2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_bandc32, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(float2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2)));
+    SIE_CUDA(cudaMalloc((void **)&s->d_a32, size_t(ns) * p->nb * sizeof(float2)));
     std::vector<double> zc(size_t(ns) * (p->ncond + 1));
     for (int32_t f = 0; f < ns; ++f) {
         for (int c = 0; c < p->ncond; ++c) zc[f * (p->ncond + 1) + c] = std::sqrt(uniq[f] * kMu0 / (2.0 * p->sigma[c]));
@@ -774,6 +783,8 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     SIE_CUDA(cudaMemcpyAsync(d_zc, zc.data(), zc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zc, p->ncond,
                                                        p->nb, ns, s->d_a);
+    SIE_LAUNCH_CHECK(p);
+    k_round_c<<<nblk_(p->nb * ns), 256, 0, st>>>(s->d_a, s->d_a32, p->nb * ns);
     SIE_LAUNCH_CHECK(p);
     int zero = 0;
     SIE_CUDA(cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -799,48 +810,56 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     return SIE_OK;
 }
 
-int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int prec, cudaStream_t st) {
+// z = P^-1 y.  T = float: FP32 band factors and FP32 bookkeeping (mixed form,
+// band width <= 31); T = double: everything in FP64.
+template <typename T>
+int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream_t st) {
     PrecondState *s = p->pc;
-    StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
+    constexpr bool f32 = sizeof(T) == 4;
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
-    k_pc_drive<<<nblk_(p->nb * R), 256, 0, st>>>(y, p->nl, s->d_a, s->d_slot, p->d_loop_of_branch, p->d_tail,
-                                                 p->d_head, s->d_off_ptr, s->d_off_port, s->d_off_sign,
-                                                 s->d_port_loop, p->nb, R, s->d_kappa);
+    C<T> *kappa = reinterpret_cast<C<T> *>(s->d_kappa);   // buffers sized for complex128
+    C<T> *ibr = reinterpret_cast<C<T> *>(s->d_ibr);
+    C<T> *u;
+    const C<T> *a;
+    if constexpr (f32) { u = s->d_u32; a = s->d_a32; } else { u = s->d_u; a = s->d_a; }
+    k_pc_drive<T><<<nblk_(p->nb * R), 256, 0, st>>>(y, p->nl, a, s->d_slot, p->d_loop_of_branch, p->d_tail,
+                                                    p->d_head, s->d_off_ptr, s->d_off_port, s->d_off_sign,
+                                                    s->d_port_loop, p->nb, R, kappa);
     SIE_LAUNCH_CHECK(p);
     if (s->nunk > 0) {
-        const int64_t warps = int64_t(R) * nblk;
         if (s->W <= 31) {
-            const int v = prec == SIE_PREC_MIXED ? 0 : 1;
+            const int v = f32 ? 0 : 1;
             const int64_t gw = int64_t(s->ngroups[v]) * nblk;
-            const size_t sm32 = size_t(4) * 2 * PC_CH * PC_CH * sizeof(float2);
-            const size_t sm64 = size_t(4) * 2 * PC_CH * PC_CH * sizeof(double2);
-            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<float, 1>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm32)));
-            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<double, 1>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm64)));
-            if (prec == SIE_PREC_MIXED)
-                k_pc_solve_grp<float, 1><<<nblk_(gw * 32, 128), 128, sm32, st>>>(
-                    s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
-                    s->d_band32, s->d_bandc32, s->d_slot, s->d_grp_start[0], s->d_grp_count[0], s->ngroups[0], s->d_u,
-                    s->d_u32);
-            else
-                k_pc_solve_grp<double, 1><<<nblk_(gw * 32, 128), 128, sm64, st>>>(
-                    s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
-                    s->d_band, s->d_bandc, s->d_slot, s->d_grp_start[1], s->d_grp_count[1], s->ngroups[1], s->d_u, s->d_u);
+            const size_t sm = size_t(4) * 2 * PC_CH * PC_CH * sizeof(C<T>);
+            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<T, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+            const C<T> *band, *bandc;
+            if constexpr (f32) { band = s->d_band32; bandc = s->d_bandc32; } else { band = s->d_band; bandc = s->d_bandc; }
+            k_pc_solve_grp<T, 1><<<nblk_(gw * 32, 128), 128, sm, st>>>(
+                kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band, bandc,
+                s->d_slot, s->d_grp_start[v], s->d_grp_count[v], s->ngroups[v], u);
         } else {
-            k_pc_solve<<<nblk_(warps * 32, 128), 128, 0, st>>>(s->d_kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
-                                                                s->d_blk_off, nblk, s->W, s->nunk, p->nb, s->d_band,
-                                                                s->d_slot, R, s->d_u);
+            if constexpr (f32) return fail(SIE_ERR_ARG, "preconditioner: FP32 sweeps need a band width <= 31");
+            else
+                k_pc_solve<<<nblk_(int64_t(R) * nblk * 32, 128), 128, 0, st>>>(
+                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
+                    s->d_band, s->d_slot, R, u);
         }
         SIE_LAUNCH_CHECK(p);
     }
-    k_pc_currents<<<nblk_(p->nb * R), 256, 0, st>>>(s->d_u, s->nunk, s->d_kappa, s->d_a, s->d_slot,
-                                                    s->d_unk_of_node, p->d_tail, p->d_head, p->nb, R, s->d_ibr);
+    k_pc_currents<T><<<nblk_(p->nb * R), 256, 0, st>>>(u, s->nunk, kappa, a, s->d_slot, s->d_unk_of_node,
+                                                       p->d_tail, p->d_head, p->nb, R, ibr);
     SIE_LAUNCH_CHECK(p);
-    k_pc_out<<<nblk_(p->nl * R), 256, 0, st>>>(s->d_ibr, p->d_link_branch, s->d_src_ptr, s->d_src_br, s->d_src_sg,
-                                               p->nb, p->nl, R, z);
+    k_pc_out<T><<<nblk_(p->nl * R), 256, 0, st>>>(ibr, p->d_link_branch, s->d_src_ptr, s->d_src_br, s->d_src_sg,
+                                                  p->nb, p->nl, R, z);
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
+}
+
+int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int prec, cudaStream_t st) {
+    StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
+    if (prec == SIE_PREC_MIXED && p->pc->W <= 31) return pc_apply_t<float>(p, y, z, R, st);
+    return pc_apply_t<double>(p, y, z, R, st);
 }
 
 // ------------------------------------------------------------------ GMRES kernels
