@@ -7,7 +7,7 @@ frequencies 1 MHz - 10 GHz x 8 ports = 128 right-hand sides.
 
 One step = one application of the preconditioned loop operator
 z = P(w)^-1 A Z_b(w) A^T x to all 128 right-hand sides (mixed precision: FP32
-grid, FFT and near field; FP64 loop maps and preconditioner), i.e. 128 pFFT
+grid, FFT, near field and preconditioner; double-float loop maps), i.e. 128 pFFT
 matvecs.  `value` = matvecs per second over all ranks.  Beside it: the plain
 FP64 form, GMRES time to a 1e-6 preconditioned residual (plain and mixed), the
 roofline of the dominant stage (device time from CUDA events recorded on the

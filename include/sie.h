@@ -153,7 +153,9 @@ void pfft_plan_destroy(pfft_plan *p);
  * conductor, w = omega[r] (host array, one angular frequency per right-hand
  * side).  prec = SIE_PREC_FP64 computes every step in FP64; SIE_PREC_MIXED runs
  * projection, FFT convolution, interpolation and the near field in FP32 and the
- * loop/branch maps and output in FP64.  x and y must not overlap.  Scratch is
+ * loop/branch maps (prefix sums, branch differences, the Z_s/c_L combination)
+ * in double-float (FP32 pairs, about 48 significant bits); y is complex128 in
+ * both.  x and y must not overlap.  Scratch is
  * plan-owned and grown on demand (SIE_ERR_OOM if that fails). */
 int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega,
                 int32_t space, int32_t prec, void *cuda_stream);
@@ -163,8 +165,9 @@ int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double
  * vectors y, z (device complex128 [nrhs][n_loops]) at omega[r].  P is applied
  * through the nodal Laplacian of the same circuit, factorised (FP64) per
  * conductor on first use of each distinct omega set.  prec = SIE_PREC_FP64
- * runs the triangular sweeps in FP64; SIE_PREC_MIXED runs them in FP32 on the
- * rounded factor.  Errors: SIE_ERR_BREAKDOWN for a zero pivot. */
+ * runs every step in FP64; SIE_PREC_MIXED runs the drive, the triangular sweeps
+ * on the rounded factor and the branch currents in FP32 (band width <= 31;
+ * wider bands fall back to FP64).  Errors: SIE_ERR_BREAKDOWN for a zero pivot. */
 int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
                        int32_t prec, void *cuda_stream);
 

@@ -3,7 +3,7 @@
 The CUDA path and the plain pFFT oracle run the same algorithm with the same
 parameters on the same seeded inputs, compared element by element:
   FP64 path:  relative 2-norm error per right-hand side <= 1e-10;
-  mixed path: <= 1e-5 (FP32 grid/FFT/near field, FP64 loop maps);
+  mixed path: <= 1e-5 (FP32 grid/FFT/near field, double-float loop maps);
 and against the dense MoM (the definition the pFFT approximates) <= 1e-4.
 Grids span several FFT tiles; right-hand-side counts include ragged ones.
 """
