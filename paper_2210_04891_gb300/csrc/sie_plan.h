@@ -99,6 +99,10 @@ struct pfft_plan {
     // the same spectrum with kx outermost: [Mx/2+1][My/2+1][Mz/2+1]
     double *d_Hp64 = nullptr;
     float *d_Hp32 = nullptr;
+    // paired FP32 plane convolution: spectrum with kz unfolded [Mx/2+1][My/2+1][Mz]
+    // and the four-step twiddles of axes 1 (y) and 2 (z) as (c, c, s, s)
+    float *d_Hz32 = nullptr;
+    float4 *d_tf4[3] = {nullptr, nullptr, nullptr}, *d_ti4[3] = {nullptr, nullptr, nullptr};
     // lossy kernel exp(-jkR)/R: complex spectrum of the last (omega, sigma), same layout
     double lossy_omega = -1.0, lossy_sigma = -1.0;
     double2 *d_Hl64 = nullptr;
@@ -165,5 +169,9 @@ int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, c
 int near_mma_prepare(pfft_plan *p, const std::vector<int64_t> &near_ptr, const std::vector<int32_t> &near_col,
                      cudaStream_t s);
 int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st);
+// paired FP32 (y, z) plane convolution of ngrids x-transformed grids (static
+// kernel); done = false when the plane size is not one it is built for
+bool plane_conv_supported(const pfft_plan *p);
+int plane_conv_f32(pfft_plan *p, float2 *spec, int32_t ngrids, cudaStream_t s, bool &done);
 int check_device_errors(pfft_plan *p);
 }  // namespace sie
