@@ -333,16 +333,6 @@ __global__ void k_permute_H(const double *H, double *Hp64, float *Hp32, int hx, 
     Hp32[i] = float(v);
 }
 
-// Hz[kx][ky][kz] = Hp[kx][ky][fold(kz)] for kz in [0, Mz): the z-unfolded copy
-// read in adjacent pairs by the paired plane convolution.
-__global__ void k_unfold_hz(const float *Hp, float *Hz, int64_t n, int Mz) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int kz = int(i % Mz);
-    const int64_t row = i / Mz;
-    Hz[i] = Hp[row * (Mz / 2 + 1) + (kz <= Mz / 2 ? kz : Mz - kz)];
-}
-
 // The lossy kernel exp(-jkR)/R, k = (1 - j)/delta, on the padded grid (same
 // offsets, wrap and zeroed +-N planes as k_fill_kernel):
 // exp(-jkR) = exp(-R/delta) (cos(R/delta) - j sin(R/delta)).
@@ -882,15 +872,6 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         UP(p->d_ti64[a], ti);
         UP(p->d_tf32[a], tf32);
         UP(p->d_ti32[a], ti32);
-        if (a > 0) {   // (c, c, s, s) copies for the paired plane convolution
-            std::vector<float4> tf4(M), ti4(M);
-            for (int k = 0; k < M; ++k) {
-                tf4[k] = make_float4(tf32[k].x, tf32[k].x, tf32[k].y, tf32[k].y);
-                ti4[k] = make_float4(ti32[k].x, ti32[k].x, ti32[k].y, ti32[k].y);
-            }
-            UP(p->d_tf4[a], tf4);
-            UP(p->d_ti4[a], ti4);
-        }
     }
     // device-side geometry for the setup kernels
     double *d_verts = nullptr, *d_area = nullptr, *d_r7b = nullptr, *d_r7w = nullptr, *d_tgb = nullptr, *d_tgw = nullptr;
@@ -942,10 +923,6 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         if ((rcode = plan_alloc(p, (void **)&p->d_Hp32, nh * sizeof(float)))) return bail(rcode);
         k_permute_H<<<(nh + 255) / 256, 256, 0, s>>>(p->d_H64, p->d_Hp64, p->d_Hp32, p->Mx / 2 + 1, p->My / 2 + 1,
                                                      p->Mz / 2 + 1);
-        p->launches++;
-        const int64_t nz = int64_t(p->Mx / 2 + 1) * (p->My / 2 + 1) * p->Mz;
-        if ((rcode = plan_alloc(p, (void **)&p->d_Hz32, nz * sizeof(float)))) return bail(rcode);
-        k_unfold_hz<<<unsigned((nz + 255) / 256), 256, 0, s>>>(p->d_Hp32, p->d_Hz32, nz, p->Mz);
         p->launches++;
     }
     // ---- near-field blocks

@@ -99,10 +99,6 @@ struct pfft_plan {
     // the same spectrum with kx outermost: [Mx/2+1][My/2+1][Mz/2+1]
     double *d_Hp64 = nullptr;
     float *d_Hp32 = nullptr;
-    // paired FP32 plane convolution: spectrum with kz unfolded [Mx/2+1][My/2+1][Mz]
-    // and the four-step twiddles of axes 1 (y) and 2 (z) as (c, c, s, s)
-    float *d_Hz32 = nullptr;
-    float4 *d_tf4[3] = {nullptr, nullptr, nullptr}, *d_ti4[3] = {nullptr, nullptr, nullptr};
     // lossy kernel exp(-jkR)/R: complex spectrum of the last (omega, sigma), same layout
     double lossy_omega = -1.0, lossy_sigma = -1.0;
     double2 *d_Hl64 = nullptr;

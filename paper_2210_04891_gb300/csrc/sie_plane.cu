@@ -1,6 +1,8 @@
 // Instantiations and launcher of the paired FP32 plane convolution
 // (sie_plane.cuh) for every padded plane My x Mz the plan accepts (powers of
 // two, 8..256, My Mz <= 8192; at most 99 KB of shared memory, two CTAs per SM).
+#include <algorithm>
+
 #include "sie_plan.h"
 #include "sie_plane.cuh"
 
@@ -12,8 +14,15 @@ int launch_plane(pfft_plan *p, float2 *spec, int32_t ngrids, int lgMx, cudaStrea
     using G = plane::Geo<MY, MZ>;
     auto kern = plane::k_plane_conv<MY, MZ>;
     SIE_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::kSmem)));
-    kern<<<unsigned(ngrids * p->Mx), plane::kThreads, G::kSmem, s>>>(spec, lgMx, p->d_Hz32, p->d_tf4[1],
-                                                                     p->d_ti4[1], p->d_tf4[2], p->d_ti4[2]);
+    int nsm = 0;
+    SIE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    // grids per CTA: up to 8 (the staged spectrum and twiddles serve each of
+    // them) while keeping about four waves of two CTAs per SM
+    const int64_t planes = int64_t(ngrids) * p->Mx;
+    const int gpc = int(std::max<int64_t>(1, std::min<int64_t>(8, planes / (8 * int64_t(nsm)))));
+    const int64_t ctas = int64_t(p->Mx) * ((ngrids + gpc - 1) / gpc);
+    kern<<<unsigned(ctas), plane::kThreads, G::kSmem, s>>>(spec, ngrids, gpc, lgMx, p->d_Hp32, p->d_tf32[1],
+                                                           p->d_ti32[1], p->d_tf32[2], p->d_ti32[2]);
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
@@ -42,7 +51,7 @@ int dispatch_mz(pfft_plan *p, float2 *spec, int32_t ngrids, int lgMx, cudaStream
 
 bool plane_conv_supported(const pfft_plan *p) {
     auto pow2 = [](int v) { return v >= 8 && v <= 256 && (v & (v - 1)) == 0; };
-    return p->d_Hz32 && pow2(p->My) && pow2(p->Mz) && int64_t(p->My) * p->Mz <= 8192;
+    return p->d_Hp32 && pow2(p->My) && pow2(p->Mz) && int64_t(p->My) * p->Mz <= 8192;
 }
 
 int plane_conv_f32(pfft_plan *p, float2 *spec, int32_t ngrids, cudaStream_t s, bool &done) {

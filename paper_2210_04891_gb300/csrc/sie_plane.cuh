@@ -10,8 +10,8 @@
 // handful of paired instructions and no register is ever shuffled between
 // halves.  The two transforms are
 //   z passes: rows y = 2m and 2m + 1 (same sub-transform index, same twiddle);
-//   y passes: columns kz = 2c and 2c + 1 (same twiddle, kernel values of the
-//             two columns adjacent in the kz-unfolded spectrum).
+//   y passes: columns kz = 2c and 2c + 1 (same twiddle; kernel values of the
+//             two columns from the spectrum slice staged in shared memory).
 // Shared memory is planar (separate re and im planes) so that the two values
 // of a pair are adjacent and move with one 64-bit access:
 //   Lz  (z phase): element (y, s) at (y / 2) * PZZ + 2 s + (y % 2);
@@ -172,7 +172,10 @@ template <int MY, int MZ> struct Geo {
     static constexpr int PZZ = 2 * MZ + 2;                          // Lz / Lq row-pair pitch
     static constexpr int NP = cmax(NYP * PZZ, MY * MZ);             // floats per plane of P
     static constexpr int NQ = NYP * PZZ;                            // floats per plane of Q
-    static constexpr size_t kSmem = size_t(2 * NP + 2 * NQ) * sizeof(float);
+    static constexpr int HSP = MZ / 2 + 2;                          // staged spectrum row pitch
+    static constexpr int NH = ((MY / 2 + 1) * HSP + 1) / 2 * 2;     // staged spectrum (floats, even)
+    static constexpr int NTW = 2 * (MY + MZ);                       // staged twiddles (float2)
+    static constexpr size_t kSmem = size_t(2 * NP + 2 * NQ + NH) * sizeof(float) + size_t(NTW) * sizeof(float2);
     static_assert(NYP >= 1 && A1 >= 2 && A2 >= 2 && B1 >= 2 && B2 >= 2 && A2 <= 16 && B2 <= 16, "plane size");
 };
 
@@ -212,8 +215,7 @@ __device__ __forceinline__ void ycol(int it, int &c, int &j) {
 
 // F1: z pass 1 of rows y < Ny (input z < Nz), global -> P (Lz), slot j2 + A2 k1.
 template <int MY, int MZ>
-__device__ __forceinline__ void f1(const float2 *__restrict__ src, float *Pre, float *Pim,
-                                   const float4 *__restrict__ tw) {
+__device__ __forceinline__ void f1(const float2 *__restrict__ src, float *Pre, float *Pim, const float2 *tw) {
     using G = Geo<MY, MZ>;
     constexpr int A1 = G::A1, A2 = G::A2, H1 = A1 / 2;
     for (int it = threadIdx.x; it < G::NYP * A2; it += kThreads) {
@@ -234,8 +236,8 @@ __device__ __forceinline__ void f1(const float2 *__restrict__ src, float *Pre, f
         for (int k1 = 0; k1 < A1; ++k1) {
             CP o = v[k1];
             if (k1) {
-                const float4 w = __ldg(tw + j2 * A1 + k1);
-                o = pmul(o, make_float2(w.x, w.y), make_float2(w.z, w.w));
+                const float2 w = tw[j2 * A1 + k1];
+                o = pmul(o, dup2(w.x), dup2(w.y));
             }
             const int i = m * G::PZZ + 2 * (j2 + A2 * k1);
             at2(Pre, i) = o.re;
@@ -270,8 +272,7 @@ __device__ __forceinline__ void f2(const float *Pre, const float *Pim, float *Qr
 
 // F3: y pass 1 of column pairs (2c, 2c + 1), Q (Lq, rows y < Ny) -> P (Ly), row k1 B2 + j2.
 template <int MY, int MZ>
-__device__ __forceinline__ void f3(const float *Qre, const float *Qim, float *Pre, float *Pim,
-                                   const float4 *__restrict__ tw) {
+__device__ __forceinline__ void f3(const float *Qre, const float *Qim, float *Pre, float *Pim, const float2 *tw) {
     using G = Geo<MY, MZ>;
     constexpr int B1 = G::B1, B2 = G::B2, H1 = B1 / 2, NC = MZ / 2;
     for (int it = threadIdx.x; it < NC * B2; it += kThreads) {
@@ -293,8 +294,8 @@ __device__ __forceinline__ void f3(const float *Qre, const float *Qim, float *Pr
         for (int k1 = 0; k1 < B1; ++k1) {
             CP o = v[k1];
             if (k1) {
-                const float4 w = __ldg(tw + j2 * B1 + k1);
-                o = pmul(o, make_float2(w.x, w.y), make_float2(w.z, w.w));
+                const float2 w = tw[j2 * B1 + k1];
+                o = pmul(o, dup2(w.x), dup2(w.y));
             }
             const int i = (k1 * B2 + j2) * MZ + 2 * c;
             at2(Pre, i) = o.re;
@@ -306,10 +307,16 @@ __device__ __forceinline__ void f3(const float *Qre, const float *Qim, float *Pr
 // y pass 2, times H(kx, ky, kz), inverse y pass A, in place on P (Ly): rows
 // k1 B2 + j2 in, rows k1 + B1 p2 out.  A round takes CW = kThreads / B1 column
 // pairs with all their k1, so every read of a column precedes every write.
-// Hk: this kx's spectrum [fold(ky)][kz], kz unfolded.
+// Hs: this kx's spectrum staged in shared memory, [fold(ky)][hz(fold(kz))] with
+// row pitch HSP and hz(f) = f + (f == Mz/2): the two loads of a column pair
+// then hit distinct banks (lanes c and Mz/2 - c share words).
+template <int MZ>
+__device__ __forceinline__ int hz_slot(int kz) {
+    const int f = kz <= MZ / 2 ? kz : MZ - kz;
+    return f + (f == MZ / 2 ? 1 : 0);
+}
 template <int MY, int MZ>
-__device__ __forceinline__ void ymid(float *Pre, float *Pim, const float *__restrict__ Hk,
-                                     const float4 *__restrict__ twi) {
+__device__ __forceinline__ void ymid(float *Pre, float *Pim, const float *Hs, const float2 *twi) {
     using G = Geo<MY, MZ>;
     constexpr int B1 = G::B1, B2 = G::B2, NC = MZ / 2, CW = kThreads / B1;
     const int k1 = threadIdx.x / CW, cl = threadIdx.x % CW;
@@ -327,14 +334,15 @@ __device__ __forceinline__ void ymid(float *Pre, float *Pim, const float *__rest
 #pragma unroll
             for (int k2 = 0; k2 < B2; ++k2) {
                 const int ky = k1 + B1 * k2, fy = ky <= MY / 2 ? ky : MY - ky;
-                const float2 h = __ldg(reinterpret_cast<const float2 *>(Hk + fy * MZ + 2 * c));
+                const float *hr = Hs + fy * G::HSP;
+                const float2 h = make_float2(hr[hz_slot<MZ>(2 * c)], hr[hz_slot<MZ>(2 * c + 1)]);
                 v[k2] = CP{mul2(v[k2].re, h), mul2(v[k2].im, h)};
             }
             pdft<B2, true>(v);
 #pragma unroll
             for (int p2 = 1; p2 < B2; ++p2) {
-                const float4 w = __ldg(twi + k1 * B2 + p2);
-                v[p2] = pmulc(v[p2], make_float2(w.x, w.y), make_float2(w.z, w.w));
+                const float2 w = twi[k1 * B2 + p2];
+                v[p2] = pmulc(v[p2], dup2(w.x), dup2(w.y));
             }
         }
         __syncthreads();
@@ -380,8 +388,7 @@ __device__ __forceinline__ void i2(const float *Pre, const float *Pim, float *Qr
 
 // I3: inverse z pass A of rows y < Ny, Q (Lq, kz = k1 + A1 k2) -> P (Lz), slot p2 + A2 k1.
 template <int MY, int MZ>
-__device__ __forceinline__ void i3(const float *Qre, const float *Qim, float *Pre, float *Pim,
-                                   const float4 *__restrict__ twi) {
+__device__ __forceinline__ void i3(const float *Qre, const float *Qim, float *Pre, float *Pim, const float2 *twi) {
     using G = Geo<MY, MZ>;
     constexpr int A1 = G::A1, A2 = G::A2;
     for (int it = threadIdx.x; it < G::NYP * A1; it += kThreads) {
@@ -398,8 +405,8 @@ __device__ __forceinline__ void i3(const float *Qre, const float *Qim, float *Pr
         for (int p2 = 0; p2 < A2; ++p2) {
             CP o = v[p2];
             if (p2) {
-                const float4 w = __ldg(twi + k1 * A2 + p2);
-                o = pmulc(o, make_float2(w.x, w.y), make_float2(w.z, w.w));
+                const float2 w = twi[k1 * A2 + p2];
+                o = pmulc(o, dup2(w.x), dup2(w.y));
             }
             const int i = m * G::PZZ + 2 * (p2 + A2 * k1);
             at2(Pre, i) = o.re;
@@ -431,34 +438,60 @@ __device__ __forceinline__ void i4(const float *Pre, const float *Pim, float2 *_
     }
 }
 
-// The (y, z) part of the 3-D convolution for one x-frequency plane, in place
-// on plane [Ny][Nz] of buffer [batch][Mx][Ny][Nz] (complex64), one CTA per
-// (batch, kx).  Hz: spectrum [fold(kx)][fold(ky)][kz] (kz unfolded), scaled by
-// 1/(Mx My Mz); tw*: twiddles as (c, c, s, s), tf[j2 N1 + k1] = W^(j2 k1),
-// ti[k1 N2 + p2] = W^(k1 p2) (applied conjugated).
+// The (y, z) part of the 3-D convolution, in place on planes [Ny][Nz] of the
+// buffer [ngrids][Mx][Ny][Nz] (complex64).  One CTA per (kx, run of up to G
+// grids): the kx slice of the spectrum and the four-step twiddles are staged
+// in shared memory once and serve every plane of the run.
+// Hp: spectrum [fold(kx)][fold(ky)][fold(kz)], scaled by 1/(Mx My Mz);
+// tf[j2 N1 + k1] = W^(j2 k1), ti[k1 N2 + p2] = W^(k1 p2) (applied conjugated)
+// for axis y (tfy, tiy) and z (tfz, tiz).
 template <int MY, int MZ>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_plane_conv(float2 *__restrict__ buf, int lgMx, const float *__restrict__ Hz, const float4 *__restrict__ tfy,
-                 const float4 *__restrict__ tiy, const float4 *__restrict__ tfz, const float4 *__restrict__ tiz) {
+    k_plane_conv(float2 *__restrict__ buf, int ngrids, int gpc, int lgMx, const float *__restrict__ Hp,
+                 const float2 *__restrict__ tfy, const float2 *__restrict__ tiy, const float2 *__restrict__ tfz,
+                 const float2 *__restrict__ tiz) {
     using G = Geo<MY, MZ>;
     extern __shared__ __align__(16) float psm[];
     float *Pre = psm, *Pim = psm + G::NP, *Qre = psm + 2 * G::NP, *Qim = Qre + G::NQ;
+    float *Hs = Qim + G::NQ;
+    float2 *s_tfy = reinterpret_cast<float2 *>(Hs + G::NH), *s_tiy = s_tfy + MY, *s_tfz = s_tiy + MY,
+           *s_tiz = s_tfz + MZ;
     const int Mx = 1 << lgMx;
     const int kx = blockIdx.x & (Mx - 1), fx = kx <= Mx / 2 ? kx : Mx - kx;
-    float2 *plane = buf + int64_t(blockIdx.x) * G::Ny * G::Nz;
-    const float *Hk = Hz + int64_t(fx) * (MY / 2 + 1) * MZ;
-    f1<MY, MZ>(plane, Pre, Pim, tfz);
+    const int b0 = (blockIdx.x >> lgMx) * gpc, b1 = min(ngrids, b0 + gpc);
+    {
+        constexpr int HY = MY / 2 + 1, HZ = MZ / 2 + 1;
+        const float *Hk = Hp + int64_t(fx) * HY * HZ;
+        for (int i = threadIdx.x; i < HY * HZ; i += kThreads) {
+            const int fy = i / HZ, fz = i - fy * HZ;
+            Hs[fy * G::HSP + fz + (fz == MZ / 2 ? 1 : 0)] = __ldg(Hk + i);
+        }
+        for (int i = threadIdx.x; i < MY; i += kThreads) {
+            s_tfy[i] = __ldg(tfy + i);
+            s_tiy[i] = __ldg(tiy + i);
+        }
+        for (int i = threadIdx.x; i < MZ; i += kThreads) {
+            s_tfz[i] = __ldg(tfz + i);
+            s_tiz[i] = __ldg(tiz + i);
+        }
+    }
     __syncthreads();
-    f2<MY, MZ>(Pre, Pim, Qre, Qim);
-    __syncthreads();
-    f3<MY, MZ>(Qre, Qim, Pre, Pim, tfy);
-    __syncthreads();
-    ymid<MY, MZ>(Pre, Pim, Hk, tiy);
-    i2<MY, MZ>(Pre, Pim, Qre, Qim);
-    __syncthreads();
-    i3<MY, MZ>(Qre, Qim, Pre, Pim, tiz);
-    __syncthreads();
-    i4<MY, MZ>(Pre, Pim, plane);
+    for (int b = b0; b < b1; ++b) {
+        float2 *plane = buf + (int64_t(b) * Mx + kx) * G::Ny * G::Nz;
+        f1<MY, MZ>(plane, Pre, Pim, s_tfz);
+        __syncthreads();
+        f2<MY, MZ>(Pre, Pim, Qre, Qim);
+        __syncthreads();
+        f3<MY, MZ>(Qre, Qim, Pre, Pim, s_tfy);
+        __syncthreads();
+        ymid<MY, MZ>(Pre, Pim, Hs, s_tiy);
+        i2<MY, MZ>(Pre, Pim, Qre, Qim);
+        __syncthreads();
+        i3<MY, MZ>(Qre, Qim, Pre, Pim, s_tiz);
+        __syncthreads();
+        i4<MY, MZ>(Pre, Pim, plane);
+        __syncthreads();
+    }
 }
 
 }  // namespace plane
