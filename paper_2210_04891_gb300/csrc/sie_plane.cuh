@@ -213,19 +213,45 @@ __device__ __forceinline__ void ycol(int it, int &c, int &j) {
     }
 }
 
-// F1: z pass 1 of rows y < Ny (input z < Nz), global -> P (Lz), slot j2 + A2 k1.
+// F1: z pass 1 of rows y < Ny (input z < Nz), global -> P (Lz), slot j2 + A2 k1;
+// tw = W_Mz^(j2 k1) stored [k1][j2].  The global loads are split off (f1_load)
+// so that a CTA issues the next plane's loads while it finishes the current one.
+template <int MY, int MZ> struct F1In {
+    static constexpr int kItems = (Geo<MY, MZ>::NYP * Geo<MY, MZ>::A2 + kThreads - 1) / kThreads;
+    float2 a[kItems][Geo<MY, MZ>::A1 / 2], b[kItems][Geo<MY, MZ>::A1 / 2];   // rows 2m, 2m + 1
+};
 template <int MY, int MZ>
-__device__ __forceinline__ void f1(const float2 *__restrict__ src, float *Pre, float *Pim, const float2 *tw) {
+__device__ __forceinline__ void f1_load(const float2 *__restrict__ src, F1In<MY, MZ> &in) {
+    using G = Geo<MY, MZ>;
+    constexpr int A2 = G::A2, H1 = G::A1 / 2;
+#pragma unroll
+    for (int q = 0; q < F1In<MY, MZ>::kItems; ++q) {
+        const int it = threadIdx.x + q * kThreads;
+        if (it < G::NYP * A2) {
+            const int j2 = it % A2, m = zrow<G::NYP, A2>(it / A2);
+            const float2 *r0 = src + (2 * m) * G::Nz + j2, *r1 = r0 + G::Nz;
+#pragma unroll
+            for (int j1 = 0; j1 < H1; ++j1) {
+                in.a[q][j1] = __ldg(r0 + A2 * j1);
+                in.b[q][j1] = __ldg(r1 + A2 * j1);
+            }
+        }
+    }
+}
+template <int MY, int MZ>
+__device__ __forceinline__ void f1(const F1In<MY, MZ> &in, float *Pre, float *Pim, const float2 *tw) {
     using G = Geo<MY, MZ>;
     constexpr int A1 = G::A1, A2 = G::A2, H1 = A1 / 2;
-    for (int it = threadIdx.x; it < G::NYP * A2; it += kThreads) {
+#pragma unroll
+    for (int q = 0; q < F1In<MY, MZ>::kItems; ++q) {
+        const int it = threadIdx.x + q * kThreads;
+        if (it >= G::NYP * A2) break;
         const int j2 = it % A2, m = zrow<G::NYP, A2>(it / A2);
-        const float2 *r0 = src + (2 * m) * G::Nz + j2, *r1 = r0 + G::Nz;
         CP v[16];
 #pragma unroll
         for (int j1 = 0; j1 < A1; ++j1) {
             if (j1 < H1) {
-                const float2 a = __ldg(r0 + A2 * j1), b = __ldg(r1 + A2 * j1);
+                const float2 a = in.a[q][j1], b = in.b[q][j1];
                 v[j1] = CP{make_float2(a.x, b.x), make_float2(a.y, b.y)};
             } else {
                 v[j1] = CP{dup2(0.f), dup2(0.f)};
@@ -236,7 +262,7 @@ __device__ __forceinline__ void f1(const float2 *__restrict__ src, float *Pre, f
         for (int k1 = 0; k1 < A1; ++k1) {
             CP o = v[k1];
             if (k1) {
-                const float2 w = tw[j2 * A1 + k1];
+                const float2 w = tw[k1 * A2 + j2];
                 o = pmul(o, dup2(w.x), dup2(w.y));
             }
             const int i = m * G::PZZ + 2 * (j2 + A2 * k1);
@@ -471,14 +497,19 @@ __global__ void __launch_bounds__(kThreads, 2)
             s_tiy[i] = __ldg(tiy + i);
         }
         for (int i = threadIdx.x; i < MZ; i += kThreads) {
-            s_tfz[i] = __ldg(tfz + i);
+            // F1 reads W^(j2 k1) with lanes over j2: stored [k1][j2]
+            const int j2 = i / G::A1, k1 = i - j2 * G::A1;
+            s_tfz[k1 * G::A2 + j2] = __ldg(tfz + i);
             s_tiz[i] = __ldg(tiz + i);
         }
     }
+    const int64_t pstride = int64_t(Mx) * G::Ny * G::Nz;
+    F1In<MY, MZ> in;
+    if (b0 < b1) f1_load<MY, MZ>(buf + int64_t(b0) * pstride + int64_t(kx) * G::Ny * G::Nz, in);
     __syncthreads();
     for (int b = b0; b < b1; ++b) {
-        float2 *plane = buf + (int64_t(b) * Mx + kx) * G::Ny * G::Nz;
-        f1<MY, MZ>(plane, Pre, Pim, s_tfz);
+        float2 *plane = buf + int64_t(b) * pstride + int64_t(kx) * G::Ny * G::Nz;
+        f1<MY, MZ>(in, Pre, Pim, s_tfz);
         __syncthreads();
         f2<MY, MZ>(Pre, Pim, Qre, Qim);
         __syncthreads();
@@ -487,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         ymid<MY, MZ>(Pre, Pim, Hs, s_tiy);
         i2<MY, MZ>(Pre, Pim, Qre, Qim);
         __syncthreads();
+        if (b + 1 < b1) f1_load<MY, MZ>(plane + pstride, in);   // next plane, in flight during I3 and I4
         i3<MY, MZ>(Qre, Qim, Pre, Pim, s_tiz);
         __syncthreads();
         i4<MY, MZ>(Pre, Pim, plane);
