@@ -65,7 +65,7 @@ SM_COUNT, FP32_LANES_PER_SM = 152, 128      # GB300: 2 dies x 76 SMs, 128 FP32 F
 # current kernel, with the number of grids (3 x right-hand sides) of that capture; the
 # figure is scaled to a launch of the bench by grids.  Only kernels captured since their
 # last change are listed.
-MEASURED_TRAFFIC = {"fft_yz": (346.44e6, 48)}   # k_fft_yzc<float, 512, float>, 2 frequencies x 8 ports
+MEASURED_TRAFFIC = {"fft_yz": (347.94e6, 48)}   # k_plane_conv<128, 64>, 2 frequencies x 8 ports
 
 
 def alu_peak_tflops(sm_mhz):
