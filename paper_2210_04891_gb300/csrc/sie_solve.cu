@@ -57,16 +57,18 @@ struct PrecondState {
     std::vector<double> slot_omega;
     double2 *d_band = nullptr;        // [nslots][nunk][W + 1], band[i][d] = K[i][i-d]
     double2 *d_bandc = nullptr;       // same, column-major copy bandc[i][d] = L[i+d][i]
-    float2 *d_band32 = nullptr, *d_bandc32 = nullptr;   // FP32 roundings of both (mixed form)
+    // sweep tiles (band width <= 31, see k_pc_tiles) in FP64 and FP32, reciprocal pivots
+    std::vector<int64_t> tile_off;    // [nblk + 1] first chunk of each block
+    int64_t *d_tile_off = nullptr;
+    int64_t nchunks = 0;
+    double2 *d_tile64 = nullptr, *d_dinv64 = nullptr;
+    float2 *d_tile32 = nullptr, *d_dinv32 = nullptr;
     float2 *d_u32 = nullptr;          // FP32 sweep buffer [R][nunk]
     double2 *d_a = nullptr;           // [nslots][nb] 1/D_e
     float2 *d_a32 = nullptr;          // its FP32 rounding (mixed form)
     double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
     int32_t cap_rhs = 0;
     int32_t *d_slot = nullptr;        // [R] factor slot per right-hand side
-    // runs of right-hand sides with equal slots (one per warp; see pc_prepare)
-    int32_t *d_grp_start[2] = {nullptr, nullptr}, *d_grp_count[2] = {nullptr, nullptr};
-    int32_t ngroups[2] = {0, 0};
     int *d_status = nullptr;
     std::vector<void *> allocs;
 };
@@ -74,11 +76,9 @@ struct PrecondState {
 void plan_free_precond(pfft_plan *p) {
     if (!p || !p->pc) return;
     for (void *a : p->pc->allocs) cudaFree(a);
-    for (void *a : {(void *)p->pc->d_band32, (void *)p->pc->d_bandc32, (void *)p->pc->d_u32, (void *)p->pc->d_a32})
+    for (void *a : {(void *)p->pc->d_tile64, (void *)p->pc->d_dinv64, (void *)p->pc->d_tile32,
+                    (void *)p->pc->d_dinv32, (void *)p->pc->d_u32, (void *)p->pc->d_a32})
         if (a) cudaFree(a);
-    for (int v = 0; v < 2; ++v)
-        for (void *a : {(void *)p->pc->d_grp_start[v], (void *)p->pc->d_grp_count[v]})
-            if (a) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
                     (void *)p->pc->d_ibr, (void *)p->pc->d_slot})
         if (a) cudaFree(a);
@@ -271,8 +271,13 @@ int build_symbolic(pfft_plan *p) {
     std::vector<int32_t> port_loop(std::max<int64_t>(np, 1), 0);
     for (int64_t q = 0; q < np; ++q) port_loop[q] = L->loop_of_branch[nb + q];
     std::vector<int64_t> bo(s->blk_off);
+    s->tile_off.assign(1, 0);
+    for (size_t k = 0; k + 1 < bo.size(); ++k) s->tile_off.push_back(s->tile_off.back() + (bo[k + 1] - bo[k] + 31) / 32);
+    s->nchunks = s->tile_off.back();
+    std::vector<int64_t> to(s->tile_off);
     int rc;
     if ((rc = pc_upload(s, &s->d_blk_off, bo))) return rc;
+    if ((rc = pc_upload(s, &s->d_tile_off, to))) return rc;
     if ((rc = pc_upload(s, &s->d_unk_of_node, unk))) return rc;
     if ((rc = pc_upload(s, &s->d_off_ptr, off_ptr))) return rc;
     if ((rc = pc_upload(s, &s->d_off_port, off_port))) return rc;
@@ -472,83 +477,121 @@ template <typename V> __device__ __forceinline__ V shfl_c(V v, int src) {
     return v;
 }
 
-// Band solve L d L^T u = rhs of one conductor block for RB right-hand sides
-// that share a factor slot (requires W <= 31), one warp, after assembling
-// rhs_i = -sum over the incident branches of s * kappa_e.
+// Band solve L d L^T u = rhs of one conductor block for one right-hand side,
+// one warp (requires W <= 31), after assembling rhs_i = -sum over the incident
+// branches of s * kappa_e.
 //
 // The sweeps keep a circular window in registers: lane (row mod 32) holds the
 // running value of its row for the 32 rows from the current pivot on.  A step
 // broadcasts the finished pivot with a shuffle, every lane subtracts its band
 // entry times the pivot, and the pivot's lane takes over the row 32 further
-// on.  The band is staged into shared memory 32 rows at a time with
-// asynchronous copies issued two chunks ahead, at a pitch of 32 entries: a
-// lane's entry of a step sits at (step, (lane - step) mod 32) and every entry
-// the copies do not write (the diagonal, distances beyond W) stays zero, so a
-// full chunk runs unrolled with no bounds tests.  The factor stores zeros
-// outside the block (forward: i + d >= n; backward: i - d < 0).
+// on.  The band entries come from sweep tiles built with the factor: per chunk
+// of 32 pivots, tile[lane][step] (pitch 33) is the entry lane `lane` applies at
+// step `step` (zero where it has none), so a step reads its entry with one
+// shared-memory load at a fixed offset, conflict-free, and no index
+// arithmetic.  Tiles are copied into shared memory two chunks ahead.
 constexpr int PC_CH = 32;
+constexpr int PC_TP = 33;                          // tile pitch (complex)
+constexpr int PC_TILE = PC_CH * PC_TP;             // complex per tile
+
+// tiles[slot][dir][chunk][lane][PC_TP]: dir 0 forward (entries of L below the
+// pivot, from bandc), dir 1 backward (from band); chunk c of block b covers
+// pivots 32 c .. 32 c + 31 (forward) or n-1-32c .. n-32-32c (backward).
+template <typename T>
+__global__ void k_pc_tiles(const double2 *__restrict__ band, const double2 *__restrict__ bandc,
+                           const int64_t *__restrict__ blk_off, const int64_t *__restrict__ tile_off, int32_t nblk,
+                           int32_t W, int64_t nunk, int64_t nchunks, int32_t ns, C<T> *__restrict__ tiles) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t per = nchunks * PC_TILE;
+    if (i >= int64_t(ns) * 2 * per) return;
+    const int j = int(i % PC_TP);
+    int64_t t = i / PC_TP;
+    const int L = int(t % PC_CH);
+    t /= PC_CH;
+    const int64_t gc = t % nchunks;
+    t /= nchunks;
+    const int dir = int(t % 2);
+    const int64_t s = t / 2;
+    int lo = 0, hi = nblk - 1;   // block holding chunk gc: tile_off[b] <= gc < tile_off[b + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (tile_off[mid] <= gc) lo = mid; else hi = mid - 1;
+    }
+    const int64_t c = gc - tile_off[lo], o = blk_off[lo], n = blk_off[lo + 1] - o;
+    C<T> v = mk<T>(T(0), T(0));
+    if (j < PC_CH) {
+        const int d = (L - j) & 31;
+        const int64_t row = dir == 0 ? PC_CH * c + j : n - 1 - PC_CH * c - j;
+        const bool ok = d >= 1 && d <= W && row >= 0 && row < n && (dir == 0 ? row + d < n : row - d >= 0);
+        if (ok) {
+            const double2 e = (dir == 0 ? bandc : band)[(s * nunk + o + row) * (W + 1) + d];
+            v = mk<T>(T(e.x), T(e.y));
+        }
+    }
+    tiles[i] = v;
+}
+
+// dinv[slot][i] = 1 / d_i, the reciprocal pivots of the LDL^T factor (FP64, rounded to T).
+template <typename T>
+__global__ void k_pc_dinv(const double2 *__restrict__ band, int64_t total, int32_t Wp, C<T> *__restrict__ dinv) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const double2 d = band[i * Wp];
+    const double den = d.x * d.x + d.y * d.y;
+    dinv[i] = mk<T>(T(d.x / den), T(-d.y / den));
+}
+
+// copy one tile into shared memory with 16-byte asynchronous copies
+template <typename T>
+__device__ __forceinline__ void pc_stage_tile(C<T> *dst, const C<T> *src, int lane) {
+    constexpr int n16 = PC_TILE * int(sizeof(C<T>)) / 16;
+    const unsigned s0 = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    const char *g = reinterpret_cast<const char *>(src);
+    for (int k = lane; k < n16; k += 32)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0 + 16u * unsigned(k)), "l"(g + 16 * k));
+}
+
+// One step of a sweep: pivot j of the chunk; tl = this lane's tile row.
+template <typename T>
+__device__ __forceinline__ void pc_step(const C<T> *tl, int j, int lane, C<T> &w, const C<T> &pf, C<T> &done) {
+    const C<T> l = tl[j];
+    const C<T> xi = shfl_c(w, j);
+    const C<T> t = csub(w, cmul(l, xi));
+    const bool me = lane == j;
+    done = me ? xi : done;
+    w = me ? pf : t;
+}
 
 template <typename T>
-__device__ __forceinline__ void pc_stage32(C<T> *dst, const C<T> *src, int64_t row0, int W, int64_t n, int lane) {
-    // entries d = 1..W of rows [row0, row0 + 32) of a [n][W + 1] band -> dst[(row - row0) * 32 + d];
-    // lane d copies entry d of every row
-    const int Wp = W + 1;
-    const bool mine = lane >= 1 && lane <= W;
-    const unsigned s0 = static_cast<unsigned>(__cvta_generic_to_shared(dst + lane));
-#pragma unroll 8
-    for (int r = 0; r < PC_CH; ++r) {
-        const int64_t i = row0 + r;
-        if (!mine || i < 0 || i >= n) continue;
-        const unsigned saddr = s0 + unsigned(r * PC_CH * sizeof(C<T>));
-        const C<T> *g = src + i * Wp + lane;
-        if constexpr (sizeof(C<T>) == 8)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(g));
-        else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g));
-    }
-}
-
-// One step of a sweep: pivot j of the chunk, its band entries at row jr of the staged chunk.
-template <typename T, int RB>
-__device__ __forceinline__ void pc_step(const C<T> *bs, int j, int jr, int lane, C<T> (&w)[RB], C<T> (&pf)[RB],
-                                        C<T> (&done)[RB]) {
-    const C<T> l = bs[jr * PC_CH + ((lane - j) & 31)];
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-        const C<T> xi = shfl_c(w[k], j);
-        w[k] = csub(w[k], cmul(l, xi));
-        if (lane == j) { done[k] = xi; w[k] = pf[k]; }
-    }
-}
-
-template <typename T, int RB>
-__global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
+__global__ void __launch_bounds__(128, 3) k_pc_sweep(
     const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
-    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
-    int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
-    const int32_t *__restrict__ grp_start, const int32_t *__restrict__ grp_count, int32_t ngroups,
-    C<T> *__restrict__ xs) {
+    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, const int64_t *__restrict__ tile_off,
+    int32_t nblk, int64_t nunk, int64_t nchunks, int64_t nb, const C<T> *__restrict__ tiles,
+    const C<T> *__restrict__ dinv, const int32_t *__restrict__ slot, int32_t R, C<T> *__restrict__ xs) {
     extern __shared__ __align__(16) unsigned char pc_smem[];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    if (wid >= int64_t(ngroups) * nblk) return;
-    const int32_t g = int32_t(wid / nblk), b = int32_t(wid % nblk);
-    const int32_t r0 = grp_start[g], nr = grp_count[g];
+    if (wid >= int64_t(R) * nblk) return;
+    const int32_t r = int32_t(wid / nblk), b = int32_t(wid % nblk);
     const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
-    const int Wp = W + 1;
-    const C<T> *B = band + (int64_t(slot[r0]) * nunk + o) * Wp;
-    const C<T> *Bc = bandc + (int64_t(slot[r0]) * nunk + o) * Wp;
+    const int64_t sl = slot[r];
+    const C<T> *Tf = tiles + ((sl * 2 + 0) * nchunks + tile_off[b]) * PC_TILE;
+    const C<T> *Tb = tiles + ((sl * 2 + 1) * nchunks + tile_off[b]) * PC_TILE;
+    const C<T> *dv = dinv + sl * nunk + o;
     const C<T> zero = mk<T>(T(0), T(0));
-    C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_CH * PC_CH;   // [warp][2][32][32]
-    C<T> *buf1 = buf0 + PC_CH * PC_CH;
-    for (int t = lane; t < 2 * PC_CH * PC_CH; t += 32) buf0[t] = zero;
-    // right-hand sides of the nodal system; four rows per lane and step so that
-    // their gathers overlap (a triangle node has up to three branches)
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-        if (k >= nr) break;
-        const C<T> *kr = kappa + int64_t(r0 + k) * nb;
-        C<T> *x = xs + int64_t(r0 + k) * nunk + o;
+    C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_TILE;   // [warp][2][PC_TILE]
+    C<T> *buf1 = buf0 + PC_TILE;
+    C<T> *x = xs + int64_t(r) * nunk + o;
+    const int64_t nch = (n + PC_CH - 1) / PC_CH;
+    // first two forward tiles in flight while the right-hand sides are assembled
+    pc_stage_tile<T>(buf0, Tf, lane);
+    asm volatile("cp.async.commit_group;\n" ::);
+    if (nch > 1) pc_stage_tile<T>(buf1, Tf + PC_TILE, lane);
+    asm volatile("cp.async.commit_group;\n" ::);
+    {
+        // right-hand sides of the nodal system; four rows per lane and step so
+        // that their gathers overlap (a triangle node has up to three branches)
+        const C<T> *kr = kappa + int64_t(r) * nb;
         for (int64_t i0 = lane; i0 < n; i0 += 4 * 32) {
             int32_t qa[4], qb[4];
             C<T> acc[4];
@@ -576,89 +619,53 @@ __global__ void __launch_bounds__(128, 1) k_pc_solve_grp(
         }
     }
     __syncwarp();
-    const int64_t nch = (n + PC_CH - 1) / PC_CH;
-    C<T> w[RB], pf[RB], pn[RB], done[RB];
-    // ---------------- forward: y_{i+d} -= L[i+d][i] y_i   (chunk c = steps [32c, 32c+32))
-    pc_stage32<T>(buf0, Bc, 0, W, n, lane);
-    asm volatile("cp.async.commit_group;\n" ::);
-    pc_stage32<T>(buf1, Bc, PC_CH, W, n, lane);
-    asm volatile("cp.async.commit_group;\n" ::);
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-        const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
-        w[k] = lane < n ? x[lane] : zero;
-        pf[k] = lane + 32 < n ? x[lane + 32] : zero;
-        done[k] = zero;
-    }
+    // ---------------- forward: y_{i+d} -= L[i+d][i] y_i, then y_i /= d_i at the store
+    C<T> w = lane < n ? x[lane] : zero, pf = lane + 32 < n ? x[lane + 32] : zero, done = zero;
     for (int64_t c = 0; c < nch; ++c) {
         const int64_t base = c * PC_CH;
-#pragma unroll
-        for (int k = 0; k < RB; ++k) {          // rows taken over during chunk c + 1
-            const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
-            pn[k] = base + 64 + lane < n ? x[base + 64 + lane] : zero;
-        }
-        // pivot of the row this lane finishes in chunk c (the diagonal step is applied at the store)
-        const C<T> dg = base + lane < n ? B[(base + lane) * Wp] : mk<T>(T(1), T(0));
+        const C<T> pn = base + 64 + lane < n ? x[base + 64 + lane] : zero;   // row taken over in chunk c + 1
+        const C<T> di = base + lane < n ? dv[base + lane] : zero;
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
-        const C<T> *bs = (c & 1) ? buf1 : buf0;
+        const C<T> *tl = ((c & 1) ? buf1 : buf0) + lane * PC_TP;
         if (base + PC_CH <= n) {
 #pragma unroll
-            for (int j = 0; j < PC_CH; ++j) pc_step<T, RB>(bs, j, j, lane, w, pf, done);
+            for (int j = 0; j < PC_CH; ++j) pc_step<T>(tl, j, lane, w, pf, done);
         } else {
-            for (int j = 0; j < int(n - base); ++j) pc_step<T, RB>(bs, j, j, lane, w, pf, done);
+            for (int j = 0; j < int(n - base); ++j) pc_step<T>(tl, j, lane, w, pf, done);
         }
-        {
-            const T den = dg.x * dg.x + dg.y * dg.y;
-            const C<T> inv = mk<T>(dg.x / den, -dg.y / den);
-#pragma unroll
-            for (int k = 0; k < RB; ++k) {
-                if (k < nr && base + lane < n) xs[int64_t(r0 + k) * nunk + o + base + lane] = cmul(done[k], inv);
-                pf[k] = pn[k];
-            }
-        }
+        if (base + lane < n) x[base + lane] = cmul(done, di);
+        pf = pn;
         __syncwarp();
-        pc_stage32<T>((c & 1) ? buf1 : buf0, Bc, base + 2 * PC_CH, W, n, lane);
+        if (c + 2 < nch) pc_stage_tile<T>((c & 1) ? buf1 : buf0, Tf + (c + 2) * PC_TILE, lane);
         asm volatile("cp.async.commit_group;\n" ::);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     __syncwarp();
-    // ---------------- backward: x_{i-d} -= L[i][i-d] x_i   (chunk c = steps i = n-1-32c-j)
-    // staged rows of chunk c: [n - 32(c+1), n - 32c), row i at index i - (n - 32(c+1))
-    pc_stage32<T>(buf0, B, n - PC_CH, W, n, lane);
+    // ---------------- backward: x_{i-d} -= L[i][i-d] x_i   (chunk c = pivots i = n-1-32c-j)
+    pc_stage_tile<T>(buf0, Tb, lane);
     asm volatile("cp.async.commit_group;\n" ::);
-    pc_stage32<T>(buf1, B, n - 2 * PC_CH, W, n, lane);
+    if (nch > 1) pc_stage_tile<T>(buf1, Tb + PC_TILE, lane);
     asm volatile("cp.async.commit_group;\n" ::);
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-        const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
-        w[k] = n - 1 - lane >= 0 ? x[n - 1 - lane] : zero;
-        pf[k] = n - 33 - lane >= 0 ? x[n - 33 - lane] : zero;
-        done[k] = zero;
-    }
+    w = n - 1 - lane >= 0 ? x[n - 1 - lane] : zero;
+    pf = n - 33 - lane >= 0 ? x[n - 33 - lane] : zero;
+    done = zero;
     for (int64_t c = 0; c < nch; ++c) {
-        const int64_t top = n - 1 - c * PC_CH;          // i of step j = 0
-#pragma unroll
-        for (int k = 0; k < RB; ++k) {
-            const C<T> *x = xs + int64_t(r0 + (k < nr ? k : 0)) * nunk + o;
-            pn[k] = top - 64 - lane >= 0 ? x[top - 64 - lane] : zero;
-        }
+        const int64_t top = n - 1 - c * PC_CH;          // pivot of step j = 0
+        const C<T> pn = top - 64 - lane >= 0 ? x[top - 64 - lane] : zero;
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
-        const C<T> *bs = (c & 1) ? buf1 : buf0;
+        const C<T> *tl = ((c & 1) ? buf1 : buf0) + lane * PC_TP;
         if (top - (PC_CH - 1) >= 0) {
 #pragma unroll
-            for (int j = 0; j < PC_CH; ++j) pc_step<T, RB>(bs, j, PC_CH - 1 - j, lane, w, pf, done);
+            for (int j = 0; j < PC_CH; ++j) pc_step<T>(tl, j, lane, w, pf, done);
         } else {
-            for (int j = 0; j <= int(top); ++j) pc_step<T, RB>(bs, j, PC_CH - 1 - j, lane, w, pf, done);
+            for (int j = 0; j <= int(top); ++j) pc_step<T>(tl, j, lane, w, pf, done);
         }
-#pragma unroll
-        for (int k = 0; k < RB; ++k) {   // final values in place (every row still to be read lies below)
-            if (k < nr && top - lane >= 0) xs[int64_t(r0 + k) * nunk + o + top - lane] = done[k];
-            pf[k] = pn[k];
-        }
+        if (top - lane >= 0) x[top - lane] = done;   // final values in place (every row still to be read lies below)
+        pf = pn;
         __syncwarp();
-        pc_stage32<T>((c & 1) ? buf1 : buf0, B, n - (c + 3) * PC_CH, W, n, lane);
+        if (c + 2 < nch) pc_stage_tile<T>((c & 1) ? buf1 : buf0, Tb + (c + 2) * PC_TILE, lane);
         asm volatile("cp.async.commit_group;\n" ::);
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -732,34 +739,14 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         s->cap_rhs = R;
     }
     SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    for (int v = 0; v < 2; ++v) {
-        // one right-hand side per warp: the sweeps are latency-bound chains, so
-        // independent chains (right-hand sides x conductors) are what fills the GPU
-        const int32_t gmax = 1;
-        std::vector<int32_t> gs, gc;
-        for (int32_t r = 0; r < R;) {
-            int32_t e = r + 1;
-            while (e < R && e - r < gmax && slot[e] == slot[r]) ++e;
-            gs.push_back(r);
-            gc.push_back(e - r);
-            r = e;
-        }
-        if (s->d_grp_start[v]) cudaFree(s->d_grp_start[v]);
-        if (s->d_grp_count[v]) cudaFree(s->d_grp_count[v]);
-        SIE_CUDA(cudaMalloc((void **)&s->d_grp_start[v], gs.size() * sizeof(int32_t)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_grp_count[v], gc.size() * sizeof(int32_t)));
-        SIE_CUDA(cudaMemcpyAsync(s->d_grp_start[v], gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        SIE_CUDA(cudaMemcpyAsync(s->d_grp_count[v], gc.data(), gc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        SIE_CUDA(cudaStreamSynchronize(st));
-        s->ngroups[v] = int32_t(gs.size());
-    }
     if (uniq == s->slot_omega) return SIE_OK;   // factors cached
     const int32_t ns = int32_t(uniq.size());
     if (s->d_band) cudaFree(s->d_band);
     if (s->d_bandc) cudaFree(s->d_bandc);
-    if (s->d_band32) cudaFree(s->d_band32);
-    if (s->d_bandc32) cudaFree(s->d_bandc32);
-    s->d_band32 = s->d_bandc32 = nullptr;
+    for (void *q : {(void *)s->d_tile64, (void *)s->d_dinv64, (void *)s->d_tile32, (void *)s->d_dinv32})
+        if (q) cudaFree(q);
+    s->d_tile64 = s->d_dinv64 = nullptr;
+    s->d_tile32 = s->d_dinv32 = nullptr;
     if (s->d_a) cudaFree(s->d_a);
     if (s->d_a32) cudaFree(s->d_a32);
     s->d_band = nullptr;
@@ -769,8 +756,14 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     s->slot_omega.clear();
     SIE_CUDA(cudaMalloc((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
-    SIE_CUDA(cudaMalloc((void **)&s->d_band32, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(float2)));
-    SIE_CUDA(cudaMalloc((void **)&s->d_bandc32, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(float2)));
+    const bool tiled = s->W <= 31 && s->nunk > 0;
+    const int64_t ntile = int64_t(ns) * 2 * s->nchunks * PC_TILE;
+    if (tiled) {
+        SIE_CUDA(cudaMalloc((void **)&s->d_tile64, size_t(ntile) * sizeof(double2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_tile32, size_t(ntile) * sizeof(float2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_dinv64, size_t(ns) * s->nunk * sizeof(double2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_dinv32, size_t(ns) * s->nunk * sizeof(float2)));
+    }
     SIE_CUDA(cudaMalloc((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_a32, size_t(ns) * p->nb * sizeof(float2)));
     std::vector<double> zc(size_t(ns) * (p->ncond + 1));
@@ -794,11 +787,19 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         k_pc_factor<<<ns * nblk, 256, 0, st>>>(s->d_blk_off, nblk, s->W, s->nunk, s->d_row_ptr, s->d_row_br,
                                                 s->d_row_oth, s->d_a, p->nb, s->d_band, s->d_bandc, s->d_status);
         SIE_LAUNCH_CHECK(p);
-        const int64_t nbnd = int64_t(ns) * s->nunk * (s->W + 1);
-        k_round_c<<<nblk_(nbnd), 256, 0, st>>>(s->d_band, s->d_band32, nbnd);
-        SIE_LAUNCH_CHECK(p);
-        k_round_c<<<nblk_(nbnd), 256, 0, st>>>(s->d_bandc, s->d_bandc32, nbnd);
-        SIE_LAUNCH_CHECK(p);
+        if (tiled) {
+            k_pc_tiles<double><<<nblk_(ntile), 256, 0, st>>>(s->d_band, s->d_bandc, s->d_blk_off, s->d_tile_off, nblk,
+                                                               s->W, s->nunk, s->nchunks, ns, s->d_tile64);
+            SIE_LAUNCH_CHECK(p);
+            k_pc_tiles<float><<<nblk_(ntile), 256, 0, st>>>(s->d_band, s->d_bandc, s->d_blk_off, s->d_tile_off, nblk,
+                                                              s->W, s->nunk, s->nchunks, ns, s->d_tile32);
+            SIE_LAUNCH_CHECK(p);
+            const int64_t nd = int64_t(ns) * s->nunk;
+            k_pc_dinv<double><<<nblk_(nd), 256, 0, st>>>(s->d_band, nd, s->W + 1, s->d_dinv64);
+            SIE_LAUNCH_CHECK(p);
+            k_pc_dinv<float><<<nblk_(nd), 256, 0, st>>>(s->d_band, nd, s->W + 1, s->d_dinv32);
+            SIE_LAUNCH_CHECK(p);
+        }
     }
     int status = 0;
     SIE_CUDA(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -828,16 +829,15 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
     SIE_LAUNCH_CHECK(p);
     if (s->nunk > 0) {
         if (s->W <= 31) {
-            const int v = f32 ? 0 : 1;
-            const int64_t gw = int64_t(s->ngroups[v]) * nblk;
-            const size_t sm = size_t(4) * 2 * PC_CH * PC_CH * sizeof(C<T>);
-            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_solve_grp<T, 1>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-            const C<T> *band, *bandc;
-            if constexpr (f32) { band = s->d_band32; bandc = s->d_bandc32; } else { band = s->d_band; bandc = s->d_bandc; }
-            k_pc_solve_grp<T, 1><<<nblk_(gw * 32, 128), 128, sm, st>>>(
-                kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band, bandc,
-                s->d_slot, s->d_grp_start[v], s->d_grp_count[v], s->ngroups[v], u);
+            // four warps per CTA, two tiles of shared memory per warp
+            const size_t sm = size_t(4) * 2 * PC_TILE * sizeof(C<T>);
+            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(sm)));
+            const C<T> *tiles, *dinv;
+            if constexpr (f32) { tiles = s->d_tile32; dinv = s->d_dinv32; } else { tiles = s->d_tile64; dinv = s->d_dinv64; }
+            k_pc_sweep<T><<<nblk_(int64_t(R) * nblk * 32, 128), 128, sm, st>>>(
+                kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, s->d_tile_off, nblk, s->nunk, s->nchunks,
+                p->nb, tiles, dinv, s->d_slot, R, u);
         } else {
             if constexpr (f32) return fail(SIE_ERR_ARG, "preconditioner: FP32 sweeps need a band width <= 31");
             else
