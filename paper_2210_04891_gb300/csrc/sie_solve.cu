@@ -551,15 +551,27 @@ __device__ __forceinline__ void pc_stage_tile(C<T> *dst, const C<T> *src, int la
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0 + 16u * unsigned(k)), "l"(g + 16 * k));
 }
 
-// One step of a sweep: pivot j of the chunk; tl = this lane's tile row.
+// One step of a sweep: pivot j of the chunk; tl = this lane's tile row.  The
+// update w - l xi is fused (four FMAs); the pivot's lane keeps xi and takes pf.
 template <typename T>
 __device__ __forceinline__ void pc_step(const C<T> *tl, int j, int lane, C<T> &w, const C<T> &pf, C<T> &done) {
     const C<T> l = tl[j];
     const C<T> xi = shfl_c(w, j);
-    const C<T> t = csub(w, cmul(l, xi));
+    const T tx = fma(-l.x, xi.x, fma(l.y, xi.y, w.x));
+    const T ty = fma(-l.x, xi.y, fma(-l.y, xi.x, w.y));
     const bool me = lane == j;
-    done = me ? xi : done;
-    w = me ? pf : t;
+    done.x = me ? xi.x : done.x;
+    done.y = me ? xi.y : done.y;
+    w.x = me ? pf.x : tx;
+    w.y = me ? pf.y : ty;
+}
+// the 32 steps of a full chunk, unrolled at compile time
+template <typename T, int J>
+__device__ __forceinline__ void pc_chunk(const C<T> *tl, int lane, C<T> &w, const C<T> &pf, C<T> &done) {
+    if constexpr (J < PC_CH) {
+        pc_step<T>(tl, J, lane, w, pf, done);
+        pc_chunk<T, J + 1>(tl, lane, w, pf, done);
+    }
 }
 
 template <typename T>
@@ -629,8 +641,7 @@ __global__ void __launch_bounds__(128, 3) k_pc_sweep(
         __syncwarp();
         const C<T> *tl = ((c & 1) ? buf1 : buf0) + lane * PC_TP;
         if (base + PC_CH <= n) {
-#pragma unroll
-            for (int j = 0; j < PC_CH; ++j) pc_step<T>(tl, j, lane, w, pf, done);
+            pc_chunk<T, 0>(tl, lane, w, pf, done);
         } else {
             for (int j = 0; j < int(n - base); ++j) pc_step<T>(tl, j, lane, w, pf, done);
         }
@@ -657,8 +668,7 @@ __global__ void __launch_bounds__(128, 3) k_pc_sweep(
         __syncwarp();
         const C<T> *tl = ((c & 1) ? buf1 : buf0) + lane * PC_TP;
         if (top - (PC_CH - 1) >= 0) {
-#pragma unroll
-            for (int j = 0; j < PC_CH; ++j) pc_step<T>(tl, j, lane, w, pf, done);
+            pc_chunk<T, 0>(tl, lane, w, pf, done);
         } else {
             for (int j = 0; j <= int(top); ++j) pc_step<T>(tl, j, lane, w, pf, done);
         }
