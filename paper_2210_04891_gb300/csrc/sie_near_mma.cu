@@ -132,9 +132,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
                     tc::bulk_g2s(st, a.Ac + u * (kARaw / 4), 2 * kARaw, &raw_full[s]);
                     for (int j = 0; j < 2; ++j) {
                         const int64_t t = a.u_tri[u + j];
-                        for (int l = 0; l < 3; ++l)
-                            tc::bulk_g2s(st + 2 * kARaw + (3 * j + l) * kXRow,
-                                         a.cT + (t * 3 + l) * R + int64_t(slab) * kSlabRhs, xbytes, &raw_full[s]);
+                        const float2 *src = a.cT + t * 3 * R + int64_t(slab) * kSlabRhs;
+                        if (R == kSlabRhs) {   // the triangle's three rows are one contiguous 3 KB block
+                            tc::bulk_g2s(st + 2 * kARaw + 3 * j * kXRow, src, 3 * kXRow, &raw_full[s]);
+                        } else {
+                            for (int l = 0; l < 3; ++l)
+                                tc::bulk_g2s(st + 2 * kARaw + (3 * j + l) * kXRow, src + l * R, xbytes, &raw_full[s]);
+                        }
                     }
                 }
             }
