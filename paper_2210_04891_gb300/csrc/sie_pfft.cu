@@ -75,7 +75,8 @@ __device__ __forceinline__ float4 shfl_up(float4 v, int d) {
 }
 
 // Inclusive prefix sum of each row of a [R][n] array of elements, in place.
-// One CTA of 1024 threads per row, 4 items per thread per chunk.
+// One CTA of 1024 threads per row, 4 items per thread per chunk; the next
+// chunk's loads are issued before the current chunk's block scan.
 template <typename E>
 __global__ void __launch_bounds__(1024) k_scan_rows(E *buf, int64_t n) {
     __shared__ E warp_tot[32];
@@ -83,13 +84,25 @@ __global__ void __launch_bounds__(1024) k_scan_rows(E *buf, int64_t n) {
     E *row = buf + blockIdx.x * n;
     E carry = ezero<E>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    E vn[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = 4 * int64_t(threadIdx.x) + k;
+        vn[k] = i < n ? row[i] : ezero<E>();
+    }
     for (int64_t base = 0; base < n; base += 4 * 1024) {
         E v[4];
-        E run = ezero<E>();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = vn[k];
         const int64_t i0 = base + 4 * int64_t(threadIdx.x);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            v[k] = (i0 + k < n) ? row[i0 + k] : ezero<E>();
+            const int64_t i = i0 + 4 * 1024 + k;
+            vn[k] = i < n ? row[i] : ezero<E>();
+        }
+        E run = ezero<E>();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
             run = eadd(run, v[k]);
             v[k] = run;
         }
@@ -126,25 +139,27 @@ __global__ void __launch_bounds__(1024) k_scan_rows(E *buf, int64_t n) {
 
 // Tour values for A^T: at node v's enter slot the current the links inject
 // into v (+x on links entering v, -x on links leaving it); 0 at exit slots.
+// Grid (slots, right-hand sides).
 template <typename E>
 __global__ void k_tour_inject(const double2 *__restrict__ x, int64_t nl, E *__restrict__ tour, int64_t nslots,
                               const int32_t *__restrict__ tour_node, const int8_t *__restrict__ tour_enter,
                               const int32_t *__restrict__ nl_ptr, const int32_t *__restrict__ nl_loop,
-                              const int8_t *__restrict__ nl_sign, int32_t nrhs) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= nslots * nrhs) return;
-    int64_t r = i / nslots, s = i % nslots;
+                              const int8_t *__restrict__ nl_sign) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const int64_t r = blockIdx.y;
     E out = ezero<E>();
     const int v = tour_node[s];
     if (tour_enter[s] && nl_ptr[v] < nl_ptr[v + 1]) {
+        const double2 *xr = x + r * nl;
         double2 acc = make_double2(0.0, 0.0);   // a few link currents, exact inputs
         for (int k = nl_ptr[v]; k < nl_ptr[v + 1]; ++k) {
-            const double2 xv = x[r * nl + nl_loop[k]];
+            const double2 xv = xr[nl_loop[k]];
             acc = nl_sign[k] > 0 ? cadd(acc, xv) : csub(acc, xv);
         }
         eset(out, acc);
     }
-    tour[i] = out;
+    tour[r * nslots + s] = out;
 }
 
 // Branch current of branch b for right-hand side r (loop space): a link carries
@@ -217,12 +232,14 @@ template <typename T, int V> __device__ __forceinline__ void stv(C<T> *p, const 
 // acc[a][j][v] += sum over the records e of row [e0, e1) of
 //                 sum_b rec_e.b[3a+b] X[col_e][b][r],   r = rl + 32 V j + v.
 // X is [rows][3][R] (right-hand sides innermost).  FULL: every r < R.
-template <typename T, int V, int J, bool FULL>
+// UNR records in flight per warp (measured: 1 for the projection, 4 for the
+// interpolation and the triangle gathers).
+template <typename T, int V, int J, bool FULL, int UNR = 4>
 __device__ __forceinline__ void gather_rows(const Rec<T> *__restrict__ rec, int64_t e0, int64_t e1,
                                             const C<T> *__restrict__ X, int32_t R, int32_t rl,
                                             C<T> (&acc)[3][J][V]) {
     const int64_t ld = 3 * int64_t(R);
-#pragma unroll 2
+#pragma unroll UNR
     for (int64_t e = e0; e < e1; ++e) {
         T b[9];
         const int64_t col = load_rec<T>(rec + e, b);
@@ -283,8 +300,8 @@ __global__ void __launch_bounds__(256) k_project(const int64_t *__restrict__ ptr
     C<T> acc[3][J][V];
     zero<T, V, J>(acc);
     if (n < Ng) {
-        if (rbase + SLAB <= R) gather_rows<T, V, J, true>(rec, ptr[n], ptr[n + 1], cT, R, rl, acc);
-        else gather_rows<T, V, J, false>(rec, ptr[n], ptr[n + 1], cT, R, rl, acc);
+        if (rbase + SLAB <= R) gather_rows<T, V, J, true, 1>(rec, ptr[n], ptr[n + 1], cT, R, rl, acc);
+        else gather_rows<T, V, J, false, 1>(rec, ptr[n], ptr[n + 1], cT, R, rl, acc);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -458,22 +475,22 @@ __global__ void k_branch_out(const E *__restrict__ y_tri, const int32_t *__restr
 
 // Tour values for A: +delta(v) at v's enter slot, -delta(v) at its exit slot,
 // delta(v) = voltage of v's parent twig walked from v towards the root.
+// Grid (slots, right-hand sides).
 template <typename E>
 __global__ void k_tour_voltage(const E *__restrict__ y_br, int64_t ldy, E *__restrict__ tour, int64_t nslots,
                                const int32_t *__restrict__ tour_node, const int8_t *__restrict__ tour_enter,
-                               const int32_t *__restrict__ parent_branch, const int32_t *__restrict__ tail,
-                               int32_t nrhs) {
-    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= nslots * nrhs) return;
-    int64_t r = i / nslots, s = i % nslots;
-    int v = tour_node[s];
-    int t = parent_branch[v];
+                               const int32_t *__restrict__ parent_branch, const int32_t *__restrict__ tail) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const int64_t r = blockIdx.y;
+    const int v = tour_node[s];
+    const int t = parent_branch[v];
     E d = ezero<E>();
     if (t >= 0) {
         d = y_br[r * ldy + t];
         if ((tail[t] != v) != !tour_enter[s]) d = eneg(d);
     }
-    tour[i] = d;
+    tour[r * nslots + s] = d;
 }
 
 template <typename E>
@@ -606,8 +623,9 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     E *y_tri = (E *)s.y_tri, *y_br = (E *)s.y_br;
     std::unique_ptr<StageTimer> tm(new StageTimer(p, SIE_STAGE_LOOP_TO_BRANCH, st));
     if (space == SIE_SPACE_LOOP) {
-        k_tour_inject<<<nblk(nslots * R), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tour_node, p->d_tour_enter,
-                                                         p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign, R);
+        k_tour_inject<<<dim3(nblk(nslots), unsigned(R)), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tour_node,
+                                                                         p->d_tour_enter, p->d_nl_ptr, p->d_nl_loop,
+                                                                         p->d_nl_sign);
         SIE_LAUNCH_CHECK(p);
         k_scan_rows<E><<<R, 1024, 0, st>>>(tour, nslots);
         SIE_LAUNCH_CHECK(p);
@@ -651,8 +669,8 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     k_branch_out<E, E><<<nblk(ldy * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, ldy, R,
                                                         y_br);
     SIE_LAUNCH_CHECK(p);
-    k_tour_voltage<E><<<nblk(nslots * R), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_tour_node, p->d_tour_enter,
-                                                         p->d_parent_branch, p->d_tail, R);
+    k_tour_voltage<E><<<dim3(nblk(nslots), unsigned(R)), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_tour_node,
+                                                                       p->d_tour_enter, p->d_parent_branch, p->d_tail);
     SIE_LAUNCH_CHECK(p);
     k_scan_rows<E><<<R, 1024, 0, st>>>(tour, nslots);
     SIE_LAUNCH_CHECK(p);
