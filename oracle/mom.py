@@ -9,6 +9,13 @@ L = Im Z / w; the loop values R_o, L_o of Sec. V-D follow from Z).
 
 Per frequency (Eq. ImpedanceOp, with the e^{jwt} convention and the principal
 root): Z_s = sqrt(j w mu0 / sigma) = (1 + j) sqrt(w mu0 / (2 sigma)).
+Thickness-aware variant (the low-frequency remedy Sec. II-A names; reading in
+the design notes): a conductor given an effective thickness t (twice its
+cross-section area over its perimeter) uses the impedance of one face of a slab
+of thickness t, Z_s = (gamma / sigma) coth(gamma t / 2) with
+gamma = (1 + j) sqrt(w mu0 sigma / 2) = (1 + j) / delta.  It tends to the value
+above when delta << t and to the DC sheet value 2 / (sigma t) as w -> 0, where
+a uniform perimeter current gives the bar's DC resistance rho L / (w t).
 Parity: pinned by closed forms (uniform-perimeter skin resistance of a long
 polygonal wire, R proportional to sqrt(f), Neumann inductance of a long tube)
 and invariants (Z = Z^T, R > 0, L > 0, tree independence) in
@@ -22,14 +29,28 @@ from .graph import build_loops
 from .integrals import (MU0, gram_matrix, symmetric_blocks, tri_branches, dense_rules)
 
 
-def surface_impedance(omega, sigma):
-    return (1.0 + 1.0j) * np.sqrt(omega * MU0 / (2.0 * sigma))
+def surface_impedance(omega, sigma, t_eff=0.0):
+    """Z_s of a conductor; t_eff > 0 selects the slab form (module docstring)."""
+    sigma = np.asarray(sigma, dtype=float)
+    t_eff = np.broadcast_to(np.asarray(t_eff, dtype=float), sigma.shape)
+    classic = (1.0 + 1.0j) * np.sqrt(omega * MU0 / (2.0 * sigma))
+    gamma = (1.0 + 1.0j) * np.sqrt(omega * MU0 * sigma / 2.0)
+    z = gamma * t_eff / 2.0
+    # z coth z: its Taylor series where |z| is small, 1 / tanh otherwise
+    small = np.abs(z) < 1e-2
+    zs_ = np.where(small, 1.0, z)
+    zcoth = np.where(small, 1.0 + z ** 2 / 3.0 - z ** 4 / 45.0, zs_ / np.tanh(zs_))
+    slab = 2.0 / (sigma * np.where(t_eff > 0, t_eff, 1.0)) * zcoth
+    out = np.where(t_eff > 0, slab, classic)
+    return out[()] if out.ndim == 0 else out
 
 
-def branch_zs(mesh, loops, omega):
-    """Z_s of each branch's conductor (both triangles of a branch share it)."""
+def branch_zs(mesh, loops, omega, t_eff=None):
+    """Z_s of each branch's conductor (both triangles of a branch share it);
+    t_eff: effective thickness per conductor (None or 0: the classic form)."""
     cond = mesh.cond[loops.br_tri[:, 0]]
-    return surface_impedance(omega, mesh.sigma[cond])
+    t = np.zeros(mesh.ncond) if t_eff is None else np.asarray(t_eff, dtype=float)
+    return surface_impedance(omega, mesh.sigma[cond], t[cond])
 
 
 def assemble_from_blocks(mesh, loops, pi, pj, blocks):
@@ -63,14 +84,15 @@ def dense_Lt(mesh, loops, rules=None, far_ratio=4.0):
 class DenseMoM:
     """Dense loop system of one mesh; Z(f) by direct solves."""
 
-    def __init__(self, mesh, loops=None, Lt=None):
+    def __init__(self, mesh, loops=None, Lt=None, t_eff=None):
         self.mesh = mesh
         self.loops = build_loops(mesh) if loops is None else loops
         self.G = gram_matrix(mesh, self.loops).toarray()
         self.Lt = dense_Lt(mesh, self.loops) if Lt is None else Lt
+        self.t_eff = t_eff
 
     def Zb(self, omega):
-        zs = branch_zs(self.mesh, self.loops, omega)
+        zs = branch_zs(self.mesh, self.loops, omega, self.t_eff)
         return zs[:, None] * self.G + (1j * omega * MU0 / (4.0 * np.pi)) * self.Lt
 
     def Zl(self, omega):
@@ -98,6 +120,12 @@ class DenseMoM:
             Y = np.array([[I[self.loops.port_loop(q), p] for p in range(P)] for q in range(P)])
             out[fi] = np.linalg.inv(Y)
         return out
+
+
+def bar_effective_thickness(width, thickness):
+    """2 A / P of a width x thickness rectangle: the slab thickness whose DC
+    sheet impedance makes a uniform perimeter current carry the bar's DC resistance."""
+    return width * thickness / (width + thickness)
 
 
 def resistance_inductance(Z, freqs):

@@ -260,15 +260,16 @@ class Pfft:
 class PfftSystem:
     """Loop-space product y = A (Z_s G + j w mu0/4pi (L_d + I H B)) A^T x."""
 
-    def __init__(self, mesh, loops, params: PfftParams):
+    def __init__(self, mesh, loops, params: PfftParams, t_eff=None):
         self.mesh, self.loops = mesh, loops
+        self.t_eff = t_eff   # effective thickness per conductor: slab surface impedance (mom.py)
         self.op = Pfft(mesh, loops, params)
         self.G = gram_matrix(mesh, loops)
         nb = loops.nb
         self.A = loops.A[:, :nb].tocsr()
 
     def branch_product(self, alpha, omega):
-        zs = branch_zs(self.mesh, self.loops, omega)
+        zs = branch_zs(self.mesh, self.loops, omega, self.t_eff)
         return zs * (self.G @ alpha) + (1j * omega * MU0 / (4.0 * np.pi)) * self.op.Lt_apply(alpha)
 
     def matvec(self, x, omega):
@@ -277,6 +278,6 @@ class PfftSystem:
     def diag_Zb(self, omega):
         """diag(Z_b): Gram and inductive self terms (the near blocks hold the
         direct self integrals)."""
-        zs = branch_zs(self.mesh, self.loops, omega)
+        zs = branch_zs(self.mesh, self.loops, omega, self.t_eff)
         Ld = self.op.near_matrix(self.op.L_direct)
         return zs * self.G.diagonal() + (1j * omega * MU0 / (4.0 * np.pi)) * Ld.diagonal()
