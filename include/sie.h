@@ -144,6 +144,23 @@ int pfft_plan_create(const sie_mesh *m, const sie_loops *l, const pfft_params *p
                      pfft_plan **out);
 void pfft_plan_destroy(pfft_plan *p);
 
+/* Surface model of each conductor.  The paper's surface impedance (Eq.
+ * ImpedanceOp) Z_s = (1 + j) / (sigma delta) assumes delta well below the
+ * conductor's thickness; Sec. II-A names a thickness-aware model as the remedy
+ * at low frequency.  With t_eff[c] > 0 conductor c uses the impedance of one
+ * face of a slab of thickness t_eff[c]:
+ *   Z_s = (gamma / sigma) coth(gamma t / 2),  gamma = (1 + j) / delta,
+ * which equals the classic value to within 2 exp(-t / delta) when delta << t
+ * and tends to the DC sheet value 2 / (sigma t) as omega -> 0.  For a bar of
+ * cross-section w x t, t_eff = 2 w t / (2 (w + t)) (twice the area over the
+ * perimeter) makes a uniform perimeter current carry the volume DC resistance
+ * rho L / (w t); omega = 0 then has a solution (the classic model's loop system
+ * is singular there).  t_eff = NULL or t_eff[c] = 0 selects the classic form.
+ * Applies to every later pfft_matvec, pfft_precond_apply and sie_solve call of
+ * the plan (cached preconditioner factors are rebuilt).  ncond must equal the
+ * mesh's conductor count; thicknesses must be finite and >= 0 (SIE_ERR_ARG). */
+int pfft_plan_set_surface_model(pfft_plan *p, const double *t_eff, int32_t ncond);
+
 /* The product of Eq. (FinalME) for nrhs right-hand sides at once (Sec. IV-A/B):
  *   space = SIE_SPACE_LOOP:   y = A [Z_s G + c_L (L_d + I H B)] A^T x,
  *                              x, y device complex128 [nrhs][n_loops];
@@ -167,7 +184,9 @@ int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double
  * conductor on first use of each distinct omega set.  prec = SIE_PREC_FP64
  * runs every step in FP64; SIE_PREC_MIXED runs the drive, the triangular sweeps
  * on the rounded factor and the branch currents in FP32 (band width <= 31;
- * wider bands fall back to FP64).  Errors: SIE_ERR_BREAKDOWN for a zero pivot. */
+ * wider bands fall back to FP64).  omega[r] > 0, or 0 when every conductor has
+ * a slab surface model (SIE_ERR_ARG otherwise).  Errors: SIE_ERR_BREAKDOWN for
+ * a zero pivot. */
 int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
                        int32_t prec, void *cuda_stream);
 
@@ -176,7 +195,9 @@ int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const
  * Y[f][p][q] = loop current of port p, Z(f) = Y(f)^-1.  ports[np] selects the
  * plan's ports (indices into the ports given to loop_basis_build).
  * Z_out: caller-owned host [nf][np][np].  On SIE_ERR_NOT_CONVERGED Z_out and
- * st are still filled.  `st` may be NULL. */
+ * st are still filled.  `st` may be NULL.  freqs[f] > 0, or f = 0 (DC: Z real)
+ * when every conductor has a slab surface model (pfft_plan_set_surface_model);
+ * SIE_ERR_ARG otherwise. */
 int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
               const sie_solve_opts *opts, sie_c64 *Z_out, sie_solve_stats *st);
 

@@ -35,6 +35,7 @@ class Mesh:
                                   sigma.shape[0], ctypes.byref(h)))
         self.h = h
         self.nt = tri.shape[0]
+        self.ncond = sigma.shape[0]
 
     @classmethod
     def from_synth(cls, m):
@@ -116,6 +117,16 @@ class Plan:
         self.h = h
         self.mesh, self.loops = mesh, loops      # the plan borrows the loop basis
         self.nl, self.nb, self.np = loops.nl, loops.nb, loops.np
+
+    def set_surface_model(self, t_eff=None):
+        """Slab surface impedance with effective thickness t_eff[c] per conductor
+        (None or 0: the classic form); see pfft_plan_set_surface_model."""
+        nc = self.mesh.ncond
+        if t_eff is None:
+            check(lib().pfft_plan_set_surface_model(self.h, None, nc))
+            return
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(t_eff, dtype=np.float64), (nc,)))
+        check(lib().pfft_plan_set_surface_model(self.h, t.ctypes.data_as(ctypes.c_void_p), nc))
 
     def info(self):
         v = [ctypes.c_int64() for _ in range(4)]

@@ -23,6 +23,7 @@
 // 128 right-hand sides with coalesced loads.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <memory>
 #include <type_traits>
 #include <vector>
@@ -684,6 +685,24 @@ float2 *coef_dd(const pfft_plan *p) {
     return reinterpret_cast<float2 *>(p->scr.coef + size_t(p->scr.cap_rhs) * (2 * p->ncond + 1));
 }
 
+std::complex<double> surface_impedance(const pfft_plan *p, int c, double w) {
+    using cd = std::complex<double>;
+    const double sig = p->sigma[c], t = p->t_eff.empty() ? 0.0 : p->t_eff[c];
+    if (!(t > 0.0)) return cd(1.0, 1.0) * std::sqrt(w * kMu0 / (2.0 * sig));
+    const cd gamma = cd(1.0, 1.0) * std::sqrt(w * kMu0 * sig / 2.0);
+    const cd z = gamma * (t / 2.0);
+    // z coth z: Taylor series for small |z|, else coth from exp(-2z) (Re z >= 0)
+    cd zc;
+    if (std::abs(z) < 1e-2) {
+        const cd z2 = z * z;
+        zc = 1.0 + z2 / 3.0 - z2 * z2 / 45.0;
+    } else {
+        const cd e = std::exp(-2.0 * z);
+        zc = z * (1.0 + e) / (1.0 - e);
+    }
+    return 2.0 / (sig * t) * zc;
+}
+
 // Per right-hand side: Z_s of each conductor and c_L / j (Eq. ImpedanceOp, Eq. Zb),
 // in FP64 and as double-float pairs.
 int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
@@ -694,9 +713,9 @@ int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
         const double w = omega[r];
         if (!(w >= 0.0) || !std::isfinite(w)) return fail(SIE_ERR_ARG, "pfft_matvec: omega must be finite and >= 0");
         for (int c = 0; c < p->ncond; ++c) {
-            double zs = std::sqrt(w * kMu0 / (2.0 * p->sigma[c]));
-            cf[r * (2 * p->ncond + 1) + 2 * c] = zs;
-            cf[r * (2 * p->ncond + 1) + 2 * c + 1] = zs;
+            const std::complex<double> zs = surface_impedance(p, c, w);
+            cf[r * (2 * p->ncond + 1) + 2 * c] = zs.real();
+            cf[r * (2 * p->ncond + 1) + 2 * c + 1] = zs.imag();
         }
         cf[r * (2 * p->ncond + 1) + 2 * p->ncond] = w * kMu0 / (4.0 * M_PI);
     }

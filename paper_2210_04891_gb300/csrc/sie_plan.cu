@@ -552,6 +552,7 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     p->nt = m->nt; p->nb = L->nb; p->nl = L->nl; p->np = L->np; p->nn = L->n_nodes;
     p->ncond = m->ncond;
     p->sigma = m->sigma;
+    p->t_eff.assign(p->sigma.size(), 0.0);
     p->O = O;
     p->Q = 7;
     p->Nx = prm->grid[0]; p->Ny = prm->grid[1]; p->Nz = prm->grid[2];

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <complex>
 #include <vector>
 
 #include "sie_common.cuh"
@@ -52,6 +53,7 @@ struct pfft_plan {
     pfft_params params{};
     const sie_loops *loops = nullptr;   // borrowed: must outlive the plan
     std::vector<double> sigma;          // per conductor
+    std::vector<double> t_eff;          // per conductor: slab surface impedance thickness (0: classic)
     // per triangle (device)
     int32_t *d_tb = nullptr;            // [nt][3] branch of local edge k (-1: none)
     int8_t *d_ts = nullptr;             // [nt][3] +1 on T+, -1 on T-
@@ -157,6 +159,11 @@ int plan_alloc(pfft_plan *p, void **ptr, size_t bytes);
 void plan_free(pfft_plan *p, void *ptr);
 void plan_free_precond(pfft_plan *p);
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
+// Surface impedance of conductor c at angular frequency w (Eq. ImpedanceOp):
+// classic (1 + j) sqrt(w mu0 / (2 sigma)), or with an effective thickness
+// t > 0 the impedance of one face of a slab of thickness t,
+// (gamma / sigma) coth(gamma t / 2) with gamma = (1 + j) sqrt(w mu0 sigma / 2).
+std::complex<double> surface_impedance(const pfft_plan *p, int c, double w);
 float2 *coef_dd(const pfft_plan *p);   // double-float copy of scr.coef
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);

@@ -73,6 +73,14 @@ struct PrecondState {
     std::vector<void *> allocs;
 };
 
+// DC (omega = 0) has a solution only when every conductor has a slab surface
+// model: the classic Z_s and c_L both vanish there.
+bool dc_defined(const pfft_plan *p) {
+    for (double t : p->t_eff)
+        if (!(t > 0.0)) return false;
+    return !p->t_eff.empty();
+}
+
 void plan_free_precond(pfft_plan *p) {
     if (!p || !p->pc) return;
     for (void *a : p->pc->allocs) cudaFree(a);
@@ -307,9 +315,9 @@ __global__ void k_pc_admittance(const double *__restrict__ diag_gram, const doub
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nb * nslots) return;
     int64_t f = i / nb, e = i % nb;
-    const double *cf = zs_cl + f * (ncond + 1);
-    double zs = cf[br_cond[e]], cl = cf[ncond];
-    double dr = zs * diag_gram[e], di = zs * diag_gram[e] + cl * diag_L[e];
+    const double *cf = zs_cl + f * (2 * ncond + 1);   // (Re Z_s, Im Z_s) per conductor, then c_L / j
+    const double zr = cf[2 * br_cond[e]], zi = cf[2 * br_cond[e] + 1], cl = cf[2 * ncond];
+    double dr = zr * diag_gram[e], di = zi * diag_gram[e] + cl * diag_L[e];
     double den = dr * dr + di * di;
     a[i] = make_double2(dr / den, -di / den);
 }
@@ -732,7 +740,9 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     std::sort(uniq.begin(), uniq.end());
     uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
     for (double w : uniq)
-        if (!(w > 0.0) || !std::isfinite(w)) return fail(SIE_ERR_ARG, "preconditioner: omega must be positive");
+        if (!(w > 0.0 || (w == 0.0 && dc_defined(p))) || !std::isfinite(w))
+            return fail(SIE_ERR_ARG, "preconditioner: omega must be positive (or 0 with a slab surface model on "
+                                     "every conductor)");
     slot.resize(R);
     for (int32_t r = 0; r < R; ++r) slot[r] = int32_t(std::lower_bound(uniq.begin(), uniq.end(), omega[r]) - uniq.begin());
     if (R > s->cap_rhs) {
@@ -776,10 +786,15 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     }
     SIE_CUDA(cudaMalloc((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_a32, size_t(ns) * p->nb * sizeof(float2)));
-    std::vector<double> zc(size_t(ns) * (p->ncond + 1));
+    const int zw = 2 * p->ncond + 1;
+    std::vector<double> zc(size_t(ns) * zw);
     for (int32_t f = 0; f < ns; ++f) {
-        for (int c = 0; c < p->ncond; ++c) zc[f * (p->ncond + 1) + c] = std::sqrt(uniq[f] * kMu0 / (2.0 * p->sigma[c]));
-        zc[f * (p->ncond + 1) + p->ncond] = uniq[f] * kMu0 / (4.0 * M_PI);
+        for (int c = 0; c < p->ncond; ++c) {
+            const std::complex<double> z = surface_impedance(p, c, uniq[f]);
+            zc[f * zw + 2 * c] = z.real();
+            zc[f * zw + 2 * c + 1] = z.imag();
+        }
+        zc[f * zw + 2 * p->ncond] = uniq[f] * kMu0 / (4.0 * M_PI);
     }
     double *d_zc = nullptr;
     SIE_CUDA(cudaMalloc((void **)&d_zc, zc.size() * sizeof(double)));
@@ -968,8 +983,9 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     for (int32_t i = 0; i < np; ++i)
         if (ports[i] < 0 || ports[i] >= p->np) return fail(SIE_ERR_ARG, "sie_solve: port index out of range");
     for (int32_t i = 0; i < nf; ++i)
-        if (!(freqs[i] > 0.0) || !std::isfinite(freqs[i]))
-            return fail(SIE_ERR_ARG, "sie_solve: frequencies must be positive (the surface impedance model has no DC limit)");
+        if (!(freqs[i] > 0.0 || (freqs[i] == 0.0 && dc_defined(p))) || !std::isfinite(freqs[i]))
+            return fail(SIE_ERR_ARG, "sie_solve: frequencies must be positive (DC needs the slab surface model on "
+                                     "every conductor: the classic surface impedance vanishes there)");
     const int m = std::max(1, std::min(opts->restart, 1000));
     if (!(opts->tol > 0.0) || opts->max_iter < 1) return fail(SIE_ERR_ARG, "sie_solve: bad tolerance or iteration cap");
     if (opts->prec != SIE_PREC_FP64 && opts->prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "sie_solve: bad precision");
@@ -1227,5 +1243,24 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     if (int dev_rc = check_device_errors(p)) return dev_rc;
     if (breakdown) return fail(SIE_ERR_BREAKDOWN, "sie_solve: non-finite value in the Arnoldi recurrence");
     if (nnc) return fail(SIE_ERR_NOT_CONVERGED, "sie_solve: " + std::to_string(nnc) + " right-hand sides did not converge");
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ surface model
+
+extern "C" int pfft_plan_set_surface_model(pfft_plan *p, const double *t_eff, int32_t ncond) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_plan_set_surface_model: NULL plan");
+    if (ncond != p->ncond)
+        return fail(SIE_ERR_ARG, "pfft_plan_set_surface_model: ncond must equal the mesh's conductor count (" +
+                                     std::to_string(p->ncond) + ")");
+    std::vector<double> t(size_t(ncond), 0.0);
+    if (t_eff)
+        for (int32_t c = 0; c < ncond; ++c) {
+            if (!(t_eff[c] >= 0.0) || !std::isfinite(t_eff[c]))
+                return fail(SIE_ERR_ARG, "pfft_plan_set_surface_model: thickness must be finite and >= 0");
+            t[c] = t_eff[c];
+        }
+    p->t_eff = t;
+    if (p->pc) p->pc->slot_omega.clear();   // the cached factors were built with the previous Z_s
     return SIE_OK;
 }
