@@ -201,6 +201,28 @@ int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const
 int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
               const sie_solve_opts *opts, sie_c64 *Z_out, sie_solve_stats *st);
 
+/* Post-processing of loop currents x (device complex128 [nrhs][n_loops], e.g. a
+ * solution of Eq. (LoopWithP)) into the quantities the paper plots (Sec. V):
+ *   i_branch = A^T x                 branch currents (Eq. CurT), [nrhs][n_branches];
+ *   v_branch = Z_b i_branch          voltage drops tail -> head (Eq. VolT, the
+ *                                    SIE_SPACE_BRANCH product at omega[r]),
+ *                                    [nrhs][n_branches];
+ *   phi      = node potential of each panel, [nrhs][n_tri]: the sum of the
+ *              tree-branch drops from the panel's node to its conductor's
+ *              reference node (0 V), so v_branch = phi(tail) - phi(head) on
+ *              every tree branch.  The reference node of a conductor is the
+ *              sink contact of the first port on it, else its tree root;
+ *              contact panels share their contact's potential.
+ * All three outputs are caller-owned device complex128 buffers; any may be NULL
+ * (not computed; temporaries are used where a later output needs it).  omega
+ * (host, [nrhs]) is needed for v_branch or phi, may be NULL otherwise.  The
+ * currents are exact FP64 sums; prec selects the product's arithmetic
+ * (as in pfft_matvec); the potential sums are FP64.  Synchronises cuda_stream
+ * before returning.  Errors: SIE_ERR_ARG (NULL x, nrhs < 1 or > 65535, bad
+ * prec or omega), SIE_ERR_OOM, SIE_ERR_CUDA. */
+int sie_postprocess(pfft_plan *p, const void *x, int32_t nrhs, const double *omega, int32_t prec,
+                    void *i_branch, void *v_branch, void *phi, void *cuda_stream);
+
 /* Plan introspection for tests and benchmarks: sizes (any pointer may be NULL). */
 int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, int64_t *n_tri,
                    int64_t *n_near_pairs, double *grid_h /* [3] */, double *r_near,

@@ -200,6 +200,31 @@ def pfft_matvec(plan: Plan, x, omega, space=N.SPACE_LOOP, prec=N.PREC_FP64, out=
     return y
 
 
+def postprocess(plan: Plan, x, omega=None, prec=N.PREC_FP64, currents=True, voltages=True, potentials=True,
+                stream=None):
+    """Branch currents A^T x, branch voltage drops Z_b A^T x and panel potentials
+    (conductor reference nodes at 0) of loop currents x [nrhs, n_loops]; returns
+    the three (None where not asked for)."""
+    import torch
+    _check_vec(x, plan.nl, "x")
+    R = x.shape[0]
+    om = None
+    if voltages or potentials:
+        if omega is None:
+            raise ValueError("omega is needed for voltages and potentials")
+        om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, np.float64), (R,)))
+    dev = dict(dtype=torch.complex128, device=x.device)
+    a = torch.empty((R, plan.nb), **dev) if currents else None
+    v = torch.empty((R, plan.nb), **dev) if voltages else None
+    phi = torch.empty((R, plan.mesh.nt), **dev) if potentials else None
+
+    def vp(t):
+        return ctypes.c_void_p(t.data_ptr() if t is not None else None)
+    check(lib().sie_postprocess(plan.h, ctypes.c_void_p(x.data_ptr()), R, _ptr(om) if om is not None else None,
+                                prec, vp(a), vp(v), vp(phi), _stream(stream)))
+    return a, v, phi
+
+
 def pfft_convolve(plan: Plan, grid, prec=N.PREC_FP64, stream=None):
     """phi_g = H Q_g in place for grid [nbatch, N_x, N_y, N_z] (complex128 or complex64)."""
     import torch

@@ -512,6 +512,30 @@ __global__ void k_loop_out(const E *__restrict__ y_br, int64_t ldy, const E *__r
     y[i] = o;
 }
 
+// Post-processing (Eq. CurT): current of every mesh branch, grid (branches, right-hand sides).
+__global__ void k_branch_alpha(const double2 *__restrict__ x, int64_t nl, const double2 *__restrict__ P,
+                               int64_t nslots, const int32_t *__restrict__ loop_of_branch,
+                               const int32_t *__restrict__ twig_node, const int32_t *__restrict__ head,
+                               const int32_t *__restrict__ enter, const int32_t *__restrict__ exit_, int64_t nb,
+                               double2 *__restrict__ alpha) {
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int64_t r = blockIdx.y;
+    alpha[r * nb + b] = branch_current<double>(int32_t(b), r, x, nl, P, nslots, loop_of_branch, twig_node, head,
+                                               enter, exit_);
+}
+
+// Post-processing: panel potential = root-path sum of the panel's node minus that
+// of its conductor's reference node, grid (panels, right-hand sides).
+__global__ void k_panel_phi(const double2 *__restrict__ P, int64_t nslots, const int32_t *__restrict__ slot,
+                            const int32_t *__restrict__ ref, int64_t nt, double2 *__restrict__ phi) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int64_t r = blockIdx.y;
+    const double2 *row = P + r * nslots;
+    phi[r * nt + t] = csub(row[slot[t]], row[ref[t]]);
+}
+
 inline unsigned nblk(int64_t n, int t = 256) { return unsigned((n + t - 1) / t); }
 
 }  // namespace
@@ -757,4 +781,65 @@ extern "C" int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, c
     if (rc) return rc;
     SIE_CUDA(cudaStreamSynchronize(st));
     return sie::check_device_errors(p);
+}
+
+extern "C" int sie_postprocess(pfft_plan *p, const void *x, int32_t nrhs, const double *omega, int32_t prec,
+                               void *i_branch, void *v_branch, void *phi, void *cuda_stream) {
+    using namespace sie;
+    if (!p || !x || nrhs < 1) return fail(SIE_ERR_ARG, "sie_postprocess: bad argument");
+    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "sie_postprocess: bad precision");
+    if ((v_branch || phi) && !omega) return fail(SIE_ERR_ARG, "sie_postprocess: omega is needed for voltages");
+    if (!i_branch && !v_branch && !phi) return SIE_OK;
+    if (nrhs > 65535) return fail(SIE_ERR_ARG, "sie_postprocess: at most 65535 right-hand sides per call");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    (void)cudaGetLastError();
+    const int64_t nb = p->nb, nt = p->nt, nslots = 2 * p->nn, R = nrhs;
+    int rc = scratch_reserve(p, nrhs, prec);   // the size the product below uses: no later regrowth
+    if (rc) return rc;
+    // temporaries for outputs the caller did not ask for but later steps need
+    double2 *alpha = static_cast<double2 *>(i_branch), *vb = static_cast<double2 *>(v_branch);
+    double2 *tmp_a = nullptr, *tmp_v = nullptr;
+    auto cleanup = [&]() {
+        if (tmp_a) cudaFree(tmp_a);
+        if (tmp_v) cudaFree(tmp_v);
+    };
+    if (!alpha) {
+        if (cudaMalloc((void **)&tmp_a, size_t(R) * nb * sizeof(double2)) != cudaSuccess)
+            return fail(SIE_ERR_OOM, "sie_postprocess: out of device memory");
+        alpha = tmp_a;
+    }
+    if (phi && !vb) {
+        if (cudaMalloc((void **)&tmp_v, size_t(R) * nb * sizeof(double2)) != cudaSuccess) {
+            cleanup();
+            return fail(SIE_ERR_OOM, "sie_postprocess: out of device memory");
+        }
+        vb = tmp_v;
+    }
+    double2 *tour = static_cast<double2 *>(p->scr.tour);
+    const dim3 gs(nblk(nslots), unsigned(R)), gb(nblk(nb), unsigned(R)), gt(nblk(nt), unsigned(R));
+    // branch currents: alpha = A^T x through the tour prefix sums (FP64)
+    k_tour_inject<double2><<<gs, 256, 0, st>>>(static_cast<const double2 *>(x), p->nl, tour, nslots, p->d_tour_node,
+                                               p->d_tour_enter, p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign);
+    k_scan_rows<double2><<<unsigned(R), 1024, 0, st>>>(tour, nslots);
+    k_branch_alpha<<<gb, 256, 0, st>>>(static_cast<const double2 *>(x), p->nl, tour, nslots, p->d_loop_of_branch,
+                                       p->d_twig_node, p->d_head, p->d_enter, p->d_exit, nb, alpha);
+    p->launches += 3;
+    if (cudaGetLastError() != cudaSuccess) { cleanup(); return fail(SIE_ERR_CUDA, "sie_postprocess: launch failed"); }
+    if (vb) {   // branch voltage drops: the branch-space product Z_b alpha
+        rc = matvec_async(p, alpha, vb, nrhs, omega, SIE_SPACE_BRANCH, prec, st);
+        if (rc) { cleanup(); return rc; }
+    }
+    if (phi) {   // potentials: root-path sums of the twig drops, minus the reference node's
+        k_tour_voltage<double2><<<gs, 256, 0, st>>>(vb, nb, tour, nslots, p->d_tour_node, p->d_tour_enter,
+                                                     p->d_parent_branch, p->d_tail);
+        k_scan_rows<double2><<<unsigned(R), 1024, 0, st>>>(tour, nslots);
+        k_panel_phi<<<gt, 256, 0, st>>>(tour, nslots, p->d_panel_slot, p->d_panel_ref, nt,
+                                        static_cast<double2 *>(phi));
+        p->launches += 3;
+        if (cudaGetLastError() != cudaSuccess) { cleanup(); return fail(SIE_ERR_CUDA, "sie_postprocess: launch failed"); }
+    }
+    const cudaError_t e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return fail(SIE_ERR_CUDA, std::string("sie_postprocess: ") + cudaGetErrorString(e));
+    return check_device_errors(p);
 }

@@ -829,6 +829,22 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         UP(p->d_nl_sign, nls);
         std::vector<int32_t> pb(L->parent_branch.begin(), L->parent_branch.end());
         UP(p->d_parent_branch, pb);
+        // reference node of each part: the sink contact of its first port, else its tree root
+        std::vector<int64_t> ref(L->n_comp, -1);
+        for (size_t q = 0; q < L->port_sink.size(); ++q) {
+            const int32_t v = L->port_sink[q];
+            if (ref[L->comp[v]] < 0) ref[L->comp[v]] = v;
+        }
+        for (int64_t v = 0; v < L->n_nodes; ++v)
+            if (L->parent[v] < 0 && ref[L->comp[v]] < 0) ref[L->comp[v]] = v;
+        std::vector<int32_t> ps(nt), pr(nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            const int64_t v = L->node_of_tri[t];
+            ps[t] = L->enter[v];
+            pr[t] = L->enter[ref[L->comp[v]]];
+        }
+        UP(p->d_panel_slot, ps);
+        UP(p->d_panel_ref, pr);
         UP(p->d_twig_node, twig_node);
         std::vector<int32_t> lob(L->loop_of_branch.begin(), L->loop_of_branch.end());
         UP(p->d_loop_of_branch, lob);

@@ -113,6 +113,8 @@ struct pfft_plan {
     int8_t *d_nl_sign = nullptr;
     int32_t *d_parent_branch = nullptr;  // [nn]
     int32_t *d_twig_node = nullptr;      // [nb]: node whose parent branch it is, -1 for links
+    // post-processing: tour slot of each panel's node and of its conductor's reference node
+    int32_t *d_panel_slot = nullptr, *d_panel_ref = nullptr;   // [nt]
     int32_t *d_loop_of_branch = nullptr; // [nb + np]
     int32_t *d_tail = nullptr, *d_head = nullptr;  // [nb + np]
     int32_t *d_link_branch = nullptr;    // [nl]
