@@ -115,6 +115,18 @@ typedef struct {
  * triangles or non-positive conductivity. */
 int sie_mesh_load(const double *xyz, int64_t nv, const int32_t *tri, int64_t nt,
                   const int32_t *cond_id, const double *sigma, int32_t ncond, sie_mesh **out);
+/* The same mesh from a text file of this library's own format, version 1:
+ *   sie_mesh 1
+ *   <nv> <nt> <ncond>
+ *   <sigma_0> ... <sigma_{ncond-1}>          (S/m)
+ *   <x> <y> <z>                     nv lines (m)
+ *   <v0> <v1> <v2> <cond_id>        nt lines (0-based vertex ids)
+ * Tokens are separated by any whitespace; '#' starts a comment that runs to
+ * the end of the line.  Numbers are read independently of the C locale; write
+ * coordinates with 17 significant digits for an exact round trip.  Errors:
+ * SIE_ERR_ARG (unreadable file, bad header, missing or malformed number,
+ * trailing data, and every check of sie_mesh_load). */
+int sie_mesh_load_file(const char *path, sie_mesh **out);
 void sie_mesh_destroy(sie_mesh *m);
 
 /* Circuit graph and fundamental loops (Sec. II-D, III): nodes = triangles

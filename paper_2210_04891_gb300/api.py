@@ -8,6 +8,7 @@ buffers are torch tensors (complex128, CUDA); streams are torch streams.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -41,6 +42,19 @@ class Mesh:
     def from_synth(cls, m):
         return cls(m.xyz, m.tri, m.cond, m.sigma)
 
+    @classmethod
+    def from_file(cls, path, nt=None, ncond=None):
+        """Load a mesh file (sie_mesh_load_file); nt and ncond are read from its
+        size line when not given."""
+        self = cls.__new__(cls)
+        self._keep = []
+        if nt is None or ncond is None:
+            nt, ncond = _mesh_file_sizes(path)
+        h = ctypes.c_void_p()
+        check(lib().sie_mesh_load_file(os.fsencode(path), ctypes.byref(h)))
+        self.h, self.nt, self.ncond = h, nt, ncond
+        return self
+
     def __del__(self):
         if getattr(self, "h", None) and lib is not None:
             lib().sie_mesh_destroy(self.h)
@@ -49,6 +63,35 @@ class Mesh:
 
 def sie_mesh_load(xyz, tri, cond, sigma):
     return Mesh(xyz, tri, cond, sigma)
+
+
+def sie_mesh_load_file(path):
+    return Mesh.from_file(path)
+
+
+def write_mesh_file(path, xyz, tri, cond, sigma):
+    """Write the text format sie_mesh_load_file reads (17 significant digits)."""
+    xyz = np.asarray(xyz, np.float64).reshape(-1, 3)
+    tri = np.asarray(tri, np.int64).reshape(-1, 3)
+    cond = np.asarray(cond, np.int64).reshape(-1)
+    sigma = np.asarray(sigma, np.float64).reshape(-1)
+    with open(path, "w") as f:
+        f.write("sie_mesh 1\n# nv nt ncond\n%d %d %d\n" % (xyz.shape[0], tri.shape[0], sigma.shape[0]))
+        f.write(" ".join("%.17g" % s for s in sigma) + "\n")
+        for x in xyz:
+            f.write("%.17g %.17g %.17g\n" % tuple(x))
+        for t, c in zip(tri, cond):
+            f.write("%d %d %d %d\n" % (t[0], t[1], t[2], c))
+
+
+def _mesh_file_sizes(path):
+    with open(path) as f:
+        toks = []
+        for line in f:
+            toks += line.split("#", 1)[0].split()
+            if len(toks) >= 5:
+                return int(toks[3]), int(toks[4])
+    raise ValueError("%s: no size line" % path)
 
 
 class Loops:

@@ -12,9 +12,12 @@
 // the device as prefix sums along the tour (subtree sums and root-path sums),
 // O(nodes) work instead of O(sum of loop lengths).
 #include <algorithm>
+#include <charconv>
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <fstream>
+#include <sstream>
 #include <numeric>
 #include <string>
 #include <tuple>
@@ -74,6 +77,78 @@ extern "C" int sie_mesh_load(const double *xyz, int64_t nv, const int32_t *tri, 
 }
 
 extern "C" void sie_mesh_destroy(sie_mesh *m) { delete m; }
+
+namespace {
+
+// Whitespace-separated tokens of a mesh file, '#' comments skipped; numbers are
+// parsed with std::from_chars (independent of the C locale).
+struct MeshTokens {
+    std::string text;
+    size_t pos = 0;
+    bool next(std::string_view &tok) {
+        for (;;) {
+            while (pos < text.size() && std::isspace(static_cast<unsigned char>(text[pos]))) ++pos;
+            if (pos < text.size() && text[pos] == '#') {
+                while (pos < text.size() && text[pos] != '\n') ++pos;
+                continue;
+            }
+            break;
+        }
+        if (pos >= text.size()) return false;
+        const size_t b = pos;
+        while (pos < text.size() && !std::isspace(static_cast<unsigned char>(text[pos])) && text[pos] != '#') ++pos;
+        tok = std::string_view(text).substr(b, pos - b);
+        return true;
+    }
+    template <typename T> bool number(T &v) {
+        std::string_view t;
+        if (!next(t)) return false;
+        const char *e = t.data() + t.size();
+        auto r = std::from_chars(t.data(), e, v);
+        return r.ec == std::errc() && r.ptr == e;
+    }
+};
+
+}  // namespace
+
+extern "C" int sie_mesh_load_file(const char *path, sie_mesh **out) {
+    if (!out) return sie::fail(SIE_ERR_ARG, "sie_mesh_load_file: out is NULL");
+    *out = nullptr;
+    if (!path) return sie::fail(SIE_ERR_ARG, "sie_mesh_load_file: path is NULL");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return sie::fail(SIE_ERR_ARG, std::string("sie_mesh_load_file: cannot open ") + path);
+    MeshTokens tk;
+    {
+        std::ostringstream ss;
+        ss << f.rdbuf();
+        tk.text = ss.str();
+    }
+    auto bad = [&](const std::string &what) {
+        return sie::fail(SIE_ERR_ARG, std::string("sie_mesh_load_file: ") + path + ": " + what);
+    };
+    std::string_view magic;
+    int version = 0;
+    if (!tk.next(magic) || magic != "sie_mesh" || !tk.number(version)) return bad("not a sie_mesh file");
+    if (version != 1) return bad("unsupported version " + std::to_string(version));
+    int64_t nv = 0, nt = 0, nc = 0;
+    if (!tk.number(nv) || !tk.number(nt) || !tk.number(nc)) return bad("bad size line");
+    if (nv < 3 || nt < 1 || nc < 1 || nv > (int64_t(1) << 30) || nt > (int64_t(1) << 30) || nc > (1 << 20))
+        return bad("sizes out of range");
+    std::vector<double> sigma(nc), xyz(3 * nv);
+    std::vector<int32_t> tri(3 * nt), cond(nt);
+    for (auto &s : sigma)
+        if (!tk.number(s)) return bad("bad conductivity");
+    for (auto &x : xyz)
+        if (!tk.number(x)) return bad("bad or missing vertex coordinate");
+    for (int64_t t = 0; t < nt; ++t) {
+        if (!tk.number(tri[3 * t]) || !tk.number(tri[3 * t + 1]) || !tk.number(tri[3 * t + 2]) ||
+            !tk.number(cond[t]))
+            return bad("bad or missing triangle " + std::to_string(t));
+    }
+    std::string_view extra;
+    if (tk.next(extra)) return bad("trailing data after the last triangle");
+    return sie_mesh_load(xyz.data(), nv, tri.data(), nt, cond.data(), sigma.data(), int32_t(nc), out);
+}
 
 namespace {
 

@@ -20,7 +20,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 KERNEL_STATIC = 0
 
 # every symbol include/sie.h declares
-EXPORTS = ["sie_mesh_load", "sie_mesh_destroy", "loop_basis_build", "sie_loops_destroy", "sie_loops_export",
+EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basis_build", "sie_loops_destroy", "sie_loops_export",
            "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_lossy", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "pfft_plan_set_surface_model", "sie_postprocess", "sie_last_error"]
@@ -78,6 +78,7 @@ def lib():
     P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.sie_mesh_load.argtypes = [P, I64, P, I64, P, P, I32, PP]
+    L.sie_mesh_load_file.argtypes = [ctypes.c_char_p, PP]
     L.sie_mesh_destroy.argtypes = [P]
     L.loop_basis_build.argtypes = [P, ctypes.POINTER(SiePort), I32, PP, ctypes.POINTER(SieLoopStats)]
     L.sie_loops_destroy.argtypes = [P]
