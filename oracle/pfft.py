@@ -77,8 +77,12 @@ def stencil_1d(t, order, n):
 class Pfft:
     """pFFT operator of one mesh and loop basis (plain FP64)."""
 
-    def __init__(self, mesh, loops, params: PfftParams, rule=None):
+    def __init__(self, mesh, loops, params: PfftParams, rule=None, targets=None):
+        """targets: optional triangle ids; the near list then holds only the pairs
+        (t, j) with t in targets, so that rows of the product are exact for the
+        branches whose triangles are all targets (sampled rows of a large mesh)."""
         self.mesh, self.loops, self.p = mesh, loops, params
+        self.targets = None if targets is None else np.unique(np.asarray(targets, dtype=np.int64))
         self.rule = radon7() if rule is None else rule
         self.lo, self.h, self.N = grid_of(mesh, params.grid, params.box)
         g = tri_geometry(mesh.xyz, mesh.tri)
@@ -187,7 +191,7 @@ class Pfft:
         bmax = self.start.max(axis=1) + (O - 1)
         nt = self.mesh.nt
         pi, pj = [], []
-        for t in range(nt):
+        for t in (range(nt) if self.targets is None else self.targets):
             d = c - c[t]
             d2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
             box = np.all((bmin <= bmax[t]) & (bmax >= bmin[t]), axis=1)
@@ -260,10 +264,10 @@ class Pfft:
 class PfftSystem:
     """Loop-space product y = A (Z_s G + j w mu0/4pi (L_d + I H B)) A^T x."""
 
-    def __init__(self, mesh, loops, params: PfftParams, t_eff=None):
+    def __init__(self, mesh, loops, params: PfftParams, t_eff=None, targets=None):
         self.mesh, self.loops = mesh, loops
         self.t_eff = t_eff   # effective thickness per conductor: slab surface impedance (mom.py)
-        self.op = Pfft(mesh, loops, params)
+        self.op = Pfft(mesh, loops, params, targets=targets)
         self.G = gram_matrix(mesh, loops)
         nb = loops.nb
         self.A = loops.A[:, :nb].tocsr()

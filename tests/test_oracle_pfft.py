@@ -96,3 +96,22 @@ def test_converges_to_dense(bar):
         errs.append(np.linalg.norm(S.matvec(x, w) - yd) / np.linalg.norm(yd))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 1e-4
+
+
+def test_target_rows_equal_full_rows():
+    """The near list restricted to target triangles (sampled rows of large
+    meshes) gives, on every branch whose two triangles are targets, the same
+    rows as the full product; the other rows lose near terms."""
+    m = synth.tiny_wires()
+    O = build_loops(m)
+    prm = PfftParams(grid=(16, 8, 4), order=3, near_factor=5.0, near_min_diam=2.0, n_touch=8)
+    full = PfftSystem(m, O, prm)
+    rng = np.random.default_rng(4)
+    br = np.sort(rng.choice(O.nb, 12, replace=False))
+    part = PfftSystem(m, O, prm, targets=O.br_tri[br].ravel())
+    a = rng.standard_normal(O.nb) + 1j * rng.standard_normal(O.nb)
+    w = 2 * np.pi * 1e9
+    yf, yp = full.branch_product(a, w), part.branch_product(a, w)
+    assert np.abs(yp[br] - yf[br]).max() < 1e-13 * np.abs(yf[br]).max()
+    other = np.setdiff1d(np.arange(O.nb), np.unique(np.nonzero(np.isin(O.br_tri, O.br_tri[br]))[0]))
+    assert np.abs(yp[other] - yf[other]).min() > 1e-9 * np.abs(yf).max()
