@@ -203,7 +203,7 @@ inline int fft_threads(int elems) {
 
 namespace sie {
 
-constexpr int FFT_NMAX = 16;                       // longest in-register DFT
+constexpr int FFT_NMAX = 16;                       // longest in-register DFT of the plane passes
 // cos and sin of 2 pi i / 16, i = 0..7 (cos pi/8 = 0.9238..., sin pi/8 = 0.3826...)
 __host__ __device__ constexpr double c16(int i) {
     return i == 0 ? 1.0 : i == 1 ? 0.92387953251128674 : i == 2 ? 0.70710678118654752 : i == 3 ? 0.38268343236508977
@@ -214,7 +214,21 @@ __host__ __device__ constexpr double s16(int i) {
          : i == 4 ? 1.0 : i == 5 ? 0.92387953251128674 : i == 6 ? 0.70710678118654752 : 0.38268343236508977;
 }
 
-// In-register DFTs of length 2, 4, 8 and 16, natural order in and out,
+// cos and sin of 2 pi t / 32 for odd t in [1, 16) (pi/16 and 3 pi/16 and their
+// reflections: cos(pi/16) = 0.98078..., sin(pi/16) = 0.19509...,
+// cos(3 pi/16) = 0.83146..., sin(3 pi/16) = 0.55557...).
+__host__ __device__ constexpr double c32(int t) {
+    return t == 1 ? 0.98078528040323045 : t == 3 ? 0.83146961230254524 : t == 5 ? 0.55557023301960222
+         : t == 7 ? 0.19509032201612827 : t == 9 ? -0.19509032201612827 : t == 11 ? -0.55557023301960222
+         : t == 13 ? -0.83146961230254524 : -0.98078528040323045;
+}
+__host__ __device__ constexpr double s32(int t) {
+    return t == 1 ? 0.19509032201612827 : t == 3 ? 0.55557023301960222 : t == 5 ? 0.83146961230254524
+         : t == 7 ? 0.98078528040323045 : t == 9 ? 0.98078528040323045 : t == 11 ? 0.83146961230254524
+         : t == 13 ? 0.55557023301960222 : 0.19509032201612827;
+}
+
+// In-register DFTs of length 2, 4, 8, 16 and 32, natural order in and out,
 // built from radix-4 (and one radix-2) butterflies with the twiddles as
 // immediates; the direction is a compile-time choice.  DFT8 = 2 x 4 and
 // DFT16 = 4 x 4 are four-step products in registers: the inner DFTs run over
@@ -251,9 +265,37 @@ __device__ __forceinline__ void bfly4(C<T> &a0, C<T> &a1, C<T> &a2, C<T> &a3) {
     a3 = csub(t1, t3);
 }
 
-template <typename T, int N, bool INV>
-__device__ __forceinline__ void dft_reg(C<T> (&v)[FFT_NMAX]) {
-    if constexpr (N == 2) {
+// v * W_32^t, t in [0, 16) (even t are the W_16 twiddles).
+template <typename T, bool INV>
+__device__ __forceinline__ C<T> twiddle32(C<T> b, int t) {
+    if ((t & 1) == 0) return twiddle_mul<T, INV>(b, t >> 1);
+    const T c = T(c32(t)), sn = INV ? T(s32(t)) : T(-s32(t));
+    C<T> r;
+    r.x = b.x * c - b.y * sn;
+    r.y = b.x * sn + b.y * c;
+    return r;
+}
+
+template <typename T, int N, bool INV, int NA>
+__device__ __forceinline__ void dft_reg(C<T> (&v)[NA]) {
+    static_assert(NA >= N, "register array shorter than the DFT");
+    if constexpr (N == 32) {
+        // n = j + 2m: DFT16 over m for j = 0, 1; twiddle W_32^(j k1); DFT2 over j
+        C<T> a[16], b[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            a[m] = v[2 * m];
+            b[m] = v[2 * m + 1];
+        }
+        dft_reg<T, 16, INV>(a);
+        dft_reg<T, 16, INV>(b);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+            const C<T> t = twiddle32<T, INV>(b[k1], k1);
+            v[k1] = cadd(a[k1], t);
+            v[k1 + 16] = csub(a[k1], t);
+        }
+    } else if constexpr (N == 2) {
         const C<T> a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
@@ -313,27 +355,49 @@ inline void split4(int M, int &N1, int &N2) {
         default: { constexpr int N1 = 16, N2 = 16; BODY; } break;          \
     }
 
+// The same for the pencil kernels, which also take M = 512 = 16 x 32.
+#define SIE_SPLIT_DISPATCH_P(M, BODY)                                      \
+    switch (M) {                                                           \
+        case 8: { constexpr int N1 = 2, N2 = 4; BODY; } break;             \
+        case 16: { constexpr int N1 = 4, N2 = 4; BODY; } break;            \
+        case 32: { constexpr int N1 = 4, N2 = 8; BODY; } break;            \
+        case 64: { constexpr int N1 = 8, N2 = 8; BODY; } break;            \
+        case 128: { constexpr int N1 = 8, N2 = 16; BODY; } break;          \
+        case 256: { constexpr int N1 = 16, N2 = 16; BODY; } break;         \
+        default: { constexpr int N1 = 16, N2 = 32; BODY; } break;          \
+    }
+
+// Columns per pencil CTA: 16, or 8 when one factor is 32 (256 threads).
+template <int N1, int N2> struct Pencil {
+    static constexpr int NM = N1 > N2 ? N1 : N2;
+    static constexpr int KT = NM > 16 ? 8 : 16;
+    static constexpr int LGKT = KT == 16 ? 4 : 3;
+    static constexpr int threads = KT * NM;
+};
+
 // Four-step twiddle tables of an axis of length M = N1 N2 (built at plan
 // creation): tf[j2 * N1 + k1] = W_M^(j2 k1) for the forward pass 1 and
 // ti[k1 * N2 + p2] = W_M^(k1 p2) for the inverse pass A (used conjugated).
 
 // ---- x pencils.  Buffers [batch][rows][ncols], row x at x * ncols; one CTA
-// per (batch, 16 consecutive columns), 16 * max(N1, N2) threads, a shared
-// line per column (pitch M + 1).
+// per (batch, KT consecutive columns), KT * max(N1, N2) threads, a shared
+// line per column (pitch M + 1).  The same kernels run the y pencils of
+// grids whose (y, z) plane does not fit one CTA (batch = grid and
+// x-frequency, rows = y, columns = z).
 
 // Forward: in [batch][M/2][ncols] (zero-padded to M) -> out [batch][M][ncols].
 template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(256) k_fft_xf(const C<T> *__restrict__ in, C<T> *__restrict__ out, int ncols,
                                                 const C<T> *__restrict__ tf) {
-    constexpr int KT = 16, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
+    constexpr int KT = Pencil<N1, N2>::KT, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T> *S = reinterpret_cast<C<T> *>(smem_raw);
     const int tiles = ncols / KT;
     const int b = blockIdx.x / tiles, c0 = (blockIdx.x % tiles) * KT;
-    const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> 4;
+    const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> Pencil<N1, N2>::LGKT;
     C<T> *Sl = S + line * pitch;
     const int64_t stride = int64_t(N2) * ncols;
-    C<T> v[FFT_NMAX];
+    C<T> v[Pencil<N1, N2>::NM];
     if (q < N2) {                      // pass 1: j2 = q, DFT over j1 (x = j2 + N2 j1 < M/2)
         const int j2 = q;
         const C<T> *src = in + int64_t(b) * (M / 2) * ncols + c0 + line + int64_t(j2) * ncols;
@@ -360,14 +424,14 @@ __global__ void __launch_bounds__(256) k_fft_xf(const C<T> *__restrict__ in, C<T
 template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(256) k_fft_xi(const C<T> *__restrict__ in, C<T> *__restrict__ out, int ncols,
                                                 const C<T> *__restrict__ ti) {
-    constexpr int KT = 16, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
+    constexpr int KT = Pencil<N1, N2>::KT, M = N1 * N2, pitch = M + 1, H1 = N1 / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T> *S = reinterpret_cast<C<T> *>(smem_raw);
     const int tiles = ncols / KT;
     const int b = blockIdx.x / tiles, c0 = (blockIdx.x % tiles) * KT;
-    const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> 4;
+    const int line = threadIdx.x & (KT - 1), q = threadIdx.x >> Pencil<N1, N2>::LGKT;
     C<T> *Sl = S + line * pitch;
-    C<T> v[FFT_NMAX];
+    C<T> v[Pencil<N1, N2>::NM];
     if (q < N1) {                      // pass A: k1 = q, inverse DFT over k2, conj twiddle
         const int k1 = q;
         const C<T> *src = in + int64_t(b) * M * ncols + c0 + line + int64_t(k1) * ncols;
@@ -396,6 +460,110 @@ __global__ void __launch_bounds__(256) k_fft_xi(const C<T> *__restrict__ in, C<T
 #pragma unroll
         for (int p1 = 0; p1 < H1; ++p1) dst[p1 * int64_t(N2) * ncols] = v[p1];
     }
+}
+
+// ---- z rows of grids whose (y, z) plane does not fit one CTA.  After the x
+// and y pencils the buffer holds rows [grid][kx][ky][z < N_z]; per row the
+// zero-padded forward transform along z, the product with the kernel spectrum
+// Hp[fold kx][fold ky][fold kz] (real, or complex for the lossy kernel) and
+// the inverse transform cropped to z < N_z, in place.  RPC rows per CTA are
+// staged in shared memory (pitch M_z + 1) with coalesced loads; the four-step
+// passes map consecutive threads to consecutive rows, so every shared access
+// of a warp hits distinct banks.
+template <typename T>
+__device__ __forceinline__ C<T> kernel_mul(C<T> v, T h) { return cscale(v, h); }
+template <typename T>
+__device__ __forceinline__ C<T> kernel_mul(C<T> v, C<T> h) { return cmul(v, h); }
+
+template <int N1, int N2> struct ZRows {
+    static constexpr int NM = N1 > N2 ? N1 : N2;
+    static constexpr int RPC = 256 / NM;          // rows per CTA (256 threads)
+    static constexpr int pitch = N1 * N2 + 1;
+};
+
+template <typename T, int N1, int N2, typename HT>
+__global__ void __launch_bounds__(256) k_fft_zconv(C<T> *__restrict__ buf, int lgMx, int lgMy,
+                                                   const HT *__restrict__ Hp, const C<T> *__restrict__ tf,
+                                                   const C<T> *__restrict__ ti) {
+    constexpr int Mz = N1 * N2, Nz = Mz / 2, H1 = N1 / 2, RPC = ZRows<N1, N2>::RPC, pitch = ZRows<N1, N2>::pitch;
+    constexpr int LGNZ = Nz == 4 ? 2 : Nz == 8 ? 3 : Nz == 16 ? 4 : Nz == 32 ? 5 : Nz == 64 ? 6 : Nz == 128 ? 7 : 8;
+    static_assert((1 << LGNZ) == Nz, "row length");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T> *S = reinterpret_cast<C<T> *>(smem_raw);
+    const int64_t row0 = int64_t(blockIdx.x) * RPC;
+    C<T> *g = buf + row0 * Nz;
+    for (int i = threadIdx.x; i < RPC * Nz; i += blockDim.x) S[(i >> LGNZ) * pitch + (i & (Nz - 1))] = g[i];
+    __syncthreads();
+    const int r = threadIdx.x % RPC, q = threadIdx.x / RPC;
+    C<T> *Sr = S + r * pitch;
+    C<T> v[ZRows<N1, N2>::NM];
+    if (q < N2) {                      // forward pass 1: j2 = q, DFT over j1 (z = j2 + N2 j1 < N_z)
+        const int j2 = q;
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) v[j1] = j1 < H1 ? Sr[j2 + N2 * j1] : mk<T>(T(0), T(0));
+        dft_reg<T, N1, false>(v);
+        const C<T> *t = tf + j2 * N1;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Sr[k1 * N2 + j2] = k1 ? cmul(v[k1], t[k1]) : v[0];
+    }
+    __syncthreads();
+    const int k1 = q;
+    if (q < N1) {                      // forward pass 2, kernel product, inverse pass A (in registers)
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) v[j2] = Sr[k1 * N2 + j2];
+        dft_reg<T, N2, false>(v);      // v[k2] = X[k1 + N1 k2]
+        const int Mx = 1 << lgMx, My = 1 << lgMy;
+        const int64_t row = row0 + r;
+        const int ky = int(row & (My - 1)), kx = int((row >> lgMy) & (Mx - 1));
+        const HT *Hr = Hp + (int64_t(fold_index(kx, Mx)) * (My / 2 + 1) + fold_index(ky, My)) * (Mz / 2 + 1);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = kernel_mul<T>(v[k2], Hr[fold_index(k1 + N1 * k2, Mz)]);
+        dft_reg<T, N2, true>(v);
+    }
+    __syncthreads();                   // every thread has read its pass-2 slots
+    if (q < N1) {
+        const C<T> *t = ti + k1 * N2;
+#pragma unroll
+        for (int p2 = 0; p2 < N2; ++p2) {
+            C<T> o = v[p2];
+            if (p2) {
+                const C<T> w = t[p2];
+                o.x = v[p2].x * w.x + v[p2].y * w.y;
+                o.y = v[p2].y * w.x - v[p2].x * w.y;
+            }
+            Sr[p2 * N1 + k1] = o;
+        }
+    }
+    __syncthreads();
+    const int p2 = q;
+    if (q < N2) {                      // inverse pass B: p2 = q, DFT over k1, z = p2 + N2 p1 < N_z
+#pragma unroll
+        for (int kk = 0; kk < N1; ++kk) v[kk] = Sr[p2 * N1 + kk];
+        dft_reg<T, N1, true>(v);
+    }
+    __syncthreads();                   // every thread has read its pass-B slots
+    if (q < N2) {
+#pragma unroll
+        for (int p1 = 0; p1 < H1; ++p1) Sr[p2 + N2 * p1] = v[p1];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RPC * Nz; i += blockDim.x) g[i] = S[(i >> LGNZ) * pitch + (i & (Nz - 1))];
+}
+
+// Forward FFT of contiguous full rows of length M in place (the kernel
+// spectrum at plan creation when the (y, z) plane does not fit one CTA):
+// rows_per_cta * M <= FFT_E * blockDim.x elements staged per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_rows(C<T> *__restrict__ buf, int M, int rows_per_cta,
+                                                  const C<T> *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T> *s = reinterpret_cast<C<T> *>(smem_raw);
+    C<T> *g = buf + int64_t(blockIdx.x) * rows_per_cta * M;
+    const int n = rows_per_cta * M;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = g[i];
+    __syncthreads();
+    fft_lines<T>(s, M, rows_per_cta, M, 1, tw, false, false);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = s[i];
 }
 
 // ---- (y, z) plane passes with compile-time split (see k_fft_yzc).  The

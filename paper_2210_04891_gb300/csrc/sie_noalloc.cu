@@ -55,9 +55,10 @@ extern "C" int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, i
     if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED)
         return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: bad precision");
     const size_t cb = prec == SIE_PREC_FP64 ? 16 : 8;
-    const size_t spec_bytes = size_t(p->Mx) * p->Ny * p->Nz * cb;
+    // per grid: the x-transformed copy, and for planes larger than one CTA its y transform
+    const size_t spec_bytes = size_t(p->Mx) * (p->Ny + (p->large_plane ? p->My : 0)) * p->Nz * cb;
     if (spec_bytes > kNoallocScratchBytes)
-        return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: one grid's x-transformed copy needs " + std::to_string(spec_bytes) +
+        return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: one grid's transformed copies need " + std::to_string(spec_bytes) +
                                      " bytes, more than the fixed scratch of " +
                                      std::to_string(kNoallocScratchBytes) + " bytes; use pfft_convolve");
     (void)cudaGetLastError();

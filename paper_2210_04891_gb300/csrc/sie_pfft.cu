@@ -561,7 +561,7 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     const size_t sizes[kBufs] = {
         size_t(R) * 2 * p->nn * sizeof(double2),
         size_t(R) * 3 * p->Ng * cs,
-        size_t(R) * 3 * p->Mx * p->Ny * p->Nz * cs,
+        size_t(R) * 3 * p->Mx * (p->Ny + (p->large_plane ? p->My : 0)) * p->Nz * cs,
         size_t(R) * 3 * p->Ng * cs,
         size_t(R) * p->nt * 3 * sizeof(double2),
         size_t(R) * (p->nb + p->np) * sizeof(double2),

@@ -415,6 +415,46 @@ int set_smem(const void *fn, size_t bytes) {
 
 bool is_pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
 
+// Forward 3-D DFT of a full padded complex array hc [Mx][My][Mz] (the kernel
+// spectra).  Planes that fit one CTA: (y, z) planes into a temporary, then x
+// pencils; otherwise z rows and y pencils in place, then x pencils.  *out is
+// hc or the temporary (plan-owned; the caller frees it with plan_free).
+int kernel_fft3(pfft_plan *p, double2 *hc, double2 **out, cudaStream_t s) {
+    const int64_t nM = int64_t(p->Mx) * p->My * p->Mz;
+    double2 *res = hc;
+    int rc;
+    if (!p->large_plane) {
+        const size_t pbytes = size_t(p->My) * p->Mz * sizeof(double2);
+        if ((rc = set_smem((const void *)k_fft_plane<double>, pbytes))) return rc;
+        if ((rc = plan_alloc(p, (void **)&res, nM * sizeof(double2)))) return rc;
+        k_fft_plane<double><<<p->Mx, fft_threads(p->My * p->Mz), pbytes, s>>>(
+            hc, int64_t(p->My) * p->Mz, p->My, p->Mz, res, int64_t(p->My) * p->Mz, p->My, p->Mz, p->My, p->Mz,
+            p->d_tw64[1], p->d_tw64[2], 0);
+        p->launches++;
+    } else {
+        const int64_t nrows = int64_t(p->Mx) * p->My;
+        const int rpc = int(std::min<int64_t>(FFT_E * 256 / p->Mz, nrows));
+        const size_t rb = size_t(rpc) * p->Mz * sizeof(double2);
+        if ((rc = set_smem((const void *)k_fft_rows<double>, rb))) return rc;
+        k_fft_rows<double><<<unsigned(nrows / rpc), 256, rb, s>>>(hc, p->Mz, rpc, p->d_tw64[2]);
+        const int kty = std::min(16, p->Mz);
+        const size_t yb = size_t(kty) * (p->My + 1) * sizeof(double2);
+        if ((rc = set_smem((const void *)k_fft_pencil<double>, yb))) return rc;
+        k_fft_pencil<double><<<unsigned(p->Mx * (p->Mz / kty)), fft_threads(kty * p->My), yb, s>>>(
+            hc, int64_t(p->My) * p->Mz, p->Mz, p->My, p->My, p->My, p->My, p->Mz, kty, p->d_tw64[1], nullptr);
+        p->launches += 2;
+    }
+    const int KT = 16, ncols = p->My * p->Mz;
+    const size_t kb = size_t(KT) * (p->Mx + 1) * sizeof(double2);
+    if ((rc = set_smem((const void *)k_fft_pencil<double>, kb))) return rc;
+    k_fft_pencil<double><<<ncols / KT, fft_threads(KT * p->Mx), kb, s>>>(res, 0, ncols, p->Mx, p->Mx, p->Mx, p->My,
+                                                                       p->Mz, KT, p->d_tw64[0], nullptr);
+    p->launches++;
+    SIE_CUDA(cudaGetLastError());
+    *out = res;
+    return SIE_OK;
+}
+
 }  // namespace
 
 namespace sie {
@@ -438,30 +478,74 @@ template <> struct Tables<float> {
     static const float2 *Hl(const pfft_plan *p) { return p->d_Hl32; }
 };
 
-constexpr int kPencilCols = 16;   // columns per x-pencil CTA
-
+// Pencils along axis `axis` (0: x, ncols = N_y N_z per grid; 1: y of the large
+// plane route, ncols = N_z per (grid, x-frequency)) for `nbatch` batches.
 template <typename T, int N1, int N2>
-int launch_x(pfft_plan *p, const C<T> *in, C<T> *out, int ngrids, bool inverse, cudaStream_t s) {
+int launch_pencils(pfft_plan *p, const C<T> *in, C<T> *out, int64_t nbatch, int ncols, int axis, bool inverse,
+                   cudaStream_t s) {
     using Tb = Tables<T>;
-    const int ncols = p->Ny * p->Nz;
-    const size_t pb = size_t(kPencilCols) * (N1 * N2 + 1) * sizeof(C<T>);
-    const unsigned grid = unsigned(ngrids * (ncols / kPencilCols));
-    const int thr = kPencilCols * std::max(N1, N2);
+    using Pc = Pencil<N1, N2>;
+    const size_t pb = size_t(Pc::KT) * (N1 * N2 + 1) * sizeof(C<T>);
+    const int64_t ctas = nbatch * (ncols / Pc::KT);
+    if (ncols % Pc::KT || ctas > INT32_MAX) return fail(SIE_ERR_ARG, "pencil FFT: unsupported shape");
     if (!inverse) {
         int rc = set_smem((const void *)k_fft_xf<T, N1, N2>, pb);
         if (rc) return rc;
-        k_fft_xf<T, N1, N2><<<grid, thr, pb, s>>>(in, out, ncols, Tb::tf(p, 0));
+        k_fft_xf<T, N1, N2><<<unsigned(ctas), Pc::threads, pb, s>>>(in, out, ncols, Tb::tf(p, axis));
     } else {
         int rc = set_smem((const void *)k_fft_xi<T, N1, N2>, pb);
         if (rc) return rc;
-        k_fft_xi<T, N1, N2><<<grid, thr, pb, s>>>(in, out, ncols, Tb::ti(p, 0));
+        k_fft_xi<T, N1, N2><<<unsigned(ctas), Pc::threads, pb, s>>>(in, out, ncols, Tb::ti(p, axis));
     }
+    return SIE_OK;
+}
+
+template <typename T, int N1, int N2>
+int launch_x(pfft_plan *p, const C<T> *in, C<T> *out, int ngrids, bool inverse, cudaStream_t s) {
+    return launch_pencils<T, N1, N2>(p, in, out, ngrids, p->Ny * p->Nz, 0, inverse, s);
+}
+
+// z rows of the large plane route: forward, kernel product, inverse, in place.
+template <typename T, int N1, int N2, typename HT>
+int launch_zconv(pfft_plan *p, C<T> *rows, int64_t nrows, const HT *Hp, cudaStream_t s) {
+    using Tb = Tables<T>;
+    using Z = ZRows<N1, N2>;
+    const size_t zb = size_t(Z::RPC) * Z::pitch * sizeof(C<T>);
+    if (nrows % Z::RPC || nrows / Z::RPC > INT32_MAX) return fail(SIE_ERR_ARG, "z-row FFT: unsupported shape");
+    int rc = set_smem((const void *)k_fft_zconv<T, N1, N2, HT>, zb);
+    if (rc) return rc;
+    int lgMx = 0, lgMy = 0;
+    while ((1 << lgMx) < p->Mx) ++lgMx;
+    while ((1 << lgMy) < p->My) ++lgMy;
+    k_fft_zconv<T, N1, N2, HT><<<unsigned(nrows / Z::RPC), 256, zb, s>>>(rows, lgMx, lgMy, Hp, Tb::tf(p, 2),
+                                                                          Tb::ti(p, 2));
+    return SIE_OK;
+}
+
+// (y, z) convolution of the x-transformed grids when the plane does not fit
+// one CTA: y pencils forward into the second half of `spec`, z rows (forward,
+// kernel product, inverse), y pencils inverse back into the first half.
+template <typename T, typename HT>
+int launch_yz_large(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s) {
+    const int64_t planes = int64_t(ngrids) * p->Mx;
+    C<T> *spec2 = spec + planes * p->Ny * p->Nz;
+    int rc;
+    SIE_SPLIT_DISPATCH_P(p->My, (rc = launch_pencils<T, N1, N2>(p, spec, spec2, planes, p->Nz, 1, false, s)));
+    if (rc) return rc;
+    SIE_LAUNCH_CHECK(p);
+    SIE_SPLIT_DISPATCH_P(p->Mz, (rc = launch_zconv<T, N1, N2, HT>(p, spec2, planes * p->My, Hp, s)));
+    if (rc) return rc;
+    SIE_LAUNCH_CHECK(p);
+    SIE_SPLIT_DISPATCH_P(p->My, (rc = launch_pencils<T, N1, N2>(p, spec2, spec, planes, p->Nz, 1, true, s)));
+    if (rc) return rc;
+    SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
 
 template <typename T, typename HT>
 int launch_yzc(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s) {
     using Tb = Tables<T>;
+    if (p->large_plane) return launch_yz_large<T, HT>(p, spec, ngrids, Hp, s);
     if constexpr (sizeof(T) == 4 && sizeof(HT) == sizeof(T)) {   // static kernel in FP32: paired form
         bool done = false;
         const int rc = plane_conv_f32(p, spec, ngrids, s, done);
@@ -486,7 +570,7 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     int rc;
     {
         StageTimer tm(p, SIE_STAGE_FFT_X_FWD, s);
-        SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x<T, N1, N2>(p, grid, spec, ngrids, false, s)));
+        SIE_SPLIT_DISPATCH_P(p->Mx, (rc = launch_x<T, N1, N2>(p, grid, spec, ngrids, false, s)));
         if (rc) return rc;
         SIE_LAUNCH_CHECK(p);
     }
@@ -496,7 +580,7 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
         if (rc) return rc;
     }
     StageTimer tm(p, SIE_STAGE_FFT_X_INV, s);
-    SIE_SPLIT_DISPATCH(p->Mx, (rc = launch_x<T, N1, N2>(p, spec, grid, ngrids, true, s)));
+    SIE_SPLIT_DISPATCH_P(p->Mx, (rc = launch_x<T, N1, N2>(p, spec, grid, ngrids, true, s)));
     if (rc) return rc;
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
@@ -531,12 +615,16 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     const int O = prm->order;
     if (O < 2 || O > 4) return fail(SIE_ERR_ARG, "pfft_plan_create: order must be 2..4");
     for (int d = 0; d < 3; ++d)
-        if (!is_pow2(prm->grid[d]) || prm->grid[d] < O || prm->grid[d] < 4 || prm->grid[d] > 128)
-            return fail(SIE_ERR_ARG, "pfft_plan_create: grid sizes must be powers of two in [max(4, order), 128]");
-    if (3 * prm->grid[1] * (2 * prm->grid[2] + 1) * 16 > 200 * 1024 || 4 * prm->grid[1] * prm->grid[2] > FFT_MAX_ELEMS ||
-        16 * 2 * prm->grid[0] > FFT_MAX_ELEMS)
-        return fail(SIE_ERR_ARG, "pfft_plan_create: padded y-z plane exceeds one CTA's shared memory "
-                                 "(2N_y * 2N_z <= 8192 and 3 N_y (2N_z + 1) * 16 B <= 200 KiB)");
+        if (!is_pow2(prm->grid[d]) || prm->grid[d] < O || prm->grid[d] < 4 || prm->grid[d] > 256)
+            return fail(SIE_ERR_ARG, "pfft_plan_create: grid sizes must be powers of two in [max(4, order), 256]");
+    // the padded (y, z) plane fits one CTA's shared memory in FP64 (2N_y 2N_z <= 8192 and
+    // 3 N_y (2N_z + 1) 16 B <= 200 KiB); otherwise y pencils of N_z columns and z rows
+    const int gy = prm->grid[1], gz = prm->grid[2];
+    const bool plane_fits = gy <= 128 && gz <= 128 && 3 * gy * (2 * gz + 1) * 16 <= 200 * 1024 &&
+                            4 * gy * gz <= FFT_MAX_ELEMS;
+    if (!plane_fits && gz % (2 * gy > 256 ? 8 : 16) != 0)
+        return fail(SIE_ERR_ARG, "pfft_plan_create: a padded y-z plane larger than one CTA needs N_z >= 16 "
+                                 "(N_z >= 8 when N_y = 256)");
     if (prm->n_touch < 1 || prm->n_touch > 64) return fail(SIE_ERR_ARG, "pfft_plan_create: n_touch must be 1..64");
     if (!(prm->near_factor >= 0.0) || !(prm->near_min_diam >= 0.0)) return fail(SIE_ERR_ARG, "pfft_plan_create: negative near radius");
     if (prm->kernel != SIE_KERNEL_STATIC) return fail(SIE_ERR_ARG, "pfft_plan_create: only the static kernel is built");
@@ -557,6 +645,7 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     p->Q = 7;
     p->Nx = prm->grid[0]; p->Ny = prm->grid[1]; p->Nz = prm->grid[2];
     p->Mx = 2 * p->Nx; p->My = 2 * p->Ny; p->Mz = 2 * p->Nz;
+    p->large_plane = !plane_fits;
     p->Ng = int64_t(p->Nx) * p->Ny * p->Nz;
     const int64_t nt = m->nt, Q = p->Q;
 
@@ -914,23 +1003,13 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     k_fill_kernel<<<(nM + 255) / 256, 256, 0, s>>>(d_Hpad, d_Hc, p->Mx, p->My, p->Mz, p->h[0], p->h[1], p->h[2], prm->h0);
     p->launches++;
     {
-        const size_t pbytes = size_t(p->My) * p->Mz * sizeof(double2);
-        if ((rcode = set_smem((const void *)k_fft_plane<double>, pbytes))) return bail(rcode);
-        double2 *d_Hc2 = nullptr;
-        if ((rcode = plan_alloc(p, (void **)&d_Hc2, nM * sizeof(double2)))) return bail(rcode);
-        k_fft_plane<double><<<p->Mx, fft_threads(p->My * p->Mz), pbytes, s>>>(
-            d_Hc, int64_t(p->My) * p->Mz, p->My, p->Mz, d_Hc2, int64_t(p->My) * p->Mz, p->My, p->Mz, p->My, p->Mz,
-            p->d_tw64[1], p->d_tw64[2], 0);
-        SIE_CUDA(cudaMemcpyAsync(d_Hc, d_Hc2, nM * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        double2 *d_spec = nullptr;
+        if ((rcode = kernel_fft3(p, d_Hc, &d_spec, s))) return bail(rcode);
         SIE_CUDA(cudaStreamSynchronize(s));
-        plan_free(p, d_Hc2);
-        p->launches++;
-        const int KT = 16, ncols = p->My * p->Mz;
-        const size_t kb = size_t(KT) * (p->Mx + 1) * sizeof(double2);
-        if ((rcode = set_smem((const void *)k_fft_pencil<double>, kb))) return bail(rcode);
-        k_fft_pencil<double><<<ncols / KT, fft_threads(KT * p->Mx), kb, s>>>(
-            d_Hc, 0, ncols, p->Mx, p->Mx, p->Mx, p->My, p->Mz, KT, p->d_tw64[0], nullptr);
-        p->launches++;
+        if (d_spec != d_Hc) {
+            plan_free(p, d_Hc);
+            d_Hc = d_spec;
+        }
         const int64_t nh = int64_t(p->Mx / 2 + 1) * (p->My / 2 + 1) * (p->Mz / 2 + 1);
         if ((rcode = plan_alloc(p, (void **)&p->d_H64, nh * sizeof(double)))) return bail(rcode);
         if ((rcode = plan_alloc(p, (void **)&p->d_H32, nh * sizeof(float)))) return bail(rcode);
@@ -1069,25 +1148,17 @@ int lossy_spectrum(pfft_plan *p, double omega, double sigma, cudaStream_t s) {
     }
     double2 *d_Hc = nullptr, *d_Hc2 = nullptr;
     if ((rc = plan_alloc(p, (void **)&d_Hc, nM * sizeof(double2)))) return rc;
-    if ((rc = plan_alloc(p, (void **)&d_Hc2, nM * sizeof(double2)))) { plan_free(p, d_Hc); return rc; }
-    auto done = [&](int r) { plan_free(p, d_Hc); plan_free(p, d_Hc2); return r; };
+    auto done = [&](int r) {
+        if (d_Hc2 && d_Hc2 != d_Hc) plan_free(p, d_Hc2);
+        plan_free(p, d_Hc);
+        return r;
+    };
     const double mu0 = 4e-7 * M_PI;
     const double inv_delta = std::sqrt(omega * mu0 * sigma / 2.0);   // 1/delta, delta the skin depth
     k_fill_kernel_lossy<<<unsigned((nM + 255) / 256), 256, 0, s>>>(d_Hc, p->Mx, p->My, p->Mz, p->h[0], p->h[1],
                                                                    p->h[2], p->params.h0, inv_delta);
     p->launches++;
-    const size_t pbytes = size_t(p->My) * p->Mz * sizeof(double2);
-    if ((rc = set_smem((const void *)k_fft_plane<double>, pbytes))) return done(rc);
-    k_fft_plane<double><<<p->Mx, fft_threads(p->My * p->Mz), pbytes, s>>>(
-        d_Hc, int64_t(p->My) * p->Mz, p->My, p->Mz, d_Hc2, int64_t(p->My) * p->Mz, p->My, p->Mz, p->My, p->Mz,
-        p->d_tw64[1], p->d_tw64[2], 0);
-    p->launches++;
-    const int KT = 16, ncols = p->My * p->Mz;
-    const size_t kb = size_t(KT) * (p->Mx + 1) * sizeof(double2);
-    if ((rc = set_smem((const void *)k_fft_pencil<double>, kb))) return done(rc);
-    k_fft_pencil<double><<<ncols / KT, fft_threads(KT * p->Mx), kb, s>>>(d_Hc2, 0, ncols, p->Mx, p->Mx, p->Mx, p->My,
-                                                                       p->Mz, KT, p->d_tw64[0], nullptr);
-    p->launches++;
+    if ((rc = kernel_fft3(p, d_Hc, &d_Hc2, s))) return done(rc);
     k_extract_Hc<<<unsigned((nh + 255) / 256), 256, 0, s>>>(d_Hc2, p->d_Hl64, p->d_Hl32, p->Mx, p->My, p->Mz,
                                                           1.0 / double(nM));
     p->launches++;

@@ -25,7 +25,8 @@ struct Scratch {
     // complex (float4: re hi, re lo, im hi, im lo) in the mixed form
     void *tour = nullptr;      // [R][2 n_nodes]
     void *grid = nullptr;      // complex T [3][R][Ng]   grid currents, then grid potentials
-    void *spec = nullptr;      // complex T [3R][Mx][Ny][Nz]  grids transformed along x
+    void *spec = nullptr;      // complex T [3R][Mx][Ny][Nz]  grids transformed along x, then (large
+                               // planes) [3R][Mx][My][Nz] the same transformed along y
     void *phiT = nullptr;      // complex T [Ng][3][R]   grid potentials, right-hand sides innermost
     void *y_tri = nullptr;     // [R][nt][3]
     void *y_br = nullptr;      // [R][nb + np]
@@ -47,6 +48,8 @@ struct pfft_plan {
     int64_t nt = 0, nb = 0, nl = 0, np = 0, nn = 0;
     int32_t ncond = 0;
     int Nx = 0, Ny = 0, Nz = 0, Mx = 0, My = 0, Mz = 0, O = 3, Q = 7;
+    // the padded (y, z) plane does not fit one CTA: y pencils and z rows through device memory
+    bool large_plane = false;
     int64_t Ng = 0;
     double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0};
     double r_near = 0.0;
