@@ -201,3 +201,117 @@ def merge(meshes, name="merged"):
     return Mesh(xyz=np.concatenate(xyz), tri=np.concatenate(tri).astype(np.int32),
                 cond=np.concatenate(cond).astype(np.int32), sigma=np.concatenate(sigma),
                 ports=ports, name=name)
+
+
+def plane_pair_mesh(L=10e-3, t=35e-6, gap=100e-6, n=250, m_gap=3, n_pairs=200, via_k=2, n_ports=4, pad_k=3,
+                    site=10, jitter=0.15, seed=11, sigma=5.8e7, name="plane_pair"):
+    """Two square planes (L x L, thickness t) a gap apart, joined by via pairs.
+
+    Both planes sit on one structured lattice of n x n cells (spacing h = L/n);
+    every quad is split into two triangles with alternating diagonals.  A via
+    is a square prism of via_k x via_k cells spanning the gap (m_gap divisions
+    in height); its cells are removed from the two inner faces and its walls
+    share their end edges with the hole boundaries, so the surface is
+    conformal (one closed conductor with a handle per via).  Via pairs are
+    placed at seeded distinct sites of a coarse lattice (site x site cells),
+    the two vias of a pair 2 via_k cells apart along x.  Each port drives a
+    pad of pad_k x pad_k cells on the top plane's upper face (source) against
+    the pad below it on the bottom plane's lower face (sink), at further
+    seeded sites.  Vertices inside the two outer faces get an in-plane jitter
+    of +-jitter h.
+    """
+    rng = np.random.default_rng(seed)
+    h = L / n
+    zlev = np.concatenate([[0.0], t + gap * np.arange(m_gap + 1) / m_gap, [2 * t + gap]])
+    top_in, top_out = 1 + m_gap, 2 + m_gap          # z levels of the top plane's faces
+    nsite = n // site
+    cand = np.array([(I, J) for I in range(1, nsite - 1) for J in range(1, nsite - 1)])
+    if site < 3 * via_k + 2 or site < pad_k + 4 or len(cand) < n_pairs + n_ports:
+        raise ValueError("plane_pair_mesh: too few via/pad sites for the lattice")
+    pick = rng.permutation(len(cand))[:n_pairs + n_ports]
+    via_sites, pad_sites = cand[pick[:n_pairs]], cand[pick[n_pairs:]]
+    hole = np.zeros((n, n), bool)
+    vias = []
+    for I, J in via_sites:
+        i0, j0 = I * site + 1, J * site + 2
+        for dx in (0, 2 * via_k):
+            vias.append((i0 + dx, j0))
+            hole[i0 + dx:i0 + dx + via_k, j0:j0 + via_k] = True
+
+    def code(lz, i, j):
+        return (np.asarray(lz) * (n + 1) + np.asarray(i)) * (n + 1) + np.asarray(j)
+
+    quads, normals, tags = [], [], []   # quads: [k, 4] lattice codes; tag: face id for ports
+
+    def add(q, nrm, tag):
+        quads.append(np.stack(q, axis=-1).reshape(-1, 4))
+        normals.append(np.broadcast_to(np.asarray(nrm, float), (quads[-1].shape[0], 3)))
+        tags.append(np.full(quads[-1].shape[0], tag))
+
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    cell_i, cell_j = {}, {}
+    for lz, sgn, keep, tag in ((0, -1.0, None, 0), (1, 1.0, ~hole, 1), (top_in, -1.0, ~hole, 2),
+                               (top_out, 1.0, None, 3)):
+        ci, cj = (ii, jj) if keep is None else (ii[keep], jj[keep])
+        ci, cj = ci.ravel(), cj.ravel()
+        cell_i[tag], cell_j[tag] = ci, cj
+        add((code(lz, ci, cj), code(lz, ci + 1, cj), code(lz, ci + 1, cj + 1), code(lz, ci, cj + 1)),
+            (0.0, 0.0, sgn), tag)
+    r = np.arange(n)
+    for l0, l1 in ((0, 1), (top_in, top_out)):        # plane sides
+        for fixed, axis, sgn in ((0, 0, -1.0), (n, 0, 1.0), (0, 1, -1.0), (n, 1, 1.0)):
+            nrm = np.zeros(3)
+            nrm[axis] = sgn
+            if axis == 0:
+                q = (code(l0, fixed, r), code(l0, fixed, r + 1), code(l1, fixed, r + 1), code(l1, fixed, r))
+            else:
+                q = (code(l0, r, fixed), code(l0, r + 1, fixed), code(l1, r + 1, fixed), code(l1, r, fixed))
+            add(q, nrm, 4)
+    kk = np.arange(via_k)
+    lv = np.arange(1, 1 + m_gap)
+    for i0, j0 in vias:                               # via walls
+        K, Lv = np.meshgrid(kk, lv, indexing="ij")
+        for fixed, axis, sgn in ((i0, 0, -1.0), (i0 + via_k, 0, 1.0), (j0, 1, -1.0), (j0 + via_k, 1, 1.0)):
+            nrm = np.zeros(3)
+            nrm[axis] = sgn
+            if axis == 0:
+                a = j0 + K
+                q = (code(Lv, fixed, a), code(Lv, fixed, a + 1), code(Lv + 1, fixed, a + 1), code(Lv + 1, fixed, a))
+            else:
+                a = i0 + K
+                q = (code(Lv, a, fixed), code(Lv, a + 1, fixed), code(Lv + 1, a + 1, fixed), code(Lv + 1, a, fixed))
+            add(q, nrm, 5)
+    Q = np.concatenate(quads)
+    nrm = np.concatenate(normals)
+    tag = np.concatenate(tags)
+    used, inv = np.unique(Q.ravel(), return_inverse=True)
+    Q = inv.reshape(Q.shape)
+    lz = used // ((n + 1) * (n + 1))
+    rem = used % ((n + 1) * (n + 1))
+    vi, vj = rem // (n + 1), rem % (n + 1)
+    xyz = np.stack([vi * h, vj * h, zlev[lz]], axis=1)
+    if jitter > 0.0:
+        outer = ((lz == 0) | (lz == top_out)) & (vi > 0) & (vi < n) & (vj > 0) & (vj < n)
+        xyz[outer, :2] += rng.uniform(-jitter, jitter, (int(outer.sum()), 2)) * h
+    par = np.arange(Q.shape[0]) % 2
+    t0 = np.where(par[:, None] == 0, Q[:, [0, 1, 2]], Q[:, [0, 1, 3]])
+    t1 = np.where(par[:, None] == 0, Q[:, [0, 2, 3]], Q[:, [1, 2, 3]])
+    tris = np.empty((2 * Q.shape[0], 3), np.int64)
+    tris[0::2], tris[1::2] = t0, t1
+    tris = _orient(xyz, tris, np.repeat(nrm, 2, axis=0))
+    tri_tag = np.repeat(tag, 2)
+    # triangle ids of the two outer faces by cell (both triangles of a quad)
+    qid = {f: np.nonzero(tag == f)[0] for f in (0, 3)}
+    ports = []
+    for I, J in pad_sites:
+        a0, b0 = I * site + 3, J * site + 3
+        sets = []
+        for f in (3, 0):
+            inpad = ((cell_i[f] >= a0) & (cell_i[f] < a0 + pad_k) & (cell_j[f] >= b0) & (cell_j[f] < b0 + pad_k))
+            qs = qid[f][inpad]
+            sets.append(np.sort(np.concatenate([2 * qs, 2 * qs + 1])).astype(np.int32))
+        ports.append((sets[0], sets[1]))
+    for src, snk in ports:
+        assert np.all(tri_tag[src] == 3) and np.all(tri_tag[snk] == 0)
+    return Mesh(xyz=xyz, tri=tris.astype(np.int32), cond=np.zeros(tris.shape[0], np.int32),
+                sigma=np.array([sigma], dtype=np.float64), ports=ports, name=name)

@@ -1,14 +1,15 @@
 """Named synthetic workloads (geometry, frequencies, grid sizes) and seeded vectors.
 
 The shapes follow the paper's example classes: a straight rectangular copper
-interconnect (Sec. V-A) and an array of bond wires (Sec. V-B).  All sizes are
+interconnect (Sec. V-A), an array of bond wires (Sec. V-B) and a power
+distribution structure of two planes joined by vias (Sec. V-C).  All sizes are
 in metres, conductivities in S/m, frequencies in Hz.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .meshes import box_mesh, wire_array_mesh, merge
+from .meshes import box_mesh, wire_array_mesh, merge, plane_pair_mesh
 
 UM = 1e-6
 
@@ -31,6 +32,24 @@ def bondwires_40k():
                         jitter=0.10, seed=2, sigma=4.1e7, name="bondwires_8x2mm")
     return dict(mesh=m, freqs=np.logspace(6, 10, 16), grid=(128, 64, 32),
                 name="bondwires_8x2mm_40k")
+
+
+def pdn_500k():
+    """PDN-like plane pair: two Cu planes 10 x 10 mm, 35 um thick, 100 um apart,
+    on a 40 um cell lattice (~517k triangles), 200 seeded via pairs (square
+    80 um vias, 3 divisions across the gap), 4 ports from a pad on the top
+    plane's upper face to the pad below it on the bottom plane's lower face,
+    8 log-spaced frequencies 1 MHz - 1 GHz; pFFT grid 256 x 256 x 32."""
+    m = plane_pair_mesh(L=10e-3, t=35 * UM, gap=100 * UM, n=250, m_gap=3, n_pairs=200, via_k=2, n_ports=4,
+                        pad_k=3, site=10, jitter=0.15, seed=11, sigma=5.8e7, name="pdn_2x10mm")
+    return dict(mesh=m, freqs=np.logspace(6, 9, 8), grid=(256, 256, 32), name="pdn_2x10mm_500k")
+
+
+def tiny_pdn(seed=12):
+    """Small plane pair (0.6 x 0.6 mm, 25 um cells, 2 via pairs of one-cell vias,
+    2 ports, ~4.8k triangles) for oracle checks of the same structure."""
+    return plane_pair_mesh(L=0.6e-3, t=35 * UM, gap=100 * UM, n=24, m_gap=3, n_pairs=2, via_k=1, n_ports=2,
+                           pad_k=2, site=6, jitter=0.15, seed=seed, sigma=5.8e7, name="tiny_pdn")
 
 
 def tiny_bar(nx=10, ny=2, nz=1, L=100 * UM, W=20 * UM, T=10 * UM, jitter=0.15, seed=3):
@@ -56,6 +75,7 @@ def tiny_two_bars():
 WORKLOADS = {
     "bar_1000x20x10um_1.5k": bar_1500,
     "bondwires_8x2mm_40k": bondwires_40k,
+    "pdn_2x10mm_500k": pdn_500k,
 }
 
 
