@@ -235,6 +235,41 @@ int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *port
 int sie_postprocess(pfft_plan *p, const void *x, int32_t nrhs, const double *omega, int32_t prec,
                     void *i_branch, void *v_branch, void *phi, void *cuda_stream);
 
+/* Batches of plans (uneven geometries solved together).  A batch borrows n
+ * distinct plans on one device (each plan once) and owns a stream per plan;
+ * while a batch call runs, the caller must not use its plans elsewhere.
+ * Errors: SIE_ERR_ARG (NULL or repeated plan, plans on different devices),
+ * SIE_ERR_CUDA, SIE_ERR_OOM. */
+typedef struct sie_batch sie_batch;
+int sie_batch_create(pfft_plan *const *plans, int32_t n, sie_batch **out);
+void sie_batch_destroy(sie_batch *b);
+
+/* The product of pfft_matvec for every plan i of the batch at once:
+ * y[i] = (A) Z_b(omega[i][r]) (A^T) x[i], x[i], y[i] device complex128
+ * [nrhs[i]][n_loops_i or n_branches_i]; omega[i] host [nrhs[i]]; space and prec
+ * as in pfft_matvec, shared by all plans.  Each plan's kernels run on its own
+ * stream, forked from cuda_stream and joined back (the call returns when every
+ * result is ready).  use_graph = 1: the whole step, the per-plan coefficient
+ * uploads (from pinned staging the batch owns) and every kernel, is captured
+ * into one CUDA graph on the first call and replayed by later calls with the
+ * same x, y, nrhs, space and prec (omega may change between replays); it is
+ * captured again when any of these changes or a plan's scratch has been
+ * reallocated.  Results equal pfft_matvec's bit for bit. */
+int sie_batch_matvec(sie_batch *b, void *const *x, void *const *y, const int32_t *nrhs,
+                     const double *const *omega, int32_t space, int32_t prec, int32_t use_graph,
+                     void *cuda_stream);
+/* Graph captures and replays so far (either pointer may be NULL). */
+int sie_batch_stats(const sie_batch *b, int64_t *captures, int64_t *replays);
+
+/* sie_solve for every plan i at once (one host thread per plan, each plan's
+ * work on its batch stream): freqs[i][nf[i]], ports[i][np[i]], Z_out[i] host
+ * [nf[i]][np[i]][np[i]], st_out[n] (may be NULL).  Returns the first plan's
+ * error (message names the plan); every plan's Z and stats are still filled as
+ * sie_solve fills them. */
+int sie_batch_solve(sie_batch *b, const double *const *freqs, const int32_t *nf, const int32_t *const *ports,
+                    const int32_t *np, const sie_solve_opts *opts, sie_c64 *const *Z_out,
+                    sie_solve_stats *st_out);
+
 /* Plan introspection for tests and benchmarks: sizes (any pointer may be NULL). */
 int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, int64_t *n_tri,
                    int64_t *n_near_pairs, double *grid_h /* [3] */, double *r_near,

@@ -304,6 +304,72 @@ def pfft_precond_apply(plan: Plan, y, omega, out=None, prec=N.PREC_FP64, stream=
     return z
 
 
+class Batch:
+    """Plans of uneven geometries driven together (sie_batch_*)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        check(lib().sie_batch_create(arr, len(self.plans), ctypes.byref(h)))
+        self.h = h
+
+    def matvec(self, xs, omegas, space=N.SPACE_LOOP, prec=N.PREC_FP64, graph=True, outs=None, stream=None):
+        """[y_i] for plans i, x_i [nrhs_i, n_i] CUDA complex128, omegas[i] [nrhs_i]."""
+        import torch
+        n = len(self.plans)
+        if len(xs) != n or len(omegas) != n:
+            raise ValueError("one input and one omega array per plan")
+        ys = []
+        oms = []
+        for i, (p, x) in enumerate(zip(self.plans, xs)):
+            _check_vec(x, p.nl if space == N.SPACE_LOOP else p.nb, "x")
+            y = torch.empty_like(x) if outs is None else outs[i]
+            ys.append(y)
+            oms.append(np.ascontiguousarray(np.broadcast_to(np.asarray(omegas[i], np.float64), (x.shape[0],))))
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        r = np.array([x.shape[0] for x in xs], np.int32)
+        op = (ctypes.c_void_p * n)(*[o.ctypes.data for o in oms])
+        check(lib().sie_batch_matvec(self.h, xp, yp, _ptr(r), op, space, prec, int(graph), _stream(stream)))
+        return ys
+
+    def stats(self):
+        c, r = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().sie_batch_stats(self.h, ctypes.byref(c), ctypes.byref(r)))
+        return dict(captures=c.value, replays=r.value)
+
+    def solve(self, freqs, ports=None, tol=1e-6, restart=200, max_iter=2000, precond=1, prec=N.PREC_FP64,
+              refine=False):
+        """[(Z_i, stats_i)] of sie_solve for every plan at once; freqs[i] per plan."""
+        n = len(self.plans)
+        fs = [np.ascontiguousarray(f, np.float64) for f in freqs]
+        prs = [np.arange(p.np, dtype=np.int32) if ports is None or ports[i] is None
+               else np.ascontiguousarray(ports[i], np.int32) for i, p in enumerate(self.plans)]
+        Zs = [np.zeros((f.shape[0], q.shape[0], q.shape[0]), np.complex128) for f, q in zip(fs, prs)]
+        o = N.SolveOpts(tol=tol, restart=restart, max_iter=max_iter, precond=precond, prec=prec, refine=int(refine))
+        st = (N.SolveStats * n)()
+        fp = (ctypes.c_void_p * n)(*[f.ctypes.data for f in fs])
+        nf = np.array([f.shape[0] for f in fs], np.int32)
+        pp = (ctypes.c_void_p * n)(*[q.ctypes.data for q in prs])
+        npr = np.array([q.shape[0] for q in prs], np.int32)
+        zp = (ctypes.c_void_p * n)(*[z.ctypes.data for z in Zs])
+        rc = lib().sie_batch_solve(self.h, fp, _ptr(nf), pp, _ptr(npr), ctypes.byref(o), zp, st)
+        if rc not in (N.SIE_OK, -6):
+            check(rc)
+        out = []
+        for i in range(n):
+            d = {k: getattr(st[i], k) for k, _ in N.SolveStats._fields_}
+            d["converged"] = d["n_not_converged"] == 0
+            out.append((Zs[i], d))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().sie_batch_destroy(self.h)
+            self.h = None
+
+
 def sie_solve(plan: Plan, freqs, ports=None, tol=1e-6, restart=200, max_iter=2000, precond=1,
               prec=N.PREC_FP64, refine=False):
     f = np.ascontiguousarray(freqs, np.float64)

@@ -583,6 +583,7 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     }
     s.cap_rhs = int32_t(R);
     s.cs = int(cs);
+    ++p->scr_gen;
     return SIE_OK;
 }
 
@@ -729,10 +730,8 @@ std::complex<double> surface_impedance(const pfft_plan *p, int c, double w) {
 
 // Per right-hand side: Z_s of each conductor and c_L / j (Eq. ImpedanceOp, Eq. Zb),
 // in FP64 and as double-float pairs.
-int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
+int fill_coef(const pfft_plan *p, const double *omega, int32_t R, double *cf, float2 *cd) {
     const size_t n = size_t(R) * (2 * p->ncond + 1);
-    std::vector<double> cf(n);
-    std::vector<float2> cd(n);
     for (int32_t r = 0; r < R; ++r) {
         const double w = omega[r];
         if (!(w >= 0.0) || !std::isfinite(w)) return fail(SIE_ERR_ARG, "pfft_matvec: omega must be finite and >= 0");
@@ -747,6 +746,15 @@ int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
         const float hi = float(cf[i]);
         cd[i] = make_float2(hi, float(cf[i] - double(hi)));
     }
+    return SIE_OK;
+}
+
+int upload_coef(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st) {
+    const size_t n = size_t(R) * (2 * p->ncond + 1);
+    std::vector<double> cf(n);
+    std::vector<float2> cd(n);
+    int rc = fill_coef(p, omega, R, cf.data(), cd.data());
+    if (rc) return rc;
     SIE_CUDA(cudaMemcpyAsync(p->scr.coef, cf.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     SIE_CUDA(cudaMemcpyAsync(coef_dd(p), cd.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st));
     return SIE_OK;
@@ -758,6 +766,10 @@ int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const doubl
     if (rc) return rc;
     rc = upload_coef(p, omega, nrhs, st);
     if (rc) return rc;
+    return matvec_launch(p, x, y, nrhs, space, prec, st);
+}
+
+int matvec_launch(pfft_plan *p, const void *x, void *y, int32_t nrhs, int space, int prec, cudaStream_t st) {
     if (prec == SIE_PREC_FP64)
         return matvec_t<double>(p, (const double2 *)x, (double2 *)y, nrhs, space, st);
     return matvec_t<float>(p, (const double2 *)x, (double2 *)y, nrhs, space, st);

@@ -50,6 +50,8 @@ struct pfft_plan {
     int Nx = 0, Ny = 0, Nz = 0, Mx = 0, My = 0, Mz = 0, O = 3, Q = 7;
     // the padded (y, z) plane does not fit one CTA: y pencils and z rows through device memory
     bool large_plane = false;
+    // incremented whenever the scratch buffers are reallocated (captured graphs hold their addresses)
+    uint64_t scr_gen = 0;
     int64_t Ng = 0;
     double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0};
     double r_near = 0.0;
@@ -170,6 +172,14 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
 // (gamma / sigma) coth(gamma t / 2) with gamma = (1 + j) sqrt(w mu0 sigma / 2).
 std::complex<double> surface_impedance(const pfft_plan *p, int c, double w);
 float2 *coef_dd(const pfft_plan *p);   // double-float copy of scr.coef
+// Per-right-hand-side scalars of Eq. Zb for omega[R] into host arrays cf[R (2 ncond + 1)]
+// (FP64) and cd (the same as double-float pairs); SIE_ERR_ARG for a bad omega.
+int fill_coef(const pfft_plan *p, const double *omega, int32_t R, double *cf, float2 *cd);
+// The matvec's kernels on stream st, with scratch reserved and the coefficients
+// of this batch already in scr.coef (matvec_async = reserve + upload + launch).
+int matvec_launch(pfft_plan *p, const void *x, void *y, int32_t nrhs, int space, int prec, cudaStream_t st);
+int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega, int space, int prec,
+                 cudaStream_t st);
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
 int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s,

@@ -315,3 +315,105 @@ def plane_pair_mesh(L=10e-3, t=35e-6, gap=100e-6, n=250, m_gap=3, n_pairs=200, v
         assert np.all(tri_tag[src] == 3) and np.all(tri_tag[snk] == 0)
     return Mesh(xyz=xyz, tri=tris.astype(np.int32), cond=np.zeros(tris.shape[0], np.int32),
                 sigma=np.array([sigma], dtype=np.float64), ports=ports, name=name)
+
+
+def extruded_cells_mesh(mask, c, t, nz, src_edges, snk_edges, jitter=0.0, seed=0, sigma=5.8e7, name="extruded"):
+    """Closed surface of the region of occupied cells `mask` [nx, ny] (cell size
+    c) extruded through thickness t: a top and a bottom quad per cell, and wall
+    quads (nz divisions in height) on every lattice edge between an occupied
+    and an empty cell.  Port contacts are the wall triangles on the lattice
+    edges listed in src_edges / snk_edges, given as (axis, i, j): the edge on
+    lattice line x = i between y = j and j + 1 (axis 0) or on y = j between
+    x = i and i + 1 (axis 1).  Top and bottom vertices strictly inside the
+    region get an in-plane jitter of +-jitter c."""
+    rng = np.random.default_rng(seed)
+    mask = np.asarray(mask, bool)
+    nx, ny = mask.shape
+    occ = np.zeros((nx + 2, ny + 2), bool)
+    occ[1:-1, 1:-1] = mask
+
+    def code(k, i, j):
+        return (np.asarray(k) * (nx + 1) + np.asarray(i)) * (ny + 1) + np.asarray(j)
+
+    quads, normals, edge_key = [], [], []
+    ci, cj = np.nonzero(mask)
+    for k, sgn in ((0, -1.0), (nz, 1.0)):
+        quads.append(np.stack([code(k, ci, cj), code(k, ci + 1, cj), code(k, ci + 1, cj + 1), code(k, ci, cj + 1)],
+                              axis=-1))
+        normals.append(np.broadcast_to([0.0, 0.0, sgn], (ci.size, 3)))
+        edge_key.append(np.full(ci.size, -1, np.int64))
+    kz = np.arange(nz)
+    # walls on x-lines: between cells (i-1, j) and (i, j)
+    a, b = occ[:-1, 1:-1], occ[1:, 1:-1]                 # [nx+1, ny]: left / right cell of line i
+    for side, sgn in ((a & ~b, 1.0), (~a & b, -1.0)):
+        li, lj = np.nonzero(side)
+        I, K = np.broadcast_arrays(li[:, None], kz[None, :])
+        J = np.broadcast_to(lj[:, None], I.shape)
+        quads.append(np.stack([code(K, I, J), code(K, I, J + 1), code(K + 1, I, J + 1), code(K + 1, I, J)],
+                              axis=-1).reshape(-1, 4))
+        normals.append(np.broadcast_to([sgn, 0.0, 0.0], (I.size, 3)))
+        edge_key.append((0 * (nx + 1) + I.ravel()) * (ny + 1) + J.ravel())
+    # walls on y-lines: between cells (i, j-1) and (i, j)
+    a, b = occ[1:-1, :-1], occ[1:-1, 1:]                 # [nx, ny+1]
+    for side, sgn in ((a & ~b, 1.0), (~a & b, -1.0)):
+        li, lj = np.nonzero(side)
+        I, K = np.broadcast_arrays(li[:, None], kz[None, :])
+        J = np.broadcast_to(lj[:, None], I.shape)
+        quads.append(np.stack([code(K, I, J), code(K, I + 1, J), code(K + 1, I + 1, J), code(K + 1, I, J)],
+                              axis=-1).reshape(-1, 4))
+        normals.append(np.broadcast_to([0.0, sgn, 0.0], (I.size, 3)))
+        edge_key.append(((nx + 1) * (ny + 1)) + I.ravel() * (ny + 1) + J.ravel())
+    Q = np.concatenate(quads)
+    nrm = np.concatenate(normals)
+    ekey = np.concatenate(edge_key)
+    used, inv = np.unique(Q.ravel(), return_inverse=True)
+    Q = inv.reshape(Q.shape)
+    k = used // ((nx + 1) * (ny + 1))
+    rem = used % ((nx + 1) * (ny + 1))
+    vi, vj = rem // (ny + 1), rem % (ny + 1)
+    xyz = np.stack([vi * c, vj * c, k * (t / nz)], axis=1).astype(np.float64)
+    if jitter > 0.0:
+        # a vertex is inside the region when its four surrounding cells are occupied
+        inside = occ[vi, vj] & occ[vi + 1, vj] & occ[vi, vj + 1] & occ[vi + 1, vj + 1]
+        move = inside & ((k == 0) | (k == nz))
+        xyz[move, :2] += rng.uniform(-jitter, jitter, (int(move.sum()), 2)) * c
+    par = np.arange(Q.shape[0]) % 2
+    tris = np.empty((2 * Q.shape[0], 3), np.int64)
+    tris[0::2] = np.where(par[:, None] == 0, Q[:, [0, 1, 2]], Q[:, [0, 1, 3]])
+    tris[1::2] = np.where(par[:, None] == 0, Q[:, [0, 2, 3]], Q[:, [1, 2, 3]])
+    tris = _orient(xyz, tris, np.repeat(nrm, 2, axis=0))
+    tkey = np.repeat(ekey, 2)
+
+    def contact(edges):
+        keys = [(ax * (nx + 1) * (ny + 1)) + i * (ny + 1) + j for ax, i, j in edges]
+        return np.nonzero(np.isin(tkey, keys))[0].astype(np.int32)
+
+    ports = [(contact(src_edges), contact(snk_edges))]
+    return Mesh(xyz=xyz, tri=tris.astype(np.int32), cond=np.zeros(tris.shape[0], np.int32),
+                sigma=np.array([sigma], dtype=np.float64), ports=ports, name=name)
+
+
+def meander_mesh(n_seg, w, t, run, kw=2, gap_w=1.0, jitter=0.1, seed=0, sigma=5.8e7, name="meander"):
+    """Serpentine trace of width w and thickness t: n_seg segments alternating
+    runs of length `run` along x and jogs along y with right-angle corners
+    (the runs 2 gap_w w apart centre line to centre line minus w), on a lattice
+    of cell size w / kw, walls divided in height like the cell size.  One port
+    from the free end face of the first run (source) to that of the last run."""
+    c = w / kw
+    nr = max(2, (n_seg + 1) // 2)
+    gap = max(1, int(round(gap_w * kw)))
+    L = max(3 * kw, int(round(run / c)))
+    nx, ny = L, nr * kw + (nr - 1) * gap
+    mask = np.zeros((nx, ny), bool)
+    for r in range(nr):
+        y0 = r * (kw + gap)
+        mask[:, y0:y0 + kw] = True
+        if r + 1 < nr:                       # jog to the next run: right end after even runs, left after odd
+            xs = slice(nx - kw, nx) if r % 2 == 0 else slice(0, kw)
+            mask[xs, y0:y0 + 2 * kw + gap] = True
+    nz = max(1, int(round(t / c)))
+    src = [(0, 0, j) for j in range(kw)]
+    y_last = (nr - 1) * (kw + gap)
+    i_end = nx if (nr - 1) % 2 == 0 else 0   # the last run's free end
+    snk = [(0, i_end, y_last + j) for j in range(kw)]
+    return extruded_cells_mesh(mask, c, t, nz, src, snk, jitter=jitter, seed=seed, sigma=sigma, name=name)

@@ -1,15 +1,16 @@
 """Named synthetic workloads (geometry, frequencies, grid sizes) and seeded vectors.
 
 The shapes follow the paper's example classes: a straight rectangular copper
-interconnect (Sec. V-A), an array of bond wires (Sec. V-B) and a power
-distribution structure of two planes joined by vias (Sec. V-C).  All sizes are
+interconnect (Sec. V-A), an array of bond wires (Sec. V-B) a power
+distribution structure of two planes joined by vias (Sec. V-D), and batches of
+meander traces of uneven sizes (the interconnects of a circuit, Sec. V-C).  All sizes are
 in metres, conductivities in S/m, frequencies in Hz.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .meshes import box_mesh, wire_array_mesh, merge, plane_pair_mesh
+from .meshes import box_mesh, wire_array_mesh, merge, plane_pair_mesh, meander_mesh
 
 UM = 1e-6
 
@@ -45,6 +46,47 @@ def pdn_500k():
     return dict(mesh=m, freqs=np.logspace(6, 9, 8), grid=(256, 256, 32), name="pdn_2x10mm_500k")
 
 
+def grid_for(mesh, cell, lo=4, hi=128):
+    """pFFT grid per geometry: per axis the power of two nearest above
+    extent / cell, clamped to [lo, hi] (the grid spacing follows the panel
+    size until the axis cap)."""
+    ext = mesh.xyz.max(axis=0) - mesh.xyz.min(axis=0)
+    out = []
+    for e in ext:
+        n = lo
+        while n < hi and (n - 1) * cell < e:
+            n *= 2
+        out.append(n)
+    return tuple(out)
+
+
+def meander(k, n_tri=None):
+    """Meander trace k of the batched workload (seed k): segments U{3..12},
+    width U(10, 50) um, thickness U(5, 20) um, triangle count log-uniform in
+    [5k, 60k] (or about n_tri), 2 cells across the width; one port between
+    the free end faces."""
+    rng = np.random.default_rng(1000 + k)
+    n_seg = int(rng.integers(3, 13))
+    w = rng.uniform(10, 50) * UM
+    t = rng.uniform(5, 20) * UM
+    target = float(np.exp(rng.uniform(np.log(5e3), np.log(6e4)))) if n_tri is None else float(n_tri)
+    nr = max(2, (n_seg + 1) // 2)
+    # cells across the width such that the runs are about 25 widths long
+    kw = int(np.clip(round(np.sqrt(target / (100.0 * nr))), 2, 16))
+    c = w / kw
+    nz = max(1, int(round(t / c)))
+    # per cell of run length: 4 triangles per cell across (top and bottom) and 2 per wall layer on each side
+    per_cell_x = 4 * kw * nr + 4 * nr * nz
+    run = max(3 * kw, target / per_cell_x) * c
+    m = meander_mesh(n_seg, w, t, run, kw=kw, jitter=0.1, seed=k, sigma=5.8e7, name="meander_%d" % k)
+    return dict(mesh=m, grid=grid_for(m, c, hi=256), freqs=np.logspace(7, np.log10(5e9), 32), name=m.name)
+
+
+def meanders_32(n=32, n_tri=None):
+    """The batched uneven workload: meanders 0..n-1 (about 1M triangles for 32)."""
+    return [meander(k, n_tri) for k in range(n)]
+
+
 def tiny_pdn(seed=12):
     """Small plane pair (0.6 x 0.6 mm, 25 um cells, 2 via pairs of one-cell vias,
     2 ports, ~4.8k triangles) for oracle checks of the same structure."""
@@ -76,6 +118,7 @@ WORKLOADS = {
     "bar_1000x20x10um_1.5k": bar_1500,
     "bondwires_8x2mm_40k": bondwires_40k,
     "pdn_2x10mm_500k": pdn_500k,
+    "meanders_32x_5k-60k": meanders_32,
 }
 
 
