@@ -639,6 +639,9 @@ template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t s
     else return R % 2 == 0 ? Blocks<float, 2, 2>::tri_gather(p, R, st) : Blocks<float, 1, 4>::tri_gather(p, R, st);
 }
 
+// Smallest right-hand-side count for the tensor-core near field (mixed form).
+constexpr int32_t kNearMmaMinRhs = 96;
+
 template <typename T>
 int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, cudaStream_t st) {
     Scratch &s = p->scr;
@@ -673,9 +676,12 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
         k_regroup<T><<<grid, 256, 0, st>>>((const C<T> *)s.grid, p->d_tiles, p->Ng, B, (C<T> *)s.phiT);
         SIE_LAUNCH_CHECK(p);
     }
-    // mixed form, R even: near blocks on the tensor cores (their operand rows are
-    // 16-byte aligned only for even R); otherwise one CUDA-core gather
-    if (sizeof(T) == 4 && R % 2 == 0) {
+    // mixed form, R even and at least kNearMmaMinRhs: near blocks on the tensor
+    // cores (their operand rows are 16-byte aligned only for even R; a 128-column
+    // slab costs the same however few of its columns are used, so below about
+    // three quarters of a slab the CUDA-core gather is faster); otherwise one
+    // CUDA-core gather
+    if (sizeof(T) == 4 && R % 2 == 0 && R >= kNearMmaMinRhs) {
         rc = run_far_gather(p, R, st);          // interpolation (step 3) on the CUDA cores
         if (rc) return rc;
         tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));

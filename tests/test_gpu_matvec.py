@@ -144,10 +144,12 @@ def test_loop_matvec_mixed(wires):
 @pytest.mark.parametrize("nrhs,prec,tol", [(20, PREC_FP64, 1e-10), (20, PREC_MIXED, 1e-5),
                                            (130, PREC_MIXED, 1e-5), (2, PREC_MIXED, 1e-5),
                                            (1, PREC_MIXED, 1e-5), (7, PREC_MIXED, 1e-5),
+                                           (96, PREC_MIXED, 1e-5), (100, PREC_MIXED, 1e-5),
                                            (129, PREC_MIXED, 1e-5), (129, PREC_FP64, 1e-10)])
 def test_loop_matvec_batched(wires, nrhs, prec, tol):
-    """Ragged lane tails (20, 7), more than one 128-wide slab (130, 129); in the mixed
-    form even counts take the tensor-core near field and odd counts the CUDA-core gather."""
+    """Ragged lane tails (20, 7), one ragged 128-wide slab (96, 100), more than one slab
+    (130, 129); in the mixed form even counts from 96 up take the tensor-core near
+    field, the others the CUDA-core gather."""
     m, O, S, P = wires
     x = synth.complex_gaussian(O.nl, nrhs, seed=100 + nrhs)
     om = 2 * np.pi * np.logspace(7, 10, nrhs)
