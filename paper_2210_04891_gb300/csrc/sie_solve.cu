@@ -36,6 +36,9 @@ namespace sie {
 int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega, int space, int prec,
                  cudaStream_t st);
 
+// Bands from 32 to kWideMax - 1 wide use the CTA-wide sweeps (one thread per window row).
+constexpr int32_t kWideMax = 1024;
+
 struct PrecondState {
     // symbolic (host-built once)
     int64_t nunk = 0;                 // unknowns (permuted, concatenated by block)
@@ -64,6 +67,8 @@ struct PrecondState {
     double2 *d_tile64 = nullptr, *d_dinv64 = nullptr;
     float2 *d_tile32 = nullptr, *d_dinv32 = nullptr;
     float2 *d_u32 = nullptr;          // FP32 sweep buffer [R][nunk]
+    // bands wider than a warp (31 < W < 1024): FP32 roundings of band and bandc (mixed form)
+    float2 *d_band32 = nullptr, *d_bandc32 = nullptr;
     double2 *d_a = nullptr;           // [nslots][nb] 1/D_e
     float2 *d_a32 = nullptr;          // its FP32 rounding (mixed form)
     double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
@@ -85,7 +90,8 @@ void plan_free_precond(pfft_plan *p) {
     if (!p || !p->pc) return;
     for (void *a : p->pc->allocs) cudaFree(a);
     for (void *a : {(void *)p->pc->d_tile64, (void *)p->pc->d_dinv64, (void *)p->pc->d_tile32,
-                    (void *)p->pc->d_dinv32, (void *)p->pc->d_u32, (void *)p->pc->d_a32})
+                    (void *)p->pc->d_dinv32, (void *)p->pc->d_u32, (void *)p->pc->d_a32,
+                    (void *)p->pc->d_band32, (void *)p->pc->d_bandc32})
         if (a) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
                     (void *)p->pc->d_ibr, (void *)p->pc->d_slot})
@@ -353,6 +359,9 @@ __global__ void __launch_bounds__(256) k_pc_factor(const int64_t *__restrict__ b
         B[i * Wp] = d;
     }
     __syncthreads();
+    // pivot column staged per step: kc[r] = K[k+r][k], lc[r] = K[k+r][k] / d_k (r = 1..W)
+    __shared__ double2 kc[kWideMax], lc[kWideMax];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 tile over (row, column)
     for (int64_t k = 0; k < n; ++k) {
         const double2 dk = B[k * Wp];
         if (dk.x == 0.0 && dk.y == 0.0) {
@@ -361,26 +370,32 @@ __global__ void __launch_bounds__(256) k_pc_factor(const int64_t *__restrict__ b
         }
         const double den = dk.x * dk.x + dk.y * dk.y;
         const double2 inv = make_double2(dk.x / den, -dk.y / den);
-        const int64_t m = (int64_t(W) < n - 1 - k) ? int64_t(W) : n - 1 - k;
-        // rows i = k + r (r = 1..m): update K[i][j] for j in (k, i] by l_ik d_k l_jk
-        const int64_t tri = m * (m + 1) / 2;
-        for (int64_t t = threadIdx.x; t < tri; t += blockDim.x) {
-            // t -> (r, c) with 1 <= c <= r <= m
-            int64_t r = int64_t((sqrt(8.0 * double(t) + 1.0) - 1.0) / 2.0);
-            while (r * (r + 1) / 2 > t) --r;
-            while ((r + 1) * (r + 2) / 2 <= t) ++r;
-            int64_t c = t - r * (r + 1) / 2;   // 0..r
-            r += 1;
-            c += 1;
-            const double2 kik = B[(k + r) * Wp + r];     // K[k+r][k]
-            const double2 kjk = B[(k + c) * Wp + c];     // K[k+c][k]
-            double2 upd = cmul(cmul(kik, inv), kjk);
-            double2 &dst = B[(k + r) * Wp + (r - c)];
-            dst = csub(dst, upd);
+        const int m = int((int64_t(W) < n - 1 - k) ? int64_t(W) : n - 1 - k);
+        // rows i = k + r (r = 1..m): K[i][k+c] -= l_ik d_k l_(k+c)k for c in 1..r; the
+        // pivot column (offset r of row k + r) is never written by the update itself
+        if (W < kWideMax) {
+            for (int r = 1 + threadIdx.x; r <= m; r += blockDim.x) {
+                const double2 v = B[(k + r) * Wp + r];
+                kc[r] = v;
+                lc[r] = cmul(v, inv);
+            }
+            __syncthreads();
+            for (int r = 1 + ty; r <= m; r += 16) {
+                const double2 lr = lc[r];
+                double2 *row = B + (k + r) * Wp + r;       // row[-c] = K[k+r][k+c]
+                for (int c = 1 + tx; c <= r; c += 16) row[-c] = csub(row[-c], cmul(lr, kc[c]));
+            }
+            for (int r = 1 + threadIdx.x; r <= m; r += blockDim.x) B[(k + r) * Wp + r] = lc[r];   // l_{k+r,k}
+        } else {   // bands too wide to stage the column: read it where it is
+            for (int r = 1 + ty; r <= m; r += 16) {
+                const double2 lr = cmul(B[(k + r) * Wp + r], inv);
+                double2 *row = B + (k + r) * Wp + r;
+                for (int c = 1 + tx; c <= r; c += 16) row[-c] = csub(row[-c], cmul(lr, B[(k + c) * Wp + c]));
+            }
+            __syncthreads();
+            for (int r = 1 + threadIdx.x; r <= m; r += blockDim.x)
+                B[(k + r) * Wp + r] = cmul(B[(k + r) * Wp + r], inv);
         }
-        __syncthreads();
-        for (int64_t r = 1 + threadIdx.x; r <= m; r += blockDim.x)
-            B[(k + r) * Wp + r] = cmul(B[(k + r) * Wp + r], inv);   // l_{k+r,k}
         __syncthreads();
     }
     // column-major copy for the forward sweep: Bc[i][d] = L[i+d][i], Bc[i][0] = d_i
@@ -472,6 +487,132 @@ __global__ void k_pc_solve(const double2 *__restrict__ kappa, const int32_t *__r
         }
         if (lane == 0) x[i] = csub(x[i], acc);
         __syncwarp();
+    }
+}
+
+// Band solve L d L^T u = rhs for bands wider than a warp (31 < W < 1024), one
+// CTA of Wt >= W + 1 threads per (right-hand side, block), after assembling
+// rhs_i = -sum over the incident branches of s * kappa_e.  Right-looking
+// sweeps: thread j holds the running value of the one row of the window (the Wt
+// rows from the current pivot on) that is congruent to j; at each step the
+// pivot's owner finishes it and publishes it through shared memory (two
+// alternating slots, one barrier per step), every thread subtracts its band
+// entry times the pivot (the column-major copy gives L[k+d][k] in the forward
+// sweep, the row-major band L[k][k-d] in the backward sweep; each entry is
+// loaded one step ahead) and the owner takes over the row Wt further on, whose
+// first update comes from a later pivot since Wt > W.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_pc_sweep_wide(
+    const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
+    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
+    int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
+    C<T> *__restrict__ u) {
+    __shared__ C<T> piv[2];
+    const int64_t r = blockIdx.x / nblk, b = blockIdx.x % nblk;
+    const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
+    const int Wp = W + 1, Wt = blockDim.x, j = threadIdx.x;
+    const C<T> *B = band + (int64_t(slot[r]) * nunk + o) * Wp;
+    const C<T> *Bc = bandc + (int64_t(slot[r]) * nunk + o) * Wp;
+    C<T> *x = u + r * nunk + o;
+    const C<T> *kr = kappa + r * nb;
+    const C<T> zero = mk<T>(T(0), T(0));
+    for (int64_t i = j; i < n; i += Wt) {
+        C<T> acc = zero;
+        for (int32_t k = row_ptr[o + i]; k < row_ptr[o + i + 1]; ++k)
+            acc = row_sg[k] > 0 ? csub(acc, kr[row_br[k]]) : cadd(acc, kr[row_br[k]]);
+        x[i] = acc;
+    }
+    __syncthreads();
+    // Step k's pivot belongs to thread own = k mod Wt (a running counter); a thread's
+    // row sits d = (j - own) mod Wt rows after the pivot.  A thread loads the
+    // right-hand side of the row it takes next one ownership period (Wt steps)
+    // ahead, and its band entries kAhead steps ahead, so no step waits on memory.
+    // Loads always read a valid address (clamped) and carry a flag that is applied
+    // where the value is used: a conditional load would make the select wait for it.
+    constexpr int kAhead = sizeof(T) == 8 ? 4 : 8;
+    auto dist_of = [&](int o) { const int d = j - o; return d < 0 ? d + Wt : d; };
+    // forward sweep (unit lower L, column entries bandc[k][d] = L[k+d][k])
+    C<T> pend = x[j < n ? j : 0];
+    if (j >= n) pend = zero;
+    bool nxt_ok = j + Wt < n;
+    C<T> nxt = x[nxt_ok ? j + Wt : 0];
+    C<T> ring[kAhead];
+    bool rok[kAhead];
+#pragma unroll
+    for (int q = 0; q < kAhead; ++q) {
+        const int d = dist_of(q);
+        rok[q] = q < n && d >= 1 && d <= W && q + d < n;
+        ring[q] = Bc[rok[q] ? int64_t(q) * Wp + d : 0];
+    }
+    int own = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += kAhead) {
+#pragma unroll
+        for (int q = 0; q < kAhead; ++q) {
+            const int64_t k = k0 + q;
+            if (k < n) {
+                if (j == own) {
+                    x[k] = pend;
+                    piv[k & 1] = pend;
+                    pend = nxt_ok ? nxt : zero;
+                    nxt_ok = k + 2 * Wt < n;
+                    nxt = x[nxt_ok ? k + 2 * Wt : k];
+                }
+                __syncthreads();
+                if (rok[q]) pend = csub(pend, cmul(ring[q], piv[k & 1]));
+            }
+            int o2 = own + kAhead;
+            if (o2 >= Wt) o2 -= Wt;
+            const int d2 = dist_of(o2);
+            const int64_t k2 = k + kAhead;
+            rok[q] = k2 < n && d2 >= 1 && d2 <= W && k2 + d2 < n;
+            ring[q] = Bc[rok[q] ? k2 * Wp + d2 : 0];
+            own = own + 1 == Wt ? 0 : own + 1;
+        }
+    }
+    __syncthreads();
+    for (int64_t i = j; i < n; i += Wt) {   // diagonal: x_i /= d_i
+        const C<T> dg = B[i * Wp];
+        const T den = dg.x * dg.x + dg.y * dg.y;
+        x[i] = cmul(x[i], mk<T>(dg.x / den, -dg.y / den));
+    }
+    __syncthreads();
+    // backward sweep (L^T): step s finishes row k = n - 1 - s; row entries band[k][d] = L[k][k-d]
+    pend = x[j < n ? n - 1 - j : 0];
+    if (j >= n) pend = zero;
+    nxt_ok = j + Wt < n;
+    nxt = x[nxt_ok ? n - 1 - j - Wt : 0];
+#pragma unroll
+    for (int q = 0; q < kAhead; ++q) {
+        const int d = dist_of(q);
+        const int64_t k = n - 1 - q;
+        rok[q] = q < n && d >= 1 && d <= W && k - d >= 0;
+        ring[q] = B[rok[q] ? k * Wp + d : 0];
+    }
+    own = 0;
+    for (int64_t s0 = 0; s0 < n; s0 += kAhead) {
+#pragma unroll
+        for (int q = 0; q < kAhead; ++q) {
+            const int64_t st = s0 + q;
+            if (st < n) {
+                const int64_t k = n - 1 - st;
+                if (j == own) {
+                    x[k] = pend;
+                    piv[st & 1] = pend;
+                    pend = nxt_ok ? nxt : zero;
+                    nxt_ok = st + 2 * Wt < n;
+                    nxt = x[nxt_ok ? k - 2 * Wt : k];
+                }
+                __syncthreads();
+                if (rok[q]) pend = csub(pend, cmul(ring[q], piv[st & 1]));
+            }
+            int o2 = own + kAhead;
+            if (o2 >= Wt) o2 -= Wt;
+            const int d2 = dist_of(o2);
+            const int64_t s2 = st + kAhead, k2 = n - 1 - s2;
+            rok[q] = s2 < n && d2 >= 1 && d2 <= W && k2 - d2 >= 0;
+            ring[q] = B[rok[q] ? k2 * Wp + d2 : 0];
+            own = own + 1 == Wt ? 0 : own + 1;
+        }
     }
 }
 
@@ -769,6 +910,9 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     s->d_tile32 = s->d_dinv32 = nullptr;
     if (s->d_a) cudaFree(s->d_a);
     if (s->d_a32) cudaFree(s->d_a32);
+    if (s->d_band32) cudaFree(s->d_band32);
+    if (s->d_bandc32) cudaFree(s->d_bandc32);
+    s->d_band32 = s->d_bandc32 = nullptr;
     s->d_band = nullptr;
     s->d_bandc = nullptr;
     s->d_a = nullptr;
@@ -777,6 +921,12 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     SIE_CUDA(cudaMalloc((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
     SIE_CUDA(cudaMalloc((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
     const bool tiled = s->W <= 31 && s->nunk > 0;
+    const bool wide = s->W > 31 && s->W < kWideMax && s->nunk > 0;
+    const int64_t nband = int64_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1);
+    if (wide) {
+        SIE_CUDA(cudaMalloc((void **)&s->d_band32, size_t(nband) * sizeof(float2)));
+        SIE_CUDA(cudaMalloc((void **)&s->d_bandc32, size_t(nband) * sizeof(float2)));
+    }
     const int64_t ntile = int64_t(ns) * 2 * s->nchunks * PC_TILE;
     if (tiled) {
         SIE_CUDA(cudaMalloc((void **)&s->d_tile64, size_t(ntile) * sizeof(double2)));
@@ -825,6 +975,12 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
             k_pc_dinv<float><<<nblk_(nd), 256, 0, st>>>(s->d_band, nd, s->W + 1, s->d_dinv32);
             SIE_LAUNCH_CHECK(p);
         }
+        if (wide) {
+            k_round_c<<<nblk_(nband), 256, 0, st>>>(s->d_band, s->d_band32, nband);
+            SIE_LAUNCH_CHECK(p);
+            k_round_c<<<nblk_(nband), 256, 0, st>>>(s->d_bandc, s->d_bandc32, nband);
+            SIE_LAUNCH_CHECK(p);
+        }
     }
     int status = 0;
     SIE_CUDA(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -863,8 +1019,15 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
             k_pc_sweep<T><<<nblk_(int64_t(R) * nblk * 32, 128), 128, sm, st>>>(
                 kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, s->d_tile_off, nblk, s->nunk, s->nchunks,
                 p->nb, tiles, dinv, s->d_slot, R, u);
+        } else if (s->W < kWideMax) {
+            const int wt = (s->W + 1 + 31) / 32 * 32;
+            const C<T> *band, *bandc;
+            if constexpr (f32) { band = s->d_band32; bandc = s->d_bandc32; } else { band = s->d_band; bandc = s->d_bandc; }
+            k_pc_sweep_wide<T><<<unsigned(int64_t(R) * nblk), wt, 0, st>>>(
+                kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band, bandc,
+                s->d_slot, u);
         } else {
-            if constexpr (f32) return fail(SIE_ERR_ARG, "preconditioner: FP32 sweeps need a band width <= 31");
+            if constexpr (f32) return fail(SIE_ERR_ARG, "preconditioner: FP32 sweeps need a band width below 1024");
             else
                 k_pc_solve<<<nblk_(int64_t(R) * nblk * 32, 128), 128, 0, st>>>(
                     kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb,
@@ -883,7 +1046,7 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
 
 int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int prec, cudaStream_t st) {
     StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
-    if (prec == SIE_PREC_MIXED && p->pc->W <= 31) return pc_apply_t<float>(p, y, z, R, st);
+    if (prec == SIE_PREC_MIXED && p->pc->W < kWideMax) return pc_apply_t<float>(p, y, z, R, st);
     return pc_apply_t<double>(p, y, z, R, st);
 }
 
