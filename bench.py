@@ -11,7 +11,7 @@ grid, FFT, near field and preconditioner; double-float loop maps), i.e. 128 pFFT
 matvecs.  `value` = matvecs per second over all ranks.  Beside it: the plain
 FP64 form, GMRES time to a 1e-6 preconditioned residual (plain and mixed), the
 roofline of the dominant stage (device time from CUDA events recorded on the
-launching stream during the timed region), an end-to-end number through host
+launching stream in a second timed run of the same step with stage timing on), an end-to-end number through host
 buffers, clocks sampled during the timed region and the CPU oracle baseline.
 
 --impl reference times the plain FP64 CPU oracle on a bounded sample of the
@@ -426,8 +426,12 @@ def main():
     step(PREC_MIXED)
     torch.cuda.synchronize()
     sampler.start()
-    t_mixed, launches, prof = timed(PREC_MIXED, K, W, profile=True)
+    t_mixed, launches, _ = timed(PREC_MIXED, K, W)
     clocks = sampler.stop()
+    # stage split: a separate run with stage timing, so that the events it records stay
+    # out of the headline's timed region
+    Kp = max(3, K // 3)
+    _, _, prof = timed(PREC_MIXED, Kp, 2, profile=True)
     value, tmax = aggregate(t_mixed, R * K, dist)
     # plain FP64 form
     t_plain, _, _ = timed(PREC_FP64, max(3, K // 3), 2)
@@ -442,7 +446,7 @@ def main():
                n_near=info["n_near_pairs"], n_pair=int(pnode.size), n_active=int(np.unique(pnode).size))
     dom = max((s for s in prof if prof[s][1] > 0), key=lambda s: prof[s][0])
     ms_dom, n_dom = prof[dom]
-    stage_table = {s: {"ms_per_step": v[0] / K, "launch_groups": v[1]} for s, v in prof.items() if v[1]}
+    stage_table = {s: {"ms_per_step": v[0] / Kp, "launch_groups": v[1]} for s, v in prof.items() if v[1]}
     roofline = None
     work = stage_work(dom, ctx)
     if work:
@@ -464,11 +468,12 @@ def main():
             traffic = tb * (3 * R) / grids
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": u, "frac": achieved / peak,
                     "traffic": traffic, "kernel": dom, "peak_source": psrc,
-                    "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": ms_dom / n_dom}
+                    "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": ms_dom / n_dom,
+                    "timed_in": "stage-timed run of the same step (%d steps)" % Kp}
         for s in stage_table:
             wk = stage_work(s, ctx)
             if wk:
-                sec = stage_table[s]["ms_per_step"] * K / stage_table[s]["launch_groups"] / 1e3
+                sec = stage_table[s]["ms_per_step"] * Kp / stage_table[s]["launch_groups"] / 1e3
                 stage_table[s]["bound"] = wk[0]
                 stage_table[s]["achieved"] = wk[1] / sec / (1e9 if wk[0] == "hbm" else 1e12)
                 stage_table[s]["achieved_unit"] = "GB/s" if wk[0] == "hbm" else "TFLOP/s"
