@@ -888,54 +888,54 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     for (int32_t r = 0; r < R; ++r) slot[r] = int32_t(std::lower_bound(uniq.begin(), uniq.end(), omega[r]) - uniq.begin());
     if (R > s->cap_rhs) {
         for (void *a : {(void *)s->d_kappa, (void *)s->d_u, (void *)s->d_ibr, (void *)s->d_slot})
-            if (a) cudaFree(a);
+            if (a) cudaFreeAsync(a, st);
         s->d_kappa = s->d_u = s->d_ibr = nullptr;
         s->d_slot = nullptr;
-        SIE_CUDA(cudaMalloc((void **)&s->d_kappa, size_t(R) * p->nb * sizeof(double2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_ibr, size_t(R) * p->nb * sizeof(double2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_u, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(double2)));
-        if (s->d_u32) cudaFree(s->d_u32);
-        SIE_CUDA(cudaMalloc((void **)&s->d_u32, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(float2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_slot, size_t(R) * sizeof(int32_t)));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_kappa, size_t(R) * p->nb * sizeof(double2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_ibr, size_t(R) * p->nb * sizeof(double2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_u, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(double2), st));
+        if (s->d_u32) cudaFreeAsync(s->d_u32, st);
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_u32, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(float2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_slot, size_t(R) * sizeof(int32_t), st));
         s->cap_rhs = R;
     }
     SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     if (uniq == s->slot_omega) return SIE_OK;   // factors cached
     const int32_t ns = int32_t(uniq.size());
-    if (s->d_band) cudaFree(s->d_band);
-    if (s->d_bandc) cudaFree(s->d_bandc);
+    if (s->d_band) cudaFreeAsync(s->d_band, st);
+    if (s->d_bandc) cudaFreeAsync(s->d_bandc, st);
     for (void *q : {(void *)s->d_tile64, (void *)s->d_dinv64, (void *)s->d_tile32, (void *)s->d_dinv32})
-        if (q) cudaFree(q);
+        if (q) cudaFreeAsync(q, st);
     s->d_tile64 = s->d_dinv64 = nullptr;
     s->d_tile32 = s->d_dinv32 = nullptr;
-    if (s->d_a) cudaFree(s->d_a);
-    if (s->d_a32) cudaFree(s->d_a32);
-    if (s->d_band32) cudaFree(s->d_band32);
-    if (s->d_bandc32) cudaFree(s->d_bandc32);
+    if (s->d_a) cudaFreeAsync(s->d_a, st);
+    if (s->d_a32) cudaFreeAsync(s->d_a32, st);
+    if (s->d_band32) cudaFreeAsync(s->d_band32, st);
+    if (s->d_bandc32) cudaFreeAsync(s->d_bandc32, st);
     s->d_band32 = s->d_bandc32 = nullptr;
     s->d_band = nullptr;
     s->d_bandc = nullptr;
     s->d_a = nullptr;
     s->d_a32 = nullptr;
     s->slot_omega.clear();
-    SIE_CUDA(cudaMalloc((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
-    SIE_CUDA(cudaMalloc((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2)));
+    SIE_CUDA(cudaMallocAsync((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
+    SIE_CUDA(cudaMallocAsync((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
     const bool tiled = s->W <= 31 && s->nunk > 0;
     const bool wide = s->W > 31 && s->W < kWideMax && s->nunk > 0;
     const int64_t nband = int64_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1);
     if (wide) {
-        SIE_CUDA(cudaMalloc((void **)&s->d_band32, size_t(nband) * sizeof(float2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_bandc32, size_t(nband) * sizeof(float2)));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_band32, size_t(nband) * sizeof(float2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_bandc32, size_t(nband) * sizeof(float2), st));
     }
     const int64_t ntile = int64_t(ns) * 2 * s->nchunks * PC_TILE;
     if (tiled) {
-        SIE_CUDA(cudaMalloc((void **)&s->d_tile64, size_t(ntile) * sizeof(double2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_tile32, size_t(ntile) * sizeof(float2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_dinv64, size_t(ns) * s->nunk * sizeof(double2)));
-        SIE_CUDA(cudaMalloc((void **)&s->d_dinv32, size_t(ns) * s->nunk * sizeof(float2)));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_tile64, size_t(ntile) * sizeof(double2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_tile32, size_t(ntile) * sizeof(float2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_dinv64, size_t(ns) * s->nunk * sizeof(double2), st));
+        SIE_CUDA(cudaMallocAsync((void **)&s->d_dinv32, size_t(ns) * s->nunk * sizeof(float2), st));
     }
-    SIE_CUDA(cudaMalloc((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2)));
-    SIE_CUDA(cudaMalloc((void **)&s->d_a32, size_t(ns) * p->nb * sizeof(float2)));
+    SIE_CUDA(cudaMallocAsync((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2), st));
+    SIE_CUDA(cudaMallocAsync((void **)&s->d_a32, size_t(ns) * p->nb * sizeof(float2), st));
     const int zw = 2 * p->ncond + 1;
     std::vector<double> zc(size_t(ns) * zw);
     for (int32_t f = 0; f < ns; ++f) {
@@ -947,7 +947,7 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         zc[f * zw + 2 * p->ncond] = uniq[f] * kMu0 / (4.0 * M_PI);
     }
     double *d_zc = nullptr;
-    SIE_CUDA(cudaMalloc((void **)&d_zc, zc.size() * sizeof(double)));
+    SIE_CUDA(cudaMallocAsync((void **)&d_zc, zc.size() * sizeof(double), st));
     SIE_CUDA(cudaMemcpyAsync(d_zc, zc.data(), zc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zc, p->ncond,
                                                        p->nb, ns, s->d_a);
@@ -984,8 +984,8 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     }
     int status = 0;
     SIE_CUDA(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    cudaFreeAsync(d_zc, st);
     SIE_CUDA(cudaStreamSynchronize(st));
-    cudaFree(d_zc);
     if (status) return fail(SIE_ERR_BREAKDOWN, "preconditioner: zero pivot in the band LDL^T");
     s->slot_omega = uniq;
     s->nslots = ns;
@@ -1172,22 +1172,24 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     double2 *V = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *t = nullptr, *dh = nullptr;
     int32_t *act = nullptr, *dk = nullptr;
     double *scl = nullptr;
+    // stream-ordered workspace: a device-wide cudaFree would wait for every other
+    // plan's work (solves of several plans run concurrently in a batch)
     auto cleanup = [&]() {
         for (void *a : {(void *)V, (void *)w, (void *)b, (void *)x, (void *)t, (void *)dh, (void *)act, (void *)dk,
                         (void *)scl})
-            if (a) cudaFree(a);
+            if (a) cudaFreeAsync(a, st);
     };
 #define GM_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); set_error(std::string(#call) + ": " + cudaGetErrorString(_e)); return _e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA; } } while (0)
 #define GM_RC(expr) do { int _r = (expr); if (_r) { cleanup(); return _r; } } while (0)
-    GM_CUDA(cudaMalloc((void **)&V, size_t(m + 1) * kstride * sizeof(double2)));
-    GM_CUDA(cudaMalloc((void **)&w, size_t(R) * n * sizeof(double2)));
-    GM_CUDA(cudaMalloc((void **)&b, size_t(R) * n * sizeof(double2)));
-    GM_CUDA(cudaMalloc((void **)&x, size_t(R) * n * sizeof(double2)));
-    GM_CUDA(cudaMalloc((void **)&t, size_t(R) * n * sizeof(double2)));
-    GM_CUDA(cudaMalloc((void **)&dh, size_t(R) * (m + 2) * sizeof(double2)));
-    GM_CUDA(cudaMalloc((void **)&act, size_t(R) * sizeof(int32_t)));
-    GM_CUDA(cudaMalloc((void **)&dk, size_t(R) * sizeof(int32_t)));
-    GM_CUDA(cudaMalloc((void **)&scl, size_t(R) * sizeof(double)));
+    GM_CUDA(cudaMallocAsync((void **)&V, size_t(m + 1) * kstride * sizeof(double2), st));
+    GM_CUDA(cudaMallocAsync((void **)&w, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(cudaMallocAsync((void **)&b, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(cudaMallocAsync((void **)&x, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(cudaMallocAsync((void **)&t, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(cudaMallocAsync((void **)&dh, size_t(R) * (m + 2) * sizeof(double2), st));
+    GM_CUDA(cudaMallocAsync((void **)&act, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(cudaMallocAsync((void **)&dk, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(cudaMallocAsync((void **)&scl, size_t(R) * sizeof(double), st));
     GM_CUDA(cudaMemsetAsync(V, 0, size_t(m + 1) * kstride * sizeof(double2), st));
     GM_CUDA(cudaMemsetAsync(b, 0, size_t(R) * n * sizeof(double2), st));
     GM_CUDA(cudaMemsetAsync(x, 0, size_t(R) * n * sizeof(double2), st));
