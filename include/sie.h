@@ -202,6 +202,14 @@ int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double
 int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
                        int32_t prec, void *cuda_stream);
 
+/* Structure of the preconditioner (built on first use, or by this call): band
+ * width W of its banded LDL^T after the reverse Cuthill-McKee ordering (max
+ * over blocks), unknowns, and blocks (one per connected group of unknowns).
+ * The sweeps take warp-register tiles for W <= 31, one CTA per (right-hand
+ * side, block) for 31 < W < 1024 (FP32 in the mixed form), and a one-warp FP64
+ * sweep beyond.  Any pointer may be NULL. */
+int pfft_precond_info(pfft_plan *p, int32_t *band_width, int64_t *unknowns, int64_t *blocks);
+
 /* Port impedance extraction (Sec. III-C, V): for every frequency f and every
  * port q a unit source in port q's loop, GMRES on Eq. (LoopWithP), then
  * Y[f][p][q] = loop current of port p, Z(f) = Y(f)^-1.  ports[np] selects the

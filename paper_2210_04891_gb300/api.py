@@ -230,6 +230,13 @@ def _check_vec(x, n, name):
         raise ValueError(f"{name} must be contiguous [nrhs, {n}]")
 
 
+def precond_info(plan: Plan):
+    """Band width, unknowns and blocks of the preconditioner's banded LDL^T."""
+    w, u, b = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().pfft_precond_info(plan.h, ctypes.byref(w), ctypes.byref(u), ctypes.byref(b)))
+    return dict(band_width=w.value, unknowns=u.value, blocks=b.value)
+
+
 def pfft_matvec(plan: Plan, x, omega, space=N.SPACE_LOOP, prec=N.PREC_FP64, out=None, stream=None):
     """y = A Z_b(omega) A^T x (space=LOOP) or Z_b(omega) x (space=BRANCH), x [nrhs, n]."""
     import torch

@@ -501,8 +501,8 @@ __global__ void k_pc_solve(const double2 *__restrict__ kappa, const int32_t *__r
 // sweep, the row-major band L[k][k-d] in the backward sweep; each entry is
 // loaded one step ahead) and the owner takes over the row Wt further on, whose
 // first update comes from a later pivot since Wt > W.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_pc_sweep_wide(
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_pc_sweep_wide(
     const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
     const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
     int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
@@ -1023,9 +1023,15 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
             const int wt = (s->W + 1 + 31) / 32 * 32;
             const C<T> *band, *bandc;
             if constexpr (f32) { band = s->d_band32; bandc = s->d_bandc32; } else { band = s->d_band; bandc = s->d_bandc; }
-            k_pc_sweep_wide<T><<<unsigned(int64_t(R) * nblk), wt, 0, st>>>(
-                kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band, bandc,
-                s->d_slot, u);
+            // up to 256 threads: registers for the look-ahead ring without spilling to the cap of 1024
+            if (wt <= 256)
+                k_pc_sweep_wide<T, 256><<<unsigned(int64_t(R) * nblk), wt, 0, st>>>(
+                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band,
+                    bandc, s->d_slot, u);
+            else
+                k_pc_sweep_wide<T, 1024><<<unsigned(int64_t(R) * nblk), wt, 0, st>>>(
+                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band,
+                    bandc, s->d_slot, u);
         } else {
             if constexpr (f32) return fail(SIE_ERR_ARG, "preconditioner: FP32 sweeps need a band width below 1024");
             else
@@ -1412,6 +1418,18 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
 }
 
 // ------------------------------------------------------------------ surface model
+
+extern "C" int pfft_precond_info(pfft_plan *p, int32_t *band_width, int64_t *unknowns, int64_t *blocks) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_precond_info: NULL plan");
+    if (!p->pc) {
+        int rc = build_symbolic(p);
+        if (rc) { plan_free_precond(p); return rc; }
+    }
+    if (band_width) *band_width = p->pc->W;
+    if (unknowns) *unknowns = p->pc->nunk;
+    if (blocks) *blocks = int64_t(p->pc->blk_off.size()) - 1;
+    return SIE_OK;
+}
 
 extern "C" int pfft_plan_set_surface_model(pfft_plan *p, const double *t_eff, int32_t ncond) {
     if (!p) return fail(SIE_ERR_ARG, "pfft_plan_set_surface_model: NULL plan");
