@@ -278,6 +278,27 @@ int sie_batch_solve(sie_batch *b, const double *const *freqs, const int32_t *nf,
                     const int32_t *np, const sie_solve_opts *opts, sie_c64 *const *Z_out,
                     sie_solve_stats *st_out);
 
+/* Grid autotuning.  Candidates: the base grid, half and double it on every
+ * axis, and the base with one axis doubled (axes kept within the plan's size
+ * rules, at most SIE_TUNE_MAX).  Each is built, its FP64 loop-space product of
+ * nrhs fixed pseudo-random vectors at omega compared with that of the finest
+ * candidate built with 1.5 x base->near_factor (the reference; relative 2-norm,
+ * max over right-hand sides), and its mixed matvec timed with CUDA events on
+ * cuda_stream (5 after 2 warm-ups).  best = the fastest candidate within tol
+ * of the reference (else the reference's grid and radius); `rep` (may be NULL)
+ * gets every candidate's grid, time and error.  Builds and frees one plan at a
+ * time.  Errors: SIE_ERR_ARG, and those of pfft_plan_create / pfft_matvec. */
+#define SIE_TUNE_MAX 8
+typedef struct {
+    int32_t n_tried;
+    int32_t best;                   /* index of the chosen candidate, -1 if none was within tol */
+    int32_t grid[SIE_TUNE_MAX][3];
+    double ms[SIE_TUNE_MAX];        /* mixed matvec time, milliseconds */
+    double err[SIE_TUNE_MAX];       /* relative difference to the reference */
+} sie_tune_report;
+int pfft_autotune(const sie_mesh *m, const sie_loops *l, const pfft_params *base, int32_t nrhs, double omega,
+                  double tol, void *cuda_stream, pfft_params *best, sie_tune_report *rep);
+
 /* Plan introspection for tests and benchmarks: sizes (any pointer may be NULL). */
 int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, int64_t *n_tri,
                    int64_t *n_near_pairs, double *grid_h /* [3] */, double *r_near,

@@ -139,21 +139,43 @@ def loop_basis_build(mesh, ports):
 DEFAULT_PARAMS = dict(grid=(16, 8, 8), order=3, near_factor=4.0, near_min_diam=2.0, n_touch=16, h0=0.0)
 
 
+def _c_params(p):
+    cp = N.PfftParams()
+    for i in range(3):
+        cp.grid[i] = int(p["grid"][i])
+    cp.order = int(p["order"])
+    cp.near_factor = float(p["near_factor"])
+    cp.near_min_diam = float(p["near_min_diam"])
+    cp.n_touch = int(p["n_touch"])
+    cp.kernel = N.KERNEL_STATIC
+    cp.h0 = float(p["h0"])
+    return cp
+
+
+def autotune(mesh, loops, params, nrhs, omega, tol, stream=None):
+    """pfft_autotune: (best params dict, report dict) for the geometry."""
+    import torch
+    p = dict(DEFAULT_PARAMS)
+    p.update(params or {})
+    torch.cuda.init()
+    best = N.PfftParams()
+    rep = N.TuneReport()
+    check(lib().pfft_autotune(mesh.h, loops.h, ctypes.byref(_c_params(p)), int(nrhs), float(omega), float(tol),
+                              _stream(stream), ctypes.byref(best), ctypes.byref(rep)))
+    out = dict(p, grid=tuple(best.grid[i] for i in range(3)), near_factor=best.near_factor)
+    n = rep.n_tried
+    report = dict(best=rep.best, grids=[tuple(rep.grid[c][i] for i in range(3)) for c in range(n)],
+                  ms=[rep.ms[c] for c in range(n)], err=[rep.err[c] for c in range(n)])
+    return out, report
+
+
 class Plan:
     def __init__(self, mesh: Mesh, loops: Loops, params=None, stream=None):
         import torch
         p = dict(DEFAULT_PARAMS)
         p.update(params or {})
         self.params = p
-        cp = N.PfftParams()
-        for i in range(3):
-            cp.grid[i] = int(p["grid"][i])
-        cp.order = int(p["order"])
-        cp.near_factor = float(p["near_factor"])
-        cp.near_min_diam = float(p["near_min_diam"])
-        cp.n_touch = int(p["n_touch"])
-        cp.kernel = N.KERNEL_STATIC
-        cp.h0 = float(p["h0"])
+        cp = _c_params(p)
         torch.cuda.init()
         h = ctypes.c_void_p()
         check(lib().pfft_plan_create(mesh.h, loops.h, ctypes.byref(cp), _stream(stream), ctypes.byref(h)))

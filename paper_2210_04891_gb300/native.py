@@ -24,7 +24,7 @@ EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basi
            "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_lossy", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "pfft_plan_set_surface_model", "sie_postprocess", "sie_batch_create", "sie_batch_destroy",
-           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info", "sie_last_error"]
+           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info", "pfft_autotune", "sie_last_error"]
 STAGES = ["loop_to_branch", "point_currents", "project", "fft_x_fwd", "fft_yz", "fft_x_inv", "interp",
           "near", "branch_to_loop", "precond_apply", "precond_factor", "arnoldi"]
 (EXPORT_NEAR_PTR, EXPORT_NEAR_COL, EXPORT_LD, EXPORT_LDIRECT, EXPORT_HHAT, EXPORT_START, EXPORT_PROJ_PTR,
@@ -57,6 +57,11 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iterations_max", ctypes.c_int32), ("iterations_sum", ctypes.c_int32),
                 ("n_not_converged", ctypes.c_int32), ("residual_max", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("matvecs", ctypes.c_int64)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n_tried", ctypes.c_int32), ("best", ctypes.c_int32), ("grid", (ctypes.c_int32 * 3) * 8),
+                ("ms", ctypes.c_double * 8), ("err", ctypes.c_double * 8)]
 
 
 class SieError(RuntimeError):
@@ -100,6 +105,8 @@ def lib():
     L.sie_postprocess.argtypes = [P, P, I32, P, I32, P, P, P, P]
     L.sie_batch_create.argtypes = [P, I32, PP]
     L.pfft_precond_info.argtypes = [P, P, P, P]
+    L.pfft_autotune.argtypes = [P, P, ctypes.POINTER(PfftParams), I32, ctypes.c_double, ctypes.c_double, P,
+                                ctypes.POINTER(PfftParams), ctypes.POINTER(TuneReport)]
     L.sie_batch_destroy.argtypes = [P]
     L.sie_batch_matvec.argtypes = [P, P, P, P, P, I32, I32, I32, P]
     L.sie_batch_stats.argtypes = [P, P, P]

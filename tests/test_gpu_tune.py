@@ -1,0 +1,58 @@
+"""pfft_autotune: the chosen grid is one of the candidates, meets the accuracy
+target against the reference product, and is the fastest of those that do;
+with a target no candidate meets, the reference grid and radius come back.
+The accuracy reported for a candidate is checked independently: its FP64
+product at the tuner's grid against the reference plan's, here."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2210_04891_gb300 import api, SieError, SPACE_LOOP, PREC_FP64  # noqa: E402
+
+BASE = dict(grid=(16, 8, 8), order=3, near_factor=3.0, near_min_diam=2.0, n_touch=8, h0=0.0)
+
+
+@pytest.fixture(scope="module")
+def geometry():
+    m = synth.tiny_wires()
+    M = api.Mesh.from_synth(m)
+    return m, M, api.Loops(M, m.ports)
+
+
+def test_autotune_picks_fastest_accurate(geometry):
+    m, M, L = geometry
+    best, rep = api.autotune(M, L, BASE, nrhs=8, omega=2 * np.pi * 1e9, tol=1e-3)
+    n = len(rep["grids"])
+    assert n >= 4 and 0 <= rep["best"] < n
+    ok = [c for c in range(n) if rep["err"][c] <= 1e-3]
+    assert rep["best"] in ok
+    assert rep["ms"][rep["best"]] == min(rep["ms"][c] for c in ok)
+    assert tuple(best["grid"]) == rep["grids"][rep["best"]] and best["near_factor"] == BASE["near_factor"]
+    assert all(t > 0 for t in rep["ms"])
+    # the finest candidate (the reference's grid) is close to the reference
+    fine = max(range(n), key=lambda c: np.prod(rep["grids"][c]))
+    assert rep["err"][fine] < 1e-2
+    # independent check of one reported error: rebuild the candidate and the reference
+    c = rep["best"]
+    x = torch.from_numpy(synth.complex_gaussian(L.nl, 2, seed=3)).cuda()
+    om = 2 * np.pi * np.array([1e9, 1e9])
+    Pc = api.Plan(M, L, dict(BASE, grid=rep["grids"][c]))
+    Pr = api.Plan(M, L, dict(BASE, grid=rep["grids"][fine], near_factor=1.5 * BASE["near_factor"]))
+    yc = api.pfft_matvec(Pc, x, om, SPACE_LOOP, PREC_FP64).cpu().numpy()
+    yr = api.pfft_matvec(Pr, x, om, SPACE_LOOP, PREC_FP64).cpu().numpy()
+    e = np.linalg.norm(yc - yr, axis=1) / np.linalg.norm(yr, axis=1)
+    assert e.max() < 3 * max(rep["err"][c], 1e-12)
+
+
+def test_autotune_without_an_accurate_candidate(geometry):
+    m, M, L = geometry
+    best, rep = api.autotune(M, L, BASE, nrhs=2, omega=2 * np.pi * 1e9, tol=1e-15)
+    fine = max(range(len(rep["grids"])), key=lambda c: np.prod(rep["grids"][c]))
+    if rep["best"] < 0:
+        assert tuple(best["grid"]) == rep["grids"][fine] and best["near_factor"] == 1.5 * BASE["near_factor"]
+    with pytest.raises(SieError):
+        api.autotune(M, L, BASE, nrhs=0, omega=1.0, tol=1e-3)
