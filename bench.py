@@ -103,8 +103,8 @@ def stage_work(stage, c):
             b += 3 * R * c["n_active"] * cb + c["n_pair"] * c["rec"] + R * nt * 3 * cb
         return "hbm", b, "B"
     if stage == "near":
-        if c.get("mixed", True) and R % 2 == 0:
-            # tensor cores (split tf32): the near 3x3 blocks times complex right-hand sides
+        if c.get("mixed", True) and R % 2 == 0 and R >= 96:
+            # tensor cores (split tf32, even R from 96): the near 3x3 blocks times complex right-hand sides
             return "tensor", 36 * R * c["n_near"], "flop"
         return "alu", 36 * R * (c["n_near"] + c["n_pair"]), "flop"
     if stage == "loop_to_branch":
