@@ -294,14 +294,23 @@ def batch_main(args, ws):
     t_64, _ = run(lambda: B.matvec(xs, oms, SPACE_LOOP, PREC_FP64, graph=False, outs=outs), K64, 2)
     gm = None
     if args.gmres_freqs > 0:
-        fr = [w["freqs"][np.linspace(0, len(w["freqs"]) - 1, args.gmres_freqs).astype(int)] for w in ws]
+        # a first batched solve at other frequencies loads the solve kernels and builds each
+        # plan's symbolic preconditioner; the timed solve then factors its own frequencies
+        sel = np.linspace(0, len(ws[0]["freqs"]) - 1, args.gmres_freqs).astype(int)
+        warm = [w["freqs"][np.clip(sel + 1, 0, len(w["freqs"]) - 1)] for w in ws]
+        fr = [w["freqs"][sel] for w in ws]
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.solve(warm, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)
+        t_first = time.perf_counter() - t0
         t0 = time.perf_counter()
         res = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)
         dt = time.perf_counter() - t0
         gm = {"tol": 1e-6, "seconds": dt, "solves": int(sum(len(f) for f in fr)),
               "iterations_max": int(max(st["iterations_max"] for _, st in res)),
-              "converged": bool(all(st["converged"] for _, st in res))}
+              "converged": bool(all(st["converged"] for _, st in res)),
+              "includes": "per-frequency band factorisations of every plan",
+              "first_solve_seconds": t_first}
     line = {"metric": "pFFT matvecs/s (batched uneven geometries)", "value": R * K / t_graph, "unit": "matvec/s",
             "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": 1e3 * t_graph / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",

@@ -1058,6 +1058,10 @@ extern "C" void pfft_plan_destroy(pfft_plan *p) {
     sie::plan_free_precond(p);
     for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void *a : p->allocations) cudaFree(a);
+    if (p->pool) {
+        cudaDeviceSynchronize();   // stream-ordered frees of the solve path have completed
+        cudaMemPoolDestroy(p->pool);
+    }
     for (void *a : {p->scr.tour, p->scr.grid, p->scr.spec, p->scr.phiT, p->scr.y_tri, p->scr.y_br,
                     (void *)p->scr.coef, p->scr.cT, p->scr.ffar})
         if (a) cudaFree(a);

@@ -52,6 +52,9 @@ struct pfft_plan {
     bool large_plane = false;
     // incremented whenever the scratch buffers are reallocated (captured graphs hold their addresses)
     uint64_t scr_gen = 0;
+    // stream-ordered allocations of the solve path (GMRES workspaces, per-frequency factors):
+    // the plan's own pool, which keeps freed memory mapped until the plan is destroyed
+    cudaMemPool_t pool = nullptr;
     int64_t Ng = 0;
     double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0};
     double r_near = 0.0;

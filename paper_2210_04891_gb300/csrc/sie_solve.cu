@@ -78,6 +78,32 @@ struct PrecondState {
     std::vector<void *> allocs;
 };
 
+// The plan's memory pool (created on first use).  Stream-ordered allocations from
+// it do not synchronise the device, and with an unbounded release threshold the
+// memory a solve frees stays mapped for the next one.
+cudaError_t plan_pool(pfft_plan *p, cudaMemPool_t *out) {
+    if (!p->pool) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = p->device;
+        cudaError_t e = cudaMemPoolCreate(&p->pool, &props);
+        if (e != cudaSuccess) { p->pool = nullptr; return e; }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    *out = p->pool;
+    return cudaSuccess;
+}
+
+template <typename Ptr>
+cudaError_t pool_alloc(pfft_plan *p, Ptr **ptr, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool;
+    cudaError_t e = plan_pool(p, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync((void **)ptr, bytes, pool, st);
+}
+
 // DC (omega = 0) has a solution only when every conductor has a slab surface
 // model: the classic Z_s and c_L both vanish there.
 bool dc_defined(const pfft_plan *p) {
@@ -891,12 +917,12 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
             if (a) cudaFreeAsync(a, st);
         s->d_kappa = s->d_u = s->d_ibr = nullptr;
         s->d_slot = nullptr;
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_kappa, size_t(R) * p->nb * sizeof(double2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_ibr, size_t(R) * p->nb * sizeof(double2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_u, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_kappa, size_t(R) * p->nb * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_ibr, size_t(R) * p->nb * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_u, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(double2), st));
         if (s->d_u32) cudaFreeAsync(s->d_u32, st);
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_u32, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(float2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_slot, size_t(R) * sizeof(int32_t), st));
+        SIE_CUDA(pool_alloc(p, &s->d_u32, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(float2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_slot, size_t(R) * sizeof(int32_t), st));
         s->cap_rhs = R;
     }
     SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -918,24 +944,24 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     s->d_a = nullptr;
     s->d_a32 = nullptr;
     s->slot_omega.clear();
-    SIE_CUDA(cudaMallocAsync((void **)&s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
-    SIE_CUDA(cudaMallocAsync((void **)&s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
+    SIE_CUDA(pool_alloc(p, &s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
+    SIE_CUDA(pool_alloc(p, &s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
     const bool tiled = s->W <= 31 && s->nunk > 0;
     const bool wide = s->W > 31 && s->W < kWideMax && s->nunk > 0;
     const int64_t nband = int64_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1);
     if (wide) {
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_band32, size_t(nband) * sizeof(float2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_bandc32, size_t(nband) * sizeof(float2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_band32, size_t(nband) * sizeof(float2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_bandc32, size_t(nband) * sizeof(float2), st));
     }
     const int64_t ntile = int64_t(ns) * 2 * s->nchunks * PC_TILE;
     if (tiled) {
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_tile64, size_t(ntile) * sizeof(double2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_tile32, size_t(ntile) * sizeof(float2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_dinv64, size_t(ns) * s->nunk * sizeof(double2), st));
-        SIE_CUDA(cudaMallocAsync((void **)&s->d_dinv32, size_t(ns) * s->nunk * sizeof(float2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_tile64, size_t(ntile) * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_tile32, size_t(ntile) * sizeof(float2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_dinv64, size_t(ns) * s->nunk * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_dinv32, size_t(ns) * s->nunk * sizeof(float2), st));
     }
-    SIE_CUDA(cudaMallocAsync((void **)&s->d_a, size_t(ns) * p->nb * sizeof(double2), st));
-    SIE_CUDA(cudaMallocAsync((void **)&s->d_a32, size_t(ns) * p->nb * sizeof(float2), st));
+    SIE_CUDA(pool_alloc(p, &s->d_a, size_t(ns) * p->nb * sizeof(double2), st));
+    SIE_CUDA(pool_alloc(p, &s->d_a32, size_t(ns) * p->nb * sizeof(float2), st));
     const int zw = 2 * p->ncond + 1;
     std::vector<double> zc(size_t(ns) * zw);
     for (int32_t f = 0; f < ns; ++f) {
@@ -947,7 +973,7 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         zc[f * zw + 2 * p->ncond] = uniq[f] * kMu0 / (4.0 * M_PI);
     }
     double *d_zc = nullptr;
-    SIE_CUDA(cudaMallocAsync((void **)&d_zc, zc.size() * sizeof(double), st));
+    SIE_CUDA(pool_alloc(p, &d_zc, zc.size() * sizeof(double), st));
     SIE_CUDA(cudaMemcpyAsync(d_zc, zc.data(), zc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zc, p->ncond,
                                                        p->nb, ns, s->d_a);
@@ -1187,15 +1213,15 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
     };
 #define GM_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); set_error(std::string(#call) + ": " + cudaGetErrorString(_e)); return _e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA; } } while (0)
 #define GM_RC(expr) do { int _r = (expr); if (_r) { cleanup(); return _r; } } while (0)
-    GM_CUDA(cudaMallocAsync((void **)&V, size_t(m + 1) * kstride * sizeof(double2), st));
-    GM_CUDA(cudaMallocAsync((void **)&w, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(cudaMallocAsync((void **)&b, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(cudaMallocAsync((void **)&x, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(cudaMallocAsync((void **)&t, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(cudaMallocAsync((void **)&dh, size_t(R) * (m + 2) * sizeof(double2), st));
-    GM_CUDA(cudaMallocAsync((void **)&act, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(cudaMallocAsync((void **)&dk, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(cudaMallocAsync((void **)&scl, size_t(R) * sizeof(double), st));
+    GM_CUDA(pool_alloc(p, &V, size_t(m + 1) * kstride * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &w, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &b, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &x, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &t, size_t(R) * n * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &dh, size_t(R) * (m + 2) * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &act, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(pool_alloc(p, &dk, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(pool_alloc(p, &scl, size_t(R) * sizeof(double), st));
     GM_CUDA(cudaMemsetAsync(V, 0, size_t(m + 1) * kstride * sizeof(double2), st));
     GM_CUDA(cudaMemsetAsync(b, 0, size_t(R) * n * sizeof(double2), st));
     GM_CUDA(cudaMemsetAsync(x, 0, size_t(R) * n * sizeof(double2), st));
