@@ -625,18 +625,27 @@ template <typename T, int V, int J> struct Blocks {
     }
 };
 
-// FP64: one complex per load; FP32: two per 16-byte load when R is even (rows
-// of [.][3][R] then start on 16-byte boundaries), else one.
+// Slab shape per right-hand-side count: a warp serves one triangle (or node)
+// and 32 V J right-hand sides, V complex per load (FP32: two per 16-byte load
+// when R is even, so that rows of [.][3][R] start on 16-byte boundaries), J
+// loads per lane; the smallest slab that covers R keeps every lane busy.
+#define SIE_SLAB_DISPATCH(T, R, CALL)                                                     \
+    do {                                                                                 \
+        if constexpr (sizeof(T) == 8) {                                                   \
+            if ((R) <= 32) return Blocks<double, 1, 1>::CALL;                             \
+            return Blocks<double, 1, 2>::CALL;                                            \
+        } else {                                                                          \
+            if ((R) <= 32) return Blocks<float, 1, 1>::CALL;                              \
+            if ((R) <= 64) return (R) % 2 == 0 ? Blocks<float, 2, 1>::CALL : Blocks<float, 1, 2>::CALL; \
+            return (R) % 2 == 0 ? Blocks<float, 2, 2>::CALL : Blocks<float, 1, 4>::CALL;  \
+        }                                                                                 \
+    } while (0)
 template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) {
-    if constexpr (sizeof(T) == 8) return Blocks<double, 1, 2>::project(p, R, st);
-    else return R % 2 == 0 ? Blocks<float, 2, 2>::project(p, R, st) : Blocks<float, 1, 4>::project(p, R, st);
+    SIE_SLAB_DISPATCH(T, R, project(p, R, st));
 }
-int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
-    return R % 2 == 0 ? Blocks<float, 2, 2>::far_gather(p, R, st) : Blocks<float, 1, 4>::far_gather(p, R, st);
-}
+int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) { SIE_SLAB_DISPATCH(float, R, far_gather(p, R, st)); }
 template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
-    if constexpr (sizeof(T) == 8) return Blocks<double, 1, 2>::tri_gather(p, R, st);
-    else return R % 2 == 0 ? Blocks<float, 2, 2>::tri_gather(p, R, st) : Blocks<float, 1, 4>::tri_gather(p, R, st);
+    SIE_SLAB_DISPATCH(T, R, tri_gather(p, R, st));
 }
 
 // Smallest right-hand-side count for the tensor-core near field (mixed form).
