@@ -640,10 +640,24 @@ template <typename T, int V, int J> struct Blocks {
             return (R) % 2 == 0 ? Blocks<float, 2, 2>::CALL : Blocks<float, 1, 4>::CALL;  \
         }                                                                                 \
     } while (0)
+// The far-field gather keeps slabs at most 64 wide in FP32: its 128-wide form
+// needs 80 registers a thread, which caps residency at 3 CTAs per SM for this
+// latency-bound gather; two 64-wide slabs read each block record twice but keep
+// 4 CTAs resident (measured: 0.77 -> 0.66 ms on the bond-wire step; the
+// projection, whose block records dominate its loads, is faster 128 wide).
+#define SIE_SLAB_DISPATCH_NARROW(T, R, CALL)                                              \
+    do {                                                                                 \
+        if constexpr (sizeof(T) == 4) {                                                   \
+            if ((R) > 32) return (R) % 2 == 0 ? Blocks<float, 2, 1>::CALL : Blocks<float, 1, 2>::CALL; \
+        }                                                                                 \
+        SIE_SLAB_DISPATCH(T, R, CALL);                                                    \
+    } while (0)
 template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) {
     SIE_SLAB_DISPATCH(T, R, project(p, R, st));
 }
-int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) { SIE_SLAB_DISPATCH(float, R, far_gather(p, R, st)); }
+int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
+    SIE_SLAB_DISPATCH_NARROW(float, R, far_gather(p, R, st));
+}
 template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
     SIE_SLAB_DISPATCH(T, R, tri_gather(p, R, st));
 }
