@@ -181,8 +181,10 @@ int pfft_plan_set_surface_model(pfft_plan *p, const double *t_eff, int32_t ncond
  * with c_L = j w mu0 / (4 pi) and Z_s = (1 + j) sqrt(w mu0 / (2 sigma)) of each
  * conductor, w = omega[r] (host array, one angular frequency per right-hand
  * side).  prec = SIE_PREC_FP64 computes every step in FP64; SIE_PREC_MIXED runs
- * projection, FFT convolution, interpolation and the near field in FP32 and the
- * loop/branch maps (prefix sums, branch differences, the Z_s/c_L combination)
+ * projection, FFT convolution, interpolation and the near field in FP32 (the
+ * near field on the tensor cores for an even nrhs of at least 96, else on the
+ * CUDA cores) and the loop/branch maps (prefix sums, branch differences, the
+ * Z_s/c_L combination)
  * in double-float (FP32 pairs, about 48 significant bits); y is complex128 in
  * both.  x and y must not overlap.  Scratch is
  * plan-owned and grown on demand (SIE_ERR_OOM if that fails). */
@@ -195,8 +197,10 @@ int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double
  * through the nodal Laplacian of the same circuit, factorised (FP64) per
  * conductor on first use of each distinct omega set.  prec = SIE_PREC_FP64
  * runs every step in FP64; SIE_PREC_MIXED runs the drive, the triangular sweeps
- * on the rounded factor and the branch currents in FP32 (band width <= 31;
- * wider bands fall back to FP64).  omega[r] > 0, or 0 when every conductor has
+ * on the rounded factor and the branch currents in FP32 (band width below 1024,
+ * see pfft_precond_info; wider bands fall back to FP64).  The factor buffers and
+ * the sweeps' scratch are stream-ordered allocations on cuda_stream from a
+ * plan-owned memory pool.  omega[r] > 0, or 0 when every conductor has
  * a slab surface model (SIE_ERR_ARG otherwise).  Errors: SIE_ERR_BREAKDOWN for
  * a zero pivot. */
 int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,

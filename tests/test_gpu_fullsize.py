@@ -7,7 +7,7 @@ seconds, so the checks are properties that hold at any size:
   symmetric near blocks, I = B^T and an even kernel): u^T Z v = v^T Z u;
 * the mixed form (tensor-core near field at 128 right-hand sides) agrees with
   the FP64 form within the mixed parity bound;
-* the tensor-core near field (even count) and the CUDA-core FP32 gather (odd
+* the tensor-core near field (even count from 96) and the CUDA-core FP32 gather (odd
   count) agree on the same vectors;
 * the preconditioned solve gives a reciprocal port impedance, Z = Z^T.
 
