@@ -338,6 +338,8 @@ def main():
     ap.add_argument("--step", default="matvec+precond", choices=["matvec+precond", "matvec"],
                     help="what one step applies (matvec: the plane pair, whose band preconditioner is too wide)")
     ap.add_argument("--gmres-freqs", type=int, default=0, help="batched workloads: frequencies per geometry solved")
+    ap.add_argument("--graph", action="store_true",
+                    help="with --step matvec: replay the product as a captured CUDA graph (a batch of one plan)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -400,9 +402,15 @@ def main():
 
     if args.step == "matvec":
         z = y          # the step's result is the product itself
+    if args.graph and args.step != "matvec":
+        raise SystemExit("--graph replays the product alone: use it with --step matvec")
+    Bg = api.Batch([P]) if args.graph else None
 
     def step(prec):
-        api.pfft_matvec(P, x, om, SPACE_LOOP, prec, out=y)
+        if Bg is not None:
+            Bg.matvec([x], [om], SPACE_LOOP, prec, graph=True, outs=[y])
+        else:
+            api.pfft_matvec(P, x, om, SPACE_LOOP, prec, out=y)
         if args.step != "matvec":
             api.pfft_precond_apply(P, y, om, out=z, prec=prec)
 
@@ -453,11 +461,12 @@ def main():
     pnode = P.export(N.EXPORT_PROJ_NODE)
     ctx = dict(R=R, cb=8, rec=48, Ng=Nx * Ny * Nz, Nx=Nx, My=2 * Ny, Mz=2 * Nz, nt=info["n_tri"], nl=L.nl,
                n_near=info["n_near_pairs"], n_pair=int(pnode.size), n_active=int(np.unique(pnode).size))
-    dom = max((s for s in prof if prof[s][1] > 0), key=lambda s: prof[s][0])
-    ms_dom, n_dom = prof[dom]
+    timed_stages = [s for s in prof if prof[s][1] > 0]   # none when the step is a graph replay
+    dom = max(timed_stages, key=lambda s: prof[s][0]) if timed_stages else None
+    ms_dom, n_dom = prof[dom] if dom else (0.0, 0)
     stage_table = {s: {"ms_per_step": v[0] / Kp, "launch_groups": v[1]} for s, v in prof.items() if v[1]}
     roofline = None
-    work = stage_work(dom, ctx)
+    work = stage_work(dom, ctx) if dom else None
     if work:
         bound, amount, unit = work
         sec = ms_dom / n_dom / 1e3
@@ -538,7 +547,8 @@ def main():
                 "config": {"workload": w["name"], "triangles": int(m.nt), "loops": int(L.nl),
                            "grid": list(w["grid"]), "rhs_per_step": R, "frequencies": len(freqs), "ports": nports,
                            "near_pairs": info["n_near_pairs"],
-                           "step": "z = P^-1 A Z_b A^T x (mixed)" if args.step != "matvec" else "y = A Z_b A^T x (mixed)",
+                           "step": ("z = P^-1 A Z_b A^T x (mixed)" if args.step != "matvec" else "y = A Z_b A^T x (mixed)")
+                           + (", replayed as a CUDA graph" if args.graph else ""),
                            "l2": "inputs larger than L2 (per-step grids %.2f GB, x-padded grids %.2f GB)" % (
                                3 * R * Nx * Ny * Nz * 8 / 1e9, 6 * R * Nx * Ny * Nz * 8 / 1e9),
                            "parallelism": f"replicas x{world}"},
