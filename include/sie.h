@@ -303,6 +303,44 @@ typedef struct {
 int pfft_autotune(const sie_mesh *m, const sie_loops *l, const pfft_params *base, int32_t nrhs, double omega,
                   double tol, void *cuda_stream, pfft_params *best, sie_tune_report *rep);
 
+/* Learned correction of the preconditioner (Eq. Precond): D'_e = D_e (1 + g(f_e))
+ * for the diagonal D_e of Z_b on each branch, g a network of six per-branch
+ * features at the frequency (quarter decades of |Z_s| G_ee, c_L Lt_ee, their
+ * ratio, G_ee, Lt_ee and omega), f [6] -> tanh [H] -> tanh [H] ->
+ * g = 0.5 tanh(.), H = 16 or 32, FP32 parameters on the device, flat
+ * [W1 H x 6][b1 H][W2 H x H][b2 H][w3 H][b3].  A new network has a zero output
+ * layer: g = 0, the plain preconditioner.  Training is full-batch mean squared
+ * error against per-branch targets with Adam (device kernels); the plain
+ * preconditioner stays the fallback (pfft_plan_set_learned(p, NULL)).
+ * Errors: SIE_ERR_ARG, SIE_ERR_OOM, SIE_ERR_CUDA. */
+typedef struct sie_mlp sie_mlp;
+int sie_mlp_create(int32_t hidden, uint64_t seed, sie_mlp **out);
+void sie_mlp_destroy(sie_mlp *m);
+int64_t sie_mlp_param_count(const sie_mlp *m);
+int sie_mlp_get_params(const sie_mlp *m, float *host, int64_t n);
+int sie_mlp_set_params(sie_mlp *m, const float *host, int64_t n);   /* also resets Adam's moments */
+/* g [n] (device float) of features [n][6] (device float); synchronises cuda_stream. */
+int sie_mlp_forward(const sie_mlp *m, const float *feats, int64_t n, float *g, void *cuda_stream);
+/* Gradient (host [param_count], may be NULL) and loss (host, may be NULL) of the
+ * mean squared error (1/n) sum (g_e - t_e)^2, features and targets on the device. */
+int sie_mlp_grad(sie_mlp *m, const float *feats, const float *target, int64_t n, float *grad_host,
+                 float *loss_host, void *cuda_stream);
+/* `steps` Adam steps (lr; moments persist across calls); loss before each step into
+ * loss_host [steps] (may be NULL). */
+int sie_mlp_train(sie_mlp *m, const float *feats, const float *target, int64_t n, int32_t steps, float lr,
+                  float *loss_host, void *cuda_stream);
+/* Features of every branch of the plan at omega: feats device float [n_branches][6]. */
+int pfft_branch_features(pfft_plan *p, double omega, float *feats, void *cuda_stream);
+/* Training target per branch: t_e = sum_k Re(conj(D_e a_ke) (Z_b a_k)_e) / sum_k |D_e a_ke|^2 - 1,
+ * clipped to [-0.45, 0.45], for k probe branch currents alpha (device complex128
+ * [k][n_branches]) at omega; Z_b a_k is the branch-space product (FP64).
+ * target: device float [n_branches]. */
+int pfft_branch_probe_target(pfft_plan *p, const void *alpha, int32_t k, double omega, float *target,
+                             void *cuda_stream);
+/* Use the network (borrowed: keep it alive while set) in the plan's preconditioner,
+ * or NULL for the plain one; cached factors are rebuilt on next use. */
+int pfft_plan_set_learned(pfft_plan *p, const sie_mlp *m);
+
 /* Plan introspection for tests and benchmarks: sizes (any pointer may be NULL). */
 int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, int64_t *n_tri,
                    int64_t *n_near_pairs, double *grid_h /* [3] */, double *r_near,

@@ -333,6 +333,75 @@ def pfft_precond_apply(plan: Plan, y, omega, out=None, prec=N.PREC_FP64, stream=
     return z
 
 
+class MLP:
+    """The learned preconditioner correction's network (sie_mlp_*): f [6] -> H -> H -> g."""
+
+    def __init__(self, hidden=32, seed=0):
+        h = ctypes.c_void_p()
+        check(lib().sie_mlp_create(int(hidden), int(seed), ctypes.byref(h)))
+        self.h = h
+        self.hidden = hidden
+        self.n = int(lib().sie_mlp_param_count(h))
+
+    def params(self):
+        out = np.zeros(self.n, np.float32)
+        check(lib().sie_mlp_get_params(self.h, _ptr(out), self.n))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        check(lib().sie_mlp_set_params(self.h, _ptr(p), p.size))
+
+    def forward(self, feats, stream=None):
+        import torch
+        g = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+        check(lib().sie_mlp_forward(self.h, ctypes.c_void_p(feats.data_ptr()), feats.shape[0],
+                                    ctypes.c_void_p(g.data_ptr()), _stream(stream)))
+        return g
+
+    def grad(self, feats, target, stream=None):
+        gr = np.zeros(self.n, np.float32)
+        loss = np.zeros(1, np.float32)
+        check(lib().sie_mlp_grad(self.h, ctypes.c_void_p(feats.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                 feats.shape[0], _ptr(gr), _ptr(loss), _stream(stream)))
+        return float(loss[0]), gr
+
+    def train(self, feats, target, steps, lr=1e-2, stream=None):
+        losses = np.zeros(steps, np.float32)
+        check(lib().sie_mlp_train(self.h, ctypes.c_void_p(feats.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                  feats.shape[0], int(steps), float(lr), _ptr(losses), _stream(stream)))
+        return losses
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().sie_mlp_destroy(self.h)
+            self.h = None
+
+
+def branch_features(plan, omega, stream=None):
+    """[n_branches, 6] float32 CUDA tensor of the learned correction's features."""
+    import torch
+    f = torch.empty((plan.nb, 6), dtype=torch.float32, device="cuda")
+    check(lib().pfft_branch_features(plan.h, float(omega), ctypes.c_void_p(f.data_ptr()), _stream(stream)))
+    return f
+
+
+def branch_probe_target(plan, alpha, omega, stream=None):
+    """Per-branch probing targets (float32 [n_branches]) from probe currents alpha [k, n_branches]."""
+    import torch
+    _check_vec(alpha, plan.nb, "alpha")
+    t = torch.empty(plan.nb, dtype=torch.float32, device=alpha.device)
+    check(lib().pfft_branch_probe_target(plan.h, ctypes.c_void_p(alpha.data_ptr()), alpha.shape[0], float(omega),
+                                         ctypes.c_void_p(t.data_ptr()), _stream(stream)))
+    return t
+
+
+def set_learned(plan, mlp):
+    """Use mlp (MLP or None) in the plan's preconditioner; the plan keeps a reference."""
+    check(lib().pfft_plan_set_learned(plan.h, mlp.h if mlp is not None else None))
+    plan._learned = mlp
+
+
 class Batch:
     """Plans of uneven geometries driven together (sie_batch_*)."""
 

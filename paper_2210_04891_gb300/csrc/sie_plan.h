@@ -52,6 +52,8 @@ struct pfft_plan {
     bool large_plane = false;
     // incremented whenever the scratch buffers are reallocated (captured graphs hold their addresses)
     uint64_t scr_gen = 0;
+    // learned correction of the preconditioner's branch diagonal (borrowed; NULL: plain)
+    const sie_mlp *learned = nullptr;
     // stream-ordered allocations of the solve path (GMRES workspaces, per-frequency factors):
     // the plan's own pool, which keeps freed memory mapped until the plan is destroyed
     cudaMemPool_t pool = nullptr;
@@ -183,6 +185,11 @@ int fill_coef(const pfft_plan *p, const double *omega, int32_t R, double *cf, fl
 int matvec_launch(pfft_plan *p, const void *x, void *y, int32_t nrhs, int space, int prec, cudaStream_t st);
 int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega, int space, int prec,
                  cudaStream_t st);
+// Admittances a [nslots][nb] of the preconditioner scaled by 1 / (1 + g) when the plan
+// has a learned network (no-op otherwise); d_zs_cl as in the preconditioner's set-up.
+int learned_admittance(pfft_plan *p, const double *d_zs_cl, int32_t nslots, double2 *a, cudaStream_t st);
+// Forget the preconditioner's cached numeric factors (rebuilt on next use).
+void invalidate_precond_factors(pfft_plan *p);
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
 int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
 int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s,

@@ -978,6 +978,7 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zc, p->ncond,
                                                        p->nb, ns, s->d_a);
     SIE_LAUNCH_CHECK(p);
+    if (int rl = learned_admittance(p, d_zc, ns, s->d_a, st)) return rl;   // D' = D (1 + g)
     k_round_c<<<nblk_(p->nb * ns), 256, 0, st>>>(s->d_a, s->d_a32, p->nb * ns);
     SIE_LAUNCH_CHECK(p);
     int zero = 0;
@@ -1444,6 +1445,12 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
 }
 
 // ------------------------------------------------------------------ surface model
+
+namespace sie {
+void invalidate_precond_factors(pfft_plan *p) {
+    if (p->pc) p->pc->slot_omega.clear();
+}
+}  // namespace sie
 
 extern "C" int pfft_precond_info(pfft_plan *p, int32_t *band_width, int64_t *unknowns, int64_t *blocks) {
     if (!p) return fail(SIE_ERR_ARG, "pfft_precond_info: NULL plan");

@@ -24,7 +24,10 @@ EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basi
            "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_lossy", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "pfft_plan_set_surface_model", "sie_postprocess", "sie_batch_create", "sie_batch_destroy",
-           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info", "pfft_autotune", "sie_last_error"]
+           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
+           "sie_mlp_param_count", "sie_mlp_get_params", "sie_mlp_set_params", "sie_mlp_forward", "sie_mlp_grad",
+           "sie_mlp_train", "pfft_branch_features", "pfft_branch_probe_target", "pfft_plan_set_learned",
+           "sie_last_error"]
 STAGES = ["loop_to_branch", "point_currents", "project", "fft_x_fwd", "fft_yz", "fft_x_inv", "interp",
           "near", "branch_to_loop", "precond_apply", "precond_factor", "arnoldi"]
 (EXPORT_NEAR_PTR, EXPORT_NEAR_COL, EXPORT_LD, EXPORT_LDIRECT, EXPORT_HHAT, EXPORT_START, EXPORT_PROJ_PTR,
@@ -105,6 +108,18 @@ def lib():
     L.sie_postprocess.argtypes = [P, P, I32, P, I32, P, P, P, P]
     L.sie_batch_create.argtypes = [P, I32, PP]
     L.pfft_precond_info.argtypes = [P, P, P, P]
+    L.sie_mlp_create.argtypes = [I32, ctypes.c_uint64, PP]
+    L.sie_mlp_destroy.argtypes = [P]
+    L.sie_mlp_param_count.argtypes = [P]
+    L.sie_mlp_param_count.restype = I64
+    L.sie_mlp_get_params.argtypes = [P, P, I64]
+    L.sie_mlp_set_params.argtypes = [P, P, I64]
+    L.sie_mlp_forward.argtypes = [P, P, I64, P, P]
+    L.sie_mlp_grad.argtypes = [P, P, P, I64, P, P, P]
+    L.sie_mlp_train.argtypes = [P, P, P, I64, I32, ctypes.c_float, P, P]
+    L.pfft_branch_features.argtypes = [P, ctypes.c_double, P, P]
+    L.pfft_branch_probe_target.argtypes = [P, P, I32, ctypes.c_double, P, P]
+    L.pfft_plan_set_learned.argtypes = [P, P]
     L.pfft_autotune.argtypes = [P, P, ctypes.POINTER(PfftParams), I32, ctypes.c_double, ctypes.c_double, P,
                                 ctypes.POINTER(PfftParams), ctypes.POINTER(TuneReport)]
     L.sie_batch_destroy.argtypes = [P]
