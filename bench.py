@@ -311,6 +311,49 @@ def batch_main(args, ws):
               "converged": bool(all(st["converged"] for _, st in res)),
               "includes": "per-frequency band factorisations of every plan",
               "first_solve_seconds": t_first}
+    learned = None
+    if args.learned_eval > 0:
+        # train the correction on the first geometries' features and probing targets at
+        # 1 and 10 GHz, then solve the held-out ones with the plain and the learned form
+        ntrain = min(args.learned_eval, len(plans) - 1)
+        eval_f = np.array([1e9, 1e10])
+        feats, targets = [], []
+        for k in range(ntrain):
+            for j, f in enumerate(eval_f):
+                alpha = torch.from_numpy(synth.complex_gaussian(plans[k].nb, 4, seed=500 + 2 * k + j)).cuda()
+                feats.append(api.branch_features(plans[k], 2 * np.pi * f))
+                targets.append(api.branch_probe_target(plans[k], alpha, 2 * np.pi * f))
+        net = api.MLP(32, seed=1)
+        t0 = time.perf_counter()
+        losses = net.train(torch.cat(feats), torch.cat(targets), 400, lr=3e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        held = plans[ntrain:]
+        Bh = api.Batch(held)
+        fr = [eval_f] * len(held)
+        Bh.solve([eval_f * 1.01] * len(held), tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)   # warm-up
+        out = {}
+        for name, m in (("plain", None), ("learned", net)):
+            for p_ in held:
+                api.set_learned(p_, m)
+            t0 = time.perf_counter()
+            res = Bh.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)
+            out[name] = {"seconds": time.perf_counter() - t0,
+                         "iterations_sum": int(sum(st["iterations_sum"] for _, st in res)),
+                         "iterations_max": int(max(st["iterations_max"] for _, st in res)),
+                         "converged": bool(all(st["converged"] for _, st in res))}
+            Zs = [Z for Z, _ in res]
+            if name == "plain":
+                Zp = Zs
+            else:
+                out[name]["Z_rel_vs_plain"] = float(max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(Zs, Zp)))
+        for p_ in held:
+            api.set_learned(p_, None)
+        learned = {"train_geometries": ntrain, "held_out_geometries": len(held), "frequencies_hz": eval_f.tolist(),
+                   "train_steps": 400, "train_seconds": t_train, "loss_first": float(losses[0]),
+                   "loss_last": float(losses[-1]), **out,
+                   "chosen": "learned" if out["learned"]["iterations_sum"] < out["plain"]["iterations_sum"]
+                   else "plain (fallback)"}
     line = {"metric": "pFFT matvecs/s (batched uneven geometries)", "value": R * K / t_graph, "unit": "matvec/s",
             "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": 1e3 * t_graph / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -321,7 +364,8 @@ def batch_main(args, ws):
             "eager_streams": {"value": R * K / t_eager, "unit": "matvec/s", "ms_per_step": 1e3 * t_eager / K},
             "sequential_one_stream": {"value": R * K / t_seq, "unit": "matvec/s", "ms_per_step": 1e3 * t_seq / K},
             "plain_fp64": {"value": R * K64 / t_64, "unit": "matvec/s", "ms_per_step": 1e3 * t_64 / K64},
-            "gmres_batched": gm, "graph_stats": B.stats(), "clocks": clocks, "gpu_launches": launches}
+            "gmres_batched": gm, "learned_preconditioner": learned, "graph_stats": B.stats(), "clocks": clocks,
+            "gpu_launches": launches}
     print(json.dumps(line))
 
 
@@ -338,6 +382,9 @@ def main():
     ap.add_argument("--step", default="matvec+precond", choices=["matvec+precond", "matvec"],
                     help="what one step applies (matvec: the plane pair, whose band preconditioner is too wide)")
     ap.add_argument("--gmres-freqs", type=int, default=0, help="batched workloads: frequencies per geometry solved")
+    ap.add_argument("--learned-eval", type=int, default=0,
+                    help="batched workloads: train the learned preconditioner correction on this many geometries "
+                         "and compare it with the plain preconditioner on the others")
     ap.add_argument("--graph", action="store_true",
                     help="with --step matvec: replay the product as a captured CUDA graph (a batch of one plan)")
     args = ap.parse_args()
