@@ -173,6 +173,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def shard(units, rank, world, sizes=None):
+    """The units (independent geometries, or frequencies) rank `rank` of `world`
+    processes.  With sizes: largest first, each to the least-loaded rank so far
+    (ties to the lower rank), in the units' original order within a rank;
+    without: every world-th unit from the rank on."""
+    units = list(units)
+    if sizes is None:
+        return units[rank::world]
+    load = [0.0] * world
+    owner = [0] * len(units)
+    for i in sorted(range(len(units)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += sizes[i]
+    return [u for u, o in zip(units, owner) if o == rank]
+
+
 def aggregate(local_seconds, local_units, dist):
     """Whole-job throughput: units of all ranks / the slowest rank's time."""
     if dist is None:
@@ -242,7 +259,7 @@ def cpu_oracle_rate(name, steps=1, warmup=0):
 
 # ------------------------------------------------------------------ main
 
-def batch_main(args, ws):
+def batch_main(args, ws, dist=None, n_total=None):
     """Batched uneven geometries: one step = one product of every plan's loop
     operator on its right-hand sides (all frequencies x ports of every
     geometry), through sie_batch_matvec replaying a captured CUDA graph; beside
@@ -270,6 +287,8 @@ def batch_main(args, ws):
         for _ in range(W):
             fn()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         l0 = sum(p.launches() for p in plans)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -277,6 +296,8 @@ def batch_main(args, ws):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         return e0.elapsed_time(e1) / 1e3, sum(p.launches() for p in plans) - l0
 
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
@@ -292,8 +313,14 @@ def batch_main(args, ws):
     t_seq, _ = run(sequential, K, W)
     K64 = max(3, K // 3)
     t_64, _ = run(lambda: B.matvec(xs, oms, SPACE_LOOP, PREC_FP64, graph=False, outs=outs), K64, 2)
+    # whole-job rates: right-hand sides of all ranks over the slowest rank's time
+    v_graph, t_graph = aggregate(t_graph, R * K, dist)
+    v_eager, t_eager = aggregate(t_eager, R * K, dist)
+    v_seq, t_seq = aggregate(t_seq, R * K, dist)
+    v_64, t_64 = aggregate(t_64, R * K64, dist)
+    R_all = int(round(aggregate(1.0, R, dist)[0]))
     gm = None
-    if args.gmres_freqs > 0:
+    if args.gmres_freqs > 0 and dist is None:
         # a first batched solve at other frequencies loads the solve kernels and builds each
         # plan's symbolic preconditioner; the timed solve then factors its own frequencies
         sel = np.linspace(0, len(ws[0]["freqs"]) - 1, args.gmres_freqs).astype(int)
@@ -312,7 +339,7 @@ def batch_main(args, ws):
               "includes": "per-frequency band factorisations of every plan",
               "first_solve_seconds": t_first}
     learned = None
-    if args.learned_eval > 0:
+    if args.learned_eval > 0 and dist is None:
         # train the correction on the first geometries' features and probing targets at
         # 1 and 10 GHz, then solve the held-out ones with the plain and the learned form
         ntrain = min(args.learned_eval, len(plans) - 1)
@@ -354,16 +381,21 @@ def batch_main(args, ws):
                    "loss_last": float(losses[-1]), **out,
                    "chosen": "learned" if out["learned"]["iterations_sum"] < out["plain"]["iterations_sum"]
                    else "plain (fallback)"}
-    line = {"metric": "pFFT matvecs/s (batched uneven geometries)", "value": R * K / t_graph, "unit": "matvec/s",
-            "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": 1e3 * t_graph / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": args.workload, "geometries": len(ws),
-                       "triangles": int(sum(w["mesh"].nt for w in ws)),
-                       "loops": int(sum(p.nl for p in plans)), "rhs_per_step": R,
-                       "step": "y_i = A Z_b A^T x_i for every geometry i (mixed), one graph launch"},
-            "eager_streams": {"value": R * K / t_eager, "unit": "matvec/s", "ms_per_step": 1e3 * t_eager / K},
-            "sequential_one_stream": {"value": R * K / t_seq, "unit": "matvec/s", "ms_per_step": 1e3 * t_seq / K},
-            "plain_fp64": {"value": R * K64 / t_64, "unit": "matvec/s", "ms_per_step": 1e3 * t_64 / K64},
+    world = dist.get_world_size() if dist else 1
+    if dist and dist.get_rank() != 0:
+        return
+    line = {"metric": "pFFT matvecs/s (batched uneven geometries)", "value": v_graph, "unit": "matvec/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": 1e3 * t_graph / K, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "geometries": n_total or len(ws),
+                       "geometries_on_rank0": len(ws),
+                       "triangles_on_rank0": int(sum(w["mesh"].nt for w in ws)),
+                       "loops_on_rank0": int(sum(p.nl for p in plans)), "rhs_per_step": R_all,
+                       "step": "y_i = A Z_b A^T x_i for every geometry i (mixed), one graph launch per rank",
+                       "parallelism": "geometries sharded over %d ranks (no exchange)" % world},
+            "eager_streams": {"value": v_eager, "unit": "matvec/s", "ms_per_step": 1e3 * t_eager / K},
+            "sequential_one_stream": {"value": v_seq, "unit": "matvec/s", "ms_per_step": 1e3 * t_seq / K},
+            "plain_fp64": {"value": v_64, "unit": "matvec/s", "ms_per_step": 1e3 * t_64 / K64},
             "gmres_batched": gm, "learned_preconditioner": learned, "graph_stats": B.stats(), "clocks": clocks,
             "gpu_launches": launches}
     print(json.dumps(line))
@@ -397,11 +429,16 @@ def main():
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline covers single geometries"}))
             return
-        if world > 1 and rank != 0:
-            return
         import torch
+        dist = None
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.init_process_group("nccl")
+            dist = tdist
         torch.cuda.set_device(local)
-        batch_main(args, wl)
+        batch_main(args, shard(wl, rank, world, sizes=[w["mesh"].nt for w in wl]), dist, n_total=len(wl))
+        if dist:
+            dist.destroy_process_group()
         return
     w, m = workload(args.workload)
     freqs = w["freqs"][:args.nfreq] if args.nfreq > 0 else w["freqs"]
