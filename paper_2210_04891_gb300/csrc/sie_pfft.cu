@@ -820,8 +820,7 @@ extern "C" int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, c
     (void)cudaGetLastError();   // clear a stale error left by earlier work in this thread
     int rc = sie::matvec_async(p, x, y, nrhs, omega, space, prec, st);
     if (rc) return rc;
-    SIE_CUDA(cudaStreamSynchronize(st));
-    return sie::check_device_errors(p);
+    return sie::finish_call(p, st);
 }
 
 extern "C" int sie_postprocess(pfft_plan *p, const void *x, int32_t nrhs, const double *omega, int32_t prec,

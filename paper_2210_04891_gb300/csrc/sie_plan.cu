@@ -605,6 +605,19 @@ int check_device_errors(pfft_plan *p) {
     return fail(SIE_ERR_TIMEOUT, "a bounded device-side wait ran out (tensor-core near field); results are invalid");
 }
 
+int finish_call(pfft_plan *p, cudaStream_t st) {
+    if (!p->h_err) {
+        SIE_CUDA(cudaStreamSynchronize(st));
+        return check_device_errors(p);
+    }
+    SIE_CUDA(cudaMemcpyAsync(p->h_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SIE_CUDA(cudaStreamSynchronize(st));
+    if (!*p->h_err) return SIE_OK;
+    SIE_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    *p->h_err = 0;
+    return fail(SIE_ERR_TIMEOUT, "a bounded device-side wait ran out (tensor-core near field); results are invalid");
+}
+
 }  // namespace sie
 
 extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pfft_params *prm, void *cuda_stream,
@@ -1040,6 +1053,8 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     if ((rcode = near_mma_prepare(p, near_ptr, near_col, s))) return bail(rcode);
     if ((rcode = plan_alloc(p, (void **)&p->d_err, sizeof(int)))) return bail(rcode);
     SIE_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    if (cudaMallocHost((void **)&p->h_err, sizeof(int)) != cudaSuccess) p->h_err = nullptr;   // optional
+    else *p->h_err = 0;
     if ((rcode = plan_alloc(p, (void **)&p->d_diag_L, L->nb * sizeof(double)))) return bail(rcode);
     k_branch_diag<<<(L->nb + 255) / 256, 256, 0, s>>>(p->d_near_ptr, p->d_near_col, p->d_Ldir64, p->d_br_tri,
                                                       p->d_br_local, L->nb, p->d_diag_L);
@@ -1058,6 +1073,7 @@ extern "C" void pfft_plan_destroy(pfft_plan *p) {
     sie::plan_free_precond(p);
     for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void *a : p->allocations) cudaFree(a);
+    if (p->h_err) cudaFreeHost(p->h_err);
     if (p->pool) {
         cudaDeviceSynchronize();   // stream-ordered frees of the solve path have completed
         cudaMemPoolDestroy(p->pool);

@@ -100,6 +100,7 @@ struct pfft_plan {
     int32_t *d_nm_utri = nullptr;       // [nm_union] column triangles, ascending per tile
     float *d_nm_A = nullptr;            // [nm_union][128][3] dense L_d blocks of each tile (fp32)
     int *d_err = nullptr;               // device error flags (a bounded wait ran out)
+    int *h_err = nullptr;               // pinned host copy, read with the call's own stream sync
     // kernel spectrum, folded [My/2+1][Mz/2+1][Mx/2+1], scaled by 1/(Mx My Mz)
     double *d_H64 = nullptr;
     float *d_H32 = nullptr;
@@ -202,4 +203,7 @@ int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st);
 bool plane_conv_supported(const pfft_plan *p);
 int plane_conv_f32(pfft_plan *p, float2 *spec, int32_t ngrids, cudaStream_t s, bool &done);
 int check_device_errors(pfft_plan *p);
+// End of a synchronous call on stream st: the error flags come back with the
+// stream's one synchronisation (pinned copy) instead of a second round trip.
+int finish_call(pfft_plan *p, cudaStream_t st);
 }  // namespace sie
