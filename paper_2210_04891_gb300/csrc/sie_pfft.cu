@@ -642,9 +642,10 @@ template <typename T, int V, int J> struct Blocks {
     } while (0)
 // The far-field gather keeps slabs at most 64 wide in FP32: its 128-wide form
 // needs 80 registers a thread, which caps residency at 3 CTAs per SM for this
-// latency-bound gather; two 64-wide slabs read each block record twice but keep
-// 4 CTAs resident (measured: 0.77 -> 0.66 ms on the bond-wire step; the
-// projection, whose block records dominate its loads, is faster 128 wide).
+// latency-bound gather; two 64-wide slabs (61 registers) read each block record
+// twice but keep 4 CTAs resident (measured: 0.77 -> 0.66 ms on the bond-wire
+// step; the projection, whose block records dominate its loads, is faster 128
+// wide).
 #define SIE_SLAB_DISPATCH_NARROW(T, R, CALL)                                              \
     do {                                                                                 \
         if constexpr (sizeof(T) == 4) {                                                   \
