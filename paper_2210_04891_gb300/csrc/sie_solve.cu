@@ -517,127 +517,145 @@ __global__ void k_pc_solve(const double2 *__restrict__ kappa, const int32_t *__r
 }
 
 // Band solve L d L^T u = rhs for bands wider than a warp (31 < W < 1024), one
-// CTA of Wt >= W + 1 threads per (right-hand side, block), after assembling
-// rhs_i = -sum over the incident branches of s * kappa_e.  Right-looking
-// sweeps: thread j holds the running value of the one row of the window (the Wt
-// rows from the current pivot on) that is congruent to j; at each step the
-// pivot's owner finishes it and publishes it through shared memory (two
-// alternating slots, one barrier per step), every thread subtracts its band
-// entry times the pivot (the column-major copy gives L[k+d][k] in the forward
-// sweep, the row-major band L[k][k-d] in the backward sweep; each entry is
-// loaded one step ahead) and the owner takes over the row Wt further on, whose
-// first update comes from a later pivot since Wt > W.
+// CTA of Wt >= W threads per (right-hand side, block), after assembling
+// rhs_i = -sum over the incident branches of s * kappa_e.  The sweeps go 32 pivots at a time: the CTA
+// stages the chunk's 32 x 32 triangle of L in shared memory, warp 0 finishes the
+// chunk's rows in registers (a shuffle broadcasts each pivot, no CTA barrier),
+// then every thread subtracts the chunk's contribution from one of the W band
+// rows below (32 consecutive entries of its row of the band: the row-major band
+// in the forward sweep, the column-major copy in the backward sweep), and the
+// rows that enter the band take their right-hand sides.  Pending values live in
+// a circular shared-memory window of S >= W + 32 rows.  Three barriers per 32
+// pivots instead of one per pivot.
 template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_pc_sweep_wide(
+__global__ void __launch_bounds__(MAXT) k_pc_sweep_blk(
     const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
-    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int64_t nunk,
-    int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc, const int32_t *__restrict__ slot,
-    C<T> *__restrict__ u) {
-    __shared__ C<T> piv[2];
+    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, int32_t nblk, int32_t W, int32_t S,
+    int64_t nunk, int64_t nb, const C<T> *__restrict__ band, const C<T> *__restrict__ bandc,
+    const int32_t *__restrict__ slot, C<T> *__restrict__ u) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T> *pend = reinterpret_cast<C<T> *>(smem_raw);   // [S] window of pending rows
+    C<T> *tri = pend + S;                              // [32][33] chunk triangle
+    C<T> *xc = tri + 32 * 33;                          // [32] finished chunk values
     const int64_t r = blockIdx.x / nblk, b = blockIdx.x % nblk;
     const int64_t o = blk_off[b], n = blk_off[b + 1] - o;
-    const int Wp = W + 1, Wt = blockDim.x, j = threadIdx.x;
+    const int Wp = W + 1, nt = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     const C<T> *B = band + (int64_t(slot[r]) * nunk + o) * Wp;
     const C<T> *Bc = bandc + (int64_t(slot[r]) * nunk + o) * Wp;
     C<T> *x = u + r * nunk + o;
     const C<T> *kr = kappa + r * nb;
     const C<T> zero = mk<T>(T(0), T(0));
-    for (int64_t i = j; i < n; i += Wt) {
+    const int64_t smask = S - 1;
+    for (int64_t i = tid; i < n; i += nt) {
         C<T> acc = zero;
         for (int32_t k = row_ptr[o + i]; k < row_ptr[o + i + 1]; ++k)
             acc = row_sg[k] > 0 ? csub(acc, kr[row_br[k]]) : cadd(acc, kr[row_br[k]]);
         x[i] = acc;
     }
     __syncthreads();
-    // Step k's pivot belongs to thread own = k mod Wt (a running counter); a thread's
-    // row sits d = (j - own) mod Wt rows after the pivot.  A thread loads the
-    // right-hand side of the row it takes next one ownership period (Wt steps)
-    // ahead, and its band entries kAhead steps ahead, so no step waits on memory.
-    // Loads always read a valid address (clamped) and carry a flag that is applied
-    // where the value is used: a conditional load would make the select wait for it.
-    constexpr int kAhead = sizeof(T) == 8 ? 4 : 8;
-    auto dist_of = [&](int o) { const int d = j - o; return d < 0 ? d + Wt : d; };
-    // forward sweep (unit lower L, column entries bandc[k][d] = L[k+d][k])
-    C<T> pend = x[j < n ? j : 0];
-    if (j >= n) pend = zero;
-    bool nxt_ok = j + Wt < n;
-    C<T> nxt = x[nxt_ok ? j + Wt : 0];
-    C<T> ring[kAhead];
-    bool rok[kAhead];
-#pragma unroll
-    for (int q = 0; q < kAhead; ++q) {
-        const int d = dist_of(q);
-        rok[q] = q < n && d >= 1 && d <= W && q + d < n;
-        ring[q] = Bc[rok[q] ? int64_t(q) * Wp + d : 0];
-    }
-    int own = 0;
-    for (int64_t k0 = 0; k0 < n; k0 += kAhead) {
-#pragma unroll
-        for (int q = 0; q < kAhead; ++q) {
-            const int64_t k = k0 + q;
-            if (k < n) {
-                if (j == own) {
-                    x[k] = pend;
-                    piv[k & 1] = pend;
-                    pend = nxt_ok ? nxt : zero;
-                    nxt_ok = k + 2 * Wt < n;
-                    nxt = x[nxt_ok ? k + 2 * Wt : k];
-                }
-                __syncthreads();
-                if (rok[q]) pend = csub(pend, cmul(ring[q], piv[k & 1]));
+    // ---- forward: L z = rhs, rows in increasing order
+    for (int64_t i = tid; i < n && i < W + 32; i += nt) pend[i & smask] = x[i];
+    for (int64_t k0 = 0; k0 < n; k0 += 32) {
+        __syncthreads();                               // window rows of this chunk are final
+#pragma unroll 8
+        for (int e = tid; e < 32 * 32; e += nt) {      // tri[l][j] = L[k0+l][k0+j], j < l
+            const int l = e >> 5, j = e & 31;
+            tri[l * 33 + j] = (j < l && k0 + l < n) ? B[(k0 + l) * Wp + (l - j)] : zero;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            C<T> v = k0 + lane < n ? pend[(k0 + lane) & smask] : zero;
+#pragma unroll 4
+            for (int j = 0; j < 31; ++j) {
+                C<T> xj;
+                xj.x = __shfl_sync(0xffffffffu, v.x, j);
+                xj.y = __shfl_sync(0xffffffffu, v.y, j);
+                if (lane > j) v = csub(v, cmul(tri[lane * 33 + j], xj));
             }
-            int o2 = own + kAhead;
-            if (o2 >= Wt) o2 -= Wt;
-            const int d2 = dist_of(o2);
-            const int64_t k2 = k + kAhead;
-            rok[q] = k2 < n && d2 >= 1 && d2 <= W && k2 + d2 < n;
-            ring[q] = Bc[rok[q] ? k2 * Wp + d2 : 0];
-            own = own + 1 == Wt ? 0 : own + 1;
+            xc[lane] = v;
+            if (k0 + lane < n) x[k0 + lane] = v;
+        }
+        __syncthreads();
+        // rows k0 + 32 + t (t < W) take the chunk's contribution; rows entering the band take rhs
+        for (int t = tid; t < W; t += nt) {
+            const int64_t i = k0 + 32 + t;
+            if (i >= n) break;
+            const C<T> *row = B + i * Wp;              // L[i][k0+j] = row[32 + t - j]
+            const int j0 = 32 + t - W > 0 ? 32 + t - W : 0;   // band edge
+            // loads issued in batches of KB ahead of their multiply-adds (KB = 32 where the
+            // register budget allows, 8 under the 1024-thread cap)
+            constexpr int KB = MAXT > 256 ? 8 : 32;
+            C<T> acc = zero;
+#pragma unroll
+            for (int jb = 0; jb < 32; jb += KB) {
+                C<T> e[KB];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) e[q] = row[jb + q >= j0 ? 32 + t - jb - q : 32 + t - 31];
+#pragma unroll
+                for (int q = 0; q < KB; ++q)
+                    if (jb + q >= j0) acc = cadd(acc, cmul(e[q], xc[jb + q]));
+            }
+            pend[i & smask] = csub(pend[i & smask], acc);
+        }
+        for (int t = tid; t < 32; t += nt) {
+            const int64_t i = k0 + 32 + W + t;
+            if (i < n) pend[i & smask] = x[i];
         }
     }
     __syncthreads();
-    for (int64_t i = j; i < n; i += Wt) {   // diagonal: x_i /= d_i
+    for (int64_t i = tid; i < n; i += nt) {           // diagonal: x_i /= d_i
         const C<T> dg = B[i * Wp];
         const T den = dg.x * dg.x + dg.y * dg.y;
         x[i] = cmul(x[i], mk<T>(dg.x / den, -dg.y / den));
     }
     __syncthreads();
-    // backward sweep (L^T): step s finishes row k = n - 1 - s; row entries band[k][d] = L[k][k-d]
-    pend = x[j < n ? n - 1 - j : 0];
-    if (j >= n) pend = zero;
-    nxt_ok = j + Wt < n;
-    nxt = x[nxt_ok ? n - 1 - j - Wt : 0];
-#pragma unroll
-    for (int q = 0; q < kAhead; ++q) {
-        const int d = dist_of(q);
-        const int64_t k = n - 1 - q;
-        rok[q] = q < n && d >= 1 && d <= W && k - d >= 0;
-        ring[q] = B[rok[q] ? k * Wp + d : 0];
-    }
-    own = 0;
-    for (int64_t s0 = 0; s0 < n; s0 += kAhead) {
-#pragma unroll
-        for (int q = 0; q < kAhead; ++q) {
-            const int64_t st = s0 + q;
-            if (st < n) {
-                const int64_t k = n - 1 - st;
-                if (j == own) {
-                    x[k] = pend;
-                    piv[st & 1] = pend;
-                    pend = nxt_ok ? nxt : zero;
-                    nxt_ok = st + 2 * Wt < n;
-                    nxt = x[nxt_ok ? k - 2 * Wt : k];
-                }
-                __syncthreads();
-                if (rok[q]) pend = csub(pend, cmul(ring[q], piv[st & 1]));
+    // ---- backward: L^T u = z, rows in decreasing order; row q = n - 1 - k in the window
+    for (int64_t k = tid; k < n && k < W + 32; k += nt) pend[k & smask] = x[n - 1 - k];
+    for (int64_t k0 = 0; k0 < n; k0 += 32) {
+        __syncthreads();
+        const int64_t k1 = n - 1 - k0;                 // the chunk's top row
+#pragma unroll 8
+        for (int e = tid; e < 32 * 32; e += nt) {      // tri[l][j] = L[k1-j][k1-l], j < l
+            const int l = e >> 5, j = e & 31;
+            tri[l * 33 + j] = (j < l && k0 + l < n) ? Bc[(k1 - l) * Wp + (l - j)] : zero;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            C<T> v = k0 + lane < n ? pend[(k0 + lane) & smask] : zero;
+#pragma unroll 4
+            for (int j = 0; j < 31; ++j) {
+                C<T> xj;
+                xj.x = __shfl_sync(0xffffffffu, v.x, j);
+                xj.y = __shfl_sync(0xffffffffu, v.y, j);
+                if (lane > j) v = csub(v, cmul(tri[lane * 33 + j], xj));
             }
-            int o2 = own + kAhead;
-            if (o2 >= Wt) o2 -= Wt;
-            const int d2 = dist_of(o2);
-            const int64_t s2 = st + kAhead, k2 = n - 1 - s2;
-            rok[q] = s2 < n && d2 >= 1 && d2 <= W && k2 - d2 >= 0;
-            ring[q] = B[rok[q] ? k2 * Wp + d2 : 0];
-            own = own + 1 == Wt ? 0 : own + 1;
+            xc[lane] = v;
+            if (k0 + lane < n) x[k1 - lane] = v;
+        }
+        __syncthreads();
+        for (int t = tid; t < W; t += nt) {
+            const int64_t k = k0 + 32 + t;             // row k1 - 32 - t
+            if (k >= n) break;
+            const C<T> *col = Bc + (n - 1 - k) * Wp;   // L[k1-j][row] = col[32 + t - j]
+            const int j0 = 32 + t - W > 0 ? 32 + t - W : 0;
+            // loads issued in batches of KB ahead of their multiply-adds (KB = 32 where the
+            // register budget allows, 8 under the 1024-thread cap)
+            constexpr int KB = MAXT > 256 ? 8 : 32;
+            C<T> acc = zero;
+#pragma unroll
+            for (int jb = 0; jb < 32; jb += KB) {
+                C<T> e[KB];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) e[q] = col[jb + q >= j0 ? 32 + t - jb - q : 32 + t - 31];
+#pragma unroll
+                for (int q = 0; q < KB; ++q)
+                    if (jb + q >= j0) acc = cadd(acc, cmul(e[q], xc[jb + q]));
+            }
+            pend[k & smask] = csub(pend[k & smask], acc);
+        }
+        for (int t = tid; t < 32; t += nt) {
+            const int64_t k = k0 + 32 + W + t;
+            if (k < n) pend[k & smask] = x[n - 1 - k];
         }
     }
 }
@@ -1050,15 +1068,23 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
             const int wt = (s->W + 1 + 31) / 32 * 32;
             const C<T> *band, *bandc;
             if constexpr (f32) { band = s->d_band32; bandc = s->d_bandc32; } else { band = s->d_band; bandc = s->d_bandc; }
-            // up to 256 threads: registers for the look-ahead ring without spilling to the cap of 1024
-            if (wt <= 256)
-                k_pc_sweep_wide<T, 256><<<unsigned(int64_t(R) * nblk), wt, 0, st>>>(
-                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band,
+            // blocked sweeps: Wt >= W threads, window of S >= W + 32 rows in shared memory
+            int S = 64;
+            while (S < s->W + 32) S *= 2;
+            const size_t sm = size_t(S + 32 * 33 + 32) * sizeof(C<T>);
+            if (wt <= 256) {
+                SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep_blk<T, 256>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+                k_pc_sweep_blk<T, 256><<<unsigned(int64_t(R) * nblk), wt, sm, st>>>(
+                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, S, s->nunk, p->nb, band,
                     bandc, s->d_slot, u);
-            else
-                k_pc_sweep_wide<T, 1024><<<unsigned(int64_t(R) * nblk), wt, 0, st>>>(
-                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, s->nunk, p->nb, band,
+            } else {
+                SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep_blk<T, 1024>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+                k_pc_sweep_blk<T, 1024><<<unsigned(int64_t(R) * nblk), wt, sm, st>>>(
+                    kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, S, s->nunk, p->nb, band,
                     bandc, s->d_slot, u);
+            }
         } else {
             if constexpr (f32) return fail(SIE_ERR_ARG, "preconditioner: FP32 sweeps need a band width below 1024");
             else
