@@ -77,3 +77,19 @@ def probe_target(D, Zb_alpha, alpha):
     num = np.sum(np.real(np.conj(Da) * Zb_alpha), axis=0)
     den = np.sum(np.abs(Da) ** 2, axis=0)
     return np.clip(num / den - 1.0, -CLIP, CLIP)
+
+
+N_FEATURES = 6
+MU0_4PI = 1e-7   # mu0 / (4 pi)
+
+
+def features(zs_abs, cl, gram_diag, l_diag):
+    """Per-branch features at one frequency (F = 6), quarter decades:
+    |Z_s| G_ee, c_L Lt_ee, their ratio, G_ee, Lt_ee and omega (= c_L / (mu0 / 4 pi)),
+    each as 0.25 log10(max(x, 1e-300)) clipped to [-20, 20]."""
+    a = zs_abs * gram_diag
+    b = cl * l_diag
+    q = lambda x: np.clip(0.25 * np.log10(np.maximum(x, 1e-300)), -20.0, 20.0)
+    cols = [q(a), q(b), q(np.maximum(a, 1e-300) / np.maximum(b, 1e-300)), q(gram_diag), q(l_diag),
+            q(np.full_like(a, cl / MU0_4PI))]
+    return np.stack(cols, axis=1)

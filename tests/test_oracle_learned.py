@@ -69,3 +69,20 @@ def test_probe_target():
     big = probe_target(D, 3.0 * D * a, a)
     assert np.all(big == CLIP)
     assert SCALE > CLIP
+
+
+def test_features_definition():
+    from oracle.learned import features, MU0_4PI
+    zs = np.array([1e-2, 2e-2])
+    G = np.array([1e2, 1e4])
+    L = np.array([1e-6, 1e-4])
+    w = 2 * np.pi * 1e9
+    f = features(zs, w * MU0_4PI, G, L)
+    a, b = zs * G, w * MU0_4PI * L
+    assert f.shape == (2, 6)
+    assert np.allclose(f[:, 0], 0.25 * np.log10(a)) and np.allclose(f[:, 1], 0.25 * np.log10(b))
+    assert np.allclose(f[:, 2], f[:, 0] - f[:, 1])
+    assert np.allclose(f[:, 5], 0.25 * np.log10(w))
+    # DC: c_L = 0 gives the clipped floor for the inductive term and the clipped ceiling for the ratio
+    f0 = features(zs, 0.0, G, L)
+    assert np.all(f0[:, 1] == -20.0) and np.all(f0[:, 2] == 20.0) and np.all(f0[:, 5] == -20.0)
