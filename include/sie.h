@@ -341,6 +341,15 @@ int pfft_branch_probe_target(pfft_plan *p, const void *alpha, int32_t k, double 
  * or NULL for the plain one; cached factors are rebuilt on next use. */
 int pfft_plan_set_learned(pfft_plan *p, const sie_mlp *m);
 
+/* Self-test of failure detection: a one-thread kernel waits, with the bounded
+ * wait the tensor-core near field uses (mbarrier try_wait under a time limit),
+ * on a barrier nothing completes; the wait runs out after limit_ms (<= 1000),
+ * sets the plan's device error flag and returns, and the call reads the flag
+ * back as the library's calls do.  Expected result: SIE_ERR_TIMEOUT, with the
+ * flag cleared and the plan and its CUDA context usable; SIE_OK would mean the
+ * wait never ran out.  No fault, trap or hang is involved. */
+int sie_selftest_bounded_wait(pfft_plan *p, double limit_ms, void *cuda_stream);
+
 /* Plan introspection for tests and benchmarks: sizes (any pointer may be NULL). */
 int pfft_plan_info(const pfft_plan *p, int64_t *n_loops, int64_t *n_branches, int64_t *n_tri,
                    int64_t *n_near_pairs, double *grid_h /* [3] */, double *r_near,

@@ -396,6 +396,11 @@ def branch_probe_target(plan, alpha, omega, stream=None):
     return t
 
 
+def selftest_bounded_wait(plan, limit_ms=5.0, stream=None):
+    """Run the failure-detection self-test; returns the library's code (SIE_ERR_TIMEOUT expected)."""
+    return lib().sie_selftest_bounded_wait(plan.h, float(limit_ms), _stream(stream))
+
+
 def set_learned(plan, mlp):
     """Use mlp (MLP or None) in the plan's preconditioner; the plan keeps a reference."""
     check(lib().pfft_plan_set_learned(plan.h, mlp.h if mlp is not None else None))

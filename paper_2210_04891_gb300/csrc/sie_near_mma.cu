@@ -317,7 +317,30 @@ __global__ void k_build_near_tiles(const int32_t *__restrict__ u_tile, const int
     for (int l = 0; l < 3; ++l) Ac[3 * i + l] = v[l];
 }
 
+// Self-test of the failure-detection path: one mbarrier that expects an arrival
+// nothing makes, waited on with the same bounded wait as the tensor-core kernel;
+// the wait runs out after limit_ns and sets the same error bit.
+__global__ void k_selftest_wait(uint64_t limit_ns, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, limit_ns)) atomicOr(err, kErrNearMma);
+}
+
 }  // namespace
+
+extern "C" int sie_selftest_bounded_wait(pfft_plan *p, double limit_ms, void *cuda_stream) {
+    if (!p || !(limit_ms > 0.0) || limit_ms > 1000.0)
+        return sie::fail(SIE_ERR_ARG, "sie_selftest_bounded_wait: limit must be in (0, 1000] ms");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    (void)cudaGetLastError();
+    k_selftest_wait<<<1, 32, 0, st>>>(uint64_t(limit_ms * 1e6), p->d_err);
+    SIE_CUDA(cudaGetLastError());
+    return sie::finish_call(p, st);
+}
 
 namespace sie {
 

@@ -27,7 +27,7 @@ EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basi
            "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
            "sie_mlp_param_count", "sie_mlp_get_params", "sie_mlp_set_params", "sie_mlp_forward", "sie_mlp_grad",
            "sie_mlp_train", "pfft_branch_features", "pfft_branch_probe_target", "pfft_plan_set_learned",
-           "sie_last_error"]
+           "sie_selftest_bounded_wait", "sie_last_error"]
 STAGES = ["loop_to_branch", "point_currents", "project", "fft_x_fwd", "fft_yz", "fft_x_inv", "interp",
           "near", "branch_to_loop", "precond_apply", "precond_factor", "arnoldi"]
 (EXPORT_NEAR_PTR, EXPORT_NEAR_COL, EXPORT_LD, EXPORT_LDIRECT, EXPORT_HHAT, EXPORT_START, EXPORT_PROJ_PTR,
@@ -120,6 +120,7 @@ def lib():
     L.pfft_branch_features.argtypes = [P, ctypes.c_double, P, P]
     L.pfft_branch_probe_target.argtypes = [P, P, I32, ctypes.c_double, P, P]
     L.pfft_plan_set_learned.argtypes = [P, P]
+    L.sie_selftest_bounded_wait.argtypes = [P, ctypes.c_double, P]
     L.pfft_autotune.argtypes = [P, P, ctypes.POINTER(PfftParams), I32, ctypes.c_double, ctypes.c_double, P,
                                 ctypes.POINTER(PfftParams), ctypes.POINTER(TuneReport)]
     L.sie_batch_destroy.argtypes = [P]
