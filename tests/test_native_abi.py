@@ -80,3 +80,48 @@ def test_error_codes():
     with pytest.raises(SieError) as e:
         api.Loops(api.Mesh(xyz, tri, cond, m.sigma), [])
     assert e.value.code == -2
+
+
+# entry points whose first argument is a handle (plan, batch or network):
+# a NULL handle comes back as SIE_ERR_ARG naming the call, before any CUDA call
+HANDLE_CALLS = ["pfft_matvec", "pfft_precond_apply", "pfft_precond_info", "sie_solve", "pfft_convolve",
+                "pfft_convolve_lossy", "pfft_convolve_noalloc", "sie_postprocess", "pfft_plan_info",
+                "pfft_plan_export", "pfft_profile_enable", "pfft_profile_read", "pfft_plan_set_surface_model",
+                "sie_batch_matvec", "sie_batch_solve", "sie_batch_stats", "sie_mlp_get_params",
+                "sie_mlp_set_params", "sie_mlp_forward", "sie_mlp_grad", "sie_mlp_train",
+                "pfft_branch_features", "pfft_branch_probe_target", "pfft_plan_set_learned",
+                "sie_selftest_bounded_wait", "sie_loops_export", "pfft_plan_create", "pfft_autotune"]
+
+
+def neutral_args(fn):
+    """NULL for pointers, 1 for integers, 1.0 for reals: only the handle is wrong."""
+    out = []
+    for t in fn.argtypes:
+        if t in (ctypes.c_double, ctypes.c_float):
+            out.append(t(1.0))
+        elif t in (ctypes.c_int8, ctypes.c_int16, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int):
+            out.append(t(1))
+        else:
+            out.append(None)
+    return out
+
+
+@pytest.mark.parametrize("name", HANDLE_CALLS)
+def test_null_handle_is_an_argument_error(name):
+    lib = native.lib()
+    fn = getattr(lib, name)
+    assert fn.argtypes is not None, name
+    assert fn(*neutral_args(fn)) == -1
+    assert lib.sie_last_error().decode().startswith(name)
+
+
+def test_destroy_and_counts_accept_null():
+    lib = native.lib()
+    for name in ("pfft_plan_destroy", "sie_batch_destroy", "sie_mlp_destroy", "sie_mesh_destroy",
+                 "sie_loops_destroy"):
+        getattr(lib, name)(None)
+    assert lib.pfft_plan_launches(None) == 0
+    assert lib.sie_mlp_param_count(None) == 0
+    out = ctypes.c_void_p(1)
+    assert lib.sie_batch_create(None, 0, ctypes.byref(out)) == -1 and not out.value
+    assert lib.sie_mlp_create(24, 0, ctypes.byref(out)) == -1 and not out.value
