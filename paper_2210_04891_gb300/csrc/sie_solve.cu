@@ -767,12 +767,35 @@ __device__ __forceinline__ void pc_chunk(const C<T> *tl, int lane, C<T> &w, cons
     }
 }
 
+// Right-hand sides of the nodal systems, rhs_i = -sum over the incident
+// branches e of s * kappa_e (s = +-1), one thread per (right-hand side, row),
+// branches in their stored order.  Run as its own fully occupied kernel: inside
+// the sweep kernel, at one warp per (right-hand side, block), its chains of
+// dependent gathers were exposed.
 template <typename T>
-__global__ void __launch_bounds__(128, 3) k_pc_sweep(
-    const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ row_br,
-    const int8_t *__restrict__ row_sg, const int64_t *__restrict__ blk_off, const int64_t *__restrict__ tile_off,
-    int32_t nblk, int64_t nunk, int64_t nchunks, int64_t nb, const C<T> *__restrict__ tiles,
-    const C<T> *__restrict__ dinv, const int32_t *__restrict__ slot, int32_t R, C<T> *__restrict__ xs) {
+__global__ void k_pc_rhs(const C<T> *__restrict__ kappa, const int32_t *__restrict__ row_ptr,
+                         const int32_t *__restrict__ row_br, const int8_t *__restrict__ row_sg, int64_t nunk,
+                         int64_t nb, int32_t R, C<T> *__restrict__ xs) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= int64_t(R) * nunk) return;
+    const int64_t r = g / nunk, row = g - r * nunk;
+    const C<T> *kr = kappa + r * nb;
+    C<T> acc = mk<T>(T(0), T(0));
+    for (int32_t q = row_ptr[row]; q < row_ptr[row + 1]; ++q)
+        acc = row_sg[q] > 0 ? csub(acc, kr[row_br[q]]) : cadd(acc, kr[row_br[q]]);
+    xs[g] = acc;
+}
+
+// Tile buffers per warp in the sweep kernel: tiles are fetched NBUF - 1 chunks
+// ahead of their use.
+template <typename T> __host__ __device__ constexpr int pc_nbuf() { return sizeof(T) == 4 ? 3 : 2; }
+
+template <typename T>
+__global__ void __launch_bounds__(128, 2) k_pc_sweep(
+    const int64_t *__restrict__ blk_off, const int64_t *__restrict__ tile_off, int32_t nblk, int64_t nunk,
+    int64_t nchunks, const C<T> *__restrict__ tiles, const C<T> *__restrict__ dinv, const int32_t *__restrict__ slot,
+    int32_t R, C<T> *__restrict__ xs) {
+    constexpr int NB = pc_nbuf<T>();
     extern __shared__ __align__(16) unsigned char pc_smem[];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -784,55 +807,26 @@ __global__ void __launch_bounds__(128, 3) k_pc_sweep(
     const C<T> *Tb = tiles + ((sl * 2 + 1) * nchunks + tile_off[b]) * PC_TILE;
     const C<T> *dv = dinv + sl * nunk + o;
     const C<T> zero = mk<T>(T(0), T(0));
-    C<T> *buf0 = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * 2 * PC_TILE;   // [warp][2][PC_TILE]
-    C<T> *buf1 = buf0 + PC_TILE;
+    C<T> *buf = reinterpret_cast<C<T> *>(pc_smem) + int64_t(wl) * NB * PC_TILE;   // [warp][NB][PC_TILE]
     C<T> *x = xs + int64_t(r) * nunk + o;
     const int64_t nch = (n + PC_CH - 1) / PC_CH;
-    // first two forward tiles in flight while the right-hand sides are assembled
-    pc_stage_tile<T>(buf0, Tf, lane);
-    asm volatile("cp.async.commit_group;\n" ::);
-    if (nch > 1) pc_stage_tile<T>(buf1, Tf + PC_TILE, lane);
-    asm volatile("cp.async.commit_group;\n" ::);
-    {
-        // right-hand sides of the nodal system; four rows per lane and step so
-        // that their gathers overlap (a triangle node has up to three branches)
-        const C<T> *kr = kappa + int64_t(r) * nb;
-        for (int64_t i0 = lane; i0 < n; i0 += 4 * 32) {
-            int32_t qa[4], qb[4];
-            C<T> acc[4];
+    // the first NB tiles in flight; one commit group per chunk, so that at chunk
+    // c at most NB - 1 groups (those of chunks c + 1 .. c + NB - 1) may pend
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t i = i0 + 32 * u;
-                qa[u] = i < n ? row_ptr[o + i] : 0;
-                qb[u] = i < n ? row_ptr[o + i + 1] : 0;
-                acc[u] = zero;
-            }
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int32_t q = qa[u] + d;
-                    if (q < qb[u]) acc[u] = row_sg[q] > 0 ? csub(acc[u], kr[row_br[q]]) : cadd(acc[u], kr[row_br[q]]);
-                }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                for (int32_t q = qa[u] + 3; q < qb[u]; ++q)   // contact nodes: many branches
-                    acc[u] = row_sg[q] > 0 ? csub(acc[u], kr[row_br[q]]) : cadd(acc[u], kr[row_br[q]]);
-                const int64_t i = i0 + 32 * u;
-                if (i < n) x[i] = acc[u];
-            }
-        }
+    for (int k = 0; k < NB; ++k) {
+        if (k < nch) pc_stage_tile<T>(buf + k * PC_TILE, Tf + k * PC_TILE, lane);
+        asm volatile("cp.async.commit_group;\n" ::);
     }
-    __syncwarp();
     // ---------------- forward: y_{i+d} -= L[i+d][i] y_i, then y_i /= d_i at the store
     C<T> w = lane < n ? x[lane] : zero, pf = lane + 32 < n ? x[lane + 32] : zero, done = zero;
+    int bs = 0;   // buffer of chunk c: c mod NB
     for (int64_t c = 0; c < nch; ++c) {
         const int64_t base = c * PC_CH;
         const C<T> pn = base + 64 + lane < n ? x[base + 64 + lane] : zero;   // row taken over in chunk c + 1
         const C<T> di = base + lane < n ? dv[base + lane] : zero;
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NB - 1));
         __syncwarp();
-        const C<T> *tl = ((c & 1) ? buf1 : buf0) + lane * PC_TP;
+        const C<T> *tl = buf + bs * PC_TILE + lane * PC_TP;
         if (base + PC_CH <= n) {
             pc_chunk<T, 0>(tl, lane, w, pf, done);
         } else {
@@ -841,25 +835,28 @@ __global__ void __launch_bounds__(128, 3) k_pc_sweep(
         if (base + lane < n) x[base + lane] = cmul(done, di);
         pf = pn;
         __syncwarp();
-        if (c + 2 < nch) pc_stage_tile<T>((c & 1) ? buf1 : buf0, Tf + (c + 2) * PC_TILE, lane);
+        if (c + NB < nch) pc_stage_tile<T>(buf + bs * PC_TILE, Tf + (c + NB) * PC_TILE, lane);
         asm volatile("cp.async.commit_group;\n" ::);
+        bs = bs + 1 == NB ? 0 : bs + 1;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     __syncwarp();
     // ---------------- backward: x_{i-d} -= L[i][i-d] x_i   (chunk c = pivots i = n-1-32c-j)
-    pc_stage_tile<T>(buf0, Tb, lane);
-    asm volatile("cp.async.commit_group;\n" ::);
-    if (nch > 1) pc_stage_tile<T>(buf1, Tb + PC_TILE, lane);
-    asm volatile("cp.async.commit_group;\n" ::);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (k < nch) pc_stage_tile<T>(buf + k * PC_TILE, Tb + k * PC_TILE, lane);
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
     w = n - 1 - lane >= 0 ? x[n - 1 - lane] : zero;
     pf = n - 33 - lane >= 0 ? x[n - 33 - lane] : zero;
     done = zero;
+    bs = 0;
     for (int64_t c = 0; c < nch; ++c) {
         const int64_t top = n - 1 - c * PC_CH;          // pivot of step j = 0
         const C<T> pn = top - 64 - lane >= 0 ? x[top - 64 - lane] : zero;
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NB - 1));
         __syncwarp();
-        const C<T> *tl = ((c & 1) ? buf1 : buf0) + lane * PC_TP;
+        const C<T> *tl = buf + bs * PC_TILE + lane * PC_TP;
         if (top - (PC_CH - 1) >= 0) {
             pc_chunk<T, 0>(tl, lane, w, pf, done);
         } else {
@@ -868,8 +865,9 @@ __global__ void __launch_bounds__(128, 3) k_pc_sweep(
         if (top - lane >= 0) x[top - lane] = done;   // final values in place (every row still to be read lies below)
         pf = pn;
         __syncwarp();
-        if (c + 2 < nch) pc_stage_tile<T>((c & 1) ? buf1 : buf0, Tb + (c + 2) * PC_TILE, lane);
+        if (c + NB < nch) pc_stage_tile<T>(buf + bs * PC_TILE, Tb + (c + NB) * PC_TILE, lane);
         asm volatile("cp.async.commit_group;\n" ::);
+        bs = bs + 1 == NB ? 0 : bs + 1;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
 }
@@ -1055,15 +1053,17 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
     SIE_LAUNCH_CHECK(p);
     if (s->nunk > 0) {
         if (s->W <= 31) {
-            // four warps per CTA, two tiles of shared memory per warp
-            const size_t sm = size_t(4) * 2 * PC_TILE * sizeof(C<T>);
+            k_pc_rhs<T><<<nblk_(int64_t(R) * s->nunk), 256, 0, st>>>(kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
+                                                                       s->nunk, p->nb, R, u);
+            SIE_LAUNCH_CHECK(p);
+            // four warps per CTA, pc_nbuf tiles of shared memory per warp
+            const size_t sm = size_t(4) * pc_nbuf<T>() * PC_TILE * sizeof(C<T>);
             SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(sm)));
             const C<T> *tiles, *dinv;
             if constexpr (f32) { tiles = s->d_tile32; dinv = s->d_dinv32; } else { tiles = s->d_tile64; dinv = s->d_dinv64; }
             k_pc_sweep<T><<<nblk_(int64_t(R) * nblk * 32, 128), 128, sm, st>>>(
-                kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, s->d_tile_off, nblk, s->nunk, s->nchunks,
-                p->nb, tiles, dinv, s->d_slot, R, u);
+                s->d_blk_off, s->d_tile_off, nblk, s->nunk, s->nchunks, tiles, dinv, s->d_slot, R, u);
         } else if (s->W < kWideMax) {
             const int wt = (s->W + 1 + 31) / 32 * 32;
             const C<T> *band, *bandc;
