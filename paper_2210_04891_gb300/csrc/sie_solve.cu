@@ -671,8 +671,8 @@ template <typename V> __device__ __forceinline__ V shfl_c(V v, int src) {
 }
 
 // Band solve L d L^T u = rhs of one conductor block for one right-hand side,
-// one warp (requires W <= 31), after assembling rhs_i = -sum over the incident
-// branches of s * kappa_e.
+// one warp (requires W <= 31), in place on the right-hand sides k_pc_rhs
+// assembled (rhs_i = -sum over the incident branches of s * kappa_e).
 //
 // The sweeps keep a circular window in registers: lane (row mod 32) holds the
 // running value of its row for the 32 rows from the current pivot on.  A step
@@ -682,7 +682,8 @@ template <typename V> __device__ __forceinline__ V shfl_c(V v, int src) {
 // of 32 pivots, tile[lane][step] (pitch 33) is the entry lane `lane` applies at
 // step `step` (zero where it has none), so a step reads its entry with one
 // shared-memory load at a fixed offset, conflict-free, and no index
-// arithmetic.  Tiles are copied into shared memory two chunks ahead.
+// arithmetic.  Each warp keeps pc_nbuf tile buffers; the tile of chunk c + NB
+// is requested as soon as chunk c is done.
 constexpr int PC_CH = 32;
 constexpr int PC_TP = 33;                          // tile pitch (complex)
 constexpr int PC_TILE = PC_CH * PC_TP;             // complex per tile
