@@ -449,6 +449,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        from oracle.graph import build_loops
         nthreads = os.cpu_count()
         t0 = time.perf_counter()
         rate, sample, t_full = cpu_oracle_rate(args.workload, steps=args.steps, warmup=args.warmup)
@@ -456,7 +457,11 @@ def main():
         line = {"impl": "reference", "metric": metric, "value": rate, "unit": "matvec/s", "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_full,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": w["name"], "rhs_per_step": 1},
+                "data": "synthetic",
+                "config": {"workload": w["name"], "triangles": int(m.nt), "loops": int(build_loops(m).nl),
+                           "grid": list(w["grid"]), "rhs_per_step": 1, "frequencies": len(freqs), "ports": nports,
+                           "step": "y = A Z_b A^T x (FP64 oracle, one right-hand side per step)",
+                           "parallelism": "host cores"},
                 "cpu_baseline": {"value": rate, "unit": "matvec/s", "cores": nthreads, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": rate, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
