@@ -747,24 +747,28 @@ __device__ __forceinline__ void pc_stage_tile(C<T> *dst, const C<T> *src, int la
 
 // One step of a sweep: pivot j of the chunk; tl = this lane's tile row.  The
 // update w - l xi is fused (four FMAs); the pivot's lane keeps xi and takes pf.
+// t is every lane's updated value before that hand-over.  The pivot lane of the
+// next step was not this step's pivot, so its t equals its w, and the broadcast
+// reads t: the select stays off the chain from one pivot to the next.
 template <typename T>
-__device__ __forceinline__ void pc_step(const C<T> *tl, int j, int lane, C<T> &w, const C<T> &pf, C<T> &done) {
+__device__ __forceinline__ void pc_step(const C<T> *tl, int j, int lane, C<T> &w, C<T> &t, const C<T> &pf,
+                                        C<T> &done) {
     const C<T> l = tl[j];
-    const C<T> xi = shfl_c(w, j);
-    const T tx = fma(-l.x, xi.x, fma(l.y, xi.y, w.x));
-    const T ty = fma(-l.x, xi.y, fma(-l.y, xi.x, w.y));
+    const C<T> xi = shfl_c(t, j);
+    t.x = fma(-l.x, xi.x, fma(l.y, xi.y, w.x));
+    t.y = fma(-l.x, xi.y, fma(-l.y, xi.x, w.y));
     const bool me = lane == j;
     done.x = me ? xi.x : done.x;
     done.y = me ? xi.y : done.y;
-    w.x = me ? pf.x : tx;
-    w.y = me ? pf.y : ty;
+    w.x = me ? pf.x : t.x;
+    w.y = me ? pf.y : t.y;
 }
 // the 32 steps of a full chunk, unrolled at compile time
 template <typename T, int J>
-__device__ __forceinline__ void pc_chunk(const C<T> *tl, int lane, C<T> &w, const C<T> &pf, C<T> &done) {
+__device__ __forceinline__ void pc_chunk(const C<T> *tl, int lane, C<T> &w, C<T> &t, const C<T> &pf, C<T> &done) {
     if constexpr (J < PC_CH) {
-        pc_step<T>(tl, J, lane, w, pf, done);
-        pc_chunk<T, J + 1>(tl, lane, w, pf, done);
+        pc_step<T>(tl, J, lane, w, t, pf, done);
+        pc_chunk<T, J + 1>(tl, lane, w, t, pf, done);
     }
 }
 
@@ -819,7 +823,7 @@ __global__ void __launch_bounds__(128, 2) k_pc_sweep(
         asm volatile("cp.async.commit_group;\n" ::);
     }
     // ---------------- forward: y_{i+d} -= L[i+d][i] y_i, then y_i /= d_i at the store
-    C<T> w = lane < n ? x[lane] : zero, pf = lane + 32 < n ? x[lane + 32] : zero, done = zero;
+    C<T> w = lane < n ? x[lane] : zero, pf = lane + 32 < n ? x[lane + 32] : zero, done = zero, t = w;
     int bs = 0;   // buffer of chunk c: c mod NB
     for (int64_t c = 0; c < nch; ++c) {
         const int64_t base = c * PC_CH;
@@ -829,9 +833,9 @@ __global__ void __launch_bounds__(128, 2) k_pc_sweep(
         __syncwarp();
         const C<T> *tl = buf + bs * PC_TILE + lane * PC_TP;
         if (base + PC_CH <= n) {
-            pc_chunk<T, 0>(tl, lane, w, pf, done);
+            pc_chunk<T, 0>(tl, lane, w, t, pf, done);
         } else {
-            for (int j = 0; j < int(n - base); ++j) pc_step<T>(tl, j, lane, w, pf, done);
+            for (int j = 0; j < int(n - base); ++j) pc_step<T>(tl, j, lane, w, t, pf, done);
         }
         if (base + lane < n) x[base + lane] = cmul(done, di);
         pf = pn;
@@ -851,6 +855,7 @@ __global__ void __launch_bounds__(128, 2) k_pc_sweep(
     w = n - 1 - lane >= 0 ? x[n - 1 - lane] : zero;
     pf = n - 33 - lane >= 0 ? x[n - 33 - lane] : zero;
     done = zero;
+    t = w;
     bs = 0;
     for (int64_t c = 0; c < nch; ++c) {
         const int64_t top = n - 1 - c * PC_CH;          // pivot of step j = 0
@@ -859,9 +864,9 @@ __global__ void __launch_bounds__(128, 2) k_pc_sweep(
         __syncwarp();
         const C<T> *tl = buf + bs * PC_TILE + lane * PC_TP;
         if (top - (PC_CH - 1) >= 0) {
-            pc_chunk<T, 0>(tl, lane, w, pf, done);
+            pc_chunk<T, 0>(tl, lane, w, t, pf, done);
         } else {
-            for (int j = 0; j <= int(top); ++j) pc_step<T>(tl, j, lane, w, pf, done);
+            for (int j = 0; j <= int(top); ++j) pc_step<T>(tl, j, lane, w, t, pf, done);
         }
         if (top - lane >= 0) x[top - lane] = done;   // final values in place (every row still to be read lies below)
         pf = pn;
