@@ -59,7 +59,13 @@ def peaks():
 
 # ------------------------------------------------------------------ algorithmic work per stage launch
 
-SM_COUNT, FP32_LANES_PER_SM = 152, 128      # GB300: 2 dies x 76 SMs, 128 FP32 FMA lanes per SM
+FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM (4 sub-partitions x 32) on Blackwell
+
+
+def sm_count():
+    """SMs of the current device, read from the device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu capture of the
 # current kernel, with the number of grids (3 x right-hand sides) of that capture; the
@@ -68,9 +74,19 @@ SM_COUNT, FP32_LANES_PER_SM = 152, 128      # GB300: 2 dies x 76 SMs, 128 FP32 F
 MEASURED_TRAFFIC = {"fft_yz": (347.94e6, 48)}   # k_plane_conv<128, 64>, 2 frequencies x 8 ports
 
 
-def alu_peak_tflops(sm_mhz):
+def alu_peak_tflops(sm_mhz, nsm):
     """FP32 FMA peak of the CUDA cores: SMs x lanes x 2 flop x SM clock."""
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    return nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def plane_flops(Ny, Nz, My, Mz):
+    """Flops of one x-frequency plane of the (y, z) convolution, counted as
+    5 n log2 n per complex FFT of length n over the lines that carry data: the
+    forward z transforms of the Ny input rows (rows Ny..My-1 are zero), the
+    forward y transforms of all Mz columns, the real kernel product (2 flops a
+    point), the inverse y transforms of all columns, and the inverse z
+    transforms of the Ny rows that are kept."""
+    return (2 * Ny * 5 * Mz * np.log2(Mz) + 2 * Mz * 5 * My * np.log2(My) + 2 * My * Mz)
 
 
 def stage_work(stage, c):
@@ -85,11 +101,10 @@ def stage_work(stage, c):
     if stage == "fft_x_fwd":          # grid read, x-padded grid written
         return "hbm", 3 * R * (Ng + 2 * Ng) * cb, "B"
     if stage == "fft_yz":
-        # per x-frequency plane: forward and inverse My x Mz complex FFTs at the standard
-        # 5 N log2 N flops each, and the real kernel product (2 flops per point); the kernel
-        # is instruction-issue bound (ncu), not HBM bound (its bytes: 3R * 4 N_g * c)
-        npl = My * Mz
-        return "alu", 3 * R * 2 * Nx * (2 * 5 * npl * np.log2(npl) + 2 * npl), "flop"
+        # per x-frequency plane (2 Nx of them per grid): plane_flops; the kernel is bound by
+        # instruction issue on the FP32 pipe and shared memory (ncu), not by HBM (its bytes:
+        # stage_bytes below)
+        return "alu", 3 * R * 2 * Nx * plane_flops(My // 2, Mz // 2, My, Mz), "flop"
     if stage == "fft_x_inv":          # x-padded grid read, grid written
         return "hbm", 3 * R * (2 * Ng + Ng) * cb, "B"
     if stage == "project":
@@ -113,6 +128,15 @@ def stage_work(stage, c):
         return "hbm", R * nt * 3 * 16 + R * nl * 16, "B"
     if stage == "precond_apply":
         return "hbm", 2 * R * nl * 16, "B"
+    return None
+
+
+def stage_bytes(stage, c):
+    """Unique HBM bytes of a stage whose primary bound is not HBM, for the
+    second roofline basis: the (y, z) planes read the x-transformed grids
+    (2 N_g values per grid) and write them back."""
+    if stage == "fft_yz":
+        return 3 * c["R"] * 4 * c["Ng"] * c["cb"]
     return None
 
 
@@ -567,8 +591,10 @@ def main():
             psrc = f"{src} bf16 x 1.1/2.25 (tf32 nominal ratio)"
         else:
             mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-            achieved, peak, u = amount / sec / 1e12, alu_peak_tflops(mhz), "TFLOP/s"
-            psrc = f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {mhz:.0f} MHz"
+            nsm = sm_count()
+            achieved, peak, u = amount / sec / 1e12, alu_peak_tflops(mhz, nsm), "TFLOP/s"
+            psrc = (f"derived: {nsm} SMs (device query) x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
+                    f"{mhz:.0f} MHz (sampled max SM clock)")
         traffic = None
         if dom in MEASURED_TRAFFIC:
             tb, grids = MEASURED_TRAFFIC[dom]
@@ -577,6 +603,12 @@ def main():
                     "traffic": traffic, "kernel": dom, "peak_source": psrc,
                     "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": ms_dom / n_dom,
                     "timed_in": "stage-timed run of the same step (%d steps)" % Kp}
+        sb = stage_bytes(dom, ctx)
+        if sb:
+            # the same launch on the HBM basis: unique bytes / launch time against the copy bandwidth
+            roofline["hbm_basis"] = {"achieved": sb / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                                     "frac": sb / sec / 1e9 / hbm, "bytes_per_launch": sb,
+                                     "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
         for s in stage_table:
             wk = stage_work(s, ctx)
             if wk:
@@ -626,7 +658,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, sample, _ = cpu_oracle_rate(args.workload, steps=2, warmup=0)
+        # one warm-up product builds the oracle's sparse near matrix (it is built lazily on the
+        # first product), so the timed samples are products only, as in the reference arm
+        rate, sample, _ = cpu_oracle_rate(args.workload, steps=5, warmup=1)
         cpu = {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
 
     if rank == 0:

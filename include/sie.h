@@ -401,14 +401,20 @@ int pfft_convolve_lossy(pfft_plan *p, void *grid, int32_t nbatch, double omega, 
  * take cudaMalloc's synchronisation and latency, frameworks that own the
  * allocator).  Same arguments and result as pfft_convolve.  Its scratch is one
  * file-scope device array of 4 MiB that every GPU loading the library holds
- * until exit; a grid whose copy zero-padded along x (2N_x * N_y * N_z complex
- * values of the precision) exceeds it is rejected with SIE_ERR_ARG.  Larger
- * batches are processed in pieces that fit.  The first call on a device looks
- * up the array's device address once (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  All calls share
- * the one array, so calls that overlap on the GPU (other streams, other host
- * threads) race and corrupt each other's results; nothing in the array needs
- * clearing between calls. */
+ * until exit.  One grid needs, in values of the precision (16 B FP64, 8 B
+ * mixed): 2N_x * N_y * N_z (the copy zero-padded along x) when its padded
+ * (y, z) plane fits one CTA, and 2N_x * (N_y + 2N_y) * N_z (that copy and its
+ * y transform) when it does not (2N_y * 2N_z > 8192, N_y or N_z above 128,
+ * or 3 N_y (2N_z + 1) FP64 complex values above 200 KiB); a grid needing more
+ * than 4 MiB is rejected with SIE_ERR_ARG.
+ * Larger batches are processed in pieces that fit.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point on a device
+ * after resetting it (cudaDeviceReset).  The call synchronises cuda_stream
+ * before it returns.  All calls share the one array, so calls that overlap on
+ * the GPU (other streams, other host threads) race and corrupt each other's
+ * results; nothing in the array needs clearing between calls. */
 int pfft_convolve_noalloc(pfft_plan *p, void *grid, int32_t nbatch, int32_t prec, void *cuda_stream);
 
 /* Stage timing (tracing).  When enabled, every stage of pfft_matvec,

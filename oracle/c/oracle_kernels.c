@@ -3,7 +3,8 @@
  * only; see oracle/__init__.py).  They compute exactly what
  * oracle.integrals.pair_blocks and oracle.pfft.Pfft.grid_blocks compute, in
  * FP64, one triangle pair at a time, and are pinned against those numpy
- * versions by tests/test_oracle_native.py.
+ * versions by tests/test_oracle_integrals.py::test_native_potentials_match
+ * and tests/test_oracle_pfft.py::test_native_grid_blocks_match.
  *
  * orc_pair_blocks  : Eq. (Zb) inductive 3x3 block of a triangle pair, inner
  *                    integral over the second triangle in closed form (sum over

@@ -106,3 +106,20 @@ def test_non_manifold_rejected():
     mm = Mesh(xyz=xyz, tri=tri, cond=np.zeros(9, np.int32), sigma=np.array([1.0]))
     with pytest.raises(NonManifold):
         build_loops(mm, ports=[])
+
+
+def test_loops_per_triangle_pdn_table():
+    # Sec. III-B: on a closed surface every triangle has three edges shared by two,
+    # so b = 1.5 n and l = b - n + s + p = n/2 + s + p; the paper's PDN table (Sec. V-D)
+    # prints loops close to half the triangles for every array size
+    with open(os.path.join(GOLD, "pdn_table2.json")) as f:
+        gold = json.load(f)
+    for nt, nl in zip(gold["triangles"], gold["loops"]):
+        assert 0.5 <= nl / nt < 0.55
+    # the oracle's graph on a closed two-plane structure joined by vias, with ports:
+    # contracting the contacts removes their internal edges, so l falls just below n/2
+    m = synth.tiny_pdn()
+    L = build_loops(m)
+    assert L.nl == L.nb - L.n_nodes + L.n_comp + L.n_ports
+    assert 0.49 <= L.nl / m.nt < 0.55
+    check_invariants(m, L)

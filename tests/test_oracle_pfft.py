@@ -115,3 +115,16 @@ def test_target_rows_equal_full_rows():
     assert np.abs(yp[br] - yf[br]).max() < 1e-13 * np.abs(yf[br]).max()
     other = np.setdiff1d(np.arange(O.nb), np.unique(np.nonzero(np.isin(O.br_tri, O.br_tri[br]))[0]))
     assert np.abs(yp[other] - yf[other]).min() > 1e-9 * np.abs(yf).max()
+
+
+def test_native_grid_blocks_match(bar):
+    # the plain C loop of the grid blocks (used for speed) against the numpy
+    # version written out node by node, on every 9th near pair of the bar
+    # (self, edge- and vertex-adjacent and separated pairs)
+    m, L = bar
+    P = Pfft(m, L, PfftParams(grid=(8, 4, 4)))
+    ti, tj = P.near_i[::9], P.near_j[::9]
+    a = P.grid_blocks(ti, tj, native=False)
+    b = P.grid_blocks(ti, tj, native=True)
+    assert a.shape == b.shape and a.shape[0] > 100 and np.any(ti == tj) and np.any(ti != tj)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()

@@ -49,18 +49,57 @@ def test_noalloc_matches_convolve_twice(prec, tol):
     assert bytes1 >= bytes0
 
 
-def test_noalloc_fresh_plan_allocates_nothing():
+@pytest.mark.parametrize("prec,tol", [(N.PREC_FP64, 1e-13), (N.PREC_MIXED, 1e-6)])
+def test_noalloc_fresh_plan_allocates_nothing(prec, tol):
+    # a plan that has never convolved: the no-allocation call must neither grow its
+    # memory nor differ from the allocating call made afterwards
     m = synth.tiny_bar()
     M = api.Mesh.from_synth(m)
     L = api.Loops(M, m.ports)
     P = api.Plan(M, L, dict(grid=(8, 4, 4), order=3, near_factor=4.0, near_min_diam=2.0, n_touch=8, h0=0.0))
     before = P.info()["device_bytes"]
-    g = torch.from_numpy(synth.complex_gaussian(8 * 4 * 4, 3, seed=2).reshape(3, 8, 4, 4)).cuda()
+    dt = torch.complex128 if prec == N.PREC_FP64 else torch.complex64
+    g = torch.from_numpy(synth.complex_gaussian(8 * 4 * 4, 3, seed=2).reshape(3, 8, 4, 4)).to(dt).cuda()
+    x = g.clone()
     ref = g.clone()
-    call_noalloc(P, g, N.PREC_FP64)
-    call_noalloc(P, ref, N.PREC_FP64)
+    call_noalloc(P, g, prec)
+    call_noalloc(P, ref, prec)
     assert torch.equal(g, ref)
     assert P.info()["device_bytes"] == before
+    conv = api.pfft_convolve(P, x, prec).cpu().numpy()
+    got = g.cpu().numpy()
+    assert np.abs(got - conv).max() < tol * np.abs(conv).max()
+
+
+def _plan(mesh, grid):
+    M = api.Mesh.from_synth(mesh)
+    L = api.Loops(M, mesh.ports)
+    return api.Plan(M, L, dict(grid=grid, order=3, near_factor=1.0, near_min_diam=1.0, n_touch=4, h0=0.0))
+
+
+def test_noalloc_batch_in_pieces():
+    # FP64 64 x 16 x 16: one grid's x-padded copy is 512 KiB, so 8 grids fit the
+    # 4 MiB scratch and a batch of 10 runs as two pieces
+    P = _plan(synth.tiny_bar(), (64, 16, 16))
+    rng = np.random.default_rng(11)
+    for call in range(2):
+        g = rng.standard_normal((10, 64, 16, 16)) + 1j * rng.standard_normal((10, 64, 16, 16))
+        ref = api.pfft_convolve(P, torch.from_numpy(g).cuda(), N.PREC_FP64).cpu().numpy()
+        got = call_noalloc(P, torch.from_numpy(g).cuda(), N.PREC_FP64).cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max(), call
+
+
+def test_noalloc_large_plane():
+    # 8 x 256 x 32: the padded (y, z) plane (512 x 64) does not fit one CTA, so the
+    # scratch also holds the y transform: 16 * (256 + 512) * 32 values * 8 B = 3 MiB
+    P = _plan(synth.tiny_bar(), (8, 256, 32))
+    rng = np.random.default_rng(12)
+    for call in range(2):
+        g = rng.standard_normal((2, 8, 256, 32)) + 1j * rng.standard_normal((2, 8, 256, 32))
+        x = torch.from_numpy(g).to(torch.complex64)
+        ref = api.pfft_convolve(P, x.cuda(), N.PREC_MIXED).cpu().numpy()
+        got = call_noalloc(P, x.cuda(), N.PREC_MIXED).cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max(), call
 
 
 def test_noalloc_rejects_oversized_grid():
