@@ -216,7 +216,7 @@ class Pfft:
         Q = self.rq.shape[1]
         off = np.stack(np.meshgrid(np.arange(O), np.arange(O), np.arange(O), indexing="ij"),
                        axis=-1).reshape(-1, 3)                       # [O^3, 3]
-        out = np.zeros((len(ti), 3, 3))
+        out = np.zeros((len(ti), 3, 3), dtype=self.Hpad.dtype)   # complex for a complex kernel table
         for s0 in range(0, len(ti), 200):
             a = ti[s0:s0 + 200]
             b = tj[s0:s0 + 200]
