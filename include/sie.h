@@ -49,7 +49,7 @@ enum {
 
 enum { SIE_SPACE_LOOP = 0, SIE_SPACE_BRANCH = 1 };
 enum { SIE_PREC_FP64 = 0, SIE_PREC_MIXED = 1 };
-enum { SIE_KERNEL_STATIC = 0 };
+enum { SIE_KERNEL_STATIC = 0, SIE_KERNEL_LOSSY = 1 };
 
 typedef struct sie_mesh sie_mesh;
 typedef struct sie_loops sie_loops;
@@ -83,7 +83,9 @@ typedef struct {
     double near_factor;    /* near radius = max(near_factor * max h,           */
     double near_min_diam;  /*                   near_min_diam * max diameter)  */
     int32_t n_touch;       /* outer Gauss order for pairs sharing a vertex     */
-    int32_t kernel;        /* SIE_KERNEL_STATIC: 1/(4 pi R)                    */
+    int32_t kernel;        /* SIE_KERNEL_STATIC: 1/(4 pi R) (Eq. StaticGF);
+                              SIE_KERNEL_LOSSY: exp(-j k R)/(4 pi R) of the
+                              conductors' own conductivity (see pfft_matvec)  */
     double h0;             /* kernel value at zero grid offset (result does not
                               depend on it; kept for the independence check)   */
 } pfft_params;
@@ -187,7 +189,24 @@ int pfft_plan_set_surface_model(pfft_plan *p, const double *t_eff, int32_t ncond
  * Z_s/c_L combination)
  * in double-float (FP32 pairs, about 48 significant bits); y is complex128 in
  * both.  x and y must not overlap.  Scratch is
- * plan-owned and grown on demand (SIE_ERR_OOM if that fails). */
+ * plan-owned and grown on demand (SIE_ERR_OOM if that fails).
+ *
+ * Plans created with pfft_params.kernel = SIE_KERNEL_LOSSY use the
+ * lossy-conductor kernel exp(-j k R)/(4 pi R) in place of 1/(4 pi R) in the
+ * inductive term and in all four pFFT steps, k = (1 - j)/delta with
+ * delta = sqrt(2 / (w mu0 sigma)) the skin depth at each right-hand side's
+ * w = omega[r] (> 0) and the conductors' conductivity (one value shared by
+ * every conductor, else pfft_plan_create fails with SIE_ERR_ARG); the paper
+ * states only the static kernel (Eq. StaticGF), this is the interior kernel of
+ * the same MQS equations.  The direct near blocks are the static closed-form
+ * blocks plus int int f.f' (exp(-jkR) - 1)/R by the product of the 7-point
+ * Radon rule on both triangles (accurate while |k| times the panel diameter is
+ * at most about one; beyond, the panels do not resolve the kernel).  Per
+ * distinct w the plan builds and caches (up to 64 frequencies, least recently
+ * used replaced) the complex kernel spectrum and the complex pre-corrected near
+ * blocks, n_near x 9 x 24 bytes plus (N_x+1)(N_y+1)(N_z+1) x 24 bytes: the first
+ * call with a new w synchronises cuda_stream and allocates.  The near field runs
+ * on the CUDA cores in both precisions. */
 int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double *omega,
                 int32_t space, int32_t prec, void *cuda_stream);
 

@@ -147,7 +147,7 @@ def _c_params(p):
     cp.near_factor = float(p["near_factor"])
     cp.near_min_diam = float(p["near_min_diam"])
     cp.n_touch = int(p["n_touch"])
-    cp.kernel = N.KERNEL_STATIC
+    cp.kernel = int(p.get("kernel", N.KERNEL_STATIC))
     cp.h0 = float(p["h0"])
     return cp
 

@@ -155,6 +155,8 @@ extern "C" int sie_batch_create(pfft_plan *const *plans, int32_t n, sie_batch **
     for (int32_t i = 0; i < n; ++i) {
         if (!plans[i]) return fail(SIE_ERR_ARG, "sie_batch_create: NULL plan");
         if (plans[i]->device != plans[0]->device) return fail(SIE_ERR_ARG, "sie_batch_create: plans on different devices");
+        if (plans[i]->params.kernel != SIE_KERNEL_STATIC)
+            return fail(SIE_ERR_ARG, "sie_batch_create: batches take plans of the static kernel");
         for (int32_t j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return fail(SIE_ERR_ARG, "sie_batch_create: a plan appears twice");
     }

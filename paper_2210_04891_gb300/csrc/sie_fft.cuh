@@ -481,10 +481,14 @@ template <int N1, int N2> struct ZRows {
     static constexpr int pitch = N1 * N2 + 1;
 };
 
+// Htab / gslot (both NULL for one spectrum Hp shared by every grid): grid g of
+// the buffer uses the spectrum Htab[gslot[g]] (the lossy kernel, one spectrum
+// per angular frequency of the grid's right-hand side).
 template <typename T, int N1, int N2, typename HT>
 __global__ void __launch_bounds__(256) k_fft_zconv(C<T> *__restrict__ buf, int lgMx, int lgMy,
                                                    const HT *__restrict__ Hp, const C<T> *__restrict__ tf,
-                                                   const C<T> *__restrict__ ti) {
+                                                   const C<T> *__restrict__ ti, const HT *const *__restrict__ Htab,
+                                                   const int32_t *__restrict__ gslot) {
     constexpr int Mz = N1 * N2, Nz = Mz / 2, H1 = N1 / 2, RPC = ZRows<N1, N2>::RPC, pitch = ZRows<N1, N2>::pitch;
     constexpr int LGNZ = Nz == 4 ? 2 : Nz == 8 ? 3 : Nz == 16 ? 4 : Nz == 32 ? 5 : Nz == 64 ? 6 : Nz == 128 ? 7 : 8;
     static_assert((1 << LGNZ) == Nz, "row length");
@@ -515,7 +519,8 @@ __global__ void __launch_bounds__(256) k_fft_zconv(C<T> *__restrict__ buf, int l
         const int Mx = 1 << lgMx, My = 1 << lgMy;
         const int64_t row = row0 + r;
         const int ky = int(row & (My - 1)), kx = int((row >> lgMy) & (Mx - 1));
-        const HT *Hr = Hp + (int64_t(fold_index(kx, Mx)) * (My / 2 + 1) + fold_index(ky, My)) * (Mz / 2 + 1);
+        const HT *Hg = Htab ? Htab[gslot[row >> (lgMx + lgMy)]] : Hp;
+        const HT *Hr = Hg + (int64_t(fold_index(kx, Mx)) * (My / 2 + 1) + fold_index(ky, My)) * (Mz / 2 + 1);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) v[k2] = kernel_mul<T>(v[k2], Hr[fold_index(k1 + N1 * k2, Mz)]);
         dft_reg<T, N2, true>(v);
@@ -735,11 +740,13 @@ __device__ __forceinline__ void yz_mid(C<T> *P, int pitch, int lgMz, const HT *_
 // plane fills the shared memory of one SM).
 // Hp: kernel spectrum [fold(kx)][fold(ky)][fold(kz)], scaled by 1/(Mx My Mz):
 // real (HT = T, the static kernel) or complex (HT = C<T>, the lossy kernel).
+// Htab / gslot: as in k_fft_zconv (grid g = blockIdx.x / Mx uses Htab[gslot[g]]).
 template <typename T, int NT, typename HT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fft_yzc(C<T> *__restrict__ buf, int lgMx, int My, int Mz,
                                                  const HT *__restrict__ Hp, const C<T> *__restrict__ tfy,
                                                  const C<T> *__restrict__ tiy, const C<T> *__restrict__ tfz,
-                                                 const C<T> *__restrict__ tiz) {
+                                                 const C<T> *__restrict__ tiz, const HT *const *__restrict__ Htab,
+                                                 const int32_t *__restrict__ gslot) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pitch = Mz + 1, Ny = My / 2, Nz = Mz / 2;
     const int lgNy = ilog2(Ny), lgMz = ilog2(Mz);
@@ -748,7 +755,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fft_yzc(C<T> *__
     C<T> *P = reinterpret_cast<C<T> *>(smem_raw);
     C<T> *Qb = P + My * pitch;
     C<T> *plane = buf + int64_t(blockIdx.x) * Ny * Nz;
-    const HT *Hk = Hp + int64_t(fold_index(kx, Mx)) * (My / 2 + 1) * (Mz / 2 + 1);
+    const HT *Hg = Htab ? Htab[gslot[blockIdx.x >> lgMx]] : Hp;
+    const HT *Hk = Hg + int64_t(fold_index(kx, Mx)) * (My / 2 + 1) * (Mz / 2 + 1);
     SIE_SPLIT_DISPATCH(Mz, (yz_f1<T, N1, N2>(plane, P, pitch, Ny, tfz)));
     __syncthreads();
     SIE_SPLIT_DISPATCH(Mz, (yz_f2<T, N1, N2>(P, Qb, pitch, lgNy)));

@@ -343,35 +343,15 @@ __global__ void __launch_bounds__(256) k_regroup(const C<T> *__restrict__ grid, 
     }
 }
 
-// Per triangle T and right-hand side r:
-//   f_T[k] = sum_{T' near T} sum_l L_d(T,T')[k][l] c_T'[l]          (Eq. Lb, pre-corrected)
-//          + sum_n sum_d W(n,T)[d][k] phi_g[d][n]                   (interpolation, I = B^T)
-//   y_T[k] = Z_s sum_l G_T[k][l] c_T[l] + j c_L f_T[k]             (Eq. Zb, FP64)
-// One warp per (T, slab of 32 V J right-hand sides), lanes over right-hand
-// sides; each block record is read once per slab.  y_tri layout [R][nt][3].
+// y_T[k] = Z_s sum_l G_T[k][l] c_T[l] + j c_L f_T[k] (Eq. Zb) for the right-hand
+// sides rl + 32 V j + v < R of a warp's slab, f_T = acc (FP64, or double-float
+// from the FP32 field in the mixed form).
 template <typename T, int V, int J>
-__global__ void __launch_bounds__(256)
-    k_tri_gather(const int64_t *__restrict__ near_ptr, const Rec<T> *__restrict__ near_rec,
-                 const int64_t *__restrict__ pt_ptr, const Rec<T> *__restrict__ pt_rec, const C<T> *__restrict__ cT,
-                 const C<T> *__restrict__ phiT, const double *__restrict__ gram, const int32_t *__restrict__ cond,
-                 const double *__restrict__ coef, const float2 *__restrict__ coef_dd, int ncond, int64_t nt,
-                 int32_t R, int32_t nslab, TourE<T> *__restrict__ y_tri) {
-    constexpr int SLAB = 32 * V * J;
-    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= nt * nslab) return;
-    const int64_t t = gw / nslab;
-    const int32_t rbase = int32_t(gw % nslab) * SLAB;
-    const int32_t rl = rbase + V * lane;
-    C<T> acc[3][J][V];
-    zero<T, V, J>(acc);
-    if (rbase + SLAB <= R) {
-        gather_rows<T, V, J, true>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
-        gather_rows<T, V, J, true>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
-    } else {
-        gather_rows<T, V, J, false>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
-        gather_rows<T, V, J, false>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
-    }
+__device__ __forceinline__ void tri_epilogue(const C<T> (&acc)[3][J][V], int64_t t, int32_t rl, int32_t R,
+                                             const C<T> *__restrict__ cT, const double *__restrict__ gram,
+                                             const int32_t *__restrict__ cond, const double *__restrict__ coef,
+                                             const float2 *__restrict__ coef_dd, int ncond, int64_t nt,
+                                             TourE<T> *__restrict__ y_tri) {
     const int cd = cond[t];
     if constexpr (sizeof(T) == 4) {
         // mixed form: Gram term in FP32 like the field, Eq. Zb in double-float
@@ -426,6 +406,89 @@ __global__ void __launch_bounds__(256)
                 }
             }
     }
+}
+
+// Per triangle T and right-hand side r:
+//   f_T[k] = sum_{T' near T} sum_l L_d(T,T')[k][l] c_T'[l]          (Eq. Lb, pre-corrected)
+//          + sum_n sum_d W(n,T)[d][k] phi_g[d][n]                   (interpolation, I = B^T)
+//   y_T[k] = Z_s sum_l G_T[k][l] c_T[l] + j c_L f_T[k]             (Eq. Zb, FP64)
+// One warp per (T, slab of 32 V J right-hand sides), lanes over right-hand
+// sides; each block record is read once per slab.  y_tri layout [R][nt][3].
+template <typename T, int V, int J>
+__global__ void __launch_bounds__(256)
+    k_tri_gather(const int64_t *__restrict__ near_ptr, const Rec<T> *__restrict__ near_rec,
+                 const int64_t *__restrict__ pt_ptr, const Rec<T> *__restrict__ pt_rec, const C<T> *__restrict__ cT,
+                 const C<T> *__restrict__ phiT, const double *__restrict__ gram, const int32_t *__restrict__ cond,
+                 const double *__restrict__ coef, const float2 *__restrict__ coef_dd, int ncond, int64_t nt,
+                 int32_t R, int32_t nslab, TourE<T> *__restrict__ y_tri) {
+    constexpr int SLAB = 32 * V * J;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= nt * nslab) return;
+    const int64_t t = gw / nslab;
+    const int32_t rbase = int32_t(gw % nslab) * SLAB;
+    const int32_t rl = rbase + V * lane;
+    C<T> acc[3][J][V];
+    zero<T, V, J>(acc);
+    if (rbase + SLAB <= R) {
+        gather_rows<T, V, J, true>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
+        gather_rows<T, V, J, true>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
+    } else {
+        gather_rows<T, V, J, false>(near_rec, near_ptr[t], near_ptr[t + 1], cT, R, rl, acc);
+        gather_rows<T, V, J, false>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
+    }
+    tri_epilogue<T, V, J>(acc, t, rl, R, cT, gram, cond, coef, coef_dd, ncond, nt, y_tri);
+}
+
+// The lossy kernel (pfft_params.kernel = SIE_KERNEL_LOSSY): as k_tri_gather with
+// complex near blocks that depend on the frequency,
+//   f_T[k] = sum_{T' near T} sum_l L_d,k(w_r)(T,T')[k][l] c_T'[l]
+//          + sum_n sum_d W(n,T)[d][k] phi_g[d][n],
+// Ltab[rslot[r]] being the blocks [n_near][3][3] of right-hand side r's
+// frequency.  One warp per (T, slab of 32 J right-hand sides), one right-hand
+// side per lane and load; lanes of one frequency read the same block.
+template <typename T, int J>
+__global__ void __launch_bounds__(256)
+    k_tri_gather_lossy(const int64_t *__restrict__ near_ptr, const int32_t *__restrict__ near_col,
+                       const C<T> *const *__restrict__ Ltab, const int32_t *__restrict__ rslot,
+                       const int64_t *__restrict__ pt_ptr, const Rec<T> *__restrict__ pt_rec,
+                       const C<T> *__restrict__ cT, const C<T> *__restrict__ phiT, const double *__restrict__ gram,
+                       const int32_t *__restrict__ cond, const double *__restrict__ coef,
+                       const float2 *__restrict__ coef_dd, int ncond, int64_t nt, int32_t R, int32_t nslab,
+                       TourE<T> *__restrict__ y_tri) {
+    constexpr int SLAB = 32 * J;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= nt * nslab) return;
+    const int64_t t = gw / nslab;
+    const int32_t rl = int32_t(gw % nslab) * SLAB + lane;
+    C<T> acc[3][J][1];
+    zero<T, 1, J>(acc);
+    const C<T> *L[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int32_t r = rl + 32 * j;
+        L[j] = r < R ? Ltab[rslot[r]] : nullptr;
+    }
+    const int64_t ld = 3 * int64_t(R);
+    for (int64_t e = near_ptr[t]; e < near_ptr[t + 1]; ++e) {
+        const C<T> *x = cT + int64_t(near_col[e]) * ld;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int32_t r = rl + 32 * j;
+            if (r >= R) continue;
+            const C<T> x0 = x[r], x1 = x[R + r], x2 = x[2 * R + r];
+            const C<T> *b = L[j] + 9 * e;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const C<T> b0 = b[3 * k], b1 = b[3 * k + 1], b2 = b[3 * k + 2];
+                acc[k][j][0].x += b0.x * x0.x - b0.y * x0.y + b1.x * x1.x - b1.y * x1.y + b2.x * x2.x - b2.y * x2.y;
+                acc[k][j][0].y += b0.x * x0.y + b0.y * x0.x + b1.x * x1.y + b1.y * x1.x + b2.x * x2.y + b2.y * x2.x;
+            }
+        }
+    }
+    gather_rows<T, 1, J, false>(pt_rec, pt_ptr[t], pt_ptr[t + 1], phiT, R, rl, acc);
+    tri_epilogue<T, 1, J>(acc, t, rl, R, cT, gram, cond, coef, coef_dd, ncond, nt, y_tri);
 }
 
 // Interpolated far field alone (mixed form, where the near blocks run on the
@@ -614,6 +677,18 @@ template <typename T, int V, int J> struct Blocks {
         SIE_LAUNCH_CHECK(p);
         return SIE_OK;
     }
+    static int tri_gather_lossy(pfft_plan *p, int32_t R, cudaStream_t st) {
+        static_assert(V == 1, "one right-hand side per lane and load");
+        const int32_t nslab = (R + SLAB - 1) / SLAB;
+        const int64_t warps = p->nt * nslab;
+        const int prec = sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED;
+        k_tri_gather_lossy<T, J><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
+            p->d_near_ptr, p->d_near_col, reinterpret_cast<const C<T> *const *>(lossy_ltab(p, prec)),
+            lossy_rslot(p), p->d_pt_ptr, pt(p), (const C<T> *)p->scr.cT, (const C<T> *)p->scr.phiT, p->d_gram,
+            p->d_cond, p->scr.coef, coef_dd(p), p->ncond, p->nt, R, nslab, (TourE<T> *)p->scr.y_tri);
+        SIE_LAUNCH_CHECK(p);
+        return SIE_OK;
+    }
     static int tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
         const int32_t nslab = (R + SLAB - 1) / SLAB;
         const int64_t warps = p->nt * nslab;
@@ -662,6 +737,11 @@ int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
 template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
     SIE_SLAB_DISPATCH(T, R, tri_gather(p, R, st));
 }
+template <typename T> int run_tri_gather_lossy(pfft_plan *p, int32_t R, cudaStream_t st) {
+    if (R <= 32) return Blocks<T, 1, 1>::tri_gather_lossy(p, R, st);
+    if (R <= 64) return Blocks<T, 1, 2>::tri_gather_lossy(p, R, st);
+    return Blocks<T, 1, 4>::tri_gather_lossy(p, R, st);
+}
 
 // Smallest right-hand-side count for the tensor-core near field (mixed form).
 constexpr int32_t kNearMmaMinRhs = 96;
@@ -691,7 +771,9 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     int rc = run_project<T>(p, R, st);
     if (rc) return rc;
     tm.reset();
-    rc = fft_conv(p, s.grid, s.spec, R, sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED, st);
+    const int prec = sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED;
+    const bool lossy = p->params.kernel == SIE_KERNEL_LOSSY;
+    rc = fft_conv(p, s.grid, s.spec, R, prec, st, lossy ? lossy_sel(p, prec) : nullptr);
     if (rc) return rc;
     tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
     {
@@ -705,7 +787,11 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     // slab costs the same however few of its columns are used, so below about
     // three quarters of a slab the CUDA-core gather is faster); otherwise one
     // CUDA-core gather
-    if (sizeof(T) == 4 && R % 2 == 0 && R >= kNearMmaMinRhs) {
+    if (lossy) {
+        // complex near blocks per frequency: one CUDA-core gather (near + interpolation + y_T)
+        tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
+        rc = run_tri_gather_lossy<T>(p, R, st);
+    } else if (sizeof(T) == 4 && R % 2 == 0 && R >= kNearMmaMinRhs) {
         rc = run_far_gather(p, R, st);          // interpolation (step 3) on the CUDA cores
         if (rc) return rc;
         tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
@@ -796,6 +882,7 @@ int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const doubl
     if (rc) return rc;
     rc = upload_coef(p, omega, nrhs, st);
     if (rc) return rc;
+    if (p->params.kernel == SIE_KERNEL_LOSSY && (rc = lossy_prepare(p, omega, nrhs, st))) return rc;
     return matvec_launch(p, x, y, nrhs, space, prec, st);
 }
 

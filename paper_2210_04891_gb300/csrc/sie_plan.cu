@@ -507,7 +507,8 @@ int launch_x(pfft_plan *p, const C<T> *in, C<T> *out, int ngrids, bool inverse, 
 
 // z rows of the large plane route: forward, kernel product, inverse, in place.
 template <typename T, int N1, int N2, typename HT>
-int launch_zconv(pfft_plan *p, C<T> *rows, int64_t nrows, const HT *Hp, cudaStream_t s) {
+int launch_zconv(pfft_plan *p, C<T> *rows, int64_t nrows, const HT *Hp, const HT *const *Htab, const int32_t *gslot,
+                 cudaStream_t s) {
     using Tb = Tables<T>;
     using Z = ZRows<N1, N2>;
     const size_t zb = size_t(Z::RPC) * Z::pitch * sizeof(C<T>);
@@ -518,7 +519,7 @@ int launch_zconv(pfft_plan *p, C<T> *rows, int64_t nrows, const HT *Hp, cudaStre
     while ((1 << lgMx) < p->Mx) ++lgMx;
     while ((1 << lgMy) < p->My) ++lgMy;
     k_fft_zconv<T, N1, N2, HT><<<unsigned(nrows / Z::RPC), 256, zb, s>>>(rows, lgMx, lgMy, Hp, Tb::tf(p, 2),
-                                                                          Tb::ti(p, 2));
+                                                                          Tb::ti(p, 2), Htab, gslot);
     return SIE_OK;
 }
 
@@ -526,14 +527,15 @@ int launch_zconv(pfft_plan *p, C<T> *rows, int64_t nrows, const HT *Hp, cudaStre
 // one CTA: y pencils forward into the second half of `spec`, z rows (forward,
 // kernel product, inverse), y pencils inverse back into the first half.
 template <typename T, typename HT>
-int launch_yz_large(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s) {
+int launch_yz_large(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, const HT *const *Htab,
+                    const int32_t *gslot, cudaStream_t s) {
     const int64_t planes = int64_t(ngrids) * p->Mx;
     C<T> *spec2 = spec + planes * p->Ny * p->Nz;
     int rc;
     SIE_SPLIT_DISPATCH_P(p->My, (rc = launch_pencils<T, N1, N2>(p, spec, spec2, planes, p->Nz, 1, false, s)));
     if (rc) return rc;
     SIE_LAUNCH_CHECK(p);
-    SIE_SPLIT_DISPATCH_P(p->Mz, (rc = launch_zconv<T, N1, N2, HT>(p, spec2, planes * p->My, Hp, s)));
+    SIE_SPLIT_DISPATCH_P(p->Mz, (rc = launch_zconv<T, N1, N2, HT>(p, spec2, planes * p->My, Hp, Htab, gslot, s)));
     if (rc) return rc;
     SIE_LAUNCH_CHECK(p);
     SIE_SPLIT_DISPATCH_P(p->My, (rc = launch_pencils<T, N1, N2>(p, spec2, spec, planes, p->Nz, 1, true, s)));
@@ -543,9 +545,10 @@ int launch_yz_large(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cuda
 }
 
 template <typename T, typename HT>
-int launch_yzc(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s) {
+int launch_yzc(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStream_t s,
+               const HT *const *Htab = nullptr, const int32_t *gslot = nullptr) {
     using Tb = Tables<T>;
-    if (p->large_plane) return launch_yz_large<T, HT>(p, spec, ngrids, Hp, s);
+    if (p->large_plane) return launch_yz_large<T, HT>(p, spec, ngrids, Hp, Htab, gslot, s);
     if constexpr (sizeof(T) == 4 && sizeof(HT) == sizeof(T)) {   // static kernel in FP32: paired form
         bool done = false;
         const int rc = plane_conv_f32(p, spec, ngrids, s, done);
@@ -559,13 +562,15 @@ int launch_yzc(pfft_plan *p, C<T> *spec, int32_t ngrids, const HT *Hp, cudaStrea
     int lgMx = 0;
     while ((1 << lgMx) < p->Mx) ++lgMx;
     k_fft_yzc<T, NT, HT><<<unsigned(ngrids * p->Mx), NT, plane_bytes, s>>>(spec, lgMx, p->My, p->Mz, Hp, Tb::tf(p, 1),
-                                                                        Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2));
+                                                                        Tb::ti(p, 1), Tb::tf(p, 2), Tb::ti(p, 2),
+                                                                        Htab, gslot);
     SIE_LAUNCH_CHECK(p);
     return SIE_OK;
 }
 
 template <typename T>
-int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s, bool lossy) {
+int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_t s, bool lossy,
+               const SpecSel *sel) {
     using Tb = Tables<T>;
     int rc;
     {
@@ -576,7 +581,11 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     }
     {
         StageTimer tm(p, SIE_STAGE_FFT_YZ, s);
-        rc = lossy ? launch_yzc<T>(p, spec, ngrids, Tb::Hl(p), s) : launch_yzc<T>(p, spec, ngrids, Tb::Hp(p), s);
+        if (sel && sel->tab)   // one lossy spectrum per grid
+            rc = launch_yzc<T, C<T>>(p, spec, ngrids, nullptr, s, reinterpret_cast<const C<T> *const *>(sel->tab),
+                                     sel->gslot);
+        else
+            rc = lossy ? launch_yzc<T>(p, spec, ngrids, Tb::Hl(p), s) : launch_yzc<T>(p, spec, ngrids, Tb::Hp(p), s);
         if (rc) return rc;
     }
     StageTimer tm(p, SIE_STAGE_FFT_X_INV, s);
@@ -586,13 +595,14 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     return SIE_OK;
 }
 
-int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s, bool lossy) {
-    if (prec == SIE_PREC_FP64) return fft_conv_t<double>(p, (double2 *)grid, (double2 *)spec, ngrids, s, lossy);
-    return fft_conv_t<float>(p, (float2 *)grid, (float2 *)spec, ngrids, s, lossy);
+int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s, bool lossy,
+               const SpecSel *sel) {
+    if (prec == SIE_PREC_FP64) return fft_conv_t<double>(p, (double2 *)grid, (double2 *)spec, ngrids, s, lossy, sel);
+    return fft_conv_t<float>(p, (float2 *)grid, (float2 *)spec, ngrids, s, lossy, sel);
 }
 
-int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s) {
-    return fft_conv_n(p, grid, spec, 3 * nrhs, prec, s);
+int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s, const SpecSel *sel) {
+    return fft_conv_n(p, grid, spec, 3 * nrhs, prec, s, sel != nullptr, sel);
 }
 
 // Reads and clears the plan's device error flags (call after the work that
@@ -640,7 +650,12 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
                                  "(N_z >= 8 when N_y = 256)");
     if (prm->n_touch < 1 || prm->n_touch > 64) return fail(SIE_ERR_ARG, "pfft_plan_create: n_touch must be 1..64");
     if (!(prm->near_factor >= 0.0) || !(prm->near_min_diam >= 0.0)) return fail(SIE_ERR_ARG, "pfft_plan_create: negative near radius");
-    if (prm->kernel != SIE_KERNEL_STATIC) return fail(SIE_ERR_ARG, "pfft_plan_create: only the static kernel is built");
+    if (prm->kernel != SIE_KERNEL_STATIC && prm->kernel != SIE_KERNEL_LOSSY)
+        return fail(SIE_ERR_ARG, "pfft_plan_create: kernel must be SIE_KERNEL_STATIC or SIE_KERNEL_LOSSY");
+    if (prm->kernel == SIE_KERNEL_LOSSY)
+        for (int32_t c = 1; c < m->ncond; ++c)
+            if (m->sigma[c] != m->sigma[0])
+                return fail(SIE_ERR_ARG, "pfft_plan_create: the lossy kernel needs one conductivity for every conductor");
 
     (void)cudaGetLastError();   // a stale error from earlier work in this thread is not ours
     pfft_plan *p = new (std::nothrow) pfft_plan;
@@ -1061,9 +1076,17 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     p->launches++;
     SIE_CUDA(cudaGetLastError());
     SIE_CUDA(cudaStreamSynchronize(s));
+    if (prm->kernel == SIE_KERNEL_LOSSY) {
+        // the per-frequency near blocks of the lossy kernel are built from the vertices
+        // and the Radon rule on first use of each frequency
+        p->d_verts = d_verts;
+        p->d_r7b = d_r7b;
+        p->d_r7w = d_r7w;
+        d_verts = d_r7b = d_r7w = nullptr;
+    }
     for (void *tmp : {(void *)d_Hpad, (void *)d_Hc, (void *)d_verts, (void *)d_area, (void *)d_r7b, (void *)d_r7w,
                       (void *)d_tgb, (void *)d_tgw, (void *)d_tri})
-        plan_free(p, tmp);
+        if (tmp) plan_free(p, tmp);
     *out = p;
     return SIE_OK;
 }
@@ -1071,6 +1094,7 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
 extern "C" void pfft_plan_destroy(pfft_plan *p) {
     if (!p) return;
     sie::plan_free_precond(p);
+    sie::plan_free_lossy(p);
     for (auto &e : p->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void *a : p->allocations) cudaFree(a);
     if (p->h_err) cudaFreeHost(p->h_err);
@@ -1156,6 +1180,31 @@ extern "C" int pfft_convolve(pfft_plan *p, void *grid, int32_t nbatch, int32_t p
 }
 
 namespace sie {
+int lossy_fill_table(pfft_plan *p, double inv_delta, double2 *Hc, cudaStream_t s) {
+    const int64_t nM = int64_t(p->Mx) * p->My * p->Mz;
+    k_fill_kernel_lossy<<<unsigned((nM + 255) / 256), 256, 0, s>>>(Hc, p->Mx, p->My, p->Mz, p->h[0], p->h[1], p->h[2],
+                                                                   p->params.h0, inv_delta);
+    SIE_LAUNCH_CHECK(p);
+    return SIE_OK;
+}
+
+int lossy_table_spectrum(pfft_plan *p, double2 *Hc, double2 *H64, float2 *H32, cudaStream_t s) {
+    const int64_t nM = int64_t(p->Mx) * p->My * p->Mz;
+    const int64_t nh = int64_t(p->Mx / 2 + 1) * (p->My / 2 + 1) * (p->Mz / 2 + 1);
+    double2 *spec = nullptr;
+    int rc = kernel_fft3(p, Hc, &spec, s);
+    if (rc) return rc;
+    k_extract_Hc<<<unsigned((nh + 255) / 256), 256, 0, s>>>(spec, H64, H32, p->Mx, p->My, p->Mz, 1.0 / double(nM));
+    p->launches++;
+    const cudaError_t e = cudaGetLastError();
+    if (spec != Hc) {
+        cudaStreamSynchronize(s);
+        plan_free(p, spec);
+    }
+    if (e != cudaSuccess) return fail(SIE_ERR_CUDA, std::string("lossy spectrum: ") + cudaGetErrorString(e));
+    return SIE_OK;
+}
+
 // Spectrum of the lossy kernel for (omega, sigma), kept until another pair is asked for.
 int lossy_spectrum(pfft_plan *p, double omega, double sigma, cudaStream_t s) {
     if (p->d_Hl64 && p->lossy_omega == omega && p->lossy_sigma == sigma) return SIE_OK;

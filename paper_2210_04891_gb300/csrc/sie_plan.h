@@ -17,6 +17,7 @@ template <typename T> struct DevBuf {
 };
 
 struct PrecondState;   // sie_solve.cu
+struct LossyCache;     // sie_lossy.cu
 
 struct Scratch {
     int32_t cap_rhs = 0;   // right-hand sides the buffers are sized for
@@ -113,9 +114,16 @@ struct pfft_plan {
     double *d_Hp64 = nullptr;
     float *d_Hp32 = nullptr;
     // lossy kernel exp(-jkR)/R: complex spectrum of the last (omega, sigma), same layout
+    // (pfft_convolve_lossy)
     double lossy_omega = -1.0, lossy_sigma = -1.0;
     double2 *d_Hl64 = nullptr;
     float2 *d_Hl32 = nullptr;
+    // the lossy kernel inside pfft_matvec (params.kernel == SIE_KERNEL_LOSSY): per-frequency
+    // spectra, near blocks and branch diagonals (sie_lossy.cu), and the geometry their
+    // set-up needs, kept on the device for the plan's lifetime
+    sie::LossyCache *lossy = nullptr;
+    double *d_verts = nullptr;          // [nt][3][3] vertices
+    double *d_r7b = nullptr, *d_r7w = nullptr;   // Radon 7-point rule (barycentric [7][3], weights [7])
     // loop basis on the device
     int32_t *d_tour_node = nullptr;     // [2 nn]
     int8_t *d_tour_enter = nullptr;     // [2 nn]
@@ -192,9 +200,17 @@ int learned_admittance(pfft_plan *p, const double *d_zs_cl, int32_t nslots, doub
 // Forget the preconditioner's cached numeric factors (rebuilt on next use).
 void invalidate_precond_factors(pfft_plan *p);
 template <typename T> const C<T> *twiddle(const pfft_plan *p, int axis);
-int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s);
+// Kernel spectra chosen per grid (the lossy kernel of pfft_matvec): grid g of a
+// convolution uses the folded complex spectrum tab[gslot[g]] (device arrays;
+// tab holds double2 or float2 pointers for the FP64 and mixed forms).
+struct SpecSel {
+    const void *const *tab = nullptr;
+    const int32_t *gslot = nullptr;
+};
+int fft_conv(pfft_plan *p, void *grid, void *spec, int32_t nrhs, int prec, cudaStream_t s,
+             const SpecSel *sel = nullptr);
 int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s,
-               bool lossy = false);
+               bool lossy = false, const SpecSel *sel = nullptr);
 int near_mma_prepare(pfft_plan *p, const std::vector<int64_t> &near_ptr, const std::vector<int32_t> &near_col,
                      cudaStream_t s);
 int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st);
@@ -203,6 +219,21 @@ int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st);
 bool plane_conv_supported(const pfft_plan *p);
 int plane_conv_f32(pfft_plan *p, float2 *spec, int32_t ngrids, cudaStream_t s, bool &done);
 int check_device_errors(pfft_plan *p);
+// Lossy kernel in pfft_matvec (sie_lossy.cu).  lossy_prepare: builds the per-frequency
+// data missing for omega[R] (on stream st, synchronising it when something is built)
+// and uploads the right-hand sides' slot tables; after it, lossy_sel / lossy_ltab
+// describe this batch.  lossy_diag: the complex branch diagonal Lt_k[e][e] of each of
+// the ns frequencies into out [ns][nb].
+int lossy_prepare(pfft_plan *p, const double *omega, int32_t R, cudaStream_t st);
+const SpecSel *lossy_sel(const pfft_plan *p, int prec);
+const void *const *lossy_ltab(const pfft_plan *p, int prec);
+const int32_t *lossy_rslot(const pfft_plan *p);
+int lossy_diag(pfft_plan *p, const double *omega, int32_t ns, double2 *out, cudaStream_t st);
+void plan_free_lossy(pfft_plan *p);
+// Complex padded table of exp(-jkR)/R (1/delta given) into Hc [Mx][My][Mz]; its folded
+// spectrum scaled by 1/(Mx My Mz) into H64 / H32 (Hc may be overwritten).
+int lossy_fill_table(pfft_plan *p, double inv_delta, double2 *Hc, cudaStream_t s);
+int lossy_table_spectrum(pfft_plan *p, double2 *Hc, double2 *H64, float2 *H32, cudaStream_t s);
 // End of a synchronous call on stream st: the error flags come back with the
 // stream's one synchronisation (pinned copy) instead of a second round trip.
 int finish_call(pfft_plan *p, cudaStream_t st);

@@ -340,16 +340,20 @@ __global__ void k_round_c(const double2 *__restrict__ a, float2 *__restrict__ b,
     if (i < n) b[i] = make_float2(float(a[i].x), float(a[i].y));
 }
 
-// 1/D_e with D_e = Z_s(sigma_e, w) G_ee + j w mu0/(4 pi) Lt_ee (Eq. Zb diagonal).
+// 1/D_e with D_e = Z_s(sigma_e, w) G_ee + j w mu0/(4 pi) Lt_ee (Eq. Zb diagonal);
+// Lt_ee is the static self term diag_L[e], or with the lossy kernel the complex
+// per-frequency term diag_Lc[f][e] (diag_Lc NULL for the static kernel).
 __global__ void k_pc_admittance(const double *__restrict__ diag_gram, const double *__restrict__ diag_L,
-                                const int32_t *__restrict__ br_cond, const double *__restrict__ zs_cl, int ncond,
-                                int64_t nb, int32_t nslots, double2 *__restrict__ a) {
+                                const double2 *__restrict__ diag_Lc, const int32_t *__restrict__ br_cond,
+                                const double *__restrict__ zs_cl, int ncond, int64_t nb, int32_t nslots,
+                                double2 *__restrict__ a) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nb * nslots) return;
     int64_t f = i / nb, e = i % nb;
     const double *cf = zs_cl + f * (2 * ncond + 1);   // (Re Z_s, Im Z_s) per conductor, then c_L / j
     const double zr = cf[2 * br_cond[e]], zi = cf[2 * br_cond[e] + 1], cl = cf[2 * ncond];
-    double dr = zr * diag_gram[e], di = zi * diag_gram[e] + cl * diag_L[e];
+    const double2 L = diag_Lc ? diag_Lc[i] : make_double2(diag_L[e], 0.0);
+    double dr = zr * diag_gram[e] - cl * L.y, di = zi * diag_gram[e] + cl * L.x;
     double den = dr * dr + di * di;
     a[i] = make_double2(dr / den, -di / den);
 }
@@ -997,9 +1001,15 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     double *d_zc = nullptr;
     SIE_CUDA(pool_alloc(p, &d_zc, zc.size() * sizeof(double), st));
     SIE_CUDA(cudaMemcpyAsync(d_zc, zc.data(), zc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zc, p->ncond,
-                                                       p->nb, ns, s->d_a);
+    double2 *d_Lc = nullptr;   // lossy kernel: complex self terms per frequency slot
+    if (p->params.kernel == SIE_KERNEL_LOSSY) {
+        SIE_CUDA(pool_alloc(p, &d_Lc, size_t(ns) * std::max<int64_t>(p->nb, 1) * sizeof(double2), st));
+        if (int rl = lossy_diag(p, uniq.data(), ns, d_Lc, st)) return rl;
+    }
+    k_pc_admittance<<<nblk_(p->nb * ns), 256, 0, st>>>(p->d_diag_gram, p->d_diag_L, d_Lc, p->d_br_cond, d_zc,
+                                                       p->ncond, p->nb, ns, s->d_a);
     SIE_LAUNCH_CHECK(p);
+    if (d_Lc) cudaFreeAsync(d_Lc, st);
     if (int rl = learned_admittance(p, d_zc, ns, s->d_a, st)) return rl;   // D' = D (1 + g)
     k_round_c<<<nblk_(p->nb * ns), 256, 0, st>>>(s->d_a, s->d_a32, p->nb * ns);
     SIE_LAUNCH_CHECK(p);

@@ -17,7 +17,7 @@ ERRORS = {-1: "SIE_ERR_ARG", -2: "SIE_ERR_NONMANIFOLD", -3: "SIE_ERR_BAD_PORT", 
           -5: "SIE_ERR_CUDA", -6: "SIE_ERR_NOT_CONVERGED", -7: "SIE_ERR_BREAKDOWN", -8: "SIE_ERR_TIMEOUT"}
 SPACE_LOOP, SPACE_BRANCH = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-KERNEL_STATIC = 0
+KERNEL_STATIC, KERNEL_LOSSY = 0, 1
 
 # every symbol include/sie.h declares
 EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basis_build", "sie_loops_destroy", "sie_loops_export",
