@@ -233,6 +233,29 @@ int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const
  * sweep beyond.  Any pointer may be NULL. */
 int pfft_precond_info(pfft_plan *p, int32_t *band_width, int64_t *unknowns, int64_t *blocks);
 
+/* Factorisation route of the preconditioner (Eq. Precond asks for a direct
+ * factorisation of P; it is applied through the nodal Laplacian of the same
+ * circuit, see pfft_precond_apply):
+ *   SIE_PC_AUTO  the band LDL^T after reverse Cuthill-McKee ordering when its
+ *                band is below 1024, else nested dissection (the default);
+ *   SIE_PC_BAND  always the band LDL^T;
+ *   SIE_PC_ND    always nested dissection: the unknowns are bisected at the
+ *                median of their positions along the longest axis, recursively
+ *                (separators from the smaller side of each cut, leaves of at
+ *                most 128 unknowns), and the Laplacian is factorised as a
+ *                multifrontal LDL^T on the device (FP64; its FP32 rounding serves
+ *                the mixed form's solves), fronts of one tree level at a time.
+ * Setting a method drops the plan's preconditioner state (rebuilt on next use).
+ * Errors: SIE_ERR_ARG for an unknown method. */
+enum { SIE_PC_AUTO = 0, SIE_PC_BAND = 1, SIE_PC_ND = 2 };
+int pfft_precond_set_method(pfft_plan *p, int32_t method);
+/* Structure of a nested-dissection factorisation (built on first use, or by this
+ * call): method_used (SIE_PC_BAND or SIE_PC_ND), fronts, nnz of the factor
+ * (complex entries per frequency), largest front and complex multiply-adds of
+ * one factorisation (all 0 for the band route).  Any pointer may be NULL. */
+int pfft_precond_nd_info(pfft_plan *p, int32_t *method_used, int32_t *fronts, int64_t *nnz_factor,
+                         int32_t *max_front, int64_t *flops);
+
 /* Port impedance extraction (Sec. III-C, V): for every frequency f and every
  * port q a unit source in port q's loop, GMRES on Eq. (LoopWithP), then
  * Y[f][p][q] = loop current of port p, Z(f) = Y(f)^-1.  ports[np] selects the

@@ -77,11 +77,15 @@ def stencil_1d(t, order, n):
 class Pfft:
     """pFFT operator of one mesh and loop basis (plain FP64)."""
 
-    def __init__(self, mesh, loops, params: PfftParams, rule=None, targets=None):
+    def __init__(self, mesh, loops, params: PfftParams, rule=None, targets=None, lean=False):
         """targets: optional triangle ids; the near list then holds only the pairs
         (t, j) with t in targets, so that rows of the product are exact for the
-        branches whose triangles are all targets (sampled rows of a large mesh)."""
+        branches whose triangles are all targets (sampled rows of a large mesh).
+        lean: apply the projection B and the interpolation B^T triangle by
+        triangle (project / interpolate) instead of storing B as a sparse matrix
+        (meshes of hundreds of thousands of triangles)."""
         self.mesh, self.loops, self.p = mesh, loops, params
+        self.lean = lean
         self.targets = None if targets is None else np.unique(np.asarray(targets, dtype=np.int64))
         self.rule = radon7() if rule is None else rule
         self.lo, self.h, self.N = grid_of(mesh, params.grid, params.box)
@@ -103,7 +107,8 @@ class Pfft:
         self.tb, self.ts = tri_branches(nt, loops)
         # point current weights: J_q = sum_k c_k (w_q/2)(r_q - v_k)
         self.mom = 0.5 * self.rule[1][None, :, None, None] * (rq[:, :, None, :] - g["p"][:, None, :, :])
-        self._build_B()
+        if not lean:
+            self._build_B()
         self._build_H()
         self._build_near()
 
@@ -175,9 +180,59 @@ class Pfft:
 
     def far(self, alpha):
         """Bt H B alpha over all pairs (branch space, no mu0/4pi)."""
+        if self.lean:
+            Qg = self.project(alpha)
+            return self.interpolate(np.stack([self.convolve(Qg[c]) for c in range(3)]))
         Qg = (self.B @ alpha).reshape(3, *self.N)
         phi = np.stack([self.convolve(Qg[c]) for c in range(3)]).reshape(-1)
         return self.B.T @ phi
+
+    # -- steps 1 and 3 without storing B (the same sums, a chunk of triangles at a time)
+    def _stencil_chunk(self, t0, t1):
+        O = self.p.order
+        Nx, Ny, Nz = self.N
+        off = np.arange(O)
+        st = self.start[t0:t1]
+        ix = st[..., 0][..., None, None, None] + off[:, None, None]
+        iy = st[..., 1][..., None, None, None] + off[None, :, None]
+        iz = st[..., 2][..., None, None, None] + off[None, None, :]
+        node = ((ix * Ny + iy) * Nz + iz).reshape(t1 - t0, st.shape[1], -1)
+        lw = (self.lw[0][t0:t1][..., :, None, None] * self.lw[1][t0:t1][..., None, :, None]
+              * self.lw[2][t0:t1][..., None, None, :]).reshape(t1 - t0, st.shape[1], -1)
+        return node, lw
+
+    def project(self, alpha, chunk=20000):
+        """Q_g = B alpha [3, N_x, N_y, N_z]: each sample point's current
+        J_q = sum_k s_k alpha_k (w_q/2)(r_q - v_k) spread over its stencil with the
+        Lagrange weights (Eq. Projection)."""
+        alpha = np.asarray(alpha, dtype=complex)
+        ng = self.ng
+        out = np.zeros((3, ng), dtype=complex)
+        a_tri = np.where(self.tb >= 0, self.ts * alpha[np.maximum(self.tb, 0)], 0.0)   # [nt, 3]
+        for t0 in range(0, self.mesh.nt, chunk):
+            t1 = min(self.mesh.nt, t0 + chunk)
+            node, lw = self._stencil_chunk(t0, t1)
+            J = np.einsum("tk,tqkc->tqc", a_tri[t0:t1], self.mom[t0:t1])          # [m, Q, 3]
+            for c in range(3):
+                v = (J[:, :, c, None] * lw).ravel()
+                out[c] += (np.bincount(node.ravel(), weights=v.real, minlength=ng)
+                           + 1j * np.bincount(node.ravel(), weights=v.imag, minlength=ng))
+        return out.reshape(3, *self.N)
+
+    def interpolate(self, phi, chunk=20000):
+        """B^T phi [nb] for grid potentials phi [3, N_x, N_y, N_z] (I = B^T, Eq.
+        interpolation): each sample point's interpolated potential, tested with
+        s_k (w_q/2)(r_q - v_k) and summed into the triangle's branches."""
+        ph = np.asarray(phi).reshape(3, -1)
+        out = np.zeros(self.loops.nb, dtype=complex)
+        for t0 in range(0, self.mesh.nt, chunk):
+            t1 = min(self.mesh.nt, t0 + chunk)
+            node, lw = self._stencil_chunk(t0, t1)
+            P = np.stack([np.einsum("tqn,tqn->tq", lw, ph[c][node]) for c in range(3)], axis=-1)   # [m, Q, 3]
+            val = np.einsum("tqkc,tqc->tk", self.mom[t0:t1], P) * self.ts[t0:t1]
+            ok = self.tb[t0:t1] >= 0
+            np.add.at(out, self.tb[t0:t1][ok], val[ok])
+        return out
 
     # -- step 4: near list and pre-correction
     def _build_near(self):
@@ -264,10 +319,10 @@ class Pfft:
 class PfftSystem:
     """Loop-space product y = A (Z_s G + j w mu0/4pi (L_d + I H B)) A^T x."""
 
-    def __init__(self, mesh, loops, params: PfftParams, t_eff=None, targets=None):
+    def __init__(self, mesh, loops, params: PfftParams, t_eff=None, targets=None, lean=False):
         self.mesh, self.loops = mesh, loops
         self.t_eff = t_eff   # effective thickness per conductor: slab surface impedance (mom.py)
-        self.op = Pfft(mesh, loops, params, targets=targets)
+        self.op = Pfft(mesh, loops, params, targets=targets, lean=lean)
         self.G = gram_matrix(mesh, loops)
         nb = loops.nb
         self.A = loops.A[:, :nb].tocsr()

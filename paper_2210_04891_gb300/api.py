@@ -259,6 +259,21 @@ def precond_info(plan: Plan):
     return dict(band_width=w.value, unknowns=u.value, blocks=b.value)
 
 
+def precond_set_method(plan: Plan, method):
+    """pfft_precond_set_method: N.PC_AUTO, N.PC_BAND or N.PC_ND."""
+    check(lib().pfft_precond_set_method(plan.h, int(method)))
+
+
+def precond_nd_info(plan: Plan):
+    """Route of the preconditioner and, for nested dissection, its fronts, factor
+    entries per frequency, largest front and complex multiply-adds per factorisation."""
+    m, f, mf = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    nz, fl = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().pfft_precond_nd_info(plan.h, ctypes.byref(m), ctypes.byref(f), ctypes.byref(nz), ctypes.byref(mf),
+                                     ctypes.byref(fl)))
+    return dict(method=m.value, fronts=f.value, nnz=nz.value, max_front=mf.value, flops=fl.value)
+
+
 def pfft_matvec(plan: Plan, x, omega, space=N.SPACE_LOOP, prec=N.PREC_FP64, out=None, stream=None):
     """y = A Z_b(omega) A^T x (space=LOOP) or Z_b(omega) x (space=BRANCH), x [nrhs, n]."""
     import torch

@@ -700,6 +700,7 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
         diam[t] = dm;
         max_diam = std::max(max_diam, dm);
     }
+    p->tri_cen = cen;
     double max_h = 0.0;
     for (int d = 0; d < 3; ++d) {
         p->lo[d] = lo[d];

@@ -18,6 +18,7 @@ template <typename T> struct DevBuf {
 
 struct PrecondState;   // sie_solve.cu
 struct LossyCache;     // sie_lossy.cu
+struct NdState;        // sie_nd.cu
 
 struct Scratch {
     int32_t cap_rhs = 0;   // right-hand sides the buffers are sized for
@@ -64,6 +65,9 @@ struct pfft_plan {
     pfft_params params{};
     const sie_loops *loops = nullptr;   // borrowed: must outlive the plan
     std::vector<double> sigma;          // per conductor
+    std::vector<double> tri_cen;        // [nt][3] triangle centroids (host; the preconditioner's
+                                        // nested-dissection ordering bisects by position)
+    int32_t pc_method = 0;              // SIE_PC_AUTO, SIE_PC_BAND or SIE_PC_ND
     std::vector<double> t_eff;          // per conductor: slab surface impedance thickness (0: classic)
     // per triangle (device)
     int32_t *d_tb = nullptr;            // [nt][3] branch of local edge k (-1: none)
@@ -230,6 +234,27 @@ const void *const *lossy_ltab(const pfft_plan *p, int prec);
 const int32_t *lossy_rslot(const pfft_plan *p);
 int lossy_diag(pfft_plan *p, const double *omega, int32_t ns, double2 *out, cudaStream_t st);
 void plan_free_lossy(pfft_plan *p);
+// Nested-dissection multifrontal LDL^T of the preconditioner's nodal Laplacian
+// (sie_nd.cu): nd_build orders the nunk unknowns (adjacency uadj, positions
+// xyz [nunk][3]) and builds the fronts, perm (new -> raw); nd_rows maps the
+// Laplacian's row entries (new numbering) into their fronts; nd_factor
+// factorises one frequency slot (admittances a [nb]) into L64 / L32 [sumL]
+// through the workspace W [sumF]; nd_solve solves in place on u [R][nunk]
+// with the factors L [nslots][sumL] of each right-hand side's slot and the
+// update-vector workspace uv [R][sumU].
+int nd_build(const std::vector<std::vector<int32_t>> &uadj, const std::vector<double> &xyz, std::vector<int32_t> &perm,
+             NdState **out);
+int nd_rows(NdState *s, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &row_oth);
+int nd_factor(pfft_plan *p, NdState *s, const double2 *a, const int32_t *row_ptr, const int32_t *row_br, double2 *W,
+              double2 *L64, float2 *L32, int *status, cudaStream_t st);
+template <typename T>
+int nd_solve(pfft_plan *p, const NdState *s, const C<T> *L, const int32_t *slot, int32_t R, C<T> *u, C<T> *uv,
+             cudaStream_t st);
+int64_t nd_factor_size(const NdState *s);
+int64_t nd_workspace_size(const NdState *s);
+int64_t nd_update_size(const NdState *s);
+void nd_info(const NdState *s, int32_t *fronts, int64_t *nnz, int32_t *max_front, int64_t *flops);
+void nd_free(NdState *s);
 // Complex padded table of exp(-jkR)/R (1/delta given) into Hc [Mx][My][Mz]; its folded
 // spectrum scaled by 1/(Mx My Mz) into H64 / H32 (Hc may be overwritten).
 int lossy_fill_table(pfft_plan *p, double inv_delta, double2 *Hc, cudaStream_t s);

@@ -75,6 +75,12 @@ struct PrecondState {
     int32_t cap_rhs = 0;
     int32_t *d_slot = nullptr;        // [R] factor slot per right-hand side
     int *d_status = nullptr;
+    // nested-dissection route (bands too wide, or asked for): the multifrontal factors of
+    // every slot [nslots][sumL] in FP64 and FP32, and the solves' update vectors [R][sumU]
+    NdState *nd = nullptr;
+    double2 *d_ndL64 = nullptr;
+    float2 *d_ndL32 = nullptr;
+    double2 *d_uv = nullptr;
     std::vector<void *> allocs;
 };
 
@@ -120,8 +126,10 @@ void plan_free_precond(pfft_plan *p) {
                     (void *)p->pc->d_band32, (void *)p->pc->d_bandc32})
         if (a) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
-                    (void *)p->pc->d_ibr, (void *)p->pc->d_slot})
+                    (void *)p->pc->d_ibr, (void *)p->pc->d_slot, (void *)p->pc->d_ndL64, (void *)p->pc->d_ndL32,
+                    (void *)p->pc->d_uv})
         if (a) cudaFree(a);
+    nd_free(p->pc->nd);
     delete p->pc;
     p->pc = nullptr;
 }
@@ -272,6 +280,24 @@ int build_symbolic(pfft_plan *p) {
     for (int64_t a = 0; a < nunk; ++a)
         for (int32_t b : uadj[a]) W = std::max<int32_t>(W, std::abs(inv[a] - inv[b]));
     s->W = std::max<int32_t>(W, 1);
+    // nested dissection in place of the band when the band is too wide for the band
+    // factorisation (or when asked for): unknowns placed at their nodes' centroids
+    if (nunk > 0 && (p->pc_method == SIE_PC_ND || (p->pc_method == SIE_PC_AUTO && s->W >= kWideMax))) {
+        std::vector<double> xyz(3 * size_t(nunk), 0.0);
+        std::vector<int32_t> cnt(nunk, 0);
+        for (int64_t t = 0; t < p->nt; ++t) {
+            const int32_t u = unk_raw[L->node_of_tri[t]];
+            if (u < 0) continue;
+            for (int d = 0; d < 3; ++d) xyz[3 * size_t(u) + d] += p->tri_cen[3 * t + d];
+            cnt[u]++;
+        }
+        for (int64_t u = 0; u < nunk; ++u)
+            for (int d = 0; d < 3; ++d) xyz[3 * size_t(u) + d] /= std::max(cnt[u], 1);
+        int rcn = nd_build(uadj, xyz, perm, &s->nd);
+        if (rcn) return rcn;
+        for (int64_t i = 0; i < nunk; ++i) inv[perm[i]] = int32_t(i);
+        s->blk_off.assign({0, nunk});
+    }
     std::vector<int32_t> unk(nn, -1);
     for (int64_t v = 0; v < nn; ++v) unk[v] = unk_raw[v] >= 0 ? inv[unk_raw[v]] : -1;
     // rows: incident branches of each unknown's member nodes
@@ -291,6 +317,10 @@ int build_symbolic(pfft_plan *p) {
             row_oth.push_back(o);
         }
         row_ptr.push_back(int32_t(row_br.size()));
+    }
+    if (s->nd) {
+        int rcn = nd_rows(s->nd, row_ptr, row_oth);
+        if (rcn) return rcn;
     }
     std::vector<int32_t> off_ptr{0}, off_port;
     std::vector<int8_t> off_sign;
@@ -949,6 +979,10 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         if (s->d_u32) cudaFreeAsync(s->d_u32, st);
         SIE_CUDA(pool_alloc(p, &s->d_u32, size_t(R) * std::max<int64_t>(s->nunk, 1) * sizeof(float2), st));
         SIE_CUDA(pool_alloc(p, &s->d_slot, size_t(R) * sizeof(int32_t), st));
+        if (s->nd) {
+            if (s->d_uv) cudaFreeAsync(s->d_uv, st);
+            SIE_CUDA(pool_alloc(p, &s->d_uv, size_t(R) * std::max<int64_t>(nd_update_size(s->nd), 1) * sizeof(double2), st));
+        }
         s->cap_rhs = R;
     }
     SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -970,10 +1004,19 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     s->d_a = nullptr;
     s->d_a32 = nullptr;
     s->slot_omega.clear();
-    SIE_CUDA(pool_alloc(p, &s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
-    SIE_CUDA(pool_alloc(p, &s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
-    const bool tiled = s->W <= 31 && s->nunk > 0;
-    const bool wide = s->W > 31 && s->W < kWideMax && s->nunk > 0;
+    if (s->d_ndL64) cudaFreeAsync(s->d_ndL64, st);
+    if (s->d_ndL32) cudaFreeAsync(s->d_ndL32, st);
+    s->d_ndL64 = nullptr;
+    s->d_ndL32 = nullptr;
+    if (s->nd) {
+        SIE_CUDA(pool_alloc(p, &s->d_ndL64, size_t(ns) * std::max<int64_t>(nd_factor_size(s->nd), 1) * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_ndL32, size_t(ns) * std::max<int64_t>(nd_factor_size(s->nd), 1) * sizeof(float2), st));
+    } else {
+        SIE_CUDA(pool_alloc(p, &s->d_band, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_bandc, size_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1) * sizeof(double2), st));
+    }
+    const bool tiled = !s->nd && s->W <= 31 && s->nunk > 0;
+    const bool wide = !s->nd && s->W > 31 && s->W < kWideMax && s->nunk > 0;
     const int64_t nband = int64_t(ns) * std::max<int64_t>(s->nunk, 1) * (s->W + 1);
     if (wide) {
         SIE_CUDA(pool_alloc(p, &s->d_band32, size_t(nband) * sizeof(float2), st));
@@ -1017,7 +1060,21 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     SIE_CUDA(cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
     StageTimer tm(p, SIE_STAGE_PRECOND_FACTOR, st);
-    if (s->nunk > 0) {
+    if (s->nd && s->nunk > 0) {
+        // multifrontal LDL^T of each slot through one front workspace
+        double2 *Wf = nullptr;
+        SIE_CUDA(pool_alloc(p, &Wf, size_t(std::max<int64_t>(nd_workspace_size(s->nd), 1)) * sizeof(double2), st));
+        const int64_t sl = nd_factor_size(s->nd);
+        for (int32_t f = 0; f < ns; ++f) {
+            const int rn = nd_factor(p, s->nd, s->d_a + int64_t(f) * p->nb, s->d_row_ptr, s->d_row_br, Wf,
+                                     s->d_ndL64 + int64_t(f) * sl, s->d_ndL32 + int64_t(f) * sl, s->d_status, st);
+            if (rn) {
+                cudaFreeAsync(Wf, st);
+                return rn;
+            }
+        }
+        cudaFreeAsync(Wf, st);
+    } else if (s->nunk > 0) {
         k_pc_factor<<<ns * nblk, 256, 0, st>>>(s->d_blk_off, nblk, s->W, s->nunk, s->d_row_ptr, s->d_row_br,
                                                 s->d_row_oth, s->d_a, p->nb, s->d_band, s->d_bandc, s->d_status);
         SIE_LAUNCH_CHECK(p);
@@ -1067,7 +1124,15 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
                                                     p->d_head, s->d_off_ptr, s->d_off_port, s->d_off_sign,
                                                     s->d_port_loop, p->nb, R, kappa);
     SIE_LAUNCH_CHECK(p);
-    if (s->nunk > 0) {
+    if (s->nd && s->nunk > 0) {
+        k_pc_rhs<T><<<nblk_(int64_t(R) * s->nunk), 256, 0, st>>>(kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
+                                                                   s->nunk, p->nb, R, u);
+        SIE_LAUNCH_CHECK(p);
+        const C<T> *Lf;
+        if constexpr (f32) Lf = s->d_ndL32; else Lf = s->d_ndL64;
+        int rn = nd_solve<T>(p, s->nd, Lf, s->d_slot, R, u, reinterpret_cast<C<T> *>(s->d_uv), st);
+        if (rn) return rn;
+    } else if (s->nunk > 0) {
         if (s->W <= 31) {
             k_pc_rhs<T><<<nblk_(int64_t(R) * s->nunk), 256, 0, st>>>(kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
                                                                        s->nunk, p->nb, R, u);
@@ -1121,7 +1186,7 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
 
 int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int prec, cudaStream_t st) {
     StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
-    if (prec == SIE_PREC_MIXED && p->pc->W < kWideMax) return pc_apply_t<float>(p, y, z, R, st);
+    if (prec == SIE_PREC_MIXED && (p->pc->nd || p->pc->W < kWideMax)) return pc_apply_t<float>(p, y, z, R, st);
     return pc_apply_t<double>(p, y, z, R, st);
 }
 
@@ -1196,6 +1261,113 @@ __global__ void k_update_x(const double2 *__restrict__ V, int64_t ldv, int64_t k
 __global__ void k_sub(const double2 *__restrict__ a, const double2 *__restrict__ b, double2 *__restrict__ c, int64_t n) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) c[i] = csub(a[i], b[i]);
+}
+
+__global__ void k_add(double2 *__restrict__ a, const double2 *__restrict__ b, int64_t n) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = cadd(a[i], b[i]);
+}
+
+// Device state of one GMRES cycle per right-hand side r (Eq. LoopWithP):
+// Hessenberg matrix after the rotations H[r][j][k] (pitch m), rotations
+// cs[r][k], sn[r][k], rotated right-hand side g[r][0..m], steps taken kdone,
+// total iterations iters, residual estimate resid = |g[k]| / bnorm, run flag.
+struct GmresDev {
+    double2 *H, *cs, *sn, *g;
+    int32_t *run, *kdone, *iters;
+    double *resid, *bnorm, *scale;
+    int32_t *nrun, *bad;
+};
+
+// Start of a cycle: g = (beta, 0, ...), kdone = 0, scale = 1/beta for v_0,
+// run = act (the right-hand sides still to converge).
+__global__ void k_cycle_start(GmresDev d, int32_t m, int32_t R, const double *__restrict__ beta,
+                              const int32_t *__restrict__ act) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    d.g[int64_t(r) * (m + 1)] = make_double2(beta[r], 0.0);
+    d.kdone[r] = 0;
+    d.run[r] = act[r];
+    d.scale[r] = beta[r] > 0.0 ? 1.0 / beta[r] : 0.0;
+}
+
+// The end of Arnoldi step k per right-hand side (one thread each): column k of
+// the Hessenberg matrix, h_jk = h1_j + h2_j (classical Gram-Schmidt applied
+// twice) and h_{k+1,k} = ||w||; the previous rotations applied to it; the new
+// rotation [[conj c, conj s], [-s, c]] that annihilates h_{k+1,k}; g rotated;
+// the residual estimate |g_{k+1}| / bnorm; the scale 1/h_{k+1,k} of v_{k+1}.
+// The run flag drops on convergence (resid < tol), on the iteration cap, on a
+// happy breakdown (h_{k+1,k} = 0) or on a non-finite norm (bad is set); nrun
+// counts the right-hand sides still running.
+__global__ void k_givens(GmresDev d, int32_t k, int32_t m, int32_t R, const double2 *__restrict__ h1,
+                         const double2 *__restrict__ h2, int32_t ldh, const double *__restrict__ hn, double tol,
+                         int32_t max_iter) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    if (!d.run[r]) {
+        d.scale[r] = 0.0;
+        return;
+    }
+    const double hk1 = hn[r];
+    if (!isfinite(hk1)) {
+        d.run[r] = 0;
+        d.scale[r] = 0.0;
+        atomicExch(d.bad, 1);
+        return;
+    }
+    double2 *Hc = d.H + int64_t(r) * (m + 1) * m;
+    const double2 *cs = d.cs + int64_t(r) * m, *sn = d.sn + int64_t(r) * m;
+    for (int32_t j = 0; j <= k; ++j) Hc[int64_t(j) * m + k] = cadd(h1[int64_t(r) * ldh + j], h2[int64_t(r) * ldh + j]);
+    for (int32_t i = 0; i < k; ++i) {
+        const double2 a = Hc[int64_t(i) * m + k], b = Hc[int64_t(i + 1) * m + k];
+        const double2 c = cs[i], s = sn[i];
+        // conj(c) a + conj(s) b and -s a + c b
+        Hc[int64_t(i) * m + k] = make_double2(c.x * a.x + c.y * a.y + s.x * b.x + s.y * b.y,
+                                              c.x * a.y - c.y * a.x + s.x * b.y - s.y * b.x);
+        Hc[int64_t(i + 1) * m + k] = csub(cmul(c, b), cmul(s, a));
+    }
+    const double2 a = Hc[int64_t(k) * m + k];
+    const double den = sqrt(a.x * a.x + a.y * a.y + hk1 * hk1);
+    const double2 c = den > 0.0 ? make_double2(a.x / den, a.y / den) : make_double2(1.0, 0.0);
+    const double2 s = den > 0.0 ? make_double2(hk1 / den, 0.0) : make_double2(0.0, 0.0);
+    d.cs[int64_t(r) * m + k] = c;
+    d.sn[int64_t(r) * m + k] = s;
+    Hc[int64_t(k) * m + k] = make_double2(den, 0.0);
+    double2 *g = d.g + int64_t(r) * (m + 1);
+    const double2 gk = g[k];
+    g[k + 1] = make_double2(-(s.x * gk.x - s.y * gk.y), -(s.x * gk.y + s.y * gk.x));
+    g[k] = make_double2(c.x * gk.x + c.y * gk.y, c.x * gk.y - c.y * gk.x);
+    d.kdone[r] = k + 1;
+    d.iters[r] += 1;
+    const double2 gn = g[k + 1];
+    d.resid[r] = sqrt(gn.x * gn.x + gn.y * gn.y) / d.bnorm[r];
+    d.scale[r] = hk1 > 0.0 ? 1.0 / hk1 : 0.0;
+    if (d.resid[r] < tol || d.iters[r] >= max_iter || hk1 == 0.0) d.run[r] = 0;
+    else atomicAdd(d.nrun, 1);
+}
+
+// y = R^-1 g of the cycle per right-hand side (back substitution in the rotated
+// Hessenberg matrix), written to y[r][0..kdone).
+__global__ void k_lsq(GmresDev d, int32_t m, int32_t R, double2 *__restrict__ y, int32_t ldy) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int32_t kk = d.kdone[r];
+    const double2 *Hc = d.H + int64_t(r) * (m + 1) * m;
+    const double2 *g = d.g + int64_t(r) * (m + 1);
+    double2 *yr = y + int64_t(r) * ldy;
+    for (int32_t i = kk - 1; i >= 0; --i) {
+        double2 sum = g[i];
+        for (int32_t j = i + 1; j < kk; ++j) sum = csub(sum, cmul(Hc[int64_t(i) * m + j], yr[j]));
+        const double2 h = Hc[int64_t(i) * m + i];
+        const double dd = h.x * h.x + h.y * h.y;
+        yr[i] = make_double2((sum.x * h.x + sum.y * h.y) / dd, (sum.y * h.x - sum.x * h.y) / dd);
+    }
+}
+
+// norms[r] = ||w[r]|| from the dot of w with itself (k_dots output h[r][0]).
+__global__ void k_norms(const double2 *__restrict__ h, int32_t ldh, int32_t R, double *__restrict__ out) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) out[r] = sqrt(fmax(h[int64_t(r) * ldh].x, 0.0));
 }
 
 }  // namespace
@@ -1280,157 +1452,226 @@ extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const in
         if (use_pc) return pc_apply_async(p, t, out, R, prec, st);
         return SIE_OK;
     };
-    auto dots = [&](const double2 *vec, int32_t k, std::vector<double2> &h) -> int {   // h[r][j] for j < k
-        StageTimer tm(p, SIE_STAGE_ARNOLDI, st);
-        k_dots<<<R * k, 256, 0, st>>>(V, ldv, mstride, vec, n, k, act, dh, m + 2);
+    // device state of the cycles (GmresDev) and the Arnoldi step's buffers
+    GmresDev gd{};
+    double2 *dh2 = nullptr, *dhn = nullptr, *dy = nullptr, *rv = nullptr, *dvec = nullptr;
+    double *dnorm = nullptr, *dbeta = nullptr;
+    int32_t *hflags = nullptr;   // pinned: nrun, bad
+    auto cleanup2 = [&]() {
+        for (void *a : {(void *)gd.H, (void *)gd.cs, (void *)gd.sn, (void *)gd.g, (void *)gd.run, (void *)gd.kdone,
+                        (void *)gd.iters, (void *)gd.resid, (void *)gd.bnorm, (void *)gd.scale, (void *)gd.nrun,
+                        (void *)dh2, (void *)dhn, (void *)dy, (void *)rv, (void *)dvec, (void *)dnorm,
+                        (void *)dbeta})
+            if (a) cudaFreeAsync(a, st);
+    };
+#undef GM_CUDA
+#undef GM_RC
+#define GM_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); cleanup2(); if (hflags) cudaFreeHost(hflags); set_error(std::string(#call) + ": " + cudaGetErrorString(_e)); return _e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA; } } while (0)
+#define GM_RC(expr) do { int _r = (expr); if (_r) { cleanup(); cleanup2(); if (hflags) cudaFreeHost(hflags); return _r; } } while (0)
+    GM_CUDA(pool_alloc(p, &gd.H, size_t(R) * (m + 1) * m * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &gd.cs, size_t(R) * m * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &gd.sn, size_t(R) * m * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &gd.g, size_t(R) * (m + 1) * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &gd.run, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(pool_alloc(p, &gd.kdone, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(pool_alloc(p, &gd.iters, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(pool_alloc(p, &gd.resid, size_t(R) * sizeof(double), st));
+    GM_CUDA(pool_alloc(p, &gd.bnorm, size_t(R) * sizeof(double), st));
+    GM_CUDA(pool_alloc(p, &gd.scale, size_t(R) * sizeof(double), st));
+    GM_CUDA(pool_alloc(p, &gd.nrun, 2 * sizeof(int32_t), st));
+    gd.bad = gd.nrun + 1;
+    GM_CUDA(pool_alloc(p, &dh2, size_t(R) * (m + 2) * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &dhn, size_t(R) * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &dy, size_t(R) * (m + 1) * sizeof(double2), st));
+    GM_CUDA(pool_alloc(p, &rv, size_t(R) * n * sizeof(double2), st));      // residual b - Z x
+    GM_CUDA(pool_alloc(p, &dnorm, size_t(R) * sizeof(double), st));
+    GM_CUDA(pool_alloc(p, &dbeta, size_t(R) * sizeof(double), st));
+    if (refine) GM_CUDA(pool_alloc(p, &dvec, size_t(R) * n * sizeof(double2), st));   // the cycle's correction
+    GM_CUDA(cudaMemsetAsync(gd.iters, 0, size_t(R) * sizeof(int32_t), st));
+    GM_CUDA(cudaMemsetAsync(gd.nrun, 0, 2 * sizeof(int32_t), st));
+    GM_CUDA(cudaMallocHost((void **)&hflags, 2 * sizeof(int32_t)));
+    const unsigned rb = unsigned((R + 127) / 128);
+    // ||vec[r]|| into dnorm (device) through k_dots on a one-vector basis
+    auto norms_dev = [&](const double2 *vec, const int32_t *mask) -> int {
+        k_dots<<<R, 256, 0, st>>>(vec, ldv, ldv, vec, n, 1, mask, dhn, 1);
         SIE_LAUNCH_CHECK(p);
-        h.resize(size_t(R) * (m + 2));
-        SIE_CUDA(cudaMemcpyAsync(h.data(), dh, size_t(R) * (m + 2) * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        SIE_CUDA(cudaStreamSynchronize(st));
+        k_norms<<<rb, 128, 0, st>>>(dhn, 1, R, dnorm);
+        SIE_LAUNCH_CHECK(p);
         return SIE_OK;
     };
-    // norms via a dot with itself: place the vector in V's slot m temporarily is avoided by a separate pass
-    auto norms = [&](const double2 *vec, std::vector<double> &nr) -> int {
-        // reuse k_dots on a one-vector "basis" = vec itself
-        k_dots<<<R, 256, 0, st>>>(vec, ldv, ldv, vec, n, 1, act, dh, m + 2);
-        SIE_LAUNCH_CHECK(p);
-        std::vector<double2> h(size_t(R) * (m + 2));
-        SIE_CUDA(cudaMemcpyAsync(h.data(), dh, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        SIE_CUDA(cudaStreamSynchronize(st));
+    auto read_norms = [&](std::vector<double> &nr) -> int {
         nr.resize(R);
-        for (int32_t r = 0; r < R; ++r) nr[r] = std::sqrt(std::max(h[size_t(r) * (m + 2)].x, 0.0));
+        SIE_CUDA(cudaMemcpyAsync(nr.data(), dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        SIE_CUDA(cudaStreamSynchronize(st));
         return SIE_OK;
     };
     std::vector<int32_t> active(R, 1), done(R, 0), iters(R, 0);
     std::vector<double> bnorm(R), resid(R, 1.0);
     GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    // ||P^-1 b||
+    // ||P^-1 b|| (the outer precision's preconditioner)
     if (use_pc) GM_RC(pc_apply_async(p, b, w, R, outer_prec, st));
     else GM_CUDA(cudaMemcpyAsync(w, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    GM_RC(norms(w, bnorm));
+    GM_RC(norms_dev(w, act));
+    GM_RC(read_norms(bnorm));
+    GM_CUDA(cudaMemcpyAsync(gd.bnorm, dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // r = b - Z x with x = 0
+    GM_CUDA(cudaMemcpyAsync(rv, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     int64_t matvecs = 0;
     using cd = std::complex<double>;
-    int total_iters = 0;
     bool breakdown = false;
+    // Iterative refinement (refine): the cycles run the mixed operator on the
+    // current residual; x accumulates their corrections d.  The mixed product's
+    // error scales with |Z| |x|, not |Z x|, so one cycle lowers the true residual
+    // by a bounded factor: a cycle stops once it has reduced its own residual
+    // estimate a hundredfold (or reached half the tolerance).  The residual is
+    // then updated as r = b - Z x with the FP64 product when the cycle started
+    // from a residual above rho_fp64 (relative to ||P^-1 b||), else as
+    // r = r - Z d with the mixed product (its error is relative to the small
+    // correction).  A convergence found on a residual that mixed updates
+    // produced is confirmed on the FP64 residual before the solve stops, so the
+    // stopping test always rests on an FP64 product.
+    const double rho_fp64 = 1e4 * opts->tol;
+    double cycle_start = 1.0;
+    bool first = true, mixed_since_fp64 = false;
     while (true) {
-        // residual r = P^-1 (b - Z x), in FP64 under iterative refinement
-        GM_RC(apply_op(x, w, outer_prec));   // w = P^-1 Z x
-        matvecs += R;
-        if (use_pc) {
-            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, t, int64_t(R) * n);   // t = b - Z x (t held Z x)
-            SIE_LAUNCH_CHECK(p);
-            GM_RC(pc_apply_async(p, t, w, R, outer_prec, st));
-        } else {
-            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, w, w, int64_t(R) * n);
-            SIE_LAUNCH_CHECK(p);
-        }
+        // preconditioned residual w = P^-1 r and its norm (outer precision)
+        if (use_pc) GM_RC(pc_apply_async(p, rv, w, R, outer_prec, st));
+        else GM_CUDA(cudaMemcpyAsync(w, rv, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        GM_RC(norms_dev(w, act));
         std::vector<double> beta;
-        GM_RC(norms(w, beta));
+        GM_RC(read_norms(beta));
         bool any = false;
+        cycle_start = 0.0;
         for (int32_t r = 0; r < R; ++r) {
+            if (done[r] || !active[r]) {   // no new norm was taken for it
+                active[r] = 0;
+                continue;
+            }
             resid[r] = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
             if (!std::isfinite(resid[r])) breakdown = true;
             active[r] = !done[r] && !(resid[r] < opts->tol) && iters[r] < opts->max_iter && bnorm[r] > 0 &&
                         std::isfinite(resid[r]);
             if (resid[r] < opts->tol) done[r] = 1;
+            if (active[r]) cycle_start = std::max(cycle_start, resid[r]);
             any |= active[r] != 0;
+        }
+        if (!any && refine && mixed_since_fp64 && !breakdown) {
+            // converged on a residual from mixed updates: recompute it with the FP64
+            // product; the right-hand sides it does not confirm continue
+            GM_RC(matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, SIE_PREC_FP64, st));
+            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
+            SIE_LAUNCH_CHECK(p);
+            matvecs += R;
+            mixed_since_fp64 = false;
+            for (int32_t r = 0; r < R; ++r) {
+                active[r] = iters[r] < opts->max_iter && bnorm[r] > 0;
+                done[r] = 0;
+            }
+            GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            continue;
         }
         if (!any || breakdown) break;
         GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        std::vector<double> sc(R);
-        for (int32_t r = 0; r < R; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
-        GM_CUDA(cudaMemcpyAsync(scl, sc.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, 0, n, scl, act, R);
+        GM_CUDA(cudaMemcpyAsync(dbeta, dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GM_CUDA(cudaMemcpyAsync(gd.iters, iters.data(), size_t(R) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        // the cycle's stopping level (relative to ||P^-1 b||): the tolerance, or with
+        // refinement a hundredth of the largest starting residual, at least half the tolerance
+        const double tol_inner = refine ? std::max(0.5 * opts->tol, 1e-2 * cycle_start) : opts->tol;
+        k_cycle_start<<<rb, 128, 0, st>>>(gd, m, R, dbeta, act);
         SIE_LAUNCH_CHECK(p);
-        // Arnoldi with Givens, per right-hand side
-        std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m, 0.0));
-        std::vector<std::vector<cd>> cs(R, std::vector<cd>(m)), sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1, 0.0));
-        for (int32_t r = 0; r < R; ++r) g[r][0] = beta[r];
-        std::vector<int32_t> kdone(R, 0);
-        std::vector<int32_t> run(active);
+        k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, 0, n, gd.scale, act, R);
+        SIE_LAUNCH_CHECK(p);
+        // Arnoldi (CGS2) with the rotations on the device; one host read per step
         for (int k = 0; k < m; ++k) {
-            bool any_run = false;
-            for (int32_t r = 0; r < R; ++r) any_run |= run[r] != 0;
-            if (!any_run) break;
-            GM_CUDA(cudaMemcpyAsync(act, run.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             // w = P^-1 Z v_k
             GM_RC(apply_op(V + int64_t(k) * kstride, w, opts->prec));
             matvecs += R;
-            std::vector<double2> h1, h2;
-            GM_RC(dots(w, k + 1, h1));   // CGS pass 1
-            k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, act, dh, m + 2, R);
-            SIE_LAUNCH_CHECK(p);
-            GM_RC(dots(w, k + 1, h2));   // CGS pass 2
-            k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, act, dh, m + 2, R);
-            SIE_LAUNCH_CHECK(p);
-            std::vector<double> hn;
-            GM_RC(norms(w, hn));
-            std::vector<double> sc2(R, 0.0);
-            for (int32_t r = 0; r < R; ++r) {
-                if (!run[r]) continue;
-                std::vector<cd> col(k + 2);
-                for (int j = 0; j <= k; ++j)
-                    col[j] = cd(h1[size_t(r) * (m + 2) + j].x + h2[size_t(r) * (m + 2) + j].x,
-                                h1[size_t(r) * (m + 2) + j].y + h2[size_t(r) * (m + 2) + j].y);
-                col[k + 1] = hn[r];
-                if (!std::isfinite(hn[r])) { breakdown = true; run[r] = 0; continue; }
-                for (int i = 0; i < k; ++i) {   // rotation i: [[conj c, conj s], [-s, c]]
-                    cd tmp = std::conj(cs[r][i]) * col[i] + std::conj(sn[r][i]) * col[i + 1];
-                    col[i + 1] = -sn[r][i] * col[i] + cs[r][i] * col[i + 1];
-                    col[i] = tmp;
-                }
-                double den = std::sqrt(std::norm(col[k]) + std::norm(col[k + 1]));
-                cs[r][k] = den > 0 ? col[k] / den : cd(1.0);
-                sn[r][k] = den > 0 ? col[k + 1] / den : cd(0.0);
-                col[k] = den;
-                col[k + 1] = 0.0;
-                g[r][k + 1] = -sn[r][k] * g[r][k];
-                g[r][k] = std::conj(cs[r][k]) * g[r][k];
-                for (int j = 0; j <= k; ++j) H[r][size_t(j) * m + k] = col[j];
-                kdone[r] = k + 1;
-                iters[r] += 1;
-                resid[r] = std::abs(g[r][k + 1]) / bnorm[r];
-                sc2[r] = hn[r] > 0 ? 1.0 / hn[r] : 0.0;
-                if (resid[r] < opts->tol || iters[r] >= opts->max_iter || hn[r] == 0.0) run[r] = 0;
-            }
-            total_iters = std::max(total_iters, k + 1);
-            if (k + 1 < m) {
-                GM_CUDA(cudaMemcpyAsync(scl, sc2.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
-                k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, k + 1, n, scl, act, R);
+            {
+                StageTimer tm(p, SIE_STAGE_ARNOLDI, st);
+                k_dots<<<R * (k + 1), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh, m + 2);   // CGS pass 1
                 SIE_LAUNCH_CHECK(p);
+                k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh, m + 2, R);
+                SIE_LAUNCH_CHECK(p);
+                k_dots<<<R * (k + 1), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh2, m + 2);  // CGS pass 2
+                SIE_LAUNCH_CHECK(p);
+                k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh2, m + 2, R);
+                SIE_LAUNCH_CHECK(p);
+                GM_RC(norms_dev(w, gd.run));
+                GM_CUDA(cudaMemsetAsync(gd.nrun, 0, sizeof(int32_t), st));
+                k_givens<<<rb, 128, 0, st>>>(gd, k, m, R, dh, dh2, m + 2, dnorm, tol_inner, opts->max_iter);
+                SIE_LAUNCH_CHECK(p);
+                if (k + 1 < m) {
+                    k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, k + 1, n, gd.scale,
+                                                                        gd.run, R);
+                    SIE_LAUNCH_CHECK(p);
+                }
+                GM_CUDA(cudaMemcpyAsync(hflags, gd.nrun, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                GM_CUDA(cudaStreamSynchronize(st));
             }
+            if (hflags[1]) breakdown = true;
+            if (hflags[0] == 0) break;
         }
-        // x += V y, y from the triangular system
-        std::vector<double2> yv(size_t(R) * (m + 1), make_double2(0.0, 0.0));
-        for (int32_t r = 0; r < R; ++r) {
-            int kk = kdone[r];
-            std::vector<cd> yy(kk);
-            for (int i = kk - 1; i >= 0; --i) {
-                cd s = g[r][i];
-                for (int j = i + 1; j < kk; ++j) s -= H[r][size_t(i) * m + j] * yy[j];
-                yy[i] = s / H[r][size_t(i) * m + i];
-            }
-            for (int i = 0; i < kk; ++i) yv[size_t(r) * (m + 1) + i] = make_double2(yy[i].real(), yy[i].imag());
-        }
-        double2 *dy = nullptr;
-        GM_CUDA(cudaMalloc((void **)&dy, yv.size() * sizeof(double2)));
-        GM_CUDA(cudaMemcpyAsync(dy, yv.data(), yv.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-        GM_CUDA(cudaMemcpyAsync(dk, kdone.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        k_update_x<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, x, n, dk, dy, m + 1, R);
+        // the cycle's correction d = V y, y = R^-1 g (device back substitution)
+        k_lsq<<<rb, 128, 0, st>>>(gd, m, R, dy, m + 1);
         SIE_LAUNCH_CHECK(p);
+        double2 *xd = refine ? dvec : x;
+        if (refine) GM_CUDA(cudaMemsetAsync(dvec, 0, size_t(R) * n * sizeof(double2), st));
+        k_update_x<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, xd, n, gd.kdone, dy, m + 1, R);
+        SIE_LAUNCH_CHECK(p);
+        std::vector<double> rs(R);
+        GM_CUDA(cudaMemcpyAsync(iters.data(), gd.iters, size_t(R) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GM_CUDA(cudaMemcpyAsync(rs.data(), gd.resid, size_t(R) * sizeof(double), cudaMemcpyDeviceToHost, st));
         GM_CUDA(cudaStreamSynchronize(st));
-        cudaFree(dy);
+        if (breakdown) break;
         // without refinement the cycle's residual estimate decides; with it the
-        // FP64 residual at the top of the next restart does
+        // residual at the top of the next cycle does
         if (!refine)
             for (int32_t r = 0; r < R; ++r)
-                if (active[r] && resid[r] < opts->tol) done[r] = 1;
+                if (active[r]) {
+                    resid[r] = rs[r];
+                    if (rs[r] < opts->tol) done[r] = 1;
+                }
         bool cont = false;
         for (int32_t r = 0; r < R; ++r) cont |= !done[r] && iters[r] < opts->max_iter;
-        if (!cont) break;
+        if (!cont && !refine) break;
         for (int32_t r = 0; r < R; ++r) active[r] = !done[r] && iters[r] < opts->max_iter;
         GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        // the new residual r = b - Z x
+        if (!refine) {
+            GM_RC(matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, opts->prec, st));
+            matvecs += R;
+            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
+            SIE_LAUNCH_CHECK(p);
+        } else {
+            k_add<<<nblk_(int64_t(R) * n), 256, 0, st>>>(x, dvec, int64_t(R) * n);
+            SIE_LAUNCH_CHECK(p);
+            if (first || cycle_start > rho_fp64) {
+                GM_RC(matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, SIE_PREC_FP64, st));
+                k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
+                mixed_since_fp64 = false;
+            } else {
+                GM_RC(matvec_async(p, dvec, t, R, om.data(), SIE_SPACE_LOOP, opts->prec, st));
+                k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(rv, t, rv, int64_t(R) * n);
+                mixed_since_fp64 = true;
+            }
+            SIE_LAUNCH_CHECK(p);
+            matvecs += R;
+            first = false;
+        }
+        if (!cont) {   // refinement: iteration cap reached; report the residual of the final x
+            if (use_pc) GM_RC(pc_apply_async(p, rv, w, R, outer_prec, st));
+            else GM_CUDA(cudaMemcpyAsync(w, rv, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            GM_RC(norms_dev(w, act));
+            std::vector<double> fin;
+            GM_RC(read_norms(fin));
+            for (int32_t r = 0; r < R; ++r)
+                if (!done[r] && bnorm[r] > 0) resid[r] = fin[r] / bnorm[r];
+            break;
+        }
     }
+    cleanup2();
+    cudaFreeHost(hflags);
+    hflags = nullptr;
     // port currents -> Y -> Z
     std::vector<double2> xh(size_t(R) * n);
     GM_CUDA(cudaMemcpyAsync(xh.data(), x, xh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1493,6 +1734,34 @@ void invalidate_precond_factors(pfft_plan *p) {
     if (p->pc) p->pc->slot_omega.clear();
 }
 }  // namespace sie
+
+extern "C" int pfft_precond_set_method(pfft_plan *p, int32_t method) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_precond_set_method: NULL plan");
+    if (method != SIE_PC_AUTO && method != SIE_PC_BAND && method != SIE_PC_ND)
+        return fail(SIE_ERR_ARG, "pfft_precond_set_method: unknown method");
+    if (method != p->pc_method) {
+        cudaDeviceSynchronize();   // no solve of this plan may still use the state
+        plan_free_precond(p);
+        p->pc_method = method;
+    }
+    return SIE_OK;
+}
+
+extern "C" int pfft_precond_nd_info(pfft_plan *p, int32_t *method_used, int32_t *fronts, int64_t *nnz_factor,
+                                    int32_t *max_front, int64_t *flops) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_precond_nd_info: NULL plan");
+    if (!p->pc) {
+        int rc = build_symbolic(p);
+        if (rc) { plan_free_precond(p); return rc; }
+    }
+    if (method_used) *method_used = p->pc->nd ? SIE_PC_ND : SIE_PC_BAND;
+    if (fronts) *fronts = 0;
+    if (nnz_factor) *nnz_factor = 0;
+    if (max_front) *max_front = 0;
+    if (flops) *flops = 0;
+    if (p->pc->nd) nd_info(p->pc->nd, fronts, nnz_factor, max_front, flops);
+    return SIE_OK;
+}
 
 extern "C" int pfft_precond_info(pfft_plan *p, int32_t *band_width, int64_t *unknowns, int64_t *blocks) {
     if (!p) return fail(SIE_ERR_ARG, "pfft_precond_info: NULL plan");

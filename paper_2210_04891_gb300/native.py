@@ -18,13 +18,15 @@ ERRORS = {-1: "SIE_ERR_ARG", -2: "SIE_ERR_NONMANIFOLD", -3: "SIE_ERR_BAD_PORT", 
 SPACE_LOOP, SPACE_BRANCH = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 KERNEL_STATIC, KERNEL_LOSSY = 0, 1
+PC_AUTO, PC_BAND, PC_ND = 0, 1, 2
 
 # every symbol include/sie.h declares
 EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basis_build", "sie_loops_destroy", "sie_loops_export",
            "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_lossy", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "pfft_plan_set_surface_model", "sie_postprocess", "sie_batch_create", "sie_batch_destroy",
-           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
+           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info",
+           "pfft_precond_set_method", "pfft_precond_nd_info", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
            "sie_mlp_param_count", "sie_mlp_get_params", "sie_mlp_set_params", "sie_mlp_forward", "sie_mlp_grad",
            "sie_mlp_train", "pfft_branch_features", "pfft_branch_probe_target", "pfft_plan_set_learned",
            "sie_selftest_bounded_wait", "sie_last_error"]
@@ -108,6 +110,8 @@ def lib():
     L.sie_postprocess.argtypes = [P, P, I32, P, I32, P, P, P, P]
     L.sie_batch_create.argtypes = [P, I32, PP]
     L.pfft_precond_info.argtypes = [P, P, P, P]
+    L.pfft_precond_set_method.argtypes = [P, I32]
+    L.pfft_precond_nd_info.argtypes = [P, P, P, P, P, P]
     L.sie_mlp_create.argtypes = [I32, ctypes.c_uint64, PP]
     L.sie_mlp_destroy.argtypes = [P]
     L.sie_mlp_param_count.argtypes = [P]

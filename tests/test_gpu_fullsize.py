@@ -17,7 +17,10 @@ those rows of the product exactly (the grid part is computed in full).  Rows of
 24 random branches (branch space) and of 12 loops (loop space, 10 of at most 6
 branches and 2 of 40 to 80) for 3 of the 128 right-hand sides, FP64 within
 1e-10 and mixed within 1e-5 of the oracle (relative 2-norm over the sampled
-rows), in the 128-right-hand-side launch the benchmark times.
+rows), in the 128-right-hand-side launch the benchmark times.  The same loop
+rows of the lossy-kernel product (kernel exp(-jkR)/R, one complex spectrum and
+one set of complex near blocks per frequency) against the oracle's lossy pFFT
+restricted in the same way, FP64 1e-10 and mixed 1e-5.
 """
 import numpy as np
 import pytest
@@ -128,3 +131,29 @@ def test_sampled_rows_match_oracle_at_bench_size(bondwires, sampled_oracle):
             ref_b = S.branch_product(xa[r], om[r])[branches]
             assert sampled_rel(yl[r, loops], ref_l) < tol, (prec, r)
             assert sampled_rel(yb[r, branches], ref_b) < tol, (prec, r)
+
+
+def test_lossy_sampled_rows_match_oracle_at_bench_size(bondwires, sampled_oracle):
+    # the lossy-kernel product (per-frequency complex spectra and near blocks, 16
+    # frequencies in one 128-right-hand-side launch) against the oracle's lossy pFFT
+    # restricted to the same sampled rows, at 1 MHz, 100 MHz and 10 GHz
+    from oracle.lossy import LossyPfftSystem
+    from oracle.pfft import PfftParams
+    from paper_2210_04891_gb300 import native as N
+    w, L, P, om, x = bondwires
+    O, S, loops, branches = sampled_oracle
+    m = w["mesh"]
+    M = api.Mesh.from_synth(m)
+    Ll = api.Loops(M, m.ports)
+    Pl = api.Plan(M, Ll, dict(grid=w["grid"], order=3, near_factor=4.0, near_min_diam=2.0, n_touch=16, h0=0.0,
+                              kernel=N.KERNEL_LOSSY))
+    targets = np.unique(np.concatenate([S.op.targets]))
+    SL = LossyPfftSystem(m, O, PfftParams(grid=w["grid"], order=3, near_factor=4.0, near_min_diam=2.0, n_touch=16,
+                                          h0=0.0), targets=targets)
+    xn = x.cpu().numpy()
+    sampled = (0, 63, 127)
+    refs = {r: SL.matvec(xn[r], om[r])[loops] for r in sampled}
+    for prec, tol in ((PREC_FP64, 1e-10), (PREC_MIXED, 1e-5)):
+        yl = api.pfft_matvec(Pl, x, om, SPACE_LOOP, prec).cpu().numpy()
+        for r in sampled:
+            assert sampled_rel(yl[r, loops], refs[r]) < tol, (prec, r)

@@ -12,7 +12,13 @@ ports = 32 right-hand sides).  The oracle cannot build this operator, so:
 * the grid convolution at that size against direct sums over all 2.1M nodes
   at sampled output nodes (the oracle's kernel, oracle/lossy.py at k = 0);
 * the FP64 operator is complex symmetric, u^T Z v = v^T Z u;
-* the mixed form agrees with the FP64 form within the mixed bound.
+* the mixed form agrees with the FP64 form within the mixed bound;
+* sampled rows against the oracle pFFT on the whole structure with its near
+  list restricted to the sampled rows' triangles and B applied triangle by
+  triangle: 24 branch rows and 12 loop rows for two right-hand sides of the
+  32-right-hand-side launch (CUDA-core near field) and of a 96-right-hand-side
+  launch (tensor-core near field in the mixed form), FP64 1e-10 and mixed
+  1e-5, with element-wise checks beside the 2-norm.
 """
 import numpy as np
 import pytest
@@ -108,3 +114,61 @@ def test_pdn_mixed_matches_fp64(pdn):
     y32 = api.pfft_matvec(P, x, om, SPACE_LOOP, PREC_MIXED).cpu().numpy()
     err = np.linalg.norm(y32 - y64, axis=1) / np.linalg.norm(y64, axis=1)
     assert err.max() < 1e-5, err
+
+
+@pytest.fixture(scope="module")
+def pdn_sampled_oracle(pdn):
+    # the oracle pFFT on the full plane pair with its near list restricted to the
+    # triangles of 24 random branches and 12 loops (10 of at most 6 branches, 2 of
+    # 40 to 80), applying B and B^T triangle by triangle (no stored B)
+    w, L, P, om = pdn
+    m = w["mesh"]
+    O = build_loops(m)
+    A = O.A.tocsr()
+    ln = np.diff(A.indptr)[:O.nl - O.n_ports]
+    rng = np.random.default_rng(13)
+    loops = np.sort(np.concatenate([rng.choice(np.nonzero(ln <= 6)[0], 10, replace=False),
+                                    rng.choice(np.nonzero((ln >= 40) & (ln <= 80))[0], 2, replace=False)]))
+    loop_br = np.concatenate([A.indices[A.indptr[l]:A.indptr[l + 1]] for l in loops])
+    branches = np.sort(rng.choice(O.nb, 24, replace=False))
+    tris = np.unique(O.br_tri[np.concatenate([branches, loop_br])].ravel())
+    S = PfftSystem(m, O, PfftParams(grid=w["grid"], order=3, near_factor=4.0, near_min_diam=2.0, n_touch=16,
+                                    h0=0.0), targets=tris, lean=True)
+    return O, S, loops, branches
+
+
+def elementwise_rel(a, b, floor=1e-3):
+    # largest relative error over the entries above floor times the largest entry
+    big = np.abs(b) > floor * np.abs(b).max()
+    return float((np.abs(a - b)[big] / np.abs(b)[big]).max())
+
+
+@pytest.mark.parametrize("nrep", [1, 3])
+def test_pdn_sampled_rows_match_oracle(pdn, pdn_sampled_oracle, nrep):
+    # 32 right-hand sides (CUDA-core near gather) and 96 (tensor-core near field in
+    # the mixed form): the GPU's branch-space rows and loop-space rows for two of
+    # them against the oracle, FP64 within 1e-10 and mixed within 1e-5 (relative
+    # 2-norm over the sampled rows) and element by element within 100 times that;
+    # the loop rows are A's rows applied to the oracle's exact branch rows
+    w, L, P, om = pdn
+    O, S, loops, branches = pdn_sampled_oracle
+    oms = np.tile(om, nrep)
+    R = oms.size
+    x = synth.complex_gaussian(O.nl, R, seed=71)
+    A = O.A.tocsr()[:, :O.nb]
+    alpha = np.ascontiguousarray(np.asarray(A.T @ x.T).T)  # the loop currents' branch currents
+    sampled = (0, R - 1) if nrep == 1 else (5, R - 6)
+    refs = {}
+    for r in sampled:
+        bp = S.branch_product(alpha[r], oms[r])
+        refs[r] = (bp[branches], (A[loops] @ bp))
+    xt, at = torch.from_numpy(x).cuda(), torch.from_numpy(alpha).cuda()
+    for prec, tol in ((PREC_FP64, 1e-10), (PREC_MIXED, 1e-5)):
+        yl = api.pfft_matvec(P, xt, oms, SPACE_LOOP, prec).cpu().numpy()
+        yb = api.pfft_matvec(P, at, oms, SPACE_BRANCH, prec).cpu().numpy()
+        for r in sampled:
+            rb, rl = refs[r]
+            assert sampled_rel(yb[r, branches], rb) < tol, (prec, r, "branch")
+            assert sampled_rel(yl[r, loops], rl) < tol, (prec, r, "loop")
+            assert elementwise_rel(yb[r, branches], rb) < 100 * tol, (prec, r)
+            assert elementwise_rel(yl[r, loops], rl) < 100 * tol, (prec, r)

@@ -128,3 +128,24 @@ def test_native_grid_blocks_match(bar):
     b = P.grid_blocks(ti, tj, native=True)
     assert a.shape == b.shape and a.shape[0] > 100 and np.any(ti == tj) and np.any(ti != tj)
     assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("make", [synth.tiny_bar, synth.tiny_wires])
+def test_lean_projection_equals_sparse_B(make):
+    # steps 1 and 3 applied triangle by triangle (no stored B) against the sparse
+    # projection matrix: Q_g = B alpha and B^T phi to rounding, in chunks that
+    # split the mesh
+    m = make()
+    L = build_loops(m)
+    prm = PfftParams(grid=(8, 8, 4))
+    P = Pfft(m, L, prm)
+    Pl = Pfft(m, L, prm, lean=True)
+    a = synth.complex_gaussian(L.nb, 1, seed=3)[0]
+    q = P.B @ a
+    ql = Pl.project(a, chunk=37).reshape(-1)
+    assert np.abs(q - ql).max() < 1e-14 * np.abs(q).max()
+    phi = synth.complex_gaussian(3 * P.ng, 1, seed=4)[0]
+    b = P.B.T @ phi
+    bl = Pl.interpolate(phi.reshape(3, *P.N), chunk=41)
+    assert np.abs(b - bl).max() < 1e-14 * np.abs(b).max()
+    assert np.abs(P.far(a) - Pl.far(a)).max() < 1e-13 * np.abs(P.far(a)).max()
