@@ -355,13 +355,22 @@ def batch_main(args, ws, dist=None, n_total=None):
         B.solve(warm, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)
         t_first = time.perf_counter() - t0
         t0 = time.perf_counter()
-        res = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)
+        res = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=True, graph=True)
         dt = time.perf_counter() - t0
-        gm = {"tol": 1e-6, "seconds": dt, "solves": int(sum(len(f) for f in fr)),
+        r0 = B.stats()["replays"]
+        t0 = time.perf_counter()
+        res_t = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=True)
+        dt_t = time.perf_counter() - t0
+        gm = {"tol": 1e-6, "form": "mixed with FP64 refinement", "seconds": dt,
+              "step": "one CUDA graph replay per Arnoldi step of all plans (sie_batch_solve_graph)",
+              "solves": int(sum(len(f) for f in fr)),
               "iterations_max": int(max(st["iterations_max"] for _, st in res)),
               "converged": bool(all(st["converged"] for _, st in res)),
-              "includes": "per-frequency band factorisations of every plan",
+              "equal_to_threaded": bool(all(np.array_equal(a[0], b[0]) for a, b in zip(res, res_t))),
+              "threaded_seconds": dt_t,
+              "includes": "per-frequency factorisations of every plan's preconditioner",
               "first_solve_seconds": t_first}
+        del r0
     learned = None
     if args.learned_eval > 0 and dist is None:
         # train the correction on the first geometries' features and probing targets at
@@ -640,6 +649,11 @@ def main():
     e2e = {"value": e2e_val, "unit": "matvec/s", "h2d_bytes_per_step": int(xh.numel() * 16),
            "d2h_bytes_per_step": int(zh.numel() * 16)}
 
+    # factorisation route of the preconditioner (band LDL^T or nested dissection)
+    ndi = api.precond_nd_info(P)
+    precond_route = ({"method": "nested dissection", "fronts": ndi["fronts"], "factor_entries": ndi["nnz"],
+                      "max_front": ndi["max_front"], "complex_macs": ndi["flops"]}
+                     if ndi["method"] == N.PC_ND else {"method": "band", **api.precond_info(P)})
     gm = None
     if not args.no_gmres:
         # residual: the preconditioned relative residual of the solve (FP64 for
@@ -707,6 +721,7 @@ def main():
                 "config": {"workload": w["name"], "triangles": int(m.nt), "loops": int(L.nl),
                            "grid": list(w["grid"]), "rhs_per_step": R, "frequencies": len(freqs), "ports": nports,
                            "near_pairs": info["n_near_pairs"],
+                           "precond": precond_route,
                            "step": ("z = P^-1 A Z_b A^T x (mixed)" if args.step != "matvec" else "y = A Z_b A^T x (mixed)")
                            + (", replayed as a CUDA graph" if args.graph else ""),
                            "l2": "inputs larger than L2 (per-step grids %.2f GB, x-padded grids %.2f GB)" % (

@@ -324,6 +324,21 @@ int sie_batch_solve(sie_batch *b, const double *const *freqs, const int32_t *nf,
                     const int32_t *np, const sie_solve_opts *opts, sie_c64 *const *Z_out,
                     sie_solve_stats *st_out);
 
+/* sie_batch_solve with every plan's GMRES (Eq. LoopWithP) stepped in lockstep
+ * under CUDA graph replay: the plans' set-ups (workspace, preconditioner
+ * factors) and the ends of their restart cycles run concurrently on host
+ * threads; within a cycle one Arnoldi step of every plan whose cycle is still
+ * running (its product and preconditioner, classical Gram-Schmidt applied
+ * twice, the Givens rotations and the convergence masks, all on the device,
+ * the step index read on the device) is captured once into a graph on the
+ * plans' streams and replayed with one launch per step; the graph is captured
+ * again when a plan's cycle ends.  Per plan the arithmetic is that of sie_solve
+ * (same kernels, same order), so Z and the statistics equal sie_solve's.
+ * Arguments and errors as sie_batch_solve. */
+int sie_batch_solve_graph(sie_batch *b, const double *const *freqs, const int32_t *nf, const int32_t *const *ports,
+                          const int32_t *np, const sie_solve_opts *opts, sie_c64 *const *Z_out,
+                          sie_solve_stats *st_out);
+
 /* Grid autotuning.  Candidates: the base grid, half and double it on every
  * axis, and the base with one axis doubled (axes kept within the plan's size
  * rules, at most SIE_TUNE_MAX).  Each is built, its FP64 loop-space product of

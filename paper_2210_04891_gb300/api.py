@@ -458,8 +458,9 @@ class Batch:
         return dict(captures=c.value, replays=r.value)
 
     def solve(self, freqs, ports=None, tol=1e-6, restart=200, max_iter=2000, precond=1, prec=N.PREC_FP64,
-              refine=False):
-        """[(Z_i, stats_i)] of sie_solve for every plan at once; freqs[i] per plan."""
+              refine=False, graph=False):
+        """[(Z_i, stats_i)] of sie_solve for every plan at once; freqs[i] per plan.
+        graph=True: sie_batch_solve_graph (one graph replay per Arnoldi step of all plans)."""
         n = len(self.plans)
         fs = [np.ascontiguousarray(f, np.float64) for f in freqs]
         prs = [np.arange(p.np, dtype=np.int32) if ports is None or ports[i] is None
@@ -472,7 +473,8 @@ class Batch:
         pp = (ctypes.c_void_p * n)(*[q.ctypes.data for q in prs])
         npr = np.array([q.shape[0] for q in prs], np.int32)
         zp = (ctypes.c_void_p * n)(*[z.ctypes.data for z in Zs])
-        rc = lib().sie_batch_solve(self.h, fp, _ptr(nf), pp, _ptr(npr), ctypes.byref(o), zp, st)
+        fn = lib().sie_batch_solve_graph if graph else lib().sie_batch_solve
+        rc = fn(self.h, fp, _ptr(nf), pp, _ptr(npr), ctypes.byref(o), zp, st)
         if rc not in (N.SIE_OK, -6):
             check(rc)
         out = []

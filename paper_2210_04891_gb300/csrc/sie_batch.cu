@@ -284,3 +284,182 @@ extern "C" int sie_batch_solve(sie_batch *b, const double *const *freqs, const i
         if (rcs[i]) return fail(rcs[i], "sie_batch_solve: plan " + std::to_string(i) + ": " + msgs[i]);
     return SIE_OK;
 }
+
+namespace {
+
+// Runs fn(i) for i in [0, n) on one host thread each (the plans' set-ups and
+// cycle ends synchronise their own streams; threads let them overlap).
+template <typename F>
+void each_plan(sie_batch *b, const std::vector<size_t> &which, F fn) {
+    std::vector<std::thread> th;
+    th.reserve(which.size());
+    for (size_t i : which)
+        th.emplace_back([&, i]() {
+            cudaSetDevice(b->device);
+            fn(i);
+        });
+    for (auto &t : th) t.join();
+}
+
+// One Arnoldi step of every run in `set`, each on its plan's batch stream,
+// forked from and joined back into the origin stream.
+int enqueue_gmres_step(sie_batch *b, const std::vector<GmresRun *> &runs, const std::vector<size_t> &set,
+                       std::vector<int64_t> &launches) {
+    SIE_CUDA(cudaEventRecord(b->fork, b->origin));
+    for (size_t i : set) {
+        SIE_CUDA(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        const int64_t before = gmres_plan_launches(runs[i]);
+        int rc = gmres_step(runs[i], true);
+        if (rc) return rc;
+        launches[i] = gmres_plan_launches(runs[i]) - before;
+        SIE_CUDA(cudaEventRecord(b->done[i], b->streams[i]));
+        SIE_CUDA(cudaStreamWaitEvent(b->origin, b->done[i], 0));
+    }
+    return SIE_OK;
+}
+
+int capture_gmres_step(sie_batch *b, const std::vector<GmresRun *> &runs, const std::vector<size_t> &set,
+                       std::vector<int64_t> &launches, cudaGraphExec_t *exec) {
+    *exec = nullptr;
+    std::vector<bool> prof(b->plans.size());
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        prof[i] = b->plans[i]->prof_on;
+        b->plans[i]->prof_on = false;
+    }
+    auto restore = [&]() {
+        for (size_t i = 0; i < b->plans.size(); ++i) b->plans[i]->prof_on = prof[i];
+    };
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        restore();
+        return fail(SIE_ERR_CUDA, std::string("sie_batch_solve_graph: cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    }
+    const int rc = enqueue_gmres_step(b, runs, set, launches);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->origin, &graph);
+    restore();
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        return rc ? rc : fail(SIE_ERR_CUDA, std::string("sie_batch_solve_graph: capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        return fail(SIE_ERR_CUDA, std::string("sie_batch_solve_graph: cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    ++b->captures;
+    return SIE_OK;
+}
+
+}  // namespace
+
+extern "C" int sie_batch_solve_graph(sie_batch *b, const double *const *freqs, const int32_t *nf,
+                                     const int32_t *const *ports, const int32_t *np, const sie_solve_opts *opts,
+                                     sie_c64 *const *Z_out, sie_solve_stats *st_out) {
+    if (!b || !freqs || !nf || !ports || !np || !opts || !Z_out)
+        return fail(SIE_ERR_ARG, "sie_batch_solve_graph: NULL argument");
+    const size_t n = b->plans.size();
+    SIE_CUDA(cudaSetDevice(b->device));
+    (void)cudaGetLastError();
+    std::vector<GmresRun *> runs(n, nullptr);
+    std::vector<int> rcs(n, SIE_OK);
+    std::vector<std::string> msgs(n);
+    std::vector<size_t> all(n);
+    for (size_t i = 0; i < n; ++i) all[i] = i;
+    auto first_error = [&](const char *what) -> int {
+        for (size_t i = 0; i < n; ++i)
+            if (rcs[i]) return fail(rcs[i], std::string("sie_batch_solve_graph: ") + what + " of plan " +
+                                                std::to_string(i) + ": " + msgs[i]);
+        return SIE_OK;
+    };
+    auto cleanup = [&]() {
+        for (GmresRun *g : runs)
+            if (g) gmres_free(g);
+    };
+    // set-up of every plan (workspace, preconditioner factors) on its batch stream
+    each_plan(b, all, [&](size_t i) {
+        rcs[i] = gmres_create(b->plans[i], freqs[i], nf[i], ports[i], np[i], opts, b->streams[i], &runs[i]);
+        if (rcs[i]) msgs[i] = sie_last_error();
+    });
+    if (int rc = first_error("set-up")) { cleanup(); return rc; }
+    std::vector<size_t> live(all);           // runs not finished
+    std::vector<int64_t> launches(n, 0);
+    while (!live.empty()) {
+        std::vector<char> need(n, 0);
+        each_plan(b, live, [&](size_t i) {
+            bool nd = false;
+            rcs[i] = gmres_top(runs[i], nd);
+            need[i] = nd;
+            if (rcs[i]) msgs[i] = sie_last_error();
+        });
+        if (int rc = first_error("residual")) { cleanup(); return rc; }
+        std::vector<size_t> cyc;
+        for (size_t i : live)
+            if (need[i]) cyc.push_back(i);
+        if (cyc.empty()) break;
+        for (size_t i : cyc)
+            if (int rc = gmres_begin(runs[i])) { cleanup(); return rc; }
+        // the cycle's first step eagerly (it uploads each product's coefficients and
+        // sets the kernels' attributes), then the running set's step as one graph
+        for (size_t i : cyc)
+            if (int rc = gmres_step(runs[i], false)) { cleanup(); return rc; }
+        std::vector<size_t> running;
+        for (size_t i : cyc) {
+            SIE_CUDA(cudaStreamSynchronize(b->streams[i]));
+            if (!gmres_stepped(runs[i])) running.push_back(i);
+        }
+        cudaGraphExec_t exec = nullptr;
+        while (!running.empty()) {
+            if (!exec) {
+                if (int rc = capture_gmres_step(b, runs, running, launches, &exec)) { cleanup(); return rc; }
+            }
+            cudaError_t e = cudaGraphLaunch(exec, b->origin);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
+            if (e != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                cleanup();
+                return fail(SIE_ERR_CUDA, std::string("sie_batch_solve_graph: replay: ") + cudaGetErrorString(e));
+            }
+            ++b->replays;
+            std::vector<size_t> still;
+            for (size_t i : running) {
+                b->plans[i]->launches += launches[i];
+                if (!gmres_stepped(runs[i])) still.push_back(i);
+            }
+            if (still.size() != running.size()) {   // a cycle ended: capture the smaller set
+                cudaGraphExecDestroy(exec);
+                exec = nullptr;
+            }
+            running.swap(still);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        std::vector<char> cont(n, 0);
+        each_plan(b, cyc, [&](size_t i) {
+            bool c = false;
+            rcs[i] = gmres_end(runs[i], c);
+            cont[i] = c;
+            if (rcs[i]) msgs[i] = sie_last_error();
+        });
+        if (int rc = first_error("cycle")) { cleanup(); return rc; }
+        // a run leaves when its top needed no cycle (converged, capped or broken
+        // down) or when its cycle end says the solve is over
+        std::vector<size_t> next;
+        for (size_t i : live)
+            if (need[i] && cont[i]) next.push_back(i);
+        live.swap(next);
+    }
+    int first_rc = SIE_OK;
+    std::string first_msg;
+    for (size_t i = 0; i < n; ++i) {
+        const int rc = gmres_finish(runs[i], Z_out[i], st_out ? &st_out[i] : nullptr);
+        runs[i] = nullptr;
+        if (rc && !first_rc) {
+            first_rc = rc;
+            first_msg = "sie_batch_solve_graph: plan " + std::to_string(i) + ": " + sie_last_error();
+        }
+    }
+    if (first_rc) return fail(first_rc, first_msg);
+    return SIE_OK;
+}

@@ -255,6 +255,26 @@ int64_t nd_workspace_size(const NdState *s);
 int64_t nd_update_size(const NdState *s);
 void nd_info(const NdState *s, int32_t *fronts, int64_t *nnz, int32_t *max_front, int64_t *flops);
 void nd_free(NdState *s);
+// A port solve (Eq. LoopWithP) in steps (sie_solve.cu): gmres_create checks the
+// arguments and sets up (workspace, right-hand sides, preconditioner factors,
+// ||P^-1 b||) on stream st; gmres_top decides whether another cycle is needed;
+// gmres_begin starts one; gmres_step enqueues one Arnoldi step (graph = true:
+// every launch independent of the step index, for capture); after the stream
+// has synchronised gmres_stepped tells whether the cycle is over; gmres_end
+// closes the cycle (cont = false: the solve is over); gmres_finish extracts Z
+// and the statistics and frees the run (gmres_free frees it otherwise).
+struct GmresRun;
+int gmres_create(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
+                 const sie_solve_opts *opts, cudaStream_t st, GmresRun **out);
+int gmres_top(GmresRun *g, bool &need);
+int gmres_begin(GmresRun *g);
+int gmres_step(GmresRun *g, bool graph);
+bool gmres_stepped(GmresRun *g);
+int gmres_end(GmresRun *g, bool &cont);
+int gmres_finish(GmresRun *g, sie_c64 *Z_out, sie_solve_stats *st_out);
+void gmres_free(GmresRun *g);
+cudaStream_t gmres_stream(const GmresRun *g);
+int64_t gmres_plan_launches(const GmresRun *g);
 // Complex padded table of exp(-jkR)/R (1/delta given) into Hc [Mx][My][Mz]; its folded
 // spectrum scaled by 1/(Mx My Mz) into H64 / H32 (Hc may be overwritten).
 int lossy_fill_table(pfft_plan *p, double inv_delta, double2 *Hc, cudaStream_t s);

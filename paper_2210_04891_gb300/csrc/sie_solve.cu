@@ -1195,11 +1195,15 @@ int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int pr
 // Krylov basis layout [m+1][R][n]: vector j of right-hand side r at
 // V + j * kstride + r * ldv, so each basis vector is a contiguous [R][n] block
 // the batched matvec can take directly.
-// h[r][j] = <V_j[r], w[r]> for j < k (one CTA per (r, j)).
+// h[r][j] = <V_j[r], w[r]> for j < k (one CTA per (r, j), k CTAs per right-hand
+// side).  With kdev, only j <= *kdev are taken (the Arnoldi step index read on
+// the device, so that one captured launch serves every step).
 __global__ void k_dots(const double2 *__restrict__ V, int64_t ldv, int64_t kstride, const double2 *__restrict__ w,
-                       int64_t n, int32_t k, const int32_t *__restrict__ active, double2 *__restrict__ h, int32_t ldh) {
+                       int64_t n, int32_t k, const int32_t *__restrict__ active, double2 *__restrict__ h, int32_t ldh,
+                       const int32_t *__restrict__ kdev = nullptr) {
     const int32_t r = blockIdx.x / k, j = blockIdx.x % k;
     if (!active[r]) return;
+    if (kdev && j > *kdev) return;
     const double2 *v = V + int64_t(j) * kstride + int64_t(r) * ldv;
     const double2 *x = w + int64_t(r) * ldv;
     double re = 0.0, im = 0.0;
@@ -1220,14 +1224,15 @@ __global__ void k_dots(const double2 *__restrict__ V, int64_t ldv, int64_t kstri
     }
 }
 
-// w[r] -= sum_{j<k} h[r][j] V_j[r]
+// w[r] -= sum_{j<k} h[r][j] V_j[r]   (k = *kdev + 1 with kdev)
 __global__ void k_orth_update(const double2 *__restrict__ V, int64_t ldv, int64_t kstride, double2 *__restrict__ w,
                               int64_t n, int32_t k, const int32_t *__restrict__ active, const double2 *__restrict__ h,
-                              int32_t ldh, int32_t R) {
+                              int32_t ldh, int32_t R, const int32_t *__restrict__ kdev = nullptr) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n * R) return;
     int64_t r = i / n, e = i % n;
     if (!active[r]) return;
+    if (kdev) k = *kdev + 1;
     double2 acc = w[r * ldv + e];
     const double2 *hr = h + r * ldh;
     const double2 *v = V + r * ldv + e;
@@ -1235,16 +1240,22 @@ __global__ void k_orth_update(const double2 *__restrict__ V, int64_t ldv, int64_
     w[r * ldv + e] = acc;
 }
 
-// V_k[r] = w[r] * scale[r]
+// V_k[r] = w[r] * scale[r] (k = *kdev + 1 with kdev), also into vin when given
+// (the fixed input buffer of the next step's product)
 __global__ void k_scale_store(const double2 *__restrict__ w, int64_t ldv, double2 *__restrict__ V, int64_t kstride,
                               int32_t k, int64_t n, const double *__restrict__ scale, const int32_t *__restrict__ active,
-                              int32_t R) {
+                              int32_t R, const int32_t *__restrict__ kdev = nullptr, double2 *__restrict__ vin = nullptr) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n * R) return;
     int64_t r = i / n, e = i % n;
     if (!active[r]) return;
-    V[int64_t(k) * kstride + r * ldv + e] = cscale(w[r * ldv + e], scale[r]);
+    if (kdev) k = *kdev + 1;
+    const double2 v = cscale(w[r * ldv + e], scale[r]);
+    V[int64_t(k) * kstride + r * ldv + e] = v;
+    if (vin) vin[r * ldv + e] = v;
 }
+
+__global__ void k_step_advance(int32_t *kdev) { *kdev += 1; }
 
 // x[r] += sum_j y[r][j] V_j[r]
 __global__ void k_update_x(const double2 *__restrict__ V, int64_t ldv, int64_t kstride, double2 *__restrict__ x,
@@ -1301,9 +1312,10 @@ __global__ void k_cycle_start(GmresDev d, int32_t m, int32_t R, const double *__
 // counts the right-hand sides still running.
 __global__ void k_givens(GmresDev d, int32_t k, int32_t m, int32_t R, const double2 *__restrict__ h1,
                          const double2 *__restrict__ h2, int32_t ldh, const double *__restrict__ hn, double tol,
-                         int32_t max_iter) {
+                         int32_t max_iter, const int32_t *__restrict__ kdev = nullptr) {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
+    if (kdev) k = *kdev;
     if (!d.run[r]) {
         d.scale[r] = 0.0;
         return;
@@ -1387,344 +1399,481 @@ extern "C" int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t 
     return SIE_OK;
 }
 
-extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
-                         const sie_solve_opts *opts, sie_c64 *Z_out, sie_solve_stats *st_out) {
-    if (!p || !freqs || nf < 1 || !ports || np < 1 || !opts || !Z_out) return fail(SIE_ERR_ARG, "sie_solve: bad argument");
+namespace sie {
+
+// One port solve (Eq. LoopWithP) as a sequence of steps, so that sie_solve can
+// drive it eagerly and a batch can capture one Arnoldi step of many plans into
+// one CUDA graph and replay it (the step reads its index k on the device and
+// takes its product's input from the fixed buffer vin).
+struct GmresRun {
+    pfft_plan *p = nullptr;
+    cudaStream_t st = nullptr;
+    sie_solve_opts o{};
+    int32_t nf = 0, np = 0, R = 0, m = 0;
+    int64_t n = 0, ldv = 0, kstride = 0;
+    std::vector<double> om;
+    std::vector<int32_t> ports;
+    bool use_pc = true, refine = false;
+    int outer_prec = SIE_PREC_FP64;
+    // device
+    double2 *V = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *t = nullptr, *dh = nullptr, *dh2 = nullptr,
+            *dhn = nullptr, *dy = nullptr, *rv = nullptr, *dvec = nullptr, *vin = nullptr;
+    int32_t *act = nullptr, *kdev = nullptr;
+    double *dnorm = nullptr, *dbeta = nullptr;
+    GmresDev gd{};
+    int32_t *hflags = nullptr;   // pinned: running right-hand sides, breakdown
+    // host
+    std::vector<int32_t> active, done, iters;
+    std::vector<double> bnorm, resid;
+    int64_t matvecs = 0;
+    bool breakdown = false, first = true, mixed_since_fp64 = false;
+    double cycle_start = 1.0, tol_inner = 0.0, rho_fp64 = 0.0;
+    int32_t k_host = 0;
+    std::chrono::steady_clock::time_point t0;
+
+    ~GmresRun() {
+        for (void *a : {(void *)V, (void *)w, (void *)b, (void *)x, (void *)t, (void *)dh, (void *)dh2, (void *)dhn,
+                        (void *)dy, (void *)rv, (void *)dvec, (void *)vin, (void *)act, (void *)kdev, (void *)dnorm,
+                        (void *)dbeta, (void *)gd.H, (void *)gd.cs, (void *)gd.sn, (void *)gd.g, (void *)gd.run,
+                        (void *)gd.kdone, (void *)gd.iters, (void *)gd.resid, (void *)gd.bnorm, (void *)gd.scale,
+                        (void *)gd.nrun})
+            if (a) cudaFreeAsync(a, st);
+        if (hflags) cudaFreeHost(hflags);
+    }
+    // out = P^-1 Z in (the product from the fixed coefficients; launch = true: no
+    // coefficient upload, the form a graph captures)
+    int apply_op(const double2 *in, double2 *out, int prec, bool launch_only) {
+        int r2 = launch_only ? matvec_launch(p, in, use_pc ? t : out, R, SIE_SPACE_LOOP, prec, st)
+                             : matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, prec, st);
+        if (r2) return r2;
+        if (use_pc) return pc_apply_async(p, t, out, R, prec, st);
+        return SIE_OK;
+    }
+    // ||vec[r]|| into dnorm (device) through k_dots on a one-vector basis
+    int norms_dev(const double2 *vec, const int32_t *mask) {
+        k_dots<<<R, 256, 0, st>>>(vec, ldv, ldv, vec, n, 1, mask, dhn, 1);
+        SIE_LAUNCH_CHECK(p);
+        k_norms<<<unsigned((R + 127) / 128), 128, 0, st>>>(dhn, 1, R, dnorm);
+        SIE_LAUNCH_CHECK(p);
+        return SIE_OK;
+    }
+    int read_norms(std::vector<double> &nr) {
+        nr.resize(R);
+        SIE_CUDA(cudaMemcpyAsync(nr.data(), dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        SIE_CUDA(cudaStreamSynchronize(st));
+        return SIE_OK;
+    }
+    // residual r = b - Z x with the FP64 product
+    int residual_fp64() {
+        int rc = matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, SIE_PREC_FP64, st);
+        if (rc) return rc;
+        k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
+        SIE_LAUNCH_CHECK(p);
+        matvecs += R;
+        return SIE_OK;
+    }
+};
+
+int gmres_create(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
+                 const sie_solve_opts *opts, cudaStream_t st, GmresRun **out) {
+    *out = nullptr;
+    if (!p || !freqs || nf < 1 || !ports || np < 1 || !opts) return fail(SIE_ERR_ARG, "sie_solve: bad argument");
     for (int32_t i = 0; i < np; ++i)
         if (ports[i] < 0 || ports[i] >= p->np) return fail(SIE_ERR_ARG, "sie_solve: port index out of range");
     for (int32_t i = 0; i < nf; ++i)
         if (!(freqs[i] > 0.0 || (freqs[i] == 0.0 && dc_defined(p))) || !std::isfinite(freqs[i]))
             return fail(SIE_ERR_ARG, "sie_solve: frequencies must be positive (DC needs the slab surface model on "
                                      "every conductor: the classic surface impedance vanishes there)");
-    const int m = std::max(1, std::min(opts->restart, 1000));
     if (!(opts->tol > 0.0) || opts->max_iter < 1) return fail(SIE_ERR_ARG, "sie_solve: bad tolerance or iteration cap");
     if (opts->prec != SIE_PREC_FP64 && opts->prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "sie_solve: bad precision");
     (void)cudaGetLastError();
-    auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = p->stream;
-    const int32_t R = nf * np;
-    const int64_t n = p->nl;
-    std::vector<double> om(R);
+    auto *g = new (std::nothrow) GmresRun;
+    if (!g) return fail(SIE_ERR_OOM, "sie_solve: out of host memory");
+    g->t0 = std::chrono::steady_clock::now();
+    g->p = p;
+    g->st = st;
+    g->o = *opts;
+    g->nf = nf;
+    g->np = np;
+    g->m = std::max(1, std::min(opts->restart, 1000));
+    g->R = nf * np;
+    g->n = p->nl;
+    g->ldv = g->n;
+    g->kstride = int64_t(g->R) * g->n;
+    g->ports.assign(ports, ports + np);
+    g->om.resize(g->R);
     for (int32_t f = 0; f < nf; ++f)
-        for (int32_t q = 0; q < np; ++q) om[f * np + q] = 2.0 * M_PI * freqs[f];
-    const bool use_pc = opts->precond != 0;
-    // iterative refinement: restart residuals and the convergence test in FP64
-    const int outer_prec = (opts->refine && opts->prec == SIE_PREC_MIXED) ? SIE_PREC_FP64 : opts->prec;
-    const bool refine = outer_prec != opts->prec;
+        for (int32_t q = 0; q < np; ++q) g->om[f * np + q] = 2.0 * M_PI * freqs[f];
+    g->use_pc = opts->precond != 0;
+    // iterative refinement: residuals and the convergence test in FP64
+    g->outer_prec = (opts->refine && opts->prec == SIE_PREC_MIXED) ? SIE_PREC_FP64 : opts->prec;
+    g->refine = g->outer_prec != opts->prec;
+    g->rho_fp64 = 1e4 * opts->tol;
+    auto bail = [&](int rc) { delete g; return rc; };
+    const int32_t R = g->R, m = g->m;
+    const int64_t n = g->n;
     std::vector<int32_t> slot;
     int rc;
-    if (use_pc && (rc = pc_prepare(p, om.data(), R, slot, st))) return rc;
-    // device buffers: V [m+1][R][n], w [R][n], b [R][n], x [R][n], t [R][n]
-    const int64_t ldv = n, kstride = int64_t(R) * n, mstride = kstride;
-    double2 *V = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *t = nullptr, *dh = nullptr;
-    int32_t *act = nullptr, *dk = nullptr;
-    double *scl = nullptr;
-    // stream-ordered workspace: a device-wide cudaFree would wait for every other
-    // plan's work (solves of several plans run concurrently in a batch)
-    auto cleanup = [&]() {
-        for (void *a : {(void *)V, (void *)w, (void *)b, (void *)x, (void *)t, (void *)dh, (void *)act, (void *)dk,
-                        (void *)scl})
-            if (a) cudaFreeAsync(a, st);
-    };
-#define GM_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); set_error(std::string(#call) + ": " + cudaGetErrorString(_e)); return _e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA; } } while (0)
-#define GM_RC(expr) do { int _r = (expr); if (_r) { cleanup(); return _r; } } while (0)
-    GM_CUDA(pool_alloc(p, &V, size_t(m + 1) * kstride * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &w, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &b, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &x, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &t, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &dh, size_t(R) * (m + 2) * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &act, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(pool_alloc(p, &dk, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(pool_alloc(p, &scl, size_t(R) * sizeof(double), st));
-    GM_CUDA(cudaMemsetAsync(V, 0, size_t(m + 1) * kstride * sizeof(double2), st));
-    GM_CUDA(cudaMemsetAsync(b, 0, size_t(R) * n * sizeof(double2), st));
-    GM_CUDA(cudaMemsetAsync(x, 0, size_t(R) * n * sizeof(double2), st));
+    if (g->use_pc && (rc = pc_prepare(p, g->om.data(), R, slot, st))) return bail(rc);
+#define GA(ptr, bytes) do { cudaError_t _e = pool_alloc(p, &(ptr), (bytes), st); if (_e != cudaSuccess) return bail(fail(_e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA, std::string("sie_solve: workspace: ") + cudaGetErrorString(_e))); } while (0)
+    GA(g->V, size_t(m + 1) * g->kstride * sizeof(double2));
+    for (double2 **q : {&g->w, &g->b, &g->x, &g->t, &g->rv, &g->vin}) GA(*q, size_t(R) * n * sizeof(double2));
+    if (g->refine) GA(g->dvec, size_t(R) * n * sizeof(double2));
+    GA(g->dh, size_t(R) * (m + 2) * sizeof(double2));
+    GA(g->dh2, size_t(R) * (m + 2) * sizeof(double2));
+    GA(g->dhn, size_t(R) * sizeof(double2));
+    GA(g->dy, size_t(R) * (m + 1) * sizeof(double2));
+    GA(g->act, size_t(R) * sizeof(int32_t));
+    GA(g->kdev, sizeof(int32_t));
+    GA(g->dnorm, size_t(R) * sizeof(double));
+    GA(g->dbeta, size_t(R) * sizeof(double));
+    GA(g->gd.H, size_t(R) * (m + 1) * m * sizeof(double2));
+    GA(g->gd.cs, size_t(R) * m * sizeof(double2));
+    GA(g->gd.sn, size_t(R) * m * sizeof(double2));
+    GA(g->gd.g, size_t(R) * (m + 1) * sizeof(double2));
+    for (int32_t **q : {&g->gd.run, &g->gd.kdone, &g->gd.iters}) GA(*q, size_t(R) * sizeof(int32_t));
+    for (double **q : {&g->gd.resid, &g->gd.bnorm, &g->gd.scale}) GA(*q, size_t(R) * sizeof(double));
+    GA(g->gd.nrun, 2 * sizeof(int32_t));
+#undef GA
+    g->gd.bad = g->gd.nrun + 1;
+    if (cudaMallocHost((void **)&g->hflags, 2 * sizeof(int32_t)) != cudaSuccess) {
+        g->hflags = nullptr;
+        return bail(fail(SIE_ERR_OOM, "sie_solve: pinned host allocation failed"));
+    }
+#define GC(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return bail(fail(SIE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e))); } while (0)
+    GC(cudaMemsetAsync(g->V, 0, size_t(m + 1) * g->kstride * sizeof(double2), st));
+    GC(cudaMemsetAsync(g->b, 0, size_t(R) * n * sizeof(double2), st));
+    GC(cudaMemsetAsync(g->x, 0, size_t(R) * n * sizeof(double2), st));
+    GC(cudaMemsetAsync(g->gd.iters, 0, size_t(R) * sizeof(int32_t), st));
+    GC(cudaMemsetAsync(g->gd.nrun, 0, 2 * sizeof(int32_t), st));
     for (int32_t f = 0; f < nf; ++f)
         for (int32_t q = 0; q < np; ++q) {
-            double2 one = make_double2(1.0, 0.0);
+            static const double2 one = make_double2(1.0, 0.0);
             int64_t pl = p->loops->loop_of_branch[p->nb + ports[q]];
-            GM_CUDA(cudaMemcpyAsync(b + int64_t(f * np + q) * n + pl, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
+            GC(cudaMemcpyAsync(g->b + int64_t(f * np + q) * n + pl, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
         }
-    auto apply_op = [&](const double2 *in, double2 *out, int prec) -> int {   // out = P^-1 Z in
-        int r2 = matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, prec, st);
-        if (r2) return r2;
-        if (use_pc) return pc_apply_async(p, t, out, R, prec, st);
-        return SIE_OK;
-    };
-    // device state of the cycles (GmresDev) and the Arnoldi step's buffers
-    GmresDev gd{};
-    double2 *dh2 = nullptr, *dhn = nullptr, *dy = nullptr, *rv = nullptr, *dvec = nullptr;
-    double *dnorm = nullptr, *dbeta = nullptr;
-    int32_t *hflags = nullptr;   // pinned: nrun, bad
-    auto cleanup2 = [&]() {
-        for (void *a : {(void *)gd.H, (void *)gd.cs, (void *)gd.sn, (void *)gd.g, (void *)gd.run, (void *)gd.kdone,
-                        (void *)gd.iters, (void *)gd.resid, (void *)gd.bnorm, (void *)gd.scale, (void *)gd.nrun,
-                        (void *)dh2, (void *)dhn, (void *)dy, (void *)rv, (void *)dvec, (void *)dnorm,
-                        (void *)dbeta})
-            if (a) cudaFreeAsync(a, st);
-    };
-#undef GM_CUDA
-#undef GM_RC
-#define GM_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); cleanup2(); if (hflags) cudaFreeHost(hflags); set_error(std::string(#call) + ": " + cudaGetErrorString(_e)); return _e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA; } } while (0)
-#define GM_RC(expr) do { int _r = (expr); if (_r) { cleanup(); cleanup2(); if (hflags) cudaFreeHost(hflags); return _r; } } while (0)
-    GM_CUDA(pool_alloc(p, &gd.H, size_t(R) * (m + 1) * m * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &gd.cs, size_t(R) * m * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &gd.sn, size_t(R) * m * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &gd.g, size_t(R) * (m + 1) * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &gd.run, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(pool_alloc(p, &gd.kdone, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(pool_alloc(p, &gd.iters, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(pool_alloc(p, &gd.resid, size_t(R) * sizeof(double), st));
-    GM_CUDA(pool_alloc(p, &gd.bnorm, size_t(R) * sizeof(double), st));
-    GM_CUDA(pool_alloc(p, &gd.scale, size_t(R) * sizeof(double), st));
-    GM_CUDA(pool_alloc(p, &gd.nrun, 2 * sizeof(int32_t), st));
-    gd.bad = gd.nrun + 1;
-    GM_CUDA(pool_alloc(p, &dh2, size_t(R) * (m + 2) * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &dhn, size_t(R) * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &dy, size_t(R) * (m + 1) * sizeof(double2), st));
-    GM_CUDA(pool_alloc(p, &rv, size_t(R) * n * sizeof(double2), st));      // residual b - Z x
-    GM_CUDA(pool_alloc(p, &dnorm, size_t(R) * sizeof(double), st));
-    GM_CUDA(pool_alloc(p, &dbeta, size_t(R) * sizeof(double), st));
-    if (refine) GM_CUDA(pool_alloc(p, &dvec, size_t(R) * n * sizeof(double2), st));   // the cycle's correction
-    GM_CUDA(cudaMemsetAsync(gd.iters, 0, size_t(R) * sizeof(int32_t), st));
-    GM_CUDA(cudaMemsetAsync(gd.nrun, 0, 2 * sizeof(int32_t), st));
-    GM_CUDA(cudaMallocHost((void **)&hflags, 2 * sizeof(int32_t)));
-    const unsigned rb = unsigned((R + 127) / 128);
-    // ||vec[r]|| into dnorm (device) through k_dots on a one-vector basis
-    auto norms_dev = [&](const double2 *vec, const int32_t *mask) -> int {
-        k_dots<<<R, 256, 0, st>>>(vec, ldv, ldv, vec, n, 1, mask, dhn, 1);
-        SIE_LAUNCH_CHECK(p);
-        k_norms<<<rb, 128, 0, st>>>(dhn, 1, R, dnorm);
-        SIE_LAUNCH_CHECK(p);
-        return SIE_OK;
-    };
-    auto read_norms = [&](std::vector<double> &nr) -> int {
-        nr.resize(R);
-        SIE_CUDA(cudaMemcpyAsync(nr.data(), dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        SIE_CUDA(cudaStreamSynchronize(st));
-        return SIE_OK;
-    };
-    std::vector<int32_t> active(R, 1), done(R, 0), iters(R, 0);
-    std::vector<double> bnorm(R), resid(R, 1.0);
-    GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    // ||P^-1 b|| (the outer precision's preconditioner)
-    if (use_pc) GM_RC(pc_apply_async(p, b, w, R, outer_prec, st));
-    else GM_CUDA(cudaMemcpyAsync(w, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    GM_RC(norms_dev(w, act));
-    GM_RC(read_norms(bnorm));
-    GM_CUDA(cudaMemcpyAsync(gd.bnorm, dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    // r = b - Z x with x = 0
-    GM_CUDA(cudaMemcpyAsync(rv, b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    int64_t matvecs = 0;
-    using cd = std::complex<double>;
-    bool breakdown = false;
-    // Iterative refinement (refine): the cycles run the mixed operator on the
-    // current residual; x accumulates their corrections d.  The mixed product's
-    // error scales with |Z| |x|, not |Z x|, so one cycle lowers the true residual
-    // by a bounded factor: a cycle stops once it has reduced its own residual
-    // estimate a hundredfold (or reached half the tolerance).  The residual is
-    // then updated as r = b - Z x with the FP64 product when the cycle started
-    // from a residual above rho_fp64 (relative to ||P^-1 b||), else as
-    // r = r - Z d with the mixed product (its error is relative to the small
-    // correction).  A convergence found on a residual that mixed updates
-    // produced is confirmed on the FP64 residual before the solve stops, so the
-    // stopping test always rests on an FP64 product.
-    const double rho_fp64 = 1e4 * opts->tol;
-    double cycle_start = 1.0;
-    bool first = true, mixed_since_fp64 = false;
-    while (true) {
-        // preconditioned residual w = P^-1 r and its norm (outer precision)
-        if (use_pc) GM_RC(pc_apply_async(p, rv, w, R, outer_prec, st));
-        else GM_CUDA(cudaMemcpyAsync(w, rv, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-        GM_RC(norms_dev(w, act));
+    g->active.assign(R, 1);
+    g->done.assign(R, 0);
+    g->iters.assign(R, 0);
+    g->resid.assign(R, 1.0);
+    GC(cudaMemcpyAsync(g->act, g->active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // ||P^-1 b|| (the outer precision's preconditioner); r = b - Z x with x = 0
+    if (g->use_pc) {
+        if ((rc = pc_apply_async(p, g->b, g->w, R, g->outer_prec, st))) return bail(rc);
+    } else {
+        GC(cudaMemcpyAsync(g->w, g->b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    }
+    if ((rc = g->norms_dev(g->w, g->act))) return bail(rc);
+    if ((rc = g->read_norms(g->bnorm))) return bail(rc);
+    GC(cudaMemcpyAsync(g->gd.bnorm, g->dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GC(cudaMemcpyAsync(g->rv, g->b, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+#undef GC
+    // the product's coefficients stay in the plan's scratch for the whole solve
+    if ((rc = scratch_reserve(p, R, g->o.prec))) return bail(rc);
+    if ((rc = scratch_reserve(p, R, g->outer_prec))) return bail(rc);
+    *out = g;
+    return SIE_OK;
+}
+
+// Top of a cycle: the preconditioned residual and its norm (outer precision),
+// convergence per right-hand side.  Iterative refinement: the cycles run the
+// mixed operator on the current residual and x accumulates their corrections
+// d; the mixed product's error scales with |Z| |x|, not |Z x|, so one cycle
+// lowers the true residual by a bounded factor.  After a cycle the residual is
+// updated as r = b - Z x with the FP64 product when the cycle started from a
+// residual above 1e4 tol (relative to ||P^-1 b||), else as r = r - Z d with the
+// mixed product (its error is relative to the small correction).  A
+// convergence found on a residual that mixed updates produced is confirmed on
+// the FP64 residual here, so the stopping test always rests on an FP64 product.
+int gmres_top(GmresRun *g, bool &need) {
+    pfft_plan *p = g->p;
+    cudaStream_t st = g->st;
+    const int32_t R = g->R;
+    const int64_t n = g->n;
+    need = false;
+    for (;;) {
+        int rc;
+        if (g->use_pc) {
+            if ((rc = pc_apply_async(p, g->rv, g->w, R, g->outer_prec, st))) return rc;
+        } else {
+            SIE_CUDA(cudaMemcpyAsync(g->w, g->rv, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        }
+        if ((rc = g->norms_dev(g->w, g->act))) return rc;
         std::vector<double> beta;
-        GM_RC(read_norms(beta));
+        if ((rc = g->read_norms(beta))) return rc;
         bool any = false;
-        cycle_start = 0.0;
+        g->cycle_start = 0.0;
         for (int32_t r = 0; r < R; ++r) {
-            if (done[r] || !active[r]) {   // no new norm was taken for it
-                active[r] = 0;
+            if (g->done[r] || !g->active[r]) {   // no new norm was taken for it
+                g->active[r] = 0;
                 continue;
             }
-            resid[r] = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
-            if (!std::isfinite(resid[r])) breakdown = true;
-            active[r] = !done[r] && !(resid[r] < opts->tol) && iters[r] < opts->max_iter && bnorm[r] > 0 &&
-                        std::isfinite(resid[r]);
-            if (resid[r] < opts->tol) done[r] = 1;
-            if (active[r]) cycle_start = std::max(cycle_start, resid[r]);
-            any |= active[r] != 0;
+            g->resid[r] = g->bnorm[r] > 0 ? beta[r] / g->bnorm[r] : 0.0;
+            if (!std::isfinite(g->resid[r])) g->breakdown = true;
+            g->active[r] = !(g->resid[r] < g->o.tol) && g->iters[r] < g->o.max_iter && g->bnorm[r] > 0 &&
+                           std::isfinite(g->resid[r]);
+            if (g->resid[r] < g->o.tol) g->done[r] = 1;
+            if (g->active[r]) g->cycle_start = std::max(g->cycle_start, g->resid[r]);
+            any |= g->active[r] != 0;
         }
-        if (!any && refine && mixed_since_fp64 && !breakdown) {
-            // converged on a residual from mixed updates: recompute it with the FP64
-            // product; the right-hand sides it does not confirm continue
-            GM_RC(matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, SIE_PREC_FP64, st));
-            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
-            SIE_LAUNCH_CHECK(p);
-            matvecs += R;
-            mixed_since_fp64 = false;
+        if (!any && g->refine && g->mixed_since_fp64 && !g->breakdown) {
+            if ((rc = g->residual_fp64())) return rc;
+            g->mixed_since_fp64 = false;
             for (int32_t r = 0; r < R; ++r) {
-                active[r] = iters[r] < opts->max_iter && bnorm[r] > 0;
-                done[r] = 0;
+                g->active[r] = g->iters[r] < g->o.max_iter && g->bnorm[r] > 0;
+                g->done[r] = 0;
             }
-            GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            SIE_CUDA(cudaMemcpyAsync(g->act, g->active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             continue;
         }
-        if (!any || breakdown) break;
-        GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        GM_CUDA(cudaMemcpyAsync(dbeta, dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        GM_CUDA(cudaMemcpyAsync(gd.iters, iters.data(), size_t(R) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        // the cycle's stopping level (relative to ||P^-1 b||): the tolerance, or with
-        // refinement a hundredth of the largest starting residual, at least half the tolerance
-        const double tol_inner = refine ? std::max(0.5 * opts->tol, 1e-2 * cycle_start) : opts->tol;
-        k_cycle_start<<<rb, 128, 0, st>>>(gd, m, R, dbeta, act);
-        SIE_LAUNCH_CHECK(p);
-        k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, 0, n, gd.scale, act, R);
-        SIE_LAUNCH_CHECK(p);
-        // Arnoldi (CGS2) with the rotations on the device; one host read per step
-        for (int k = 0; k < m; ++k) {
-            // w = P^-1 Z v_k
-            GM_RC(apply_op(V + int64_t(k) * kstride, w, opts->prec));
-            matvecs += R;
-            {
-                StageTimer tm(p, SIE_STAGE_ARNOLDI, st);
-                k_dots<<<R * (k + 1), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh, m + 2);   // CGS pass 1
-                SIE_LAUNCH_CHECK(p);
-                k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh, m + 2, R);
-                SIE_LAUNCH_CHECK(p);
-                k_dots<<<R * (k + 1), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh2, m + 2);  // CGS pass 2
-                SIE_LAUNCH_CHECK(p);
-                k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, w, n, k + 1, gd.run, dh2, m + 2, R);
-                SIE_LAUNCH_CHECK(p);
-                GM_RC(norms_dev(w, gd.run));
-                GM_CUDA(cudaMemsetAsync(gd.nrun, 0, sizeof(int32_t), st));
-                k_givens<<<rb, 128, 0, st>>>(gd, k, m, R, dh, dh2, m + 2, dnorm, tol_inner, opts->max_iter);
-                SIE_LAUNCH_CHECK(p);
-                if (k + 1 < m) {
-                    k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(w, ldv, V, mstride, k + 1, n, gd.scale,
-                                                                        gd.run, R);
-                    SIE_LAUNCH_CHECK(p);
-                }
-                GM_CUDA(cudaMemcpyAsync(hflags, gd.nrun, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                GM_CUDA(cudaStreamSynchronize(st));
-            }
-            if (hflags[1]) breakdown = true;
-            if (hflags[0] == 0) break;
-        }
-        // the cycle's correction d = V y, y = R^-1 g (device back substitution)
-        k_lsq<<<rb, 128, 0, st>>>(gd, m, R, dy, m + 1);
-        SIE_LAUNCH_CHECK(p);
-        double2 *xd = refine ? dvec : x;
-        if (refine) GM_CUDA(cudaMemsetAsync(dvec, 0, size_t(R) * n * sizeof(double2), st));
-        k_update_x<<<nblk_(int64_t(R) * n), 256, 0, st>>>(V, ldv, mstride, xd, n, gd.kdone, dy, m + 1, R);
-        SIE_LAUNCH_CHECK(p);
-        std::vector<double> rs(R);
-        GM_CUDA(cudaMemcpyAsync(iters.data(), gd.iters, size_t(R) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        GM_CUDA(cudaMemcpyAsync(rs.data(), gd.resid, size_t(R) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        GM_CUDA(cudaStreamSynchronize(st));
-        if (breakdown) break;
-        // without refinement the cycle's residual estimate decides; with it the
-        // residual at the top of the next cycle does
-        if (!refine)
-            for (int32_t r = 0; r < R; ++r)
-                if (active[r]) {
-                    resid[r] = rs[r];
-                    if (rs[r] < opts->tol) done[r] = 1;
-                }
-        bool cont = false;
-        for (int32_t r = 0; r < R; ++r) cont |= !done[r] && iters[r] < opts->max_iter;
-        if (!cont && !refine) break;
-        for (int32_t r = 0; r < R; ++r) active[r] = !done[r] && iters[r] < opts->max_iter;
-        GM_CUDA(cudaMemcpyAsync(act, active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        // the new residual r = b - Z x
-        if (!refine) {
-            GM_RC(matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, opts->prec, st));
-            matvecs += R;
-            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
-            SIE_LAUNCH_CHECK(p);
-        } else {
-            k_add<<<nblk_(int64_t(R) * n), 256, 0, st>>>(x, dvec, int64_t(R) * n);
-            SIE_LAUNCH_CHECK(p);
-            if (first || cycle_start > rho_fp64) {
-                GM_RC(matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, SIE_PREC_FP64, st));
-                k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
-                mixed_since_fp64 = false;
-            } else {
-                GM_RC(matvec_async(p, dvec, t, R, om.data(), SIE_SPACE_LOOP, opts->prec, st));
-                k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(rv, t, rv, int64_t(R) * n);
-                mixed_since_fp64 = true;
-            }
-            SIE_LAUNCH_CHECK(p);
-            matvecs += R;
-            first = false;
-        }
-        if (!cont) {   // refinement: iteration cap reached; report the residual of the final x
-            if (use_pc) GM_RC(pc_apply_async(p, rv, w, R, outer_prec, st));
-            else GM_CUDA(cudaMemcpyAsync(w, rv, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            GM_RC(norms_dev(w, act));
-            std::vector<double> fin;
-            GM_RC(read_norms(fin));
-            for (int32_t r = 0; r < R; ++r)
-                if (!done[r] && bnorm[r] > 0) resid[r] = fin[r] / bnorm[r];
-            break;
-        }
+        need = any && !g->breakdown;
+        return SIE_OK;
     }
-    cleanup2();
-    cudaFreeHost(hflags);
-    hflags = nullptr;
-    // port currents -> Y -> Z
+}
+
+int gmres_begin(GmresRun *g) {
+    pfft_plan *p = g->p;
+    cudaStream_t st = g->st;
+    const int32_t R = g->R;
+    SIE_CUDA(cudaMemcpyAsync(g->act, g->active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SIE_CUDA(cudaMemcpyAsync(g->dbeta, g->dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SIE_CUDA(cudaMemcpyAsync(g->gd.iters, g->iters.data(), size_t(R) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // the cycle's stopping level (relative to ||P^-1 b||): the tolerance, or with
+    // refinement a hundredth of the largest starting residual, at least half the tolerance
+    g->tol_inner = g->refine ? std::max(0.5 * g->o.tol, 1e-2 * g->cycle_start) : g->o.tol;
+    k_cycle_start<<<unsigned((R + 127) / 128), 128, 0, st>>>(g->gd, g->m, R, g->dbeta, g->act);
+    SIE_LAUNCH_CHECK(p);
+    k_scale_store<<<nblk_(int64_t(R) * g->n), 256, 0, st>>>(g->w, g->ldv, g->V, g->kstride, 0, g->n, g->gd.scale,
+                                                             g->act, R, nullptr, g->vin);
+    SIE_LAUNCH_CHECK(p);
+    SIE_CUDA(cudaMemsetAsync(g->kdev, 0, sizeof(int32_t), st));
+    g->k_host = 0;
+    return SIE_OK;
+}
+
+// One Arnoldi step (CGS2) with the rotations on the device.  graph = true: every
+// launch is independent of k (k read from kdev, dots over all m columns with the
+// columns beyond k idle, the product from fixed coefficients), so that a
+// captured step serves every step of the cycle.
+int gmres_step(GmresRun *g, bool graph) {
+    pfft_plan *p = g->p;
+    cudaStream_t st = g->st;
+    const int32_t R = g->R, m = g->m;
+    const int64_t n = g->n;
+    int rc = g->apply_op(g->vin, g->w, g->o.prec, graph);   // w = P^-1 Z v_k (counted in gmres_stepped)
+    if (rc) return rc;
+    StageTimer tm(p, SIE_STAGE_ARNOLDI, st);
+    const int32_t K = graph ? m : g->k_host + 1;
+    k_dots<<<R * K, 256, 0, st>>>(g->V, g->ldv, g->kstride, g->w, n, K, g->gd.run, g->dh, m + 2, g->kdev);
+    SIE_LAUNCH_CHECK(p);
+    k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->V, g->ldv, g->kstride, g->w, n, K, g->gd.run, g->dh,
+                                                          m + 2, R, g->kdev);
+    SIE_LAUNCH_CHECK(p);
+    k_dots<<<R * K, 256, 0, st>>>(g->V, g->ldv, g->kstride, g->w, n, K, g->gd.run, g->dh2, m + 2, g->kdev);
+    SIE_LAUNCH_CHECK(p);
+    k_orth_update<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->V, g->ldv, g->kstride, g->w, n, K, g->gd.run, g->dh2,
+                                                          m + 2, R, g->kdev);
+    SIE_LAUNCH_CHECK(p);
+    if ((rc = g->norms_dev(g->w, g->gd.run))) return rc;
+    SIE_CUDA(cudaMemsetAsync(g->gd.nrun, 0, sizeof(int32_t), st));
+    k_givens<<<unsigned((R + 127) / 128), 128, 0, st>>>(g->gd, 0, m, R, g->dh, g->dh2, m + 2, g->dnorm,
+                                                         g->tol_inner, g->o.max_iter, g->kdev);
+    SIE_LAUNCH_CHECK(p);
+    k_scale_store<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->w, g->ldv, g->V, g->kstride, 0, n, g->gd.scale, g->gd.run,
+                                                          R, g->kdev, g->vin);
+    SIE_LAUNCH_CHECK(p);
+    k_step_advance<<<1, 1, 0, st>>>(g->kdev);
+    SIE_LAUNCH_CHECK(p);
+    SIE_CUDA(cudaMemcpyAsync(g->hflags, g->gd.nrun, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    return SIE_OK;
+}
+
+// After the step's stream has synchronised: true when the cycle is over.
+bool gmres_stepped(GmresRun *g) {
+    g->k_host += 1;
+    g->matvecs += g->R;
+    if (g->hflags[1]) g->breakdown = true;
+    return g->hflags[0] == 0 || g->k_host >= g->m || g->breakdown;
+}
+
+// End of a cycle: x += V y (y from the rotated Hessenberg matrix), convergence
+// without refinement, the new residual.  cont = false: the solve is over.
+int gmres_end(GmresRun *g, bool &cont) {
+    pfft_plan *p = g->p;
+    cudaStream_t st = g->st;
+    const int32_t R = g->R, m = g->m;
+    const int64_t n = g->n;
+    cont = false;
+    k_lsq<<<unsigned((R + 127) / 128), 128, 0, st>>>(g->gd, m, R, g->dy, m + 1);
+    SIE_LAUNCH_CHECK(p);
+    double2 *xd = g->refine ? g->dvec : g->x;
+    if (g->refine) SIE_CUDA(cudaMemsetAsync(g->dvec, 0, size_t(R) * n * sizeof(double2), st));
+    k_update_x<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->V, g->ldv, g->kstride, xd, n, g->gd.kdone, g->dy, m + 1, R);
+    SIE_LAUNCH_CHECK(p);
+    std::vector<double> rs(R);
+    SIE_CUDA(cudaMemcpyAsync(g->iters.data(), g->gd.iters, size_t(R) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SIE_CUDA(cudaMemcpyAsync(rs.data(), g->gd.resid, size_t(R) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SIE_CUDA(cudaStreamSynchronize(st));
+    if (g->breakdown) return SIE_OK;
+    // without refinement the cycle's residual estimate decides; with it the
+    // residual at the top of the next cycle does
+    if (!g->refine)
+        for (int32_t r = 0; r < R; ++r)
+            if (g->active[r]) {
+                g->resid[r] = rs[r];
+                if (rs[r] < g->o.tol) g->done[r] = 1;
+            }
+    bool more = false;
+    for (int32_t r = 0; r < R; ++r) more |= !g->done[r] && g->iters[r] < g->o.max_iter;
+    if (!more && !g->refine) return SIE_OK;
+    for (int32_t r = 0; r < R; ++r) g->active[r] = !g->done[r] && g->iters[r] < g->o.max_iter;
+    SIE_CUDA(cudaMemcpyAsync(g->act, g->active.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    int rc;
+    if (!g->refine) {
+        if ((rc = matvec_async(p, g->x, g->t, R, g->om.data(), SIE_SPACE_LOOP, g->o.prec, st))) return rc;
+        g->matvecs += R;
+        k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->b, g->t, g->rv, int64_t(R) * n);
+        SIE_LAUNCH_CHECK(p);
+    } else {
+        k_add<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->x, g->dvec, int64_t(R) * n);
+        SIE_LAUNCH_CHECK(p);
+        if (g->first || g->cycle_start > g->rho_fp64) {
+            if ((rc = g->residual_fp64())) return rc;
+            g->mixed_since_fp64 = false;
+        } else {
+            if ((rc = matvec_async(p, g->dvec, g->t, R, g->om.data(), SIE_SPACE_LOOP, g->o.prec, st))) return rc;
+            k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(g->rv, g->t, g->rv, int64_t(R) * n);
+            SIE_LAUNCH_CHECK(p);
+            g->matvecs += R;
+            g->mixed_since_fp64 = true;
+        }
+        g->first = false;
+    }
+    if (!more) {   // refinement: iteration cap reached; report the residual of the final x
+        if (g->mixed_since_fp64 && (rc = g->residual_fp64())) return rc;
+        if (g->use_pc) {
+            if ((rc = pc_apply_async(p, g->rv, g->w, R, g->outer_prec, st))) return rc;
+        } else {
+            SIE_CUDA(cudaMemcpyAsync(g->w, g->rv, size_t(R) * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        }
+        if ((rc = g->norms_dev(g->w, g->act))) return rc;
+        std::vector<double> fin;
+        if ((rc = g->read_norms(fin))) return rc;
+        for (int32_t r = 0; r < R; ++r)
+            if (!g->done[r] && g->bnorm[r] > 0) g->resid[r] = fin[r] / g->bnorm[r];
+        return SIE_OK;
+    }
+    cont = true;
+    return SIE_OK;
+}
+
+// Port currents -> Y -> Z = Y^-1 per frequency, the statistics; frees the run.
+int gmres_finish(GmresRun *g, sie_c64 *Z_out, sie_solve_stats *st_out) {
+    using cd = std::complex<double>;
+    pfft_plan *p = g->p;
+    const int32_t R = g->R, nf = g->nf, np = g->np;
+    const int64_t n = g->n;
     std::vector<double2> xh(size_t(R) * n);
-    GM_CUDA(cudaMemcpyAsync(xh.data(), x, xh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-    GM_CUDA(cudaStreamSynchronize(st));
+    cudaError_t e = cudaMemcpyAsync(xh.data(), g->x, xh.size() * sizeof(double2), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) {
+        delete g;
+        return fail(SIE_ERR_CUDA, std::string("sie_solve: ") + cudaGetErrorString(e));
+    }
     int32_t nnc = 0, itmax = 0, itsum = 0;
     double rmax = 0.0;
     for (int32_t r = 0; r < R; ++r) {
-        nnc += !(resid[r] < opts->tol);
-        itmax = std::max(itmax, iters[r]);
-        itsum += iters[r];
-        rmax = std::max(rmax, resid[r]);
+        nnc += !(g->resid[r] < g->o.tol);
+        itmax = std::max(itmax, g->iters[r]);
+        itsum += g->iters[r];
+        rmax = std::max(rmax, g->resid[r]);
     }
-    for (int32_t f = 0; f < nf; ++f) {
+    int rc = SIE_OK;
+    for (int32_t f = 0; f < nf && !rc; ++f) {
         // Y[q][p] = current in port q's loop with port p driven; Z = Y^-1 (Gauss-Jordan)
         std::vector<cd> Y(size_t(np) * np), Zi(size_t(np) * np, 0.0);
         for (int32_t q = 0; q < np; ++q)
             for (int32_t pp = 0; pp < np; ++pp) {
-                int64_t pl = p->loops->loop_of_branch[p->nb + ports[q]];
+                int64_t pl = p->loops->loop_of_branch[p->nb + g->ports[q]];
                 double2 v = xh[size_t(f * np + pp) * n + pl];
                 Y[size_t(q) * np + pp] = cd(v.x, v.y);
             }
         for (int32_t i = 0; i < np; ++i) Zi[size_t(i) * np + i] = 1.0;
-        for (int32_t c = 0; c < np; ++c) {
+        for (int32_t c = 0; c < np && !rc; ++c) {
             int32_t piv = c;
             for (int32_t r2 = c + 1; r2 < np; ++r2)
                 if (std::abs(Y[size_t(r2) * np + c]) > std::abs(Y[size_t(piv) * np + c])) piv = r2;
-            for (int32_t j = 0; j < np; ++j) { std::swap(Y[size_t(c) * np + j], Y[size_t(piv) * np + j]); std::swap(Zi[size_t(c) * np + j], Zi[size_t(piv) * np + j]); }
+            for (int32_t j = 0; j < np; ++j) {
+                std::swap(Y[size_t(c) * np + j], Y[size_t(piv) * np + j]);
+                std::swap(Zi[size_t(c) * np + j], Zi[size_t(piv) * np + j]);
+            }
             cd d = Y[size_t(c) * np + c];
-            if (d == cd(0.0)) { cleanup(); return fail(SIE_ERR_BREAKDOWN, "sie_solve: singular port admittance matrix"); }
+            if (d == cd(0.0)) {
+                rc = fail(SIE_ERR_BREAKDOWN, "sie_solve: singular port admittance matrix");
+                break;
+            }
             for (int32_t j = 0; j < np; ++j) { Y[size_t(c) * np + j] /= d; Zi[size_t(c) * np + j] /= d; }
             for (int32_t r2 = 0; r2 < np; ++r2) {
                 if (r2 == c) continue;
                 cd fct = Y[size_t(r2) * np + c];
-                for (int32_t j = 0; j < np; ++j) { Y[size_t(r2) * np + j] -= fct * Y[size_t(c) * np + j]; Zi[size_t(r2) * np + j] -= fct * Zi[size_t(c) * np + j]; }
+                for (int32_t j = 0; j < np; ++j) {
+                    Y[size_t(r2) * np + j] -= fct * Y[size_t(c) * np + j];
+                    Zi[size_t(r2) * np + j] -= fct * Zi[size_t(c) * np + j];
+                }
             }
         }
-        for (int32_t i = 0; i < np * np; ++i) Z_out[size_t(f) * np * np + i] = sie_c64{Zi[i].real(), Zi[i].imag()};
+        for (int32_t i = 0; i < np * np && !rc; ++i) Z_out[size_t(f) * np * np + i] = sie_c64{Zi[i].real(), Zi[i].imag()};
     }
-    cleanup();
     if (st_out) {
         st_out->iterations_max = itmax;
         st_out->iterations_sum = itsum;
         st_out->n_not_converged = nnc;
         st_out->residual_max = rmax;
-        st_out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        st_out->matvecs = matvecs;
+        st_out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - g->t0).count();
+        st_out->matvecs = g->matvecs;
     }
-#undef GM_CUDA
-#undef GM_RC
+    const bool breakdown = g->breakdown;
+    delete g;
+    if (rc) return rc;
     if (int dev_rc = check_device_errors(p)) return dev_rc;
     if (breakdown) return fail(SIE_ERR_BREAKDOWN, "sie_solve: non-finite value in the Arnoldi recurrence");
     if (nnc) return fail(SIE_ERR_NOT_CONVERGED, "sie_solve: " + std::to_string(nnc) + " right-hand sides did not converge");
     return SIE_OK;
+}
+
+void gmres_free(GmresRun *g) { delete g; }
+cudaStream_t gmres_stream(const GmresRun *g) { return g->st; }
+int64_t gmres_plan_launches(const GmresRun *g) { return g->p->launches; }
+
+}  // namespace sie
+
+extern "C" int sie_solve(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *ports, int32_t np,
+                         const sie_solve_opts *opts, sie_c64 *Z_out, sie_solve_stats *st_out) {
+    if (!p || !Z_out) return fail(SIE_ERR_ARG, "sie_solve: bad argument");
+    GmresRun *g = nullptr;
+    int rc = gmres_create(p, freqs, nf, ports, np, opts, p->stream, &g);
+    if (rc) return rc;
+    for (;;) {
+        bool need = false;
+        if ((rc = gmres_top(g, need)) || !need) break;
+        if ((rc = gmres_begin(g))) break;
+        for (;;) {
+            if ((rc = gmres_step(g, false))) break;
+            if (cudaStreamSynchronize(g->st) != cudaSuccess) {
+                rc = fail(SIE_ERR_CUDA, "sie_solve: Arnoldi step failed");
+                break;
+            }
+            if (gmres_stepped(g)) break;
+        }
+        if (rc) break;
+        bool cont = false;
+        if ((rc = gmres_end(g, cont)) || !cont) break;
+    }
+    if (rc) {
+        gmres_free(g);
+        return rc;
+    }
+    return gmres_finish(g, Z_out, st_out);
 }
 
 // ------------------------------------------------------------------ surface model

@@ -25,7 +25,7 @@ EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basi
            "pfft_plan_create", "pfft_plan_destroy", "pfft_matvec", "pfft_precond_apply", "sie_solve",
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_lossy", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "pfft_plan_set_surface_model", "sie_postprocess", "sie_batch_create", "sie_batch_destroy",
-           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "pfft_precond_info",
+           "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "sie_batch_solve_graph", "pfft_precond_info",
            "pfft_precond_set_method", "pfft_precond_nd_info", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
            "sie_mlp_param_count", "sie_mlp_get_params", "sie_mlp_set_params", "sie_mlp_forward", "sie_mlp_grad",
            "sie_mlp_train", "pfft_branch_features", "pfft_branch_probe_target", "pfft_plan_set_learned",
@@ -131,6 +131,7 @@ def lib():
     L.sie_batch_matvec.argtypes = [P, P, P, P, P, I32, I32, I32, P]
     L.sie_batch_stats.argtypes = [P, P, P]
     L.sie_batch_solve.argtypes = [P, P, P, P, P, ctypes.POINTER(SolveOpts), P, P]
+    L.sie_batch_solve_graph.argtypes = [P, P, P, P, P, ctypes.POINTER(SolveOpts), P, P]
     L.pfft_plan_launches.argtypes = [P]
     L.pfft_plan_launches.restype = I64
     L.sie_last_error.restype = ctypes.c_char_p

@@ -10,7 +10,9 @@ batch solve equals each plan's own solve.  A meander against the oracle pFFT
 within 1e-5.  The full workload (32 meanders, 5k-60k triangles each, 32
 frequencies) runs in one batch: graph replays equal the eager products, the
 mixed form stays within 1e-5 of FP64, and a batched solve converges with
-positive R and L on every trace.
+positive R and L on every trace.  The batched solve under graph replay (one
+replay per Arnoldi step of all plans, sie_batch_solve_graph) equals each plan's
+own solve bit for bit, on the small batch and on the full workload.
 """
 import numpy as np
 import pytest
@@ -112,6 +114,23 @@ def test_batch_solve_equals_individual(small):
         assert np.array_equal(Z, Z0)
 
 
+@pytest.mark.parametrize("prec,refine", [(PREC_FP64, False), (PREC_MIXED, True)], ids=["fp64", "mixed_refined"])
+def test_batch_solve_graph_equals_individual(small, prec, refine):
+    # every plan's GMRES stepped in lockstep by graph replay: the same kernels in the
+    # same order as the plan's own solve, so Z and the iteration counts are equal
+    ws, plans = small
+    freqs = [np.array([1e8, 2e9]), np.array([5e8]), np.array([1e7, 1e9, 4e9])]
+    B = api.Batch(plans)
+    r0 = B.stats()["replays"]
+    got = B.solve(freqs, tol=1e-8, restart=100, max_iter=400, prec=prec, refine=refine, graph=True)
+    assert B.stats()["replays"] > r0
+    for p, f, (Z, st) in zip(plans, freqs, got):
+        Z0, st0 = api.sie_solve(p, f, tol=1e-8, restart=100, max_iter=400, prec=prec, refine=refine)
+        assert st["converged"] and st0["converged"]
+        assert st["iterations_max"] == st0["iterations_max"] and st["matvecs"] == st0["matvecs"]
+        assert np.array_equal(Z, Z0)
+
+
 def test_meander_matches_oracle():
     w = synth.meander(5, n_tri=400)
     m = w["mesh"]
@@ -160,3 +179,16 @@ def test_full_batch_solve(full):
         assert st["converged"]
         z = Z[:, 0, 0]
         assert np.all(z.real > 0) and np.all(z.imag / (2 * np.pi * f) > 0)
+
+
+def test_full_batch_solve_graph(full):
+    # the 32-meander workload: one graph replay per Arnoldi step of all plans, equal
+    # to the plans' solves on host threads
+    ws, plans = full
+    B = api.Batch(plans)
+    freqs = [np.array([1e8, 5e9])] * len(plans)
+    a = B.solve(freqs, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=True, graph=True)
+    b = B.solve(freqs, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=True)
+    for (Za, sa), (Zb, sb) in zip(a, b):
+        assert sa["converged"] and sb["converged"]
+        assert np.array_equal(Za, Zb)
