@@ -301,41 +301,102 @@ __global__ void k_nd_store(FrontArgs fa, const double2 *__restrict__ W, double2 
 
 // ---------------------------------------------------------------- solve kernels
 
-// Forward: per (front, right-hand side) the frontal vector v = [rhs(I_f); 0]
-// plus the children's update vectors, the unit lower L_11 solve on the pivots
-// (column by column), v_U -= L_21 z_I, z_I back into u and v_U to the update
-// vector of f.  u: [R][nunk]; uv: [R][sumU].
+// Right-hand sides per solve CTA: a group of up to kG right-hand sides that
+// share a factor slot (the ports of one frequency), so that a front's factor
+// is read once for all of them.
+constexpr int kG = 4;
+
+// Forward: per (front, group of right-hand sides) the frontal vectors
+// v = [rhs(I_f); 0] plus the children's update vectors, the unit lower L_11
+// solve on the pivots, v_U -= L_21 z_I, z_I back into u and v_U to the update
+// vector of f.  Pivots go 32 at a time: the chunk's 32 x 32 block is staged in
+// shared memory, warp 0 solves it in registers (a shuffle hands each pivot to
+// the lanes below it), then every thread applies the chunk's 32 columns to one
+// of the rows below: three barriers per 32 pivots.  u: [R][nunk]; uv:
+// [R][sumU]; grp: [ngroups][kG] right-hand sides (-1: none), all of one slot;
+// v in shared memory: [kG][ldv].
 template <typename T>
 __global__ void __launch_bounds__(256) k_nd_fwd(FrontArgs fa, int32_t lvl0, const C<T> *__restrict__ L, int64_t sumL,
-                                                const int32_t *__restrict__ slot, int64_t nunk, int64_t sumU,
-                                                C<T> *__restrict__ u, C<T> *__restrict__ uv) {
+                                                const int32_t *__restrict__ grp, const int32_t *__restrict__ slot,
+                                                int64_t nunk, int64_t sumU, int32_t ldv, C<T> *__restrict__ u,
+                                                C<T> *__restrict__ uv) {
     extern __shared__ __align__(16) unsigned char nd_smem[];
     C<T> *v = reinterpret_cast<C<T> *>(nd_smem);
+    __shared__ C<T> blk[32][33];   // blk[j][l] = L[c0 + l][c0 + j]: the chunk's block, column j
     const int32_t f = fa.order[lvl0 + blockIdx.x];
-    const int32_t r = blockIdx.y;
+    const int32_t *gr = grp + int64_t(blockIdx.y) * kG;
     const int32_t nf = fa.nf[f], nv = fa.nv[f];
-    const C<T> *Lf = L + int64_t(slot[r]) * sumL + fa.Loff[f];
-    C<T> *ur = u + int64_t(r) * nunk + fa.first[f];
-    C<T> *uvr = uv + int64_t(r) * sumU;
-    for (int32_t t = threadIdx.x; t < nf; t += blockDim.x) v[t] = t < nv ? ur[t] : mk<T>(T(0), T(0));
+    const C<T> *Lf = L + int64_t(slot[gr[0]]) * sumL + fa.Loff[f];
+    const int lane = threadIdx.x & 31;
+    const C<T> zero = mk<T>(T(0), T(0));
+    for (int g = 0; g < kG; ++g) {
+        const int32_t r = gr[g];
+        const C<T> *ur = u + int64_t(r < 0 ? 0 : r) * nunk + fa.first[f];
+        for (int32_t t = threadIdx.x; t < nf; t += blockDim.x) v[g * ldv + t] = (r >= 0 && t < nv) ? ur[t] : zero;
+    }
     for (int32_t q = fa.child_ptr[f]; q < fa.child_ptr[f + 1]; ++q) {
         __syncthreads();
         const int32_t c = fa.child[q];
         const int32_t mc = fa.nf[c] - fa.nv[c];
         const int32_t *rp = fa.relpos + fa.Uoff[c];
-        const C<T> *uc = uvr + fa.Uoff[c];
-        for (int32_t t = threadIdx.x; t < mc; t += blockDim.x) v[rp[t]] = cadd(v[rp[t]], uc[t]);
+        for (int g = 0; g < kG; ++g) {
+            const int32_t r = gr[g];
+            if (r < 0) continue;
+            const C<T> *uc = uv + int64_t(r) * sumU + fa.Uoff[c];
+            for (int32_t t = threadIdx.x; t < mc; t += blockDim.x) v[g * ldv + rp[t]] = cadd(v[g * ldv + rp[t]], uc[t]);
+        }
     }
-    for (int32_t j = 0; j < nv; ++j) {
+    for (int32_t c0 = 0; c0 < nv; c0 += 32) {
+        const int32_t cw = min(32, nv - c0);
         __syncthreads();
-        const C<T> y = v[j];
-        const C<T> *col = Lf + int64_t(j) * nf;
-        for (int32_t i = j + 1 + threadIdx.x; i < nf; i += blockDim.x) v[i] = csub(v[i], cmul(col[i], y));
+        for (int32_t t = threadIdx.x; t < 32 * 32; t += blockDim.x) {   // stage the block (coalesced)
+            const int32_t c = t >> 5, rr = t & 31;
+            blk[c][rr] = (rr < cw && c < cw) ? Lf[int64_t(c0 + c) * nf + c0 + rr] : zero;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {   // the chunk's diagonal block, lane l on pivot row c0 + l
+            C<T> vl[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) vl[g] = lane < cw ? v[g * ldv + c0 + lane] : zero;
+            for (int32_t j = 0; j < cw; ++j) {
+                const C<T> l = blk[j][lane];
+#pragma unroll
+                for (int g = 0; g < kG; ++g) {
+                    C<T> y;
+                    y.x = __shfl_sync(0xffffffffu, vl[g].x, j);
+                    y.y = __shfl_sync(0xffffffffu, vl[g].y, j);
+                    if (lane > j) vl[g] = csub(vl[g], cmul(l, y));
+                }
+            }
+            if (lane < cw)
+#pragma unroll
+                for (int g = 0; g < kG; ++g) v[g * ldv + c0 + lane] = vl[g];
+        }
+        __syncthreads();
+        for (int32_t i = c0 + cw + threadIdx.x; i < nf; i += blockDim.x) {   // rows below the chunk
+            C<T> acc[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) acc[g] = zero;
+#pragma unroll 4
+            for (int32_t j = 0; j < cw; ++j) {
+                const C<T> l = Lf[int64_t(c0 + j) * nf + i];
+#pragma unroll
+                for (int g = 0; g < kG; ++g) acc[g] = cadd(acc[g], cmul(l, v[g * ldv + c0 + j]));
+            }
+#pragma unroll
+            for (int g = 0; g < kG; ++g) v[g * ldv + i] = csub(v[g * ldv + i], acc[g]);
+        }
     }
     __syncthreads();
-    for (int32_t t = threadIdx.x; t < nf; t += blockDim.x) {
-        if (t < nv) ur[t] = v[t];
-        else uvr[fa.Uoff[f] + (t - nv)] = v[t];
+    for (int g = 0; g < kG; ++g) {
+        const int32_t r = gr[g];
+        if (r < 0) continue;
+        C<T> *ur = u + int64_t(r) * nunk + fa.first[f];
+        C<T> *uvr = uv + int64_t(r) * sumU + fa.Uoff[f];
+        for (int32_t t = threadIdx.x; t < nf; t += blockDim.x) {
+            if (t < nv) ur[t] = v[g * ldv + t];
+            else uvr[t - nv] = v[g * ldv + t];
+        }
     }
 }
 
@@ -347,31 +408,42 @@ template <typename V> __device__ __forceinline__ V warp_sum(V a) {
     return a;
 }
 
-// Backward: per (front, right-hand side) w_I = z_I / d - L_21^T x(U_f), then the
-// unit upper L_11^T solve from the last pivot down (each step a dot product
-// over the column below the pivot, coalesced), x_I back into u.
+// Backward: per (front, group of right-hand sides) w_I = z_I / d - L_21^T x(U_f),
+// then L_11^T x_I = w_I from the last pivot down, 32 pivots at a time: first
+// the pivots after the chunk, already solved, enter by column dot products (one
+// warp per chunk column, coalesced), then warp 0 solves the chunk's
+// upper-triangular block (staged in shared memory) with shuffles.  x_I back
+// into u.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nd_bwd(FrontArgs fa, int32_t lvl0, const C<T> *__restrict__ L, int64_t sumL,
-                                                const int32_t *__restrict__ slot, int64_t nunk,
-                                                C<T> *__restrict__ u) {
+                                                const int32_t *__restrict__ grp, const int32_t *__restrict__ slot,
+                                                int64_t nunk, int32_t ldv, C<T> *__restrict__ u) {
     extern __shared__ __align__(16) unsigned char nd_smem[];
-    C<T> *v = reinterpret_cast<C<T> *>(nd_smem);   // [nf]: x_I (pivots), then x(U_f)
-    __shared__ C<T> red[8];
+    C<T> *v = reinterpret_cast<C<T> *>(nd_smem);   // [kG][ldv]: x_I (pivots), then x(U_f)
+    __shared__ C<T> blk[32][33];                   // blk[j][l] = L[c0 + j][c0 + l]
     const int32_t f = fa.order[lvl0 + blockIdx.x];
-    const int32_t r = blockIdx.y;
+    const int32_t *gr = grp + int64_t(blockIdx.y) * kG;
     const int32_t nf = fa.nf[f], nv = fa.nv[f];
     if (nv == 0) return;
-    const C<T> *Lf = L + int64_t(slot[r]) * sumL + fa.Loff[f];
-    const C<T> *ubase = u + int64_t(r) * nunk;
-    C<T> *ur = u + int64_t(r) * nunk + fa.first[f];
+    const C<T> *Lf = L + int64_t(slot[gr[0]]) * sumL + fa.Loff[f];
     const int32_t *ui = fa.uidx + fa.Uoff[f];
-    for (int32_t t = threadIdx.x; t < nf; t += blockDim.x) {
-        if (t < nv) {
-            const C<T> d = Lf[int64_t(t) * nf + t];
-            const T den = d.x * d.x + d.y * d.y;
-            v[t] = cmul(ur[t], mk<T>(d.x / den, -d.y / den));
-        } else {
-            v[t] = ubase[ui[t - nv]];
+    const C<T> zero = mk<T>(T(0), T(0));
+    for (int g = 0; g < kG; ++g) {
+        const int32_t r = gr[g];
+        const C<T> *ubase = u + int64_t(r < 0 ? 0 : r) * nunk;
+        const C<T> *ur = ubase + fa.first[f];
+        for (int32_t t = threadIdx.x; t < nf; t += blockDim.x) {
+            C<T> val = zero;
+            if (r >= 0) {
+                if (t < nv) {
+                    const C<T> d = Lf[int64_t(t) * nf + t];
+                    const T den = d.x * d.x + d.y * d.y;
+                    val = cmul(ur[t], mk<T>(d.x / den, -d.y / den));
+                } else {
+                    val = ubase[ui[t - nv]];
+                }
+            }
+            v[g * ldv + t] = val;
         }
     }
     __syncthreads();
@@ -379,28 +451,72 @@ __global__ void __launch_bounds__(256) k_nd_bwd(FrontArgs fa, int32_t lvl0, cons
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int32_t li = wid; li < nv; li += nw) {
         const C<T> *col = Lf + int64_t(li) * nf;
-        C<T> acc = mk<T>(T(0), T(0));
-        for (int32_t t = nv + lane; t < nf; t += 32) acc = cadd(acc, cmul(col[t], v[t]));
-        acc = warp_sum(acc);
-        if (lane == 0) v[li] = csub(v[li], acc);
+        C<T> acc[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) acc[g] = zero;
+        for (int32_t t = nv + lane; t < nf; t += 32) {
+            const C<T> l = col[t];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) acc[g] = cadd(acc[g], cmul(l, v[g * ldv + t]));
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            acc[g] = warp_sum(acc[g]);
+            if (lane == 0) v[g * ldv + li] = csub(v[g * ldv + li], acc[g]);
+        }
     }
-    // L_11^T x_I = w_I, last pivot first: x_j = w_j - sum_{i > j} l_ij x_i
-    for (int32_t j = nv - 1; j >= 0; --j) {
+    for (int32_t c0 = ((nv - 1) / 32) * 32; c0 >= 0; c0 -= 32) {
+        const int32_t cw = min(32, nv - c0), ce = c0 + cw;
         __syncthreads();
-        const C<T> *col = Lf + int64_t(j) * nf;
-        C<T> acc = mk<T>(T(0), T(0));
-        for (int32_t i = j + 1 + threadIdx.x; i < nv; i += blockDim.x) acc = cadd(acc, cmul(col[i], v[i]));
-        acc = warp_sum(acc);
-        if (lane == 0) red[wid] = acc;
+        // the solved pivots ce .. nv-1 into the chunk's rows: x_j -= sum_{i >= ce} l_ij x_i
+        for (int32_t jj = wid; jj < cw; jj += nw) {
+            const C<T> *col = Lf + int64_t(c0 + jj) * nf;
+            C<T> acc[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) acc[g] = zero;
+            for (int32_t i = ce + lane; i < nv; i += 32) {
+                const C<T> l = col[i];
+#pragma unroll
+                for (int g = 0; g < kG; ++g) acc[g] = cadd(acc[g], cmul(l, v[g * ldv + i]));
+            }
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                acc[g] = warp_sum(acc[g]);
+                if (lane == 0) v[g * ldv + c0 + jj] = csub(v[g * ldv + c0 + jj], acc[g]);
+            }
+        }
+        // the chunk's block of L (rows and columns c0 .. ce-1), staged for the lanes' row reads
+        for (int32_t t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+            const int32_t c = t >> 5, rr = t & 31;   // column c0 + c, row c0 + rr
+            blk[rr][c] = (rr < cw && c < cw) ? Lf[int64_t(c0 + c) * nf + c0 + rr] : zero;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            C<T> s = mk<T>(T(0), T(0));
-            for (int q = 0; q < nw; ++q) s = cadd(s, red[q]);
-            v[j] = csub(v[j], s);
+        if (threadIdx.x < 32) {   // upper-triangular block, lane l on pivot c0 + l, last pivot first
+            C<T> xl[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) xl[g] = lane < cw ? v[g * ldv + c0 + lane] : zero;
+            for (int32_t j = cw - 1; j >= 0; --j) {
+                const C<T> l = blk[j][lane];
+#pragma unroll
+                for (int g = 0; g < kG; ++g) {
+                    C<T> x;
+                    x.x = __shfl_sync(0xffffffffu, xl[g].x, j);
+                    x.y = __shfl_sync(0xffffffffu, xl[g].y, j);
+                    if (lane < j) xl[g] = csub(xl[g], cmul(l, x));
+                }
+            }
+            if (lane < cw)
+#pragma unroll
+                for (int g = 0; g < kG; ++g) v[g * ldv + c0 + lane] = xl[g];
         }
     }
     __syncthreads();
-    for (int32_t t = threadIdx.x; t < nv; t += blockDim.x) ur[t] = v[t];
+    for (int g = 0; g < kG; ++g) {
+        const int32_t r = gr[g];
+        if (r < 0) continue;
+        C<T> *ur = u + int64_t(r) * nunk + fa.first[f];
+        for (int32_t t = threadIdx.x; t < nv; t += blockDim.x) ur[t] = v[g * ldv + t];
+    }
 }
 
 }  // namespace
@@ -598,38 +714,46 @@ int nd_factor(pfft_plan *p, NdState *s, const double2 *a, const int32_t *row_ptr
 }
 
 // z = K^-1 rhs in place on u [R][nunk] (new numbering) with the factors of each
-// right-hand side's slot (L [nslots][sumL]); uv: update vectors [R][sumU].
+// right-hand side's slot (L [nslots][sumL]); grp: [ngrp][kG] groups of right-hand
+// sides sharing a slot (-1 pads); uv: update vectors [R][sumU].
 template <typename T>
-int nd_solve(pfft_plan *p, const NdState *s, const C<T> *L, const int32_t *slot, int32_t R, C<T> *u, C<T> *uv,
-             cudaStream_t st) {
+int nd_solve(pfft_plan *p, const NdState *s, const C<T> *L, const int32_t *slot, const int32_t *grp, int32_t ngrp,
+             C<T> *u, C<T> *uv, cudaStream_t st) {
     const FrontArgs fa = front_args(s);
     const int32_t H = int32_t(s->level_ptr.size()) - 1;
-    const size_t sm = size_t(std::max(s->max_nf, 1)) * sizeof(C<T>);
-    if (sm > 200 * 1024)
+    const size_t smax = size_t(kG) * std::max(s->max_nf, 1) * sizeof(C<T>);
+    if (smax > 180 * 1024)
         return fail(SIE_ERR_ARG, "preconditioner: a nested-dissection front of " + std::to_string(s->max_nf) +
                                      " unknowns exceeds the solve's shared memory");
-    if (sm > 48 * 1024) {
-        SIE_CUDA(cudaFuncSetAttribute((const void *)k_nd_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-        SIE_CUDA(cudaFuncSetAttribute((const void *)k_nd_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-    }
+    SIE_CUDA(cudaFuncSetAttribute((const void *)k_nd_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax)));
+    SIE_CUDA(cudaFuncSetAttribute((const void *)k_nd_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax)));
+    // each level's frontal vectors sized by its own largest front (the leaves are small:
+    // more CTAs resident per SM)
     for (int32_t h = 0; h < H; ++h) {
         const int32_t l0 = s->level_ptr[h], nfr = s->level_ptr[h + 1] - l0;
         if (!nfr) continue;
-        k_nd_fwd<T><<<dim3(unsigned(nfr), unsigned(R)), 256, sm, st>>>(fa, l0, L, s->sumL, slot, s->nunk, s->sumU, u, uv);
+        const int32_t ldv = std::max(s->level_max_nf[h], 1);
+        const size_t sm = size_t(kG) * ldv * sizeof(C<T>);
+        k_nd_fwd<T><<<dim3(unsigned(nfr), unsigned(ngrp)), 256, sm, st>>>(fa, l0, L, s->sumL, grp, slot, s->nunk,
+                                                                           s->sumU, ldv, u, uv);
         SIE_LAUNCH_CHECK(p);
     }
     for (int32_t h = H - 1; h >= 0; --h) {
         const int32_t l0 = s->level_ptr[h], nfr = s->level_ptr[h + 1] - l0;
         if (!nfr) continue;
-        k_nd_bwd<T><<<dim3(unsigned(nfr), unsigned(R)), 256, sm, st>>>(fa, l0, L, s->sumL, slot, s->nunk, u);
+        const int32_t ldv = std::max(s->level_max_nf[h], 1);
+        const size_t sm = size_t(kG) * ldv * sizeof(C<T>);
+        k_nd_bwd<T><<<dim3(unsigned(nfr), unsigned(ngrp)), 256, sm, st>>>(fa, l0, L, s->sumL, grp, slot, s->nunk,
+                                                                           ldv, u);
         SIE_LAUNCH_CHECK(p);
     }
     return SIE_OK;
 }
-template int nd_solve<double>(pfft_plan *, const NdState *, const double2 *, const int32_t *, int32_t, double2 *,
-                              double2 *, cudaStream_t);
-template int nd_solve<float>(pfft_plan *, const NdState *, const float2 *, const int32_t *, int32_t, float2 *, float2 *,
-                             cudaStream_t);
+template int nd_solve<double>(pfft_plan *, const NdState *, const double2 *, const int32_t *, const int32_t *,
+                              int32_t, double2 *, double2 *, cudaStream_t);
+template int nd_solve<float>(pfft_plan *, const NdState *, const float2 *, const int32_t *, const int32_t *, int32_t,
+                             float2 *, float2 *, cudaStream_t);
+int nd_group_size() { return kG; }
 
 void nd_free(NdState *s) {
     if (!s) return;

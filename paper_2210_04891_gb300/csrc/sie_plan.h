@@ -248,8 +248,9 @@ int nd_rows(NdState *s, const std::vector<int32_t> &row_ptr, const std::vector<i
 int nd_factor(pfft_plan *p, NdState *s, const double2 *a, const int32_t *row_ptr, const int32_t *row_br, double2 *W,
               double2 *L64, float2 *L32, int *status, cudaStream_t st);
 template <typename T>
-int nd_solve(pfft_plan *p, const NdState *s, const C<T> *L, const int32_t *slot, int32_t R, C<T> *u, C<T> *uv,
-             cudaStream_t st);
+int nd_solve(pfft_plan *p, const NdState *s, const C<T> *L, const int32_t *slot, const int32_t *grp, int32_t ngrp,
+             C<T> *u, C<T> *uv, cudaStream_t st);
+int nd_group_size();   // right-hand sides per solve group (grp rows)
 int64_t nd_factor_size(const NdState *s);
 int64_t nd_workspace_size(const NdState *s);
 int64_t nd_update_size(const NdState *s);

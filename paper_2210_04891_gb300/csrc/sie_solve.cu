@@ -81,6 +81,8 @@ struct PrecondState {
     double2 *d_ndL64 = nullptr;
     float2 *d_ndL32 = nullptr;
     double2 *d_uv = nullptr;
+    int32_t *d_grp = nullptr;         // [ngrp][group size] right-hand sides sharing a slot (-1 pads)
+    int32_t ngrp = 0, cap_grp = 0;
     std::vector<void *> allocs;
 };
 
@@ -127,7 +129,7 @@ void plan_free_precond(pfft_plan *p) {
         if (a) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
                     (void *)p->pc->d_ibr, (void *)p->pc->d_slot, (void *)p->pc->d_ndL64, (void *)p->pc->d_ndL32,
-                    (void *)p->pc->d_uv})
+                    (void *)p->pc->d_uv, (void *)p->pc->d_grp})
         if (a) cudaFree(a);
     nd_free(p->pc->nd);
     delete p->pc;
@@ -986,6 +988,28 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         s->cap_rhs = R;
     }
     SIE_CUDA(cudaMemcpyAsync(s->d_slot, slot.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (s->nd) {
+        // the nested-dissection solves take the right-hand sides of one slot in groups
+        const int G = nd_group_size();
+        std::vector<int32_t> grp;
+        for (int32_t f = 0; f < int32_t(uniq.size()); ++f) {
+            std::vector<int32_t> rs;
+            for (int32_t r = 0; r < R; ++r)
+                if (slot[r] == f) rs.push_back(r);
+            for (size_t k = 0; k < rs.size(); k += G)
+                for (int g = 0; g < G; ++g) grp.push_back(k + g < rs.size() ? rs[k + g] : -1);
+        }
+        const int32_t ng = int32_t(grp.size() / G);
+        if (ng > s->cap_grp) {
+            if (s->d_grp) cudaFreeAsync(s->d_grp, st);
+            s->d_grp = nullptr;
+            SIE_CUDA(pool_alloc(p, &s->d_grp, grp.size() * sizeof(int32_t), st));
+            s->cap_grp = ng;
+        }
+        SIE_CUDA(cudaMemcpyAsync(s->d_grp, grp.data(), grp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        SIE_CUDA(cudaStreamSynchronize(st));   // grp is a host temporary
+        s->ngrp = ng;
+    }
     if (uniq == s->slot_omega) return SIE_OK;   // factors cached
     const int32_t ns = int32_t(uniq.size());
     if (s->d_band) cudaFreeAsync(s->d_band, st);
@@ -1130,7 +1154,7 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
         SIE_LAUNCH_CHECK(p);
         const C<T> *Lf;
         if constexpr (f32) Lf = s->d_ndL32; else Lf = s->d_ndL64;
-        int rn = nd_solve<T>(p, s->nd, Lf, s->d_slot, R, u, reinterpret_cast<C<T> *>(s->d_uv), st);
+        int rn = nd_solve<T>(p, s->nd, Lf, s->d_slot, s->d_grp, s->ngrp, u, reinterpret_cast<C<T> *>(s->d_uv), st);
         if (rn) return rn;
     } else if (s->nunk > 0) {
         if (s->W <= 31) {
