@@ -434,6 +434,92 @@ def batch_main(args, ws, dist=None, n_total=None):
     print(json.dumps(line))
 
 
+def learned_main(args):
+    """The learned preconditioner correction at its configured scale: a 6 -> 128 ->
+    128 -> 1 network computing with FP16 weights and FP32 accumulation, trained on
+    the device on features and probing targets of `learned_train` seeded geometries
+    (meanders and bond-wire arrays, 5k-40k triangles; 256 branches sampled per
+    geometry and frequency) at 1 and 10 GHz, then judged by the plain
+    preconditioner on `learned_held_out` held-out geometries: mixed GMRES with
+    refinement to 1e-6, iterations and time of both forms."""
+    import torch
+    from paper_2210_04891_gb300 import api, PREC_MIXED
+    import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    freqs = np.array([1e9, 1e10])
+    per = 256
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    feats, targets = [], []
+    t0 = time.perf_counter()
+    ntri = 0
+    for k in range(args.learned_train):
+        w = synth.learned_geometry(1000 + k)
+        m = w["mesh"]
+        ntri += m.nt
+        M = api.Mesh.from_synth(m)
+        L = api.Loops(M, m.ports)
+        P = api.Plan(M, L, dict(PLAN_PARAMS, n_touch=8, grid=w["grid"]))
+        sel = torch.randint(0, P.nb, (per,), generator=gen, device="cuda")
+        for j, f in enumerate(freqs):
+            alpha = torch.from_numpy(synth.complex_gaussian(P.nb, 4, seed=100000 + 2 * k + j)).cuda()
+            feats.append(api.branch_features(P, 2 * np.pi * f)[sel])
+            targets.append(api.branch_probe_target(P, alpha, 2 * np.pi * f)[sel])
+        del P, L, M
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    F, T = torch.cat(feats), torch.cat(targets)
+    net = api.MLP(128, seed=1)
+    t0 = time.perf_counter()
+    losses = net.train(F, T, args.learned_steps, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"plain": {"iterations_sum": 0, "seconds": 0.0, "not_converged": 0},
+           "learned": {"iterations_sum": 0, "seconds": 0.0, "not_converged": 0}}
+    zdiff, better, worse, ntri_eval = 0.0, 0, 0, 0
+    for k in range(args.learned_held_out):
+        w = synth.learned_geometry(5000 + k)
+        m = w["mesh"]
+        ntri_eval += m.nt
+        M = api.Mesh.from_synth(m)
+        L = api.Loops(M, m.ports)
+        P = api.Plan(M, L, dict(PLAN_PARAMS, n_touch=8, grid=w["grid"]))
+        its = {}
+        for name in ("plain", "learned"):
+            api.set_learned(P, net if name == "learned" else None)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            Z, st = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=500, prec=PREC_MIXED, refine=True)
+            out[name]["seconds"] += time.perf_counter() - t1
+            out[name]["iterations_sum"] += int(st["iterations_sum"])
+            out[name]["not_converged"] += int(not st["converged"])
+            its[name] = st["iterations_sum"]
+            if name == "plain":
+                Zp = Z
+            else:
+                zdiff = max(zdiff, float(np.abs(Z - Zp).max() / np.abs(Zp).max()))
+        api.set_learned(P, None)
+        better += its["learned"] < its["plain"]
+        worse += its["learned"] > its["plain"]
+        del P, L, M
+    line = {"metric": "learned preconditioner correction: GMRES iterations and time to 1e-6, plain vs learned",
+            "value": out["plain"]["iterations_sum"] / max(1, out["learned"]["iterations_sum"]),
+            "unit": "plain / learned iterations", "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "learned_%dx_5k-40k" % args.learned_train,
+                       "network": "6 -> 128 -> 128 -> 1, tanh, FP16 weights, FP32 accumulation",
+                       "train_geometries": args.learned_train, "train_triangles": ntri,
+                       "samples": int(F.shape[0]), "branches_per_geometry_and_frequency": per,
+                       "held_out_geometries": args.learned_held_out, "held_out_triangles": ntri_eval,
+                       "frequencies_hz": freqs.tolist(), "solve": "mixed GMRES with FP64 refinement, tol 1e-6"},
+            "data_seconds": t_data, "train_steps": args.learned_steps, "train_seconds": t_train,
+            "loss_first": float(losses[0]), "loss_last": float(losses[-1]), **out,
+            "held_out_fewer_iterations": better, "held_out_more_iterations": worse,
+            "Z_rel_learned_vs_plain": zdiff,
+            "chosen": "learned" if out["learned"]["iterations_sum"] < out["plain"]["iterations_sum"]
+            else "plain (fallback)"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,6 +538,11 @@ def main():
                          "and compare it with the plain preconditioner on the others")
     ap.add_argument("--no-lossy", dest="lossy", action="store_false",
                     help="skip the lossy-kernel variant's timing")
+    ap.add_argument("--learned-train", type=int, default=2000,
+                    help="workload learned_c5: training geometries")
+    ap.add_argument("--learned-held-out", type=int, default=200,
+                    help="workload learned_c5: held-out geometries")
+    ap.add_argument("--learned-steps", type=int, default=400, help="workload learned_c5: Adam steps")
     ap.add_argument("--graph", action="store_true",
                     help="with --step matvec: replay the product as a captured CUDA graph (a batch of one plan)")
     args = ap.parse_args()
@@ -459,6 +550,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     import synth
+    if args.workload == "learned_c5":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline covers single geometries"}))
+            return
+        if rank == 0:
+            learned_main(args)
+        return
     wl = synth.WORKLOADS[args.workload]()
     if isinstance(wl, list):
         if args.impl == "reference":

@@ -364,7 +364,9 @@ int pfft_autotune(const sie_mesh *m, const sie_loops *l, const pfft_params *base
  * for the diagonal D_e of Z_b on each branch, g a network of six per-branch
  * features at the frequency (quarter decades of |Z_s| G_ee, c_L Lt_ee, their
  * ratio, G_ee, Lt_ee and omega), f [6] -> tanh [H] -> tanh [H] ->
- * g = 0.5 tanh(.), H = 16 or 32, FP32 parameters on the device, flat
+ * g = 0.5 tanh(.), H = 16 or 32 (FP32 parameters) or 128 (the network computes
+ * with FP16 roundings of FP32 master parameters, FP32 accumulation; Adam
+ * updates the masters), parameters on the device, flat
  * [W1 H x 6][b1 H][W2 H x H][b2 H][w3 H][b3].  A new network has a zero output
  * layer: g = 0, the plain preconditioner.  Training is full-batch mean squared
  * error against per-branch targets with Adam (device kernels); the plain

@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "sie_plan.h"
 
 using namespace sie;
@@ -214,6 +216,267 @@ __global__ void __launch_bounds__(128) k_learned_admittance(const float *__restr
     a[i] = make_double2(a[i].x * s, a[i].y * s);
 }
 
+// ---- the width-128 network with FP16 parameters (FP32 arithmetic)
+//
+// f [6] -> tanh [128] -> tanh [128] -> g = 0.5 tanh(.), every parameter held as
+// FP16 (the rounding of FP32 master weights that Adam updates) and converted to
+// FP32 for the arithmetic.  A CTA of 128 threads takes tiles of 32 samples:
+// thread j computes hidden unit j of every sample of the tile, so the 128 x 128
+// layer is a loop of 128 x 32 FMAs per thread over the tile's first-layer
+// activations (shared-memory broadcasts) and the FP16 weight column of unit j.
+constexpr int kW = 128, kS = 32;
+
+struct alignas(16) Net128 {   // shared-memory copy of the parameters
+    float W1[kW * kF], b1[kW], b2[kW], w3[kW], b3;
+    __half W2T[kW * kW];   // W2T[i * 128 + j] = W2[j][i]
+};
+
+__device__ void load_net128(const __half *__restrict__ p16, Net128 &N, __half *W2 /* [j][i] or null */) {
+    constexpr Layout L{kW};
+    for (int i = threadIdx.x; i < kW * kF; i += blockDim.x) N.W1[i] = __half2float(p16[L.W1() + i]);
+    for (int i = threadIdx.x; i < kW; i += blockDim.x) {
+        N.b1[i] = __half2float(p16[L.b1() + i]);
+        N.b2[i] = __half2float(p16[L.b2() + i]);
+        N.w3[i] = __half2float(p16[L.w3() + i]);
+    }
+    for (int t = threadIdx.x; t < kW * kW; t += blockDim.x) {
+        const int j = t / kW, i = t % kW;   // W2[j][i]
+        const __half w = p16[L.W2() + t];
+        N.W2T[i * kW + j] = w;
+        if (W2) W2[t] = w;
+    }
+    if (threadIdx.x == 0) N.b3 = __half2float(p16[L.b3()]);
+}
+
+// Forward pass of one tile (ft [kS][6] features, ns valid samples): h1, h2
+// [kS][128] and th[s] = tanh(z_s); returns through g[s] (s < ns).  Threads:
+// 128 (one hidden unit each).
+__device__ void fwd_tile128(const Net128 &N, const float *ft, float *h1, float *h2, float *zred, float *th, int ns) {
+    const int j = threadIdx.x;
+    for (int s = 0; s < kS; ++s) {
+        float a = N.b1[j];
+#pragma unroll
+        for (int k = 0; k < kF; ++k) a += N.W1[j * kF + k] * ft[s * kF + k];
+        h1[s * kW + j] = s < ns ? tanhf(a) : 0.f;
+    }
+    __syncthreads();
+    float acc[kS];
+#pragma unroll
+    for (int s = 0; s < kS; ++s) acc[s] = N.b2[j];
+    for (int i = 0; i < kW; i += 4) {
+        const float w0 = __half2float(N.W2T[(i + 0) * kW + j]), w1 = __half2float(N.W2T[(i + 1) * kW + j]),
+                    w2 = __half2float(N.W2T[(i + 2) * kW + j]), w3 = __half2float(N.W2T[(i + 3) * kW + j]);
+#pragma unroll
+        for (int s = 0; s < kS; ++s) {
+            const float4 h = *reinterpret_cast<const float4 *>(h1 + s * kW + i);
+            acc[s] += w0 * h.x + w1 * h.y + w2 * h.z + w3 * h.w;
+        }
+    }
+    const int lane = j & 31, wp = j >> 5;
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+        const float h = tanhf(acc[s]);
+        h2[s * kW + j] = h;
+        float z = N.w3[j] * h;
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (lane == 0) zred[wp * kS + s] = z;
+    }
+    __syncthreads();
+    if (j < kS) th[j] = tanhf(N.b3 + zred[j] + zred[kS + j] + zred[2 * kS + j] + zred[3 * kS + j]);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kW) k_mlp128_forward(const __half *__restrict__ p16, const float *__restrict__ feats,
+                                                       int64_t n, float *__restrict__ g) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Net128 &N = *reinterpret_cast<Net128 *>(smraw);
+    float *h1 = reinterpret_cast<float *>(smraw + sizeof(Net128));
+    float *h2 = h1 + kS * kW, *ft = h2 + kS * kW, *zred = ft + kS * kF, *th = zred + 4 * kS;
+    load_net128(p16, N, nullptr);
+    for (int64_t t0 = int64_t(blockIdx.x) * kS; t0 < n; t0 += int64_t(gridDim.x) * kS) {
+        const int ns = int(n - t0 < kS ? n - t0 : kS);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kS * kF; q += blockDim.x) ft[q] = q / kF < ns ? feats[t0 * kF + q] : 0.f;
+        __syncthreads();
+        fwd_tile128(N, ft, h1, h2, zred, th, ns);
+        if (threadIdx.x < ns) g[t0 + threadIdx.x] = kScale * th[threadIdx.x];
+    }
+}
+
+// Gradient of (1/n) sum (g - t)^2 over the CTA's tiles into part[blockIdx.x]
+// [param count] and the loss into lpart[blockIdx.x]; accumulators in shared
+// memory (gW2 transposed: thread j owns column j).
+__global__ void __launch_bounds__(kW) k_mlp128_backward(const __half *__restrict__ p16, const float *__restrict__ feats,
+                                                        const float *__restrict__ target, int64_t n,
+                                                        float *__restrict__ part, float *__restrict__ lpart) {
+    constexpr Layout L{kW};
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Net128 &N = *reinterpret_cast<Net128 *>(smraw);
+    __half *W2 = reinterpret_cast<__half *>(smraw + sizeof(Net128));      // [j][i]
+    float *h1 = reinterpret_cast<float *>(W2 + kW * kW);
+    float *h2 = h1 + kS * kW, *ft = h2 + kS * kW, *zred = ft + kS * kF, *th = zred + 4 * kS, *dz = th + kS;
+    float *gW2T = dz + kS, *gW1 = gW2T + kW * kW, *gb1 = gW1 + kW * kF, *gb2 = gb1 + kW, *gw3 = gb2 + kW;
+    float *gsc = gw3 + kW;   // [0] gb3, [1] loss
+    load_net128(p16, N, W2);
+    const int j = threadIdx.x;
+    for (int i = 0; i < kW; ++i) gW2T[i * kW + j] = 0.f;
+    for (int k = 0; k < kF; ++k) gW1[j * kF + k] = 0.f;
+    gb1[j] = gb2[j] = gw3[j] = 0.f;
+    if (j < 2) gsc[j] = 0.f;
+    for (int64_t t0 = int64_t(blockIdx.x) * kS; t0 < n; t0 += int64_t(gridDim.x) * kS) {
+        const int ns = int(n - t0 < kS ? n - t0 : kS);
+        __syncthreads();
+        for (int q = j; q < kS * kF; q += blockDim.x) ft[q] = q / kF < ns ? feats[t0 * kF + q] : 0.f;
+        __syncthreads();
+        fwd_tile128(N, ft, h1, h2, zred, th, ns);
+        if (j < kS) {
+            float d = 0.f;
+            if (j < ns) {
+                const float r = kScale * th[j] - target[t0 + j];
+                atomicAdd(&gsc[1], r * r / float(n));
+                d = 2.f * r / float(n) * kScale * (1.f - th[j] * th[j]);
+                atomicAdd(&gsc[0], d);
+            }
+            dz[j] = d;
+        }
+        __syncthreads();
+        // output layer and the second hidden layer (thread j: unit j)
+        float d2[kS];
+        float sw = 0.f, sb = 0.f;
+#pragma unroll
+        for (int s = 0; s < kS; ++s) {
+            const float h = h2[s * kW + j];
+            sw += dz[s] * h;
+            d2[s] = dz[s] * N.w3[j] * (1.f - h * h);
+            sb += d2[s];
+        }
+        gw3[j] += sw;
+        gb2[j] += sb;
+        for (int i = 0; i < kW; i += 4) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+            for (int s = 0; s < kS; ++s) {
+                const float4 h = *reinterpret_cast<const float4 *>(h1 + s * kW + i);
+                a0 += d2[s] * h.x;
+                a1 += d2[s] * h.y;
+                a2 += d2[s] * h.z;
+                a3 += d2[s] * h.w;
+            }
+            gW2T[(i + 0) * kW + j] += a0;
+            gW2T[(i + 1) * kW + j] += a1;
+            gW2T[(i + 2) * kW + j] += a2;
+            gW2T[(i + 3) * kW + j] += a3;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < kS; ++s) h2[s * kW + j] = d2[s];   // h2 now holds d2[s][j]
+        __syncthreads();
+        // first hidden layer (thread i = j: unit i): d1[s] = (sum_j W2[j][i] d2[s][j]) (1 - h1^2)
+        const int i = j;
+        float d1[kS];
+#pragma unroll
+        for (int s = 0; s < kS; ++s) d1[s] = 0.f;
+        for (int jj = 0; jj < kW; jj += 4) {
+            const float w0 = __half2float(W2[(jj + 0) * kW + i]), w1 = __half2float(W2[(jj + 1) * kW + i]),
+                        w2 = __half2float(W2[(jj + 2) * kW + i]), w3 = __half2float(W2[(jj + 3) * kW + i]);
+#pragma unroll
+            for (int s = 0; s < kS; ++s) {
+                const float4 d = *reinterpret_cast<const float4 *>(h2 + s * kW + jj);
+                d1[s] += w0 * d.x + w1 * d.y + w2 * d.z + w3 * d.w;
+            }
+        }
+        float gb = 0.f, gw[kF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int s = 0; s < kS; ++s) {
+            const float h = h1[s * kW + i];
+            const float d = d1[s] * (1.f - h * h);
+            gb += d;
+#pragma unroll
+            for (int k = 0; k < kF; ++k) gw[k] += d * ft[s * kF + k];
+        }
+        gb1[i] += gb;
+#pragma unroll
+        for (int k = 0; k < kF; ++k) gW1[i * kF + k] += gw[k];
+    }
+    __syncthreads();
+    float *out = part + int64_t(blockIdx.x) * L.n();
+    for (int t = j; t < kW * kF; t += blockDim.x) out[L.W1() + t] = gW1[t];
+    for (int t = j; t < kW * kW; t += blockDim.x) {
+        const int jj = t / kW, ii = t % kW;
+        out[L.W2() + t] = gW2T[ii * kW + jj];
+    }
+    out[L.b1() + j] = gb1[j];
+    out[L.b2() + j] = gb2[j];
+    out[L.w3() + j] = gw3[j];
+    if (j == 0) {
+        out[L.b3()] = gsc[0];
+        lpart[blockIdx.x] = gsc[1];
+    }
+}
+
+// grad[p] = sum over the CTAs' partial gradients; loss likewise.
+__global__ void k_mlp_reduce(const float *__restrict__ part, const float *__restrict__ lpart, int nblk, int np,
+                             float *__restrict__ grad, float *__restrict__ loss) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) {
+        float a = 0.f;
+        for (int b = 0; b < nblk; ++b) a += part[int64_t(b) * np + p];
+        grad[p] = a;
+    }
+    if (p == 0) {
+        float l = 0.f;
+        for (int b = 0; b < nblk; ++b) l += lpart[b];
+        *loss = l;
+    }
+}
+
+__global__ void k_round_half(const float *__restrict__ p, __half *__restrict__ h, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) h[i] = __float2half_rn(p[i]);
+}
+
+// a_e /= 1 + g(f_e) with the width-128 network, tiles of 32 (slot, branch) items.
+__global__ void __launch_bounds__(kW) k_learned_admittance128(const __half *__restrict__ p16,
+                                                              const double *__restrict__ diag_gram,
+                                                              const double *__restrict__ diag_L,
+                                                              const int32_t *__restrict__ br_cond,
+                                                              const double *__restrict__ zs_cl, int ncond, int64_t nb,
+                                                              int32_t nslots, double2 *__restrict__ a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Net128 &N = *reinterpret_cast<Net128 *>(smraw);
+    float *h1 = reinterpret_cast<float *>(smraw + sizeof(Net128));
+    float *h2 = h1 + kS * kW, *ft = h2 + kS * kW, *zred = ft + kS * kF, *th = zred + 4 * kS;
+    load_net128(p16, N, nullptr);
+    const int64_t n = nb * int64_t(nslots);
+    for (int64_t t0 = int64_t(blockIdx.x) * kS; t0 < n; t0 += int64_t(gridDim.x) * kS) {
+        const int ns = int(n - t0 < kS ? n - t0 : kS);
+        __syncthreads();
+        if (threadIdx.x < kS) {
+            float f[kF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (threadIdx.x < ns) {
+                const int64_t i = t0 + threadIdx.x, fs = i / nb, e = i % nb;
+                const double *cf = zs_cl + fs * (2 * ncond + 1);
+                const int c = br_cond[e];
+                branch_features(sqrt(cf[2 * c] * cf[2 * c] + cf[2 * c + 1] * cf[2 * c + 1]), cf[2 * ncond],
+                                diag_gram[e], diag_L[e], f);
+            }
+#pragma unroll
+            for (int k = 0; k < kF; ++k) ft[threadIdx.x * kF + k] = f[k];
+        }
+        __syncthreads();
+        fwd_tile128(N, ft, h1, h2, zred, th, ns);
+        if (threadIdx.x < ns) {
+            const int64_t i = t0 + threadIdx.x;
+            const double sc = 1.0 / (1.0 + double(kScale * th[threadIdx.x]));
+            a[i] = make_double2(a[i].x * sc, a[i].y * sc);
+        }
+    }
+}
+
+constexpr size_t kSmemFwd128 = sizeof(Net128) + sizeof(float) * (2 * kS * kW + kS * kF + 5 * kS);
+constexpr size_t kSmemBwd128 = sizeof(Net128) + sizeof(__half) * kW * kW +
+                               sizeof(float) * (2 * kS * kW + kS * kF + 6 * kS + kW * kW + kW * kF + 3 * kW + 2);
+
 // splitmix64 for the initial weights
 uint64_t mix64(uint64_t z) {
     z += 0x9e3779b97f4a7c15ull;
@@ -229,8 +492,31 @@ struct sie_mlp {
     int device = 0;
     int64_t t = 0;                      // Adam steps taken
     float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr, *d_loss = nullptr;
+    // width 128: the FP16 parameters the network computes with (rounded from d_p),
+    // and the backward pass's per-CTA partial gradients and losses
+    __half *d_p16 = nullptr;
+    float *d_part = nullptr, *d_lpart = nullptr;
+    int nblk = 0;
     int n() const { return Layout{H}.n(); }
 };
+
+namespace {
+int refresh_half(sie_mlp *m, cudaStream_t st) {
+    if (!m->d_p16) return SIE_OK;
+    k_round_half<<<(m->n() + 255) / 256, 256, 0, st>>>(m->d_p, m->d_p16, m->n());
+    SIE_CUDA(cudaGetLastError());
+    return SIE_OK;
+}
+int set_smem128() {
+    SIE_CUDA(cudaFuncSetAttribute((const void *)k_mlp128_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(kSmemFwd128)));
+    SIE_CUDA(cudaFuncSetAttribute((const void *)k_learned_admittance128,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemFwd128)));
+    SIE_CUDA(cudaFuncSetAttribute((const void *)k_mlp128_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(kSmemBwd128)));
+    return SIE_OK;
+}
+}  // namespace
 
 namespace sie {
 // Scale the admittances a [nslots][nb] by 1 / (1 + g) with the plan's learned network.
@@ -239,7 +525,13 @@ int learned_admittance(pfft_plan *p, const double *d_zs_cl, int32_t nslots, doub
     if (!m) return SIE_OK;
     const int64_t n = p->nb * int64_t(nslots);
     const unsigned grid = unsigned((n + 127) / 128);
-    if (m->H == 16)
+    if (m->H == kW) {
+        int rc = set_smem128();
+        if (rc) return rc;
+        const int64_t tiles = (n + kS - 1) / kS;
+        k_learned_admittance128<<<unsigned(std::min<int64_t>(tiles, 4096)), kW, kSmemFwd128, st>>>(
+            m->d_p16, p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zs_cl, p->ncond, p->nb, nslots, a);
+    } else if (m->H == 16)
         k_learned_admittance<16><<<grid, 128, 0, st>>>(m->d_p, p->d_diag_gram, p->d_diag_L, p->d_br_cond, d_zs_cl,
                                                        p->ncond, p->nb, nslots, a);
     else
@@ -253,7 +545,8 @@ int learned_admittance(pfft_plan *p, const double *d_zs_cl, int32_t nslots, doub
 extern "C" int sie_mlp_create(int32_t hidden, uint64_t seed, sie_mlp **out) {
     if (!out) return fail(SIE_ERR_ARG, "sie_mlp_create: out is NULL");
     *out = nullptr;
-    if (hidden != 16 && hidden != 32) return fail(SIE_ERR_ARG, "sie_mlp_create: hidden width must be 16 or 32");
+    if (hidden != 16 && hidden != 32 && hidden != kW)
+        return fail(SIE_ERR_ARG, "sie_mlp_create: hidden width must be 16, 32 or 128");
     sie_mlp *m = new (std::nothrow) sie_mlp;
     if (!m) return fail(SIE_ERR_OOM, "sie_mlp_create: out of host memory");
     m->H = hidden;
@@ -277,14 +570,27 @@ extern "C" int sie_mlp_create(int32_t hidden, uint64_t seed, sie_mlp **out) {
     if ((e = cudaMemcpy(m->d_p, p.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
     cudaMemset(m->d_m, 0, b);
     cudaMemset(m->d_v, 0, b);
+    if (hidden == kW) {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+        m->nblk = std::max(1, nsm);
+        if ((e = cudaMalloc(&m->d_p16, size_t(L.n()) * sizeof(__half))) != cudaSuccess) return bail(e);
+        if ((e = cudaMalloc(&m->d_part, size_t(m->nblk) * L.n() * sizeof(float))) != cudaSuccess) return bail(e);
+        if ((e = cudaMalloc(&m->d_lpart, size_t(m->nblk) * sizeof(float))) != cudaSuccess) return bail(e);
+        if (refresh_half(m, nullptr) || cudaDeviceSynchronize() != cudaSuccess) {
+            sie_mlp_destroy(m);
+            return fail(SIE_ERR_CUDA, "sie_mlp_create: FP16 copy failed");
+        }
+    }
     *out = m;
     return SIE_OK;
 }
 
 extern "C" void sie_mlp_destroy(sie_mlp *m) {
     if (!m) return;
-    for (float *d : {m->d_p, m->d_g, m->d_m, m->d_v, m->d_loss})
+    for (float *d : {m->d_p, m->d_g, m->d_m, m->d_v, m->d_loss, m->d_part, m->d_lpart})
         if (d) cudaFree(d);
+    if (m->d_p16) cudaFree(m->d_p16);
     delete m;
 }
 
@@ -302,6 +608,9 @@ extern "C" int sie_mlp_set_params(sie_mlp *m, const float *host, int64_t n) {
     SIE_CUDA(cudaMemset(m->d_m, 0, size_t(n) * sizeof(float)));
     SIE_CUDA(cudaMemset(m->d_v, 0, size_t(n) * sizeof(float)));
     m->t = 0;
+    int rc = refresh_half(m, nullptr);
+    if (rc) return rc;
+    SIE_CUDA(cudaDeviceSynchronize());
     return SIE_OK;
 }
 
@@ -309,8 +618,16 @@ extern "C" int sie_mlp_forward(const sie_mlp *m, const float *feats, int64_t n, 
     if (!m || !feats || !g || n < 1) return fail(SIE_ERR_ARG, "sie_mlp_forward: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const unsigned grid = unsigned((n + 127) / 128);
-    if (m->H == 16) k_mlp_forward<16><<<grid, 128, 0, st>>>(m->d_p, feats, n, g);
-    else k_mlp_forward<32><<<grid, 128, 0, st>>>(m->d_p, feats, n, g);
+    if (m->H == kW) {
+        int rc = set_smem128();
+        if (rc) return rc;
+        const int64_t tiles = (n + kS - 1) / kS;
+        k_mlp128_forward<<<unsigned(std::min<int64_t>(tiles, 4096)), kW, kSmemFwd128, st>>>(m->d_p16, feats, n, g);
+    } else if (m->H == 16) {
+        k_mlp_forward<16><<<grid, 128, 0, st>>>(m->d_p, feats, n, g);
+    } else {
+        k_mlp_forward<32><<<grid, 128, 0, st>>>(m->d_p, feats, n, g);
+    }
     SIE_CUDA(cudaGetLastError());
     SIE_CUDA(cudaStreamSynchronize(st));
     return SIE_OK;
@@ -319,6 +636,17 @@ extern "C" int sie_mlp_forward(const sie_mlp *m, const float *feats, int64_t n, 
 namespace {
 int mlp_grad(sie_mlp *m, const float *feats, const float *target, int64_t n, cudaStream_t st) {
     const size_t b = size_t(m->n()) * sizeof(float);
+    if (m->H == kW) {   // per-CTA partials in shared memory, then one reduction pass
+        int rc = set_smem128();
+        if (rc) return rc;
+        const int64_t tiles = (n + kS - 1) / kS;
+        const int nb = int(std::min<int64_t>(tiles, m->nblk));
+        k_mlp128_backward<<<nb, kW, kSmemBwd128, st>>>(m->d_p16, feats, target, n, m->d_part, m->d_lpart);
+        SIE_CUDA(cudaGetLastError());
+        k_mlp_reduce<<<(m->n() + 255) / 256, 256, 0, st>>>(m->d_part, m->d_lpart, nb, m->n(), m->d_g, m->d_loss);
+        SIE_CUDA(cudaGetLastError());
+        return SIE_OK;
+    }
     SIE_CUDA(cudaMemsetAsync(m->d_g, 0, b, st));
     SIE_CUDA(cudaMemsetAsync(m->d_loss, 0, sizeof(float), st));
     const unsigned grid = unsigned((n + 127) / 128);
@@ -354,6 +682,7 @@ extern "C" int sie_mlp_train(sie_mlp *m, const float *feats, const float *target
         const float c1 = float(1.0 - std::pow(0.9, double(m->t))), c2 = float(1.0 - std::pow(0.999, double(m->t)));
         k_adam<<<(np + 255) / 256, 256, 0, st>>>(m->d_p, m->d_g, m->d_m, m->d_v, np, lr, c1, c2);
         SIE_CUDA(cudaGetLastError());
+        if ((rc = refresh_half(m, st))) return rc;
         if (loss_host) SIE_CUDA(cudaMemcpyAsync(loss_host + s, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
     }
     SIE_CUDA(cudaStreamSynchronize(st));

@@ -87,6 +87,31 @@ def meanders_32(n=32, n_tri=None):
     return [meander(k, n_tri) for k in range(n)]
 
 
+def learned_geometry(seed):
+    """A geometry of the learned-preconditioner study (seed): even seeds a
+    meander trace, odd seeds a bond-wire array; triangle count log-uniform in
+    [5k, 40k].  Meander: the batched workload's generator with that count.
+    Bond wires: U{1..8} Au wires, radius U(10, 30) um (16-gon), pitch U(3, 8)
+    radii, axial segments as long as a side of the polygon (axial jitter
+    +-10%) and as many as the triangle count asks, one port per wire.  Grid
+    from grid_for with two panel sizes as the cell."""
+    rng = np.random.default_rng(seed)
+    target = float(np.exp(rng.uniform(np.log(5e3), np.log(4e4))))
+    if seed % 2 == 0:
+        w = meander(seed, n_tri=target)
+        return dict(w, name="learned_meander_%d" % seed)
+    nw = int(rng.integers(1, 9))
+    r = rng.uniform(10, 30) * UM
+    pitch = rng.uniform(3, 8) * r
+    n_sides = 16
+    seg = 2 * np.pi * r / n_sides                      # square-ish panels
+    n_seg = max(4, int(round(target / (nw * 2 * n_sides) - 1)))
+    m = wire_array_mesh(nw, r, n_seg * seg, pitch, n_sides=n_sides, n_seg=n_seg, jitter=0.10, seed=seed,
+                        sigma=4.1e7, name="learned_wires_%d" % seed)
+    return dict(mesh=m, freqs=np.array([1e9, 1e10]), grid=grid_for(m, 2 * seg),
+                name="learned_wires_%d" % seed)
+
+
 def tiny_pdn(seed=12):
     """Small plane pair (0.6 x 0.6 mm, 25 um cells, 2 via pairs of one-cell vias,
     2 ports, ~4.8k triangles) for oracle checks of the same structure."""

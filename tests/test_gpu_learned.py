@@ -92,6 +92,53 @@ def test_forward_and_gradient_match_oracle(H):
     assert np.abs(grad - gr).max() < 1e-4 * np.abs(gr).max()
 
 
+def test_width128_fp16_network_matches_oracle():
+    # the configured network (6 -> 128 -> 128 -> 1) computes with FP16 roundings of
+    # its FP32 master parameters and FP32 accumulation: the oracle's FP64 forward,
+    # loss and gradient at those rounded parameters (straight-through gradient)
+    H = 128
+    rng = np.random.default_rng(H)
+    n = 3000   # several CTA partials and a ragged last tile
+    p = random_params(H, 7)
+    f = rng.uniform(-3, 3, (n, 6))
+    t = rng.uniform(-0.4, 0.4, n)
+    net = api.MLP(H, seed=1)
+    net.set_params(flat(p).astype(np.float32))
+    p16 = {k: v.astype(np.float32).astype(np.float16).astype(np.float64) for k, v in p.items()}
+    f32 = f.astype(np.float32).astype(np.float64)
+    fd = torch.from_numpy(f.astype(np.float32)).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    g_ref, _ = OL.forward(p16, f32)
+    assert np.abs(net.forward(fd).cpu().numpy() - g_ref).max() < 2e-5
+    loss_ref, grad_ref = OL.loss_and_grad(p16, f32, t.astype(np.float32))
+    loss, grad = net.grad(fd, td)
+    assert abs(loss - loss_ref) < 1e-5 * max(1.0, loss_ref)
+    gr = flat(grad_ref)
+    assert np.abs(grad - gr).max() < 2e-4 * np.abs(gr).max()
+    # Adam moves the FP32 masters; the network then computes with their new FP16 roundings
+    before = net.params()
+    net.train(fd, td, 1, lr=1e-3)
+    after = net.params()
+    assert np.abs(after - before).max() > 0
+    keys = ("W1", "b1", "W2", "b2", "w3", "b3")
+    parts = np.split(after, np.cumsum([p[k].size for k in keys])[:-1])
+    pa = {k: v.reshape(p[k].shape).astype(np.float16).astype(np.float64) for k, v in zip(keys, parts)}
+    g_after, _ = OL.forward(pa, f32)
+    assert np.abs(net.forward(fd).cpu().numpy() - g_after).max() < 2e-5
+
+
+def test_width128_new_network_is_the_plain_preconditioner(wires):
+    m, O, S, P = wires
+    om = 2 * np.pi * np.array([1e8, 1e9, 5e9])
+    y = torch.from_numpy(synth.complex_gaussian(O.nl, 3, seed=14)).cuda()
+    z0 = api.pfft_precond_apply(P, y, om)
+    net = api.MLP(128, seed=3)
+    api.set_learned(P, net)
+    z1 = api.pfft_precond_apply(P, y, om)
+    api.set_learned(P, None)
+    assert torch.equal(z0, z1)
+
+
 def test_probe_target_matches_oracle(wires):
     m, O, S, P = wires
     w = 2 * np.pi * 1e9
