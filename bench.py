@@ -412,8 +412,7 @@ def batch_main(args, ws, dist=None, n_total=None):
         learned = {"train_geometries": ntrain, "held_out_geometries": len(held), "frequencies_hz": eval_f.tolist(),
                    "train_steps": 400, "train_seconds": t_train, "loss_first": float(losses[0]),
                    "loss_last": float(losses[-1]), **out,
-                   "chosen": "learned" if out["learned"]["iterations_sum"] < out["plain"]["iterations_sum"]
-                   else "plain (fallback)"}
+                   "chosen": judge_learned(out)}
     world = dist.get_world_size() if dist else 1
     if dist and dist.get_rank() != 0:
         return
@@ -432,6 +431,20 @@ def batch_main(args, ws, dist=None, n_total=None):
             "gmres_batched": gm, "learned_preconditioner": learned, "graph_stats": B.stats(), "clocks": clocks,
             "gpu_launches": launches}
     print(json.dumps(line))
+
+
+LEARNED_MIN_GAIN = 0.02
+
+
+def judge_learned(out):
+    """The plain preconditioner judges the learned one: the learned form is kept
+    only when it saves at least 2% of the GMRES iterations on the held-out set
+    and leaves no more solves unconverged; otherwise the plain P is the fallback."""
+    p, l = out["plain"], out["learned"]
+    gain = 1.0 - l["iterations_sum"] / max(1, p["iterations_sum"])
+    if gain >= LEARNED_MIN_GAIN and l.get("not_converged", 0) <= p.get("not_converged", 0):
+        return "learned"
+    return "plain (fallback: %.2f%% fewer iterations, below the %.0f%% bar)" % (100 * gain, 100 * LEARNED_MIN_GAIN)
 
 
 def learned_main(args):
@@ -515,8 +528,7 @@ def learned_main(args):
             "loss_first": float(losses[0]), "loss_last": float(losses[-1]), **out,
             "held_out_fewer_iterations": better, "held_out_more_iterations": worse,
             "Z_rel_learned_vs_plain": zdiff,
-            "chosen": "learned" if out["learned"]["iterations_sum"] < out["plain"]["iterations_sum"]
-            else "plain (fallback)"}
+            "chosen": judge_learned(out)}
     print(json.dumps(line))
 
 

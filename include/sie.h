@@ -360,6 +360,44 @@ typedef struct {
 int pfft_autotune(const sie_mesh *m, const sie_loops *l, const pfft_params *base, int32_t nrhs, double omega,
                   double tol, void *cuda_stream, pfft_params *best, sie_tune_report *rep);
 
+/* Kernel launch shapes of a plan's product (none changes the result beyond the
+ * rounding of the near-field path in the mixed form):
+ *   near      0: automatic (mixed form: tensor cores for an even right-hand-side
+ *                count of at least 96, else the CUDA-core gather);
+ *             1: tensor cores for any even count (mixed form);
+ *             2: the CUDA-core gather;
+ *   far_slab  right-hand sides per warp in the mixed far-field gather, 64 or 128
+ *             (0: 64);
+ *   proj_slab right-hand sides per warp in the projection, 64 or 128 (0: 128);
+ *   plane_gpc grids per CTA in the (y, z) plane kernel, 1..8 (0: up to 8, as
+ *             many as keep about four waves).
+ * Errors: SIE_ERR_ARG for a value outside these. */
+typedef struct {
+    int32_t near;
+    int32_t far_slab;
+    int32_t proj_slab;
+    int32_t plane_gpc;
+} sie_kernel_tuning;
+int pfft_plan_set_kernel_tuning(pfft_plan *p, const sie_kernel_tuning *t);   /* NULL: all automatic */
+int pfft_plan_get_kernel_tuning(const pfft_plan *p, sie_kernel_tuning *t);
+
+/* Kernel autotuning of a plan: its mixed loop-space product at nrhs right-hand
+ * sides and omega timed with CUDA events on cuda_stream (5 products after 2
+ * warm-ups) for every combination of near path (automatic and the other
+ * applicable one), far-field slab (64, 128), projection slab (64, 128) and
+ * plane grids per CTA (automatic, 2, 4); the fastest is set on the plan and
+ * returned in best; rep (may be NULL) gets every candidate and its time.
+ * Errors: those of pfft_matvec. */
+#define SIE_KTUNE_MAX 32
+typedef struct {
+    int32_t n_tried;
+    int32_t best;
+    sie_kernel_tuning cand[SIE_KTUNE_MAX];
+    double ms[SIE_KTUNE_MAX];
+} sie_kernel_tune_report;
+int pfft_autotune_kernels(pfft_plan *p, int32_t nrhs, double omega, void *cuda_stream, sie_kernel_tuning *best,
+                          sie_kernel_tune_report *rep);
+
 /* Learned correction of the preconditioner (Eq. Precond): D'_e = D_e (1 + g(f_e))
  * for the diagonal D_e of Z_b on each branch, g a network of six per-branch
  * features at the frequency (quarter decades of |Z_s| G_ee, c_L Lt_ee, their

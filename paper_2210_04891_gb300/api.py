@@ -259,6 +259,29 @@ def precond_info(plan: Plan):
     return dict(band_width=w.value, unknowns=u.value, blocks=b.value)
 
 
+def set_kernel_tuning(plan: Plan, near=0, far_slab=0, proj_slab=0, plane_gpc=0):
+    """pfft_plan_set_kernel_tuning (all 0: automatic)."""
+    t = N.KernelTuning(near=near, far_slab=far_slab, proj_slab=proj_slab, plane_gpc=plane_gpc)
+    check(lib().pfft_plan_set_kernel_tuning(plan.h, ctypes.byref(t)))
+
+
+def get_kernel_tuning(plan: Plan):
+    t = N.KernelTuning()
+    check(lib().pfft_plan_get_kernel_tuning(plan.h, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in N.KernelTuning._fields_}
+
+
+def autotune_kernels(plan: Plan, nrhs, omega, stream=None):
+    """pfft_autotune_kernels: (chosen tuning, [(candidate, ms)])."""
+    best = N.KernelTuning()
+    rep = N.KernelTuneReport()
+    check(lib().pfft_autotune_kernels(plan.h, int(nrhs), float(omega), _stream(stream), ctypes.byref(best),
+                                      ctypes.byref(rep)))
+    cands = [({f: getattr(rep.cand[i], f) for f, _ in N.KernelTuning._fields_}, rep.ms[i])
+             for i in range(rep.n_tried)]
+    return {f: getattr(best, f) for f, _ in N.KernelTuning._fields_}, cands
+
+
 def precond_set_method(plan: Plan, method):
     """pfft_precond_set_method: N.PC_AUTO, N.PC_BAND or N.PC_ND."""
     check(lib().pfft_precond_set_method(plan.h, int(method)))

@@ -729,9 +729,11 @@ template <typename T, int V, int J> struct Blocks {
         SIE_SLAB_DISPATCH(T, R, CALL);                                                    \
     } while (0)
 template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) {
+    if (p->kt.proj_slab == 64) SIE_SLAB_DISPATCH_NARROW(T, R, project(p, R, st));
     SIE_SLAB_DISPATCH(T, R, project(p, R, st));
 }
 int run_far_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
+    if (p->kt.far_slab == 128) SIE_SLAB_DISPATCH(float, R, far_gather(p, R, st));
     SIE_SLAB_DISPATCH_NARROW(float, R, far_gather(p, R, st));
 }
 template <typename T> int run_tri_gather(pfft_plan *p, int32_t R, cudaStream_t st) {
@@ -791,7 +793,7 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
         // complex near blocks per frequency: one CUDA-core gather (near + interpolation + y_T)
         tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
         rc = run_tri_gather_lossy<T>(p, R, st);
-    } else if (sizeof(T) == 4 && R % 2 == 0 && R >= kNearMmaMinRhs) {
+    } else if (sizeof(T) == 4 && R % 2 == 0 && p->kt.near != 2 && (R >= kNearMmaMinRhs || p->kt.near == 1)) {
         rc = run_far_gather(p, R, st);          // interpolation (step 3) on the CUDA cores
         if (rc) return rc;
         tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));

@@ -68,6 +68,7 @@ struct pfft_plan {
     std::vector<double> tri_cen;        // [nt][3] triangle centroids (host; the preconditioner's
                                         // nested-dissection ordering bisects by position)
     int32_t pc_method = 0;              // SIE_PC_AUTO, SIE_PC_BAND or SIE_PC_ND
+    sie_kernel_tuning kt{};             // kernel launch shapes (pfft_plan_set_kernel_tuning)
     std::vector<double> t_eff;          // per conductor: slab surface impedance thickness (0: classic)
     // per triangle (device)
     int32_t *d_tb = nullptr;            // [nt][3] branch of local edge k (-1: none)

@@ -19,7 +19,8 @@ int launch_plane(pfft_plan *p, float2 *spec, int32_t ngrids, int lgMx, cudaStrea
     // grids per CTA: up to 8 (the staged spectrum and twiddles serve each of
     // them) while keeping about four waves of two CTAs per SM
     const int64_t planes = int64_t(ngrids) * p->Mx;
-    const int gpc = int(std::max<int64_t>(1, std::min<int64_t>(8, planes / (8 * int64_t(nsm)))));
+    const int cap = p->kt.plane_gpc > 0 ? p->kt.plane_gpc : 8;
+    const int gpc = int(std::max<int64_t>(1, std::min<int64_t>(cap, planes / (8 * int64_t(nsm)))));
     const int64_t ctas = int64_t(p->Mx) * ((ngrids + gpc - 1) / gpc);
     kern<<<unsigned(ctas), plane::kThreads, G::kSmem, s>>>(spec, ngrids, gpc, lgMx, p->d_Hp32, p->d_tf32[1],
                                                            p->d_ti32[1], p->d_tf32[2], p->d_ti32[2]);

@@ -157,6 +157,53 @@ __device__ __forceinline__ void pdft(CP (&v)[16]) {
     }
 }
 
+// DFT of length N whose inputs v[N/2 .. N) are zero (the zero-padded first
+// stage of a forward transform), natural order in and out: the even outputs
+// are the half-length DFT of v[0 .. N/2), the odd ones that of v[j] W_N^j.
+template <int N>
+__device__ __forceinline__ void pdft_zpad(CP (&v)[16]) {
+    constexpr int H = N / 2;
+    if constexpr (N == 2) {
+        v[1] = v[0];
+    } else {
+        CP e[16], o[16];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            e[j] = v[j];
+            o[j] = j ? ptw16<false>(v[j], j * (16 / N)) : v[j];
+        }
+        pdft<H, false>(e);
+        pdft<H, false>(o);
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            v[2 * m] = e[m];
+            v[2 * m + 1] = o[m];
+        }
+    }
+}
+
+// The first N/2 outputs of the inverse DFT of length N (the cropped last
+// stage of an inverse transform): out[p] = E[p] + W_N^-p O[p] with E and O the
+// half-length inverse DFTs of the even and odd inputs.
+template <int N>
+__device__ __forceinline__ void pidft_half(CP (&v)[16]) {
+    constexpr int H = N / 2;
+    if constexpr (N == 2) {
+        v[0] = padd(v[0], v[1]);
+    } else {
+        CP e[16], o[16];
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            e[m] = v[2 * m];
+            o[m] = v[2 * m + 1];
+        }
+        pdft<H, true>(e);
+        pdft<H, true>(o);
+#pragma unroll
+        for (int p = 0; p < H; ++p) v[p] = padd(e[p], p ? ptw16<true>(o[p], p * (16 / N)) : o[p]);
+    }
+}
+
 __host__ __device__ constexpr int split_n1(int M) {
     int lg = 0;
     while ((1 << lg) < M) ++lg;
@@ -249,15 +296,11 @@ __device__ __forceinline__ void f1(const F1In<MY, MZ> &in, float *Pre, float *Pi
         const int j2 = it % A2, m = zrow<G::NYP, A2>(it / A2);
         CP v[16];
 #pragma unroll
-        for (int j1 = 0; j1 < A1; ++j1) {
-            if (j1 < H1) {
-                const float2 a = in.a[q][j1], b = in.b[q][j1];
-                v[j1] = CP{make_float2(a.x, b.x), make_float2(a.y, b.y)};
-            } else {
-                v[j1] = CP{dup2(0.f), dup2(0.f)};
-            }
+        for (int j1 = 0; j1 < H1; ++j1) {
+            const float2 a = in.a[q][j1], b = in.b[q][j1];
+            v[j1] = CP{make_float2(a.x, b.x), make_float2(a.y, b.y)};
         }
-        pdft<A1, false>(v);
+        pdft_zpad<A1>(v);   // inputs j1 >= A1 / 2 are the zero padding
 #pragma unroll
         for (int k1 = 0; k1 < A1; ++k1) {
             CP o = v[k1];
@@ -306,16 +349,12 @@ __device__ __forceinline__ void f3(const float *Qre, const float *Qim, float *Pr
         ycol<NC>(it, c, j2);
         CP v[16];
 #pragma unroll
-        for (int j1 = 0; j1 < B1; ++j1) {
-            if (j1 < H1) {
-                const int y = j2 + B2 * j1;
-                const int i0 = (y >> 1) * G::PZZ + 2 * c + (y & 1), i1 = i0 + MZ;   // kz = 2c, 2c + 1
-                v[j1] = CP{make_float2(Qre[i0], Qre[i1]), make_float2(Qim[i0], Qim[i1])};
-            } else {
-                v[j1] = CP{dup2(0.f), dup2(0.f)};
-            }
+        for (int j1 = 0; j1 < H1; ++j1) {
+            const int y = j2 + B2 * j1;
+            const int i0 = (y >> 1) * G::PZZ + 2 * c + (y & 1), i1 = i0 + MZ;   // kz = 2c, 2c + 1
+            v[j1] = CP{make_float2(Qre[i0], Qre[i1]), make_float2(Qim[i0], Qim[i1])};
         }
-        pdft<B1, false>(v);
+        pdft_zpad<B1>(v);   // rows y >= N_y are the zero padding
 #pragma unroll
         for (int k1 = 0; k1 < B1; ++k1) {
             CP o = v[k1];
@@ -399,7 +438,7 @@ __device__ __forceinline__ void i2(const float *Pre, const float *Pim, float *Qr
             const int i = (p2 * B1 + k1) * MZ + 2 * c;
             v[k1] = CP{ld2(Pre, i), ld2(Pim, i)};
         }
-        pdft<B1, true>(v);
+        pidft_half<B1>(v);   // only rows y < N_y are kept
 #pragma unroll
         for (int p1 = 0; p1 < H1; ++p1) {
             const int y = p2 + B2 * p1;
@@ -454,7 +493,7 @@ __device__ __forceinline__ void i4(const float *Pre, const float *Pim, float2 *_
             const int i = m * G::PZZ + 2 * (p2 + A2 * k1);
             v[k1] = CP{ld2(Pre, i), ld2(Pim, i)};
         }
-        pdft<A1, true>(v);
+        pidft_half<A1>(v);   // only z < N_z is kept
         float2 *r0 = dst + (2 * m) * G::Nz + p2, *r1 = r0 + G::Nz;
 #pragma unroll
         for (int p1 = 0; p1 < H1; ++p1) {

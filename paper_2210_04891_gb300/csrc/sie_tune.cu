@@ -153,3 +153,83 @@ extern "C" int pfft_autotune(const sie_mesh *m, const sie_loops *l, const pfft_p
     if (rep) *rep = r;
     return done(SIE_OK);
 }
+
+extern "C" int pfft_plan_set_kernel_tuning(pfft_plan *p, const sie_kernel_tuning *t) {
+    if (!p) return fail(SIE_ERR_ARG, "pfft_plan_set_kernel_tuning: NULL plan");
+    sie_kernel_tuning k{};
+    if (t) k = *t;
+    if (k.near < 0 || k.near > 2 || (k.far_slab != 0 && k.far_slab != 64 && k.far_slab != 128) ||
+        (k.proj_slab != 0 && k.proj_slab != 64 && k.proj_slab != 128) || k.plane_gpc < 0 || k.plane_gpc > 8)
+        return fail(SIE_ERR_ARG, "pfft_plan_set_kernel_tuning: value out of range");
+    p->kt = k;
+    return SIE_OK;
+}
+
+extern "C" int pfft_plan_get_kernel_tuning(const pfft_plan *p, sie_kernel_tuning *t) {
+    if (!p || !t) return fail(SIE_ERR_ARG, "pfft_plan_get_kernel_tuning: NULL argument");
+    *t = p->kt;
+    return SIE_OK;
+}
+
+extern "C" int pfft_autotune_kernels(pfft_plan *p, int32_t nrhs, double omega, void *cuda_stream,
+                                     sie_kernel_tuning *best, sie_kernel_tune_report *rep) {
+    if (!p || nrhs < 1 || !(omega > 0.0) || !std::isfinite(omega))
+        return fail(SIE_ERR_ARG, "pfft_autotune_kernels: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the near paths that apply at this count: automatic, and the other one when the
+    // count is even (the tensor-core path needs an even count)
+    std::vector<int32_t> nears{0};
+    if (nrhs % 2 == 0) nears.push_back(nrhs >= 96 ? 2 : 1);
+    std::vector<sie_kernel_tuning> cand;
+    for (int32_t nr : nears)
+        for (int32_t fs : {64, 128})
+            for (int32_t ps : {64, 128})
+                for (int32_t g : {0, 2, 4}) cand.push_back(sie_kernel_tuning{nr, fs, ps, g});
+    if (int(cand.size()) > SIE_KTUNE_MAX) cand.resize(SIE_KTUNE_MAX);
+    const int64_t nl = p->nl;
+    const size_t vbytes = size_t(nrhs) * nl * sizeof(double2);
+    std::vector<double2> hx(size_t(nrhs) * nl);
+    for (size_t i = 0; i < hx.size(); ++i) hx[i] = make_double2(uniform(2 * i + 7), uniform(2 * i + 8));
+    std::vector<double> om(nrhs, omega);
+    TuneBuf x, y;
+    SIE_CUDA(cudaMalloc(&x.p, vbytes));
+    SIE_CUDA(cudaMalloc(&y.p, vbytes));
+    SIE_CUDA(cudaMemcpy(x.p, hx.data(), vbytes, cudaMemcpyHostToDevice));
+    const sie_kernel_tuning keep = p->kt;
+    sie_kernel_tune_report r{};
+    r.n_tried = int32_t(cand.size());
+    r.best = -1;
+    cudaEvent_t e0, e1;
+    SIE_CUDA(cudaEventCreate(&e0));
+    SIE_CUDA(cudaEventCreate(&e1));
+    auto done = [&](int code) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (code) p->kt = keep;
+        return code;
+    };
+    for (size_t c = 0; c < cand.size(); ++c) {
+        p->kt = cand[c];
+        r.cand[c] = cand[c];
+        int rc = SIE_OK;
+        for (int w = 0; w < 2 && !rc; ++w)
+            rc = pfft_matvec(p, x.p, y.p, nrhs, om.data(), SIE_SPACE_LOOP, SIE_PREC_MIXED, cuda_stream);
+        float ms = 0.f;
+        if (!rc) {
+            constexpr int kReps = 5;
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < kReps && !rc; ++k)
+                rc = pfft_matvec(p, x.p, y.p, nrhs, om.data(), SIE_SPACE_LOOP, SIE_PREC_MIXED, cuda_stream);
+            cudaEventRecord(e1, st);
+            if (!rc && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            ms /= kReps;
+        }
+        if (rc) return done(rc);
+        r.ms[c] = ms;
+        if (r.best < 0 || r.ms[c] < r.ms[r.best]) r.best = int32_t(c);
+    }
+    p->kt = cand[r.best];
+    if (best) *best = p->kt;
+    if (rep) *rep = r;
+    return done(SIE_OK);
+}

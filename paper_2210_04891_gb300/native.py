@@ -26,7 +26,8 @@ EXPORTS = ["sie_mesh_load", "sie_mesh_load_file", "sie_mesh_destroy", "loop_basi
            "pfft_plan_info", "pfft_plan_export", "pfft_convolve", "pfft_convolve_lossy", "pfft_convolve_noalloc", "pfft_profile_enable", "pfft_profile_read",
            "pfft_plan_launches", "pfft_plan_set_surface_model", "sie_postprocess", "sie_batch_create", "sie_batch_destroy",
            "sie_batch_matvec", "sie_batch_stats", "sie_batch_solve", "sie_batch_solve_graph", "pfft_precond_info",
-           "pfft_precond_set_method", "pfft_precond_nd_info", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
+           "pfft_precond_set_method", "pfft_precond_nd_info",
+           "pfft_plan_set_kernel_tuning", "pfft_plan_get_kernel_tuning", "pfft_autotune_kernels", "pfft_autotune", "sie_mlp_create", "sie_mlp_destroy",
            "sie_mlp_param_count", "sie_mlp_get_params", "sie_mlp_set_params", "sie_mlp_forward", "sie_mlp_grad",
            "sie_mlp_train", "pfft_branch_features", "pfft_branch_probe_target", "pfft_plan_set_learned",
            "sie_selftest_bounded_wait", "sie_last_error"]
@@ -51,6 +52,16 @@ class PfftParams(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32 * 3), ("order", ctypes.c_int32), ("near_factor", ctypes.c_double),
                 ("near_min_diam", ctypes.c_double), ("n_touch", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("h0", ctypes.c_double)]
+
+
+class KernelTuning(ctypes.Structure):
+    _fields_ = [("near", ctypes.c_int32), ("far_slab", ctypes.c_int32), ("proj_slab", ctypes.c_int32),
+                ("plane_gpc", ctypes.c_int32)]
+
+
+class KernelTuneReport(ctypes.Structure):
+    _fields_ = [("n_tried", ctypes.c_int32), ("best", ctypes.c_int32), ("cand", KernelTuning * 32),
+                ("ms", ctypes.c_double * 32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -111,6 +122,9 @@ def lib():
     L.sie_batch_create.argtypes = [P, I32, PP]
     L.pfft_precond_info.argtypes = [P, P, P, P]
     L.pfft_precond_set_method.argtypes = [P, I32]
+    L.pfft_plan_set_kernel_tuning.argtypes = [P, P]
+    L.pfft_plan_get_kernel_tuning.argtypes = [P, P]
+    L.pfft_autotune_kernels.argtypes = [P, I32, D, P, P, P]
     L.pfft_precond_nd_info.argtypes = [P, P, P, P, P, P]
     L.sie_mlp_create.argtypes = [I32, ctypes.c_uint64, PP]
     L.sie_mlp_destroy.argtypes = [P]

@@ -56,3 +56,30 @@ def test_autotune_without_an_accurate_candidate(geometry):
         assert tuple(best["grid"]) == rep["grids"][fine] and best["near_factor"] == 1.5 * BASE["near_factor"]
     with pytest.raises(SieError):
         api.autotune(M, L, BASE, nrhs=0, omega=1.0, tol=1e-3)
+
+
+def test_kernel_tuning_variants_and_autotune():
+    # the launch shapes change no result beyond the near path's rounding; the kernel
+    # autotuner times every applicable combination and leaves the fastest set
+    from paper_2210_04891_gb300 import SPACE_LOOP, PREC_MIXED
+    m = synth.tiny_wires()
+    M = api.Mesh.from_synth(m)
+    L = api.Loops(M, m.ports)
+    P = api.Plan(M, L, dict(grid=(16, 8, 4), order=3, near_factor=4.0, near_min_diam=2.0, n_touch=8, h0=0.0))
+    R = 40
+    x = torch.from_numpy(synth.complex_gaussian(L.nl, R, seed=3)).cuda()
+    om = 2 * np.pi * np.logspace(8, 10, R)
+    ref = api.pfft_matvec(P, x, om, SPACE_LOOP, PREC_MIXED)
+    for fs in (64, 128):
+        for ps in (64, 128):
+            for g in (0, 1, 2, 4):
+                api.set_kernel_tuning(P, 0, fs, ps, g)
+                assert torch.equal(api.pfft_matvec(P, x, om, SPACE_LOOP, PREC_MIXED), ref), (fs, ps, g)
+    api.set_kernel_tuning(P, near=1)   # tensor cores at 40 right-hand sides
+    y = api.pfft_matvec(P, x, om, SPACE_LOOP, PREC_MIXED)
+    assert (torch.linalg.norm(y - ref, dim=1) / torch.linalg.norm(ref, dim=1)).max().item() < 1e-5
+    best, cands = api.autotune_kernels(P, R, om[0])
+    assert len(cands) == 24 and api.get_kernel_tuning(P) == best
+    assert min(ms for _, ms in cands) == [ms for c, ms in cands if c == best][0]
+    with pytest.raises(Exception):
+        api.set_kernel_tuning(P, plane_gpc=9)
