@@ -48,7 +48,7 @@ enum {
 };
 
 enum { SIE_SPACE_LOOP = 0, SIE_SPACE_BRANCH = 1 };
-enum { SIE_PREC_FP64 = 0, SIE_PREC_MIXED = 1 };
+enum { SIE_PREC_FP64 = 0, SIE_PREC_MIXED = 1, SIE_PREC_DF = 2 };
 enum { SIE_KERNEL_STATIC = 0, SIE_KERNEL_LOSSY = 1 };
 
 typedef struct sie_mesh sie_mesh;
@@ -99,7 +99,10 @@ typedef struct {
     int32_t refine;        /* with SIE_PREC_MIXED: 1 = iterative refinement:
                               every restart residual P^-1 (b - Z x) (and the
                               convergence test) in FP64, the Arnoldi cycles in
-                              the mixed form; 0 = all in the mixed form        */
+                              the mixed form; 2 = the same with the residual
+                              products b - Z x in double-float (SIE_PREC_DF;
+                              P^-1 and the norms stay FP64); 0 = all in the
+                              mixed form                                       */
 } sie_solve_opts;
 
 typedef struct {
@@ -188,7 +191,14 @@ int pfft_plan_set_surface_model(pfft_plan *p, const double *t_eff, int32_t ncond
  * CUDA cores) and the loop/branch maps (prefix sums, branch differences, the
  * Z_s/c_L combination)
  * in double-float (FP32 pairs, about 48 significant bits); y is complex128 in
- * both.  x and y must not overlap.  Scratch is
+ * both.  SIE_PREC_DF computes every step in double-float on the FP32 pipes
+ * (block records, twiddles and the kernel spectrum rounded once from FP64 to
+ * double-float pairs, sums and products by the error-free two-sum and FMA
+ * two-product): an FP64-class product (agreeing with SIE_PREC_FP64 to about
+ * 1e-12 relative) at a fraction of its cost on a GPU whose FP64 rate is a small
+ * share of its FP32 rate; static kernel only (SIE_ERR_ARG for a lossy plan);
+ * the first call builds the double-float tables (about the size of the FP64
+ * block records) on the plan's stream.  x and y must not overlap.  Scratch is
  * plan-owned and grown on demand (SIE_ERR_OOM if that fails).
  *
  * Plans created with pfft_params.kernel = SIE_KERNEL_LOSSY use the

@@ -515,6 +515,10 @@ class Batch:
 
 def sie_solve(plan: Plan, freqs, ports=None, tol=1e-6, restart=200, max_iter=2000, precond=1,
               prec=N.PREC_FP64, refine=False):
+    """Port impedances Z[f] by preconditioned loop-basis GMRES (Eq. LoopWithP).
+    refine (with prec = PREC_MIXED): False / REFINE_OFF all mixed, True / REFINE_FP64
+    iterative refinement with FP64 residual products, REFINE_DF the same with
+    double-float residual products."""
     f = np.ascontiguousarray(freqs, np.float64)
     pr = np.arange(plan.np, dtype=np.int32) if ports is None else np.ascontiguousarray(ports, np.int32)
     o = N.SolveOpts(tol=tol, restart=restart, max_iter=max_iter, precond=precond, prec=prec, refine=int(refine))

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["sie_plan.cu", "sie_pfft.cu", "sie_near_mma.cu", "sie_solve.cu", "sie_noalloc.cu", "sie_plane.cu", "sie_batch.cu", "sie_tune.cu", "sie_learned.cu",
-      "sie_lossy.cu", "sie_nd.cu"]
+      "sie_lossy.cu", "sie_nd.cu", "sie_df.cu"]
 CPP = ["sie_host.cpp"]
 
 

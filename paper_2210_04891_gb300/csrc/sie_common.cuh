@@ -5,13 +5,20 @@
 #include <cstdint>
 #include <string>
 
+#include "sie_dd.cuh"
 #include "sie_internal.h"
 
 namespace sie {
 
+// complex double-float: 16 bytes like complex128
+struct alignas(16) cdf {
+    df x, y;
+};
+
 template <typename T> struct cpx;
 template <> struct cpx<float> { using type = float2; };
 template <> struct cpx<double> { using type = double2; };
+template <> struct cpx<df> { using type = cdf; };
 template <typename T> using C = typename cpx<T>::type;
 
 template <typename T> __host__ __device__ __forceinline__ C<T> mk(T re, T im) { C<T> z; z.x = re; z.y = im; return z; }
@@ -43,7 +50,13 @@ template <> struct alignas(16) Rec<double> {
     double b[9];
     int64_t col;
 };
-static_assert(sizeof(Rec<float>) == 48 && sizeof(Rec<double>) == 80, "packed block records");
+template <> struct alignas(16) Rec<df> {
+    df b[9];
+    int32_t col;
+    int32_t pad;
+};
+static_assert(sizeof(Rec<float>) == 48 && sizeof(Rec<double>) == 80 && sizeof(Rec<df>) == 80,
+              "packed block records");
 
 template <typename T> __device__ __forceinline__ int64_t load_rec(const Rec<T> *__restrict__ r, T (&b)[9]);
 template <> __device__ __forceinline__ int64_t load_rec<float>(const Rec<float> *__restrict__ r, float (&b)[9]) {
@@ -65,6 +78,19 @@ template <> __device__ __forceinline__ int64_t load_rec<double>(const Rec<double
     const double2 u = __ldg(v + 4);
     b[8] = u.x;
     return __double_as_longlong(u.y);
+}
+
+template <> __device__ __forceinline__ int64_t load_rec<df>(const Rec<df> *__restrict__ r, df (&b)[9]) {
+    const float4 *v = reinterpret_cast<const float4 *>(r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 u = __ldg(v + i);
+        b[2 * i] = df(u.x, u.y);
+        b[2 * i + 1] = df(u.z, u.w);
+    }
+    const float4 u = __ldg(v + 4);
+    b[8] = df(u.x, u.y);
+    return __float_as_int(u.z);
 }
 
 inline bool cuda_ok(cudaError_t e, const char *what) {

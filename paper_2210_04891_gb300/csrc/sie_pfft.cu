@@ -45,8 +45,11 @@ template <typename V> __device__ __forceinline__ V shfl_up(V v, int d) {
 }
 
 // Elements of the loop/branch maps after the field computation: complex128 in
-// the FP64 form, double-float float4 (sie_dd.cuh) in the mixed form.
-template <typename T> using TourE = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+// the FP64 form, double-float float4 (sie_dd.cuh) in the mixed and double-float forms.
+template <typename T> using TourE = typename std::conditional<std::is_same<T, double>::value, double2, float4>::type;
+template <typename T> constexpr bool is_f32 = std::is_same<T, float>::value;
+template <typename T> constexpr bool is_f64 = std::is_same<T, double>::value;
+template <typename T> constexpr bool is_df = std::is_same<T, df>::value;
 
 __device__ __forceinline__ double2 eadd(double2 a, double2 b) { return cadd(a, b); }
 __device__ __forceinline__ float4 eadd(float4 a, float4 b) {
@@ -67,6 +70,11 @@ __device__ __forceinline__ void eset(float4 &e, float4 v) { e = v; }
 __device__ __forceinline__ double2 to_c(double2 v, double2) { return v; }
 __device__ __forceinline__ float2 to_c(double2 v, float2) { return make_float2(float(v.x), float(v.y)); }
 __device__ __forceinline__ float2 to_c(float4 e, float2) { return make_float2(e.x + e.y, e.z + e.w); }
+__device__ __forceinline__ cdf to_c(double2 v, cdf) {
+    const DD a = dd_from(v.x), b = dd_from(v.y);
+    return cdf{df(a.hi, a.lo), df(b.hi, b.lo)};
+}
+__device__ __forceinline__ cdf to_c(float4 e, cdf) { return cdf{df(e.x, e.y), df(e.z, e.w)}; }
 __device__ __forceinline__ float4 shfl_up(float4 v, int d) {
     v.x = __shfl_up_sync(0xffffffffu, v.x, d);
     v.y = __shfl_up_sync(0xffffffffu, v.y, d);
@@ -214,10 +222,13 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const Tou
 // V complex values at p (16-byte aligned when V = 2).
 template <typename T, int V> __device__ __forceinline__ void ldv(const C<T> *p, C<T> (&v)[V]) {
     if constexpr (V == 2) {
-        static_assert(sizeof(T) == 4, "two complex per load only in FP32");
+        static_assert(is_f32<T>, "two complex per load only in FP32");
         const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
         v[0] = make_float2(u.x, u.y);
         v[1] = make_float2(u.z, u.w);
+    } else if constexpr (is_df<T>) {
+        const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = cdf{df(u.x, u.y), df(u.z, u.w)};
     } else {
         v[0] = __ldg(p);
     }
@@ -353,7 +364,35 @@ __device__ __forceinline__ void tri_epilogue(const C<T> (&acc)[3][J][V], int64_t
                                              const float2 *__restrict__ coef_dd, int ncond, int64_t nt,
                                              TourE<T> *__restrict__ y_tri) {
     const int cd = cond[t];
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (is_df<T>) {
+        // double-float product: Gram term and Eq. Zb in double-float like the field
+        DD G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) G[i] = dd_from(__ldg(gram + 9 * t + i));
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int32_t r = rl + 32 * V * j + v;
+                if (r >= R) continue;
+                const float2 *cf = coef_dd + int64_t(r) * (2 * ncond + 1);
+                const float2 zr = cf[2 * cd], zi = cf[2 * cd + 1], cl = cf[2 * ncond];
+                cdf c[3];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) c[l] = cT[(t * 3 + l) * R + r];
+                float4 *out = y_tri + (int64_t(r) * nt + t) * 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    DD gr = dd_mul(G[3 * k], to_dd(c[0].x)), gi = dd_mul(G[3 * k], to_dd(c[0].y));
+#pragma unroll
+                    for (int l = 1; l < 3; ++l) {
+                        gr = dd_add(gr, dd_mul(G[3 * k + l], to_dd(c[l].x)));
+                        gi = dd_add(gi, dd_mul(G[3 * k + l], to_dd(c[l].y)));
+                    }
+                    out[k] = dd_zb_df(zr, zi, cl, gr, gi, to_dd(acc[k][j][v].x), to_dd(acc[k][j][v].y));
+                }
+            }
+    } else if constexpr (is_f32<T>) {
         // mixed form: Gram term in FP32 like the field, Eq. Zb in double-float
         float G[9];
 #pragma unroll
@@ -611,7 +650,9 @@ namespace sie {
 // buffer, so alternating precisions (iterative refinement) never reallocates.
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
     Scratch &s = p->scr;
-    const bool mixed = prec != SIE_PREC_FP64;
+    // complex values of the field steps: complex64 in the mixed form, 16 bytes
+    // (complex128 or complex double-float) otherwise
+    const bool mixed = prec == SIE_PREC_MIXED;
     const int want_cs = mixed ? int(sizeof(float2)) : int(sizeof(double2));
     if (s.cap_rhs >= nrhs && s.cs >= want_cs && (!mixed || s.ffar)) return SIE_OK;
     const int64_t R = std::max<int64_t>({int64_t(nrhs), int64_t(s.cap_rhs), 1});
@@ -654,13 +695,19 @@ int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec) {
 template <typename T, int V, int J> struct Blocks {
     static constexpr int SLAB = 32 * V * J;
     static const Rec<T> *pn(const pfft_plan *p) {
-        if constexpr (sizeof(T) == 8) return p->d_pn_rec64; else return p->d_pn_rec32;
+        if constexpr (is_df<T>) return p->d_pn_recdf;
+        else if constexpr (is_f64<T>) return p->d_pn_rec64;
+        else return p->d_pn_rec32;
     }
     static const Rec<T> *pt(const pfft_plan *p) {
-        if constexpr (sizeof(T) == 8) return p->d_pt_rec64; else return p->d_pt_rec32;
+        if constexpr (is_df<T>) return p->d_pt_recdf;
+        else if constexpr (is_f64<T>) return p->d_pt_rec64;
+        else return p->d_pt_rec32;
     }
     static const Rec<T> *nr(const pfft_plan *p) {
-        if constexpr (sizeof(T) == 8) return p->d_near_rec64; else return p->d_near_rec32;
+        if constexpr (is_df<T>) return p->d_near_recdf;
+        else if constexpr (is_f64<T>) return p->d_near_rec64;
+        else return p->d_near_rec32;
     }
     static int project(pfft_plan *p, int32_t R, cudaStream_t st) {
         const dim3 grid(unsigned((p->Ng + kProjNodes - 1) / kProjNodes), unsigned((R + SLAB - 1) / SLAB));
@@ -678,10 +725,10 @@ template <typename T, int V, int J> struct Blocks {
         return SIE_OK;
     }
     static int tri_gather_lossy(pfft_plan *p, int32_t R, cudaStream_t st) {
-        static_assert(V == 1, "one right-hand side per lane and load");
+        static_assert(V == 1 && !is_df<T>, "one right-hand side per lane and load; FP64 or mixed");
         const int32_t nslab = (R + SLAB - 1) / SLAB;
         const int64_t warps = p->nt * nslab;
-        const int prec = sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED;
+        const int prec = is_f64<T> ? SIE_PREC_FP64 : SIE_PREC_MIXED;
         k_tri_gather_lossy<T, J><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
             p->d_near_ptr, p->d_near_col, reinterpret_cast<const C<T> *const *>(lossy_ltab(p, prec)),
             lossy_rslot(p), p->d_pt_ptr, pt(p), (const C<T> *)p->scr.cT, (const C<T> *)p->scr.phiT, p->d_gram,
@@ -706,7 +753,10 @@ template <typename T, int V, int J> struct Blocks {
 // loads per lane; the smallest slab that covers R keeps every lane busy.
 #define SIE_SLAB_DISPATCH(T, R, CALL)                                                     \
     do {                                                                                 \
-        if constexpr (sizeof(T) == 8) {                                                   \
+        if constexpr (is_df<T>) {                                                         \
+            if ((R) <= 32) return Blocks<df, 1, 1>::CALL;                                 \
+            return Blocks<df, 1, 2>::CALL;                                                \
+        } else if constexpr (is_f64<T>) {                                                 \
             if ((R) <= 32) return Blocks<double, 1, 1>::CALL;                             \
             return Blocks<double, 1, 2>::CALL;                                            \
         } else {                                                                          \
@@ -723,7 +773,7 @@ template <typename T, int V, int J> struct Blocks {
 // wide).
 #define SIE_SLAB_DISPATCH_NARROW(T, R, CALL)                                              \
     do {                                                                                 \
-        if constexpr (sizeof(T) == 4) {                                                   \
+        if constexpr (is_f32<T>) {                                                        \
             if ((R) > 32) return (R) % 2 == 0 ? Blocks<float, 2, 1>::CALL : Blocks<float, 1, 2>::CALL; \
         }                                                                                 \
         SIE_SLAB_DISPATCH(T, R, CALL);                                                    \
@@ -773,8 +823,8 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     int rc = run_project<T>(p, R, st);
     if (rc) return rc;
     tm.reset();
-    const int prec = sizeof(T) == 8 ? SIE_PREC_FP64 : SIE_PREC_MIXED;
-    const bool lossy = p->params.kernel == SIE_KERNEL_LOSSY;
+    const int prec = is_df<T> ? SIE_PREC_DF : is_f64<T> ? SIE_PREC_FP64 : SIE_PREC_MIXED;
+    const bool lossy = !is_df<T> && p->params.kernel == SIE_KERNEL_LOSSY;
     rc = fft_conv(p, s.grid, s.spec, R, prec, st, lossy ? lossy_sel(p, prec) : nullptr);
     if (rc) return rc;
     tm.reset(new StageTimer(p, SIE_STAGE_INTERP, st));
@@ -789,11 +839,14 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     // slab costs the same however few of its columns are used, so below about
     // three quarters of a slab the CUDA-core gather is faster); otherwise one
     // CUDA-core gather
-    if (lossy) {
+    if constexpr (is_df<T>) {
+        tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
+        rc = run_tri_gather<T>(p, R, st);       // near + interpolation + y_T in one gather
+    } else if (lossy) {
         // complex near blocks per frequency: one CUDA-core gather (near + interpolation + y_T)
         tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
         rc = run_tri_gather_lossy<T>(p, R, st);
-    } else if (sizeof(T) == 4 && R % 2 == 0 && p->kt.near != 2 && (R >= kNearMmaMinRhs || p->kt.near == 1)) {
+    } else if (is_f32<T> && R % 2 == 0 && p->kt.near != 2 && (R >= kNearMmaMinRhs || p->kt.near == 1)) {
         rc = run_far_gather(p, R, st);          // interpolation (step 3) on the CUDA cores
         if (rc) return rc;
         tm.reset(new StageTimer(p, SIE_STAGE_NEAR, st));
@@ -885,12 +938,18 @@ int matvec_async(pfft_plan *p, const void *x, void *y, int32_t nrhs, const doubl
     rc = upload_coef(p, omega, nrhs, st);
     if (rc) return rc;
     if (p->params.kernel == SIE_KERNEL_LOSSY && (rc = lossy_prepare(p, omega, nrhs, st))) return rc;
+    if (prec == SIE_PREC_DF && (rc = df_prepare(p, st))) return rc;
     return matvec_launch(p, x, y, nrhs, space, prec, st);
 }
 
 int matvec_launch(pfft_plan *p, const void *x, void *y, int32_t nrhs, int space, int prec, cudaStream_t st) {
     if (prec == SIE_PREC_FP64)
         return matvec_t<double>(p, (const double2 *)x, (double2 *)y, nrhs, space, st);
+    if (prec == SIE_PREC_DF) {
+        if (!p->df_ready || p->params.kernel != SIE_KERNEL_STATIC)
+            return fail(SIE_ERR_ARG, "double-float product: static kernel plans only, tables built first");
+        return matvec_t<df>(p, (const double2 *)x, (double2 *)y, nrhs, space, st);
+    }
     return matvec_t<float>(p, (const double2 *)x, (double2 *)y, nrhs, space, st);
 }
 
@@ -901,7 +960,10 @@ extern "C" int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, c
     if (!p || !x || !y || !omega) return fail(SIE_ERR_ARG, "pfft_matvec: NULL argument");
     if (nrhs < 1) return fail(SIE_ERR_ARG, "pfft_matvec: nrhs must be >= 1");
     if (space != SIE_SPACE_LOOP && space != SIE_SPACE_BRANCH) return fail(SIE_ERR_ARG, "pfft_matvec: bad space");
-    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "pfft_matvec: bad precision");
+    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED && prec != SIE_PREC_DF)
+        return fail(SIE_ERR_ARG, "pfft_matvec: bad precision");
+    if (prec == SIE_PREC_DF && p->params.kernel != SIE_KERNEL_STATIC)
+        return fail(SIE_ERR_ARG, "pfft_matvec: the double-float product takes the static kernel only");
     const int64_t n = space == SIE_SPACE_LOOP ? p->nl : p->nb;
     const char *xb = (const char *)x, *yb = (const char *)y;
     const size_t bytes = size_t(nrhs) * n * sizeof(double2);

@@ -13,6 +13,7 @@
 // n_touch^2 for pairs sharing a vertex, Radon 7 otherwise) and the grid's own
 // contribution (I H B)_pair, L_d = L_direct - (I H B)_pair (Eq. Lb).
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -477,6 +478,11 @@ template <> struct Tables<float> {
     static const float *Hp(const pfft_plan *p) { return p->d_Hp32; }
     static const float2 *Hl(const pfft_plan *p) { return p->d_Hl32; }
 };
+template <> struct Tables<df> {   // the double-float product: static kernel only
+    static const cdf *tf(const pfft_plan *p, int a) { return p->d_tfdf[a]; }
+    static const cdf *ti(const pfft_plan *p, int a) { return p->d_tidf[a]; }
+    static const df *Hp(const pfft_plan *p) { return p->d_Hpdf; }
+};
 
 // Pencils along axis `axis` (0: x, ncols = N_y N_z per grid; 1: y of the large
 // plane route, ncols = N_z per (grid, x-frequency)) for `nbatch` batches.
@@ -581,7 +587,9 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
     }
     {
         StageTimer tm(p, SIE_STAGE_FFT_YZ, s);
-        if (sel && sel->tab)   // one lossy spectrum per grid
+        if constexpr (std::is_same<T, df>::value)
+            rc = launch_yzc<T>(p, spec, ngrids, Tb::Hp(p), s);
+        else if (sel && sel->tab)   // one lossy spectrum per grid
             rc = launch_yzc<T, C<T>>(p, spec, ngrids, nullptr, s, reinterpret_cast<const C<T> *const *>(sel->tab),
                                      sel->gslot);
         else
@@ -598,6 +606,10 @@ int fft_conv_t(pfft_plan *p, C<T> *grid, C<T> *spec, int32_t ngrids, cudaStream_
 int fft_conv_n(pfft_plan *p, void *grid, void *spec, int32_t ngrids, int prec, cudaStream_t s, bool lossy,
                const SpecSel *sel) {
     if (prec == SIE_PREC_FP64) return fft_conv_t<double>(p, (double2 *)grid, (double2 *)spec, ngrids, s, lossy, sel);
+    if (prec == SIE_PREC_DF) {
+        if (lossy || !p->df_ready) return fail(SIE_ERR_ARG, "double-float convolution: static kernel, tables built");
+        return fft_conv_t<df>(p, (cdf *)grid, (cdf *)spec, ngrids, s, false, nullptr);
+    }
     return fft_conv_t<float>(p, (float2 *)grid, (float2 *)spec, ngrids, s, lossy, sel);
 }
 

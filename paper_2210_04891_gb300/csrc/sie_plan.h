@@ -118,6 +118,12 @@ struct pfft_plan {
     // the same spectrum with kx outermost: [Mx/2+1][My/2+1][Mz/2+1]
     double *d_Hp64 = nullptr;
     float *d_Hp32 = nullptr;
+    // double-float copies for the SIE_PREC_DF product, built on its first use
+    // (df_prepare): block records, four-step twiddles, kernel spectrum
+    bool df_ready = false;
+    sie::Rec<sie::df> *d_pn_recdf = nullptr, *d_pt_recdf = nullptr, *d_near_recdf = nullptr;
+    sie::cdf *d_tfdf[3] = {nullptr, nullptr, nullptr}, *d_tidf[3] = {nullptr, nullptr, nullptr};
+    sie::df *d_Hpdf = nullptr;
     // lossy kernel exp(-jkR)/R: complex spectrum of the last (omega, sigma), same layout
     // (pfft_convolve_lossy)
     double lossy_omega = -1.0, lossy_sigma = -1.0;
@@ -185,6 +191,9 @@ int plan_alloc(pfft_plan *p, void **ptr, size_t bytes);
 void plan_free(pfft_plan *p, void *ptr);
 void plan_free_precond(pfft_plan *p);
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);
+// Builds the double-float tables of the SIE_PREC_DF product from the FP64 ones
+// on stream st (once per plan; no-op afterwards).
+int df_prepare(pfft_plan *p, cudaStream_t st);
 // Surface impedance of conductor c at angular frequency w (Eq. ImpedanceOp):
 // classic (1 + j) sqrt(w mu0 / (2 sigma)), or with an effective thickness
 // t > 0 the impedance of one face of a slab of thickness t,

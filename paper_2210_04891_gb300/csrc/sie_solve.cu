@@ -1439,6 +1439,7 @@ struct GmresRun {
     std::vector<int32_t> ports;
     bool use_pc = true, refine = false;
     int outer_prec = SIE_PREC_FP64;
+    int resid_prec = SIE_PREC_FP64;   // the refinement's residual products: FP64 or double-float
     // device
     double2 *V = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *t = nullptr, *dh = nullptr, *dh2 = nullptr,
             *dhn = nullptr, *dy = nullptr, *rv = nullptr, *dvec = nullptr, *vin = nullptr;
@@ -1487,9 +1488,10 @@ struct GmresRun {
         SIE_CUDA(cudaStreamSynchronize(st));
         return SIE_OK;
     }
-    // residual r = b - Z x with the FP64 product
+    // residual r = b - Z x with the FP64-class product (FP64, or double-float on
+    // the FP32 pipes with opts.refine = 2)
     int residual_fp64() {
-        int rc = matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, SIE_PREC_FP64, st);
+        int rc = matvec_async(p, x, t, R, om.data(), SIE_SPACE_LOOP, resid_prec, st);
         if (rc) return rc;
         k_sub<<<nblk_(int64_t(R) * n), 256, 0, st>>>(b, t, rv, int64_t(R) * n);
         SIE_LAUNCH_CHECK(p);
@@ -1510,6 +1512,7 @@ int gmres_create(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *p
                                      "every conductor: the classic surface impedance vanishes there)");
     if (!(opts->tol > 0.0) || opts->max_iter < 1) return fail(SIE_ERR_ARG, "sie_solve: bad tolerance or iteration cap");
     if (opts->prec != SIE_PREC_FP64 && opts->prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "sie_solve: bad precision");
+    if (opts->refine < 0 || opts->refine > 2) return fail(SIE_ERR_ARG, "sie_solve: refine must be 0, 1 or 2");
     (void)cudaGetLastError();
     auto *g = new (std::nothrow) GmresRun;
     if (!g) return fail(SIE_ERR_OOM, "sie_solve: out of host memory");
@@ -1532,6 +1535,13 @@ int gmres_create(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *p
     // iterative refinement: residuals and the convergence test in FP64
     g->outer_prec = (opts->refine && opts->prec == SIE_PREC_MIXED) ? SIE_PREC_FP64 : opts->prec;
     g->refine = g->outer_prec != opts->prec;
+    if (g->refine && opts->refine == 2) {
+        if (p->params.kernel != SIE_KERNEL_STATIC) {
+            delete g;
+            return fail(SIE_ERR_ARG, "sie_solve: double-float residuals (refine = 2) take the static kernel only");
+        }
+        g->resid_prec = SIE_PREC_DF;
+    }
     g->rho_fp64 = 1e4 * opts->tol;
     auto bail = [&](int rc) { delete g; return rc; };
     const int32_t R = g->R, m = g->m;
@@ -1595,6 +1605,7 @@ int gmres_create(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *p
     // the product's coefficients stay in the plan's scratch for the whole solve
     if ((rc = scratch_reserve(p, R, g->o.prec))) return bail(rc);
     if ((rc = scratch_reserve(p, R, g->outer_prec))) return bail(rc);
+    if (g->resid_prec == SIE_PREC_DF && (rc = df_prepare(p, st))) return bail(rc);
     *out = g;
     return SIE_OK;
 }

@@ -16,7 +16,8 @@ SIE_OK = 0
 ERRORS = {-1: "SIE_ERR_ARG", -2: "SIE_ERR_NONMANIFOLD", -3: "SIE_ERR_BAD_PORT", -4: "SIE_ERR_OOM",
           -5: "SIE_ERR_CUDA", -6: "SIE_ERR_NOT_CONVERGED", -7: "SIE_ERR_BREAKDOWN", -8: "SIE_ERR_TIMEOUT"}
 SPACE_LOOP, SPACE_BRANCH = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2   # PREC_DF: double-float on the FP32 pipes (FP64-class)
+REFINE_OFF, REFINE_FP64, REFINE_DF = 0, 1, 2   # sie_solve_opts.refine
 KERNEL_STATIC, KERNEL_LOSSY = 0, 1
 PC_AUTO, PC_BAND, PC_ND = 0, 1, 2
 
