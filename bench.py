@@ -290,7 +290,7 @@ def batch_main(args, ws, dist=None, n_total=None):
     it the same batch launched eagerly on per-plan streams, and the plans one
     after another on one stream (pfft_matvec), all mixed; and FP64 eager."""
     import torch
-    from paper_2210_04891_gb300 import api, SPACE_LOOP, PREC_FP64, PREC_MIXED
+    from paper_2210_04891_gb300 import api, SPACE_LOOP, PREC_FP64, PREC_MIXED, REFINE_OFF, REFINE_FP64, REFINE_DF
     import synth
     plans, xs, oms = [], [], []
     for k, w in enumerate(ws):
@@ -355,13 +355,13 @@ def batch_main(args, ws, dist=None, n_total=None):
         B.solve(warm, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED)
         t_first = time.perf_counter() - t0
         t0 = time.perf_counter()
-        res = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=True, graph=True)
+        res = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=REFINE_DF, graph=True)
         dt = time.perf_counter() - t0
         r0 = B.stats()["replays"]
         t0 = time.perf_counter()
-        res_t = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=True)
+        res_t = B.solve(fr, tol=1e-6, restart=200, max_iter=1000, prec=PREC_MIXED, refine=REFINE_DF)
         dt_t = time.perf_counter() - t0
-        gm = {"tol": 1e-6, "form": "mixed with FP64 refinement", "seconds": dt,
+        gm = {"tol": 1e-6, "form": "mixed with refinement (double-float residual products)", "seconds": dt,
               "step": "one CUDA graph replay per Arnoldi step of all plans (sie_batch_solve_graph)",
               "solves": int(sum(len(f) for f in fr)),
               "iterations_max": int(max(st["iterations_max"] for _, st in res)),
@@ -456,7 +456,7 @@ def learned_main(args):
     preconditioner on `learned_held_out` held-out geometries: mixed GMRES with
     refinement to 1e-6, iterations and time of both forms."""
     import torch
-    from paper_2210_04891_gb300 import api, PREC_MIXED
+    from paper_2210_04891_gb300 import api, PREC_MIXED, REFINE_DF
     import synth
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     freqs = np.array([1e9, 1e10])
@@ -502,7 +502,7 @@ def learned_main(args):
             api.set_learned(P, net if name == "learned" else None)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            Z, st = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=500, prec=PREC_MIXED, refine=True)
+            Z, st = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=500, prec=PREC_MIXED, refine=REFINE_DF)
             out[name]["seconds"] += time.perf_counter() - t1
             out[name]["iterations_sum"] += int(st["iterations_sum"])
             out[name]["not_converged"] += int(not st["converged"])
@@ -621,7 +621,7 @@ def main():
         tdist.init_process_group("nccl")
         dist = tdist
     torch.cuda.set_device(local)
-    from paper_2210_04891_gb300 import api, SPACE_LOOP, PREC_FP64, PREC_MIXED
+    from paper_2210_04891_gb300 import api, SPACE_LOOP, PREC_FP64, PREC_MIXED, REFINE_OFF, REFINE_FP64, REFINE_DF
 
     M = api.Mesh.from_synth(m)
     L = api.Loops(M, m.ports)
@@ -767,10 +767,13 @@ def main():
     gm = None
     if not args.no_gmres:
         # residual: the preconditioned relative residual of the solve (FP64 for
-        # plain_fp64 and mixed_refined, the mixed operator's own for mixed)
+        # plain_fp64; for the refined forms P^-1 (b - Z x) with an FP64 product
+        # (mixed_refined) or a double-float one (mixed_refined_df), P^-1 and the
+        # norms in FP64; the mixed operator's own for mixed)
         gm = {"tol": 1e-6, "rhs": R}
-        for nm, prec, refine in (("plain_fp64", PREC_FP64, False), ("mixed", PREC_MIXED, False),
-                                 ("mixed_refined", PREC_MIXED, True)):
+        for nm, prec, refine in (("plain_fp64", PREC_FP64, REFINE_OFF), ("mixed", PREC_MIXED, REFINE_OFF),
+                                 ("mixed_refined", PREC_MIXED, REFINE_FP64),
+                                 ("mixed_refined_df", PREC_MIXED, REFINE_DF)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Z, st = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=400, prec=prec, refine=refine)
@@ -781,9 +784,9 @@ def main():
                 Zref = Z
             else:
                 gm[nm]["Z_rel_vs_plain"] = float(np.abs(Z - Zref).max() / np.abs(Zref).max())
-        # the mixed solve converged on the FP64-accurate residual is the comparable one
-        gm["headline"] = "mixed_refined"
-        gm["speedup_vs_plain"] = gm["plain_fp64"]["seconds"] / gm["mixed_refined"]["seconds"]
+        # the mixed solve converged on an FP64-class residual is the comparable one
+        gm["headline"] = "mixed_refined_df"
+        gm["speedup_vs_plain"] = gm["plain_fp64"]["seconds"] / gm["mixed_refined_df"]["seconds"]
 
     lossy = None
     if args.lossy and not args.graph:

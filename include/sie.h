@@ -378,7 +378,10 @@ int pfft_autotune(const sie_mesh *m, const sie_loops *l, const pfft_params *base
  *             2: the CUDA-core gather;
  *   far_slab  right-hand sides per warp in the mixed far-field gather, 64 or 128
  *             (0: 64);
- *   proj_slab right-hand sides per warp in the projection, 64 or 128 (0: 128);
+ *   proj_slab the projection: 32 = node chunks with their triangles' currents
+ *             staged in shared memory, 32 right-hand sides per slab (mixed
+ *             form); 64 or 128 = right-hand sides per warp of the direct
+ *             gather (0: 128);
  *   plane_gpc grids per CTA in the (y, z) plane kernel, 1..8 (0: up to 8, as
  *             many as keep about four waves).
  * Errors: SIE_ERR_ARG for a value outside these. */
@@ -394,8 +397,8 @@ int pfft_plan_get_kernel_tuning(const pfft_plan *p, sie_kernel_tuning *t);
 /* Kernel autotuning of a plan: its mixed loop-space product at nrhs right-hand
  * sides and omega timed with CUDA events on cuda_stream (5 products after 2
  * warm-ups) for every combination of near path (automatic and the other
- * applicable one), far-field slab (64, 128), projection slab (64, 128) and
- * plane grids per CTA (automatic, 2, 4); the fastest is set on the plan and
+ * applicable one), far-field slab (64, 128), projection (32, 64, 128) and
+ * plane grids per CTA (automatic, 4); the fastest is set on the plan and
  * returned in best; rep (may be NULL) gets every candidate and its time.
  * Errors: those of pfft_matvec. */
 #define SIE_KTUNE_MAX 32

@@ -329,6 +329,79 @@ __global__ void __launch_bounds__(256) k_project(const int64_t *__restrict__ ptr
     }
 }
 
+// Grid currents (Eq. Projection) of the mixed form by node chunks whose
+// triangles' local currents are staged in shared memory: one CTA per (chunk,
+// slab of kChunkRhs right-hand sides).  The rows c_T [T][3][R] of the chunk's
+// triangles are read once per slab (coalesced 256-byte rows) instead of once
+// per (node, triangle) record, which the direct form reads through L2 (a
+// triangle has about 57 stencil nodes); each warp then takes one node at a
+// time, lanes over right-hand sides, sums its records in order (the sums of
+// k_project) from the staged rows named by the records' chunk-local indices,
+// and groups of 8 nodes pass through shared memory so that each grid row
+// [d][r] gets runs of consecutive nodes (a tile's z extent is 8).
+constexpr int kPTRows = 3 * kChunkRhs + 2;   // staging pitch: the 8-node reads hit distinct banks
+constexpr size_t kPTSmem = size_t(kChunkTri) * 3 * kChunkRhs * sizeof(float2) + size_t(8) * kPTRows * sizeof(float2);
+
+__global__ void __launch_bounds__(256, 4)
+    k_project_tiled(const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ nodes,
+                    const int32_t *__restrict__ tri_ptr, const int32_t *__restrict__ tri,
+                    const int64_t *__restrict__ pn_ptr, const Rec<float> *__restrict__ rec,
+                    const uint16_t *__restrict__ lcol, const float2 *__restrict__ cT, int64_t Ng, int32_t R,
+                    float2 *__restrict__ grid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *X = reinterpret_cast<float2 *>(smem_raw);   // [kChunkTri][3][kChunkRhs]
+    float2 *O = X + kChunkTri * 3 * kChunkRhs;         // [8][kPTRows]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = blockIdx.x;
+    const int32_t r0 = int32_t(blockIdx.y) * kChunkRhs;
+    const int32_t nr = min(kChunkRhs, R - r0);
+    const int32_t t0 = tri_ptr[c], nT = tri_ptr[c + 1] - t0;
+    // staging by asynchronous 8-byte copies, all in flight at once (lanes beyond
+    // the slab's last right-hand side copy nothing and zero-fill)
+    for (int i = w; i < 3 * nT; i += 8) {
+        const int32_t t = tri[t0 + i / 3];
+        const int l = i - 3 * (i / 3);
+        const bool in = lane < nr;
+        const float2 *src = cT + (int64_t(t) * 3 + l) * R + r0 + (in ? lane : 0);
+        const uint32_t dst = uint32_t(__cvta_generic_to_shared(X + i * kChunkRhs + lane));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(in ? 8 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int32_t n0 = node_ptr[c], nN = node_ptr[c + 1] - n0;
+    for (int32_t g = 0; g < nN; g += 8) {
+        float2 acc[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[d] = make_float2(0.f, 0.f);
+        if (g + w < nN) {
+            const int64_t n = nodes[n0 + g + w];
+#pragma unroll 2
+            for (int64_t e = pn_ptr[n]; e < pn_ptr[n + 1]; ++e) {
+                float b[9];
+                load_rec<float>(rec + e, b);
+                const float2 *x = X + int(__ldg(lcol + e)) * (3 * kChunkRhs) + lane;
+                const float2 x0 = x[0], x1 = x[kChunkRhs], x2 = x[2 * kChunkRhs];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc[a].x += b[3 * a] * x0.x + b[3 * a + 1] * x1.x + b[3 * a + 2] * x2.x;
+                    acc[a].y += b[3 * a] * x0.y + b[3 * a + 1] * x1.y + b[3 * a + 2] * x2.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) O[w * kPTRows + d * kChunkRhs + lane] = acc[d];
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * kChunkRhs * 8; i += 256) {
+            const int row = i >> 3, nd = i & 7;
+            const int d = row / kChunkRhs, r = row - d * kChunkRhs;
+            if (r < nr && g + nd < nN)
+                grid[(int64_t(d) * R + r0 + r) * Ng + nodes[n0 + g + nd]] = O[nd * kPTRows + row];
+        }
+        __syncthreads();
+    }
+}
+
 // Grid potentials regrouped with the right-hand sides innermost:
 // phiT[n][b] = grid[b][n], b = d R + r, for the 32-node tiles that hold a
 // stencil node (no other node is interpolated from).
@@ -779,6 +852,27 @@ template <typename T, int V, int J> struct Blocks {
         SIE_SLAB_DISPATCH(T, R, CALL);                                                    \
     } while (0)
 template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) {
+    if constexpr (is_f32<T>) {
+        // mixed form: staged node chunks when asked for (pfft_plan_set_kernel_tuning,
+        // the autotuner); the direct gather is the default (measured on the bond
+        // wires at 128 right-hand sides: 0.68 ms direct against 1.28 ms staged, whose
+        // 32-wide slabs read each block record four times as often)
+        if (p->n_pchunk > 0 && p->kt.proj_slab == kChunkRhs) {
+            if (p->n_pchunk > INT32_MAX) return fail(SIE_ERR_ARG, "projection: too many node chunks");
+            static bool smem_set = false;   // the attribute is per function; set it once per process
+            if (!smem_set) {
+                SIE_CUDA(cudaFuncSetAttribute((const void *)k_project_tiled,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(kPTSmem)));
+                smem_set = true;
+            }
+            const dim3 grid(unsigned(p->n_pchunk), unsigned((R + kChunkRhs - 1) / kChunkRhs));
+            k_project_tiled<<<grid, 256, kPTSmem, st>>>(p->d_pch_node_ptr, p->d_pch_nodes, p->d_pch_tri_ptr,
+                                                        p->d_pch_tri, p->d_pn_ptr, p->d_pn_rec32, p->d_pn_lcol,
+                                                        (const float2 *)p->scr.cT, p->Ng, R, (float2 *)p->scr.grid);
+            SIE_LAUNCH_CHECK(p);
+            return SIE_OK;
+        }
+    }
     if (p->kt.proj_slab == 64) SIE_SLAB_DISPATCH_NARROW(T, R, project(p, R, st));
     SIE_SLAB_DISPATCH(T, R, project(p, R, st));
 }

@@ -835,6 +835,52 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     for (int64_t tl = 0; tl * 32 < p->Ng; ++tl)
         if (pn_ptr[std::min<int64_t>(p->Ng, tl * 32 + 32)] > pn_ptr[tl * 32]) tiles.push_back(int32_t(tl));
     p->n_tiles = int64_t(tiles.size());
+    // projection chunks: node tiles of 2 x 4 x 8 (x, y, z), nodes ascending, cut
+    // where the next node's triangles would take the chunk past kChunkTri; the
+    // local index of each node record's triangle in its chunk.  A node touching
+    // more than kChunkTri triangles leaves the plan on the direct projection.
+    std::vector<int32_t> pch_node_ptr{0}, pch_nodes, pch_tri_ptr{0}, pch_tri;
+    std::vector<uint16_t> pn_lcol(size_t(std::max<int64_t>(n_pair, 1)), 0);
+    bool chunks_ok = true;
+    for (int64_t n = 0; n < p->Ng && chunks_ok; ++n) chunks_ok = pn_ptr[n + 1] - pn_ptr[n] <= kChunkTri;
+    if (chunks_ok) {
+        std::vector<int64_t> stamp(nt, -1);
+        std::vector<int32_t> local(nt, 0);
+        int64_t chunk = 0;
+        int32_t ntri = 0;
+        auto close = [&]() {
+            if (int64_t(pch_nodes.size()) == pch_node_ptr.back()) return;
+            pch_node_ptr.push_back(int32_t(pch_nodes.size()));
+            pch_tri_ptr.push_back(int32_t(pch_tri.size()));
+            ++chunk;
+            ntri = 0;
+        };
+        for (int x0 = 0; x0 < p->Nx; x0 += 2)
+            for (int y0 = 0; y0 < p->Ny; y0 += 4)
+                for (int z0 = 0; z0 < p->Nz; z0 += 8) {
+                    for (int x = x0; x < std::min(x0 + 2, p->Nx); ++x)
+                        for (int y = y0; y < std::min(y0 + 4, p->Ny); ++y)
+                            for (int z = z0; z < std::min(z0 + 8, p->Nz); ++z) {
+                                const int64_t n = (int64_t(x) * p->Ny + y) * p->Nz + z;
+                                int32_t fresh = 0;
+                                for (int64_t e = pn_ptr[n]; e < pn_ptr[n + 1]; ++e)
+                                    fresh += stamp[pn_rec64[e].col] != chunk;
+                                if (ntri + fresh > kChunkTri) close();
+                                for (int64_t e = pn_ptr[n]; e < pn_ptr[n + 1]; ++e) {
+                                    const int64_t t = pn_rec64[e].col;
+                                    if (stamp[t] != chunk) {
+                                        stamp[t] = chunk;
+                                        local[t] = ntri++;
+                                        pch_tri.push_back(int32_t(t));
+                                    }
+                                    pn_lcol[e] = uint16_t(local[t]);
+                                }
+                                pch_nodes.push_back(int32_t(n));
+                            }
+                    close();
+                }
+    }
+    p->n_pchunk = chunks_ok ? int64_t(pch_node_ptr.size()) - 1 : 0;
     // ---- near list (exact criterion per pair; a cell list only prunes candidates)
     std::vector<int32_t> bmin(3 * nt), bmax(3 * nt);
     for (int64_t t = 0; t < nt; ++t)
@@ -942,6 +988,13 @@ extern "C" int pfft_plan_create(const sie_mesh *m, const sie_loops *L, const pff
     UP(p->d_pt_rec64, pt_rec64);
     UP(p->d_pt_rec32, pt_rec32);
     UP(p->d_tiles, tiles);
+    if (p->n_pchunk > 0) {
+        UP(p->d_pch_node_ptr, pch_node_ptr);
+        UP(p->d_pch_nodes, pch_nodes);
+        UP(p->d_pch_tri_ptr, pch_tri_ptr);
+        UP(p->d_pch_tri, pch_tri);
+        UP(p->d_pn_lcol, pn_lcol);
+    }
     UP(p->d_near_ptr, near_ptr);
     UP(p->d_near_col, near_col);
     {

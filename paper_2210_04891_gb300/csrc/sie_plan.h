@@ -16,6 +16,11 @@ template <typename T> struct DevBuf {
     size_t n = 0;
 };
 
+// Projection chunks of the mixed form (k_project_tiled): at most kChunkTri
+// triangles staged per chunk, kChunkRhs right-hand sides per slab.
+constexpr int kChunkTri = 64;
+constexpr int kChunkRhs = 32;
+
 struct PrecondState;   // sie_solve.cu
 struct LossyCache;     // sie_lossy.cu
 struct NdState;        // sie_nd.cu
@@ -90,6 +95,16 @@ struct pfft_plan {
     int64_t *d_pt_ptr = nullptr;        // [nt + 1]  rows = triangles, nodes ascending
     sie::Rec<double> *d_pt_rec64 = nullptr;  //   b[3k + d] = W[d][k], col = n
     sie::Rec<float> *d_pt_rec32 = nullptr;
+    // projection chunks of the mixed form (k_project_tiled): node tiles of
+    // 2 x 4 x 8 (x, y, z) nodes, split where their triangles exceed kChunkTri;
+    // a chunk's triangles are staged once per slab in shared memory and each
+    // node record names its triangle by its index in the chunk (pn_lcol)
+    int64_t n_pchunk = 0;
+    int32_t *d_pch_node_ptr = nullptr;  // [n_pchunk + 1] into d_pch_nodes
+    int32_t *d_pch_nodes = nullptr;     // nodes of each chunk, ascending
+    int32_t *d_pch_tri_ptr = nullptr;   // [n_pchunk + 1] into d_pch_tri
+    int32_t *d_pch_tri = nullptr;       // triangles of each chunk
+    uint16_t *d_pn_lcol = nullptr;      // [n_pair] per node record: index of its triangle in the chunk
     int64_t n_tiles = 0;                // 32-node tiles that hold at least one stencil node
     int32_t *d_tiles = nullptr;         // [n_tiles] tile index n / 32, ascending
     // near field CSR over triangles (row T: near T', ascending), 3x3 blocks

@@ -159,7 +159,8 @@ extern "C" int pfft_plan_set_kernel_tuning(pfft_plan *p, const sie_kernel_tuning
     sie_kernel_tuning k{};
     if (t) k = *t;
     if (k.near < 0 || k.near > 2 || (k.far_slab != 0 && k.far_slab != 64 && k.far_slab != 128) ||
-        (k.proj_slab != 0 && k.proj_slab != 64 && k.proj_slab != 128) || k.plane_gpc < 0 || k.plane_gpc > 8)
+        (k.proj_slab != 0 && k.proj_slab != 32 && k.proj_slab != 64 && k.proj_slab != 128) || k.plane_gpc < 0 ||
+        k.plane_gpc > 8)
         return fail(SIE_ERR_ARG, "pfft_plan_set_kernel_tuning: value out of range");
     p->kt = k;
     return SIE_OK;
@@ -183,8 +184,8 @@ extern "C" int pfft_autotune_kernels(pfft_plan *p, int32_t nrhs, double omega, v
     std::vector<sie_kernel_tuning> cand;
     for (int32_t nr : nears)
         for (int32_t fs : {64, 128})
-            for (int32_t ps : {64, 128})
-                for (int32_t g : {0, 2, 4}) cand.push_back(sie_kernel_tuning{nr, fs, ps, g});
+            for (int32_t ps : {32, 64, 128})
+                for (int32_t g : {0, 4}) cand.push_back(sie_kernel_tuning{nr, fs, ps, g});
     if (int(cand.size()) > SIE_KTUNE_MAX) cand.resize(SIE_KTUNE_MAX);
     const int64_t nl = p->nl;
     const size_t vbytes = size_t(nrhs) * nl * sizeof(double2);

@@ -71,7 +71,7 @@ def test_kernel_tuning_variants_and_autotune():
     om = 2 * np.pi * np.logspace(8, 10, R)
     ref = api.pfft_matvec(P, x, om, SPACE_LOOP, PREC_MIXED)
     for fs in (64, 128):
-        for ps in (64, 128):
+        for ps in (32, 64, 128):   # staged node chunks, direct gathers 64 and 128 wide
             for g in (0, 1, 2, 4):
                 api.set_kernel_tuning(P, 0, fs, ps, g)
                 assert torch.equal(api.pfft_matvec(P, x, om, SPACE_LOOP, PREC_MIXED), ref), (fs, ps, g)
