@@ -101,8 +101,10 @@ typedef struct {
                               convergence test) in FP64, the Arnoldi cycles in
                               the mixed form; 2 = the same with the residual
                               products b - Z x in double-float (SIE_PREC_DF;
-                              P^-1 and the norms stay FP64); 0 = all in the
-                              mixed form                                       */
+                              P^-1 and the norms stay FP64) and, where the
+                              preconditioner takes the narrow band route, its
+                              sweeps inside the cycles in double-float; 0 = all
+                              in the mixed form                                */
 } sie_solve_opts;
 
 typedef struct {
@@ -227,7 +229,10 @@ int pfft_matvec(pfft_plan *p, const void *x, void *y, int32_t nrhs, const double
  * conductor on first use of each distinct omega set.  prec = SIE_PREC_FP64
  * runs every step in FP64; SIE_PREC_MIXED runs the drive, the triangular sweeps
  * on the rounded factor and the branch currents in FP32 (band width below 1024,
- * see pfft_precond_info; wider bands fall back to FP64).  The factor buffers and
+ * see pfft_precond_info; wider bands fall back to FP64); SIE_PREC_DF runs them
+ * in double-float (factor rounded to FP32 pairs) where the band width is at most
+ * 31 and in FP64 otherwise (an FP32 LDL^T solve of the nodal Laplacian, whose
+ * condition grows with the mesh, keeps few correct digits).  The factor buffers and
  * the sweeps' scratch are stream-ordered allocations on cuda_stream from a
  * plan-owned memory pool.  omega[r] > 0, or 0 when every conductor has
  * a slab surface model (SIE_ERR_ARG otherwise).  Errors: SIE_ERR_BREAKDOWN for

@@ -84,6 +84,21 @@ __host__ __device__ __forceinline__ df operator*(df a, df b) {
     const DD s = dd_mul(DD{a.hi, a.lo}, DD{b.hi, b.lo});
     return df(s.hi, s.lo);
 }
+// a * b + c in double-float (the product's error-free FMA part inside dd_mul)
+__host__ __device__ __forceinline__ df fma(df a, df b, df c) {
+    const DD p = dd_mul(DD{a.hi, a.lo}, DD{b.hi, b.lo});
+    const DD s = dd_add(p, DD{c.hi, c.lo});
+    return df(s.hi, s.lo);
+}
+__host__ __device__ __forceinline__ double to_f64(df a) { return double(a.hi) + double(a.lo); }
+__host__ __device__ __forceinline__ double to_f64(float a) { return double(a); }
+__host__ __device__ __forceinline__ double to_f64(double a) { return a; }
+// warp shuffles of one scalar (both halves of a double-float)
+__device__ __forceinline__ float shfl1(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl1(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ df shfl1(df v, int src) {
+    return df(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
 __host__ __device__ __forceinline__ df &operator+=(df &a, df b) { return a = a + b; }
 __host__ __device__ __forceinline__ df &operator-=(df &a, df b) { return a = a - b; }
 __host__ __device__ __forceinline__ df &operator*=(df &a, df b) { return a = a * b; }

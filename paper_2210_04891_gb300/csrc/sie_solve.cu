@@ -26,6 +26,7 @@
 #include <deque>
 #include <map>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "sie_plan.h"
@@ -66,11 +67,13 @@ struct PrecondState {
     int64_t nchunks = 0;
     double2 *d_tile64 = nullptr, *d_dinv64 = nullptr;
     float2 *d_tile32 = nullptr, *d_dinv32 = nullptr;
+    cdf *d_tiledf = nullptr, *d_dinvdf = nullptr;   // double-float sweeps (SIE_PREC_DF)
     float2 *d_u32 = nullptr;          // FP32 sweep buffer [R][nunk]
     // bands wider than a warp (31 < W < 1024): FP32 roundings of band and bandc (mixed form)
     float2 *d_band32 = nullptr, *d_bandc32 = nullptr;
     double2 *d_a = nullptr;           // [nslots][nb] 1/D_e
     float2 *d_a32 = nullptr;          // its FP32 rounding (mixed form)
+    cdf *d_adf = nullptr;             // its double-float rounding (narrow bands)
     double2 *d_kappa = nullptr, *d_u = nullptr, *d_ibr = nullptr;   // scratch [R][...]
     int32_t cap_rhs = 0;
     int32_t *d_slot = nullptr;        // [R] factor slot per right-hand side
@@ -125,7 +128,8 @@ void plan_free_precond(pfft_plan *p) {
     for (void *a : p->pc->allocs) cudaFree(a);
     for (void *a : {(void *)p->pc->d_tile64, (void *)p->pc->d_dinv64, (void *)p->pc->d_tile32,
                     (void *)p->pc->d_dinv32, (void *)p->pc->d_u32, (void *)p->pc->d_a32,
-                    (void *)p->pc->d_band32, (void *)p->pc->d_bandc32})
+                    (void *)p->pc->d_band32, (void *)p->pc->d_bandc32, (void *)p->pc->d_tiledf,
+                    (void *)p->pc->d_dinvdf, (void *)p->pc->d_adf})
         if (a) cudaFree(a);
     for (void *a : {(void *)p->pc->d_band, (void *)p->pc->d_bandc, (void *)p->pc->d_a, (void *)p->pc->d_kappa, (void *)p->pc->d_u,
                     (void *)p->pc->d_ibr, (void *)p->pc->d_slot, (void *)p->pc->d_ndL64, (void *)p->pc->d_ndL32,
@@ -367,6 +371,12 @@ int build_symbolic(pfft_plan *p) {
     return SIE_OK;
 }
 
+// FP64 complex values rounded to double-float pairs (k_round_cdf) or to FP32 (k_round_c)
+__global__ void k_round_cdf(const double2 *__restrict__ a, cdf *__restrict__ b, int64_t n) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    b[i] = cdf{df(a[i].x), df(a[i].y)};
+}
 __global__ void k_round_c(const double2 *__restrict__ a, float2 *__restrict__ b, int64_t n) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) b[i] = make_float2(float(a[i].x), float(a[i].y));
@@ -701,8 +711,8 @@ __global__ void __launch_bounds__(MAXT) k_pc_sweep_blk(
 // pivot on.  A step broadcasts the finished pivot with one shuffle and each lane
 // applies one multiply-add; the pivot's lane then takes the row 32 further on.
 template <typename V> __device__ __forceinline__ V shfl_c(V v, int src) {
-    v.x = __shfl_sync(0xffffffffu, v.x, src);
-    v.y = __shfl_sync(0xffffffffu, v.y, src);
+    v.x = shfl1(v.x, src);
+    v.y = shfl1(v.y, src);
     return v;
 }
 
@@ -949,7 +959,7 @@ __global__ void k_pc_out(const C<T> *__restrict__ ibr, const int32_t *__restrict
         for (int32_t k = src_ptr[q]; k < src_ptr[q + 1]; ++k)
             v = src_sg[k] > 0 ? cadd(v, ir[src_br[k]]) : csub(v, ir[src_br[k]]);
     }
-    z[i] = make_double2(double(v.x), double(v.y));
+    z[i] = make_double2(to_f64(v.x), to_f64(v.y));
 }
 
 inline unsigned nblk_(int64_t n, int t = 256) { return unsigned((n + t - 1) / t); }
@@ -1014,10 +1024,13 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     const int32_t ns = int32_t(uniq.size());
     if (s->d_band) cudaFreeAsync(s->d_band, st);
     if (s->d_bandc) cudaFreeAsync(s->d_bandc, st);
-    for (void *q : {(void *)s->d_tile64, (void *)s->d_dinv64, (void *)s->d_tile32, (void *)s->d_dinv32})
+    for (void *q : {(void *)s->d_tile64, (void *)s->d_dinv64, (void *)s->d_tile32, (void *)s->d_dinv32,
+                    (void *)s->d_tiledf, (void *)s->d_dinvdf, (void *)s->d_adf})
         if (q) cudaFreeAsync(q, st);
     s->d_tile64 = s->d_dinv64 = nullptr;
     s->d_tile32 = s->d_dinv32 = nullptr;
+    s->d_tiledf = s->d_dinvdf = nullptr;
+    s->d_adf = nullptr;
     if (s->d_a) cudaFreeAsync(s->d_a, st);
     if (s->d_a32) cudaFreeAsync(s->d_a32, st);
     if (s->d_band32) cudaFreeAsync(s->d_band32, st);
@@ -1052,6 +1065,9 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
         SIE_CUDA(pool_alloc(p, &s->d_tile32, size_t(ntile) * sizeof(float2), st));
         SIE_CUDA(pool_alloc(p, &s->d_dinv64, size_t(ns) * s->nunk * sizeof(double2), st));
         SIE_CUDA(pool_alloc(p, &s->d_dinv32, size_t(ns) * s->nunk * sizeof(float2), st));
+        SIE_CUDA(pool_alloc(p, &s->d_tiledf, size_t(ntile) * sizeof(cdf), st));
+        SIE_CUDA(pool_alloc(p, &s->d_dinvdf, size_t(ns) * s->nunk * sizeof(cdf), st));
+        SIE_CUDA(pool_alloc(p, &s->d_adf, size_t(ns) * p->nb * sizeof(cdf), st));
     }
     SIE_CUDA(pool_alloc(p, &s->d_a, size_t(ns) * p->nb * sizeof(double2), st));
     SIE_CUDA(pool_alloc(p, &s->d_a32, size_t(ns) * p->nb * sizeof(float2), st));
@@ -1080,6 +1096,10 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
     if (int rl = learned_admittance(p, d_zc, ns, s->d_a, st)) return rl;   // D' = D (1 + g)
     k_round_c<<<nblk_(p->nb * ns), 256, 0, st>>>(s->d_a, s->d_a32, p->nb * ns);
     SIE_LAUNCH_CHECK(p);
+    if (tiled) {
+        k_round_cdf<<<nblk_(p->nb * ns), 256, 0, st>>>(s->d_a, s->d_adf, p->nb * ns);
+        SIE_LAUNCH_CHECK(p);
+    }
     int zero = 0;
     SIE_CUDA(cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
@@ -1114,6 +1134,11 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
             SIE_LAUNCH_CHECK(p);
             k_pc_dinv<float><<<nblk_(nd), 256, 0, st>>>(s->d_band, nd, s->W + 1, s->d_dinv32);
             SIE_LAUNCH_CHECK(p);
+            k_pc_tiles<df><<<nblk_(ntile), 256, 0, st>>>(s->d_band, s->d_bandc, s->d_blk_off, s->d_tile_off, nblk,
+                                                           s->W, s->nunk, s->nchunks, ns, s->d_tiledf);
+            SIE_LAUNCH_CHECK(p);
+            k_pc_dinv<df><<<nblk_(nd), 256, 0, st>>>(s->d_band, nd, s->W + 1, s->d_dinvdf);
+            SIE_LAUNCH_CHECK(p);
         }
         if (wide) {
             k_round_c<<<nblk_(nband), 256, 0, st>>>(s->d_band, s->d_band32, nband);
@@ -1137,18 +1162,35 @@ int pc_prepare(pfft_plan *p, const double *omega, int32_t R, std::vector<int32_t
 template <typename T>
 int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream_t st) {
     PrecondState *s = p->pc;
-    constexpr bool f32 = sizeof(T) == 4;
+    constexpr bool f32 = std::is_same<T, float>::value;
+    constexpr bool dfl = std::is_same<T, df>::value;   // double-float: narrow bands only
     const int32_t nblk = int32_t(s->blk_off.size() - 1);
     C<T> *kappa = reinterpret_cast<C<T> *>(s->d_kappa);   // buffers sized for complex128
     C<T> *ibr = reinterpret_cast<C<T> *>(s->d_ibr);
     C<T> *u;
     const C<T> *a;
-    if constexpr (f32) { u = s->d_u32; a = s->d_a32; } else { u = s->d_u; a = s->d_a; }
+    if constexpr (f32) { u = s->d_u32; a = s->d_a32; }
+    else if constexpr (dfl) { u = reinterpret_cast<cdf *>(s->d_u); a = s->d_adf; }
+    else { u = s->d_u; a = s->d_a; }
     k_pc_drive<T><<<nblk_(p->nb * R), 256, 0, st>>>(y, p->nl, a, s->d_slot, p->d_loop_of_branch, p->d_tail,
                                                     p->d_head, s->d_off_ptr, s->d_off_port, s->d_off_sign,
                                                     s->d_port_loop, p->nb, R, kappa);
     SIE_LAUNCH_CHECK(p);
-    if (s->nd && s->nunk > 0) {
+    if constexpr (dfl) {
+        if (s->nd || s->W > 31 || !s->d_tiledf) return fail(SIE_ERR_ARG, "preconditioner: double-float sweeps "
+                                                                         "need the narrow band route");
+        if (s->nunk > 0) {
+            k_pc_rhs<T><<<nblk_(int64_t(R) * s->nunk), 256, 0, st>>>(kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
+                                                                       s->nunk, p->nb, R, u);
+            SIE_LAUNCH_CHECK(p);
+            const size_t sm = size_t(4) * pc_nbuf<T>() * PC_TILE * sizeof(C<T>);
+            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(sm)));
+            k_pc_sweep<T><<<nblk_(int64_t(R) * nblk * 32, 128), 128, sm, st>>>(
+                s->d_blk_off, s->d_tile_off, nblk, s->nunk, s->nchunks, s->d_tiledf, s->d_dinvdf, s->d_slot, R, u);
+            SIE_LAUNCH_CHECK(p);
+        }
+    } else if (s->nd && s->nunk > 0) {
         k_pc_rhs<T><<<nblk_(int64_t(R) * s->nunk), 256, 0, st>>>(kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg,
                                                                    s->nunk, p->nb, R, u);
         SIE_LAUNCH_CHECK(p);
@@ -1208,10 +1250,14 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
     return SIE_OK;
 }
 
+// Narrow band route (one warp per sweep): the one with double-float sweeps.
+bool pc_df_route(const pfft_plan *p) { return p->pc && !p->pc->nd && p->pc->W <= 31 && p->pc->d_tiledf; }
+
 int pc_apply_async(pfft_plan *p, const double2 *y, double2 *z, int32_t R, int prec, cudaStream_t st) {
     StageTimer tm(p, SIE_STAGE_PRECOND_APPLY, st);
     if (prec == SIE_PREC_MIXED && (p->pc->nd || p->pc->W < kWideMax)) return pc_apply_t<float>(p, y, z, R, st);
-    return pc_apply_t<double>(p, y, z, R, st);
+    if (prec == SIE_PREC_DF && pc_df_route(p)) return pc_apply_t<df>(p, y, z, R, st);
+    return pc_apply_t<double>(p, y, z, R, st);   // FP64 (and double-float where no narrow band)
 }
 
 // ------------------------------------------------------------------ GMRES kernels
@@ -1411,7 +1457,8 @@ __global__ void k_norms(const double2 *__restrict__ h, int32_t ldh, int32_t R, d
 extern "C" int pfft_precond_apply(pfft_plan *p, const void *y, void *z, int32_t nrhs, const double *omega,
                                   int32_t prec, void *cuda_stream) {
     if (!p || !y || !z || !omega || nrhs < 1) return fail(SIE_ERR_ARG, "pfft_precond_apply: bad argument");
-    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED) return fail(SIE_ERR_ARG, "pfft_precond_apply: bad precision");
+    if (prec != SIE_PREC_FP64 && prec != SIE_PREC_MIXED && prec != SIE_PREC_DF)
+        return fail(SIE_ERR_ARG, "pfft_precond_apply: bad precision");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     (void)cudaGetLastError();
     std::vector<int32_t> slot;
@@ -1440,6 +1487,7 @@ struct GmresRun {
     bool use_pc = true, refine = false;
     int outer_prec = SIE_PREC_FP64;
     int resid_prec = SIE_PREC_FP64;   // the refinement's residual products: FP64 or double-float
+    int pc_prec = SIE_PREC_FP64;      // the preconditioner inside the cycles
     // device
     double2 *V = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *t = nullptr, *dh = nullptr, *dh2 = nullptr,
             *dhn = nullptr, *dy = nullptr, *rv = nullptr, *dvec = nullptr, *vin = nullptr;
@@ -1471,7 +1519,7 @@ struct GmresRun {
         int r2 = launch_only ? matvec_launch(p, in, use_pc ? t : out, R, SIE_SPACE_LOOP, prec, st)
                              : matvec_async(p, in, use_pc ? t : out, R, om.data(), SIE_SPACE_LOOP, prec, st);
         if (r2) return r2;
-        if (use_pc) return pc_apply_async(p, t, out, R, prec, st);
+        if (use_pc) return pc_apply_async(p, t, out, R, prec == o.prec ? pc_prec : prec, st);
         return SIE_OK;
     }
     // ||vec[r]|| into dnorm (device) through k_dots on a one-vector basis
@@ -1549,6 +1597,11 @@ int gmres_create(pfft_plan *p, const double *freqs, int32_t nf, const int32_t *p
     std::vector<int32_t> slot;
     int rc;
     if (g->use_pc && (rc = pc_prepare(p, g->om.data(), R, slot, st))) return bail(rc);
+    // the cycles' preconditioner: the product's precision, except that double-float
+    // refinement (refine = 2) takes double-float sweeps where the band is narrow (the
+    // FP32 sweeps of the nodal Laplacian's LDL^T limit how far one cycle can go)
+    g->pc_prec = g->o.prec;
+    if (g->refine && opts->refine == 2 && g->use_pc && pc_df_route(p)) g->pc_prec = SIE_PREC_DF;
 #define GA(ptr, bytes) do { cudaError_t _e = pool_alloc(p, &(ptr), (bytes), st); if (_e != cudaSuccess) return bail(fail(_e == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA, std::string("sie_solve: workspace: ") + cudaGetErrorString(_e))); } while (0)
     GA(g->V, size_t(m + 1) * g->kstride * sizeof(double2));
     for (double2 **q : {&g->w, &g->b, &g->x, &g->t, &g->rv, &g->vin}) GA(*q, size_t(R) * n * sizeof(double2));

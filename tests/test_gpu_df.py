@@ -15,6 +15,12 @@ on a grid whose (y, z) plane takes the large-plane route; at the bond-wire
 size (40,192 triangles, 128 right-hand sides) against FP64; and GMRES with
 double-float refinement residuals against the FP64-residual refinement and the
 plain FP64 solve.
+
+The preconditioner's sweeps (Eq. Precond, the LDL^T solve of the nodal
+Laplacian) in double-float agree with FP64 within 1e-11 where the band is
+narrow (one warp per sweep), and are the FP64 sweeps elsewhere; the FP32
+sweeps of the same factor are far less accurate, which is why double-float
+refinement uses them inside its cycles.
 """
 import numpy as np
 import pytest
@@ -148,3 +154,35 @@ def test_df_at_bondwire_size_matches_fp64():
                           refine=REFINE_DF)
     assert st["converged"] and st["residual_max"] < 1e-6
     assert np.abs(Z - np.transpose(Z, (0, 2, 1))).max() < 1e-6 * np.abs(Z).max()
+
+
+@pytest.mark.parametrize("name,make,grid", MESHES, ids=[m[0] for m in MESHES])
+def test_df_preconditioner_matches_fp64(name, make, grid):
+    m = make()
+    O, S, P = build(m, grid)
+    om = 2 * np.pi * np.array([1e8, 1e9, 1e9, 2e10])
+    y = torch.from_numpy(synth.complex_gaussian(O.nl, om.size, seed=64)).cuda()
+    z64 = api.pfft_precond_apply(P, y, om).cpu().numpy()
+    zdf = api.pfft_precond_apply(P, y, om, prec=PREC_DF).cpu().numpy()
+    z32 = api.pfft_precond_apply(P, y, om, prec=PREC_MIXED).cpu().numpy()
+    narrow = api.precond_nd_info(P)["method"] != N.PC_ND and api.precond_info(P)["band_width"] <= 31
+    if narrow:
+        assert rel(zdf, z64).max() < 1e-11, (name, rel(zdf, z64).max())
+        assert rel(zdf, z64).max() < 1e-3 * max(rel(z32, z64).max(), 1e-12)
+    else:
+        assert np.array_equal(zdf, z64)   # FP64 sweeps where the band is not narrow
+
+
+def test_df_refinement_at_bondwire_size_takes_fewer_cycles():
+    w = synth.bondwires_40k()
+    m = w["mesh"]
+    M = api.Mesh.from_synth(m)
+    L = api.Loops(M, m.ports)
+    P = api.Plan(M, L, dict(PARAMS, grid=w["grid"], n_touch=16))
+    freqs = w["freqs"][::4]
+    Z64, st64 = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=400, prec=PREC_FP64)
+    Z1, st1 = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=400, prec=PREC_MIXED, refine=REFINE_FP64)
+    Z2, st2 = api.sie_solve(P, freqs, tol=1e-6, restart=100, max_iter=400, prec=PREC_MIXED, refine=REFINE_DF)
+    assert st1["converged"] and st2["converged"] and st2["residual_max"] < 1e-6
+    assert st2["iterations_max"] < st1["iterations_max"]
+    assert np.abs(Z2 - Z64).max() < 1e-6 * np.abs(Z64).max()
