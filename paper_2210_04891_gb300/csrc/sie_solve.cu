@@ -796,11 +796,53 @@ __device__ __forceinline__ void pc_stage_tile(C<T> *dst, const C<T> *src, int la
 // t is every lane's updated value before that hand-over.  The pivot lane of the
 // next step was not this step's pivot, so its t equals its w, and the broadcast
 // reads t: the select stays off the chain from one pivot to the next.
+// Double-float step, t = w - l xi with the pivot-to-pivot chain on the high
+// parts only: hi = (w.hi + p1) + p2 with p1, p2 the FP32 products of the high
+// parts (two FP32 operations deep), and every rounding error of those products
+// (two-product) and sums (two-sum), the low-part products and w.lo collected in
+// lo, which is added last and which no later high part waits for.  The pair
+// stays unnormalised during the sweep: a row takes at most W <= 31 updates
+// before it is a pivot, so lo stays a few units of hi's last place and hi + lo
+// carries about 48 bits; the stores normalise it.
+__device__ __forceinline__ float tprod(float a, float b, float &e) {
+    const float p = a * b;
+    e = fmaf(a, b, -p);
+    return p;
+}
+__device__ __forceinline__ float tsum(float a, float b, float &e) {
+    const float s = a + b, bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+// w - (a1 x1 + a2 x2) with (a, x) double-float pairs, the high-part chain two deep
+__device__ __forceinline__ df df_sub2(df w, df a1, df x1, df a2, df x2) {
+    float e1, e2, f1, f2;
+    const float p1 = tprod(-a1.hi, x1.hi, e1), p2 = tprod(-a2.hi, x2.hi, e2);
+    const float s1 = tsum(w.hi, p1, f1), s2 = tsum(s1, p2, f2);
+    float lo = (((w.lo + e1) + e2) + (f1 + f2));
+    lo = fmaf(-a1.lo, x1.hi, lo);
+    lo = fmaf(-a2.lo, x2.hi, lo);
+    lo = fmaf(-a1.hi, x1.lo, lo);
+    lo = fmaf(-a2.hi, x2.lo, lo);
+    return df(s2, lo);
+}
+
 template <typename T>
 __device__ __forceinline__ void pc_step(const C<T> *tl, int j, int lane, C<T> &w, C<T> &t, const C<T> &pf,
                                         C<T> &done) {
     const C<T> l = tl[j];
     const C<T> xi = shfl_c(t, j);
+    if constexpr (std::is_same<T, df>::value) {
+        // re: w.re - (l.re xi.re - l.im xi.im), im: w.im - (l.re xi.im + l.im xi.re)
+        t.x = df_sub2(w.x, l.x, xi.x, -l.y, xi.y);
+        t.y = df_sub2(w.y, l.x, xi.y, l.y, xi.x);
+        const bool me = lane == j;
+        done.x = me ? xi.x : done.x;
+        done.y = me ? xi.y : done.y;
+        w.x = me ? pf.x : t.x;
+        w.y = me ? pf.y : t.y;
+        return;
+    }
     t.x = fma(-l.x, xi.x, fma(l.y, xi.y, w.x));
     t.y = fma(-l.x, xi.y, fma(-l.y, xi.x, w.y));
     const bool me = lane == j;
@@ -1727,8 +1769,12 @@ int gmres_begin(GmresRun *g) {
     SIE_CUDA(cudaMemcpyAsync(g->dbeta, g->dnorm, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     SIE_CUDA(cudaMemcpyAsync(g->gd.iters, g->iters.data(), size_t(R) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     // the cycle's stopping level (relative to ||P^-1 b||): the tolerance, or with
-    // refinement a hundredth of the largest starting residual, at least half the tolerance
-    g->tol_inner = g->refine ? std::max(0.5 * g->o.tol, 1e-2 * g->cycle_start) : g->o.tol;
+    // refinement a fixed fraction of the largest starting residual, at least half the tolerance
+    // (the reduction one cycle reaches on the bond-wire array: 1e-2 with the FP32
+    // preconditioner, whose sweeps limit the cycle; 1e-3 with double-float sweeps,
+    // measured against 1e-2 and 1e-4: 26 iterations against 32 and 28)
+    const double per_cycle = g->pc_prec == SIE_PREC_DF ? 1e-3 : 1e-2;
+    g->tol_inner = g->refine ? std::max(0.5 * g->o.tol, per_cycle * g->cycle_start) : g->o.tol;
     k_cycle_start<<<unsigned((R + 127) / 128), 128, 0, st>>>(g->gd, g->m, R, g->dbeta, g->act);
     SIE_LAUNCH_CHECK(p);
     k_scale_store<<<nblk_(int64_t(R) * g->n), 256, 0, st>>>(g->w, g->ldv, g->V, g->kstride, 0, g->n, g->gd.scale,
