@@ -6,7 +6,9 @@
 // row m = 3 t_local + k).  A tile's columns are the union U of the near
 // triangles of its rows, ascending; each column triangle T' contributes 4
 // K-slots (its local currents l = 0, 1, 2 and a zero), so one
-// M = 128, N = 256, K = 8 step covers two column triangles.  N = 256 real
+// M = 128, N = 256, K = 8 step covers two column triangles, and a pipeline
+// chunk four (two K steps: the per-chunk waits, fences, arrivals and copy
+// issues of the feed are shared by twice the work of one step).  N = 256 real
 // columns are 128 complex right-hand sides (column 2r the real part, 2r + 1
 // the imaginary part): L_d is real, so real and imaginary parts are
 // independent columns of one real product.
@@ -22,9 +24,9 @@
 // rows per triangle and slab of 128 right-hand sides).
 //
 // Persistent CTAs (one per SM) walk the (tile, slab) items; warp roles:
-//   warp 0     producer: bulk copies of the compact operands, 6-stage raw ring
+//   warp 0     producer: bulk copies of the compact operands, 4-stage raw ring
 //   warp 1     TMEM owner (2 accumulators x 256 columns) and MMA issuer
-//   warps 2-5  converters: raw ring -> split, MMA-layout images (3-stage ring)
+//   warps 2-5  converters: raw ring -> split, MMA-layout images (2-stage ring)
 //   warps 6-9  epilogue: accumulator -> + far field + Z_s Gram term -> y_T
 //              (double-float complex), overlapping the next item's MMAs
 //              (double-buffered TMEM)
@@ -46,20 +48,21 @@ constexpr int kTileTri = 42;                    // triangles per row tile
 constexpr int kRows = 128;                      // MMA M
 constexpr int kCols = 256;                      // MMA N (128 complex right-hand sides)
 constexpr int kSlabRhs = kCols / 2;
-constexpr int kRawStages = 6, kCvStages = 3;
+constexpr int kPos = 4;                        // column triangles per chunk: two K = 8 steps
+constexpr int kRawStages = 4, kCvStages = 2;
 constexpr uint32_t kARaw = kRows * 3 * 4;       // compact A bytes per union position (1.5 KB)
 constexpr uint32_t kXRow = kSlabRhs * 8;        // one c_T row of a slab (1 KB)
-constexpr uint32_t kRawBytes = 2 * kARaw + 2 * 3 * kXRow;          // 9 KB
+constexpr uint32_t kRawBytes = kPos * kARaw + kPos * 3 * kXRow;    // 18 KB
 constexpr uint32_t kAImg = kRows * 16;          // A image per position (2 KB)
 constexpr uint32_t kXImg = kCols * 16;          // X image per triangle (4 KB)
-constexpr uint32_t kCvBytes = 2 * (2 * kAImg) + 2 * (2 * kXImg);  // 24 KB
+constexpr uint32_t kCvBytes = 2 * (kPos * kAImg) + 2 * (kPos * kXImg);  // 48 KB
 constexpr uint32_t kSmemBytes = kRawStages * kRawBytes + kCvStages * kCvBytes + 1024;
 constexpr int kThreads = 320;
 constexpr uint64_t kWaitNs = 2000000000ull;     // bounded mbarrier waits: 2 s
 constexpr uint32_t kErrNearMma = 1;
 
 struct NearMmaArgs {
-    const int64_t *u_ptr;     // [ntiles + 1], even counts
+    const int64_t *u_ptr;     // [ntiles + 1], counts multiples of kPos
     const int32_t *u_tri;     // [n_union]
     const float *Ac;          // [n_union][128][3]
     const float2 *ffar;       // [nt][3][R]
@@ -120,24 +123,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
             for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
                 const int tile = w % a.ntiles, slab = w / a.ntiles;
                 const int64_t u0 = a.u_ptr[tile];
-                const int nchunk = int((a.u_ptr[tile + 1] - u0) / 2);
+                const int nchunk = int((a.u_ptr[tile + 1] - u0) / kPos);
                 const int32_t nr = min(kSlabRhs, R - slab * kSlabRhs);
                 const uint32_t xbytes = uint32_t(nr) * 8;
                 for (int c = 0; c < nchunk; ++c, ++g) {
                     const uint32_t s = g % kRawStages, use = g / kRawStages;
                     if (use > 0 && !tc::mbar_wait(&raw_empty[s], (use - 1) & 1, kWaitNs)) { ok = false; break; }
                     unsigned char *st = raw + s * kRawBytes;
-                    const int64_t u = u0 + 2 * c;
-                    tc::mbar_expect_tx(&raw_full[s], 2 * kARaw + 6 * xbytes);
-                    tc::bulk_g2s(st, a.Ac + u * (kARaw / 4), 2 * kARaw, &raw_full[s]);
-                    for (int j = 0; j < 2; ++j) {
+                    const int64_t u = u0 + kPos * c;
+                    tc::mbar_expect_tx(&raw_full[s], kPos * kARaw + kPos * 3 * xbytes);
+                    tc::bulk_g2s(st, a.Ac + u * (kARaw / 4), kPos * kARaw, &raw_full[s]);
+                    for (int j = 0; j < kPos; ++j) {
                         const int64_t t = a.u_tri[u + j];
                         const float2 *src = a.cT + t * 3 * R + int64_t(slab) * kSlabRhs;
                         if (R == kSlabRhs) {   // the triangle's three rows are one contiguous 3 KB block
-                            tc::bulk_g2s(st + 2 * kARaw + 3 * j * kXRow, src, 3 * kXRow, &raw_full[s]);
+                            tc::bulk_g2s(st + kPos * kARaw + 3 * j * kXRow, src, 3 * kXRow, &raw_full[s]);
                         } else {
                             for (int l = 0; l < 3; ++l)
-                                tc::bulk_g2s(st + 2 * kARaw + (3 * j + l) * kXRow, src + l * R, xbytes, &raw_full[s]);
+                                tc::bulk_g2s(st + kPos * kARaw + (3 * j + l) * kXRow, src + l * R, xbytes,
+                                             &raw_full[s]);
                         }
                     }
                 }
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
             bool ok = true;
             for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++item) {
                 const int tile = w % a.ntiles;
-                const int nchunk = int((a.u_ptr[tile + 1] - a.u_ptr[tile]) / 2);
+                const int nchunk = int((a.u_ptr[tile + 1] - a.u_ptr[tile]) / kPos);
                 const uint32_t ab = item & 1, use_a = item >> 1;
                 if (use_a > 0 && !tc::mbar_wait(&acc_empty[ab], (use_a - 1) & 1, kWaitNs)) { ok = false; break; }
                 tc::fence_after_sync();
@@ -162,14 +166,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
                     if (!tc::mbar_wait(&cv_full[s], use & 1, kWaitNs)) { ok = false; break; }
                     tc::fence_after_sync();
                     unsigned char *st = cv + s * kCvBytes;
-                    // A images: core matrices (8 rows x 4 slots) +128 B along M, +2 KB along K
-                    const uint64_t Ab = tc::sdesc(st, kAImg, 128), As = tc::sdesc(st + 2 * kAImg, kAImg, 128);
-                    // X images: (8 columns x 4 slots) +128 B along N, +4 KB along K
-                    const uint64_t Xb = tc::sdesc(st + 4 * kAImg, kXImg, 128);
-                    const uint64_t Xs = tc::sdesc(st + 4 * kAImg + 2 * kXImg, kXImg, 128);
-                    tc::mma_tf32(d, Ab, Xb, idesc, c > 0);
-                    tc::mma_tf32(d, Ab, Xs, idesc, true);
-                    tc::mma_tf32(d, As, Xb, idesc, true);
+                    // A images: core matrices (8 rows x 4 slots) +128 B along M, +2 KB along K;
+                    // X images: (8 columns x 4 slots) +128 B along N, +4 KB along K; step ks
+                    // takes positions 2 ks and 2 ks + 1 of the chunk
+#pragma unroll
+                    for (int ks = 0; ks < kPos / 2; ++ks) {
+                        unsigned char *a0 = st + 2 * ks * kAImg, *x0 = st + 2 * kPos * kAImg + 2 * ks * kXImg;
+                        const uint64_t Ab = tc::sdesc(a0, kAImg, 128), As = tc::sdesc(a0 + kPos * kAImg, kAImg, 128);
+                        const uint64_t Xb = tc::sdesc(x0, kXImg, 128), Xs = tc::sdesc(x0 + kPos * kXImg, kXImg, 128);
+                        tc::mma_tf32(d, Ab, Xb, idesc, c > 0 || ks > 0);
+                        tc::mma_tf32(d, Ab, Xs, idesc, true);
+                        tc::mma_tf32(d, As, Xb, idesc, true);
+                    }
                     tc::mma_commit(&cv_empty[s]);
                 }
                 if (!ok) break;
@@ -186,19 +194,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
         bool ok = true;
         for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
             const int tile = w % a.ntiles;
-            const int nchunk = int((a.u_ptr[tile + 1] - a.u_ptr[tile]) / 2);
+            const int nchunk = int((a.u_ptr[tile + 1] - a.u_ptr[tile]) / kPos);
             for (int c = 0; c < nchunk; ++c, ++g) {
                 const uint32_t sr = g % kRawStages, ur = g / kRawStages;
                 const uint32_t sc = g % kCvStages, uc = g / kCvStages;
                 if (!tc::mbar_wait(&raw_full[sr], ur & 1, kWaitNs)) { ok = false; break; }
                 if (uc > 0 && !tc::mbar_wait(&cv_empty[sc], (uc - 1) & 1, kWaitNs)) { ok = false; break; }
                 const float *rA = reinterpret_cast<const float *>(raw + sr * kRawBytes);
-                const float *rX = rA + 2 * kARaw / 4;
+                const float *rX = rA + kPos * kARaw / 4;
                 float4 *img = reinterpret_cast<float4 *>(cv + sc * kCvBytes);
-                float4 *iAb = img, *iAs = img + 2 * kAImg / 16;
-                float4 *iXb = img + 4 * kAImg / 16, *iXs = iXb + 2 * kXImg / 16;
+                float4 *iAb = img, *iAs = img + kPos * kAImg / 16;
+                float4 *iXb = img + 2 * kPos * kAImg / 16, *iXs = iXb + kPos * kXImg / 16;
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {    // A: row tid of position j; image (g = m/8) * 128 B + (m % 8) * 16 B
+                for (int j = 0; j < kPos; ++j) {   // A: row tid of position j; image (g = m/8) * 128 B + (m % 8) * 16 B
                     const float *r3 = rA + j * (kARaw / 4) + 3 * tid;
                     float4 b, sp;
                     split4(r3[0], r3[1], r3[2], b, sp);
@@ -207,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_mma(NearMmaArgs a) {
                     iAs[o] = sp;
                 }
 #pragma unroll
-                for (int j = 0; j < 2; ++j)      // X: columns n = tid, tid + 128 of triangle j
+                for (int j = 0; j < kPos; ++j)   // X: columns n = tid, tid + 128 of triangle j
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int n = tid + 128 * h;
@@ -363,7 +371,7 @@ int near_mma_prepare(pfft_plan *p, const std::vector<int64_t> &near_ptr, const s
             u_col.push_back(c);
             u_tile.push_back(int32_t(i));
         }
-        if (cols.size() % 2) {   // pad to whole K = 8 steps: a zero block on a valid triangle
+        for (size_t k = cols.size(); k % kPos; ++k) {   // pad to whole chunks: zero blocks on a valid triangle
             u_tri.push_back(cols.back());
             u_col.push_back(-1);
             u_tile.push_back(int32_t(i));
