@@ -219,6 +219,26 @@ __global__ void k_alpha_tri(const double2 *__restrict__ x, int64_t nl, const Tou
     }
 }
 
+// acc += b x for double-float b and x into an unnormalised double-float sum:
+// the high part takes one FP32 add per term (the chain a gather runs along),
+// the two-product error of the high parts, the two-sum error of that add and
+// the cross products of high and low parts go to the low part, one add per
+// term.  A sum of n terms keeps about 48 bits plus log2(n); readers treat
+// (hi, lo) as the value hi + lo, whatever its normalisation.
+__device__ __forceinline__ void df_acc(df &acc, df b, df x) {
+    const float p = b.hi * x.hi;
+    const float e = fmaf(b.hi, x.hi, -p);
+    const float s = acc.hi + p, bb = s - acc.hi;
+    const float f = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += fmaf(b.lo, x.hi, fmaf(b.hi, x.lo, e + f));
+}
+// the same value as a normalised pair (two-sum of its parts)
+__device__ __forceinline__ df df_norm(df a) {
+    const float s = a.hi + a.lo, bb = s - a.hi;
+    return df(s, (a.hi - (s - bb)) + (a.lo - bb));
+}
+
 // V complex values at p (16-byte aligned when V = 2).
 template <typename T, int V> __device__ __forceinline__ void ldv(const C<T> *p, C<T> (&v)[V]) {
     if constexpr (V == 2) {
@@ -234,7 +254,9 @@ template <typename T, int V> __device__ __forceinline__ void ldv(const C<T> *p, 
     }
 }
 template <typename T, int V> __device__ __forceinline__ void stv(C<T> *p, const C<T> (&v)[V]) {
-    if constexpr (V == 2) {
+    if constexpr (is_df<T>) {
+        *p = cdf{df_norm(v[0].x), df_norm(v[0].y)};
+    } else if constexpr (V == 2) {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
     } else {
         *p = v[0];
@@ -268,8 +290,17 @@ __device__ __forceinline__ void gather_rows(const Rec<T> *__restrict__ rec, int6
                 for (int v = 0; v < V; ++v)
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        acc[a][j][v].x += b[3 * a] * x0[v].x + b[3 * a + 1] * x1[v].x + b[3 * a + 2] * x2[v].x;
-                        acc[a][j][v].y += b[3 * a] * x0[v].y + b[3 * a + 1] * x1[v].y + b[3 * a + 2] * x2[v].y;
+                        if constexpr (is_df<T>) {
+                            df_acc(acc[a][j][v].x, b[3 * a], x0[v].x);
+                            df_acc(acc[a][j][v].x, b[3 * a + 1], x1[v].x);
+                            df_acc(acc[a][j][v].x, b[3 * a + 2], x2[v].x);
+                            df_acc(acc[a][j][v].y, b[3 * a], x0[v].y);
+                            df_acc(acc[a][j][v].y, b[3 * a + 1], x1[v].y);
+                            df_acc(acc[a][j][v].y, b[3 * a + 2], x2[v].y);
+                        } else {
+                            acc[a][j][v].x += b[3 * a] * x0[v].x + b[3 * a + 1] * x1[v].x + b[3 * a + 2] * x2[v].x;
+                            acc[a][j][v].y += b[3 * a] * x0[v].y + b[3 * a + 1] * x1[v].y + b[3 * a + 2] * x2[v].y;
+                        }
                     }
             }
         }
@@ -462,7 +493,8 @@ __device__ __forceinline__ void tri_epilogue(const C<T> (&acc)[3][J][V], int64_t
                         gr = dd_add(gr, dd_mul(G[3 * k + l], to_dd(c[l].x)));
                         gi = dd_add(gi, dd_mul(G[3 * k + l], to_dd(c[l].y)));
                     }
-                    out[k] = dd_zb_df(zr, zi, cl, gr, gi, to_dd(acc[k][j][v].x), to_dd(acc[k][j][v].y));
+                    out[k] = dd_zb_df(zr, zi, cl, gr, gi, to_dd(df_norm(acc[k][j][v].x)),
+                                         to_dd(df_norm(acc[k][j][v].y)));
                 }
             }
     } else if constexpr (is_f32<T>) {
