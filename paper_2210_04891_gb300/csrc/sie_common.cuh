@@ -31,6 +31,21 @@ template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
     return z;
 }
 template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
+// Complex double-float sums and differences leave the pair unnormalised: the
+// two-sum of the high parts is exact and its error joins the low parts, with no
+// renormalisation (every reader takes hi + lo as the value; products and stores
+// normalise).  In the FFT passes a value takes one such add per butterfly stage,
+// so its low part stays within a few units of the high part's last place.
+__host__ __device__ __forceinline__ df df_qadd(df a, df b) {
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    return df(s, ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo));
+}
+template <> __host__ __device__ __forceinline__ cdf cadd<cdf>(cdf a, cdf b) {
+    return cdf{df_qadd(a.x, b.x), df_qadd(a.y, b.y)};
+}
+template <> __host__ __device__ __forceinline__ cdf csub<cdf>(cdf a, cdf b) {
+    return cdf{df_qadd(a.x, -b.x), df_qadd(a.y, -b.y)};
+}
 // multiply by -i (forward) or +i (inverse)
 template <typename V> __device__ __forceinline__ V mul_mi(V a, bool inv) {
     V z;
