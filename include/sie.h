@@ -101,10 +101,10 @@ typedef struct {
                               convergence test) in FP64, the Arnoldi cycles in
                               the mixed form; 2 = the same with the residual
                               products b - Z x in double-float (SIE_PREC_DF;
-                              P^-1 and the norms stay FP64) and, where the
+                              the norms stay FP64) and, where the
                               preconditioner takes the narrow band route, its
-                              sweeps inside the cycles in double-float; 0 = all
-                              in the mixed form                                */
+                              sweeps (inside the cycles and in the tests'
+                              P^-1) in double-float; 0 = all in the mixed form */
 } sie_solve_opts;
 
 typedef struct {
