@@ -524,9 +524,9 @@ int pfft_convolve_lossy(pfft_plan *p, void *grid, int32_t nbatch, double omega, 
  * than 4 MiB is rejected with SIE_ERR_ARG.
  * Larger batches are processed in pieces that fit.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, with that device
- * current) and keeps it for the life of the process; make that first call
- * before any stream capture, and do not call this entry point on a device
- * after resetting it (cudaDeviceReset).  The call synchronises cuda_stream
+ * current) and keeps it with the id of the device's context; a later call in
+ * a new context (after cudaDeviceReset) looks it up again.  Make the first
+ * call on each device before any stream capture.  The call synchronises cuda_stream
  * before it returns.  All calls share the one array, so calls that overlap on
  * the GPU (other streams, other host threads) race and corrupt each other's
  * results; nothing in the array needs clearing between calls. */

@@ -725,8 +725,8 @@ int nd_solve(pfft_plan *p, const NdState *s, const C<T> *L, const int32_t *slot,
     if (smax > 180 * 1024)
         return fail(SIE_ERR_ARG, "preconditioner: a nested-dissection front of " + std::to_string(s->max_nf) +
                                      " unknowns exceeds the solve's shared memory");
-    SIE_CUDA(cudaFuncSetAttribute((const void *)k_nd_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax)));
-    SIE_CUDA(cudaFuncSetAttribute((const void *)k_nd_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax)));
+    if (int rc = set_smem((const void *)k_nd_fwd<T>, smax)) return rc;
+    if (int rc = set_smem((const void *)k_nd_bwd<T>, smax)) return rc;
     // each level's frontal vectors sized by its own largest front (the leaves are small:
     // more CTAs resident per SM)
     for (int32_t h = 0; h < H; ++h) {

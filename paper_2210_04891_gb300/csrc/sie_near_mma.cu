@@ -407,7 +407,7 @@ int near_mma_prepare(pfft_plan *p, const std::vector<int64_t> &near_ptr, const s
 
 int near_mma_launch(pfft_plan *p, int32_t R, cudaStream_t st) {
     if (R % 2) return fail(SIE_ERR_ARG, "tensor-core near field: the right-hand-side count must be even");
-    SIE_CUDA(cudaFuncSetAttribute(k_near_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)));
+    if (int rc = set_smem((const void *)k_near_mma, kSmemBytes)) return rc;
     int dev = 0, nsm = 0;
     SIE_CUDA(cudaGetDevice(&dev));
     SIE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

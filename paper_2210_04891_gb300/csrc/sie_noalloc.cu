@@ -12,6 +12,8 @@
 // exits.
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "sie_plan.h"
 
 using namespace sie;
@@ -27,22 +29,59 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};   // unique id of the context the address belongs to
 
-// Device address of the scratch array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// Unique id of the current device's context (cuCtxGetId, reached through the
+// runtime so that the library needs no link to the driver library), or 0 when
+// the driver cannot say.  A device reset retires the primary context and the
+// next runtime call creates a new one, with a new id, into which the module and
+// its array may load at another address.
+unsigned long long current_context_id() {
+    using GetCurrent = PFN_cuCtxGetCurrent_v4000;
+    using GetId = PFN_cuCtxGetId_v12000;
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f1);
+            get_id = reinterpret_cast<GetId>(f2);
+        }
+        (void)cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name is only a host-side stand-in, so the address is
+// looked up with cudaGetSymbolAddress (with that device current) the first time
+// a device is used and kept; it is looked up again when the device's context
+// has changed since (after cudaDeviceReset), or on every call if the context's
+// id cannot be read.
 int scratch_address(void **out) {
     int dev = 0;
     SIE_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(SIE_ERR_ARG, "pfft_convolve_noalloc: device index out of range");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             return fail(SIE_ERR_CUDA, std::string("pfft_convolve_noalloc: cudaGetSymbolAddress failed: ") +
                                           cudaGetErrorString(e));
         g_scratch_addr[dev] = ptr;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return SIE_OK;

@@ -891,12 +891,7 @@ template <typename T> int run_project(pfft_plan *p, int32_t R, cudaStream_t st) 
         // 32-wide slabs read each block record four times as often)
         if (p->n_pchunk > 0 && p->kt.proj_slab == kChunkRhs) {
             if (p->n_pchunk > INT32_MAX) return fail(SIE_ERR_ARG, "projection: too many node chunks");
-            static bool smem_set = false;   // the attribute is per function; set it once per process
-            if (!smem_set) {
-                SIE_CUDA(cudaFuncSetAttribute((const void *)k_project_tiled,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(kPTSmem)));
-                smem_set = true;
-            }
+            if (int rc = set_smem((const void *)k_project_tiled, kPTSmem)) return rc;
             const dim3 grid(unsigned(p->n_pchunk), unsigned((R + kChunkRhs - 1) / kChunkRhs));
             k_project_tiled<<<grid, 256, kPTSmem, st>>>(p->d_pch_node_ptr, p->d_pch_nodes, p->d_pch_tri_ptr,
                                                         p->d_pch_tri, p->d_pn_ptr, p->d_pn_rec32, p->d_pn_lcol,

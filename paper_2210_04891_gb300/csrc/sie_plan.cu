@@ -16,6 +16,8 @@
 #include <type_traits>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -409,11 +411,6 @@ __global__ void k_pack_near(const int32_t *__restrict__ col, const double *__res
     r32[e] = b;
 }
 
-int set_smem(const void *fn, size_t bytes) {
-    if (bytes > 48 * 1024) SIE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
-    return SIE_OK;
-}
-
 bool is_pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
 
 // Forward 3-D DFT of a full padded complex array hc [Mx][My][Mz] (the kernel
@@ -459,6 +456,28 @@ int kernel_fft3(pfft_plan *p, double2 *hc, double2 **out, cudaStream_t s) {
 }  // namespace
 
 namespace sie {
+
+// The dynamic shared-memory limit is an attribute of the function on a device,
+// shared by every plan and host thread, while the bytes a launch needs can
+// differ from plan to plan (band widths, front sizes, plane sizes).  So the
+// limit is only ever raised, under a lock: a plan needing less can never lower
+// it between another thread's setting and that thread's launch.  It is raised
+// for requests below 48 KB too: the default limit is 48 KB less the kernel's
+// static shared memory.
+int set_smem(const void *fn, size_t bytes) {
+    int dev = 0;
+    SIE_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> limit;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = limit[std::make_pair(fn, dev)];
+    if (bytes > cur) {
+        SIE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+        cur = bytes;
+    }
+    return SIE_OK;
+}
+
 
 // FFT convolution of ngrids grids [Nx][Ny][Nz] (in `grid`, overwritten with
 // the result) through the buffer `spec` [ngrids][Mx][Ny][Nz]: x pencils

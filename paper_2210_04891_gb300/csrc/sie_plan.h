@@ -203,6 +203,8 @@ struct StageTimer {
     }
 };
 int plan_alloc(pfft_plan *p, void **ptr, size_t bytes);
+// raise a kernel's dynamic shared-memory limit to at least bytes (thread-safe, never lowers it)
+int set_smem(const void *fn, size_t bytes);
 void plan_free(pfft_plan *p, void *ptr);
 void plan_free_precond(pfft_plan *p);
 int scratch_reserve(pfft_plan *p, int32_t nrhs, int prec);

@@ -13,7 +13,7 @@ template <int MY, int MZ>
 int launch_plane(pfft_plan *p, float2 *spec, int32_t ngrids, int lgMx, cudaStream_t s) {
     using G = plane::Geo<MY, MZ>;
     auto kern = plane::k_plane_conv<MY, MZ>;
-    SIE_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::kSmem)));
+    if (int rc = set_smem((const void *)kern, G::kSmem)) return rc;
     int nsm = 0;
     SIE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
     // grids per CTA: up to 8 (the staged spectrum and twiddles serve each of

@@ -1226,8 +1226,7 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
                                                                        s->nunk, p->nb, R, u);
             SIE_LAUNCH_CHECK(p);
             const size_t sm = size_t(4) * pc_nbuf<T>() * PC_TILE * sizeof(C<T>);
-            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(sm)));
+            if (int rc = set_smem((const void *)k_pc_sweep<T>, sm)) return rc;
             k_pc_sweep<T><<<nblk_(int64_t(R) * nblk * 32, 128), 128, sm, st>>>(
                 s->d_blk_off, s->d_tile_off, nblk, s->nunk, s->nchunks, s->d_tiledf, s->d_dinvdf, s->d_slot, R, u);
             SIE_LAUNCH_CHECK(p);
@@ -1247,8 +1246,7 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
             SIE_LAUNCH_CHECK(p);
             // four warps per CTA, pc_nbuf tiles of shared memory per warp
             const size_t sm = size_t(4) * pc_nbuf<T>() * PC_TILE * sizeof(C<T>);
-            SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(sm)));
+            if (int rc = set_smem((const void *)k_pc_sweep<T>, sm)) return rc;
             const C<T> *tiles, *dinv;
             if constexpr (f32) { tiles = s->d_tile32; dinv = s->d_dinv32; } else { tiles = s->d_tile64; dinv = s->d_dinv64; }
             k_pc_sweep<T><<<nblk_(int64_t(R) * nblk * 32, 128), 128, sm, st>>>(
@@ -1262,14 +1260,12 @@ int pc_apply_t(pfft_plan *p, const double2 *y, double2 *z, int32_t R, cudaStream
             while (S < s->W + 32) S *= 2;
             const size_t sm = size_t(S + 32 * 33 + 32) * sizeof(C<T>);
             if (wt <= 256) {
-                SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep_blk<T, 256>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+                if (int rc = set_smem((const void *)k_pc_sweep_blk<T, 256>, sm)) return rc;
                 k_pc_sweep_blk<T, 256><<<unsigned(int64_t(R) * nblk), wt, sm, st>>>(
                     kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, S, s->nunk, p->nb, band,
                     bandc, s->d_slot, u);
             } else {
-                SIE_CUDA(cudaFuncSetAttribute((const void *)k_pc_sweep_blk<T, 1024>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+                if (int rc = set_smem((const void *)k_pc_sweep_blk<T, 1024>, sm)) return rc;
                 k_pc_sweep_blk<T, 1024><<<unsigned(int64_t(R) * nblk), wt, sm, st>>>(
                     kappa, s->d_row_ptr, s->d_row_br, s->d_row_sg, s->d_blk_off, nblk, s->W, S, s->nunk, p->nb, band,
                     bandc, s->d_slot, u);
