@@ -148,27 +148,53 @@ __global__ void __launch_bounds__(1024) k_scan_rows(E *buf, int64_t n) {
 
 // Tour values for A^T: at node v's enter slot the current the links inject
 // into v (+x on links entering v, -x on links leaving it); 0 at exit slots.
-// Grid (slots, right-hand sides).
+// Grid (slots, right-hand-side groups): a thread takes one slot and kTourRc
+// right-hand sides, so the slot's index chain (node, link list, loops) is read
+// once for the group and the group's loads of x are independent.
+constexpr int kTourRc = 8;
 template <typename E>
 __global__ void k_tour_inject(const double2 *__restrict__ x, int64_t nl, E *__restrict__ tour, int64_t nslots,
                               const int32_t *__restrict__ tour_node, const int8_t *__restrict__ tour_enter,
                               const int32_t *__restrict__ nl_ptr, const int32_t *__restrict__ nl_loop,
-                              const int8_t *__restrict__ nl_sign) {
+                              const int8_t *__restrict__ nl_sign, int32_t nrhs) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nslots) return;
-    const int64_t r = blockIdx.y;
-    E out = ezero<E>();
+    const int32_t r0 = int32_t(blockIdx.y) * kTourRc;
+    const int nr = min(kTourRc, nrhs - r0);
     const int v = tour_node[s];
-    if (tour_enter[s] && nl_ptr[v] < nl_ptr[v + 1]) {
-        const double2 *xr = x + r * nl;
-        double2 acc = make_double2(0.0, 0.0);   // a few link currents, exact inputs
-        for (int k = nl_ptr[v]; k < nl_ptr[v + 1]; ++k) {
-            const double2 xv = xr[nl_loop[k]];
-            acc = nl_sign[k] > 0 ? cadd(acc, xv) : csub(acc, xv);
-        }
-        eset(out, acc);
+    int32_t k0 = 0, k1 = 0;
+    if (tour_enter[s]) {
+        k0 = nl_ptr[v];
+        k1 = nl_ptr[v + 1];
     }
-    tour[r * nslots + s] = out;
+    if (k1 <= k0) {   // no link at this slot (most slots): zeros, no FP64 work
+#pragma unroll
+        for (int j = 0; j < kTourRc; ++j)
+            if (j < nr) tour[int64_t(r0 + j) * nslots + s] = ezero<E>();
+        return;
+    }
+    double2 acc[kTourRc];   // a few link currents, exact inputs
+#pragma unroll
+    for (int j = 0; j < kTourRc; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int32_t k = k0; k < k1; ++k) {
+        const double2 *xl = x + int64_t(r0) * nl + nl_loop[k];
+        const bool pos = nl_sign[k] > 0;
+#pragma unroll
+        for (int j = 0; j < kTourRc; ++j)
+            if (j < nr) {
+                const double2 xv = xl[int64_t(j) * nl];
+                acc[j] = pos ? cadd(acc[j], xv) : csub(acc[j], xv);
+            }
+    }
+    // the conversion to the tour's element (double-float pairs in the mixed
+    // form) runs on the FP64 pipe: only here, on the slots that carry links
+#pragma unroll
+    for (int j = 0; j < kTourRc; ++j)
+        if (j < nr) {
+            E out;
+            eset(out, acc[j]);
+            tour[int64_t(r0 + j) * nslots + s] = out;
+        }
 }
 
 // Branch current of branch b for right-hand side r (loop space): a link carries
@@ -683,22 +709,28 @@ __global__ void k_branch_out(const E *__restrict__ y_tri, const int32_t *__restr
 
 // Tour values for A: +delta(v) at v's enter slot, -delta(v) at its exit slot,
 // delta(v) = voltage of v's parent twig walked from v towards the root.
-// Grid (slots, right-hand sides).
+// Grid (slots, right-hand-side groups of kTourRc), as k_tour_inject.
 template <typename E>
 __global__ void k_tour_voltage(const E *__restrict__ y_br, int64_t ldy, E *__restrict__ tour, int64_t nslots,
                                const int32_t *__restrict__ tour_node, const int8_t *__restrict__ tour_enter,
-                               const int32_t *__restrict__ parent_branch, const int32_t *__restrict__ tail) {
+                               const int32_t *__restrict__ parent_branch, const int32_t *__restrict__ tail,
+                               int32_t nrhs) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nslots) return;
-    const int64_t r = blockIdx.y;
+    const int32_t r0 = int32_t(blockIdx.y) * kTourRc;
+    const int nr = min(kTourRc, nrhs - r0);
     const int v = tour_node[s];
     const int t = parent_branch[v];
-    E d = ezero<E>();
-    if (t >= 0) {
-        d = y_br[r * ldy + t];
-        if ((tail[t] != v) != !tour_enter[s]) d = eneg(d);
+    const bool neg = t >= 0 && ((tail[t] != v) != !tour_enter[s]);
+    E d[kTourRc];
+#pragma unroll
+    for (int j = 0; j < kTourRc; ++j) {
+        d[j] = ezero<E>();
+        if (t >= 0 && j < nr) d[j] = y_br[int64_t(r0 + j) * ldy + t];
     }
-    tour[r * nslots + s] = d;
+#pragma unroll
+    for (int j = 0; j < kTourRc; ++j)
+        if (j < nr) tour[int64_t(r0 + j) * nslots + s] = neg ? eneg(d[j]) : d[j];
 }
 
 template <typename E>
@@ -929,9 +961,8 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     E *y_tri = (E *)s.y_tri, *y_br = (E *)s.y_br;
     std::unique_ptr<StageTimer> tm(new StageTimer(p, SIE_STAGE_LOOP_TO_BRANCH, st));
     if (space == SIE_SPACE_LOOP) {
-        k_tour_inject<<<dim3(nblk(nslots), unsigned(R)), 256, 0, st>>>(x, p->nl, tour, nslots, p->d_tour_node,
-                                                                         p->d_tour_enter, p->d_nl_ptr, p->d_nl_loop,
-                                                                         p->d_nl_sign);
+        k_tour_inject<<<dim3(nblk(nslots), unsigned((R + kTourRc - 1) / kTourRc)), 256, 0, st>>>(
+            x, p->nl, tour, nslots, p->d_tour_node, p->d_tour_enter, p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign, R);
         SIE_LAUNCH_CHECK(p);
         k_scan_rows<E><<<R, 1024, 0, st>>>(tour, nslots);
         SIE_LAUNCH_CHECK(p);
@@ -987,8 +1018,8 @@ int matvec_t(pfft_plan *p, const double2 *x, double2 *y, int32_t R, int space, c
     k_branch_out<E, E><<<nblk(ldy * R), 256, 0, st>>>(y_tri, p->d_br_tri, p->d_br_local, p->nt, p->nb, ldy, R,
                                                         y_br);
     SIE_LAUNCH_CHECK(p);
-    k_tour_voltage<E><<<dim3(nblk(nslots), unsigned(R)), 256, 0, st>>>(y_br, ldy, tour, nslots, p->d_tour_node,
-                                                                       p->d_tour_enter, p->d_parent_branch, p->d_tail);
+    k_tour_voltage<E><<<dim3(nblk(nslots), unsigned((R + kTourRc - 1) / kTourRc)), 256, 0, st>>>(
+        y_br, ldy, tour, nslots, p->d_tour_node, p->d_tour_enter, p->d_parent_branch, p->d_tail, R);
     SIE_LAUNCH_CHECK(p);
     k_scan_rows<E><<<R, 1024, 0, st>>>(tour, nslots);
     SIE_LAUNCH_CHECK(p);
@@ -1129,10 +1160,11 @@ extern "C" int sie_postprocess(pfft_plan *p, const void *x, int32_t nrhs, const 
         vb = tmp_v;
     }
     double2 *tour = static_cast<double2 *>(p->scr.tour);
-    const dim3 gs(nblk(nslots), unsigned(R)), gb(nblk(nb), unsigned(R)), gt(nblk(nt), unsigned(R));
+    const dim3 gs(nblk(nslots), unsigned((R + kTourRc - 1) / kTourRc)), gb(nblk(nb), unsigned(R)),
+        gt(nblk(nt), unsigned(R));
     // branch currents: alpha = A^T x through the tour prefix sums (FP64)
     k_tour_inject<double2><<<gs, 256, 0, st>>>(static_cast<const double2 *>(x), p->nl, tour, nslots, p->d_tour_node,
-                                               p->d_tour_enter, p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign);
+                                               p->d_tour_enter, p->d_nl_ptr, p->d_nl_loop, p->d_nl_sign, R);
     k_scan_rows<double2><<<unsigned(R), 1024, 0, st>>>(tour, nslots);
     k_branch_alpha<<<gb, 256, 0, st>>>(static_cast<const double2 *>(x), p->nl, tour, nslots, p->d_loop_of_branch,
                                        p->d_twig_node, p->d_head, p->d_enter, p->d_exit, nb, alpha);
@@ -1144,7 +1176,7 @@ extern "C" int sie_postprocess(pfft_plan *p, const void *x, int32_t nrhs, const 
     }
     if (phi) {   // potentials: root-path sums of the twig drops, minus the reference node's
         k_tour_voltage<double2><<<gs, 256, 0, st>>>(vb, nb, tour, nslots, p->d_tour_node, p->d_tour_enter,
-                                                     p->d_parent_branch, p->d_tail);
+                                                     p->d_parent_branch, p->d_tail, R);
         k_scan_rows<double2><<<unsigned(R), 1024, 0, st>>>(tour, nslots);
         k_panel_phi<<<gt, 256, 0, st>>>(tour, nslots, p->d_panel_slot, p->d_panel_ref, nt,
                                         static_cast<double2 *>(phi));
