@@ -55,6 +55,29 @@ def test_loop_basis_matches_oracle(make):
     assert L.stats["n_loops"] == L.stats["n_branches"] - L.stats["n_nodes"] + L.stats["n_comp"] + L.stats["n_ports"]
 
 
+@pytest.mark.parametrize("name", ["bondwires_8x2mm_40k", "pdn_2x10mm_500k"])
+def test_loop_basis_matches_oracle_at_full_size(name):
+    # the bond-wire array (40,192 triangles, 20,096 loops) and the plane pair with its vias
+    # (516,800 triangles, 258,373 loops): integer work, so bit for bit: branch list, component
+    # and node counts, and every signed entry of A (compared as sorted CSR matrices)
+    import scipy.sparse as sp
+    m = synth.WORKLOADS[name]()["mesh"]
+    L = api.Loops(api.Mesh.from_synth(m), m.ports)
+    O = build_loops(m)
+    assert (L.nl, L.nb) == (O.nl, O.nb)
+    assert L.stats["n_comp"] == O.n_comp and L.stats["n_nodes"] == O.n_nodes
+    rp, col, val, br = L.export()
+    assert np.array_equal(br, O.br_tri)
+    G = sp.csr_matrix((np.asarray(val, dtype=np.int64), np.asarray(col), np.asarray(rp)), shape=O.A.shape)
+    A = sp.csr_matrix(O.A, dtype=np.int64)
+    G.sort_indices()
+    A.sort_indices()
+    assert np.array_equal(G.indptr, A.indptr)
+    assert np.array_equal(G.indices, A.indices)
+    assert np.array_equal(G.data, A.data)
+    assert set(np.unique(G.data).tolist()) <= {-1, 1}
+
+
 def test_error_codes():
     m = synth.tiny_two_bars()
     M = api.Mesh.from_synth(m)
