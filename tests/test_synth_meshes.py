@@ -51,3 +51,30 @@ def test_meander_workload_sizes():
         assert 4e3 <= w["mesh"].nt <= 7e4
         assert all(4 <= g <= 256 and g & (g - 1) == 0 for g in w["grid"])
         assert len(w["freqs"]) == 32
+
+
+@pytest.mark.parametrize("name,nt,nl,nports,grid,nf,f0,f1,genus", [
+    ("bar_1000x20x10um_1.5k", 1508, None, 1, (64, 16, 16), 1, 1e9, 1e9, 0),
+    ("bondwires_8x2mm_40k", 40192, 20096, 8, (128, 64, 32), 16, 1e6, 1e10, 0),
+    ("pdn_2x10mm_500k", 516800, 258373, 4, (256, 256, 32), 8, 1e6, 1e9, 399),
+])
+def test_named_workloads_follow_their_recipe(name, nt, nl, nports, grid, nf, f0, f1, genus):
+    # the sizes the input recipe states and the bench lines are quoted on: triangles,
+    # loops (from the host loop basis), ports, grid, log-spaced frequencies, and the
+    # surface topology (every wire and the bar closed genus 0; the plane pair one
+    # closed surface with a handle per via but one)
+    from paper_2210_04891_gb300 import api
+    w = synth.WORKLOADS[name]()
+    m = w["mesh"]
+    assert m.nt == nt and len(m.ports) == nports and tuple(w["grid"]) == grid
+    f = np.asarray(w["freqs"])
+    assert f.size == nf and np.isclose(f[0], f0) and np.isclose(f[-1], f1)
+    if nf > 2:
+        assert np.allclose(np.diff(np.log(f)), np.log(f1 / f0) / (nf - 1))
+    counts, directed, chi, vol = topology(m)
+    assert counts == {2} and directed and vol > 0
+    ncomp = 8 if name.startswith("bondwires") else 1
+    assert (2 * ncomp - chi) // 2 == genus
+    if nl is not None:
+        L = api.Loops(api.Mesh.from_synth(m), m.ports)
+        assert L.nl == nl
